@@ -1,0 +1,456 @@
+"""Pins of the oracle against what the paper and mathematics fix (no GPU).
+
+Each test checks oracle/dense.py or oracle/matfree.c against an independent
+fact: a closed form, an exact identity, brute force on a tiny case, a library
+routine reached by a different route, or a number the paper prints
+(tests/golden/paper_numbers.json).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dense as D
+from oracle import matfree as MF
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_numbers.json")))
+
+
+def rng(seed=0):
+    return np.random.default_rng(seed)
+
+
+# ---------------------------------------------------------------- P1 free fermions
+@pytest.mark.parametrize("L", [4, 6])
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_free_fermion_logdet_exact_kinetic(L, mu):
+    """x = 0, exact kinetic: det M = prod_k (1 + e^{-beta (eps_k - mu)}) with
+    eps_k = -2t(cos kx + cos ky) (Eq. (detM_alt) for free fermions)."""
+    m = D.Model(L=L, Ltau=10, mu=mu, kinetic="exact")
+    x = np.zeros((m.Ltau, m.N))
+    ks = 2 * np.pi * np.arange(L) / L
+    eps = np.array([-2 * m.t * (np.cos(kx) + np.cos(ky)) for kx in ks for ky in ks])
+    ref = np.sum(np.log1p(np.exp(-m.beta * (eps - m.mu))))
+    assert abs(D.logdet_M(m, x) - ref) < 1e-11
+
+
+def test_checkerboard_exact_at_L4_and_second_order():
+    """At L = 4 the two x-colours (and the two y-colours) commute, so the
+    checkerboard product equals exp(-dtau K) exactly; at L = 8 the error is
+    O(dtau^2) (halving dtau quarters it) (Sec. II D)."""
+    m4 = D.Model(L=4, Ltau=4)
+    ex = D.kinetic_propagator(D.Model(L=4, Ltau=4, kinetic="exact"))
+    assert np.abs(D.kinetic_propagator(m4) - ex).max() < 1e-14
+    errs = []
+    for dt in (0.1, 0.05):
+        a = D.kinetic_propagator(D.Model(L=8, Ltau=4, dtau=dt))
+        b = D.kinetic_propagator(D.Model(L=8, Ltau=4, dtau=dt, kinetic="exact"))
+        errs.append(np.abs(a - b).max())
+    assert 3.6 < errs[0] / errs[1] < 4.4
+
+
+def test_checkerboard_factors_spectrum_and_transpose():
+    """Each colour is symmetric with eigenvalues exp(+-dtau t) (N/2 each), and
+    C^T = C1 C2 C3 C4."""
+    m = D.Model(L=6, Ltau=4, t=1.3)
+    Cs = D.checkerboard_factors(m)
+    for C in Cs:
+        assert np.allclose(C, C.T)
+        ev = np.sort(np.linalg.eigvalsh(C))
+        ref = np.sort([np.exp(-m.dtau * m.t)] * (m.N // 2) + [np.exp(m.dtau * m.t)] * (m.N // 2))
+        assert np.abs(ev - ref).max() < 1e-13
+    C1, C2, C3, C4 = Cs
+    assert np.abs(D.kinetic_propagator(m).T - C1 @ C2 @ C3 @ C4).max() < 1e-14
+
+
+def test_free_fermion_checkerboard_close_to_exact():
+    m = D.Model(L=8, Ltau=10)
+    x = np.zeros((m.Ltau, m.N))
+    me = D.Model(L=8, Ltau=10, kinetic="exact")
+    assert abs(D.logdet_M(m, x) - D.logdet_M(me, x)) < 0.05
+
+
+# ---------------------------------------------------------------- P2 particle-hole
+@pytest.mark.parametrize("kinetic", ["exact", "checkerboard"])
+def test_particle_hole_logdet(kinetic):
+    """mu = 0, bipartite lattice: log det M(-x) - log det M(x) = dtau alpha sum x,
+    so |det A(-x)| = |det A(x)| with det Lambda^2 = e^{dtau alpha sum x}
+    (Eqs. (Z_path_orig), (Lambda_constraint))."""
+    m = D.Model(L=4, Ltau=8, alpha=1.3, kinetic=kinetic)
+    x = rng(1).standard_normal((m.Ltau, m.N))
+    lhs = D.logdet_M(m, -x) - D.logdet_M(m, x)
+    assert abs(lhs - m.dtau * m.alpha * x.sum()) < 1e-11
+    s, la = np.linalg.slogdet(D.A_matrix(m, x))
+    s2, la2 = np.linalg.slogdet(D.A_matrix(m, -x))
+    assert abs(la - la2) < 1e-11
+
+
+def test_lambda_determinant_and_inverse():
+    """det Lambda^2 = exp(dtau alpha sum x) (Eq. (Lambda_constraint)) and
+    Eq. (Lambda_inv) is the inverse of Eq. (Lambda_def)."""
+    m = D.Model(L=4, Ltau=6, alpha=0.7)
+    x = rng(2).standard_normal((m.Ltau, m.N))
+    Lm, Li = D.Lambda(m, x), D.Lambda_inv(m, x)
+    assert np.abs(Lm @ Li - np.eye(m.n)).max() < 1e-13
+    s, ld = np.linalg.slogdet(Lm)
+    assert abs(2 * ld - m.dtau * m.alpha * x.sum()) < 1e-11
+
+
+# ---------------------------------------------------------------- P3 t = 0
+def test_atomic_limit_logdet():
+    """t = 0: det M = prod_i (1 + exp(-dtau sum_tau (alpha x_{i,tau} - mu)))
+    (single-site form of Sec. IV, Eq. (detM_alt))."""
+    m = D.Model(L=4, Ltau=8, t=0.0, mu=0.2, alpha=1.1)
+    x = rng(3).standard_normal((m.Ltau, m.N))
+    ref = np.sum(np.log1p(np.exp(-m.dtau * np.sum(m.alpha * x - m.mu, axis=0))))
+    assert abs(D.logdet_M(m, x) - ref) < 1e-12
+
+
+def test_single_site_adiabatic_reflection_symmetry():
+    """t = 0, mu = 0, x constant in tau: D_x = D_{-x} (App. B, Eq. (A_x)), so
+    S_F(xbar, Phi) = S_F(-xbar, Phi) for any Phi."""
+    m = D.Model(L=4, Ltau=6, t=0.0, alpha=1.4)
+    xbar = rng(4).standard_normal(m.N)
+    x = np.tile(xbar, (m.Ltau, 1))
+    Phi = rng(5).standard_normal((2, m.Ltau, m.N))
+    assert abs(D.S_F(m, x, Phi) - D.S_F(m, -x, Phi)) < 1e-11 * abs(D.S_F(m, x, Phi))
+
+
+# ---------------------------------------------------------------- P4 S_F at x0
+def test_SF_at_sampling_point_and_solution():
+    """Phi = A(x0)^T R gives S_F(x0, Phi) = |R|^2 / 2 (Sec. II D) and
+    v = (M^T M)^{-1} Lambda^{-T} Phi = M^{-1} R."""
+    m = D.Model(L=4, Ltau=8, alpha=1.2)
+    x = rng(6).standard_normal((m.Ltau, m.N))
+    R = rng(7).standard_normal((2, m.Ltau, m.N))
+    Phi = D.phi_from_R(m, x, R)
+    assert abs(D.S_F(m, x, Phi) - 0.5 * np.sum(R * R)) < 1e-10
+    b = D.b_from_phi(m, x, Phi[0])
+    assert np.abs(b - D.MT_apply(m, x, R[0])).max() < 1e-12
+    v = D.solve_MTM(m, x, b)
+    assert np.abs(D.M_apply(m, x, v) - R[0]).max() < 1e-12
+
+
+# ---------------------------------------------------------------- P5 forces
+def test_force_matches_finite_differences():
+    """dS_F/dx (Eq. (dSF_dx)) against central differences of S_F at fixed Phi."""
+    m = D.Model(L=4, Ltau=8, alpha=1.2)
+    g = rng(8)
+    x = g.standard_normal((m.Ltau, m.N))
+    Phi = D.phi_from_R(m, x + 0.3 * g.standard_normal(x.shape), g.standard_normal((2, m.Ltau, m.N)))
+    F = D.dSF_dx(m, x, Phi)
+    h = 1e-5
+    for _ in range(12):
+        tau, i = g.integers(m.Ltau), g.integers(m.N)
+        xp, xm = x.copy(), x.copy()
+        xp[tau, i] += h
+        xm[tau, i] -= h
+        fd = (D.S_F(m, xp, Phi) - D.S_F(m, xm, Phi)) / (2 * h)
+        assert abs(fd - F[tau, i]) < 1e-7 * max(1.0, abs(F[tau, i]))
+
+
+def test_force_structured_equals_fully_dense():
+    m = D.Model(L=4, Ltau=5, alpha=0.9)
+    g = rng(9)
+    x = g.standard_normal((m.Ltau, m.N))
+    Phi = g.standard_normal((2, m.Ltau, m.N))
+    F = D.dSF_dx(m, x, Phi)
+    comps = [(0, 0), (0, 7), (1, 3), (4, 15), (2, 9)]
+    ref = D.dSF_dx_fully_dense(m, x, Phi, comps)
+    assert np.abs(ref - np.array([F[c] for c in comps])).max() < 1e-12
+
+
+def test_force_phi_average_is_logdet_derivative():
+    """Phi ~ N(0, A^T A): E[dS_F,sigma/dx] = -d ln|det M|/dx - dtau alpha / 2.
+    Exact (no sampling): sum over Phi_k = A^T e_k for all unit vectors e_k,
+    since sum_k e_k e_k^T = I; right side by central differences of slogdet."""
+    m = D.Model(L=4, Ltau=4, alpha=1.1)
+    g = rng(10)
+    x = g.standard_normal((m.Ltau, m.N))
+    A = D.A_matrix(m, x)
+    Phis = A.T @ np.eye(m.n)          # column k = A^T e_k
+    Phis = Phis.T.reshape(m.n, m.Ltau, m.N)
+    F = D.dSF_dx(m, x, Phis)          # sums over the "pseudofermions"
+    h = 1e-5
+    for (tau, i) in [(0, 0), (1, 5), (3, 15), (2, 8)]:
+        xp, xm = x.copy(), x.copy()
+        xp[tau, i] += h
+        xm[tau, i] -= h
+        dld = (D.logdet_M(m, xp) - D.logdet_M(m, xm)) / (2 * h)
+        assert abs(F[tau, i] - (-dld - 0.5 * m.dtau * m.alpha)) < 1e-7
+
+
+def test_bosonic_force_finite_differences():
+    m = D.Model(L=4, Ltau=12, omega0=0.7)
+    x = rng(11).standard_normal((m.Ltau, m.N))
+    F = D.dSB_dx(m, x)
+    h = 1e-5
+    for (tau, i) in [(0, 0), (11, 3), (5, 9)]:
+        xp, xm = x.copy(), x.copy()
+        xp[tau, i] += h
+        xm[tau, i] -= h
+        assert abs((D.S_B(m, xp) - D.S_B(m, xm)) / (2 * h) - F[tau, i]) < 1e-6
+
+
+# ---------------------------------------------------------------- P6 / P7 Fourier
+def test_Q_fourier_equals_stencil():
+    """Qx = F^{-1} Qtilde F x equals the stencil of Eq. (dSB_dx)."""
+    m = D.Model(L=4, Ltau=20, omega0=0.8)
+    x = rng(12).standard_normal((m.Ltau, m.N))
+    assert np.abs(D.Q_apply(m, x) - D.dSB_dx(m, x)).max() < 1e-12
+
+
+def test_Q_extremes_and_ratio():
+    """Qtilde/dtau = omega0^2 at omega = 0 and omega0^2 + 4/dtau^2 at
+    omega = Ltau/2 (Sec. III B)."""
+    m = D.Model(L=4, Ltau=40, omega0=0.5)
+    q = D.Q_tilde(m) / m.dtau
+    assert abs(q[0] - m.omega0 ** 2) < 1e-12
+    assert abs(q[m.Ltau // 2] - (m.omega0 ** 2 + 4 / m.dtau ** 2)) < 1e-9
+    assert abs(q.max() / q.min() - (1 + 4 / (m.omega0 ** 2 * m.dtau ** 2))) < 1e-9
+
+
+def test_fourier_acceleration_dt_ratio():
+    """Paper: dt = 1e-2 with m_reg = omega0 and dt = 7.05e-4 with m_reg = inf
+    give the top mode omega = Ltau/2 the same time scale."""
+    gd = GOLD["dt_equal_top_mode"]
+    m = D.Model(L=4, Ltau=40, omega0=gd["omega0"], dtau=gd["dtau"])
+    w = m.Ltau // 2
+    Om1 = np.sqrt(D.Q_tilde(m)[w] / D.mass_tilde(m, m.omega0)[w])
+    Oinf = np.sqrt(D.Q_tilde(m)[w] / D.mass_tilde(m, np.inf)[w])
+    dt_inf = gd["dt_mreg_omega0"] * Om1 / Oinf
+    assert abs(dt_inf - gd["dt_mreg_inf"]) < 0.005e-4
+
+
+def test_mass_operator_powers():
+    """Mass^{1/2} Mass^{1/2} = Mass and Mass Mass^{-1} = I along tau; the mass
+    is constant dtau when m_reg = inf (Sec. III B 1)."""
+    m = D.Model(L=4, Ltau=16)
+    p = rng(13).standard_normal((m.Ltau, m.N))
+    h = D.mass_apply(m, D.mass_apply(m, p, 1.0, 0.5), 1.0, 0.5)
+    assert np.abs(h - D.mass_apply(m, p, 1.0, 1.0)).max() < 1e-12
+    assert np.abs(D.mass_apply(m, D.mass_apply(m, p, 1.0, -1.0), 1.0, 1.0) - p).max() < 1e-12
+    assert np.abs(D.mass_apply(m, p, np.inf, 1.0) - m.dtau * p).max() < 1e-14
+
+
+# ---------------------------------------------------------------- P12 leapfrog
+def test_leapfrog_reversible():
+    m = D.Model(L=4, Ltau=8, alpha=1.0)
+    g = rng(14)
+    x = g.standard_normal((m.Ltau, m.N))
+    Phi = D.phi_from_R(m, x, g.standard_normal((2, m.Ltau, m.N)))
+    p = D.mass_apply(m, g.standard_normal((m.Ltau, m.N)), 1.0, 0.5)
+    x1, p1 = D.leapfrog_split(m, x, p, Phi, 0.02, 4, 3, 1.0)
+    x2, p2 = D.leapfrog_split(m, x1, -p1, Phi, 0.02, 4, 3, 1.0)
+    assert np.abs(x2 - x).max() < 1e-11
+    assert np.abs(p2 + p).max() < 1e-10
+
+
+def test_leapfrog_energy_error_second_order():
+    """|dH| scales as dt^2 at fixed trajectory length."""
+    m = D.Model(L=4, Ltau=8, alpha=1.0)
+    g = rng(15)
+    x = g.standard_normal((m.Ltau, m.N))
+    R = g.standard_normal((2, m.Ltau, m.N))
+    Rp = g.standard_normal((m.Ltau, m.N))
+    dH = []
+    for dt, Nt in ((0.04, 5), (0.02, 10)):
+        _, _, Hi, Hf = D.hmc_update(m, x, R, Rp, dt, Nt, 2, 1.0)
+        dH.append(abs(Hf - Hi))
+    assert 3.0 < dH[0] / dH[1] < 5.0
+
+
+def test_harmonic_modes_without_fermions():
+    """alpha = 0: S = S_B and every Fourier mode of x is a harmonic oscillator
+    of frequency sqrt(Qtilde/Mass~); leapfrog follows it to O(dt^2)."""
+    m = D.Model(L=4, Ltau=16, alpha=0.0, omega0=1.0)
+    g = rng(16)
+    x0 = g.standard_normal((m.Ltau, m.N))
+    Phi = np.zeros((1, m.Ltau, m.N))
+    p0 = np.zeros_like(x0)
+    dt, Nt, nt = 0.01, 50, 2
+    x1, _ = D.leapfrog_split(m, x0, p0, Phi, dt, Nt, nt, 1.0)
+    Om = np.sqrt(D.Q_tilde(m) / D.mass_tilde(m, 1.0))
+    F = D.fourier_matrix(m.Ltau)
+    ref = (F.conj().T @ (np.cos(Om * dt * Nt)[:, None] * (F @ x0))).real
+    assert np.abs(x1 - ref).max() < 5e-3 * np.abs(x0).max()
+
+
+# ---------------------------------------------------------------- P8-P10 preconditioner
+def test_precond_block_diagonal_in_U_basis():
+    """U P U^dag is block diagonal with blocks I - e^{-i phi_omega} Bbar
+    (Eqs. (Mww), (P_block))."""
+    m = D.Model(L=4, Ltau=6)
+    x = rng(17).standard_normal((m.Ltau, m.N))
+    N, T = m.N, m.Ltau
+    UU = np.kron(D.U_matrix(T), np.eye(N))
+    Pt = UU @ D.precond_matrix(m, x) @ UU.conj().T
+    Bb = D.Bbar(m, x)
+    for w in range(T):
+        for w2 in range(T):
+            blk = Pt[w * N:(w + 1) * N, w2 * N:(w2 + 1) * N]
+            ref = np.eye(N) - np.exp(-1j * D.phi_omega(T, w)) * Bb if w == w2 else 0.0
+            assert np.abs(blk - ref).max() < 1e-13
+
+
+def test_precond_exact_in_adiabatic_limit():
+    """x constant in tau: P = M (Sec. VI B), so PCG with the exact-enough KPM
+    inverse converges in very few iterations."""
+    m = D.Model(L=4, Ltau=8)
+    xc = np.tile(rng(18).standard_normal(m.N), (m.Ltau, 1))
+    assert np.abs(D.precond_matrix(m, xc) - D.fermion_matrix(m, xc)).max() < 1e-15
+    b = rng(19).standard_normal((m.Ltau, m.N))
+    _, it_exact = D.pcg(m, xc, b, tol=1e-10, precond=True, a1=16, a2=16)
+    assert it_exact <= 2
+    _, it1 = D.pcg(m, xc, b, tol=1e-10, precond=True)
+    _, it0 = D.pcg(m, xc, b, tol=1e-10, precond=False)
+    assert it0 > 2 * it1
+
+
+def test_kpm_converges_to_lu_inverse():
+    """With growing order (a1 = a2 -> large) the KPM P^{-1} v approaches the LU
+    solve of Eq. (P_def)."""
+    m = D.Model(L=4, Ltau=8)
+    x = rng(20).standard_normal((m.Ltau, m.N))
+    v = rng(21).standard_normal((m.Ltau, m.N))
+    ref = np.linalg.solve(D.precond_matrix(m, x), v.reshape(-1)).reshape(m.Ltau, m.N)
+    errs = [np.abs(D.precond_inverse_apply(m, x, v, a1=a, a2=a) - ref).max() for a in (1, 4, 16)]
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-12
+
+
+def test_kpm_transpose_is_exact_transpose():
+    m = D.Model(L=4, Ltau=8)
+    g = rng(22)
+    x = g.standard_normal((m.Ltau, m.N))
+    v, w = g.standard_normal((2, m.Ltau, m.N))
+    lhs = np.sum(w * D.precond_inverse_apply(m, x, v))
+    rhs = np.sum(v * D.precond_inverse_apply(m, x, w, trans=True))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_kpm_mirror_half_is_conjugate():
+    """f_{T-1-omega} = conj(f_omega) on real b (App. C B): coefficients
+    computed directly at phi_{T-1-omega} are the conjugates."""
+    T = 40
+    for w in (0, 3, 11):
+        c = D.chebyshev_coeffs(D.phi_omega(T, w), 0.7, 1.6, 12)
+        c2 = D.chebyshev_coeffs(D.phi_omega(T, T - 1 - w), 0.7, 1.6, 12)
+        assert np.abs(c2 - np.conj(c)).max() < 1e-13
+
+
+def test_spectral_bounds_contain_Bbar_spectrum():
+    """The deterministic bounds contain the spectrum of Bbar, and for x = 0
+    they match the paper's estimates 0.7 and 1.6 (App. C)."""
+    for seed in range(3):
+        m = D.Model(L=6, Ltau=8, alpha=1.0)
+        x = rng(30 + seed).standard_normal((m.Ltau, m.N)) * 2
+        ev = np.linalg.eigvals(D.Bbar(m, x))
+        bmin, bmax = D.spectral_bounds(m, x)
+        # the norm bound holds for every eigenvalue modulus; with the
+        # checkerboard C the spectrum may leave the real axis slightly for
+        # strongly fluctuating fields
+        assert bmin <= np.abs(ev).min() and np.abs(ev).max() <= bmax
+        assert np.abs(ev.imag).max() < 0.05 * np.abs(ev).max()
+        assert bmin <= ev.real.min() and ev.real.max() <= bmax
+    gb = GOLD["bbar_bounds_free"]
+    m = D.Model(L=6, Ltau=8)
+    bmin, bmax = D.spectral_bounds(m, np.zeros((m.Ltau, m.N)))
+    assert abs(bmin - gb["bmin"]) < 0.05 and abs(bmax - gb["bmax"]) < 0.15
+
+
+def test_chebyshev_coefficients_closed_form():
+    """For f(y) = 1/(a - c y) the Chebyshev series is geometric:
+    c_0 = 2r/(c(1-r^2)), c_m = 4 r^{m+1}/(c(1-r^2)) with r + 1/r = 2a/c, |r| < 1;
+    the quadrature of Eq. (Cheby-Gauss) reproduces it."""
+    for phi in (0.05, 0.3, 2.0):
+        bmin, bmax = 0.7, 1.6
+        db = bmax - bmin
+        a = 1 - np.exp(-1j * phi) * (bmin + db / 2)
+        c = np.exp(-1j * phi) * db / 2
+        z = a / c
+        r = z - np.sqrt(z * z - 1)
+        if abs(r) > 1:
+            r = z + np.sqrt(z * z - 1)
+        K = 24
+        ref = np.array([2 * r / (c * (1 - r * r))] + [4 * r ** (k + 1) / (c * (1 - r * r)) for k in range(1, K)])
+        got = D.chebyshev_coeffs(phi, bmin, bmax, K, NQ=max(2 * K, 4000))
+        assert np.abs(got - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_matvec_count_worked_example():
+    g1, g2 = GOLD["n_matvec_per_Ltau"], GOLD["n_matvec_bound_per_Ltau"]
+    T = g1["Ltau"]
+    assert abs(D.n_matvec_count(T, g1["delta_b"]) / T - g1["value"]) < 1e-9
+    assert abs(D.n_matvec_bound(T, g2["delta_b"]) / T - g2["value"]) < 0.01
+
+
+# ---------------------------------------------------------------- P11 measurements
+def test_cross_correlation_direct_equals_fft():
+    g = rng(40)
+    a, b = g.standard_normal((2, 8, 16))
+    out = D.cross_corr_direct(a, b, 4)
+    fa, fb = np.fft.fftn(a.reshape(8, 4, 4)), np.fft.fftn(b.reshape(8, 4, 4))
+    ref = np.fft.ifftn(np.conj(fa) * fb).real
+    assert np.abs(out - ref).max() < 1e-12
+
+
+def test_green_average_complete_probe_sets_are_exact():
+    """sum_k (G xi_k) xi_k^T = G for the unit vectors and (times n) for the
+    rows of a Hadamard matrix, so the stochastic average (Eq. (G_approx_better))
+    over a complete +-1 set equals the exact average of Eq. (G_avg-1)."""
+    import scipy.linalg
+    m = D.Model(L=4, Ltau=4, alpha=1.0)
+    x = rng(41).standard_normal((m.Ltau, m.N))
+    exact = D.green_average_exact(m, x)
+    H = scipy.linalg.hadamard(m.n).astype(float).reshape(m.n, m.Ltau, m.N)
+    est = D.green_average(m, x, H)
+    assert np.abs(est - exact).max() < 1e-12
+    # antiperiodicity of the doubled domain
+    assert np.abs(exact[m.Ltau:] + exact[:m.Ltau]).max() < 1e-13
+
+
+def test_four_point_pair_sum_identity():
+    """Type-2 products: sum_{n<m} (c_n star c_m) at +Delta and -Delta adds up to
+    (sum c) star (sum c) - sum_n c_n star c_n (computed here with FFTs)."""
+    m = D.Model(L=4, Ltau=4, alpha=1.0)
+    g = rng(42)
+    x = g.standard_normal((m.Ltau, m.N))
+    xi = np.sign(g.standard_normal((4, m.Ltau, m.N)))
+    G = D.green_matrix(m, x)
+    Gxi = np.array([(G @ v.reshape(-1)).reshape(m.Ltau, m.N) for v in xi])
+    out = D.four_point_pairs(m, x, xi, Gxi)
+    npairs = 6
+    c = [(D.extend(a) * D.extend(b)).reshape(2 * m.Ltau, m.L, m.L) for a, b in zip(xi, Gxi)]
+    F = [np.fft.fftn(ci) for ci in c]
+    S = sum(F)
+    tot = np.fft.ifftn(np.conj(S) * S - sum(np.conj(f) * f for f in F)).real
+    neg = np.roll(np.flip(out[1], axis=(0, 1, 2)), 1, axis=(0, 1, 2))  # value at -Delta
+    assert np.abs((out[1] + neg) * (2.0 * m.n * npairs) - tot).max() < 1e-10
+
+
+# ---------------------------------------------------------------- matrix-free C oracle
+def test_matfree_operators_equal_dense():
+    m = D.Model(L=4, Ltau=10, alpha=1.2, mu=0.1)
+    g = rng(50)
+    x = g.standard_normal((m.Ltau, m.N))
+    v = g.standard_normal((m.Ltau, m.N))
+    assert np.abs(MF.M_apply(m, x, v) - D.M_apply(m, x, v)).max() < 1e-13
+    assert np.abs(MF.MT_apply(m, x, v) - D.MT_apply(m, x, v)).max() < 1e-13
+
+
+def test_matfree_cg_and_force_equal_dense():
+    m = D.Model(L=4, Ltau=10, alpha=1.2)
+    g = rng(51)
+    x = g.standard_normal((m.Ltau, m.N))
+    R = g.standard_normal((1, m.Ltau, m.N))
+    Phi = D.phi_from_R(m, x + 0.2, R)
+    b = D.b_from_phi(m, x, Phi[0])
+    v, it, res = MF.cg(m, x, b, tol=1e-13)
+    assert it > 0 and res < 1e-13
+    vd = D.solve_MTM(m, x, b)
+    assert np.abs(v - vd).max() < 1e-9 * np.abs(vd).max()
+    F = MF.force_fermion(m, x, vd, b) + MF.force_boson(m, x)
+    Fd = D.dSF_dx(m, x, Phi) + D.dSB_dx(m, x)
+    assert np.abs(F - Fd).max() < 1e-11 * np.abs(Fd).max()
