@@ -1,0 +1,454 @@
+#!/usr/bin/env python
+"""Benchmark of the Holstein HMC hot path on GB300.
+
+Workload (one "step"): L=32 (N=1024), Ltau=200, beta=20, omega0=0.5,
+alpha=1, t=1, mu=0, dtau=0.1, x ~ N(0, 1/omega0^2) i.i.d., 16 Gaussian
+pseudofermion draws R_k. One step runs the whole single-chain hot path on
+that batch: field set-up (expV, dbar, spectral bounds), b_k = M^T R_k, the
+mixed-precision CG solve of M^T M v_k = b_k for all 16 right-hand sides to a
+certified FP64 residual 1e-8 (FP32 operator and iterations, FP64 dot
+products, FP64 reliable updates every 50 iterations), and the phonon force
+summed over the 16 solutions.
+
+Metric: CG solves/s (whole job, all ranks); the JSON line also carries
+matvecs/s, the roofline of the dominant kernel (the fused FP32 M^T M of the
+CG iteration, timed live with CUDA events on its stream during the timed
+region), the FP64-only solve rate on the same inputs, the end-to-end rate
+through the public API with host buffers, the clocks seen during the timed
+region, and the oracle timed on the host cores (cpu_baseline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --mode matvec --rhs 64      # fused M^T M alone, cold L2
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import holstein_inputs as hi  # noqa: E402
+
+METRIC = "CG solves/s (M^T M v = b, certified FP64 residual 1e-8) at L=32, Ltau=200"
+WORKLOAD = hi.WORKLOADS["big32"]
+TOL = 1e-8
+RELIABLE_EVERY = 50
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def args_parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["step", "matvec"], default="step")
+    ap.add_argument("--rhs", type=int, default=16)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; independent replicas)
+# ----------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(world, val):
+    if world == 1:
+        return val
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([val], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(world, val):
+    if world == 1:
+        return val
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([val], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands (matrix-free C, FP64, OpenMP)
+# ----------------------------------------------------------------------------
+def cpu_oracle_solves(n_solves, seed_offset=0, with_force=True):
+    """Time n_solves single-rhs oracle CG solves (+ force) of the benchmark
+    workload. Returns (seconds, iterations list, threads)."""
+    from oracle import matfree as MF
+    w = WORKLOAD
+    x = hi.phonon_field(w, seed=w.seed + seed_offset)
+    R = hi.gaussian_vectors(w, n_solves, seed=2 + seed_offset)
+    t0 = time.perf_counter()
+    its = []
+    for k in range(n_solves):
+        b = MF.MT_apply(w, x, R[k])
+        v, it, res = MF.cg(w, x, b, tol=TOL, max_iter=100000)
+        its.append(it)
+        if with_force:
+            MF.force_fermion(w, x, v, b)
+    return time.perf_counter() - t0, its, MF.num_threads()
+
+
+def cpu_baseline_block(target_s=15.0):
+    one, its, thr = cpu_oracle_solves(1)
+    n = max(1, min(16, int(target_s / max(one, 1e-3))))
+    if n > 1:
+        tt, its2, thr = cpu_oracle_solves(n, seed_offset=0)
+    else:
+        tt, its2 = one, its
+    return {"value": n / tt, "unit": "CG solves/s", "cores": thr, "kind": "oracle",
+            "sample": f"{n} single-rhs FP64 textbook CG solves (+ force) of the L=32 Ltau=200 "
+                      f"workload to residual 1e-8 (matrix-free C oracle, OpenMP), mean "
+                      f"{float(np.mean(its2)):.0f} iterations"}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(a):
+    import torch
+    import paper_2203_01291_gb300 as hg
+    from paper_2203_01291_gb300 import build as hb
+    world, rank, local = dist_setup(a.gpus)
+    if rank == 0 or world > 1:
+        hb.build()
+    barrier(world)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = WORKLOAD
+    nr = w.n_rhs
+    x = hi.phonon_field(w, seed=w.seed + 100 * rank)
+    R = hi.gaussian_vectors(w, nr, seed=2 + 100 * rank)
+    ctx = hg.Context.from_workload(w, max_rhs=nr)
+    xd = torch.tensor(x, device=dev)
+    Rd = torch.tensor(R, device=dev)
+    bd = torch.empty_like(Rd)
+    vd = torch.empty_like(Rd)
+    Fd = torch.empty_like(xd)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stats = {"iters": [], "resid": []}
+
+    def step(xin, Rin, prec=hg.HOL_F32):
+        ctx.set_field(xin)
+        ctx.fermion_matvec(hg.HOL_OP_MT, Rin, bd)
+        it, res = ctx.cg_solve(bd, vd, tol=TOL, prec=prec, reliable_every=RELIABLE_EVERY,
+                               check_every=10, max_iter=50000)
+        ctx.force(vd, bd, Fd, with_bosonic=True)
+        return it, res
+
+    for _ in range(a.warmup):
+        flush.zero_()
+        step(xd, Rd)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    ctx.timer_enable(True)
+    l0 = hg.hol_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        flush.zero_()
+        it, res = step(xd, Rd)
+        stats["iters"].append(it)
+        stats["resid"].append(res)
+    e1.record()
+    torch.cuda.synchronize()
+    launches = hg.hol_launch_count() - l0
+    ms_total = e0.elapsed_time(e1)
+    op_cnt, op_ms = ctx.timer_read(hg.TIMER_OPERATOR)
+    up_cnt, up_ms = ctx.timer_read(hg.TIMER_UPDATE)
+    fo_cnt, fo_ms = ctx.timer_read(hg.TIMER_FORCE)
+    ctx.timer_enable(False)
+    clk = clocks.stop()
+    barrier(world)
+    ms_max = reduce_max(world, ms_total)
+
+    iters = np.array(stats["iters"])          # [steps][rhs]
+    assert np.all(np.array(stats["resid"]) < TOL)
+    solves = a.steps * nr
+    total_solves = reduce_sum(world, solves)
+    value = total_solves / (ms_max / 1e3)
+    # matvec count: 2 per CG iteration per rhs, M^T for b, 2 per reliable update
+    # (counted as one per 50 iterations plus the final certification), 1 in the force
+    rel = np.ceil(iters / RELIABLE_EVERY) + 1
+    mv = float(np.sum(2 * iters + 1 + 2 * rel + 1))
+    total_mv = reduce_sum(world, mv)
+
+    # roofline of the fused FP32 M^T M (reads r, p_old; writes p_new, q; reads expV)
+    n = w.n
+    alg_bytes = float(np.sum(iters)) * n * 4 * 4 + op_cnt * n * 4
+    op_avg_ms = op_ms / max(op_cnt, 1)
+    achieved = alg_bytes / (op_ms / 1e3) / 1e9
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("k_cg_mtm32_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # FP64-only path on the same inputs (mixed vs FP64 at equal residual)
+    fp64 = None
+    if not a.no_fp64:
+        step(xd, Rd, prec=hg.HOL_F64)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        ksteps = 2
+        f0.record()
+        its64 = []
+        for _ in range(ksteps):
+            flush.zero_()
+            it64, res64 = step(xd, Rd, prec=hg.HOL_F64)
+            its64.append(it64)
+            assert np.all(res64 < TOL)
+        f1.record()
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1) / ksteps
+        fp64 = {"solves_per_s": nr / (ms64 / 1e3), "ms_per_step": ms64,
+                "mean_iters": float(np.mean(its64)),
+                "mixed_over_fp64": (solves / (ms_total / 1e3)) / (nr / (ms64 / 1e3))}
+
+    # end to end through the public API: host (pinned) inputs -> device,
+    # solve + force, solutions and force back to host, every step
+    xh = torch.tensor(x).pin_memory()
+    Rh = torch.tensor(R).pin_memory()
+    vh = torch.empty(vd.shape, dtype=torch.float64).pin_memory()
+    Fh = torch.empty(Fd.shape, dtype=torch.float64).pin_memory()
+    ke = max(1, min(a.steps, 5))
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record()
+    for _ in range(ke):
+        flush.zero_()
+        xd.copy_(xh, non_blocking=True)
+        Rd.copy_(Rh, non_blocking=True)
+        step(xd, Rd)
+        vh.copy_(vd, non_blocking=True)
+        Fh.copy_(Fd, non_blocking=True)
+    g1.record()
+    torch.cuda.synchronize()
+    ms_e2e = reduce_max(world, g0.elapsed_time(g1) / ke)
+    e2e = {"value": reduce_sum(world, nr) / (ms_e2e / 1e3), "unit": "CG solves/s",
+           "h2d_bytes_per_step": int(xh.numel() * 8 + Rh.numel() * 8),
+           "d2h_bytes_per_step": int(vh.numel() * 8 + Fh.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu = cpu_baseline_block()
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "CG solves/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 operator+iterations, f64 dots/solution/reliable updates",
+            "data": "synthetic (seeded i.i.d. Gaussian phonon field and pseudofermion draws)",
+            "config": {"workload": "L=32 N=1024 Ltau=200 beta=20 dtau=0.1 t=1 mu=0 omega0=0.5 "
+                                   "alpha=1 x~N(0,4), 16 rhs b=M^T R, mixed CG to 1e-8 "
+                                   "(reliable update every 50) + force",
+                       "l2": "flushed between steps (256 MB write inside the timed loop)",
+                       "per_rank": "independent replica, own seeds"},
+            "matvecs_per_s": total_mv / (ms_max / 1e3),
+            "mean_cg_iters": float(np.mean(iters)),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "kernel": "k_cg_mtm32 (fused p=r+beta p, q=M^T M p, |Mp|^2)",
+                         "alg_bytes_per_launch": alg_bytes / max(op_cnt, 1),
+                         "avg_launch_ms": op_avg_ms, "launches": op_cnt,
+                         "peak_src": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "kernel_ms": {"cg_operator": op_ms, "cg_update": up_ms, "force": fo_ms,
+                          "timed_total": ms_total},
+            "fp64_compare": fp64,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_matvec(a):
+    """Fused FP32 M^T M alone on `rhs` right-hand sides, cold L2 per launch."""
+    import torch
+    import paper_2203_01291_gb300 as hg
+    from paper_2203_01291_gb300 import build as hb
+    hb.build()
+    torch.cuda.set_device(0)
+    w = WORKLOAD
+    nr = a.rhs
+    ctx = hg.Context.from_workload(w, max_rhs=nr)
+    ctx.set_field(torch.tensor(hi.phonon_field(w), device="cuda"))
+    v = torch.tensor(hi.gaussian_vectors(w, nr, seed=5), device="cuda", dtype=torch.float32)
+    q = torch.empty_like(v)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for _ in range(a.warmup):
+        ctx.fermion_matvec(hg.HOL_OP_MTM, v, q)
+    times = []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.fermion_matvec(hg.HOL_OP_MTM, v, q)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    alg = nr * w.n * 4 * 2 + w.n * 4          # v in, q out, expV
+    hbm = peaks().get("hbm_gbs", 6800.0)
+    print(json.dumps({"mode": "matvec", "rhs": nr, "median_ms": ms,
+                      "alg_bytes": alg, "achieved_gbs": alg / (ms / 1e3) / 1e9,
+                      "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / hbm,
+                      "matvecs_per_s": 2 * nr / (ms / 1e3)}))
+    ctx.close()
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the oracle as it stands, timed on the host cores
+# ----------------------------------------------------------------------------
+def run_reference(a):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import matfree as MF
+    MF.build()
+    for k in range(a.warmup):
+        cpu_oracle_solves(1, seed_offset=1000 + k)
+    t0 = time.perf_counter()
+    its = []
+    for k in range(a.steps):
+        _, it, thr = cpu_oracle_solves(1, seed_offset=k)
+        its += it
+    dt = time.perf_counter() - t0
+    value = a.steps / dt
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "CG solves/s",
+           "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "L=32 N=1024 Ltau=200 beta=20 omega0=0.5 alpha=1, "
+                                  "one rhs per step, FP64 CG to 1e-8 + force"},
+           "cpu_baseline": {"value": value, "unit": "CG solves/s", "cores": MF.num_threads(),
+                            "kind": "oracle",
+                            "sample": f"{a.steps} single-rhs solves, mean "
+                                      f"{float(np.mean(its)):.0f} iterations"},
+           "e2e": {"value": value, "unit": "CG solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    a = args_parse()
+    if a.impl == "reference":
+        run_reference(a)
+    elif a.mode == "matvec":
+        run_matvec(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * holstein.h -- C ABI of the GB300 (sm_103a) library for the hot path of
+ * hybrid Monte Carlo for the Holstein model (Cohen-Stead, Bradley, Miles,
+ * Batrouni, Scalettar, Barros, "Fast and scalable quantum Monte Carlo
+ * simulations of electron-phonon models").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Lattice: periodic L x L square lattice, N = L*L sites, site index
+ *   i = ix + L*iy, nearest-neighbour hopping t (Sec. II B). L must be even,
+ *   4 <= L <= 32. Imaginary time has T = Ltau slices (Sec. II C), T even.
+ * - Space-time vectors are real arrays laid out [rhs][tau][i] (tau-slice
+ *   contiguous), length n = N*T per right-hand side.
+ * - All array arguments are DEVICE pointers unless the comment says "host".
+ *   The caller allocates and owns them; the library never frees them.
+ * - The context owns its scratch memory (allocated in hol_create, released in
+ *   hol_destroy) and is bound to the CUDA device current at hol_create.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Calls enqueue work on that stream; calls that return host-side results
+ *   (cg_solve statistics, dH) synchronise that stream before returning.
+ * - Every call returns 0 (HOL_OK) or a negative HOL_E* code; no exception or
+ *   abort crosses the ABI. hol_last_error() describes the last failure on the
+ *   calling thread.
+ * - Precision: HOL_F64 arrays are double; HOL_F32 arrays are float.
+ */
+#ifndef HOLSTEIN_H
+#define HOLSTEIN_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HOL_OK        0
+#define HOL_EINVAL   -1   /* bad argument (size, null pointer, unsupported shape) */
+#define HOL_ENOTCONV -2   /* CG did not reach the tolerance within max_iter     */
+#define HOL_ENUMERIC -3   /* NaN / Inf met in a reduction                        */
+#define HOL_ETIMEOUT -4   /* a bounded device-side wait gave up                  */
+#define HOL_ECUDA    -5   /* a CUDA runtime call failed                          */
+#define HOL_ENOMEM   -6   /* device allocation failed                            */
+
+/* operator selector for fermion_matvec */
+#define HOL_OP_M   0      /* out = M v                                          */
+#define HOL_OP_MT  1      /* out = M^T v                                        */
+#define HOL_OP_MTM 2      /* out = M^T M v                                      */
+
+/* precision selector */
+#define HOL_F64 0
+#define HOL_F32 1
+
+typedef struct hol_params {
+    int L;            /* linear lattice size (even, 4..32)                      */
+    int Ltau;         /* number of imaginary-time slices T = beta / dtau (even) */
+    double dtau;      /* imaginary-time step                                    */
+    double t;         /* nearest-neighbour hopping                              */
+    double mu;        /* chemical potential                                     */
+    double alpha;     /* electron-phonon coupling                               */
+    double omega0;    /* phonon frequency (phonon mass is 1)                    */
+    int max_rhs;      /* largest n_rhs any later call will pass (>= 1)          */
+} hol_params;
+
+typedef struct hol_ctx hol_ctx;
+
+/* Create a context for one lattice shape and set of couplings. Allocates the
+ * context's scratch on the current device. Returns HOL_EINVAL for an
+ * unsupported shape, HOL_ENOMEM if the scratch does not fit. */
+int hol_create(const hol_params* p, hol_ctx** out);
+
+/* Release the context and its scratch. NULL is accepted. */
+int hol_destroy(hol_ctx* ctx);
+
+/* Message describing the last error on the calling thread (static storage). */
+const char* hol_last_error(void);
+
+/*
+ * Set the phonon field x[tau][i] (FP64, device) the operators act on
+ * (Sec. II C, Eqs. (B_def), (V_K_def)): computes
+ *   expV[tau][i] = exp(-dtau (alpha x[tau][i] - mu))     (FP64 and FP32 copies)
+ *   dbar[i]      = (1/T) sum_tau expV[tau][i]             (Eq. (expnVbar))
+ *   the spectral bounds of Bbar = diag(dbar) exp(-dtau K) (App. C D; the
+ *   deterministic norm bound min/max(dbar) * exp(-/+ 4 dtau |t|)),
+ *   and the Chebyshev plan of the preconditioner (Eqs. (NP_heuristic),
+ *   (Cheby-Gauss)). x is copied; the caller may reuse its buffer at once.
+ */
+int hol_set_field(hol_ctx* ctx, const double* x, void* stream);
+
+/*
+ * Apply the space-time fermion matrix of Eq. (M_def) to n_rhs vectors:
+ *   (M v)_tau   = v_tau + s_tau B_tau v_{tau-1},  s_0 = +1, s_{tau>0} = -1,
+ *   (M^T u)_tau = u_tau + s_{tau+1} B_{tau+1}^T u_{tau+1},
+ * with B_tau = exp(-dtau V_tau) C (Eq. (B_def)) and C the checkerboard
+ * product C4 C3 C2 C1 of Sec. II D (colours: x-bonds from even ix, x-bonds
+ * from odd ix, y-bonds from even iy, y-bonds from odd iy; each bond the
+ * two-site factor [[cosh, sinh], [sinh, cosh]](dtau t)); tau-1, tau+1 mod T.
+ * op: HOL_OP_M, HOL_OP_MT or HOL_OP_MTM. prec: HOL_F64 (v, out double) or
+ * HOL_F32 (float). v and out: [n_rhs][T][N], must not overlap.
+ * Requires hol_set_field. 1 <= n_rhs <= max_rhs.
+ */
+int fermion_matvec(hol_ctx* ctx, int op, int prec, const void* v, void* out,
+                   int n_rhs, void* stream);
+
+typedef struct hol_cg_opts {
+    double tol;          /* stop when |b - M^T M v| / |b| < tol (Sec. VI B)    */
+    int max_iter;        /* iteration cap per right-hand side                  */
+    int precond;         /* 0: plain CG; 1: adiabatic preconditioner (Sec. VI) */
+    int prec;            /* HOL_F64: all FP64. HOL_F32: FP32 matvecs and
+                            iterations, FP64 dot products, FP64 solution and
+                            true-residual (reliable) updates                   */
+    int reliable_every;  /* HOL_F32: iterations between FP64 residual updates  */
+    int check_every;     /* iterations between host convergence polls          */
+} hol_cg_opts;
+
+/*
+ * Solve (M^T M) v = b (Eq. (CG)) for n_rhs right-hand sides by conjugate
+ * gradients from v = 0 (so v is a deterministic function of x and b), with
+ * the preconditioner z = P^{-1} P^{-T} r when opts->precond (Eq. (CG_precon)).
+ * b, v: FP64 [n_rhs][T][N] (device). Convergence of every right-hand side is
+ * certified with an FP64 true residual |b - M^T M v| / |b| < tol.
+ * iters, resid: HOST arrays of n_rhs entries (nullable) receiving the
+ * iterations and the final true relative residual of each right-hand side.
+ * Returns HOL_ENOTCONV if some right-hand side did not converge (v then holds
+ * the last iterate). Synchronises `stream`.
+ */
+int cg_solve(hol_ctx* ctx, const double* b, double* v, int n_rhs,
+             const hol_cg_opts* opts, int* iters, double* resid, void* stream);
+
+/*
+ * Phonon force of Sec. III A: dS/dx[tau][i] (FP64, device, [T][N]) for the
+ * action S = S_B + S_F with S_F = (1/2) sum_sigma Phi_sigma^T (A^T A)^{-1}
+ * Phi_sigma, A = M Lambda (Eqs. (S_F), (dSF_dx)). Inputs are the solved
+ * pairs (v_sigma, b_sigma), b = Lambda^{-T} Phi, v = (M^T M)^{-1} b, for
+ * n_pf pseudofermions ([n_pf][T][N], FP64). With dA = dM Lambda + M dLambda
+ * for the Holstein B_tau the fermion part is, per pseudofermion,
+ *   dS_F/dx_{i,tau} = dtau alpha s_tau u_{i,tau} y_{i,tau}
+ *                     - (dtau alpha / 2) b_{i,tau-1} v_{i,tau-1},
+ *   u = M v, y_tau = exp(-dtau V_tau) C v_{tau-1}.
+ * with_bosonic != 0 adds dS_B/dx of Eq. (dSB_dx) for the field of the last
+ * hol_set_field. S_F (device, nullable, one double) receives
+ * (1/2) sum_sigma b_sigma . v_sigma (Eq. (Sf_Psi)). dSdx is overwritten.
+ */
+int force(hol_ctx* ctx, const double* v, const double* b, int n_pf,
+          double* dSdx, int with_bosonic, double* S_F, void* stream);
+
+/*
+ * Pseudofermion draw (Sec. II D, Eq. (PhiSample-1)): Phi = A^T R with
+ * A = M Lambda, for the field of the last hol_set_field. R, Phi: FP64
+ * [n_pf][T][N] (device); R holds standard-normal draws supplied by the caller.
+ * Uses context scratch; R and Phi must not overlap.
+ */
+int pseudofermion_phi(hol_ctx* ctx, const double* R, double* Phi, int n_pf, void* stream);
+
+/*
+ * CG right-hand side b = Lambda^{-T} Phi (Sec. II D, below Eq. (psi_def)),
+ * Lambda of Eq. (Lambda_def) at the field of the last hol_set_field:
+ *   b_{i,tau} = s'_{tau+1} exp(-dtau alpha x_{i,tau+1} / 2) Phi_{i,tau+1},
+ *   s'_0 = +1, s'_{tau>0} = -1, tau+1 mod T.
+ * Phi, b: FP64 [n_pf][T][N] (device), must not overlap.
+ */
+int phi_to_rhs(hol_ctx* ctx, const double* Phi, double* b, int n_pf, void* stream);
+
+/*
+ * Instrumentation (no counterpart in the paper; used by the benchmark).
+ * hol_launch_count: number of kernels this library has launched in the
+ * process so far. hol_timer_enable(ctx, 1) starts recording CUDA events
+ * around every kernel of the classes below on the stream each call is given
+ * (it resets the counts; 0 stops recording). hol_timer_read returns, for one
+ * class, how many regions were recorded and their summed device time in ms
+ * (it waits for the recorded events). Classes: 0 CG operator (fused M^T M),
+ * 1 CG vector update, 2 force, 3 preconditioner, 4 other.
+ */
+unsigned long long hol_launch_count(void);
+int hol_timer_enable(hol_ctx* ctx, int on);
+int hol_timer_read(hol_ctx* ctx, int klass, int* count, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOLSTEIN_H */

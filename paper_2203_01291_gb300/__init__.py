@@ -1,0 +1,206 @@
+"""GB300 (sm_103a) library for the hot path of hybrid Monte Carlo for the
+Holstein model (Cohen-Stead et al., arXiv:2203.01291).
+
+Every computation runs in the CUDA library built from csrc/ and exposed
+through the C ABI of include/holstein.h; this module only marshals
+arguments (torch tensors -> device pointers, current CUDA stream). There is
+no CPU fallback: without the built library, or without a GPU, the calls
+raise.
+
+    ctx = Context(L=32, Ltau=200, dtau=0.1, t=1.0, mu=0.0, alpha=1.0,
+                  omega0=0.5, max_rhs=16)
+    ctx.set_field(x)                                  # x: cuda float64 [T, N]
+    ctx.fermion_matvec(HOL_OP_MTM, v, out)           # v, out: [n_rhs, T, N]
+    iters, resid = ctx.cg_solve(b, v, tol=1e-8, prec=HOL_F32)
+    ctx.force(v, b, dSdx, with_bosonic=True)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from ._abi import (HOL_ECUDA, HOL_EINVAL, HOL_ENOMEM, HOL_ENOTCONV, HOL_ENUMERIC, HOL_ETIMEOUT,
+                   HOL_F32, HOL_F64, HOL_OK, HOL_OP_M, HOL_OP_MT, HOL_OP_MTM, hol_cg_opts,
+                   hol_params, load, library_path)
+
+__all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F64", "HOL_F32",
+           "hol_create", "hol_destroy", "hol_set_field", "fermion_matvec", "cg_solve", "force",
+           "pseudofermion_phi", "phi_to_rhs", "hol_launch_count", "hol_timer_enable",
+           "hol_timer_read",
+           "library_path", "load"]
+
+
+class HolError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def _check(rc: int) -> None:
+    if rc != HOL_OK:
+        raise HolError(rc, load().hol_last_error().decode(errors="replace"))
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ptr(t: torch.Tensor, dtype: torch.dtype, numel: int | None = None, name: str = "tensor"):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- ABI mirrors
+def hol_create(params: hol_params) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().hol_create(ctypes.byref(params), ctypes.byref(h)))
+    return h
+
+
+def hol_destroy(handle) -> None:
+    _check(load().hol_destroy(handle))
+
+
+def hol_set_field(handle, x: torch.Tensor, n: int) -> None:
+    _check(load().hol_set_field(handle, _ptr(x, torch.float64, n, "x"), _stream()))
+
+
+def fermion_matvec(handle, op: int, prec: int, v: torch.Tensor, out: torch.Tensor, n_rhs: int,
+                   n: int) -> None:
+    dt = torch.float64 if prec == HOL_F64 else torch.float32
+    _check(load().fermion_matvec(handle, op, prec, _ptr(v, dt, n_rhs * n, "v"),
+                                 _ptr(out, dt, n_rhs * n, "out"), n_rhs, _stream()))
+
+
+def cg_solve(handle, b: torch.Tensor, v: torch.Tensor, n_rhs: int, n: int, opts: hol_cg_opts,
+             raise_on_nonconv: bool = True):
+    it = (ctypes.c_int * n_rhs)()
+    rs = (ctypes.c_double * n_rhs)()
+    rc = load().cg_solve(handle, _ptr(b, torch.float64, n_rhs * n, "b"),
+                         _ptr(v, torch.float64, n_rhs * n, "v"), n_rhs, ctypes.byref(opts), it,
+                         rs, _stream())
+    if rc != HOL_OK and (rc != HOL_ENOTCONV or raise_on_nonconv):
+        _check(rc)
+    return np.array(it[:], dtype=np.int64), np.array(rs[:], dtype=np.float64)
+
+
+def force(handle, v: torch.Tensor, b: torch.Tensor, n_pf: int, dSdx: torch.Tensor,
+          with_bosonic: bool, S_F: torch.Tensor | None, n: int) -> None:
+    sf = _ptr(S_F, torch.float64, 1, "S_F") if S_F is not None else None
+    _check(load().force(handle, _ptr(v, torch.float64, n_pf * n, "v"),
+                        _ptr(b, torch.float64, n_pf * n, "b"), n_pf,
+                        _ptr(dSdx, torch.float64, n, "dSdx"), int(bool(with_bosonic)), sf,
+                        _stream()))
+
+
+def pseudofermion_phi(handle, R: torch.Tensor, Phi: torch.Tensor, n_pf: int, n: int) -> None:
+    _check(load().pseudofermion_phi(handle, _ptr(R, torch.float64, n_pf * n, "R"),
+                                    _ptr(Phi, torch.float64, n_pf * n, "Phi"), n_pf, _stream()))
+
+
+def phi_to_rhs(handle, Phi: torch.Tensor, b: torch.Tensor, n_pf: int, n: int) -> None:
+    _check(load().phi_to_rhs(handle, _ptr(Phi, torch.float64, n_pf * n, "Phi"),
+                             _ptr(b, torch.float64, n_pf * n, "b"), n_pf, _stream()))
+
+
+def hol_launch_count() -> int:
+    return int(load().hol_launch_count())
+
+
+def hol_timer_enable(handle, on: bool) -> None:
+    _check(load().hol_timer_enable(handle, int(bool(on))))
+
+
+def hol_timer_read(handle, klass: int):
+    cnt = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(load().hol_timer_read(handle, klass, ctypes.byref(cnt), ctypes.byref(ms)))
+    return cnt.value, ms.value
+
+
+TIMER_OPERATOR, TIMER_UPDATE, TIMER_FORCE, TIMER_PRECOND, TIMER_OTHER = range(5)
+
+
+# ---------------------------------------------------------------- convenience
+class Context:
+    """One lattice shape and set of couplings (owns the library context)."""
+
+    def __init__(self, L: int, Ltau: int, dtau: float = 0.1, t: float = 1.0, mu: float = 0.0,
+                 alpha: float = 1.0, omega0: float = 1.0, max_rhs: int = 1):
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2203_01291_gb300 needs a CUDA GPU; there is no CPU fallback")
+        self.L, self.Ltau, self.N = L, Ltau, L * L
+        self.n = self.N * Ltau
+        self.max_rhs = max_rhs
+        self.params = hol_params(L, Ltau, dtau, t, mu, alpha, omega0, max_rhs)
+        self._h = hol_create(self.params)
+
+    @classmethod
+    def from_workload(cls, w, max_rhs: int | None = None) -> "Context":
+        return cls(L=w.L, Ltau=w.Ltau, dtau=w.dtau, t=w.t, mu=w.mu, alpha=w.alpha,
+                   omega0=w.omega0, max_rhs=max_rhs or max(1, w.n_rhs))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            hol_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _nrhs(self, v: torch.Tensor) -> int:
+        if v.numel() % self.n:
+            raise ValueError("vector length is not a multiple of N*Ltau")
+        return v.numel() // self.n
+
+    def set_field(self, x: torch.Tensor) -> None:
+        hol_set_field(self._h, x, self.n)
+
+    def fermion_matvec(self, op: int, v: torch.Tensor, out: torch.Tensor) -> None:
+        prec = HOL_F64 if v.dtype == torch.float64 else HOL_F32
+        fermion_matvec(self._h, op, prec, v, out, self._nrhs(v), self.n)
+
+    def cg_solve(self, b: torch.Tensor, v: torch.Tensor, tol: float = 1e-10,
+                 max_iter: int = 10000, precond: bool = False, prec: int = HOL_F64,
+                 reliable_every: int = 50, check_every: int = 10,
+                 raise_on_nonconv: bool = True):
+        opts = hol_cg_opts(tol, max_iter, int(bool(precond)), prec, reliable_every, check_every)
+        return cg_solve(self._h, b, v, self._nrhs(b), self.n, opts, raise_on_nonconv)
+
+    def force(self, v: torch.Tensor, b: torch.Tensor, dSdx: torch.Tensor,
+              with_bosonic: bool = True, S_F: torch.Tensor | None = None) -> None:
+        force(self._h, v, b, self._nrhs(v), dSdx, with_bosonic, S_F, self.n)
+
+    def pseudofermion_phi(self, R: torch.Tensor, Phi: torch.Tensor) -> None:
+        pseudofermion_phi(self._h, R, Phi, self._nrhs(R), self.n)
+
+    def phi_to_rhs(self, Phi: torch.Tensor, b: torch.Tensor) -> None:
+        phi_to_rhs(self._h, Phi, b, self._nrhs(Phi), self.n)
+
+    def timer_enable(self, on: bool = True) -> None:
+        hol_timer_enable(self._h, on)
+
+    def timer_read(self, klass: int):
+        return hol_timer_read(self._h, klass)

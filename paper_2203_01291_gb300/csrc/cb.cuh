@@ -1,0 +1,102 @@
+// Register-resident checkerboard propagator for one tau slice of the L x L
+// lattice (Sec. II D "minimal split checkerboard", C = C4 C3 C2 C1).
+//
+// A lane group of L consecutive lanes holds one slice: lane ix holds the
+// column x = ix, all L rows iy in registers c[iy]. The x-bonds (colours 1, 2)
+// pair neighbouring lanes and are exchanged with one warp shuffle per row;
+// the y-bonds (colours 3, 4) pair neighbouring registers of the same lane.
+// No shared memory and no barriers are involved.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace hol {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Lane-group geometry for side L: G = floor(32/L) groups per warp. Lanes
+// beyond G*L shadow group 0 (same loads and arithmetic, never store).
+template <int L>
+struct LaneGeom {
+    static constexpr int G = 32 / L;
+    int g, ix, p1, p2;
+    bool ok;
+    __device__ __forceinline__ LaneGeom()
+    {
+        const int lane = threadIdx.x & 31;
+        g = lane / L;
+        ix = lane - g * L;
+        ok = g < G;
+        if (!ok) {
+            g = 0;
+            ix = lane - G * L;
+        }
+        const int base = g * L;
+        p1 = base + (ix ^ 1);                                   // colour 1 partner
+        p2 = base + ((ix & 1) ? (ix + 1 == L ? 0 : ix + 1)      // colour 2 partner
+                              : (ix == 0 ? L - 1 : ix - 1));
+    }
+};
+
+// Two-site bond factor [[ch, sh], [sh, ch]] on (own, partner) across lanes.
+template <typename R, int L>
+__device__ __forceinline__ void cb_xbond(R (&c)[L], int partner, R ch, R sh)
+{
+#pragma unroll
+    for (int iy = 0; iy < L; ++iy) {
+        const R o = __shfl_sync(kFull, c[iy], partner);
+        c[iy] = fma(ch, c[iy], sh * o);
+    }
+}
+
+// Bond factor on register pairs (iy, iy+1 mod L), iy = P, P+2, ...
+template <typename R, int L, int P>
+__device__ __forceinline__ void cb_ybond(R (&c)[L], R ch, R sh)
+{
+#pragma unroll
+    for (int iy = P; iy < L; iy += 2) {
+        const int j = (iy + 1) % L;
+        const R a = c[iy], b = c[j];
+        c[iy] = fma(ch, a, sh * b);
+        c[j] = fma(sh, a, ch * b);
+    }
+}
+
+// c <- C c with C = C4 C3 C2 C1 (colour 1 acts first).
+template <typename R, int L>
+__device__ __forceinline__ void cb_apply(R (&c)[L], const LaneGeom<L>& g, R ch, R sh)
+{
+    cb_xbond<R, L>(c, g.p1, ch, sh);
+    cb_xbond<R, L>(c, g.p2, ch, sh);
+    cb_ybond<R, L, 0>(c, ch, sh);
+    cb_ybond<R, L, 1>(c, ch, sh);
+}
+
+// c <- C^T c with C^T = C1 C2 C3 C4 (colour 4 acts first).
+template <typename R, int L>
+__device__ __forceinline__ void cb_apply_t(R (&c)[L], const LaneGeom<L>& g, R ch, R sh)
+{
+    cb_ybond<R, L, 1>(c, ch, sh);
+    cb_ybond<R, L, 0>(c, ch, sh);
+    cb_xbond<R, L>(c, g.p2, ch, sh);
+    cb_xbond<R, L>(c, g.p1, ch, sh);
+}
+
+// Warp-wide sum of a double, identical result in every lane (fixed order).
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Sum of a[0..n) by one full warp (lane-strided, then butterfly); every lane
+// gets the same bits.
+__device__ __forceinline__ double warp_sum_array(const double* __restrict__ a, int n)
+{
+    double s = 0.0;
+    for (int k = (threadIdx.x & 31); k < n; k += 32) s += a[k];
+    return warp_sum(s);
+}
+
+}  // namespace hol

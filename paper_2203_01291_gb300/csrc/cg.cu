@@ -1,0 +1,419 @@
+// Conjugate gradients on M^T M v = b (Eq. (CG), Sec. VI B stopping rule).
+//
+// One CG iteration is two kernels:
+//   1. direction + operator: p_new = r + beta p_old, q = M^T M p_new and the
+//      partial sums of p_new . q = |M p_new|^2 (matvec.cu);
+//   2. update: alpha = (r.r)/(p.q), x += alpha p, r -= alpha q and the partial
+//      sums of the new r.r.
+// beta and alpha are recomputed by every consumer from the partial sums in a
+// fixed order, so no extra launch or grid barrier sits on the critical path.
+// All dot products accumulate in FP64.
+//
+// Mixed precision (opts->prec == HOL_F32): x is an FP32 increment e on top
+// of the FP64 solution v; every `reliable_every` iterations, and whenever the
+// recursive residual estimate says "converged", e is folded into v and the
+// true residual b - M^T M v is recomputed in FP64 (reliable update) and
+// replaces r. Every reported convergence is certified by that FP64 residual.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "cb.cuh"
+#include "internal.cuh"
+
+namespace hol {
+namespace {
+
+template <typename R>
+struct V4;
+template <>
+struct V4<float> {
+    float v[4];
+    __device__ __forceinline__ void ld(const float* p)
+    {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ __forceinline__ void st(float* p) const
+    {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct V4<double> {
+    double v[4];
+    __device__ __forceinline__ void ld(const double* p)
+    {
+        const double2 a = *reinterpret_cast<const double2*>(p);
+        const double2 b = *reinterpret_cast<const double2*>(p + 2);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    __device__ __forceinline__ void st(double* p) const
+    {
+        *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+    }
+};
+
+// Block sum of a double (any blockDim multiple of 32, <= 1024); result valid
+// in thread 0.
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double red[32];
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+    return s;
+}
+
+// x += alpha p, r -= alpha q, new (r.r) partials; alpha = rr / pq from partials.
+template <typename R>
+__global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restrict__ r,
+                                                   const R* __restrict__ p, const R* __restrict__ q,
+                                                   long n, const int* __restrict__ mask,
+                                                   const double* __restrict__ pq_part, int pq_stride,
+                                                   int pq_n, const double* __restrict__ rr_part,
+                                                   int rr_n, double* __restrict__ rr_out)
+{
+    const int rhs = blockIdx.y;
+    if (mask != nullptr && mask[rhs] == 0) return;
+    __shared__ double s_alpha;
+    if (threadIdx.x < 32) {
+        const double pq = warp_sum_array(pq_part + (long)rhs * pq_stride, pq_n);
+        const double rr = warp_sum_array(rr_part + (long)rhs * kRedStride, rr_n);
+        if (threadIdx.x == 0) s_alpha = rr / pq;
+    }
+    __syncthreads();
+    const R a = (R)s_alpha;
+    const long base = (long)rhs * n;
+    double acc = 0.0;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n;
+         k += (long)gridDim.x * blockDim.x) {
+        const long o = base + 4 * k;
+        V4<R> xv, rv, pv, qv;
+        xv.ld(x + o);
+        rv.ld(r + o);
+        pv.ld(p + o);
+        qv.ld(q + o);
+        R part = R(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            xv.v[j] = fma(a, pv.v[j], xv.v[j]);
+            rv.v[j] = fma(-a, qv.v[j], rv.v[j]);
+            part = fma(rv.v[j], rv.v[j], part);
+        }
+        xv.st(x + o);
+        rv.st(r + o);
+        acc += (double)part;
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) rr_out[(long)rhs * kRedStride + blockIdx.x] = s;
+}
+
+// Start: r = b (FP64 or rounded to FP32), x = 0; partials of |b|^2 and |r|^2.
+template <typename R>
+__global__ void __launch_bounds__(256) k_cg_init(const double* __restrict__ b, R* __restrict__ r,
+                                                 R* __restrict__ x, long n,
+                                                 double* __restrict__ bn_out,
+                                                 double* __restrict__ rr_out)
+{
+    const int rhs = blockIdx.y;
+    const long base = (long)rhs * n;
+    double ab = 0.0, ar = 0.0;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+         k += (long)gridDim.x * blockDim.x) {
+        const double bv = b[base + k];
+        const R rv = (R)bv;
+        r[base + k] = rv;
+        if (x != nullptr) x[base + k] = R(0);
+        ab += bv * bv;
+        ar += (double)rv * (double)rv;
+    }
+    double s = block_sum(ab);
+    if (threadIdx.x == 0) bn_out[(long)rhs * kRedStride + blockIdx.x] = s;
+    __syncthreads();
+    s = block_sum(ar);
+    if (threadIdx.x == 0) rr_out[(long)rhs * kRedStride + blockIdx.x] = s;
+}
+
+// Reliable update, part 1 (mixed only): v += e, e = 0.
+__global__ void __launch_bounds__(256) k_fold(double* __restrict__ v, float* __restrict__ e, long n,
+                                              const int* __restrict__ mask)
+{
+    const int rhs = blockIdx.y;
+    if (mask[rhs] == 0) return;
+    const long base = (long)rhs * n;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+         k += (long)gridDim.x * blockDim.x) {
+        v[base + k] += (double)e[base + k];
+        e[base + k] = 0.0f;
+    }
+}
+
+// Reliable update, part 3: r <- true residual rt (FP64; rounded to FP32 in
+// the mixed path); partials of |rt|^2 (true) and |r|^2 (recursion).
+template <typename R>
+__global__ void __launch_bounds__(256) k_recast(const double* rt, R* r,
+                                                long n, const int* __restrict__ mask,
+                                                double* __restrict__ tr_out,
+                                                double* __restrict__ rr_out)
+{
+    const int rhs = blockIdx.y;
+    if (mask[rhs] == 0) return;
+    const long base = (long)rhs * n;
+    double at = 0.0, ar = 0.0;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+         k += (long)gridDim.x * blockDim.x) {
+        const double tv = rt[base + k];
+        const R rv = (R)tv;
+        if ((const void*)r != (const void*)rt) r[base + k] = rv;
+        at += tv * tv;
+        ar += (double)rv * (double)rv;
+    }
+    double s = block_sum(at);
+    if (threadIdx.x == 0) tr_out[(long)rhs * kRedStride + blockIdx.x] = s;
+    __syncthreads();
+    s = block_sum(ar);
+    if (threadIdx.x == 0) rr_out[(long)rhs * kRedStride + blockIdx.x] = s;
+}
+
+// out[rhs] = sum_k bank[rhs*kRedStride + k], k < cnt; one warp per rhs.
+__global__ void k_rows(const double* __restrict__ bank, int cnt, int n_rhs, double* __restrict__ out)
+{
+    const int rhs = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (rhs >= n_rhs) return;
+    const double s = warp_sum_array(bank + (long)rhs * kRedStride, cnt);
+    if ((threadIdx.x & 31) == 0) out[rhs] = s;
+}
+
+struct Banks {
+    double* pq;
+    double* rr[2];
+    double* tr;
+    double* bn;
+    double* red;   // [4][max_rhs] reduced per-rhs values
+};
+
+Banks banks_of(hol_ctx* c)
+{
+    Banks b;
+    b.pq = c->part;
+    b.rr[0] = c->part + 1 * c->part_len;
+    b.rr[1] = c->part + 2 * c->part_len;
+    b.tr = c->part + 3 * c->part_len;
+    b.bn = c->part + 4 * c->part_len;
+    b.red = c->part + 5 * c->part_len;
+    return b;
+}
+
+// Reduce bank rows to per-rhs values and copy them to the pinned host buffer.
+int rows_to_host(hol_ctx* c, const double* bank, int cnt, int n_rhs, double* host, cudaStream_t s)
+{
+    double* red = banks_of(c).red;
+    k_rows<<<ceil_div(32L * n_rhs, 256), 256, 0, s>>>(bank, cnt, n_rhs, red);
+    HOL_CHECK_LAUNCH("k_rows");
+    HOL_CUDA(cudaMemcpyAsync(host, red, n_rhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HOL_CUDA(cudaStreamSynchronize(s));
+    return HOL_OK;
+}
+
+}  // namespace
+
+int elementwise_blocks(const hol_ctx* c)
+{
+    const long v4 = c->n / 4;
+    long nb = (v4 + 1023) / 1024;   // about four vec4 per thread
+    if (nb < 1) nb = 1;
+    if (nb > kRedStride) nb = kRedStride;
+    return (int)nb;
+}
+
+// The CG loop shared by the FP64 and mixed paths (no preconditioner).
+static int cg_plain(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_opts* o,
+                    int* iters, double* resid, cudaStream_t s)
+{
+    const bool mixed = (o->prec == HOL_F32);
+    const long n = c->n;
+    const int nb2 = elementwise_blocks(c);
+    const dim3 g2(nb2, n_rhs);
+    const Banks B = banks_of(c);
+    const int pstride = matvec_pstride(c);
+    const int pq_n = c->T / c->mv_k;
+    int* act_d = c->mask;
+    int* rel_d = c->mask + c->p.max_rhs;
+    int* act_h = c->hflag;
+    int* rel_h = c->hflag + c->p.max_rhs;
+    double* hb = c->hbuf;
+
+    // FP64 path buffers / mixed path buffers
+    double* r64 = c->v64a;
+    double* p64[2] = {c->v64b, c->v64c};
+    double* q64 = c->v64d;
+    double* w64 = c->v64e;
+    float* r32 = c->v32a;
+    float* p32[2] = {c->v32b, c->v32c};
+    float* q32 = c->v32d;
+    float* e32 = c->v32e;
+    double* t64 = c->v64a;   // mixed: M v during a reliable update
+    double* rt64 = c->v64b;  // mixed: true residual
+
+    HOL_CUDA(cudaMemsetAsync(v, 0, (size_t)n_rhs * n * sizeof(double), s));
+    if (mixed)
+        k_cg_init<float><<<g2, 256, 0, s>>>(b, r32, e32, n, B.bn, B.rr[0]);
+    else
+        k_cg_init<double><<<g2, 256, 0, s>>>(b, r64, nullptr, n, B.bn, B.rr[0]);
+    HOL_CHECK_LAUNCH("k_cg_init");
+    int rc = rows_to_host(c, B.bn, nb2, n_rhs, hb, s);
+    if (rc) return rc;
+    std::vector<double> bnorm(n_rhs), true_res(n_rhs, 1.0);
+    std::vector<int> it(n_rhs, 0), since(n_rhs, 0), done(n_rhs, 0);
+    int n_active = 0;
+    for (int k = 0; k < n_rhs; ++k) {
+        bnorm[k] = sqrt(hb[k]);
+        if (!isfinite(bnorm[k])) return set_error(HOL_ENUMERIC, "cg_solve: non-finite |b|");
+        if (bnorm[k] == 0.0) {   // v = 0 is exact
+            done[k] = 1;
+            true_res[k] = 0.0;
+            act_h[k] = 0;
+        } else {
+            act_h[k] = 1;
+            ++n_active;
+        }
+        rel_h[k] = 0;
+    }
+    HOL_CUDA(cudaMemcpyAsync(act_d, act_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
+
+    int cur = 0;     // bank holding the current r.r partials
+    int pp = 0;      // p buffer holding the current direction
+    int first = 1;
+    int k_it = 0;
+    const int chk = o->check_every > 0 ? o->check_every : 10;
+    const int rel_every = (mixed && o->reliable_every > 0) ? o->reliable_every : 1 << 30;
+    while (n_active > 0 && k_it < o->max_iter) {
+        int chunk = chk;
+        if (chunk > o->max_iter - k_it) chunk = o->max_iter - k_it;
+        for (int j = 0; j < chunk; ++j) {
+            if (mixed) {
+                // on the first step beta = 0 and p_old is not yet defined: pass r
+                timer_start(c, KT_OPERATOR, s);
+                rc = launch_cg_mtm32(c, r32, first ? r32 : p32[pp], p32[1 - pp], q32, n_rhs,
+                                     act_d, B.rr[cur],
+                                     B.rr[1 - cur], kRedStride, nb2, first, B.pq, s);
+                if (rc) return rc;
+                timer_stop(c, KT_OPERATOR, s);
+                pp = 1 - pp;
+                timer_start(c, KT_UPDATE, s);
+                k_cg_update<float><<<g2, 256, 0, s>>>(e32, r32, p32[pp], q32, n, act_d, B.pq,
+                                                      pstride, pq_n, B.rr[cur], nb2, B.rr[1 - cur]);
+            } else {
+                BetaSrc bs{B.rr[cur], B.rr[1 - cur], kRedStride, nb2, first};
+                timer_start(c, KT_OPERATOR, s);
+                rc = launch_M_upd64(c, r64, first ? r64 : p64[pp], p64[1 - pp], w64, n_rhs, act_d,
+                                    bs, B.pq, s);
+                if (rc) return rc;
+                pp = 1 - pp;
+                rc = launch_MT(c, HOL_F64, w64, q64, n_rhs, act_d, s);
+                if (rc) return rc;
+                timer_stop(c, KT_OPERATOR, s);
+                timer_start(c, KT_UPDATE, s);
+                k_cg_update<double><<<g2, 256, 0, s>>>(v, r64, p64[pp], q64, n, act_d, B.pq,
+                                                       pstride, pq_n, B.rr[cur], nb2,
+                                                       B.rr[1 - cur]);
+            }
+            HOL_CHECK_LAUNCH("k_cg_update");
+            timer_stop(c, KT_UPDATE, s);
+            cur = 1 - cur;
+            first = 0;
+        }
+        k_it += chunk;
+        rc = rows_to_host(c, B.rr[cur], nb2, n_rhs, hb, s);
+        if (rc) return rc;
+        int n_rel = 0;
+        for (int k = 0; k < n_rhs; ++k) {
+            rel_h[k] = 0;
+            if (!act_h[k]) continue;
+            it[k] += chunk;
+            since[k] += chunk;
+            const double est = sqrt(hb[k]) / bnorm[k];
+            if (!isfinite(est))
+                return set_error(HOL_ENUMERIC, "cg_solve: non-finite residual (rhs %d, iter %d)",
+                                 k, it[k]);
+            if (est < o->tol || since[k] >= rel_every || k_it >= o->max_iter) {
+                rel_h[k] = 1;
+                ++n_rel;
+            }
+        }
+        if (n_rel == 0) continue;
+        // reliable update / convergence certification for the flagged rhs
+        HOL_CUDA(cudaMemcpyAsync(rel_d, rel_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
+        if (mixed) {
+            k_fold<<<g2, 256, 0, s>>>(v, e32, n, rel_d);
+            HOL_CHECK_LAUNCH("k_fold");
+            if ((rc = launch_M(c, HOL_F64, v, t64, n_rhs, rel_d, nullptr, s))) return rc;
+            if ((rc = launch_MT_resid64(c, t64, b, rt64, n_rhs, rel_d, s))) return rc;
+            k_recast<float><<<g2, 256, 0, s>>>(rt64, r32, n, rel_d, B.tr, B.rr[cur]);
+        } else {
+            if ((rc = launch_M(c, HOL_F64, v, w64, n_rhs, rel_d, nullptr, s))) return rc;
+            if ((rc = launch_MT_resid64(c, w64, b, r64, n_rhs, rel_d, s))) return rc;
+            k_recast<double><<<g2, 256, 0, s>>>(r64, r64, n, rel_d, B.tr, B.rr[cur]);
+        }
+        HOL_CHECK_LAUNCH("k_recast");
+        rc = rows_to_host(c, B.tr, nb2, n_rhs, hb, s);
+        if (rc) return rc;
+        int changed = 0;
+        for (int k = 0; k < n_rhs; ++k) {
+            if (!rel_h[k]) continue;
+            since[k] = 0;
+            true_res[k] = sqrt(hb[k]) / bnorm[k];
+            if (!isfinite(true_res[k]))
+                return set_error(HOL_ENUMERIC, "cg_solve: non-finite true residual (rhs %d)", k);
+            if (true_res[k] < o->tol) {
+                done[k] = 1;
+                act_h[k] = 0;
+                --n_active;
+                changed = 1;
+            }
+        }
+        if (changed)
+            HOL_CUDA(cudaMemcpyAsync(act_d, act_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    HOL_CUDA(cudaStreamSynchronize(s));
+    int all = 1;
+    for (int k = 0; k < n_rhs; ++k) {
+        if (iters) iters[k] = it[k];
+        if (resid) resid[k] = true_res[k];
+        all &= done[k];
+    }
+    if (!all)
+        return set_error(HOL_ENOTCONV, "cg_solve: not converged within %d iterations", o->max_iter);
+    return HOL_OK;
+}
+
+int cg_precond(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_opts* o,
+               int* iters, double* resid, cudaStream_t s);   // precond.cu
+
+}  // namespace hol
+
+using namespace hol;
+
+extern "C" int cg_solve(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_opts* o,
+                        int* iters, double* resid, void* stream)
+{
+    if (!c || !b || !v || !o) return set_error(HOL_EINVAL, "cg_solve: null argument");
+    if (!c->field_set) return set_error(HOL_EINVAL, "cg_solve: hol_set_field not called");
+    if (n_rhs < 1 || n_rhs > c->p.max_rhs)
+        return set_error(HOL_EINVAL, "cg_solve: n_rhs=%d outside [1, %d]", n_rhs, c->p.max_rhs);
+    if (o->prec != HOL_F64 && o->prec != HOL_F32)
+        return set_error(HOL_EINVAL, "cg_solve: bad precision %d", o->prec);
+    if (!(o->tol > 0.0) || o->max_iter < 1)
+        return set_error(HOL_EINVAL, "cg_solve: tol must be > 0 and max_iter >= 1");
+    if (b == v) return set_error(HOL_EINVAL, "cg_solve: b and v must not overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (o->precond) return cg_precond(c, b, v, n_rhs, o, iters, resid, s);
+    return cg_plain(c, b, v, n_rhs, o, iters, resid, s);
+}

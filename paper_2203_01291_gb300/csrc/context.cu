@@ -1,0 +1,330 @@
+// Context life cycle, error reporting, field set-up (Sec. II C) and the
+// fermion_matvec entry point.
+#include <math.h>
+#include <stdarg.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "cb.cuh"
+#include "internal.cuh"
+
+namespace hol {
+
+static thread_local char g_err[512] = "no error";
+static unsigned long long g_launches = 0;
+
+void count_launch() { __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED); }
+
+void timer_start(const hol_ctx* c, int k, cudaStream_t s)
+{
+    KTimer* t = c->timer;
+    if (!t || !t->on) return;
+    if (t->used[k] >= t->cap) {
+        t->dropped[k]++;
+        return;
+    }
+    cudaEventRecord(t->ev[k][2 * t->used[k]], s);
+}
+
+void timer_stop(const hol_ctx* c, int k, cudaStream_t s)
+{
+    KTimer* t = c->timer;
+    if (!t || !t->on || t->used[k] >= t->cap) return;
+    cudaEventRecord(t->ev[k][2 * t->used[k] + 1], s);
+    t->used[k]++;
+}
+
+static void timer_free(KTimer* t)
+{
+    if (!t) return;
+    for (int k = 0; k < KT_COUNT; ++k) {
+        if (!t->ev[k]) continue;
+        for (int j = 0; j < 2 * t->cap; ++j)
+            if (t->ev[k][j]) cudaEventDestroy(t->ev[k][j]);
+        free(t->ev[k]);
+    }
+    free(t);
+}
+
+int set_error(int code, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char* what)
+{
+    return set_error(e == cudaErrorMemoryAllocation ? HOL_ENOMEM : HOL_ECUDA, "%s: %s (%s)", what,
+                     cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+namespace {
+
+// expV = exp(-dtau (alpha x - mu)) in FP64 and FP32; copy of x.
+__global__ void k_expv(const double* __restrict__ x, double* __restrict__ xc,
+                       double* __restrict__ ev64, float* __restrict__ ev32, long n, double dtau,
+                       double alpha, double mu)
+{
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+         k += (long)gridDim.x * blockDim.x) {
+        const double xv = x[k];
+        const double e = exp(-dtau * (alpha * xv - mu));
+        xc[k] = xv;
+        ev64[k] = e;
+        ev32[k] = (float)e;
+    }
+}
+
+// dbar_i = (1/T) sum_tau expV[tau][i] (Eq. (expnVbar)); one thread per site.
+__global__ void k_dbar(const double* __restrict__ ev, double* __restrict__ dbar, int N, int T)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double s = 0.0;
+    for (int tau = 0; tau < T; ++tau) s += ev[(long)tau * N + i];
+    dbar[i] = s / T;
+}
+
+// Norm bounds of the Bbar spectrum: every checkerboard colour has
+// eigenvalues exp(+-dtau t), so |Bbar| <= max(dbar) e^{4 dtau |t|} and
+// |Bbar^{-1}| <= e^{4 dtau |t|} / min(dbar). One block.
+__global__ void k_bounds(const double* __restrict__ dbar, int N, double g4, double* __restrict__ scal)
+{
+    __shared__ double smin[32], smax[32];
+    double lo = 1e300, hi = -1e300;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        lo = fmin(lo, dbar[i]);
+        hi = fmax(hi, dbar[i]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(kFull, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(kFull, hi, o));
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        smin[w] = lo;
+        smax[w] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            lo = fmin(lo, smin[k]);
+            hi = fmax(hi, smax[k]);
+        }
+        scal[S_BMIN] = lo / g4;
+        scal[S_BMAX] = hi * g4;
+    }
+}
+
+void free_ctx(hol_ctx* c)
+{
+    if (!c) return;
+    void* dev[] = {c->x, c->ev64, c->ev32, c->dbar, c->scal, c->part, c->v64a, c->v64b,
+                   c->v64c, c->v64d, c->v64e, c->v32a, c->v32b, c->v32c, c->v32d, c->v32e,
+                   c->mask, c->kpm.np, c->kpm.coef, c->cbuf0, c->cbuf1};
+    for (void* p : dev)
+        if (p) cudaFree(p);
+    timer_free(c->timer);
+    if (c->hbuf) cudaFreeHost(c->hbuf);
+    if (c->hflag) cudaFreeHost(c->hflag);
+    free(c);
+}
+
+}  // namespace
+
+int kpm_setup(hol_ctx* c, cudaStream_t s);   // precond.cu
+
+}  // namespace hol
+
+using namespace hol;
+
+extern "C" const char* hol_last_error(void) { return g_err; }
+
+extern "C" int hol_create(const hol_params* p, hol_ctx** out)
+{
+    if (!p || !out) return set_error(HOL_EINVAL, "hol_create: null argument");
+    *out = nullptr;
+    if (p->L < 4 || p->L > kMaxL || (p->L & 1))
+        return set_error(HOL_EINVAL, "hol_create: L=%d must be even and in [4, %d]", p->L, kMaxL);
+    if (p->Ltau < 2 || (p->Ltau & 1))
+        return set_error(HOL_EINVAL, "hol_create: Ltau=%d must be even and >= 2", p->Ltau);
+    if (p->max_rhs < 1 || p->max_rhs > 4096)
+        return set_error(HOL_EINVAL, "hol_create: max_rhs=%d out of range", p->max_rhs);
+    if (!(p->dtau > 0.0) || !isfinite(p->t) || !isfinite(p->mu) || !isfinite(p->alpha) ||
+        !isfinite(p->omega0))
+        return set_error(HOL_EINVAL, "hol_create: non-finite or non-positive parameter");
+
+    hol_ctx* c = (hol_ctx*)calloc(1, sizeof(hol_ctx));
+    if (!c) return set_error(HOL_ENOMEM, "hol_create: host allocation failed");
+    c->p = *p;
+    c->L = p->L;
+    c->N = p->L * p->L;
+    c->T = p->Ltau;
+    c->n = (long)c->N * c->T;
+    c->ch = cosh(p->dtau * p->t);
+    c->sh = sinh(p->dtau * p->t);
+    c->mv_k = (c->T % 4 == 0 && c->T >= 8) ? 2 : 1;
+    c->mv_warps = 4;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        free_ctx(c);
+        return set_error(HOL_ECUDA, "hol_create: no CUDA device");
+    }
+
+    const long n = c->n, R = p->max_rhs;
+    const long pstride = matvec_pstride(c);
+    c->part_len = R * (pstride > kRedStride ? pstride : kRedStride);
+    c->cbuf_len = R * (long)(c->T / 2) * c->N;   // complex half spectra
+    c->kpm.max_np = 0;
+
+#define ALLOC(ptr, bytes)                                                 \
+    do {                                                                  \
+        cudaError_t e = cudaMalloc((void**)&(ptr), (bytes));              \
+        if (e != cudaSuccess) {                                           \
+            free_ctx(c);                                                  \
+            return cuda_error(e, "hol_create: cudaMalloc " #ptr);         \
+        }                                                                 \
+    } while (0)
+    ALLOC(c->x, n * sizeof(double));
+    ALLOC(c->ev64, n * sizeof(double));
+    ALLOC(c->ev32, n * sizeof(float));
+    ALLOC(c->dbar, c->N * sizeof(double));
+    ALLOC(c->scal, S_COUNT * sizeof(double));
+    ALLOC(c->part, kBanks * c->part_len * sizeof(double));
+    ALLOC(c->v64a, R * n * sizeof(double));
+    ALLOC(c->v64b, R * n * sizeof(double));
+    ALLOC(c->v64c, R * n * sizeof(double));
+    ALLOC(c->v64d, R * n * sizeof(double));
+    ALLOC(c->v64e, R * n * sizeof(double));
+    ALLOC(c->v32a, R * n * sizeof(float));
+    ALLOC(c->v32b, R * n * sizeof(float));
+    ALLOC(c->v32c, R * n * sizeof(float));
+    ALLOC(c->v32d, R * n * sizeof(float));
+    ALLOC(c->v32e, R * n * sizeof(float));
+    ALLOC(c->mask, 2 * R * sizeof(int));
+    ALLOC(c->cbuf0, c->cbuf_len * sizeof(double2));
+    ALLOC(c->cbuf1, c->cbuf_len * sizeof(double2));
+#undef ALLOC
+    if (cudaMallocHost((void**)&c->hbuf, 16 * R * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->hflag, 4 * R * sizeof(int)) != cudaSuccess) {
+        free_ctx(c);
+        return set_error(HOL_ENOMEM, "hol_create: pinned host allocation failed");
+    }
+    if (cudaMemset(c->scal, 0, S_COUNT * sizeof(double)) != cudaSuccess) {
+        free_ctx(c);
+        return set_error(HOL_ECUDA, "hol_create: memset");
+    }
+    *out = c;
+    return HOL_OK;
+}
+
+extern "C" int hol_destroy(hol_ctx* c)
+{
+    if (!c) return HOL_OK;
+    cudaDeviceSynchronize();
+    free_ctx(c);
+    return HOL_OK;
+}
+
+extern "C" int hol_set_field(hol_ctx* c, const double* x, void* stream)
+{
+    if (!c || !x) return set_error(HOL_EINVAL, "hol_set_field: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = ceil_div(c->n, 256) < 4096 ? ceil_div(c->n, 256) : 4096;
+    k_expv<<<nb, 256, 0, s>>>(x, c->x, c->ev64, c->ev32, c->n, c->p.dtau, c->p.alpha, c->p.mu);
+    HOL_CHECK_LAUNCH("k_expv");
+    k_dbar<<<ceil_div(c->N, 128), 128, 0, s>>>(c->ev64, c->dbar, c->N, c->T);
+    HOL_CHECK_LAUNCH("k_dbar");
+    k_bounds<<<1, 256, 0, s>>>(c->dbar, c->N, exp(4.0 * c->p.dtau * fabs(c->p.t)), c->scal);
+    HOL_CHECK_LAUNCH("k_bounds");
+    int rc = kpm_setup(c, s);
+    if (rc) return rc;
+    c->field_set = 1;
+    return HOL_OK;
+}
+
+extern "C" int fermion_matvec(hol_ctx* c, int op, int prec, const void* v, void* out, int n_rhs,
+                              void* stream)
+{
+    if (!c || !v || !out) return set_error(HOL_EINVAL, "fermion_matvec: null argument");
+    if (!c->field_set) return set_error(HOL_EINVAL, "fermion_matvec: hol_set_field not called");
+    if (n_rhs < 1 || n_rhs > c->p.max_rhs)
+        return set_error(HOL_EINVAL, "fermion_matvec: n_rhs=%d outside [1, %d]", n_rhs,
+                         c->p.max_rhs);
+    if (prec != HOL_F64 && prec != HOL_F32)
+        return set_error(HOL_EINVAL, "fermion_matvec: bad precision %d", prec);
+    if (v == out) return set_error(HOL_EINVAL, "fermion_matvec: v and out must not overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (op) {
+    case HOL_OP_M:
+        return launch_M(c, prec, v, out, n_rhs, nullptr, nullptr, s);
+    case HOL_OP_MT:
+        return launch_MT(c, prec, v, out, n_rhs, nullptr, s);
+    case HOL_OP_MTM:
+        if (prec == HOL_F32)
+            return launch_cg_mtm32(c, (const float*)v, (const float*)v, nullptr, (float*)out, n_rhs,
+                                   nullptr, nullptr, nullptr, 0, 0, 1, nullptr, s);
+        else {
+            int rc = launch_M(c, HOL_F64, v, c->v64a, n_rhs, nullptr, nullptr, s);
+            if (rc) return rc;
+            return launch_MT(c, HOL_F64, c->v64a, out, n_rhs, nullptr, s);
+        }
+    }
+    return set_error(HOL_EINVAL, "fermion_matvec: bad op %d", op);
+}
+
+extern "C" unsigned long long hol_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+extern "C" int hol_timer_enable(hol_ctx* c, int on)
+{
+    if (!c) return set_error(HOL_EINVAL, "hol_timer_enable: null context");
+    if (on && !c->timer) {
+        KTimer* t = (KTimer*)calloc(1, sizeof(KTimer));
+        if (!t) return set_error(HOL_ENOMEM, "hol_timer_enable: host allocation");
+        t->cap = 4096;
+        for (int k = 0; k < KT_COUNT; ++k) {
+            t->ev[k] = (cudaEvent_t*)calloc(2 * t->cap, sizeof(cudaEvent_t));
+            if (!t->ev[k]) {
+                timer_free(t);
+                return set_error(HOL_ENOMEM, "hol_timer_enable: host allocation");
+            }
+            for (int j = 0; j < 2 * t->cap; ++j) {
+                cudaError_t e = cudaEventCreate(&t->ev[k][j]);
+                if (e != cudaSuccess) {
+                    timer_free(t);
+                    return cuda_error(e, "hol_timer_enable: cudaEventCreate");
+                }
+            }
+        }
+        c->timer = t;
+    }
+    if (c->timer) {
+        c->timer->on = on ? 1 : 0;
+        if (on)
+            for (int k = 0; k < KT_COUNT; ++k) c->timer->used[k] = c->timer->dropped[k] = 0;
+    }
+    return HOL_OK;
+}
+
+extern "C" int hol_timer_read(hol_ctx* c, int klass, int* count, double* total_ms)
+{
+    if (!c || !count || !total_ms || klass < 0 || klass >= KT_COUNT)
+        return set_error(HOL_EINVAL, "hol_timer_read: bad argument");
+    *count = 0;
+    *total_ms = 0.0;
+    KTimer* t = c->timer;
+    if (!t) return HOL_OK;
+    double tot = 0.0;
+    for (int j = 0; j < t->used[klass]; ++j) {
+        HOL_CUDA(cudaEventSynchronize(t->ev[klass][2 * j + 1]));
+        float ms = 0.0f;
+        HOL_CUDA(cudaEventElapsedTime(&ms, t->ev[klass][2 * j], t->ev[klass][2 * j + 1]));
+        tot += ms;
+    }
+    *count = t->used[klass];
+    *total_ms = tot;
+    return HOL_OK;
+}

@@ -1,0 +1,158 @@
+// Phonon force dS/dx = dS_B/dx + dS_F/dx (Sec. III A) and S_F (Eq. (Sf_Psi)).
+//
+// With b = Lambda^{-T} Phi and v = (M^T M)^{-1} b, Eq. (dSF_dx) with
+// dA = dM Lambda + M dLambda reduces, for the Holstein B_tau, to one M sweep:
+//   dS_F/dx_{i,tau} = dtau alpha s_tau u_{i,tau} y_{i,tau}
+//                     - (dtau alpha / 2) b_{i,tau-1} v_{i,tau-1},
+//   y_tau = exp(-dtau V_tau) C v_{tau-1},  u_tau = v_tau + s_tau y_tau,
+// so the kernel recomputes B_tau v_{tau-1} slice by slice (nothing of M is
+// stored) and adds the bosonic stencil of Eq. (dSB_dx).
+#include "cb.cuh"
+#include "internal.cuh"
+
+namespace hol {
+namespace {
+
+struct ForceArgs {
+    int T, K, nrun, n_pf;
+    long n;
+    int with_bos;
+    double ch, sh, da, dtau, w02;
+};
+
+template <int L>
+__global__ void __launch_bounds__(128) k_force(const double* __restrict__ v,
+                                               const double* __restrict__ b,
+                                               const double* __restrict__ x,
+                                               const double* __restrict__ ev,
+                                               double* __restrict__ F,
+                                               double* __restrict__ sf_part, ForceArgs a)
+{
+    constexpr int N = L * L;
+    const LaneGeom<L> geo;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp * LaneGeom<L>::G >= a.nrun) return;
+    const int run = warp * LaneGeom<L>::G + geo.g;
+    const bool valid = geo.ok && run < a.nrun;
+    const int t0 = (run < a.nrun ? run : a.nrun - 1) * a.K;
+    double acc = 0.0;
+    for (int s = 0; s < a.K; ++s) {
+        const int tau = t0 + s;
+        const int tm = (tau == 0) ? a.T - 1 : tau - 1;
+        const int tp = (tau + 1 == a.T) ? 0 : tau + 1;
+        const double sg = (tau == 0) ? 1.0 : -1.0;
+        double f[L];
+#pragma unroll
+        for (int iy = 0; iy < L; ++iy) {
+            f[iy] = 0.0;
+            if (a.with_bos) {
+                const long o = iy * L + geo.ix;
+                const double xc = x[(long)tau * N + o];
+                const double lap = x[(long)tp * N + o] - 2.0 * xc + x[(long)tm * N + o];
+                f[iy] = a.dtau * (a.w02 * xc - lap / (a.dtau * a.dtau));
+            }
+        }
+        for (int sp = 0; sp < a.n_pf; ++sp) {
+            const long base = (long)sp * a.n + geo.ix;
+            double c[L];
+#pragma unroll
+            for (int iy = 0; iy < L; ++iy) {
+                const long o = base + (long)tm * N + iy * L;
+                const double vv = v[o];
+                const double bv = b[o] * vv;
+                acc += bv;
+                f[iy] -= 0.5 * a.da * bv;
+                c[iy] = vv;
+            }
+            cb_apply<double, L>(c, geo, a.ch, a.sh);
+#pragma unroll
+            for (int iy = 0; iy < L; ++iy) {
+                const double y = ev[(long)tau * N + iy * L + geo.ix] * c[iy];
+                const double vt = v[base + (long)tau * N + iy * L];
+                f[iy] += a.da * (sg * vt * y + y * y);
+            }
+        }
+        if (valid) {
+#pragma unroll
+            for (int iy = 0; iy < L; ++iy) F[(long)tau * N + iy * L + geo.ix] = f[iy];
+        }
+    }
+    // per-unit sum of b.v over the slices tau-1 of the run
+    __shared__ double red[32 * 4];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    red[w * 32 + lane] = valid ? acc : 0.0;
+    __syncwarp();
+    if (valid && geo.ix == 0) {
+        double ssum = 0.0;
+        for (int k = 0; k < L; ++k) ssum += red[w * 32 + geo.g * L + k];
+        sf_part[run] = ssum;
+    }
+}
+
+// S_F = (1/2) sum of the unit partials (one warp).
+__global__ void k_sf_finish(const double* __restrict__ part, int cnt, double* __restrict__ out)
+{
+    const double s = warp_sum_array(part, cnt);
+    if (threadIdx.x == 0) *out = 0.5 * s;
+}
+
+template <int L>
+int run_force(hol_ctx* c, const double* v, const double* b, int n_pf, double* F, int with_bos,
+              double* sf_part, cudaStream_t s)
+{
+    ForceArgs a;
+    a.T = c->T;
+    a.K = c->mv_k;
+    a.nrun = c->T / c->mv_k;
+    a.n_pf = n_pf;
+    a.n = c->n;
+    a.with_bos = with_bos;
+    a.ch = c->ch;
+    a.sh = c->sh;
+    a.da = c->p.dtau * c->p.alpha;
+    a.dtau = c->p.dtau;
+    a.w02 = c->p.omega0 * c->p.omega0;
+    const int warps = ceil_div(a.nrun, LaneGeom<L>::G);
+    k_force<L><<<ceil_div(warps, 4), 128, 0, s>>>(v, b, c->x, c->ev64, F, sf_part, a);
+    HOL_CHECK_LAUNCH("k_force");
+    return HOL_OK;
+}
+
+}  // namespace
+
+int launch_force(hol_ctx* c, const double* v, const double* b, int n_pf, double* F, int with_bos,
+                 double* S_F, cudaStream_t s)
+{
+    double* sf_part = c->part + 6 * c->part_len;
+    int rc = HOL_EINVAL;
+    switch (c->L) {
+#define X(LL) case LL: rc = run_force<LL>(c, v, b, n_pf, F, with_bos, sf_part, s); break;
+        X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32)
+#undef X
+    default:
+        return set_error(HOL_EINVAL, "unsupported L=%d", c->L);
+    }
+    if (rc) return rc;
+    if (S_F != nullptr) {
+        k_sf_finish<<<1, 32, 0, s>>>(sf_part, c->T / c->mv_k, S_F);
+        HOL_CHECK_LAUNCH("k_sf_finish");
+    }
+    return HOL_OK;
+}
+
+}  // namespace hol
+
+using namespace hol;
+
+extern "C" int force(hol_ctx* c, const double* v, const double* b, int n_pf, double* dSdx,
+                     int with_bosonic, double* S_F, void* stream)
+{
+    if (!c || !v || !b || !dSdx) return set_error(HOL_EINVAL, "force: null argument");
+    if (!c->field_set) return set_error(HOL_EINVAL, "force: hol_set_field not called");
+    if (n_pf < 0 || n_pf > c->p.max_rhs)
+        return set_error(HOL_EINVAL, "force: n_pf=%d outside [0, %d]", n_pf, c->p.max_rhs);
+    timer_start(c, KT_FORCE, (cudaStream_t)stream);
+    int rc = launch_force(c, v, b, n_pf, dSdx, with_bosonic, S_F, (cudaStream_t)stream);
+    timer_stop(c, KT_FORCE, (cudaStream_t)stream);
+    return rc;
+}

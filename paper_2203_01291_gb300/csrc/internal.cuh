@@ -1,0 +1,166 @@
+// Internal declarations of the Holstein GB300 library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/holstein.h"
+
+namespace hol {
+
+// ----------------------------------------------------------------------------
+// error reporting
+// ----------------------------------------------------------------------------
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+
+#define HOL_CUDA(call)                                        \
+    do {                                                      \
+        cudaError_t e__ = (call);                             \
+        if (e__ != cudaSuccess) return hol::cuda_error(e__, #call); \
+    } while (0)
+
+// Every kernel launch is followed by this check, which also counts it.
+#define HOL_CHECK_LAUNCH(what)                                \
+    do {                                                      \
+        hol::count_launch();                                  \
+        cudaError_t e__ = cudaGetLastError();                 \
+        if (e__ != cudaSuccess) return hol::cuda_error(e__, what); \
+    } while (0)
+
+void count_launch();
+
+// Optional CUDA-event timing of kernel classes (hol_timer_* entry points).
+enum TimerClass { KT_OPERATOR = 0, KT_UPDATE = 1, KT_FORCE = 2, KT_PRECOND = 3, KT_OTHER = 4,
+                  KT_COUNT = 5 };
+struct KTimer {
+    int on;
+    int cap;                       // event pairs per class
+    int used[KT_COUNT];
+    int dropped[KT_COUNT];
+    cudaEvent_t* ev[KT_COUNT];     // 2*cap events per class
+};
+// Record the start / stop of a timed region of class k on stream s (no-op
+// when timing is off or the pool is full).
+void timer_start(const hol_ctx* c, int k, cudaStream_t s);
+void timer_stop(const hol_ctx* c, int k, cudaStream_t s);
+
+// Largest supported lattice side (one lane per column, L values per lane).
+constexpr int kMaxL = 32;
+// Blocks per right-hand side of the element-wise CG kernels (fixed, so the
+// partial-sum banks have a fixed stride).
+constexpr int kRedStride = 256;
+// Number of partial-sum banks in hol_ctx::part.
+constexpr int kBanks = 8;
+
+// Device-side scalars kept by a context (FP64).
+enum Scalar {
+    S_BMIN = 0,   // lower bound of the Bbar spectrum (modulus)
+    S_BMAX = 1,   // upper bound
+    S_SF = 2,     // scratch for the fermion action
+    S_COUNT = 8
+};
+
+// Chebyshev plan of the adiabatic preconditioner (set in hol_set_field).
+struct KpmPlan {
+    int max_np;          // capacity per omega
+    int* np;             // [T/2]  polynomial order N_P(omega)
+    double2* coef;       // [T/2][max_np] complex c_m(omega)
+};
+
+}  // namespace hol
+
+struct hol_ctx {
+    hol_params p;
+    int L, N, T;
+    long n;              // N * T
+    int device;
+    double ch, sh;       // cosh, sinh (dtau t)
+
+    // field-derived data (hol_set_field)
+    double* x;           // [T][N] copy of the field
+    double* ev64;        // [T][N] exp(-dtau (alpha x - mu))
+    float* ev32;         // [T][N] float copy
+    double* dbar;        // [N] tau-average of ev64
+    double* scal;        // [S_COUNT] device scalars
+    int field_set;
+
+    hol::KpmPlan kpm;
+
+    // solver workspace, sized for max_rhs right-hand sides
+    double* part;        // partial sums, 4 banks of part_len doubles
+    long part_len;
+    double* v64a;        // FP64 vectors [max_rhs][T][N]
+    double* v64b;
+    double* v64c;
+    double* v64d;
+    double* v64e;
+    float* v32a;         // FP32 vectors [max_rhs][T][N]
+    float* v32b;
+    float* v32c;
+    float* v32d;
+    float* v32e;
+    int* mask;           // [2*max_rhs] active / reliable-update flags (device)
+    double2* cbuf0;      // complex half-spectrum buffers [max_rhs][T/2][N]
+    double2* cbuf1;
+    long cbuf_len;
+    double* hbuf;        // pinned host staging (doubles)
+    int* hflag;          // pinned host staging (ints)
+
+    hol::KTimer* timer;  // kernel timers (nullptr until enabled)
+
+    // per-shape launch choices
+    int mv_k;            // tau slices per lane group in the matvec kernels
+    int mv_warps;        // warps per block in the matvec kernels
+};
+
+namespace hol {
+
+// fermion operator kernels (matvec.cu) -----------------------------------------
+enum MtEpilogue { MT_PLAIN = 0, MT_RESID = 1 };
+
+// out = M v (double or float per prec). norm_part (nullable): per-unit
+// sums of |out|^2 at stride matvec_pstride(c) per right-hand side.
+int launch_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs,
+             const int* mask, double* norm_part, cudaStream_t s);
+// Where the CG beta = rr_new / rr_old of each right-hand side comes from:
+// partial sums at rn[rhs*stride + k] and ro[rhs*stride + k], k < n.
+struct BetaSrc {
+    const double* rn;
+    const double* ro;
+    int stride;
+    int n;
+    int first;   // nonzero: beta = 0
+};
+// FP64 CG direction update fused with M: pnew = r + beta pold, w = M pnew.
+int launch_M_upd64(const hol_ctx* c, const double* r, const double* pold, double* pnew,
+                   double* w, int n_rhs, const int* mask, BetaSrc beta,
+                   double* norm_part, cudaStream_t s);
+// out = M^T u.
+int launch_MT(const hol_ctx* c, int prec, const void* u, void* out, int n_rhs,
+              const int* mask, cudaStream_t s);
+// FP64: out = b - M^T u.
+int launch_MT_resid64(const hol_ctx* c, const double* u, const double* b, double* out,
+                      int n_rhs, const int* mask, cudaStream_t s);
+// FP32 fused CG step: pnew = r + beta pold (beta from the partial sums
+// rr_new / rr_old, 0 when first), q = M^T M pnew, pq_part = |M pnew|^2.
+// pnew and pq_part may be null.
+int launch_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pnew,
+                    float* q, int n_rhs, const int* mask, const double* rr_new,
+                    const double* rr_old, int rr_stride, int rr_n, int first,
+                    double* pq_part, cudaStream_t s);
+int matvec_pstride(const hol_ctx* c);          // per-rhs stride of unit partials
+int matvec_units(const hol_ctx* c, int n_rhs); // upper bound of units per call
+
+// Lambda^T (transpose_forward) or Lambda^{-T} applied to nv vectors.
+int launch_lambda(const hol_ctx* c, bool transpose_forward, const double* w, double* out,
+                  int nv, cudaStream_t s);
+int launch_force(hol_ctx* c, const double* v, const double* b, int n_pf, double* F,
+                 int with_bos, double* S_F, cudaStream_t s);
+int elementwise_blocks(const hol_ctx* c);
+
+// helpers ----------------------------------------------------------------------
+inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace hol

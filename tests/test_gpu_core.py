@@ -1,0 +1,285 @@
+"""GPU parity of the core path (set-up, M / M^T / M^T M, CG, force, Phi and b)
+against the oracle, through the C ABI. Marked gpu.
+
+Tolerances
+----------
+* FP64 operators: 1e-13 of max|ref| (a handful of roundings per entry).
+* FP32 operators: 3e-6 of max|ref| (FP32 epsilon 6e-8 times the ~20
+  roundings of a checkerboard sweep, two sweeps for M^T M, some headroom).
+* FP64 CG: the certified true residual is below tol; the solution error is
+  bounded by kappa(M^T M) * tol with kappa computed from the dense matrix.
+* Forces from the same (v, b): 1e-12 of max|ref| in FP64.
+"""
+import numpy as np
+import pytest
+import torch
+
+import holstein_inputs as hi
+from oracle import dense as D
+from oracle import matfree as MF
+
+pytestmark = pytest.mark.gpu
+
+hg = pytest.importorskip("paper_2203_01291_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    hg.build.build()
+    torch.cuda.set_device(0)
+
+
+DEV = "cuda"
+SHAPES = [(4, 40), (6, 12), (8, 24), (12, 10), (16, 8)]
+MF_SHAPES = [(20, 6), (24, 8), (28, 4), (32, 6), (10, 14), (30, 4)]
+
+
+def _field(L, T, seed=3, std=1.0):
+    w = hi.Workload("t", L=L, Ltau=T, alpha=1.2, mu=0.1, omega0=0.8, x_std=std, seed=seed)
+    return w, hi.phonon_field(w)
+
+
+def _ctx(w, max_rhs):
+    return hg.Context(L=w.L, Ltau=w.Ltau, dtau=w.dtau, t=w.t, mu=w.mu, alpha=w.alpha,
+                      omega0=w.omega0, max_rhs=max_rhs)
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
+
+
+@pytest.mark.parametrize("L,T", SHAPES)
+def test_operators_vs_dense(L, T):
+    w, x = _field(L, T)
+    m = D.model_of(w)
+    nr = 3
+    v = hi.gaussian_vectors(w, nr, seed=7)
+    Mx = D.fermion_matrix(m, x)
+    ref = {hg.HOL_OP_M: np.stack([(Mx @ a.reshape(-1)).reshape(T, -1) for a in v]),
+           hg.HOL_OP_MT: np.stack([(Mx.T @ a.reshape(-1)).reshape(T, -1) for a in v])}
+    ref[hg.HOL_OP_MTM] = np.stack([(Mx.T @ (Mx @ a.reshape(-1))).reshape(T, -1) for a in v])
+    with _ctx(w, nr) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        for op, r in ref.items():
+            for dt, tol in ((torch.float64, 1e-13), (torch.float32, 3e-6)):
+                vt = torch.tensor(v, device=DEV, dtype=dt)
+                out = torch.empty_like(vt)
+                ctx.fermion_matvec(op, vt, out)
+                assert _rel(out.cpu().double().numpy(), r) < tol, (op, dt)
+
+
+@pytest.mark.parametrize("L,T", MF_SHAPES)
+def test_operators_vs_matrix_free(L, T):
+    w, x = _field(L, T, seed=11)
+    v = hi.gaussian_vectors(w, 2, seed=8)
+    ref_M = np.stack([MF.M_apply(w, x, a) for a in v])
+    ref_MT = np.stack([MF.MT_apply(w, x, a) for a in v])
+    ref_MTM = np.stack([MF.MTM_apply(w, x, a) for a in v])
+    with _ctx(w, 2) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        for op, r in ((hg.HOL_OP_M, ref_M), (hg.HOL_OP_MT, ref_MT), (hg.HOL_OP_MTM, ref_MTM)):
+            for dt, tol in ((torch.float64, 1e-13), (torch.float32, 3e-6)):
+                vt = torch.tensor(v, device=DEV, dtype=dt)
+                out = torch.empty_like(vt)
+                ctx.fermion_matvec(op, vt, out)
+                assert _rel(out.cpu().double().numpy(), r) < tol, (op, dt)
+
+
+def test_operators_full_size_big32():
+    """L=32, Ltau=200, 16 right-hand sides (the benchmark workload): every
+    output element against the matrix-free oracle."""
+    w = hi.WORKLOADS["big32"]
+    x = hi.phonon_field(w)
+    v = hi.gaussian_vectors(w, w.n_rhs, seed=21)
+    with _ctx(w, w.n_rhs) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        for op, f in ((hg.HOL_OP_M, MF.M_apply), (hg.HOL_OP_MT, MF.MT_apply),
+                      (hg.HOL_OP_MTM, MF.MTM_apply)):
+            ref = np.stack([f(w, x, a) for a in v])
+            for dt, tol in ((torch.float64, 1e-13), (torch.float32, 3e-6)):
+                vt = torch.tensor(v, device=DEV, dtype=dt)
+                out = torch.empty_like(vt)
+                ctx.fermion_matvec(op, vt, out)
+                assert _rel(out.cpu().double().numpy(), ref) < tol, (op, dt)
+
+
+def test_cg_fp64_tiny_vs_lu():
+    w = hi.WORKLOADS["tiny"]
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    R = hi.gaussian_vectors(w, 2, seed=2)
+    b = np.stack([D.MT_apply(m, x, r) for r in R])        # b = M^T R (Phi = A^T R)
+    Mx = D.fermion_matrix(m, x)
+    kappa = np.linalg.cond(Mx.T @ Mx)
+    vref = np.stack([D.solve_MTM(m, x, bb) for bb in b])
+    tol = 1e-13
+    with _ctx(w, 2) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        bt = torch.tensor(b, device=DEV)
+        v = torch.empty_like(bt)
+        its, res = ctx.cg_solve(bt, v, tol=tol, prec=hg.HOL_F64)
+        vg = v.cpu().numpy()
+    for k in range(2):
+        assert res[k] < tol
+        assert D.rel_residual(m, x, b[k], vg[k]) < 2 * tol
+        assert np.linalg.norm(vg[k] - vref[k]) / np.linalg.norm(vref[k]) < 2 * kappa * tol
+        # v = M^{-1} R (Sec. II D)
+        assert _rel(D.M_apply(m, x, vg[k]), R[k]) < 1e-9
+
+
+@pytest.mark.parametrize("check_every", [1, 7, 25])
+def test_cg_mixed_tiny(check_every):
+    w = hi.WORKLOADS["tiny"]
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    R = hi.gaussian_vectors(w, 2, seed=2)
+    b = np.stack([D.MT_apply(m, x, r) for r in R])
+    vref = np.stack([D.solve_MTM(m, x, bb) for bb in b])
+    Mx = D.fermion_matrix(m, x)
+    kappa = np.linalg.cond(Mx.T @ Mx)
+    with _ctx(w, 2) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        bt = torch.tensor(b, device=DEV)
+        v = torch.empty_like(bt)
+        its, res = ctx.cg_solve(bt, v, tol=1e-8, prec=hg.HOL_F32, reliable_every=20,
+                                check_every=check_every)
+        vg = v.cpu().numpy()
+    for k in range(2):
+        assert res[k] < 1e-8
+        assert D.rel_residual(m, x, b[k], vg[k]) < 1e-8
+        assert np.linalg.norm(vg[k] - vref[k]) / np.linalg.norm(vref[k]) < kappa * 1e-8
+
+
+def test_cg_big32_mixed_and_fp64_certified_by_oracle():
+    """The benchmark solve: 16 right-hand sides b = M^T R at L=32, Ltau=200,
+    mixed precision to 1e-8 and FP64 to 1e-8; residuals recomputed by the
+    matrix-free oracle; the two solutions agree to the conditioning bound."""
+    w = hi.WORKLOADS["big32"]
+    x = hi.phonon_field(w)
+    R = hi.gaussian_vectors(w, w.n_rhs, seed=2)
+    with _ctx(w, w.n_rhs) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        Rt = torch.tensor(R, device=DEV)
+        bt = torch.empty_like(Rt)
+        ctx.fermion_matvec(hg.HOL_OP_MT, Rt, bt)          # b = M^T R on the GPU
+        b = bt.cpu().numpy()
+        assert _rel(b[0], MF.MT_apply(w, x, R[0])) < 1e-13
+        vm = torch.empty_like(bt)
+        its_m, res_m = ctx.cg_solve(bt, vm, tol=1e-8, prec=hg.HOL_F32, reliable_every=50)
+        v64 = torch.empty_like(bt)
+        its_d, res_d = ctx.cg_solve(bt, v64, tol=1e-8, prec=hg.HOL_F64)
+        vm, v64 = vm.cpu().numpy(), v64.cpu().numpy()
+    for k in range(w.n_rhs):
+        assert res_m[k] < 1e-8 and res_d[k] < 1e-8
+        assert MF.rel_residual(w, x, b[k], vm[k]) < 1.01e-8
+        assert MF.rel_residual(w, x, b[k], v64[k]) < 1.01e-8
+        # v = M^{-1} R: |M v - R| / |R| <= |M^{-T}| |b - M^T M v| / |R| is small
+        assert np.linalg.norm(MF.M_apply(w, x, vm[k]) - R[k]) / np.linalg.norm(R[k]) < 1e-4
+
+
+def test_cg_zero_rhs_and_errors():
+    w = hi.WORKLOADS["tiny"]
+    x = hi.phonon_field(w)
+    with _ctx(w, 2) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        b = torch.zeros(2, w.Ltau, w.N, device=DEV, dtype=torch.float64)
+        b[1] = 1.0
+        v = torch.empty_like(b)
+        its, res = ctx.cg_solve(b, v, tol=1e-10)
+        assert res[0] == 0.0 and float(v[0].abs().max()) == 0.0 and res[1] < 1e-10
+        with pytest.raises(hg.HolError) as e:
+            ctx.cg_solve(b, v, tol=1e-12, max_iter=1)
+        assert e.value.code == hg._abi.HOL_ENOTCONV
+        with pytest.raises(hg.HolError):
+            ctx.cg_solve(b, b, tol=1e-10)              # aliasing refused
+        bad = torch.zeros(3, w.Ltau, w.N, device=DEV, dtype=torch.float64)
+        with pytest.raises(hg.HolError):
+            ctx.cg_solve(bad, torch.empty_like(bad))  # n_rhs > max_rhs
+
+
+def test_invalid_shapes_rejected():
+    for L, T in ((3, 8), (34, 8), (8, 7), (2, 8)):
+        with pytest.raises(hg.HolError):
+            hg.Context(L=L, Ltau=T)
+
+
+def test_phi_and_rhs_vs_dense():
+    w = hi.WORKLOADS["tiny"]
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    R = hi.gaussian_vectors(w, 2, seed=5)
+    Phi_ref = D.phi_from_R(m, x, R)
+    x2 = x + 0.3
+    b_ref = D.b_from_phi(m, x2, Phi_ref)
+    with _ctx(w, 2) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        Phi = torch.empty(2, w.Ltau, w.N, device=DEV, dtype=torch.float64)
+        ctx.pseudofermion_phi(torch.tensor(R, device=DEV), Phi)
+        assert _rel(Phi.cpu().numpy(), Phi_ref) < 1e-13
+        ctx.set_field(torch.tensor(x2, device=DEV))
+        b = torch.empty_like(Phi)
+        ctx.phi_to_rhs(Phi, b)
+        assert _rel(b.cpu().numpy(), b_ref) < 1e-13
+
+
+@pytest.mark.parametrize("L,T", [(4, 40), (6, 10), (8, 12)])
+def test_force_vs_dense_definition(L, T):
+    w, x = _field(L, T, seed=13)
+    m = D.model_of(w)
+    Phi = hi.gaussian_vectors(w, 2, seed=14)
+    b = D.b_from_phi(m, x, Phi)
+    v = np.stack([D.solve_MTM(m, x, bb) for bb in b])
+    F_ref = D.dS_dx(m, x, Phi)
+    SF_ref = D.S_F(m, x, Phi)
+    with _ctx(w, 2) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        F = torch.empty(w.Ltau, w.N, device=DEV, dtype=torch.float64)
+        SF = torch.empty(1, device=DEV, dtype=torch.float64)
+        ctx.force(torch.tensor(v, device=DEV), torch.tensor(b, device=DEV), F, True, SF)
+        assert _rel(F.cpu().numpy(), F_ref) < 1e-12
+        assert abs(float(SF) - SF_ref) < 1e-11 * abs(SF_ref)
+        Fb = torch.empty_like(F)
+        ctx.force(torch.tensor(v, device=DEV), torch.tensor(b, device=DEV), Fb, False)
+        assert _rel(Fb.cpu().numpy(), D.dSF_dx(m, x, Phi)) < 1e-12
+
+
+def test_force_full_size_grad24_vs_matrix_free():
+    w = hi.WORKLOADS["grad24"]
+    x = hi.phonon_field(w)
+    v = hi.gaussian_vectors(w, 2, seed=30)
+    b = hi.gaussian_vectors(w, 2, seed=31)
+    ref = MF.force_fermion(w, x, v[0], b[0]) + MF.force_fermion(w, x, v[1], b[1]) \
+        + MF.force_boson(w, x)
+    with _ctx(w, 2) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        F = torch.empty(w.Ltau, w.N, device=DEV, dtype=torch.float64)
+        SF = torch.empty(1, device=DEV, dtype=torch.float64)
+        ctx.force(torch.tensor(v, device=DEV), torch.tensor(b, device=DEV), F, True, SF)
+        assert _rel(F.cpu().numpy(), ref) < 1e-12
+        assert abs(float(SF) - 0.5 * np.sum(b * v)) < 1e-10 * np.abs(b * v).sum()
+
+
+def test_end_to_end_force_matches_oracle_tiny():
+    """x -> Phi (GPU) -> b -> CG (GPU, FP64) -> force (GPU) against the dense
+    oracle's Eq. (dSF_dx) at the same Phi."""
+    w = hi.WORKLOADS["tiny"]
+    m = D.model_of(w)
+    x0 = hi.phonon_field(w)
+    x = x0 + 0.05 * hi.gaussian_vectors(w, 1, seed=40)[0]
+    R = hi.gaussian_vectors(w, 2, seed=41)
+    Phi_ref = D.phi_from_R(m, x0, R)
+    F_ref = D.dS_dx(m, x, Phi_ref)
+    with _ctx(w, 2) as ctx:
+        ctx.set_field(torch.tensor(x0, device=DEV))
+        Phi = torch.empty(2, w.Ltau, w.N, device=DEV, dtype=torch.float64)
+        ctx.pseudofermion_phi(torch.tensor(R, device=DEV), Phi)
+        ctx.set_field(torch.tensor(x, device=DEV))
+        b = torch.empty_like(Phi)
+        ctx.phi_to_rhs(Phi, b)
+        v = torch.empty_like(b)
+        ctx.cg_solve(b, v, tol=1e-13)
+        F = torch.empty(w.Ltau, w.N, device=DEV, dtype=torch.float64)
+        ctx.force(v, b, F, True)
+        assert _rel(F.cpu().numpy(), F_ref) < 1e-9
