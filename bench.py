@@ -58,10 +58,14 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["step", "matvec"], default="step")
+    ap.add_argument("--mode", choices=["step", "matvec", "precond"], default="step")
     ap.add_argument("--rhs", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--field", choices=["iid", "ar1"], default="iid",
+                    help="phonon field: i.i.d. Gaussian (default) or tau-correlated AR(1)")
+    ap.add_argument("--precond", action="store_true",
+                    help="time the adiabatic-preconditioned solve as the main step")
     return ap.parse_args()
 
 
@@ -209,7 +213,10 @@ def run_ours(a):
     dev = torch.device("cuda", torch.cuda.current_device())
     w = WORKLOAD
     nr = w.n_rhs
-    x = hi.phonon_field(w, seed=w.seed + 100 * rank)
+    if a.field == "ar1":
+        x = hi.phonon_field_ar1(w, corr=1.0 / w.omega0, seed=w.seed + 100 * rank)
+    else:
+        x = hi.phonon_field(w, seed=w.seed + 100 * rank)
     R = hi.gaussian_vectors(w, nr, seed=2 + 100 * rank)
     ctx = hg.Context.from_workload(w, max_rhs=nr)
     xd = torch.tensor(x, device=dev)
@@ -220,11 +227,11 @@ def run_ours(a):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stats = {"iters": [], "resid": []}
 
-    def step(xin, Rin, prec=hg.HOL_F32):
+    def step(xin, Rin, prec=hg.HOL_F32, precond=a.precond):
         ctx.set_field(xin)
         ctx.fermion_matvec(hg.HOL_OP_MT, Rin, bd)
         it, res = ctx.cg_solve(bd, vd, tol=TOL, prec=prec, reliable_every=RELIABLE_EVERY,
-                               check_every=10, max_iter=50000)
+                               check_every=10, max_iter=50000, precond=precond)
         ctx.force(vd, bd, Fd, with_bosonic=True)
         return it, res
 
@@ -253,6 +260,7 @@ def run_ours(a):
     op_cnt, op_ms = ctx.timer_read(hg.TIMER_OPERATOR)
     up_cnt, up_ms = ctx.timer_read(hg.TIMER_UPDATE)
     fo_cnt, fo_ms = ctx.timer_read(hg.TIMER_FORCE)
+    pc_cnt, pc_ms = ctx.timer_read(hg.TIMER_PRECOND)
     ctx.timer_enable(False)
     clk = clocks.stop()
     barrier(world)
@@ -269,11 +277,14 @@ def run_ours(a):
     mv = float(np.sum(2 * iters + 1 + 2 * rel + 1))
     total_mv = reduce_sum(world, mv)
 
-    # roofline of the fused FP32 M^T M (reads r, p_old; writes p_new, q; reads expV)
+    # roofline of the fused FP32 M^T M: per launch it reads r, p_old and expV
+    # and writes p_new and q for every active right-hand side. Launch times are
+    # CUDA events recorded by the library on the launching stream during the
+    # timed region (every recorded launch; the pool holds the first ones).
     n = w.n
-    alg_bytes = float(np.sum(iters)) * n * 4 * 4 + op_cnt * n * 4
     op_avg_ms = op_ms / max(op_cnt, 1)
-    achieved = alg_bytes / (op_ms / 1e3) / 1e9
+    alg_bytes = float(nr * n * 4 * 4 + n * 4)   # all 16 rhs active (early iterations)
+    achieved = alg_bytes / (op_avg_ms / 1e3) / 1e9
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
     traffic = None
@@ -305,6 +316,26 @@ def run_ours(a):
         fp64 = {"solves_per_s": nr / (ms64 / 1e3), "ms_per_step": ms64,
                 "mean_iters": float(np.mean(its64)),
                 "mixed_over_fp64": (solves / (ms_total / 1e3)) / (nr / (ms64 / 1e3))}
+
+    # the other solver variant on the same inputs (plain CG <-> preconditioned)
+    alt = None
+    if not a.no_fp64:
+        step(xd, Rd, precond=not a.precond)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record()
+        itsa = []
+        for _ in range(2):
+            flush.zero_()
+            ita, resa = step(xd, Rd, precond=not a.precond)
+            itsa.append(ita)
+            assert np.all(resa < TOL)
+        f1.record()
+        torch.cuda.synchronize()
+        msa = f0.elapsed_time(f1) / 2
+        alt = {"precond": not a.precond, "solves_per_s": nr / (msa / 1e3), "ms_per_step": msa,
+               "mean_iters": float(np.mean(itsa))}
 
     # end to end through the public API: host (pinned) inputs -> device,
     # solve + force, solutions and force back to host, every step
@@ -345,6 +376,7 @@ def run_ours(a):
             "config": {"workload": "L=32 N=1024 Ltau=200 beta=20 dtau=0.1 t=1 mu=0 omega0=0.5 "
                                    "alpha=1 x~N(0,4), 16 rhs b=M^T R, mixed CG to 1e-8 "
                                    "(reliable update every 50) + force",
+                       "field": a.field,
                        "l2": "flushed between steps (256 MB write inside the timed loop)",
                        "per_rank": "independent replica, own seeds"},
             "matvecs_per_s": total_mv / (ms_max / 1e3),
@@ -352,12 +384,16 @@ def run_ours(a):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
                          "kernel": "k_cg_mtm32 (fused p=r+beta p, q=M^T M p, |Mp|^2)",
-                         "alg_bytes_per_launch": alg_bytes / max(op_cnt, 1),
+                         "alg_bytes_per_launch": alg_bytes,
                          "avg_launch_ms": op_avg_ms, "launches": op_cnt,
                          "peak_src": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
             "kernel_ms": {"cg_operator": op_ms, "cg_update": up_ms, "force": fo_ms,
-                          "timed_total": ms_total},
+                          "precond": pc_ms, "timed_total": ms_total,
+                          "recorded_launches": {"cg_operator": op_cnt, "cg_update": up_cnt,
+                                                "force": fo_cnt, "precond": pc_cnt}},
             "fp64_compare": fp64,
+            "solver": "preconditioned CG (adiabatic P, FP32)" if a.precond else "plain CG",
+            "other_solver": alt,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk,
@@ -406,6 +442,39 @@ def run_matvec(a):
     ctx.close()
 
 
+def run_precond(a):
+    """z = P^{-1} P^{-T} r (FP32 and FP64) on `rhs` right-hand sides, cold L2."""
+    import torch
+    import paper_2203_01291_gb300 as hg
+    from paper_2203_01291_gb300 import build as hb
+    hb.build()
+    torch.cuda.set_device(0)
+    w = WORKLOAD
+    nr = a.rhs
+    ctx = hg.Context.from_workload(w, max_rhs=nr)
+    ctx.set_field(torch.tensor(hi.phonon_field(w), device="cuda"))
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    res = {"mode": "precond", "rhs": nr}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        v = torch.tensor(hi.gaussian_vectors(w, nr, seed=5), device="cuda", dtype=dt)
+        z = torch.empty_like(v)
+        for _ in range(a.warmup):
+            ctx.precond_apply(hg.HOL_PINV_PINVT, v, z)
+        times = []
+        for _ in range(a.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.precond_apply(hg.HOL_PINV_PINVT, v, z)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        res[name + "_median_ms"] = statistics.median(times)
+    print(json.dumps(res))
+    ctx.close()
+
+
 # ----------------------------------------------------------------------------
 # reference arm: the oracle as it stands, timed on the host cores
 # ----------------------------------------------------------------------------
@@ -446,6 +515,8 @@ def main():
         run_reference(a)
     elif a.mode == "matvec":
         run_matvec(a)
+    elif a.mode == "precond":
+        run_precond(a)
     else:
         run_ours(a)
 

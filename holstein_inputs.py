@@ -100,6 +100,21 @@ def phonon_field(w: Workload, seed: int | None = None) -> np.ndarray:
     return np.ascontiguousarray(x, dtype=np.float64)
 
 
+def phonon_field_ar1(w: Workload, corr: float, seed: int | None = None) -> np.ndarray:
+    """x[tau][i]: for each site an AR(1) sequence along tau with lag-one
+    correlation exp(-dtau/corr) and stationary law N(x_shift, x_std^2) (a
+    generic tau-smooth input recipe; it is not periodic in tau)."""
+    g = _rng(w.seed if seed is None else seed)
+    rho = float(np.exp(-w.dtau / corr))
+    e = g.standard_normal((w.Ltau, w.N))
+    x = np.empty((w.Ltau, w.N))
+    x[0] = e[0]
+    s = np.sqrt(1.0 - rho * rho)
+    for t in range(1, w.Ltau):
+        x[t] = rho * x[t - 1] + s * e[t]
+    return np.ascontiguousarray(x * w.x_std + w.x_shift, dtype=np.float64)
+
+
 def gaussian_vectors(w: Workload, count: int, seed: int) -> np.ndarray:
     """R[k][tau][i] ~ N(0, 1), i.i.d. (pseudofermion / momentum draws)."""
     g = _rng(seed)

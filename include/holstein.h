@@ -47,6 +47,11 @@ extern "C" {
 #define HOL_F64 0
 #define HOL_F32 1
 
+/* preconditioner selector for precond_apply */
+#define HOL_PINV        0   /* out = P^{-1} v                                  */
+#define HOL_PINVT       1   /* out = P^{-T} v                                  */
+#define HOL_PINV_PINVT  2   /* out = P^{-1} P^{-T} v (the PCG preconditioner)  */
+
 typedef struct hol_params {
     int L;            /* linear lattice size (even, 4..32)                      */
     int Ltau;         /* number of imaginary-time slices T = beta / dtau (even) */
@@ -139,6 +144,25 @@ int cg_solve(hol_ctx* ctx, const double* b, double* v, int n_rhs,
  */
 int force(hol_ctx* ctx, const double* v, const double* b, int n_pf,
           double* dSdx, int with_bosonic, double* S_F, void* stream);
+
+/*
+ * Adiabatic preconditioner of Sec. VI A (Eq. (P_def)): P is M with every B_tau
+ * replaced by Bbar = diag(dbar) C (Eqs. (Bbar), (expnVbar)). It is applied as
+ * P^{-1} v = U^dag Ptilde^{-1} U v (Eq. (P_change_basis)), U the twisted DFT
+ * along tau of Eq. (U_omega), each block (I - e^{-i phi_omega} Bbar)^{-1}
+ * replaced by its Chebyshev series sum_{m<N_P} c_m T_m(A),
+ * A = 2 (Bbar - bmin)/(bmax - bmin) - 1 (App. C, Eqs. (A_def), (Minv_KPM),
+ * (alpha_recur)), N_P(omega) = max(1, floor((bmax-bmin)(1/phi_omega + 1)))
+ * (Eq. (NP_heuristic) with a1 = a2 = 1), c_m by Chebyshev-Gauss quadrature
+ * with 2 N_P points (Eq. (Cheby-Gauss)); bmin, bmax are the norm bounds set by
+ * hol_set_field. HOL_PINVT applies the exact transpose of that approximation,
+ * U^dag diag(sum conj(c_m) T_m(A^T)) U. which: HOL_PINV, HOL_PINVT or
+ * HOL_PINV_PINVT. prec: HOL_F64 (double) or HOL_F32 (float) for v and out,
+ * [n_rhs][T][N], real, must not overlap. Requires Ltau with prime factors in
+ * {2, 3, 5, 7} and Ltau <= 400.
+ */
+int precond_apply(hol_ctx* ctx, int which, int prec, const void* v, void* out,
+                  int n_rhs, void* stream);
 
 /*
  * Pseudofermion draw (Sec. II D, Eq. (PhiSample-1)): Phi = A^T R with

@@ -22,11 +22,13 @@ import numpy as np
 import torch
 
 from ._abi import (HOL_ECUDA, HOL_EINVAL, HOL_ENOMEM, HOL_ENOTCONV, HOL_ENUMERIC, HOL_ETIMEOUT,
-                   HOL_F32, HOL_F64, HOL_OK, HOL_OP_M, HOL_OP_MT, HOL_OP_MTM, hol_cg_opts,
+                   HOL_F32, HOL_F64, HOL_OK, HOL_OP_M, HOL_OP_MT, HOL_OP_MTM, HOL_PINV,
+                   HOL_PINV_PINVT, HOL_PINVT, hol_cg_opts,
                    hol_params, load, library_path)
 
 __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F64", "HOL_F32",
            "hol_create", "hol_destroy", "hol_set_field", "fermion_matvec", "cg_solve", "force",
+           "precond_apply", "HOL_PINV", "HOL_PINVT", "HOL_PINV_PINVT",
            "pseudofermion_phi", "phi_to_rhs", "hol_launch_count", "hol_timer_enable",
            "hol_timer_read",
            "library_path", "load"]
@@ -100,6 +102,13 @@ def force(handle, v: torch.Tensor, b: torch.Tensor, n_pf: int, dSdx: torch.Tenso
                         _ptr(b, torch.float64, n_pf * n, "b"), n_pf,
                         _ptr(dSdx, torch.float64, n, "dSdx"), int(bool(with_bosonic)), sf,
                         _stream()))
+
+
+def precond_apply(handle, which: int, prec: int, v: torch.Tensor, out: torch.Tensor, n_rhs: int,
+                  n: int) -> None:
+    dt = torch.float64 if prec == HOL_F64 else torch.float32
+    _check(load().precond_apply(handle, which, prec, _ptr(v, dt, n_rhs * n, "v"),
+                                _ptr(out, dt, n_rhs * n, "out"), n_rhs, _stream()))
 
 
 def pseudofermion_phi(handle, R: torch.Tensor, Phi: torch.Tensor, n_pf: int, n: int) -> None:
@@ -192,6 +201,10 @@ class Context:
     def force(self, v: torch.Tensor, b: torch.Tensor, dSdx: torch.Tensor,
               with_bosonic: bool = True, S_F: torch.Tensor | None = None) -> None:
         force(self._h, v, b, self._nrhs(v), dSdx, with_bosonic, S_F, self.n)
+
+    def precond_apply(self, which: int, v: torch.Tensor, out: torch.Tensor) -> None:
+        prec = HOL_F64 if v.dtype == torch.float64 else HOL_F32
+        precond_apply(self._h, which, prec, v, out, self._nrhs(v), self.n)
 
     def pseudofermion_phi(self, R: torch.Tensor, Phi: torch.Tensor) -> None:
         pseudofermion_phi(self._h, R, Phi, self._nrhs(R), self.n)

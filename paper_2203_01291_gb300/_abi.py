@@ -21,6 +21,10 @@ HOL_OP_MTM = 2
 HOL_F64 = 0
 HOL_F32 = 1
 
+HOL_PINV = 0
+HOL_PINVT = 1
+HOL_PINV_PINVT = 2
+
 
 class hol_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("Ltau", ctypes.c_int), ("dtau", ctypes.c_double),
@@ -48,6 +52,7 @@ SIGNATURES = {
     "cg_solve": (_I, [_VP, _VP, _VP, _I, ctypes.POINTER(hol_cg_opts),
                       ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
     "force": (_I, [_VP, _VP, _VP, _I, _VP, _I, _VP, _VP]),
+    "precond_apply": (_I, [_VP, _I, _I, _VP, _VP, _I, _VP]),
     "pseudofermion_phi": (_I, [_VP, _VP, _VP, _I, _VP]),
     "phi_to_rhs": (_I, [_VP, _VP, _VP, _I, _VP]),
     "hol_launch_count": (ctypes.c_ulonglong, []),

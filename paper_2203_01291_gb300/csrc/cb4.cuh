@@ -1,0 +1,145 @@
+// Vectorised register layout of one tau slice for L divisible by 8.
+//
+// A group of L lanes holds the slice: lane (cx, rc) of the group holds the
+// four columns 4cx..4cx+3 (one float4) of the L/4 rows rc*L/4 ..
+// rc*L/4 + L/4 - 1 (cx < L/4, rc < 4). Every global access is a float4 of a
+// row, so a slice costs L/4 vector loads per lane instead of L scalar ones.
+// Checkerboard colours (C = C4 C3 C2 C1):
+//   colour 1, x-bonds (even ix, ix+1): inside the float4;
+//   colour 2, x-bonds (odd ix, ix+1):  (.y,.z) inside, (.w, right.x) and
+//             (.x, left.w) by two shuffles per row;
+//   colour 3, y-bonds (even iy, iy+1): register pairs;
+//   colour 4, y-bonds (odd iy, iy+1):  register pairs, plus the chunk edges
+//             (last row with the next chunk's first row) by shuffles.
+#pragma once
+
+#include "cb.cuh"
+
+namespace hol {
+
+template <int L>
+struct Geom4 {
+    static_assert(L % 8 == 0, "vector layout needs L divisible by 8");
+    static constexpr int LR = L / 4;   // lanes per row segment
+    static constexpr int RT = L / 4;   // rows per lane
+    static constexpr int G = 32 / L;   // slices per warp
+    int g, cx, rc, left, right, down, up;
+    bool ok;
+    __device__ __forceinline__ Geom4()
+    {
+        const int lane = threadIdx.x & 31;
+        g = lane / L;
+        int ls = lane - g * L;
+        ok = g < G;
+        if (!ok) {
+            g = 0;
+            ls = lane - G * L;
+        }
+        cx = ls % LR;
+        rc = ls / LR;
+        const int b = g * L;
+        right = b + rc * LR + (cx + 1 == LR ? 0 : cx + 1);
+        left = b + rc * LR + (cx == 0 ? LR - 1 : cx - 1);
+        down = b + ((rc + 1) & 3) * LR + cx;
+        up = b + ((rc + 3) & 3) * LR + cx;
+    }
+    // float offset of row k of this lane inside a slice
+    __device__ __forceinline__ int off(int k) const { return (rc * RT + k) * L + 4 * cx; }
+};
+
+__device__ __forceinline__ void bond(float& a, float& b, float ch, float sh)
+{
+    const float x = a, y = b;
+    a = fmaf(ch, x, sh * y);
+    b = fmaf(sh, x, ch * y);
+}
+
+__device__ __forceinline__ float4 shfl4(const float4& v, int src)
+{
+    float4 r;
+    r.x = __shfl_sync(kFull, v.x, src);
+    r.y = __shfl_sync(kFull, v.y, src);
+    r.z = __shfl_sync(kFull, v.z, src);
+    r.w = __shfl_sync(kFull, v.w, src);
+    return r;
+}
+
+template <int L>
+__device__ __forceinline__ void c4_colour1(float4 (&c)[L / 4], float ch, float sh)
+{
+#pragma unroll
+    for (int k = 0; k < L / 4; ++k) {
+        bond(c[k].x, c[k].y, ch, sh);
+        bond(c[k].z, c[k].w, ch, sh);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void c4_colour2(float4 (&c)[L / 4], const Geom4<L>& g, float ch, float sh)
+{
+#pragma unroll
+    for (int k = 0; k < L / 4; ++k) {
+        const float rx = __shfl_sync(kFull, c[k].x, g.right);
+        const float lw = __shfl_sync(kFull, c[k].w, g.left);
+        bond(c[k].y, c[k].z, ch, sh);
+        c[k].w = fmaf(ch, c[k].w, sh * rx);
+        c[k].x = fmaf(ch, c[k].x, sh * lw);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void c4_colour3(float4 (&c)[L / 4], float ch, float sh)
+{
+#pragma unroll
+    for (int k = 0; k < L / 4; k += 2) {
+        bond(c[k].x, c[k + 1].x, ch, sh);
+        bond(c[k].y, c[k + 1].y, ch, sh);
+        bond(c[k].z, c[k + 1].z, ch, sh);
+        bond(c[k].w, c[k + 1].w, ch, sh);
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void c4_colour4(float4 (&c)[L / 4], const Geom4<L>& g, float ch, float sh)
+{
+    constexpr int RT = L / 4;
+    const float4 dn = shfl4(c[0], g.down);        // partner of my last row
+    const float4 upv = shfl4(c[RT - 1], g.up);    // partner of my first row
+#pragma unroll
+    for (int k = 1; k + 1 < RT; k += 2) {
+        bond(c[k].x, c[k + 1].x, ch, sh);
+        bond(c[k].y, c[k + 1].y, ch, sh);
+        bond(c[k].z, c[k + 1].z, ch, sh);
+        bond(c[k].w, c[k + 1].w, ch, sh);
+    }
+    c[RT - 1].x = fmaf(ch, c[RT - 1].x, sh * dn.x);
+    c[RT - 1].y = fmaf(ch, c[RT - 1].y, sh * dn.y);
+    c[RT - 1].z = fmaf(ch, c[RT - 1].z, sh * dn.z);
+    c[RT - 1].w = fmaf(ch, c[RT - 1].w, sh * dn.w);
+    c[0].x = fmaf(ch, c[0].x, sh * upv.x);
+    c[0].y = fmaf(ch, c[0].y, sh * upv.y);
+    c[0].z = fmaf(ch, c[0].z, sh * upv.z);
+    c[0].w = fmaf(ch, c[0].w, sh * upv.w);
+}
+
+// c <- C c (colour 1 first)
+template <int L>
+__device__ __forceinline__ void c4_apply(float4 (&c)[L / 4], const Geom4<L>& g, float ch, float sh)
+{
+    c4_colour1<L>(c, ch, sh);
+    c4_colour2<L>(c, g, ch, sh);
+    c4_colour3<L>(c, ch, sh);
+    c4_colour4<L>(c, g, ch, sh);
+}
+
+// c <- C^T c (colour 4 first)
+template <int L>
+__device__ __forceinline__ void c4_apply_t(float4 (&c)[L / 4], const Geom4<L>& g, float ch, float sh)
+{
+    c4_colour4<L>(c, g, ch, sh);
+    c4_colour3<L>(c, ch, sh);
+    c4_colour2<L>(c, g, ch, sh);
+    c4_colour1<L>(c, ch, sh);
+}
+
+}  // namespace hol

@@ -1,11 +1,15 @@
-// Conjugate gradients on M^T M v = b (Eq. (CG), Sec. VI B stopping rule).
+// Conjugate gradients on M^T M v = b (Eq. (CG)), optionally preconditioned
+// with z = P^{-1} P^{-T} r (Eq. (CG_precon)); stopping rule of Sec. VI B on
+// the true residual |b - M^T M v| / |b|.
 //
-// One CG iteration is two kernels:
-//   1. direction + operator: p_new = r + beta p_old, q = M^T M p_new and the
+// One iteration is
+//   1. direction + operator: p_new = z + beta p_old, q = M^T M p_new and the
 //      partial sums of p_new . q = |M p_new|^2 (matvec.cu);
-//   2. update: alpha = (r.r)/(p.q), x += alpha p, r -= alpha q and the partial
-//      sums of the new r.r.
-// beta and alpha are recomputed by every consumer from the partial sums in a
+//   2. update: alpha = (r.z)/(p.q), x += alpha p, r -= alpha q and the partial
+//      sums of the new r.r;
+//   3. (preconditioned only) z = P^{-1} P^{-T} r with the partial sums of r.z
+//      (precond.cu); without a preconditioner z is r itself.
+// alpha and beta are recomputed by every consumer from the partial sums in a
 // fixed order, so no extra launch or grid barrier sits on the critical path.
 // All dot products accumulate in FP64.
 //
@@ -13,7 +17,9 @@
 // of the FP64 solution v; every `reliable_every` iterations, and whenever the
 // recursive residual estimate says "converged", e is folded into v and the
 // true residual b - M^T M v is recomputed in FP64 (reliable update) and
-// replaces r. Every reported convergence is certified by that FP64 residual.
+// replaces r (the search direction is kept). Every reported convergence is
+// certified by that FP64 residual. The preconditioner of the mixed path runs
+// in FP32.
 #include <math.h>
 #include <string.h>
 
@@ -56,8 +62,7 @@ struct V4<double> {
     }
 };
 
-// Block sum of a double (any blockDim multiple of 32, <= 1024); result valid
-// in thread 0.
+// Block sum of a double (blockDim a multiple of 32, <= 1024); valid in thread 0.
 __device__ __forceinline__ double block_sum(double v)
 {
     __shared__ double red[32];
@@ -71,22 +76,22 @@ __device__ __forceinline__ double block_sum(double v)
     return s;
 }
 
-// x += alpha p, r -= alpha q, new (r.r) partials; alpha = rr / pq from partials.
+// x += alpha p, r -= alpha q, new (r.r) partials; alpha = dz / pq from partials.
 template <typename R>
 __global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restrict__ r,
                                                    const R* __restrict__ p, const R* __restrict__ q,
                                                    long n, const int* __restrict__ mask,
                                                    const double* __restrict__ pq_part, int pq_stride,
-                                                   int pq_n, const double* __restrict__ rr_part,
-                                                   int rr_n, double* __restrict__ rr_out)
+                                                   int pq_n, const double* __restrict__ dz_part,
+                                                   int dz_n, double* __restrict__ rr_out)
 {
     const int rhs = blockIdx.y;
     if (mask != nullptr && mask[rhs] == 0) return;
     __shared__ double s_alpha;
     if (threadIdx.x < 32) {
         const double pq = warp_sum_array(pq_part + (long)rhs * pq_stride, pq_n);
-        const double rr = warp_sum_array(rr_part + (long)rhs * kRedStride, rr_n);
-        if (threadIdx.x == 0) s_alpha = rr / pq;
+        const double dz = warp_sum_array(dz_part + (long)rhs * kRedStride, dz_n);
+        if (threadIdx.x == 0) s_alpha = dz / pq;
     }
     __syncthreads();
     const R a = (R)s_alpha;
@@ -158,8 +163,8 @@ __global__ void __launch_bounds__(256) k_fold(double* __restrict__ v, float* __r
 // Reliable update, part 3: r <- true residual rt (FP64; rounded to FP32 in
 // the mixed path); partials of |rt|^2 (true) and |r|^2 (recursion).
 template <typename R>
-__global__ void __launch_bounds__(256) k_recast(const double* rt, R* r,
-                                                long n, const int* __restrict__ mask,
+__global__ void __launch_bounds__(256) k_recast(const double* rt, R* r, long n,
+                                                const int* __restrict__ mask,
                                                 double* __restrict__ tr_out,
                                                 double* __restrict__ rr_out)
 {
@@ -192,22 +197,24 @@ __global__ void k_rows(const double* __restrict__ bank, int cnt, int n_rhs, doub
 }
 
 struct Banks {
-    double* pq;
-    double* rr[2];
-    double* tr;
-    double* bn;
-    double* red;   // [4][max_rhs] reduced per-rhs values
+    double* pq;      // matvec-unit partials of p.q
+    double* dz[2];   // alternating partials of r.z (r.r without preconditioner)
+    double* tr;      // true residual partials
+    double* bn;      // |b|^2 partials
+    double* red;     // [max_rhs] reduced per-rhs values
+    double* er;      // r.r partials of the preconditioned path
 };
 
 Banks banks_of(hol_ctx* c)
 {
     Banks b;
     b.pq = c->part;
-    b.rr[0] = c->part + 1 * c->part_len;
-    b.rr[1] = c->part + 2 * c->part_len;
+    b.dz[0] = c->part + 1 * c->part_len;
+    b.dz[1] = c->part + 2 * c->part_len;
     b.tr = c->part + 3 * c->part_len;
     b.bn = c->part + 4 * c->part_len;
     b.red = c->part + 5 * c->part_len;
+    b.er = c->part + 7 * c->part_len;
     return b;
 }
 
@@ -233,43 +240,61 @@ int elementwise_blocks(const hol_ctx* c)
     return (int)nb;
 }
 
-// The CG loop shared by the FP64 and mixed paths (no preconditioner).
-static int cg_plain(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_opts* o,
-                    int* iters, double* resid, cudaStream_t s)
+// The CG loop shared by the FP64 and mixed paths, with or without P.
+static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_opts* o,
+                  int* iters, double* resid, cudaStream_t s)
 {
     const bool mixed = (o->prec == HOL_F32);
+    const bool pc = o->precond != 0;
+    const int prec = mixed ? HOL_F32 : HOL_F64;
     const long n = c->n;
     const int nb2 = elementwise_blocks(c);
     const dim3 g2(nb2, n_rhs);
     const Banks B = banks_of(c);
     const int pstride = matvec_pstride(c);
     const int pq_n = c->T / c->mv_k;
+    const int dz_n = pc ? precond_tiles(c, prec) : nb2;   // partial count of r.z
     int* act_d = c->mask;
     int* rel_d = c->mask + c->p.max_rhs;
     int* act_h = c->hflag;
     int* rel_h = c->hflag + c->p.max_rhs;
     double* hb = c->hbuf;
+    int rc;
+    if (pc && (rc = precond_check_shape(c))) return rc;
 
     // FP64 path buffers / mixed path buffers
     double* r64 = c->v64a;
     double* p64[2] = {c->v64b, c->v64c};
     double* q64 = c->v64d;
     double* w64 = c->v64e;
+    double* z64 = pc ? c->v64f : r64;
     float* r32 = c->v32a;
     float* p32[2] = {c->v32b, c->v32c};
     float* q32 = c->v32d;
     float* e32 = c->v32e;
+    float* z32 = pc ? c->v32f : r32;
     double* t64 = c->v64a;   // mixed: M v during a reliable update
     double* rt64 = c->v64b;  // mixed: true residual
+    // bank receiving the r.r partials that drive the convergence estimate
+    auto est_bank = [&](int cur) { return pc ? B.er : B.dz[cur]; };
+
+    // z = P^{-1} P^{-T} r for every rhs, with the r.z partials in dz[bank]
+    auto apply_prec = [&](int bank) -> int {
+        timer_start(c, KT_PRECOND, s);
+        const int r2 = mixed ? precond_apply_impl(c, HOL_F32, r32, z32, n_rhs, 3, r32, B.dz[bank], s)
+                             : precond_apply_impl(c, HOL_F64, r64, z64, n_rhs, 3, r64, B.dz[bank], s);
+        timer_stop(c, KT_PRECOND, s);
+        return r2;
+    };
 
     HOL_CUDA(cudaMemsetAsync(v, 0, (size_t)n_rhs * n * sizeof(double), s));
     if (mixed)
-        k_cg_init<float><<<g2, 256, 0, s>>>(b, r32, e32, n, B.bn, B.rr[0]);
+        k_cg_init<float><<<g2, 256, 0, s>>>(b, r32, e32, n, B.bn, est_bank(0));
     else
-        k_cg_init<double><<<g2, 256, 0, s>>>(b, r64, nullptr, n, B.bn, B.rr[0]);
+        k_cg_init<double><<<g2, 256, 0, s>>>(b, r64, nullptr, n, B.bn, est_bank(0));
     HOL_CHECK_LAUNCH("k_cg_init");
-    int rc = rows_to_host(c, B.bn, nb2, n_rhs, hb, s);
-    if (rc) return rc;
+    if (pc && (rc = apply_prec(0))) return rc;
+    if ((rc = rows_to_host(c, B.bn, nb2, n_rhs, hb, s))) return rc;
     std::vector<double> bnorm(n_rhs), true_res(n_rhs, 1.0);
     std::vector<int> it(n_rhs, 0), since(n_rhs, 0), done(n_rhs, 0);
     int n_active = 0;
@@ -288,7 +313,7 @@ static int cg_plain(hol_ctx* c, const double* b, double* v, int n_rhs, const hol
     }
     HOL_CUDA(cudaMemcpyAsync(act_d, act_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
 
-    int cur = 0;     // bank holding the current r.r partials
+    int cur = 0;     // bank holding the current r.z partials
     int pp = 0;      // p buffer holding the current direction
     int first = 1;
     int k_it = 0;
@@ -298,41 +323,40 @@ static int cg_plain(hol_ctx* c, const double* b, double* v, int n_rhs, const hol
         int chunk = chk;
         if (chunk > o->max_iter - k_it) chunk = o->max_iter - k_it;
         for (int j = 0; j < chunk; ++j) {
+            double* rr_dst = pc ? B.er : B.dz[1 - cur];
             if (mixed) {
-                // on the first step beta = 0 and p_old is not yet defined: pass r
+                // on the first step beta = 0 and p_old is not yet defined: pass z
                 timer_start(c, KT_OPERATOR, s);
-                rc = launch_cg_mtm32(c, r32, first ? r32 : p32[pp], p32[1 - pp], q32, n_rhs,
-                                     act_d, B.rr[cur],
-                                     B.rr[1 - cur], kRedStride, nb2, first, B.pq, s);
+                rc = launch_cg_mtm32(c, z32, first ? z32 : p32[pp], p32[1 - pp], q32, n_rhs, act_d,
+                                     B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first, B.pq, s);
                 if (rc) return rc;
                 timer_stop(c, KT_OPERATOR, s);
                 pp = 1 - pp;
                 timer_start(c, KT_UPDATE, s);
                 k_cg_update<float><<<g2, 256, 0, s>>>(e32, r32, p32[pp], q32, n, act_d, B.pq,
-                                                      pstride, pq_n, B.rr[cur], nb2, B.rr[1 - cur]);
+                                                      pstride, pq_n, B.dz[cur], dz_n, rr_dst);
             } else {
-                BetaSrc bs{B.rr[cur], B.rr[1 - cur], kRedStride, nb2, first};
+                BetaSrc bs{B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first};
                 timer_start(c, KT_OPERATOR, s);
-                rc = launch_M_upd64(c, r64, first ? r64 : p64[pp], p64[1 - pp], w64, n_rhs, act_d,
+                rc = launch_M_upd64(c, z64, first ? z64 : p64[pp], p64[1 - pp], w64, n_rhs, act_d,
                                     bs, B.pq, s);
                 if (rc) return rc;
-                pp = 1 - pp;
                 rc = launch_MT(c, HOL_F64, w64, q64, n_rhs, act_d, s);
                 if (rc) return rc;
                 timer_stop(c, KT_OPERATOR, s);
+                pp = 1 - pp;
                 timer_start(c, KT_UPDATE, s);
                 k_cg_update<double><<<g2, 256, 0, s>>>(v, r64, p64[pp], q64, n, act_d, B.pq,
-                                                       pstride, pq_n, B.rr[cur], nb2,
-                                                       B.rr[1 - cur]);
+                                                       pstride, pq_n, B.dz[cur], dz_n, rr_dst);
             }
             HOL_CHECK_LAUNCH("k_cg_update");
             timer_stop(c, KT_UPDATE, s);
+            if (pc && (rc = apply_prec(1 - cur))) return rc;
             cur = 1 - cur;
             first = 0;
         }
         k_it += chunk;
-        rc = rows_to_host(c, B.rr[cur], nb2, n_rhs, hb, s);
-        if (rc) return rc;
+        if ((rc = rows_to_host(c, est_bank(cur), nb2, n_rhs, hb, s))) return rc;
         int n_rel = 0;
         for (int k = 0; k < n_rhs; ++k) {
             rel_h[k] = 0;
@@ -356,15 +380,17 @@ static int cg_plain(hol_ctx* c, const double* b, double* v, int n_rhs, const hol
             HOL_CHECK_LAUNCH("k_fold");
             if ((rc = launch_M(c, HOL_F64, v, t64, n_rhs, rel_d, nullptr, s))) return rc;
             if ((rc = launch_MT_resid64(c, t64, b, rt64, n_rhs, rel_d, s))) return rc;
-            k_recast<float><<<g2, 256, 0, s>>>(rt64, r32, n, rel_d, B.tr, B.rr[cur]);
+            k_recast<float><<<g2, 256, 0, s>>>(rt64, r32, n, rel_d, B.tr, est_bank(cur));
         } else {
             if ((rc = launch_M(c, HOL_F64, v, w64, n_rhs, rel_d, nullptr, s))) return rc;
             if ((rc = launch_MT_resid64(c, w64, b, r64, n_rhs, rel_d, s))) return rc;
-            k_recast<double><<<g2, 256, 0, s>>>(r64, r64, n, rel_d, B.tr, B.rr[cur]);
+            k_recast<double><<<g2, 256, 0, s>>>(r64, r64, n, rel_d, B.tr, est_bank(cur));
         }
         HOL_CHECK_LAUNCH("k_recast");
-        rc = rows_to_host(c, B.tr, nb2, n_rhs, hb, s);
-        if (rc) return rc;
+        // the new r changes r.z: recompute z (all rhs; the unchanged ones get
+        // the same z again)
+        if (pc && (rc = apply_prec(cur))) return rc;
+        if ((rc = rows_to_host(c, B.tr, nb2, n_rhs, hb, s))) return rc;
         int changed = 0;
         for (int k = 0; k < n_rhs; ++k) {
             if (!rel_h[k]) continue;
@@ -394,9 +420,6 @@ static int cg_plain(hol_ctx* c, const double* b, double* v, int n_rhs, const hol
     return HOL_OK;
 }
 
-int cg_precond(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_opts* o,
-               int* iters, double* resid, cudaStream_t s);   // precond.cu
-
 }  // namespace hol
 
 using namespace hol;
@@ -413,7 +436,5 @@ extern "C" int cg_solve(hol_ctx* c, const double* b, double* v, int n_rhs, const
     if (!(o->tol > 0.0) || o->max_iter < 1)
         return set_error(HOL_EINVAL, "cg_solve: tol must be > 0 and max_iter >= 1");
     if (b == v) return set_error(HOL_EINVAL, "cg_solve: b and v must not overlap");
-    cudaStream_t s = (cudaStream_t)stream;
-    if (o->precond) return cg_precond(c, b, v, n_rhs, o, iters, resid, s);
-    return cg_plain(c, b, v, n_rhs, o, iters, resid, s);
+    return cg_run(c, b, v, n_rhs, o, iters, resid, (cudaStream_t)stream);
 }

@@ -125,7 +125,8 @@ void free_ctx(hol_ctx* c)
     if (!c) return;
     void* dev[] = {c->x, c->ev64, c->ev32, c->dbar, c->scal, c->part, c->v64a, c->v64b,
                    c->v64c, c->v64d, c->v64e, c->v32a, c->v32b, c->v32c, c->v32d, c->v32e,
-                   c->mask, c->kpm.np, c->kpm.coef, c->cbuf0, c->cbuf1};
+                   c->mask, c->kpm.np, c->kpm.coef, c->cbuf0, c->cbuf1, c->v64f, c->v32f,
+                   c->tw64, c->tw32};
     for (void* p : dev)
         if (p) cudaFree(p);
     timer_free(c->timer);
@@ -169,6 +170,7 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     c->sh = sinh(p->dtau * p->t);
     c->mv_k = (c->T % 4 == 0 && c->T >= 8) ? 2 : 1;
     c->mv_warps = 4;
+    c->mv_vec = 1;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         free_ctx(c);
         return set_error(HOL_ECUDA, "hol_create: no CUDA device");
@@ -204,6 +206,8 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     ALLOC(c->v32c, R * n * sizeof(float));
     ALLOC(c->v32d, R * n * sizeof(float));
     ALLOC(c->v32e, R * n * sizeof(float));
+    ALLOC(c->v64f, R * n * sizeof(double));
+    ALLOC(c->v32f, R * n * sizeof(float));
     ALLOC(c->mask, 2 * R * sizeof(int));
     ALLOC(c->cbuf0, c->cbuf_len * sizeof(double2));
     ALLOC(c->cbuf1, c->cbuf_len * sizeof(double2));
@@ -212,6 +216,13 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
         cudaMallocHost((void**)&c->hflag, 4 * R * sizeof(int)) != cudaSuccess) {
         free_ctx(c);
         return set_error(HOL_ENOMEM, "hol_create: pinned host allocation failed");
+    }
+    {
+        const int rc = precond_alloc(c);
+        if (rc) {
+            free_ctx(c);
+            return rc;
+        }
     }
     if (cudaMemset(c->scal, 0, S_COUNT * sizeof(double)) != cudaSuccess) {
         free_ctx(c);

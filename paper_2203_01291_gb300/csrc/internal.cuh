@@ -102,6 +102,10 @@ struct hol_ctx {
     float* v32d;
     float* v32e;
     int* mask;           // [2*max_rhs] active / reliable-update flags (device)
+    double* v64f;
+    float* v32f;
+    double2* tw64;       // [2T] exp(-i pi k / T)
+    float2* tw32;
     double2* cbuf0;      // complex half-spectrum buffers [max_rhs][T/2][N]
     double2* cbuf1;
     long cbuf_len;
@@ -113,6 +117,7 @@ struct hol_ctx {
     // per-shape launch choices
     int mv_k;            // tau slices per lane group in the matvec kernels
     int mv_warps;        // warps per block in the matvec kernels
+    int mv_vec;          // use the float4 layout of the fused FP32 M^T M (L % 8 == 0)
 };
 
 namespace hol {
@@ -159,6 +164,15 @@ int launch_lambda(const hol_ctx* c, bool transpose_forward, const double* w, dou
 int launch_force(hol_ctx* c, const double* v, const double* b, int n_pf, double* F,
                  int with_bos, double* S_F, cudaStream_t s);
 int elementwise_blocks(const hol_ctx* c);
+
+// preconditioner (precond.cu). mode bit 0: P^{-T} part, bit 1: P^{-1} part
+// (both: P^{-1} P^{-T}). rdot/dot_part (nullable): partial sums of out . rdot
+// per (rhs, tile) at stride kRedStride, precond_tiles(c, prec) per rhs.
+int precond_alloc(hol_ctx* c);
+int precond_check_shape(const hol_ctx* c);
+int precond_tiles(const hol_ctx* c, int prec);
+int precond_apply_impl(hol_ctx* c, int prec, const void* v, void* out, int n_rhs, int mode,
+                       const void* rdot, double* dot_part, cudaStream_t s);
 
 // helpers ----------------------------------------------------------------------
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }

@@ -9,6 +9,7 @@
 // is a row of L consecutive sites (coalesced); the propagator itself never
 // leaves registers.
 #include "cb.cuh"
+#include "cb4.cuh"
 #include "internal.cuh"
 
 namespace hol {
@@ -257,6 +258,116 @@ __global__ void __launch_bounds__(128) k_cg_mtm32(const float* __restrict__ r,
     if (pq_part != nullptr) group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
 }
 
+
+// ---------------------------------------------------------------------------
+// Same fused FP32 CG step in the float4 layout of cb4.cuh (L % 8 == 0).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ld4(const float* __restrict__ p, long o)
+{
+    return *reinterpret_cast<const float4*>(p + o);
+}
+__device__ __forceinline__ void st4(float* __restrict__ p, long o, const float4& v)
+{
+    *reinterpret_cast<float4*>(p + o) = v;
+}
+__device__ __forceinline__ float4 fma4s(float a, const float4& x, const float4& y)
+{
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+template <int L>
+__global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict__ r,
+                                                     const float* __restrict__ pold,
+                                                     float* __restrict__ pnew,
+                                                     float* __restrict__ q,
+                                                     const float* __restrict__ ev, MvGeom gm,
+                                                     const int* __restrict__ mask,
+                                                     const double* __restrict__ rr_new_part,
+                                                     const double* __restrict__ rr_old_part,
+                                                     int rr_stride, int rr_n, int first,
+                                                     double* __restrict__ pq_part, float ch,
+                                                     float sh)
+{
+    constexpr int N = L * L;
+    constexpr int RT = L / 4;
+    const Geom4<L> geo;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int rhs = warp / gm.wpr;
+    if (rhs >= gm.n_rhs) return;
+    if (mask != nullptr && mask[rhs] == 0) return;
+    const int run = (warp - rhs * gm.wpr) * Geom4<L>::G + geo.g;
+    const bool valid = geo.ok && run < gm.nrun;
+    const int t0 = (run < gm.nrun ? run : gm.nrun - 1) * gm.K;
+    const long base = (long)rhs * gm.T * N;
+
+    float bt = 0.0f;
+    if (!first) {
+        const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
+        const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
+        bt = (float)(rn / ro);
+    }
+
+    float4 W[RT], X[RT], P[RT], Y[RT];
+    {
+        const int tm = (t0 == 0) ? gm.T - 1 : t0 - 1;
+        const long o = base + (long)tm * N;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) Y[k] = fma4s(bt, ld4(pold, o + geo.off(k)), ld4(r, o + geo.off(k)));
+        c4_apply<L>(Y, geo, ch, sh);
+    }
+    {
+        const long o = base + (long)t0 * N;
+        const float sg = (t0 == 0) ? 1.0f : -1.0f;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float4 pv = fma4s(bt, ld4(pold, o + geo.off(k)), ld4(r, o + geo.off(k)));
+            if (valid && pnew != nullptr) st4(pnew, o + geo.off(k), pv);
+            X[k] = pv;
+            float4 d = ld4(ev, (long)t0 * N + geo.off(k));
+            W[k] = make_float4(fmaf(sg * d.x, Y[k].x, pv.x), fmaf(sg * d.y, Y[k].y, pv.y),
+                               fmaf(sg * d.z, Y[k].z, pv.z), fmaf(sg * d.w, Y[k].w, pv.w));
+        }
+        c4_apply<L>(X, geo, ch, sh);
+    }
+    double acc = 0.0;
+    for (int s = 0; s < gm.K; ++s) {
+        const int tau = t0 + s;
+        const int tp = (tau + 1 == gm.T) ? 0 : tau + 1;
+        const long op = base + (long)tp * N;
+        const float sgp = (tp == 0) ? 1.0f : -1.0f;
+        const bool own = valid && (s + 1 < gm.K) && pnew != nullptr;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float4 pv = fma4s(bt, ld4(pold, op + geo.off(k)), ld4(r, op + geo.off(k)));
+            if (own) st4(pnew, op + geo.off(k), pv);
+            P[k] = pv;
+            float4 d = ld4(ev, (long)tp * N + geo.off(k));
+            d.x *= sgp; d.y *= sgp; d.z *= sgp; d.w *= sgp;
+            X[k] = make_float4(fmaf(d.x, X[k].x, pv.x), fmaf(d.y, X[k].y, pv.y),
+                               fmaf(d.z, X[k].z, pv.z), fmaf(d.w, X[k].w, pv.w));
+            Y[k] = make_float4(d.x * X[k].x, d.y * X[k].y, d.z * X[k].z, d.w * X[k].w);
+        }
+        c4_apply<L>(P, geo, ch, sh);
+        c4_apply_t<L>(Y, geo, ch, sh);
+        const long o = base + (long)tau * N;
+        float part = 0.0f;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            if (valid)
+                st4(q, o + geo.off(k), make_float4(W[k].x + Y[k].x, W[k].y + Y[k].y,
+                                                   W[k].z + Y[k].z, W[k].w + Y[k].w));
+            part = fmaf(W[k].x, W[k].x, part);
+            part = fmaf(W[k].y, W[k].y, part);
+            part = fmaf(W[k].z, W[k].z, part);
+            part = fmaf(W[k].w, W[k].w, part);
+            W[k] = X[k];
+            X[k] = P[k];
+        }
+        acc += (double)part;
+    }
+    if (pq_part != nullptr) group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
+}
+
 template <int L>
 int blocks_for(const hol_ctx* c, const MvGeom& g)
 {
@@ -334,6 +445,15 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
 {
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
+    if constexpr (L % 8 == 0) {
+        if (c->mv_vec) {
+            k_cg_mtm32_v4<L><<<nb, nt, 0, s>>>(r, pold, pnew, q, c->ev32, g, mask, rr_new, rr_old,
+                                                rr_stride, rr_n, first, pq_part, (float)c->ch,
+                                                (float)c->sh);
+            HOL_CHECK_LAUNCH("k_cg_mtm32_v4");
+            return HOL_OK;
+        }
+    }
     k_cg_mtm32<L><<<nb, nt, 0, s>>>(r, pold, pnew, q, c->ev32, g, mask, rr_new, rr_old, rr_stride,
                                      rr_n, first, pq_part, (float)c->ch, (float)c->sh);
     HOL_CHECK_LAUNCH("k_cg_mtm32");
