@@ -182,6 +182,33 @@ int pseudofermion_phi(hol_ctx* ctx, const double* R, double* Phi, int n_pf, void
 int phi_to_rhs(hol_ctx* ctx, const double* Phi, double* b, int n_pf, void* stream);
 
 /*
+ * Allocation-free FP64 fermion operator (no counterpart in the paper).
+ *
+ * For callers that cannot call cudaMalloc: code whose device memory is owned
+ * entirely by another allocator (a framework's caching allocator, or a budget
+ * fixed at start-up), and code that must not trigger the device-wide
+ * synchronisation that cudaMalloc / cudaFree can imply. It needs no context:
+ * out = M v, M^T v or M^T M v (op = HOL_OP_M, HOL_OP_MT, HOL_OP_MTM; same
+ * operator and same kernels as fermion_matvec with HOL_F64) for the field x
+ * and the couplings in p (p->max_rhs is ignored). x: FP64 [T][N]; v, out: FP64
+ * [n_rhs][T][N], device, must not overlap.
+ *
+ * Scratch: one file-scope device array of 2^20 doubles (8 MiB) that every GPU
+ * loading this library holds until the process exits. A call needs N*T
+ * doubles of it (the exp(-dtau V) table) plus n_rhs*N*T more for HOL_OP_MTM
+ * (the intermediate M v); larger requests return HOL_EINVAL. Nothing in it
+ * has to start at zero: every call writes what it reads. The first call on a
+ * device (with that device current) looks up the array's device address and
+ * caches it; make that first call before any stream capture. Every call
+ * shares the one array, so calls whose work overlaps on the GPU (different
+ * streams, or different host threads on one device) race: serialise them.
+ * The call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).
+ */
+int fermion_matvec_static(const hol_params* p, const double* x, int op, const double* v,
+                          double* out, int n_rhs, void* stream);
+
+/*
  * Instrumentation (no counterpart in the paper; used by the benchmark).
  * hol_launch_count: number of kernels this library has launched in the
  * process so far. hol_timer_enable(ctx, 1) starts recording CUDA events

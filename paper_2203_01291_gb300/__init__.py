@@ -30,7 +30,7 @@ __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F6
            "hol_create", "hol_destroy", "hol_set_field", "fermion_matvec", "cg_solve", "force",
            "precond_apply", "HOL_PINV", "HOL_PINVT", "HOL_PINV_PINVT",
            "pseudofermion_phi", "phi_to_rhs", "hol_launch_count", "hol_timer_enable",
-           "hol_timer_read",
+           "hol_timer_read", "fermion_matvec_static",
            "library_path", "load"]
 
 
@@ -119,6 +119,17 @@ def pseudofermion_phi(handle, R: torch.Tensor, Phi: torch.Tensor, n_pf: int, n: 
 def phi_to_rhs(handle, Phi: torch.Tensor, b: torch.Tensor, n_pf: int, n: int) -> None:
     _check(load().phi_to_rhs(handle, _ptr(Phi, torch.float64, n_pf * n, "Phi"),
                              _ptr(b, torch.float64, n_pf * n, "b"), n_pf, _stream()))
+
+
+def fermion_matvec_static(params: hol_params, x: torch.Tensor, op: int, v: torch.Tensor,
+                          out: torch.Tensor, n_rhs: int) -> None:
+    """Context-free FP64 operator whose scratch is a fixed device array (no
+    allocation); see include/holstein.h."""
+    n = params.L * params.L * params.Ltau
+    _check(load().fermion_matvec_static(ctypes.byref(params), _ptr(x, torch.float64, n, "x"), op,
+                                        _ptr(v, torch.float64, n_rhs * n, "v"),
+                                        _ptr(out, torch.float64, n_rhs * n, "out"), n_rhs,
+                                        _stream()))
 
 
 def hol_launch_count() -> int:
