@@ -182,6 +182,57 @@ int pseudofermion_phi(hol_ctx* ctx, const double* R, double* Phi, int n_pf, void
 int phi_to_rhs(hol_ctx* ctx, const double* Phi, double* b, int n_pf, void* stream);
 
 /*
+ * Fourier-accelerated molecular dynamics (Sec. III B, Algorithm 1).
+ * The dynamical mass is Mass = F^{-1} Mass~ F along tau (Eq. (dynamical_M_def))
+ * with Mass~_omega = dtau (m_reg^2 + omega0^2 + (4/dtau^2) sin^2(pi omega/T))
+ * / (m_reg^2 + omega0^2); m_reg = INFINITY gives the constant mass dtau.
+ */
+typedef struct hol_md_opts {
+    double dt;               /* fermionic time step Delta t                          */
+    int n_steps;             /* N_t fermionic steps per trajectory                   */
+    int n_sub;               /* n_t bosonic sub-steps of Delta t / n_t per step      */
+    double m_reg;            /* Fourier-acceleration regulator (>= 0 or INFINITY)   */
+    hol_cg_opts cg_force;    /* solves for the forces inside the trajectory          */
+    hol_cg_opts cg_action;   /* solve for S_F at the end of a trajectory             */
+} hol_md_opts;
+
+/*
+ * out = Mass^{-1} p (which = 0), Mass^{1/2} p (1) or Mass p (2) for one
+ * [T][N] FP64 field (device); p and out must not overlap. Each site's tau
+ * line is transformed with a mixed-radix FFT (Ltau with prime factors in
+ * {2, 3, 5, 7}).
+ */
+int mass_apply(hol_ctx* ctx, int which, double m_reg, const double* p, double* out,
+               void* stream);
+
+/*
+ * Integrate n_steps steps of the split leapfrog of Algorithm 1 from (x, p)
+ * in place (x, p: FP64 [T][N], device), at fixed pseudofermions Phi (FP64
+ * [n_pf][T][N]). Each step: p -= dt/2 dS_F/dx; n_sub times { p -= dt'/2
+ * dS_B/dx; x += dt' Mass^{-1} p; p -= dt'/2 dS_B/dx }; p -= dt/2 dS_F/dx,
+ * dt' = dt/n_sub, dS_F/dx from cg_solve with opts->cg_force and the force of
+ * `force`; the closing and opening half kicks of consecutive steps are one
+ * force evaluation. Leaves the field of the last force set in the context.
+ */
+int md_integrate(hol_ctx* ctx, double* x, double* p, const double* Phi, int n_pf,
+                 const hol_md_opts* opts, void* stream);
+
+/*
+ * One HMC update (Algorithm 1): Phi = A^T(x) R_pf (R_pf: [n_pf][T][N]
+ * standard-normal draws), p = Mass^{1/2} R_p (R_p: [T][N] draws), H_i =
+ * S_B + |R_pf|^2/2 + p.Mass^{-1}p/2, md_integrate, H_f = S_B + S_F + kinetic
+ * energy with S_F from cg_solve(opts->cg_action), and the Metropolis test
+ * u < exp(-(H_f - H_i)) with the caller's uniform draw u (Eq. (metropolis)).
+ * x (device, in/out) holds the accepted field on return. accepted, dH (host,
+ * nullable) receive the decision and H_f - H_i; terms (host, nullable, 6
+ * doubles) receive S_B, S_F, kinetic energy at the start and at the end.
+ * Synchronises `stream`.
+ */
+int fourier_accel_leapfrog(hol_ctx* ctx, double* x, const double* R_pf, const double* R_p,
+                           int n_pf, const hol_md_opts* opts, double u, int* accepted,
+                           double* dH, double* terms, void* stream);
+
+/*
  * Allocation-free FP64 fermion operator (no counterpart in the paper).
  *
  * For callers that cannot call cudaMalloc: code whose device memory is owned

@@ -23,14 +23,15 @@ import torch
 
 from ._abi import (HOL_ECUDA, HOL_EINVAL, HOL_ENOMEM, HOL_ENOTCONV, HOL_ENUMERIC, HOL_ETIMEOUT,
                    HOL_F32, HOL_F64, HOL_OK, HOL_OP_M, HOL_OP_MT, HOL_OP_MTM, HOL_PINV,
-                   HOL_PINV_PINVT, HOL_PINVT, hol_cg_opts,
+                   HOL_PINV_PINVT, HOL_PINVT, hol_cg_opts, hol_md_opts,
                    hol_params, load, library_path)
 
 __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F64", "HOL_F32",
            "hol_create", "hol_destroy", "hol_set_field", "fermion_matvec", "cg_solve", "force",
            "precond_apply", "HOL_PINV", "HOL_PINVT", "HOL_PINV_PINVT",
            "pseudofermion_phi", "phi_to_rhs", "hol_launch_count", "hol_timer_enable",
-           "hol_timer_read", "fermion_matvec_static",
+           "hol_timer_read", "fermion_matvec_static", "mass_apply", "md_integrate",
+           "fourier_accel_leapfrog", "hol_md_opts",
            "library_path", "load"]
 
 
@@ -132,6 +133,42 @@ def fermion_matvec_static(params: hol_params, x: torch.Tensor, op: int, v: torch
                                         _stream()))
 
 
+def mass_apply(handle, which: int, m_reg: float, p: torch.Tensor, out: torch.Tensor,
+               n: int) -> None:
+    _check(load().mass_apply(handle, which, float(m_reg), _ptr(p, torch.float64, n, "p"),
+                             _ptr(out, torch.float64, n, "out"), _stream()))
+
+
+def md_integrate(handle, x: torch.Tensor, p: torch.Tensor, Phi: torch.Tensor, n_pf: int,
+                 opts: hol_md_opts, n: int) -> None:
+    _check(load().md_integrate(handle, _ptr(x, torch.float64, n, "x"),
+                               _ptr(p, torch.float64, n, "p"),
+                               _ptr(Phi, torch.float64, n_pf * n, "Phi"), n_pf,
+                               ctypes.byref(opts), _stream()))
+
+
+def fourier_accel_leapfrog(handle, x: torch.Tensor, R_pf: torch.Tensor, R_p: torch.Tensor,
+                           n_pf: int, opts: hol_md_opts, u: float, n: int):
+    acc = ctypes.c_int()
+    dH = ctypes.c_double()
+    terms = (ctypes.c_double * 6)()
+    _check(load().fourier_accel_leapfrog(handle, _ptr(x, torch.float64, n, "x"),
+                                         _ptr(R_pf, torch.float64, n_pf * n, "R_pf"),
+                                         _ptr(R_p, torch.float64, n, "R_p"), n_pf,
+                                         ctypes.byref(opts), float(u), ctypes.byref(acc),
+                                         ctypes.byref(dH), terms, _stream()))
+    return bool(acc.value), dH.value, np.array(terms[:])
+
+
+def md_opts(dt: float, n_steps: int, n_sub: int, m_reg: float, force_tol: float = 1e-5,
+            action_tol: float = 1e-10, prec: int = HOL_F32, precond: bool = False,
+            reliable_every: int = 50, check_every: int = 10) -> hol_md_opts:
+    """hol_md_opts with the paper's solver tolerances (Sec. VI B) as defaults."""
+    f = hol_cg_opts(force_tol, 100000, int(precond), prec, reliable_every, check_every)
+    a = hol_cg_opts(action_tol, 100000, int(precond), prec, reliable_every, check_every)
+    return hol_md_opts(dt, n_steps, n_sub, float(m_reg), f, a)
+
+
 def hol_launch_count() -> int:
     return int(load().hol_launch_count())
 
@@ -222,6 +259,18 @@ class Context:
 
     def phi_to_rhs(self, Phi: torch.Tensor, b: torch.Tensor) -> None:
         phi_to_rhs(self._h, Phi, b, self._nrhs(Phi), self.n)
+
+    def mass_apply(self, which: int, m_reg: float, p: torch.Tensor, out: torch.Tensor) -> None:
+        mass_apply(self._h, which, m_reg, p, out, self.n)
+
+    def md_integrate(self, x: torch.Tensor, p: torch.Tensor, Phi: torch.Tensor,
+                     opts: hol_md_opts) -> None:
+        md_integrate(self._h, x, p, Phi, self._nrhs(Phi), opts, self.n)
+
+    def fourier_accel_leapfrog(self, x: torch.Tensor, R_pf: torch.Tensor, R_p: torch.Tensor,
+                               opts: hol_md_opts, u: float):
+        """Algorithm 1; returns (accepted, dH, [S_B, S_F, K] at start and end)."""
+        return fourier_accel_leapfrog(self._h, x, R_pf, R_p, self._nrhs(R_pf), opts, u, self.n)
 
     def timer_enable(self, on: bool = True) -> None:
         hol_timer_enable(self._h, on)

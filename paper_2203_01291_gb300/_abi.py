@@ -38,6 +38,12 @@ class hol_cg_opts(ctypes.Structure):
                 ("check_every", ctypes.c_int)]
 
 
+class hol_md_opts(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("n_steps", ctypes.c_int), ("n_sub", ctypes.c_int),
+                ("m_reg", ctypes.c_double), ("cg_force", hol_cg_opts),
+                ("cg_action", hol_cg_opts)]
+
+
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -53,6 +59,11 @@ SIGNATURES = {
                       ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
     "force": (_I, [_VP, _VP, _VP, _I, _VP, _I, _VP, _VP]),
     "precond_apply": (_I, [_VP, _I, _I, _VP, _VP, _I, _VP]),
+    "mass_apply": (_I, [_VP, _I, _D, _VP, _VP, _VP]),
+    "md_integrate": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.POINTER(hol_md_opts), _VP]),
+    "fourier_accel_leapfrog": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.POINTER(hol_md_opts), _D,
+                                    ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                    _VP]),
     "pseudofermion_phi": (_I, [_VP, _VP, _VP, _I, _VP]),
     "phi_to_rhs": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fermion_matvec_static": (_I, [ctypes.POINTER(hol_params), _VP, _I, _VP, _VP, _I, _VP]),

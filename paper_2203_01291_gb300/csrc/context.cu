@@ -126,7 +126,8 @@ void free_ctx(hol_ctx* c)
     void* dev[] = {c->x, c->ev64, c->ev32, c->dbar, c->scal, c->part, c->v64a, c->v64b,
                    c->v64c, c->v64d, c->v64e, c->v32a, c->v32b, c->v32c, c->v32d, c->v32e,
                    c->mask, c->kpm.np, c->kpm.coef, c->cbuf0, c->cbuf1, c->v64f, c->v32f,
-                   c->tw64, c->tw32};
+                   c->tw64, c->tw32, c->md_phi, c->md_b, c->md_v, c->md_F, c->md_p,
+                   c->md_x0, c->md_g, c->md_s};
     for (void* p : dev)
         if (p) cudaFree(p);
     timer_free(c->timer);
@@ -218,7 +219,8 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
         return set_error(HOL_ENOMEM, "hol_create: pinned host allocation failed");
     }
     {
-        const int rc = precond_alloc(c);
+        int rc = precond_alloc(c);
+        if (!rc) rc = leapfrog_alloc(c);
         if (rc) {
             free_ctx(c);
             return rc;

@@ -106,6 +106,14 @@ struct hol_ctx {
     float* v32f;
     double2* tw64;       // [2T] exp(-i pi k / T)
     float2* tw32;
+    double* md_phi;      // leapfrog: Phi [max_rhs][T][N]
+    double* md_b;        // leapfrog: b = Lambda^{-T} Phi
+    double* md_v;        // leapfrog: v = (M^T M)^{-1} b
+    double* md_F;        // leapfrog: force / filter scratch [T][N]
+    double* md_p;        // leapfrog: momentum [T][N]
+    double* md_x0;       // leapfrog: x at the start of a trajectory
+    double* md_g;        // leapfrog: mass tables [3][T]
+    double* md_s;        // leapfrog: energy terms [16]
     double2* cbuf0;      // complex half-spectrum buffers [max_rhs][T/2][N]
     double2* cbuf1;
     long cbuf_len;
@@ -169,6 +177,7 @@ int elementwise_blocks(const hol_ctx* c);
 // (both: P^{-1} P^{-T}). rdot/dot_part (nullable): partial sums of out . rdot
 // per (rhs, tile) at stride kRedStride, precond_tiles(c, prec) per rhs.
 int precond_alloc(hol_ctx* c);
+int leapfrog_alloc(hol_ctx* c);
 int precond_check_shape(const hol_ctx* c);
 int precond_tiles(const hol_ctx* c, int prec);
 int precond_apply_impl(hol_ctx* c, int prec, const void* v, void* out, int n_rhs, int mode,
