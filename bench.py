@@ -62,6 +62,8 @@ def args_parse():
     ap.add_argument("--rhs", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the trajectory and measurement legs")
     ap.add_argument("--field", choices=["iid", "ar1"], default="iid",
                     help="phonon field: i.i.d. Gaussian (default) or tau-correlated AR(1)")
     ap.add_argument("--precond", action="store_true",
@@ -362,6 +364,10 @@ def run_ours(a):
            "h2d_bytes_per_step": int(xh.numel() * 8 + Rh.numel() * 8),
            "d2h_bytes_per_step": int(vh.numel() * 8 + Fh.numel() * 8)}
 
+    extra = None
+    if not a.no_extra:
+        extra = {"trajectory": trajectory_leg(dev), "measurement": measurement_leg(dev)}
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_baseline_block()
@@ -395,6 +401,7 @@ def run_ours(a):
             "solver": "preconditioned CG (adiabatic P, FP32)" if a.precond else "plain CG",
             "other_solver": alt,
             "e2e": e2e,
+            "other_rows": extra,
             "gpu_launches": int(launches),
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -404,6 +411,68 @@ def run_ours(a):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def trajectory_leg(dev, n_traj=2):
+    """Algorithm 1 on the hmc16 workload: L=16, Ltau=160, alpha=1.5, omega0=1,
+    x ~ N(0.5, 1), two pseudofermions, N_t=20, n_t=4, dt=0.01, m_reg=omega0,
+    adiabatic preconditioner, mixed precision, force solves to 1e-5 and the
+    action solve to 1e-10 (Sec. VI B)."""
+    import torch
+    import paper_2203_01291_gb300 as hg
+    w = hi.WORKLOADS["hmc16"]
+    o = hg.md_opts(0.01, 20, 4, w.omega0, force_tol=1e-5, action_tol=1e-10,
+                   prec=hg.HOL_F32, precond=True)
+    with hg.Context.from_workload(w, max_rhs=2) as ctx:
+        x = torch.tensor(hi.phonon_field(w), device=dev)
+        u = hi.uniforms(n_traj + 1, seed=77)
+        acc, dhs = [], []
+        for k in range(n_traj + 1):
+            R = torch.tensor(hi.gaussian_vectors(w, 2, seed=300 + k), device=dev)
+            Rp = torch.tensor(hi.gaussian_vectors(w, 1, seed=400 + k)[0], device=dev)
+            if k == 1:
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+            a_, dh, _ = ctx.fourier_accel_leapfrog(x, R, Rp, o, float(u[k]))
+            if k >= 1:
+                acc.append(a_)
+                dhs.append(dh)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n_traj
+    return {"workload": "hmc16 L=16 Ltau=160, N_t=20 n_t=4 dt=0.01, PCG mixed",
+            "trajectories_per_s": 1e3 / ms, "ms_per_trajectory": ms,
+            "accepted": int(sum(acc)), "of": n_traj, "mean_abs_dH": float(np.mean(np.abs(dhs)))}
+
+
+def measurement_leg(dev, n_rv=128):
+    """Stochastic Green's function (2-point and the type-2 Wick product) of one
+    L=28, Ltau=120 chain (beta=12, omega0=1, alpha=1, x ~ N(0, 1)) with 128
+    Z2 probes solved in mixed precision to 1e-8."""
+    import torch
+    import paper_2203_01291_gb300 as hg
+    w = hi.Workload("chain28", L=28, Ltau=120, omega0=1.0, alpha=1.0, seed=1047)
+    with hg.Context.from_workload(w, max_rhs=16) as ctx:
+        ctx.set_field(torch.tensor(hi.phonon_field(w), device=dev))
+        xi = torch.tensor(hi.z2_vectors(w, n_rv, seed=5), device=dev)
+        Gxi = torch.empty_like(xi)
+        G2 = torch.empty(2 * w.Ltau, w.L, w.L, dtype=torch.float64, device=dev)
+        G4 = torch.empty(3, 2 * w.Ltau, w.L, w.L, dtype=torch.float64, device=dev)
+        ctx.stochastic_measure(xi[:16].contiguous(), Gxi[:16], G2, G4, 2, tol=1e-8,
+                               prec=hg.HOL_F32)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        its = ctx.stochastic_measure(xi, Gxi, G2, G4, 2, tol=1e-8, prec=hg.HOL_F32)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    return {"workload": "L=28 Ltau=120 chain, 128 Z2 probes, 2-point + type-2 Wick",
+            "measurements_per_s": 1e3 / ms, "ms_per_measurement": ms,
+            "mean_cg_iters": float(np.mean(its))}
 
 
 def run_matvec(a):

@@ -233,6 +233,30 @@ int fourier_accel_leapfrog(hol_ctx* ctx, double* x, const double* R_pf, const do
                            double* dH, double* terms, void* stream);
 
 /*
+ * Stochastic Green's-function measurement with FFT averaging (Sec. V).
+ * xi: n_rv probe vectors [n_rv][T][N] (FP64, device; e.g. Z2 draws, so that
+ * <xi_i xi_j> = delta_ij, Eq. (Hutch_approx)). Gxi (device, caller-owned,
+ * [n_rv][T][N]) receives G xi = M^{-1} xi, solved as M^T M v = M^T xi with
+ * cg_solve(opts) in batches of max_rhs. G2 (device, [2T][L][L], indexed
+ * [dl][dy][dx]) receives the space-time averaged Green function of
+ * Eqs. (G_avg-1), (G_def-1), (cross_corr), averaged over the probes
+ * (Eq. (G_approx_better)) and normalised as the mean over the original
+ * N*T sites (circular sum over the doubled domain / (2 N T)); G2[dl+T] =
+ * -G2[dl]. four_point (bit mask, 0 = none) selects the pair-averaged Wick
+ * products of Sec. V C (Eq. (GG_approx_better)), written to G4 (device,
+ * [3][2T][L][L], same normalisation, averaged over the n_rv (n_rv-1)/2 pairs
+ * n < m): bit 0 (xi_n . xi_m) star (Gxi_n . Gxi_m), bit 1 (xi_n . Gxi_n) star
+ * (xi_m . Gxi_m) (prefix sums, cost linear in n_rv), bit 2 (xi_n . Gxi_m) star
+ * (xi_m . Gxi_n) (bits 0 and 2 cost one pair of transforms per pair); needs
+ * n_rv >= 2 and max_rhs >= 2. iters (host, nullable, n_rv) receives CG
+ * iterations. L and Ltau need prime factors in {2, 3, 5, 7}. Uses the context
+ * scratch; synchronises `stream` (through cg_solve).
+ */
+int stochastic_measure(hol_ctx* ctx, const double* xi, int n_rv, const hol_cg_opts* opts,
+                       double* Gxi, double* G2, double* G4, int four_point, int* iters,
+                       void* stream);
+
+/*
  * Allocation-free FP64 fermion operator (no counterpart in the paper).
  *
  * For callers that cannot call cudaMalloc: code whose device memory is owned
@@ -258,6 +282,20 @@ int fourier_accel_leapfrog(hol_ctx* ctx, double* x, const double* R_pf, const do
  */
 int fermion_matvec_static(const hol_params* p, const double* x, int op, const double* v,
                           double* out, int n_rhs, void* stream);
+
+/*
+ * Launch-shape autotuner (no counterpart in the paper). Times the fused FP32
+ * M^T M kernel of the CG iteration for n_rhs right-hand sides over its launch
+ * candidates (tau slices per lane group, warps per block, vector or scalar
+ * register layout) with CUDA events on `stream`, and keeps the fastest in the
+ * context for all later calls (results are unchanged up to rounding; every
+ * candidate computes the same operator). Host outputs (nullable): the chosen
+ * slices per group, warps per block, layout (2 = float4 with
+ * asynchronous prefetch, 1 = float4, 0 = scalar), and its time in ms.
+ * Requires hol_set_field; overwrites context scratch; synchronises `stream`.
+ */
+int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_vec,
+             double* best_ms, void* stream);
 
 /*
  * Instrumentation (no counterpart in the paper; used by the benchmark).

@@ -31,7 +31,7 @@ __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F6
            "precond_apply", "HOL_PINV", "HOL_PINVT", "HOL_PINV_PINVT",
            "pseudofermion_phi", "phi_to_rhs", "hol_launch_count", "hol_timer_enable",
            "hol_timer_read", "fermion_matvec_static", "mass_apply", "md_integrate",
-           "fourier_accel_leapfrog", "hol_md_opts",
+           "fourier_accel_leapfrog", "hol_md_opts", "stochastic_measure", "hol_tune",
            "library_path", "load"]
 
 
@@ -169,6 +169,26 @@ def md_opts(dt: float, n_steps: int, n_sub: int, m_reg: float, force_tol: float 
     return hol_md_opts(dt, n_steps, n_sub, float(m_reg), f, a)
 
 
+def stochastic_measure(handle, xi: torch.Tensor, n_rv: int, opts: hol_cg_opts, Gxi: torch.Tensor,
+                       G2: torch.Tensor, G4: torch.Tensor | None, four_point: int, n: int):
+    it = (ctypes.c_int * n_rv)()
+    g4 = _ptr(G4, torch.float64, 6 * n, "G4") if G4 is not None else None
+    _check(load().stochastic_measure(handle, _ptr(xi, torch.float64, n_rv * n, "xi"), n_rv,
+                                     ctypes.byref(opts), _ptr(Gxi, torch.float64, n_rv * n, "Gxi"),
+                                     _ptr(G2, torch.float64, 2 * n, "G2"), g4, int(four_point), it,
+                                     _stream()))
+    return np.array(it[:], dtype=np.int64)
+
+
+def hol_tune(handle, n_rhs: int) -> dict:
+    k, w, v = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(load().hol_tune(handle, n_rhs, ctypes.byref(k), ctypes.byref(w), ctypes.byref(v),
+                           ctypes.byref(ms), _stream()))
+    return {"slices_per_group": k.value, "warps_per_block": w.value, "float4_layout": v.value,
+            "ms": ms.value}
+
+
 def hol_launch_count() -> int:
     return int(load().hol_launch_count())
 
@@ -271,6 +291,18 @@ class Context:
                                opts: hol_md_opts, u: float):
         """Algorithm 1; returns (accepted, dH, [S_B, S_F, K] at start and end)."""
         return fourier_accel_leapfrog(self._h, x, R_pf, R_p, self._nrhs(R_pf), opts, u, self.n)
+
+    def stochastic_measure(self, xi: torch.Tensor, Gxi: torch.Tensor, G2: torch.Tensor,
+                           G4: torch.Tensor | None = None, four_point: int = 0,
+                           tol: float = 1e-10, prec: int = HOL_F64, precond: bool = False,
+                           max_iter: int = 100000):
+        opts = hol_cg_opts(tol, max_iter, int(bool(precond)), prec, 50, 10)
+        return stochastic_measure(self._h, xi, self._nrhs(xi), opts, Gxi, G2, G4, four_point,
+                                  self.n)
+
+    def tune(self, n_rhs: int) -> dict:
+        """Pick the fastest launch shape of the fused M^T M for n_rhs (needs a field)."""
+        return hol_tune(self._h, n_rhs)
 
     def timer_enable(self, on: bool = True) -> None:
         hol_timer_enable(self._h, on)

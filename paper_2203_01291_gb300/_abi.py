@@ -64,9 +64,13 @@ SIGNATURES = {
     "fourier_accel_leapfrog": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.POINTER(hol_md_opts), _D,
                                     ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D),
                                     _VP]),
+    "stochastic_measure": (_I, [_VP, _VP, _I, ctypes.POINTER(hol_cg_opts), _VP, _VP, _VP, _I,
+                                ctypes.POINTER(_I), _VP]),
     "pseudofermion_phi": (_I, [_VP, _VP, _VP, _I, _VP]),
     "phi_to_rhs": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fermion_matvec_static": (_I, [ctypes.POINTER(hol_params), _VP, _I, _VP, _VP, _I, _VP]),
+    "hol_tune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                      ctypes.POINTER(_D), _VP]),
     "hol_launch_count": (ctypes.c_ulonglong, []),
     "hol_timer_enable": (_I, [_VP, _I]),
     "hol_timer_read": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),

@@ -38,48 +38,53 @@ struct LaneGeom {
     }
 };
 
-// Two-site bond factor [[ch, sh], [sh, ch]] on (own, partner) across lanes.
+// Each bond factor [[cosh, sinh], [sinh, cosh]](dtau t) is applied as
+// cosh * [[1, th], [th, 1]] with th = tanh(dtau t); the four factors cosh of
+// the four colours are folded into the stored diagonal exp(-dtau V) (times
+// cosh^4), so a bond costs one FMA per site.
+
+// Bond [[1, th], [th, 1]] on (own, partner) across lanes.
 template <typename R, int L>
-__device__ __forceinline__ void cb_xbond(R (&c)[L], int partner, R ch, R sh)
+__device__ __forceinline__ void cb_xbond(R (&c)[L], int partner, R th)
 {
 #pragma unroll
     for (int iy = 0; iy < L; ++iy) {
         const R o = __shfl_sync(kFull, c[iy], partner);
-        c[iy] = fma(ch, c[iy], sh * o);
+        c[iy] = fma(th, o, c[iy]);
     }
 }
 
-// Bond factor on register pairs (iy, iy+1 mod L), iy = P, P+2, ...
+// Bond on register pairs (iy, iy+1 mod L), iy = P, P+2, ...
 template <typename R, int L, int P>
-__device__ __forceinline__ void cb_ybond(R (&c)[L], R ch, R sh)
+__device__ __forceinline__ void cb_ybond(R (&c)[L], R th)
 {
 #pragma unroll
     for (int iy = P; iy < L; iy += 2) {
         const int j = (iy + 1) % L;
         const R a = c[iy], b = c[j];
-        c[iy] = fma(ch, a, sh * b);
-        c[j] = fma(sh, a, ch * b);
+        c[iy] = fma(th, b, a);
+        c[j] = fma(th, a, b);
     }
 }
 
-// c <- C c with C = C4 C3 C2 C1 (colour 1 acts first).
+// c <- C' c with C' = C4' C3' C2' C1' (colour 1 acts first), C = cosh^4 C'.
 template <typename R, int L>
-__device__ __forceinline__ void cb_apply(R (&c)[L], const LaneGeom<L>& g, R ch, R sh)
+__device__ __forceinline__ void cb_apply(R (&c)[L], const LaneGeom<L>& g, R th)
 {
-    cb_xbond<R, L>(c, g.p1, ch, sh);
-    cb_xbond<R, L>(c, g.p2, ch, sh);
-    cb_ybond<R, L, 0>(c, ch, sh);
-    cb_ybond<R, L, 1>(c, ch, sh);
+    cb_xbond<R, L>(c, g.p1, th);
+    cb_xbond<R, L>(c, g.p2, th);
+    cb_ybond<R, L, 0>(c, th);
+    cb_ybond<R, L, 1>(c, th);
 }
 
-// c <- C^T c with C^T = C1 C2 C3 C4 (colour 4 acts first).
+// c <- C'^T c (colour 4 acts first).
 template <typename R, int L>
-__device__ __forceinline__ void cb_apply_t(R (&c)[L], const LaneGeom<L>& g, R ch, R sh)
+__device__ __forceinline__ void cb_apply_t(R (&c)[L], const LaneGeom<L>& g, R th)
 {
-    cb_ybond<R, L, 1>(c, ch, sh);
-    cb_ybond<R, L, 0>(c, ch, sh);
-    cb_xbond<R, L>(c, g.p2, ch, sh);
-    cb_xbond<R, L>(c, g.p1, ch, sh);
+    cb_ybond<R, L, 1>(c, th);
+    cb_ybond<R, L, 0>(c, th);
+    cb_xbond<R, L>(c, g.p2, th);
+    cb_xbond<R, L>(c, g.p1, th);
 }
 
 // Warp-wide sum of a double, identical result in every lane (fixed order).

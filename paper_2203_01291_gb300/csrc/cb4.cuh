@@ -47,11 +47,12 @@ struct Geom4 {
     __device__ __forceinline__ int off(int k) const { return (rc * RT + k) * L + 4 * cx; }
 };
 
-__device__ __forceinline__ void bond(float& a, float& b, float ch, float sh)
+// bond [[1, th], [th, 1]] (cosh folded into the diagonal, see cb.cuh)
+__device__ __forceinline__ void bond(float& a, float& b, float th)
 {
     const float x = a, y = b;
-    a = fmaf(ch, x, sh * y);
-    b = fmaf(sh, x, ch * y);
+    a = fmaf(th, y, x);
+    b = fmaf(th, x, y);
 }
 
 __device__ __forceinline__ float4 shfl4(const float4& v, int src)
@@ -65,81 +66,81 @@ __device__ __forceinline__ float4 shfl4(const float4& v, int src)
 }
 
 template <int L>
-__device__ __forceinline__ void c4_colour1(float4 (&c)[L / 4], float ch, float sh)
+__device__ __forceinline__ void c4_colour1(float4 (&c)[L / 4], float th)
 {
 #pragma unroll
     for (int k = 0; k < L / 4; ++k) {
-        bond(c[k].x, c[k].y, ch, sh);
-        bond(c[k].z, c[k].w, ch, sh);
+        bond(c[k].x, c[k].y, th);
+        bond(c[k].z, c[k].w, th);
     }
 }
 
 template <int L>
-__device__ __forceinline__ void c4_colour2(float4 (&c)[L / 4], const Geom4<L>& g, float ch, float sh)
+__device__ __forceinline__ void c4_colour2(float4 (&c)[L / 4], const Geom4<L>& g, float th)
 {
 #pragma unroll
     for (int k = 0; k < L / 4; ++k) {
         const float rx = __shfl_sync(kFull, c[k].x, g.right);
         const float lw = __shfl_sync(kFull, c[k].w, g.left);
-        bond(c[k].y, c[k].z, ch, sh);
-        c[k].w = fmaf(ch, c[k].w, sh * rx);
-        c[k].x = fmaf(ch, c[k].x, sh * lw);
+        bond(c[k].y, c[k].z, th);
+        c[k].w = fmaf(th, rx, c[k].w);
+        c[k].x = fmaf(th, lw, c[k].x);
     }
 }
 
 template <int L>
-__device__ __forceinline__ void c4_colour3(float4 (&c)[L / 4], float ch, float sh)
+__device__ __forceinline__ void c4_colour3(float4 (&c)[L / 4], float th)
 {
 #pragma unroll
     for (int k = 0; k < L / 4; k += 2) {
-        bond(c[k].x, c[k + 1].x, ch, sh);
-        bond(c[k].y, c[k + 1].y, ch, sh);
-        bond(c[k].z, c[k + 1].z, ch, sh);
-        bond(c[k].w, c[k + 1].w, ch, sh);
+        bond(c[k].x, c[k + 1].x, th);
+        bond(c[k].y, c[k + 1].y, th);
+        bond(c[k].z, c[k + 1].z, th);
+        bond(c[k].w, c[k + 1].w, th);
     }
 }
 
 template <int L>
-__device__ __forceinline__ void c4_colour4(float4 (&c)[L / 4], const Geom4<L>& g, float ch, float sh)
+__device__ __forceinline__ void c4_colour4(float4 (&c)[L / 4], const Geom4<L>& g, float th)
 {
     constexpr int RT = L / 4;
     const float4 dn = shfl4(c[0], g.down);        // partner of my last row
     const float4 upv = shfl4(c[RT - 1], g.up);    // partner of my first row
 #pragma unroll
     for (int k = 1; k + 1 < RT; k += 2) {
-        bond(c[k].x, c[k + 1].x, ch, sh);
-        bond(c[k].y, c[k + 1].y, ch, sh);
-        bond(c[k].z, c[k + 1].z, ch, sh);
-        bond(c[k].w, c[k + 1].w, ch, sh);
+        bond(c[k].x, c[k + 1].x, th);
+        bond(c[k].y, c[k + 1].y, th);
+        bond(c[k].z, c[k + 1].z, th);
+        bond(c[k].w, c[k + 1].w, th);
     }
-    c[RT - 1].x = fmaf(ch, c[RT - 1].x, sh * dn.x);
-    c[RT - 1].y = fmaf(ch, c[RT - 1].y, sh * dn.y);
-    c[RT - 1].z = fmaf(ch, c[RT - 1].z, sh * dn.z);
-    c[RT - 1].w = fmaf(ch, c[RT - 1].w, sh * dn.w);
-    c[0].x = fmaf(ch, c[0].x, sh * upv.x);
-    c[0].y = fmaf(ch, c[0].y, sh * upv.y);
-    c[0].z = fmaf(ch, c[0].z, sh * upv.z);
-    c[0].w = fmaf(ch, c[0].w, sh * upv.w);
+    c[RT - 1].x = fmaf(th, dn.x, c[RT - 1].x);
+    c[RT - 1].y = fmaf(th, dn.y, c[RT - 1].y);
+    c[RT - 1].z = fmaf(th, dn.z, c[RT - 1].z);
+    c[RT - 1].w = fmaf(th, dn.w, c[RT - 1].w);
+    c[0].x = fmaf(th, upv.x, c[0].x);
+    c[0].y = fmaf(th, upv.y, c[0].y);
+    c[0].z = fmaf(th, upv.z, c[0].z);
+    c[0].w = fmaf(th, upv.w, c[0].w);
 }
 
 // c <- C c (colour 1 first)
 template <int L>
-__device__ __forceinline__ void c4_apply(float4 (&c)[L / 4], const Geom4<L>& g, float ch, float sh)
+__device__ __forceinline__ void c4_apply(float4 (&c)[L / 4], const Geom4<L>& g, float th)
 {
-    c4_colour1<L>(c, ch, sh);
-    c4_colour2<L>(c, g, ch, sh);
-    c4_colour3<L>(c, ch, sh);
-    c4_colour4<L>(c, g, ch, sh);
+    c4_colour1<L>(c, th);
+    c4_colour2<L>(c, g, th);
+    c4_colour3<L>(c, th);
+    c4_colour4<L>(c, g, th);
 }
 
 // c <- C^T c (colour 4 first)
 template <int L>
-__device__ __forceinline__ void c4_apply_t(float4 (&c)[L / 4], const Geom4<L>& g, float ch, float sh)
+__device__ __forceinline__ void c4_apply_t(float4 (&c)[L / 4], const Geom4<L>& g, float th)
 {
-    c4_colour4<L>(c, g, ch, sh);
-    c4_colour3<L>(c, ch, sh);
-    c4_colour2<L>(c, g, ch, sh);
-    c4_colour1<L>(c, ch, sh);
+    c4_colour4<L>(c, g, th);
+    c4_colour3<L>(c, th);
+    c4_colour2<L>(c, g, th);
+    c4_colour1<L>(c, th);
 }
 
 }  // namespace hol

@@ -63,15 +63,16 @@ int cuda_error(cudaError_t e, const char* what)
 
 namespace {
 
-// expV = exp(-dtau (alpha x - mu)) in FP64 and FP32; copy of x.
+// ev = cosh^4 exp(-dtau (alpha x - mu)) in FP64 and FP32 (the cosh factors
+// of the four checkerboard colours, see cb.cuh); copy of x.
 __global__ void k_expv(const double* __restrict__ x, double* __restrict__ xc,
                        double* __restrict__ ev64, float* __restrict__ ev32, long n, double dtau,
-                       double alpha, double mu)
+                       double alpha, double mu, double ch4)
 {
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
          k += (long)gridDim.x * blockDim.x) {
         const double xv = x[k];
-        const double e = exp(-dtau * (alpha * xv - mu));
+        const double e = ch4 * exp(-dtau * (alpha * xv - mu));
         xc[k] = xv;
         ev64[k] = e;
         ev32[k] = (float)e;
@@ -90,8 +91,10 @@ __global__ void k_dbar(const double* __restrict__ ev, double* __restrict__ dbar,
 
 // Norm bounds of the Bbar spectrum: every checkerboard colour has
 // eigenvalues exp(+-dtau t), so |Bbar| <= max(dbar) e^{4 dtau |t|} and
-// |Bbar^{-1}| <= e^{4 dtau |t|} / min(dbar). One block.
-__global__ void k_bounds(const double* __restrict__ dbar, int N, double g4, double* __restrict__ scal)
+// |Bbar^{-1}| <= e^{4 dtau |t|} / min(dbar), dbar of Eq. (expnVbar) (the
+// stored dbar carries the factor cosh^4, removed here). One block.
+__global__ void k_bounds(const double* __restrict__ dbar, int N, double g4, double ch4,
+                         double* __restrict__ scal)
 {
     __shared__ double smin[32], smax[32];
     double lo = 1e300, hi = -1e300;
@@ -115,8 +118,8 @@ __global__ void k_bounds(const double* __restrict__ dbar, int N, double g4, doub
             lo = fmin(lo, smin[k]);
             hi = fmax(hi, smax[k]);
         }
-        scal[S_BMIN] = lo / g4;
-        scal[S_BMAX] = hi * g4;
+        scal[S_BMIN] = lo / ch4 / g4;
+        scal[S_BMAX] = hi / ch4 * g4;
     }
 }
 
@@ -127,7 +130,7 @@ void free_ctx(hol_ctx* c)
                    c->v64c, c->v64d, c->v64e, c->v32a, c->v32b, c->v32c, c->v32d, c->v32e,
                    c->mask, c->kpm.np, c->kpm.coef, c->cbuf0, c->cbuf1, c->v64f, c->v32f,
                    c->tw64, c->tw32, c->md_phi, c->md_b, c->md_v, c->md_F, c->md_p,
-                   c->md_x0, c->md_g, c->md_s};
+                   c->md_x0, c->md_g, c->md_s, c->ms_acc, c->twL64};
     for (void* p : dev)
         if (p) cudaFree(p);
     timer_free(c->timer);
@@ -167,11 +170,15 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     c->N = p->L * p->L;
     c->T = p->Ltau;
     c->n = (long)c->N * c->T;
-    c->ch = cosh(p->dtau * p->t);
-    c->sh = sinh(p->dtau * p->t);
+    c->th = tanh(p->dtau * p->t);
+    {
+        const double ch = cosh(p->dtau * p->t);
+        c->ch4 = ch * ch * ch * ch;
+    }
     c->mv_k = (c->T % 4 == 0 && c->T >= 8) ? 2 : 1;
     c->mv_warps = 4;
     c->mv_vec = 1;
+    c->kpm_reg = 1;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         free_ctx(c);
         return set_error(HOL_ECUDA, "hol_create: no CUDA device");
@@ -221,6 +228,7 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     {
         int rc = precond_alloc(c);
         if (!rc) rc = leapfrog_alloc(c);
+        if (!rc) rc = measure_alloc(c);
         if (rc) {
             free_ctx(c);
             return rc;
@@ -247,11 +255,13 @@ extern "C" int hol_set_field(hol_ctx* c, const double* x, void* stream)
     if (!c || !x) return set_error(HOL_EINVAL, "hol_set_field: null argument");
     cudaStream_t s = (cudaStream_t)stream;
     const int nb = ceil_div(c->n, 256) < 4096 ? ceil_div(c->n, 256) : 4096;
-    k_expv<<<nb, 256, 0, s>>>(x, c->x, c->ev64, c->ev32, c->n, c->p.dtau, c->p.alpha, c->p.mu);
+    k_expv<<<nb, 256, 0, s>>>(x, c->x, c->ev64, c->ev32, c->n, c->p.dtau, c->p.alpha, c->p.mu,
+                              c->ch4);
     HOL_CHECK_LAUNCH("k_expv");
     k_dbar<<<ceil_div(c->N, 128), 128, 0, s>>>(c->ev64, c->dbar, c->N, c->T);
     HOL_CHECK_LAUNCH("k_dbar");
-    k_bounds<<<1, 256, 0, s>>>(c->dbar, c->N, exp(4.0 * c->p.dtau * fabs(c->p.t)), c->scal);
+    k_bounds<<<1, 256, 0, s>>>(c->dbar, c->N, exp(4.0 * c->p.dtau * fabs(c->p.t)), c->ch4,
+                               c->scal);
     HOL_CHECK_LAUNCH("k_bounds");
     int rc = kpm_setup(c, s);
     if (rc) return rc;

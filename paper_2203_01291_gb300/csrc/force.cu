@@ -17,7 +17,7 @@ struct ForceArgs {
     int T, K, nrun, n_pf;
     long n;
     int with_bos;
-    double ch, sh, da, dtau, w02;
+    double th, da, dtau, w02;
 };
 
 template <int L>
@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(128) k_force(const double* __restrict__ v,
                 f[iy] -= 0.5 * a.da * bv;
                 c[iy] = vv;
             }
-            cb_apply<double, L>(c, geo, a.ch, a.sh);
+            cb_apply<double, L>(c, geo, a.th);
 #pragma unroll
             for (int iy = 0; iy < L; ++iy) {
                 const double y = ev[(long)tau * N + iy * L + geo.ix] * c[iy];
@@ -107,8 +107,7 @@ int run_force(hol_ctx* c, const double* v, const double* b, int n_pf, double* F,
     a.n_pf = n_pf;
     a.n = c->n;
     a.with_bos = with_bos;
-    a.ch = c->ch;
-    a.sh = c->sh;
+    a.th = c->th;
     a.da = c->p.dtau * c->p.alpha;
     a.dtau = c->p.dtau;
     a.w02 = c->p.omega0 * c->p.omega0;

@@ -76,13 +76,14 @@ struct hol_ctx {
     int L, N, T;
     long n;              // N * T
     int device;
-    double ch, sh;       // cosh, sinh (dtau t)
+    double th;           // tanh(dtau t): checkerboard bond [[1, th], [th, 1]]
+    double ch4;          // cosh(dtau t)^4, folded into the stored exp(-dtau V)
 
     // field-derived data (hol_set_field)
     double* x;           // [T][N] copy of the field
-    double* ev64;        // [T][N] exp(-dtau (alpha x - mu))
+    double* ev64;        // [T][N] cosh^4 exp(-dtau (alpha x - mu))
     float* ev32;         // [T][N] float copy
-    double* dbar;        // [N] tau-average of ev64
+    double* dbar;        // [N] tau-average of ev64 (so cosh^4 times Eq. (expnVbar))
     double* scal;        // [S_COUNT] device scalars
     int field_set;
 
@@ -114,6 +115,8 @@ struct hol_ctx {
     double* md_x0;       // leapfrog: x at the start of a trajectory
     double* md_g;        // leapfrog: mass tables [3][T]
     double* md_s;        // leapfrog: energy terms [16]
+    double2* ms_acc;     // measurement accumulators [5][T][N] complex
+    double2* twL64;      // [2L] exp(-i pi k / L)
     double2* cbuf0;      // complex half-spectrum buffers [max_rhs][T/2][N]
     double2* cbuf1;
     long cbuf_len;
@@ -126,6 +129,7 @@ struct hol_ctx {
     int mv_k;            // tau slices per lane group in the matvec kernels
     int mv_warps;        // warps per block in the matvec kernels
     int mv_vec;          // use the float4 layout of the fused FP32 M^T M (L % 8 == 0)
+    int kpm_reg;         // use the register KPM kernel (FP32, L = 16 or 32)
 };
 
 namespace hol {
@@ -178,6 +182,7 @@ int elementwise_blocks(const hol_ctx* c);
 // per (rhs, tile) at stride kRedStride, precond_tiles(c, prec) per rhs.
 int precond_alloc(hol_ctx* c);
 int leapfrog_alloc(hol_ctx* c);
+int measure_alloc(hol_ctx* c);
 int precond_check_shape(const hol_ctx* c);
 int precond_tiles(const hol_ctx* c, int prec);
 int precond_apply_impl(hol_ctx* c, int prec, const void* v, void* out, int n_rhs, int mode,

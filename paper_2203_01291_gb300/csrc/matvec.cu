@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(128) k_M(const R* __restrict__ v, const R* __r
                                            R* __restrict__ pnew, R* __restrict__ out,
                                            const R* __restrict__ ev, MvGeom gm,
                                            const int* __restrict__ mask, BetaSrc bsrc,
-                                           double* __restrict__ norm_part, R ch, R sh)
+                                           double* __restrict__ norm_part, R th)
 {
     constexpr int N = L * L;
     const LaneGeom<L> geo;
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(128) k_M(const R* __restrict__ v, const R* __r
     for (int s = 0; s < gm.K; ++s) {
         const int tau = t0 + s;
         const long o = base + (long)tau * N;
-        cb_apply<R, L>(a, geo, (R)ch, (R)sh);
+        cb_apply<R, L>(a, geo, (R)th);
 #pragma unroll
         for (int iy = 0; iy < L; ++iy) {
             R val = v[o + iy * L];
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(128) k_M(const R* __restrict__ v, const R* __r
 template <typename R, int L, int EPI>
 __global__ void __launch_bounds__(128) k_MT(const R* __restrict__ u, const R* __restrict__ bvec,
                                             R* __restrict__ out, const R* __restrict__ ev,
-                                            MvGeom gm, const int* __restrict__ mask, R ch, R sh)
+                                            MvGeom gm, const int* __restrict__ mask, R th)
 {
     constexpr int N = L * L;
     const LaneGeom<L> geo;
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(128) k_MT(const R* __restrict__ u, const R* __
         const int tp = (tau + 1 == gm.T) ? 0 : tau + 1;
 #pragma unroll
         for (int iy = 0; iy < L; ++iy) a[iy] *= ev[(long)tp * N + iy * L + geo.ix];
-        cb_apply_t<R, L>(a, geo, (R)ch, (R)sh);
+        cb_apply_t<R, L>(a, geo, (R)th);
         const long o = base + (long)tau * N;
         const R sg = (tp == 0) ? R(1) : R(-1);
 #pragma unroll
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(128) k_cg_mtm32(const float* __restrict__ r,
                                                   const double* __restrict__ rr_new_part,
                                                   const double* __restrict__ rr_old_part,
                                                   int rr_stride, int rr_n, int first,
-                                                  double* __restrict__ pq_part, float ch, float sh)
+                                                  double* __restrict__ pq_part, float th)
 {
     constexpr int N = L * L;
     const LaneGeom<L> geo;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(128) k_cg_mtm32(const float* __restrict__ r,
         const long o = base + (long)tm * N;
 #pragma unroll
         for (int iy = 0; iy < L; ++iy) Y[iy] = fmaf(bt, pold[o + iy * L], r[o + iy * L]);
-        cb_apply<float, L>(Y, geo, ch, sh);
+        cb_apply<float, L>(Y, geo, th);
     }
     // W <- w_{t0} = p_{t0} + s_{t0} D_{t0} C p_{t0-1};  X <- C p_{t0}
     {
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(128) k_cg_mtm32(const float* __restrict__ r,
             X[iy] = pv;
             W[iy] = fmaf(sg * ev[(long)t0 * N + iy * L + geo.ix], Y[iy], pv);
         }
-        cb_apply<float, L>(X, geo, ch, sh);
+        cb_apply<float, L>(X, geo, th);
     }
     double acc = 0.0;
     for (int s = 0; s < gm.K; ++s) {
@@ -242,8 +242,8 @@ __global__ void __launch_bounds__(128) k_cg_mtm32(const float* __restrict__ r,
             X[iy] = fmaf(d, X[iy], pv);       // w_{tau+1}
             Y[iy] = d * X[iy];
         }
-        cb_apply<float, L>(P, geo, ch, sh);     // C p_{tau+1}
-        cb_apply_t<float, L>(Y, geo, ch, sh);   // C^T s D w_{tau+1}
+        cb_apply<float, L>(P, geo, th);     // C p_{tau+1}
+        cb_apply_t<float, L>(Y, geo, th);   // C^T s D w_{tau+1}
         const long o = base + (long)tau * N;
         float part = 0.0f;
 #pragma unroll
@@ -285,8 +285,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
                                                      const double* __restrict__ rr_new_part,
                                                      const double* __restrict__ rr_old_part,
                                                      int rr_stride, int rr_n, int first,
-                                                     double* __restrict__ pq_part, float ch,
-                                                     float sh)
+                                                     double* __restrict__ pq_part, float th)
 {
     constexpr int N = L * L;
     constexpr int RT = L / 4;
@@ -313,7 +312,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
         const long o = base + (long)tm * N;
 #pragma unroll
         for (int k = 0; k < RT; ++k) Y[k] = fma4s(bt, ld4(pold, o + geo.off(k)), ld4(r, o + geo.off(k)));
-        c4_apply<L>(Y, geo, ch, sh);
+        c4_apply<L>(Y, geo, th);
     }
     {
         const long o = base + (long)t0 * N;
@@ -327,7 +326,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
             W[k] = make_float4(fmaf(sg * d.x, Y[k].x, pv.x), fmaf(sg * d.y, Y[k].y, pv.y),
                                fmaf(sg * d.z, Y[k].z, pv.z), fmaf(sg * d.w, Y[k].w, pv.w));
         }
-        c4_apply<L>(X, geo, ch, sh);
+        c4_apply<L>(X, geo, th);
     }
     double acc = 0.0;
     for (int s = 0; s < gm.K; ++s) {
@@ -347,8 +346,8 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
                                fmaf(d.z, X[k].z, pv.z), fmaf(d.w, X[k].w, pv.w));
             Y[k] = make_float4(d.x * X[k].x, d.y * X[k].y, d.z * X[k].z, d.w * X[k].w);
         }
-        c4_apply<L>(P, geo, ch, sh);
-        c4_apply_t<L>(Y, geo, ch, sh);
+        c4_apply<L>(P, geo, th);
+        c4_apply_t<L>(Y, geo, th);
         const long o = base + (long)tau * N;
         float part = 0.0f;
 #pragma unroll
@@ -365,6 +364,143 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
         }
         acc += (double)part;
     }
+    if (pq_part != nullptr) group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
+}
+
+
+// ---------------------------------------------------------------------------
+// Float4 fused CG step with the r and p_old rows of the next tau slice
+// prefetched into a per-lane shared-memory ring by cp.async (16-byte async
+// copies, two stages), so the global loads of slice tau+1 are in flight
+// while slice tau is computed. Each lane copies and later reads only its own
+// slots, so cp.async.wait_group is the only synchronisation needed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND)); }
+
+template <int L>
+__global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict__ r,
+                                                         const float* __restrict__ pold,
+                                                         float* __restrict__ pnew,
+                                                         float* __restrict__ q,
+                                                         const float* __restrict__ ev, MvGeom gm,
+                                                         const int* __restrict__ mask,
+                                                         const double* __restrict__ rr_new_part,
+                                                         const double* __restrict__ rr_old_part,
+                                                         int rr_stride, int rr_n, int first,
+                                                         double* __restrict__ pq_part, float th)
+{
+    constexpr int N = L * L;
+    constexpr int RT = L / 4;
+    extern __shared__ __align__(16) float4 ring[];   // [warp][slot][array][RT][32]
+    const Geom4<L> geo;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* my = ring + (long)wib * (2 * 2 * RT * 32);
+    auto slot_ptr = [&](int slot, int arr, int k) -> float4* {
+        return my + ((slot * 2 + arr) * RT + k) * 32 + lane;
+    };
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int rhs = warp / gm.wpr;
+    if (rhs >= gm.n_rhs) return;
+    if (mask != nullptr && mask[rhs] == 0) return;
+    const int run = (warp - rhs * gm.wpr) * Geom4<L>::G + geo.g;
+    const bool valid = geo.ok && run < gm.nrun;
+    const int t0 = (run < gm.nrun ? run : gm.nrun - 1) * gm.K;
+    const long base = (long)rhs * gm.T * N;
+    // slice sequence: j = 0 -> t0-1 (halo), j = 1.. -> t0, t0+1, ..., t0+K
+    auto seq = [&](int j) -> int {
+        int t = t0 - 1 + j;
+        if (t < 0) t += gm.T;
+        if (t >= gm.T) t -= gm.T;
+        return t;
+    };
+    auto issue = [&](int j) {
+        const long o = base + (long)seq(j) * N;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            cp_async16(slot_ptr(j & 1, 0, k), r + o + geo.off(k));
+            cp_async16(slot_ptr(j & 1, 1, k), pold + o + geo.off(k));
+        }
+        cp_async_commit();
+    };
+    const int last = gm.K + 1;   // index of the last slice in the sequence
+    issue(0);
+    issue(1);
+
+    float bt = 0.0f;
+    if (!first) {
+        const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
+        const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
+        bt = (float)(rn / ro);
+    }
+
+    float4 W[RT], X[RT], P[RT], Y[RT];
+    cp_async_wait<1>();   // slice j = 0 has landed
+#pragma unroll
+    for (int k = 0; k < RT; ++k) Y[k] = fma4s(bt, *slot_ptr(0, 1, k), *slot_ptr(0, 0, k));
+    c4_apply<L>(Y, geo, th);
+    if (2 <= last) issue(2); else cp_async_commit();
+    cp_async_wait<1>();   // slice j = 1 (t0)
+    {
+        const long o = base + (long)t0 * N;
+        const float sg = (t0 == 0) ? 1.0f : -1.0f;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float4 pv = fma4s(bt, *slot_ptr(1, 1, k), *slot_ptr(1, 0, k));
+            if (valid && pnew != nullptr) st4(pnew, o + geo.off(k), pv);
+            X[k] = pv;
+            const float4 d = ld4(ev, (long)t0 * N + geo.off(k));
+            W[k] = make_float4(fmaf(sg * d.x, Y[k].x, pv.x), fmaf(sg * d.y, Y[k].y, pv.y),
+                               fmaf(sg * d.z, Y[k].z, pv.z), fmaf(sg * d.w, Y[k].w, pv.w));
+        }
+        c4_apply<L>(X, geo, th);
+    }
+    double acc = 0.0;
+    for (int s = 0; s < gm.K; ++s) {
+        const int j = s + 2;             // slice t0 + 1 + s
+        if (j + 1 <= last) issue(j + 1); else cp_async_commit();
+        cp_async_wait<1>();
+        const int tau = t0 + s;
+        const int tp = (tau + 1 == gm.T) ? 0 : tau + 1;
+        const long op = base + (long)tp * N;
+        const float sgp = (tp == 0) ? 1.0f : -1.0f;
+        const bool own = valid && (s + 1 < gm.K) && pnew != nullptr;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float4 pv = fma4s(bt, *slot_ptr(j & 1, 1, k), *slot_ptr(j & 1, 0, k));
+            if (own) st4(pnew, op + geo.off(k), pv);
+            P[k] = pv;
+            float4 d = ld4(ev, (long)tp * N + geo.off(k));
+            d.x *= sgp; d.y *= sgp; d.z *= sgp; d.w *= sgp;
+            X[k] = make_float4(fmaf(d.x, X[k].x, pv.x), fmaf(d.y, X[k].y, pv.y),
+                               fmaf(d.z, X[k].z, pv.z), fmaf(d.w, X[k].w, pv.w));
+            Y[k] = make_float4(d.x * X[k].x, d.y * X[k].y, d.z * X[k].z, d.w * X[k].w);
+        }
+        c4_apply<L>(P, geo, th);
+        c4_apply_t<L>(Y, geo, th);
+        const long o = base + (long)tau * N;
+        float part = 0.0f;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            if (valid)
+                st4(q, o + geo.off(k), make_float4(W[k].x + Y[k].x, W[k].y + Y[k].y,
+                                                   W[k].z + Y[k].z, W[k].w + Y[k].w));
+            part = fmaf(W[k].x, W[k].x, part);
+            part = fmaf(W[k].y, W[k].y, part);
+            part = fmaf(W[k].z, W[k].z, part);
+            part = fmaf(W[k].w, W[k].w, part);
+            W[k] = X[k];
+            X[k] = P[k];
+        }
+        acc += (double)part;
+    }
+    cp_async_wait<0>();
     if (pq_part != nullptr) group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
 }
 
@@ -389,12 +525,11 @@ int run_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs, const
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     if (prec == HOL_F64)
         k_M<double, L, false><<<nb, nt, 0, s>>>((const double*)v, nullptr, nullptr, (double*)out,
-                                                c->ev64, g, mask, BetaSrc{}, norm_part, c->ch,
-                                                c->sh);
+                                                c->ev64, g, mask, BetaSrc{}, norm_part, c->th);
     else
         k_M<float, L, false><<<nb, nt, 0, s>>>((const float*)v, nullptr, nullptr, (float*)out,
                                                c->ev32, g, mask, BetaSrc{}, norm_part,
-                                               (float)c->ch, (float)c->sh);
+                                               (float)c->th);
     HOL_CHECK_LAUNCH("k_M");
     return HOL_OK;
 }
@@ -406,7 +541,7 @@ int run_M_upd64(const hol_ctx* c, const double* r, const double* pold, double* p
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     k_M<double, L, true><<<nb, nt, 0, s>>>(r, pold, pnew, w, c->ev64, g, mask, beta, norm_part,
-                                           c->ch, c->sh);
+                                           c->th);
     HOL_CHECK_LAUNCH("k_M upd");
     return HOL_OK;
 }
@@ -419,10 +554,10 @@ int run_MT(const hol_ctx* c, int prec, const void* u, void* out, int n_rhs, cons
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     if (prec == HOL_F64)
         k_MT<double, L, MT_PLAIN><<<nb, nt, 0, s>>>((const double*)u, nullptr, (double*)out,
-                                                    c->ev64, g, mask, c->ch, c->sh);
+                                                    c->ev64, g, mask, c->th);
     else
         k_MT<float, L, MT_PLAIN><<<nb, nt, 0, s>>>((const float*)u, nullptr, (float*)out, c->ev32,
-                                                   g, mask, (float)c->ch, (float)c->sh);
+                                                   g, mask, (float)c->th);
     HOL_CHECK_LAUNCH("k_MT");
     return HOL_OK;
 }
@@ -433,7 +568,7 @@ int run_MT_resid(const hol_ctx* c, const double* u, const double* b, double* out
 {
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-    k_MT<double, L, MT_RESID><<<nb, nt, 0, s>>>(u, b, out, c->ev64, g, mask, c->ch, c->sh);
+    k_MT<double, L, MT_RESID><<<nb, nt, 0, s>>>(u, b, out, c->ev64, g, mask, c->th);
     HOL_CHECK_LAUNCH("k_MT resid");
     return HOL_OK;
 }
@@ -446,16 +581,25 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     if constexpr (L % 8 == 0) {
+        if (c->mv_vec == 2) {
+            const size_t sm = (size_t)c->mv_warps * 2 * 2 * (L / 4) * 32 * sizeof(float4);
+            if (sm > 48 * 1024)
+                HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_mtm32_v4a<L>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_cg_mtm32_v4a<L><<<nb, nt, sm, s>>>(r, pold, pnew, q, c->ev32, g, mask, rr_new, rr_old,
+                                                  rr_stride, rr_n, first, pq_part, (float)c->th);
+            HOL_CHECK_LAUNCH("k_cg_mtm32_v4a");
+            return HOL_OK;
+        }
         if (c->mv_vec) {
             k_cg_mtm32_v4<L><<<nb, nt, 0, s>>>(r, pold, pnew, q, c->ev32, g, mask, rr_new, rr_old,
-                                                rr_stride, rr_n, first, pq_part, (float)c->ch,
-                                                (float)c->sh);
+                                                rr_stride, rr_n, first, pq_part, (float)c->th);
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4");
             return HOL_OK;
         }
     }
     k_cg_mtm32<L><<<nb, nt, 0, s>>>(r, pold, pnew, q, c->ev32, g, mask, rr_new, rr_old, rr_stride,
-                                     rr_n, first, pq_part, (float)c->ch, (float)c->sh);
+                                     rr_n, first, pq_part, (float)c->th);
     HOL_CHECK_LAUNCH("k_cg_mtm32");
     return HOL_OK;
 }

@@ -44,12 +44,14 @@ int static_scratch(double** out)
     return HOL_OK;
 }
 
+// cosh^4 exp(-dtau (alpha x - mu)): the diagonal with the cosh factors of
+// the checkerboard colours folded in, as the operator kernels expect
 __global__ void k_expv_static(const double* __restrict__ x, double* __restrict__ ev, long n,
-                              double dtau, double alpha, double mu)
+                              double dtau, double alpha, double mu, double ch4)
 {
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
          k += (long)gridDim.x * blockDim.x)
-        ev[k] = exp(-dtau * (alpha * x[k] - mu));
+        ev[k] = ch4 * exp(-dtau * (alpha * x[k] - mu));
 }
 
 }  // namespace
@@ -86,15 +88,16 @@ extern "C" int fermion_matvec_static(const hol_params* p, const double* x, int o
     c.N = p->L * p->L;
     c.T = p->Ltau;
     c.n = n;
-    c.ch = cosh(p->dtau * p->t);
-    c.sh = sinh(p->dtau * p->t);
+    c.th = tanh(p->dtau * p->t);
+    const double ch = cosh(p->dtau * p->t);
+    c.ch4 = ch * ch * ch * ch;
     c.mv_k = (c.T % 4 == 0 && c.T >= 8) ? 2 : 1;
     c.mv_warps = 4;
     c.ev64 = scratch;
     cudaStream_t s = (cudaStream_t)stream;
     int nb = (int)((n + 255) / 256);
     if (nb > 4096) nb = 4096;
-    k_expv_static<<<nb, 256, 0, s>>>(x, scratch, n, p->dtau, p->alpha, p->mu);
+    k_expv_static<<<nb, 256, 0, s>>>(x, scratch, n, p->dtau, p->alpha, p->mu, c.ch4);
     HOL_CHECK_LAUNCH("k_expv_static");
     switch (op) {
     case HOL_OP_M:

@@ -133,13 +133,13 @@ __global__ void __launch_bounds__(256) k_tau_inv(const typename Cx<R>::T2* __res
 struct KpmArgs {
     int L, N, Th, max_np;
     int mode;         // bit 0: apply conj-coefficient series of A^T first; bit 1: then series of A
-    double ch, sh;
+    double th;        // tanh(dtau t); dbar carries cosh^4 (see cb.cuh)
 };
 
 // In-place checkerboard colour (0: x-even, 1: x-odd, 2: y-even, 3: y-odd) on
 // a complex vector in shared memory; pairs are processed in parallel.
 template <typename C2, typename R>
-__device__ __forceinline__ void kpm_colour(C2* v, int colour, int L, R ch, R sh)
+__device__ __forceinline__ void kpm_colour(C2* v, int colour, int L, R th)
 {
     const int half = L / 2;
     const int npair = L * half;
@@ -158,10 +158,10 @@ __device__ __forceinline__ void kpm_colour(C2* v, int colour, int L, R ch, R sh)
         }
         const C2 a = v[i], b = v[j];
         C2 na, nb;
-        na.x = fma(ch, a.x, sh * b.x);
-        na.y = fma(ch, a.y, sh * b.y);
-        nb.x = fma(sh, a.x, ch * b.x);
-        nb.y = fma(sh, a.y, ch * b.y);
+        na.x = fma(th, b.x, a.x);
+        na.y = fma(th, b.y, a.y);
+        nb.x = fma(th, a.x, b.x);
+        nb.y = fma(th, a.y, b.y);
         v[i] = na;
         v[j] = nb;
     }
@@ -181,7 +181,7 @@ __device__ void kpm_series(typename Cx<R>::T2* cur, const double* __restrict__ d
 {
     using C2 = typename Cx<R>::T2;
     const int N = ka.N;
-    const R ch = (R)ka.ch, sh = (R)ka.sh;
+    const R th = (R)ka.th;
     C2 prev[kKpmMaxE], acc[kKpmMaxE], old[kKpmMaxE];
     R dd[kKpmMaxE];
     {
@@ -215,15 +215,15 @@ __device__ void kpm_series(typename Cx<R>::T2* cur, const double* __restrict__ d
         }
         __syncthreads();
         if (trans) {
-            kpm_colour<C2, R>(cur, 3, ka.L, ch, sh);
-            kpm_colour<C2, R>(cur, 2, ka.L, ch, sh);
-            kpm_colour<C2, R>(cur, 1, ka.L, ch, sh);
-            kpm_colour<C2, R>(cur, 0, ka.L, ch, sh);
+            kpm_colour<C2, R>(cur, 3, ka.L, th);
+            kpm_colour<C2, R>(cur, 2, ka.L, th);
+            kpm_colour<C2, R>(cur, 1, ka.L, th);
+            kpm_colour<C2, R>(cur, 0, ka.L, th);
         } else {
-            kpm_colour<C2, R>(cur, 0, ka.L, ch, sh);
-            kpm_colour<C2, R>(cur, 1, ka.L, ch, sh);
-            kpm_colour<C2, R>(cur, 2, ka.L, ch, sh);
-            kpm_colour<C2, R>(cur, 3, ka.L, ch, sh);
+            kpm_colour<C2, R>(cur, 0, ka.L, th);
+            kpm_colour<C2, R>(cur, 1, ka.L, th);
+            kpm_colour<C2, R>(cur, 2, ka.L, th);
+            kpm_colour<C2, R>(cur, 3, ka.L, th);
         }
         double2 c = coef[m];
         if (conjc) c.y = -c.y;
@@ -292,17 +292,270 @@ __global__ void __launch_bounds__(256) k_kpm(const typename Cx<R>::T2* __restric
     for (int i = threadIdx.x; i < N; i += blockDim.x) vout[off + i] = cur[i];
 }
 
+// ---------------------------------------------------------------- KPM, registers
+// FP32 KPM for L = 16 and 32 with the slice in registers. Lane (j, cx) of
+// warp w holds rows 2J, 2J+1 (J = w * PPW + j) and columns 4cx..4cx+3 of the
+// complex N-vector; x-bonds and in-warp y-bonds are shuffles, the colour-4
+// bond between the last row of one warp and the first row of the next goes
+// through shared memory (one barrier per Bbar apply, slots alternate).
+struct CV {
+    float4 re, im;
+};
+
+__device__ __forceinline__ void bond2(float& a, float& b, float th)
+{
+    const float x = a, y = b;
+    a = fmaf(th, y, x);
+    b = fmaf(th, x, y);
+}
+__device__ __forceinline__ void bond4(float4& a, float4& b, float th)
+{
+    bond2(a.x, b.x, th);
+    bond2(a.y, b.y, th);
+    bond2(a.z, b.z, th);
+    bond2(a.w, b.w, th);
+}
+__device__ __forceinline__ void addmul4(float4& a, const float4& b, float th)
+{
+    a.x = fmaf(th, b.x, a.x);
+    a.y = fmaf(th, b.y, a.y);
+    a.z = fmaf(th, b.z, a.z);
+    a.w = fmaf(th, b.w, a.w);
+}
+__device__ __forceinline__ float4 shf(const float4& v, int src)
+{
+    return make_float4(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src),
+                       __shfl_sync(kFull, v.z, src), __shfl_sync(kFull, v.w, src));
+}
+
+template <int L>
+struct KGeo {
+    static constexpr int LR = L / 4;          // lanes per row segment
+    static constexpr int PPW = 32 / LR;       // row pairs per warp
+    static constexpr int W = L / (2 * PPW);   // warps per problem
+    int lane, w, j, cx, right, left, down, up;
+    __device__ __forceinline__ KGeo()
+    {
+        lane = threadIdx.x & 31;
+        w = threadIdx.x >> 5;
+        j = lane / LR;
+        cx = lane - j * LR;
+        right = j * LR + (cx + 1 == LR ? 0 : cx + 1);
+        left = j * LR + (cx == 0 ? LR - 1 : cx - 1);
+        down = (lane + LR) & 31;
+        up = (lane + 32 - LR) & 31;
+    }
+    __device__ __forceinline__ int row0() const { return 2 * (w * PPW + j); }
+};
+
+// colour 1 (x, even ix): inside the float4
+__device__ __forceinline__ void kc1(CV (&v)[2], float th)
+{
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        bond2(v[r].re.x, v[r].re.y, th);
+        bond2(v[r].re.z, v[r].re.w, th);
+        bond2(v[r].im.x, v[r].im.y, th);
+        bond2(v[r].im.z, v[r].im.w, th);
+    }
+}
+// colour 2 (x, odd ix): (.y,.z) inside, .w with right.x, .x with left.w
+template <int L>
+__device__ __forceinline__ void kc2(CV (&v)[2], const KGeo<L>& g, float th)
+{
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const float rxr = __shfl_sync(kFull, v[r].re.x, g.right);
+        const float rxi = __shfl_sync(kFull, v[r].im.x, g.right);
+        const float lwr = __shfl_sync(kFull, v[r].re.w, g.left);
+        const float lwi = __shfl_sync(kFull, v[r].im.w, g.left);
+        bond2(v[r].re.y, v[r].re.z, th);
+        bond2(v[r].im.y, v[r].im.z, th);
+        v[r].re.w = fmaf(th, rxr, v[r].re.w);
+        v[r].im.w = fmaf(th, rxi, v[r].im.w);
+        v[r].re.x = fmaf(th, lwr, v[r].re.x);
+        v[r].im.x = fmaf(th, lwi, v[r].im.x);
+    }
+}
+// colour 3 (y, even iy): rows 2J, 2J+1 of the same lane
+__device__ __forceinline__ void kc3(CV (&v)[2], float th)
+{
+    bond4(v[0].re, v[1].re, th);
+    bond4(v[0].im, v[1].im, th);
+}
+// colour 4 (y, odd iy): row 2J+1 with row 2J+2 (next lane group / next warp)
+template <int L>
+__device__ __forceinline__ void kc4(CV (&v)[2], const KGeo<L>& g, float th, float4* xbuf, int par)
+{
+    CV dn, upv;
+    dn.re = shf(v[0].re, g.down);
+    dn.im = shf(v[0].im, g.down);
+    upv.re = shf(v[1].re, g.up);
+    upv.im = shf(v[1].im, g.up);
+    if (KGeo<L>::W > 1) {
+        constexpr int LR = KGeo<L>::LR;
+        constexpr int PPW = KGeo<L>::PPW;
+        constexpr int W = KGeo<L>::W;
+        // slots: [par][w][0: first row of warp, 1: last row of warp][cx][re,im]
+        float4* sl = xbuf + par * (W * 2 * LR * 2);
+        if (g.j == 0) {
+            sl[((g.w * 2 + 0) * LR + g.cx) * 2 + 0] = v[0].re;
+            sl[((g.w * 2 + 0) * LR + g.cx) * 2 + 1] = v[0].im;
+        }
+        if (g.j == PPW - 1) {
+            sl[((g.w * 2 + 1) * LR + g.cx) * 2 + 0] = v[1].re;
+            sl[((g.w * 2 + 1) * LR + g.cx) * 2 + 1] = v[1].im;
+        }
+        __syncthreads();
+        if (g.j == PPW - 1) {
+            const int wn = (g.w + 1) % W;
+            dn.re = sl[((wn * 2 + 0) * LR + g.cx) * 2 + 0];
+            dn.im = sl[((wn * 2 + 0) * LR + g.cx) * 2 + 1];
+        }
+        if (g.j == 0) {
+            const int wp = (g.w + W - 1) % W;
+            upv.re = sl[((wp * 2 + 1) * LR + g.cx) * 2 + 0];
+            upv.im = sl[((wp * 2 + 1) * LR + g.cx) * 2 + 1];
+        }
+    }
+    addmul4(v[1].re, dn.re, th);
+    addmul4(v[1].im, dn.im, th);
+    addmul4(v[0].re, upv.re, th);
+    addmul4(v[0].im, upv.im, th);
+}
+
+template <int L>
+__global__ void __launch_bounds__(32 * (L / (2 * (32 / (L / 4)))))
+    k_kpm_reg(const float2* __restrict__ vin, float2* __restrict__ vout,
+              const double* __restrict__ dbar, const double* __restrict__ scal,
+              const int* __restrict__ npv, const double2* __restrict__ coef, int n_rhs, int Th,
+              int max_np, int mode, float th)
+{
+    constexpr int N = L * L;
+    __shared__ float4 xbuf[2 * 2 * 4 * 8 * 2];
+    const KGeo<L> g;
+    const int wq = blockIdx.x / n_rhs, rhs = blockIdx.x - wq * n_rhs;
+    const long off = ((long)rhs * Th + wq) * N;
+    const int r0 = g.row0();
+    CV cur[2];
+    float4 d[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const long e = off + (long)(r0 + r) * L + 4 * g.cx;
+        const float4 a = *reinterpret_cast<const float4*>(vin + e);
+        const float4 b = *reinterpret_cast<const float4*>(vin + e + 2);
+        cur[r].re = make_float4(a.x, a.z, b.x, b.z);
+        cur[r].im = make_float4(a.y, a.w, b.y, b.w);
+        const int i = (r0 + r) * L + 4 * g.cx;
+        d[r] = make_float4((float)dbar[i], (float)dbar[i + 1], (float)dbar[i + 2],
+                           (float)dbar[i + 3]);
+    }
+    const double bmin = scal[S_BMIN], bmax = scal[S_BMAX];
+    const double db = bmax - bmin;
+    const float a = (float)(2.0 / db), c0 = (float)(-2.0 * bmin / db - 1.0);
+    const int np = npv[wq];
+    const double2* cw = coef + (long)wq * max_np;
+    int par = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool trans = (pass == 0);
+        if (trans && !(mode & 1)) continue;
+        if (!trans && !(mode & 2)) continue;
+        const float sgn = trans ? -1.0f : 1.0f;    // conj coefficients for the transpose
+        CV acc[2], prev[2];
+        {
+            const double2 c = cw[0];
+            const float cr = (float)c.x, ci = sgn * (float)c.y;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                prev[r] = cur[r];
+                acc[r].re = make_float4(cr * cur[r].re.x - ci * cur[r].im.x, cr * cur[r].re.y - ci * cur[r].im.y,
+                                        cr * cur[r].re.z - ci * cur[r].im.z, cr * cur[r].re.w - ci * cur[r].im.w);
+                acc[r].im = make_float4(cr * cur[r].im.x + ci * cur[r].re.x, cr * cur[r].im.y + ci * cur[r].re.y,
+                                        cr * cur[r].im.z + ci * cur[r].re.z, cr * cur[r].im.w + ci * cur[r].re.w);
+            }
+        }
+        for (int m = 1; m < np; ++m) {
+            CV old[2], b[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                old[r] = cur[r];
+                b[r] = cur[r];
+                if (trans) {
+                    b[r].re.x *= d[r].x; b[r].re.y *= d[r].y; b[r].re.z *= d[r].z; b[r].re.w *= d[r].w;
+                    b[r].im.x *= d[r].x; b[r].im.y *= d[r].y; b[r].im.z *= d[r].z; b[r].im.w *= d[r].w;
+                }
+            }
+            if (trans) {
+                kc4<L>(b, g, th, xbuf, par);
+                kc3(b, th);
+                kc2<L>(b, g, th);
+                kc1(b, th);
+            } else {
+                kc1(b, th);
+                kc2<L>(b, g, th);
+                kc3(b, th);
+                kc4<L>(b, g, th, xbuf, par);
+            }
+            par ^= 1;
+            const double2 c = cw[m];
+            const float cr = (float)c.x, ci = sgn * (float)c.y;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (!trans) {
+                    b[r].re.x *= d[r].x; b[r].re.y *= d[r].y; b[r].re.z *= d[r].z; b[r].re.w *= d[r].w;
+                    b[r].im.x *= d[r].x; b[r].im.y *= d[r].y; b[r].im.z *= d[r].z; b[r].im.w *= d[r].w;
+                }
+                // alpha_m = (m == 1 ? 1 : 2) (a B + c0) alpha_{m-1} - (m == 1 ? 0 : alpha_{m-2})
+                const float f2 = (m == 1) ? 1.0f : 2.0f;
+                const float pm = (m == 1) ? 0.0f : 1.0f;
+                float* nre = &cur[r].re.x;
+                float* nim = &cur[r].im.x;
+                const float* bre = &b[r].re.x;
+                const float* bim = &b[r].im.x;
+                const float* ore = &old[r].re.x;
+                const float* oim = &old[r].im.x;
+                const float* pre = &prev[r].re.x;
+                const float* pim = &prev[r].im.x;
+                float* are = &acc[r].re.x;
+                float* aim = &acc[r].im.x;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float xr = f2 * fmaf(a, bre[e], c0 * ore[e]) - pm * pre[e];
+                    const float xi = f2 * fmaf(a, bim[e], c0 * oim[e]) - pm * pim[e];
+                    nre[e] = xr;
+                    nim[e] = xi;
+                    are[e] = fmaf(cr, xr, fmaf(-ci, xi, are[e]));
+                    aim[e] = fmaf(cr, xi, fmaf(ci, xr, aim[e]));
+                }
+                prev[r] = old[r];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) cur[r] = acc[r];
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const long e = off + (long)(r0 + r) * L + 4 * g.cx;
+        *reinterpret_cast<float4*>(vout + e) = make_float4(cur[r].re.x, cur[r].im.x, cur[r].re.y, cur[r].im.y);
+        *reinterpret_cast<float4*>(vout + e + 2) = make_float4(cur[r].re.z, cur[r].im.z, cur[r].re.w, cur[r].im.w);
+    }
+}
+
 // N_P(omega) and c_m(omega), m < N_P, one block per omega < T/2.
+// f(cos theta_n) is evaluated once per quadrature node into shared memory;
+// cos(m theta_n) follows from a rotation by m pi / N_Q per node, so the
+// coefficient sums cost FMAs only (FP64 throughput is scarce on this part).
 __global__ void k_kpm_coeffs(const double* __restrict__ scal, int T, int max_np,
                              int* __restrict__ npv, double2* __restrict__ coef,
                              int* __restrict__ clamped)
 {
+    extern __shared__ double2 fq[];              // [2 max_np]
     const int w = blockIdx.x;
     const double bmin = scal[S_BMIN], bmax = scal[S_BMAX];
     const double db = bmax - bmin;
     const double phi = 2.0 * M_PI / T * (w + 0.5);
-    double npd = floor(db * (1.0 / phi + 1.0));
-    int np = npd < 1.0 ? 1 : (npd > (double)max_np ? max_np : (int)npd);
+    const double npd = floor(db * (1.0 / phi + 1.0));
+    const int np = npd < 1.0 ? 1 : (npd > (double)max_np ? max_np : (int)npd);
     if (threadIdx.x == 0) {
         npv[w] = np;
         if (npd > (double)max_np) atomicExch(clamped, 1);
@@ -310,18 +563,27 @@ __global__ void k_kpm_coeffs(const double* __restrict__ scal, int T, int max_np,
     const int nq = 2 * np;
     double sp, cp;
     sincos(phi, &sp, &cp);
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        const double y = cospi((q + 0.5) / nq);
+        const double bb = bmin + (y + 1.0) * db * 0.5;
+        // f = 1 / (1 - e^{-i phi} bb) = 1 / ((1 - bb cos phi) + i bb sin phi)
+        const double re = 1.0 - bb * cp, im = bb * sp;
+        const double den = re * re + im * im;
+        fq[q] = make_double2(re / den, -im / den);
+    }
+    __syncthreads();
     for (int m = threadIdx.x; m < np; m += blockDim.x) {
+        double c, sn, cd, sd;
+        sincospi(0.5 * m / nq, &sn, &c);      // angle m theta_0
+        sincospi((double)m / nq, &sd, &cd);   // step m pi / N_Q
         double sr = 0.0, si = 0.0;
         for (int q = 0; q < nq; ++q) {
-            const double th = (q + 0.5) / nq;            // theta / pi
-            const double y = cospi(th);
-            const double bb = bmin + (y + 1.0) * db * 0.5;
-            // f = 1 / (1 - e^{-i phi} bb) = 1 / ((1 - bb cos phi) + i bb sin phi)
-            const double re = 1.0 - bb * cp, im = bb * sp;
-            const double den = re * re + im * im;
-            const double cm = cospi(m * th);
-            sr += cm * re / den;
-            si += cm * (-im) / den;
+            const double2 f = fq[q];
+            sr = fma(c, f.x, sr);
+            si = fma(c, f.y, si);
+            const double c2 = c * cd - sn * sd;
+            sn = fma(sn, cd, c * sd);
+            c = c2;
         }
         const double qm = (m == 0) ? 2.0 : 1.0;   // q_m / (pi/2)
         const double fac = 2.0 / (qm * nq);       // pi / (q_m N_Q)
@@ -381,14 +643,33 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     ka.Th = c->T / 2;
     ka.max_np = c->kpm.max_np;
     ka.mode = mode;
-    ka.ch = c->ch;
-    ka.sh = c->sh;
-    const int kt = kpm_threads(c);
-    const size_t ks = (size_t)c->N * sizeof(C2);
-    if ((rc = set_smem_attr<R>((const void*)k_kpm<R>, ks))) return rc;
-    k_kpm<R><<<ka.Th * n_rhs, kt, ks, s>>>(h0, h1, c->dbar, c->scal, c->kpm.np, c->kpm.coef,
-                                           n_rhs, ka);
-    HOL_CHECK_LAUNCH("k_kpm");
+    ka.th = c->th;
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+        if (c->kpm_reg && (c->L == 32 || c->L == 16)) {
+            const float th = (float)c->th;
+            const float2* i2 = reinterpret_cast<const float2*>(h0);
+            float2* o2 = reinterpret_cast<float2*>(h1);
+            if (c->L == 32)
+                k_kpm_reg<32><<<ka.Th * n_rhs, 128, 0, s>>>(i2, o2, c->dbar, c->scal, c->kpm.np,
+                                                             c->kpm.coef, n_rhs, ka.Th, ka.max_np,
+                                                             mode, th);
+            else
+                k_kpm_reg<16><<<ka.Th * n_rhs, 32, 0, s>>>(i2, o2, c->dbar, c->scal, c->kpm.np,
+                                                            c->kpm.coef, n_rhs, ka.Th, ka.max_np,
+                                                            mode, th);
+            HOL_CHECK_LAUNCH("k_kpm_reg");
+            done = true;
+        }
+    }
+    if (!done) {
+        const int kt = kpm_threads(c);
+        const size_t ks = (size_t)c->N * sizeof(C2);
+        if ((rc = set_smem_attr<R>((const void*)k_kpm<R>, ks))) return rc;
+        k_kpm<R><<<ka.Th * n_rhs, kt, ks, s>>>(h0, h1, c->dbar, c->scal, c->kpm.np, c->kpm.coef,
+                                               n_rhs, ka);
+        HOL_CHECK_LAUNCH("k_kpm");
+    }
     k_tau_inv<R><<<gf, 256, sm, s>>>(h1, out, w2, c->T, c->N, TS, plan, (R)2 * isq, rdot,
                                      dot_part);
     HOL_CHECK_LAUNCH("k_tau_inv");
@@ -445,8 +726,12 @@ int precond_alloc(hol_ctx* c)
 
 int kpm_setup(hol_ctx* c, cudaStream_t s)
 {
-    k_kpm_coeffs<<<c->T / 2, 128, 0, s>>>(c->scal, c->T, c->kpm.max_np, c->kpm.np, c->kpm.coef,
-                                          c->kpm.np + c->T / 2);
+    const size_t sm = 2 * (size_t)c->kpm.max_np * sizeof(double2);
+    if (sm > 48 * 1024)
+        HOL_CUDA(cudaFuncSetAttribute((const void*)k_kpm_coeffs,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_kpm_coeffs<<<c->T / 2, 128, sm, s>>>(c->scal, c->T, c->kpm.max_np, c->kpm.np, c->kpm.coef,
+                                           c->kpm.np + c->T / 2);
     HOL_CHECK_LAUNCH("k_kpm_coeffs");
     return HOL_OK;
 }

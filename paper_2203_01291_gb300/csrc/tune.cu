@@ -1,0 +1,85 @@
+// Launch-shape autotuner for the fused FP32 M^T M kernel of the CG iteration.
+//
+// Candidates: K (tau slices streamed per lane group) among the divisors
+// {1, 2, 4, 5, 8, 10} of Ltau, 1, 2 or 4 warps per block, and for L % 8 == 0
+// the float4 layout with cp.async prefetch (2), without (1), or the scalar
+// register layout (0). Each candidate is timed with CUDA
+// events on the caller's stream (2 warm-up and 10 timed launches on the
+// context's scratch vectors) and the fastest is kept in the context for every
+// later call. Candidates whose per-unit partial sums would not fit the
+// context's partial-sum bank are skipped.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+using namespace hol;
+
+extern "C" int hol_tune(hol_ctx* c, int n_rhs, int* best_k, int* best_warps, int* best_vec,
+                        double* best_ms, void* stream)
+{
+    if (!c) return set_error(HOL_EINVAL, "hol_tune: null context");
+    if (!c->field_set) return set_error(HOL_EINVAL, "hol_tune: hol_set_field not called");
+    if (n_rhs < 1 || n_rhs > c->p.max_rhs)
+        return set_error(HOL_EINVAL, "hol_tune: n_rhs=%d outside [1, %d]", n_rhs, c->p.max_rhs);
+    cudaStream_t s = (cudaStream_t)stream;
+    HOL_CUDA(cudaMemsetAsync(c->v32a, 0, (size_t)n_rhs * c->n * sizeof(float), s));
+    cudaEvent_t e0, e1;
+    HOL_CUDA(cudaEventCreate(&e0));
+    HOL_CUDA(cudaEventCreate(&e1));
+    const int ks[6] = {1, 2, 4, 5, 8, 10};
+    const int ws[3] = {1, 2, 4};
+    const int old_k = c->mv_k, old_w = c->mv_warps, old_v = c->mv_vec;
+    int bk = old_k, bw = old_w, bv = old_v;
+    double bms = 1e30;
+    int rc = HOL_OK;
+    for (int vec = (c->L % 8 == 0) ? 2 : 0; vec >= 0 && !rc; --vec) {
+        for (int ki = 0; ki < 6 && !rc; ++ki) {
+            const int k = ks[ki];
+            if (c->T % k) continue;
+            c->mv_k = k;
+            if ((long)matvec_pstride(c) * c->p.max_rhs > c->part_len) continue;
+            for (int wi = 0; wi < 3 && !rc; ++wi) {
+                c->mv_warps = ws[wi];
+                c->mv_vec = vec;
+                for (int r = 0; r < 2 && !rc; ++r)
+                    rc = launch_cg_mtm32(c, c->v32a, c->v32a, nullptr, c->v32b, n_rhs, nullptr,
+                                         nullptr, nullptr, 0, 0, 1, nullptr, s);
+                if (rc) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 10 && !rc; ++r)
+                    rc = launch_cg_mtm32(c, c->v32a, c->v32a, nullptr, c->v32b, n_rhs, nullptr,
+                                         nullptr, nullptr, 0, 0, 1, nullptr, s);
+                cudaEventRecord(e1, s);
+                if (rc) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = set_error(HOL_ECUDA, "hol_tune: event synchronise failed");
+                    break;
+                }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms / 10.0 < bms) {
+                    bms = ms / 10.0;
+                    bk = k;
+                    bw = ws[wi];
+                    bv = vec;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        c->mv_k = old_k;
+        c->mv_warps = old_w;
+        c->mv_vec = old_v;
+        return rc;
+    }
+    c->mv_k = bk;
+    c->mv_warps = bw;
+    c->mv_vec = bv;
+    if (best_k) *best_k = bk;
+    if (best_warps) *best_warps = bw;
+    if (best_vec) *best_vec = bv;
+    if (best_ms) *best_ms = bms;
+    return HOL_OK;
+}

@@ -1,0 +1,87 @@
+"""The differentiable fermionic action S_F(x) (torch.autograd.Function backed by
+the library's solve and force kernels). Marked gpu.
+
+* tiny workload: value and gradient against the dense oracle (Eqs. (S_F),
+  (dSF_dx)) to 1e-9 relative.
+* grad24 workload (L=24, Ltau=160): the FP64 gradient against central finite
+  differences (h = 1e-5) of the GPU S_F on 64 random components, and the
+  mixed-precision gradient (FP32 iterations, FP64 reliable updates, solve to
+  1e-10) against the FP64 one. Tolerances: FD error ~ eps_solve * S_F / h plus
+  O(h^2); with S_F ~ 5e4 and solves to 1e-13 the bound is ~5e-4 absolute,
+  but the two solves at x +- h share their iteration history and the
+  difference is far smaller; we assert 1e-6 of max|grad|. The mixed gradient
+  carries kappa * 1e-10 and is asserted to 1e-6 relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+import holstein_inputs as hi
+from oracle import dense as D
+
+pytestmark = pytest.mark.gpu
+
+hg = pytest.importorskip("paper_2203_01291_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    hg.build.build()
+    torch.cuda.set_device(0)
+
+
+DEV = "cuda"
+
+
+def test_fermion_action_and_gradient_vs_oracle_tiny():
+    from paper_2203_01291_gb300.autograd import fermion_action
+    w = hi.WORKLOADS["tiny"]
+    m = D.model_of(w)
+    x0 = hi.phonon_field(w)
+    Phi = hi.gaussian_vectors(w, 2, seed=12)
+    with hg.Context.from_workload(w, max_rhs=2) as ctx:
+        x = torch.tensor(x0, device=DEV, requires_grad=True)
+        S = fermion_action(x, torch.tensor(Phi, device=DEV), ctx, tol=1e-13)
+        S.backward()
+        assert abs(float(S.detach()) - D.S_F(m, x0, Phi)) < 1e-9 * abs(D.S_F(m, x0, Phi))
+        g = x.grad.cpu().numpy()
+        ref = D.dSF_dx(m, x0, Phi)
+        assert np.abs(g - ref).max() < 1e-9 * np.abs(ref).max()
+
+
+def test_grad24_finite_differences_and_mixed():
+    from paper_2203_01291_gb300.autograd import fermion_action
+    w = hi.WORKLOADS["grad24"]
+    x0 = hi.phonon_field(w)
+    rng = np.random.default_rng(24)
+    comps = [(int(rng.integers(w.Ltau)), int(rng.integers(w.N))) for _ in range(64)]
+    with hg.Context.from_workload(w, max_rhs=1) as ctx:
+        Rt = torch.tensor(hi.gaussian_vectors(w, 1, seed=25), device=DEV)
+        Phi = torch.empty_like(Rt)
+        ctx.set_field(torch.tensor(x0, device=DEV))
+        ctx.pseudofermion_phi(Rt, Phi)          # Phi = A^T(x0) R
+        x = torch.tensor(x0, device=DEV, requires_grad=True)
+        S = fermion_action(x, Phi, ctx, tol=1e-13)
+        # S_F(x0, A(x0)^T R) = |R|^2 / 2 (Sec. II D)
+        assert abs(float(S) - 0.5 * float((Rt * Rt).sum())) < 1e-9 * float(S)
+        S.backward()
+        g = x.grad.cpu().numpy()
+        h = 1e-5
+        fd = []
+        for (tau, i) in comps:
+            xp = torch.tensor(x0, device=DEV)
+            xp[tau, i] += h
+            sp = float(fermion_action(xp, Phi, ctx, tol=1e-13))
+            xp[tau, i] -= 2 * h
+            sm = float(fermion_action(xp, Phi, ctx, tol=1e-13))
+            fd.append((sp - sm) / (2 * h))
+        fd = np.array(fd)
+        gc = np.array([g[c] for c in comps])
+        assert np.abs(fd - gc).max() < 1e-6 * np.abs(g).max()
+        xm = torch.tensor(x0, device=DEV, requires_grad=True)
+        Sm = fermion_action(xm, Phi, ctx, tol=1e-10, prec=hg.HOL_F32)
+        Sm.backward()
+        gm = xm.grad.cpu().numpy()
+        assert np.abs(gm - g).max() < 1e-6 * np.abs(g).max()

@@ -199,6 +199,28 @@ def test_cg_zero_rhs_and_errors():
             ctx.cg_solve(bad, torch.empty_like(bad))  # n_rhs > max_rhs
 
 
+@pytest.mark.parametrize("L,T", [(32, 40), (12, 20)])
+def test_autotuner_choice_keeps_results(L, T):
+    """hol_tune picks a launch shape; the fused M^T M and a mixed solve stay
+    correct with it."""
+    w, x = _field(L, T, seed=17)
+    v = hi.gaussian_vectors(w, 3, seed=18)
+    ref = np.stack([MF.MTM_apply(w, x, a) for a in v])
+    with _ctx(w, 3) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        choice = ctx.tune(3)
+        assert T % choice["slices_per_group"] == 0 and choice["ms"] > 0
+        vt = torch.tensor(v, device=DEV, dtype=torch.float32)
+        out = torch.empty_like(vt)
+        ctx.fermion_matvec(hg.HOL_OP_MTM, vt, out)
+        assert _rel(out.cpu().double().numpy(), ref) < 3e-6
+        bt = torch.tensor(v, device=DEV)
+        sol = torch.empty_like(bt)
+        its, res = ctx.cg_solve(bt, sol, tol=1e-8, prec=hg.HOL_F32)
+        assert np.all(res < 1e-8)
+        assert max(MF.rel_residual(w, x, v[k], sol.cpu().numpy()[k]) for k in range(3)) < 1.01e-8
+
+
 def test_invalid_shapes_rejected():
     for L, T in ((3, 8), (34, 8), (8, 7), (2, 8)):
         with pytest.raises(hg.HolError):

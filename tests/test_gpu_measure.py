@@ -1,0 +1,90 @@
+"""GPU parity of the FFT-accelerated stochastic measurements (Sec. V) against
+the oracle's direct O(N^2) sums. Marked gpu.
+
+Tolerance 1e-10 of max|ref|: the probes are solved with FP64 CG to 1e-13
+(error ~ kappa * 1e-13 ~ 1e-10 relative at these sizes) and the FFT adds
+O(log n) epsilon.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+import torch
+
+import holstein_inputs as hi
+from oracle import dense as D
+
+pytestmark = pytest.mark.gpu
+
+hg = pytest.importorskip("paper_2203_01291_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    hg.build.build()
+    torch.cuda.set_device(0)
+
+
+DEV = "cuda"
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
+
+
+def _run(w, x, xi, four_point=0, max_rhs=4):
+    with hg.Context.from_workload(w, max_rhs=max_rhs) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        xt = torch.tensor(xi, device=DEV)
+        Gxi = torch.empty_like(xt)
+        G2 = torch.empty(2 * w.Ltau, w.L, w.L, dtype=torch.float64, device=DEV)
+        G4 = torch.empty(3, 2 * w.Ltau, w.L, w.L, dtype=torch.float64, device=DEV) \
+            if four_point else None
+        its = ctx.stochastic_measure(xt, Gxi, G2, G4, four_point, tol=1e-13)
+        torch.cuda.synchronize()
+        return (Gxi.cpu().numpy(), G2.cpu().numpy(),
+                None if G4 is None else G4.cpu().numpy(), its)
+
+
+@pytest.mark.parametrize("L,T,nrv", [(4, 8, 3), (6, 12, 5), (4, 10, 2)])
+def test_two_and_four_point_vs_direct_sums(L, T, nrv):
+    w = hi.Workload("g", L=L, Ltau=T, alpha=1.1, mu=0.0)
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    xi = hi.z2_vectors(w, nrv, seed=3)
+    Gxi, G2, G4, its = _run(w, x, xi, four_point=7)
+    G = D.green_matrix(m, x)
+    Gref = np.array([(G @ v.reshape(-1)).reshape(T, -1) for v in xi])
+    assert _rel(Gxi, Gref) < 1e-10
+    ref2 = D.green_average(m, x, xi)
+    assert _rel(G2, ref2) < 1e-10
+    ref4 = D.four_point_pairs(m, x, xi)
+    for k in range(3):
+        assert _rel(G4[k], ref4[k]) < 1e-10, k
+
+
+def test_complete_hadamard_probes_give_exact_average():
+    """The rows of a Hadamard matrix are +-1 vectors with sum_k h_k h_k^T = n I,
+    so the probe average equals the exact space-time average of G^ext."""
+    w = hi.Workload("h", L=4, Ltau=4, alpha=1.0)
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    H = scipy.linalg.hadamard(w.n).astype(float).reshape(w.n, w.Ltau, w.N)
+    _, G2, _, _ = _run(w, x, H, max_rhs=16)
+    assert _rel(G2, D.green_average_exact(m, x)) < 1e-10
+
+
+def test_chain_size_two_point_and_type2():
+    """An L=8, Ltau=20 chain-sized case with 12 probes (two solve batches),
+    the 2-point function and the type-2 Wick product."""
+    w = hi.Workload("c", L=8, Ltau=20, alpha=1.0)
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    xi = hi.z2_vectors(w, 12, seed=5)
+    Gxi, G2, G4, _ = _run(w, x, xi, four_point=2, max_rhs=8)
+    G = D.green_matrix(m, x)
+    Gref = np.array([(G @ v.reshape(-1)).reshape(w.Ltau, -1) for v in xi])
+    assert _rel(G2, D.green_average(m, x, xi, Gref)) < 1e-10
+    assert _rel(G4[1], D.four_point_pairs(m, x, xi, Gref)[1]) < 1e-10
+    assert float(np.abs(G4[0]).max()) == 0.0 and float(np.abs(G4[2]).max()) == 0.0

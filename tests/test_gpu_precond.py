@@ -42,7 +42,8 @@ def _setup(L, T, seed=3, std=1.0, alpha=1.0, nr=2):
     return w, x, ctx
 
 
-@pytest.mark.parametrize("L,T", [(4, 40), (6, 12), (8, 24), (12, 10), (4, 14), (8, 30)])
+@pytest.mark.parametrize("L,T", [(4, 40), (6, 12), (8, 24), (12, 10), (4, 14), (8, 30),
+                                 (16, 20), (32, 12), (16, 6)])
 def test_precond_apply_vs_oracle(L, T):
     w, x, ctx = _setup(L, T)
     m = D.model_of(w)
