@@ -43,6 +43,7 @@ METRIC = "CG solves/s (M^T M v = b, certified FP64 residual 1e-8) at L=32, Ltau=
 WORKLOAD = hi.WORKLOADS["big32"]
 TOL = 1e-8
 RELIABLE_EVERY = 50
+TIMER_STRIDE = 8          # CUDA events around one in every 8 launches of each kernel class
 
 
 def peaks():
@@ -62,6 +63,9 @@ def args_parse():
     ap.add_argument("--rhs", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--option", action="append", default=[],
+                    help="NAME=VALUE launch option applied after tuning (hol_set_option)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the trajectory and measurement legs")
     ap.add_argument("--field", choices=["iid", "ar1"], default="iid",
@@ -237,6 +241,11 @@ def run_ours(a):
         ctx.force(vd, bd, Fd, with_bosonic=True)
         return it, res
 
+    ctx.set_field(xd)
+    tuned = ctx.tune(nr) if not a.no_tune else None
+    for opt in a.option:
+        name, val = opt.split("=")
+        ctx.set_option(name, int(val))
     for _ in range(a.warmup):
         flush.zero_()
         step(xd, Rd)
@@ -245,7 +254,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     clocks = Clocks(torch.cuda.current_device())
     clocks.start()
-    ctx.timer_enable(True)
+    ctx.timer_enable(TIMER_STRIDE)
     l0 = hg.hol_launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -259,11 +268,15 @@ def run_ours(a):
     torch.cuda.synchronize()
     launches = hg.hol_launch_count() - l0
     ms_total = e0.elapsed_time(e1)
-    op_cnt, op_ms = ctx.timer_read(hg.TIMER_OPERATOR)
-    up_cnt, up_ms = ctx.timer_read(hg.TIMER_UPDATE)
-    fo_cnt, fo_ms = ctx.timer_read(hg.TIMER_FORCE)
-    pc_cnt, pc_ms = ctx.timer_read(hg.TIMER_PRECOND)
-    ctx.timer_enable(False)
+    op_cnt, op_ms, op_units = ctx.timer_read(hg.TIMER_OPERATOR)
+    up_cnt, up_ms, _ = ctx.timer_read(hg.TIMER_UPDATE)
+    fo_cnt, fo_ms, _ = ctx.timer_read(hg.TIMER_FORCE)
+    pc_cnt, pc_ms, _ = ctx.timer_read(hg.TIMER_PRECOND)
+    ctx_kernel_name = ("k_cg_persist (fused CG chunk: p = r + beta p, q = M^T M p in shared "
+                       "memory, e += alpha p, r -= alpha q; per iteration r, p, e read and "
+                       "written once)" if op_avg_ms_hint(op_ms, op_cnt, up_cnt)
+                       else "k_cg_mtm32* (fused p = r + beta p, q = M^T M p, |Mp|^2)")
+    ctx.timer_enable(0)
     clk = clocks.stop()
     barrier(world)
     ms_max = reduce_max(world, ms_total)
@@ -279,14 +292,15 @@ def run_ours(a):
     mv = float(np.sum(2 * iters + 1 + 2 * rel + 1))
     total_mv = reduce_sum(world, mv)
 
-    # roofline of the fused FP32 M^T M: per launch it reads r, p_old and expV
-    # and writes p_new and q for every active right-hand side. Launch times are
-    # CUDA events recorded by the library on the launching stream during the
-    # timed region (every recorded launch; the pool holds the first ones).
-    n = w.n
+    # roofline of the dominant kernel (the CG operator: the persistent fused
+    # CG chunk when the grid fits, else the fused M^T M). The library records
+    # CUDA events around one in every TIMER_STRIDE launches on the launching
+    # stream during the timed region, with each launch's algorithmic bytes
+    # (every array read once and written once: r, p, e, expV; the tau halo
+    # re-reads are not counted).
     op_avg_ms = op_ms / max(op_cnt, 1)
-    alg_bytes = float(nr * n * 4 * 4 + n * 4)   # all 16 rhs active (early iterations)
-    achieved = alg_bytes / (op_avg_ms / 1e3) / 1e9
+    alg_bytes = op_units / max(op_cnt, 1)
+    achieved = op_units / max(op_ms / 1e3, 1e-12) / 1e9
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
     traffic = None
@@ -368,6 +382,10 @@ def run_ours(a):
     if not a.no_extra:
         extra = {"trajectory": trajectory_leg(dev), "measurement": measurement_leg(dev)}
 
+    alu = {"fp64_fma_gflops": hg.hol_fma_peak(hg.HOL_F64),
+           "fp32_fma_gflops": hg.hol_fma_peak(hg.HOL_F32),
+           "how": "project FMA microbenchmark (hol_fma_peak), 2 flops per FMA"}
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = cpu_baseline_block()
@@ -377,7 +395,9 @@ def run_ours(a):
             "metric": METRIC, "value": value, "unit": "CG solves/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 operator+iterations, f64 dots/solution/reliable updates",
+            "dtype": "f32+f64",
+            "precision": "FP32 operator and CG iterations; FP64 dot products, solution and "
+                         "reliable updates; convergence certified by an FP64 true residual",
             "data": "synthetic (seeded i.i.d. Gaussian phonon field and pseudofermion draws)",
             "config": {"workload": "L=32 N=1024 Ltau=200 beta=20 dtau=0.1 t=1 mu=0 omega0=0.5 "
                                    "alpha=1 x~N(0,4), 16 rhs b=M^T R, mixed CG to 1e-8 "
@@ -387,14 +407,17 @@ def run_ours(a):
                        "per_rank": "independent replica, own seeds"},
             "matvecs_per_s": total_mv / (ms_max / 1e3),
             "mean_cg_iters": float(np.mean(iters)),
+            "tuned_launch": tuned,
+            "options": a.option,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
-                         "kernel": "k_cg_mtm32 (fused p=r+beta p, q=M^T M p, |Mp|^2)",
+                         "kernel": ctx_kernel_name,
                          "alg_bytes_per_launch": alg_bytes,
                          "avg_launch_ms": op_avg_ms, "launches": op_cnt,
                          "peak_src": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
             "kernel_ms": {"cg_operator": op_ms, "cg_update": up_ms, "force": fo_ms,
                           "precond": pc_ms, "timed_total": ms_total,
+                          "timer_stride": TIMER_STRIDE,
                           "recorded_launches": {"cg_operator": op_cnt, "cg_update": up_cnt,
                                                 "force": fo_cnt, "precond": pc_cnt}},
             "fp64_compare": fp64,
@@ -402,6 +425,7 @@ def run_ours(a):
             "other_solver": alt,
             "e2e": e2e,
             "other_rows": extra,
+            "alu_peaks": alu,
             "gpu_launches": int(launches),
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -475,6 +499,11 @@ def measurement_leg(dev, n_rv=128):
             "mean_cg_iters": float(np.mean(its))}
 
 
+def op_avg_ms_hint(op_ms, op_cnt, up_cnt):
+    """The persistent path records no separate update launches."""
+    return op_cnt > 0 and up_cnt == 0
+
+
 def run_matvec(a):
     """Fused FP32 M^T M alone on `rhs` right-hand sides, cold L2 per launch."""
     import torch
@@ -486,6 +515,7 @@ def run_matvec(a):
     nr = a.rhs
     ctx = hg.Context.from_workload(w, max_rhs=nr)
     ctx.set_field(torch.tensor(hi.phonon_field(w), device="cuda"))
+    tuned = ctx.tune(nr) if not a.no_tune else None
     v = torch.tensor(hi.gaussian_vectors(w, nr, seed=5), device="cuda", dtype=torch.float32)
     q = torch.empty_like(v)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -504,7 +534,7 @@ def run_matvec(a):
     ms = statistics.median(times)
     alg = nr * w.n * 4 * 2 + w.n * 4          # v in, q out, expV
     hbm = peaks().get("hbm_gbs", 6800.0)
-    print(json.dumps({"mode": "matvec", "rhs": nr, "median_ms": ms,
+    print(json.dumps({"mode": "matvec", "rhs": nr, "median_ms": ms, "tuned_launch": tuned,
                       "alg_bytes": alg, "achieved_gbs": alg / (ms / 1e3) / 1e9,
                       "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / hbm,
                       "matvecs_per_s": 2 * nr / (ms / 1e3)}))

@@ -257,6 +257,26 @@ int stochastic_measure(hol_ctx* ctx, const double* xi, int n_rv, const hol_cg_op
                        void* stream);
 
 /*
+ * Independent chains of possibly different lattice sizes, each with its own
+ * context (created by the caller), driven concurrently: a pool of n_threads
+ * host threads, each with its own CUDA stream, takes the chains in order.
+ * hmc_batch runs one fourier_accel_leapfrog (Algorithm 1) per chain with
+ * x[k], R_pf[k] ([n_pf][T_k][N_k]), R_p[k], the uniform u[k] (host array);
+ * accepted, dH (host arrays of n_chains, nullable) receive the results.
+ * measure_batch runs stochastic_measure per chain (field already set) with
+ * n_rv probes xi[k] into Gxi[k], G2[k] and, if G4 is not null, G4[k].
+ * Chains never share device buffers; the result of each chain is the same as
+ * a separate call. Returns the first failing chain's error. Synchronises all
+ * the streams it used.
+ */
+int hmc_batch(hol_ctx* const* ctxs, int n_chains, double* const* x, const double* const* R_pf,
+              const double* const* R_p, int n_pf, const hol_md_opts* opts, const double* u,
+              int* accepted, double* dH, int n_threads);
+int measure_batch(hol_ctx* const* ctxs, int n_chains, const double* const* xi, int n_rv,
+                  const hol_cg_opts* opts, double* const* Gxi, double* const* G2,
+                  double* const* G4, int four_point, int n_threads);
+
+/*
  * Allocation-free FP64 fermion operator (no counterpart in the paper).
  *
  * For callers that cannot call cudaMalloc: code whose device memory is owned
@@ -298,18 +318,36 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
              double* best_ms, void* stream);
 
 /*
+ * Runtime launch options of a context (no counterpart in the paper; results
+ * are the same up to rounding whichever is chosen):
+ *   "slices_per_group"  tau slices streamed per lane group (divides Ltau)
+ *   "warps_per_block"   1, 2 or 4 for the operator kernels
+ *   "layout"            0 scalar, 1 float4, 2 float4 with cp.async prefetch
+ *                       (1 and 2 need L % 8 == 0)
+ *   "kpm_registers"     register KPM kernel for FP32, L = 16 or 32 (0/1)
+ *   "persistent_cg"     plain mixed CG chunks in one cooperative launch (0/1)
+ * Returns HOL_EINVAL for an unknown name or a value out of range.
+ */
+int hol_set_option(hol_ctx* ctx, const char* name, int value);
+
+/*
  * Instrumentation (no counterpart in the paper; used by the benchmark).
  * hol_launch_count: number of kernels this library has launched in the
- * process so far. hol_timer_enable(ctx, 1) starts recording CUDA events
- * around every kernel of the classes below on the stream each call is given
- * (it resets the counts; 0 stops recording). hol_timer_read returns, for one
+ * process so far. hol_timer_enable(ctx, k) with k >= 1 starts recording CUDA
+ * events around one in every k kernel regions of each class below, on the
+ * stream each call is given (it resets the counts; 0 stops recording). hol_timer_read returns, for one
  * class, how many regions were recorded and their summed device time in ms
- * (it waits for the recorded events). Classes: 0 CG operator (fused M^T M),
+ * (it waits for the recorded events) and (nullable) the summed work units of
+ * those regions (for the CG classes: right-hand sides still iterating).
+ * Classes: 0 CG operator (fused M^T M),
  * 1 CG vector update, 2 force, 3 preconditioner, 4 other.
  */
 unsigned long long hol_launch_count(void);
+/* Measured FMA throughput of the current GPU in GFLOP/s (prec HOL_F64 or
+ * HOL_F32; 2 flops per FMA): the ALU roofline of the FP64 path. */
+int hol_fma_peak(int prec, double* gflops, void* stream);
 int hol_timer_enable(hol_ctx* ctx, int on);
-int hol_timer_read(hol_ctx* ctx, int klass, int* count, double* total_ms);
+int hol_timer_read(hol_ctx* ctx, int klass, int* count, double* total_ms, double* units);
 
 #ifdef __cplusplus
 }

@@ -32,6 +32,7 @@ __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F6
            "pseudofermion_phi", "phi_to_rhs", "hol_launch_count", "hol_timer_enable",
            "hol_timer_read", "fermion_matvec_static", "mass_apply", "md_integrate",
            "fourier_accel_leapfrog", "hol_md_opts", "stochastic_measure", "hol_tune",
+           "hmc_batch", "measure_batch", "hol_set_option", "hol_fma_peak",
            "library_path", "load"]
 
 
@@ -189,19 +190,67 @@ def hol_tune(handle, n_rhs: int) -> dict:
             "ms": ms.value}
 
 
+def _ptrs(ts, dtype=torch.float64):
+    arr = (ctypes.c_void_p * len(ts))()
+    for k, t in enumerate(ts):
+        arr[k] = _ptr(t, dtype, None, f"tensor {k}").value
+    return arr
+
+
+def hmc_batch(contexts, xs, R_pfs, R_ps, opts: hol_md_opts, us, n_threads: int = 8):
+    """Algorithm 1 once for every chain (own context, own stream), run
+    concurrently; returns (accepted[n], dH[n])."""
+    n = len(contexts)
+    hs = (ctypes.c_void_p * n)(*[c.handle.value for c in contexts])
+    n_pf = R_pfs[0].numel() // contexts[0].n
+    acc = (ctypes.c_int * n)()
+    dh = (ctypes.c_double * n)()
+    u = (ctypes.c_double * n)(*[float(v) for v in us])
+    torch.cuda.current_stream().synchronize()   # inputs were written on torch's stream
+    _check(load().hmc_batch(hs, n, _ptrs(xs), _ptrs(R_pfs), _ptrs(R_ps), n_pf,
+                            ctypes.byref(opts), u, acc, dh, int(n_threads)))
+    return np.array(acc[:], dtype=bool), np.array(dh[:])
+
+
+def measure_batch(contexts, xis, Gxis, G2s, opts: hol_cg_opts, G4s=None, four_point: int = 0,
+                  n_threads: int = 8) -> None:
+    n = len(contexts)
+    hs = (ctypes.c_void_p * n)(*[c.handle.value for c in contexts])
+    n_rv = xis[0].numel() // contexts[0].n
+    g4 = _ptrs(G4s) if G4s is not None else None
+    torch.cuda.current_stream().synchronize()
+    _check(load().measure_batch(hs, n, _ptrs(xis), n_rv, ctypes.byref(opts), _ptrs(Gxis),
+                                _ptrs(G2s), g4, int(four_point), int(n_threads)))
+
+
+def hol_set_option(handle, name: str, value: int) -> None:
+    _check(load().hol_set_option(handle, name.encode(), int(value)))
+
+
+def hol_fma_peak(prec: int) -> float:
+    """Measured FMA throughput (GFLOP/s) of the current GPU."""
+    g = ctypes.c_double()
+    _check(load().hol_fma_peak(int(prec), ctypes.byref(g), _stream()))
+    return g.value
+
+
 def hol_launch_count() -> int:
     return int(load().hol_launch_count())
 
 
-def hol_timer_enable(handle, on: bool) -> None:
-    _check(load().hol_timer_enable(handle, int(bool(on))))
+def hol_timer_enable(handle, stride: int) -> None:
+    """stride k >= 1: time one in every k kernel regions per class; 0: off."""
+    _check(load().hol_timer_enable(handle, int(stride)))
 
 
 def hol_timer_read(handle, klass: int):
+    """(recorded regions, their summed device ms, their summed work units)"""
     cnt = ctypes.c_int()
     ms = ctypes.c_double()
-    _check(load().hol_timer_read(handle, klass, ctypes.byref(cnt), ctypes.byref(ms)))
-    return cnt.value, ms.value
+    un = ctypes.c_double()
+    _check(load().hol_timer_read(handle, klass, ctypes.byref(cnt), ctypes.byref(ms),
+                                 ctypes.byref(un)))
+    return cnt.value, ms.value, un.value
 
 
 TIMER_OPERATOR, TIMER_UPDATE, TIMER_FORCE, TIMER_PRECOND, TIMER_OTHER = range(5)
@@ -300,12 +349,16 @@ class Context:
         return stochastic_measure(self._h, xi, self._nrhs(xi), opts, Gxi, G2, G4, four_point,
                                   self.n)
 
+    def set_option(self, name: str, value: int) -> None:
+        """Launch option (see include/holstein.h, hol_set_option)."""
+        hol_set_option(self._h, name, value)
+
     def tune(self, n_rhs: int) -> dict:
         """Pick the fastest launch shape of the fused M^T M for n_rhs (needs a field)."""
         return hol_tune(self._h, n_rhs)
 
-    def timer_enable(self, on: bool = True) -> None:
-        hol_timer_enable(self._h, on)
+    def timer_enable(self, stride: int = 1) -> None:
+        hol_timer_enable(self._h, int(stride))
 
     def timer_read(self, klass: int):
         return hol_timer_read(self._h, klass)

@@ -69,11 +69,19 @@ SIGNATURES = {
     "pseudofermion_phi": (_I, [_VP, _VP, _VP, _I, _VP]),
     "phi_to_rhs": (_I, [_VP, _VP, _VP, _I, _VP]),
     "fermion_matvec_static": (_I, [ctypes.POINTER(hol_params), _VP, _I, _VP, _VP, _I, _VP]),
+    "hmc_batch": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                       ctypes.POINTER(_VP), _I, ctypes.POINTER(hol_md_opts),
+                       ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D), _I]),
+    "measure_batch": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), _I,
+                           ctypes.POINTER(hol_cg_opts), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                           ctypes.POINTER(_VP), _I, _I]),
+    "hol_set_option": (_I, [_VP, ctypes.c_char_p, _I]),
     "hol_tune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                       ctypes.POINTER(_D), _VP]),
     "hol_launch_count": (ctypes.c_ulonglong, []),
+    "hol_fma_peak": (_I, [_I, ctypes.POINTER(_D), _VP]),
     "hol_timer_enable": (_I, [_VP, _I]),
-    "hol_timer_read": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "hol_timer_read": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
 }
 
 _lib = None

@@ -104,4 +104,20 @@ __device__ __forceinline__ double warp_sum_array(const double* __restrict__ a, i
     return warp_sum(s);
 }
 
+// Sum `acc` over the L lanes of each group and store it for valid units.
+template <int L>
+__device__ __forceinline__ void group_store_sum(double acc, bool valid, double* __restrict__ dst)
+{
+    __shared__ double red[32 * 8];   // up to 8 warps per block
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    red[w * 32 + lane] = valid ? acc : 0.0;
+    __syncwarp();
+    const LaneGeom<L> geo;
+    if (valid && geo.ix == 0) {
+        double s = 0.0;
+        for (int k = 0; k < L; ++k) s += red[w * 32 + geo.g * L + k];
+        *dst = s;
+    }
+}
+
 }  // namespace hol

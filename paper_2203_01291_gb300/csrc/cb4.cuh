@@ -143,4 +143,17 @@ __device__ __forceinline__ void c4_apply_t(float4 (&c)[L / 4], const Geom4<L>& g
     c4_colour1<L>(c, th);
 }
 
+__device__ __forceinline__ float4 ld4(const float* __restrict__ p, long o)
+{
+    return *reinterpret_cast<const float4*>(p + o);
+}
+__device__ __forceinline__ void st4(float* __restrict__ p, long o, const float4& v)
+{
+    *reinterpret_cast<float4*>(p + o) = v;
+}
+__device__ __forceinline__ float4 fma4s(float a, const float4& x, const float4& y)
+{
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
 }  // namespace hol

@@ -87,18 +87,15 @@ __global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restr
 {
     const int rhs = blockIdx.y;
     if (mask != nullptr && mask[rhs] == 0) return;
-    __shared__ double s_alpha;
-    if (threadIdx.x < 32) {
-        const double pq = warp_sum_array(pq_part + (long)rhs * pq_stride, pq_n);
-        const double dz = warp_sum_array(dz_part + (long)rhs * kRedStride, dz_n);
-        if (threadIdx.x == 0) s_alpha = dz / pq;
-    }
-    __syncthreads();
-    const R a = (R)s_alpha;
+    // every warp forms alpha itself (same partials, same order, same bits),
+    // so no barrier sits before the streaming loop
+    const double pq = warp_sum_array(pq_part + (long)rhs * pq_stride, pq_n);
+    const double dz = warp_sum_array(dz_part + (long)rhs * kRedStride, dz_n);
+    const R a = (R)(dz / pq);
     const long base = (long)rhs * n;
+    const long stride = (long)gridDim.x * blockDim.x;
     double acc = 0.0;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n;
-         k += (long)gridDim.x * blockDim.x) {
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n; k += stride) {
         const long o = base + 4 * k;
         V4<R> xv, rv, pv, qv;
         xv.ld(x + o);
@@ -280,7 +277,7 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
 
     // z = P^{-1} P^{-T} r for every rhs, with the r.z partials in dz[bank]
     auto apply_prec = [&](int bank) -> int {
-        timer_start(c, KT_PRECOND, s);
+        timer_start(c, KT_PRECOND, s, (double)n_rhs);
         const int r2 = mixed ? precond_apply_impl(c, HOL_F32, r32, z32, n_rhs, 3, r32, B.dz[bank], s)
                              : precond_apply_impl(c, HOL_F64, r64, z64, n_rhs, 3, r64, B.dz[bank], s);
         timer_stop(c, KT_PRECOND, s);
@@ -319,25 +316,49 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
     int k_it = 0;
     const int chk = o->check_every > 0 ? o->check_every : 10;
     const int rel_every = (mixed && o->reliable_every > 0) ? o->reliable_every : 1 << 30;
+    // valid partial sums in each r.z bank (the fused persistent chunk writes
+    // one per unit, the element-wise kernels one per block)
+    int cnt[2] = {nb2, nb2};
+    const double nd = (double)n;
+    // the plain mixed solve runs whole chunks in one cooperative launch when
+    // the grid can be resident (persist.cu)
+    const bool persistent =
+        mixed && !pc && c->persist &&
+        launch_cg_persist(c, r32, p32[0], p32[1], e32, n_rhs, act_d, B.pq, B.dz[0], B.dz[1], 0,
+                          nb2, nb2, 0, 1, 1, 1, s) == HOL_OK;
+    const int nrun = c->T / c->mv_k;
     while (n_active > 0 && k_it < o->max_iter) {
         int chunk = chk;
         if (chunk > o->max_iter - k_it) chunk = o->max_iter - k_it;
-        for (int j = 0; j < chunk; ++j) {
+        if (persistent) {
+            timer_start(c, KT_OPERATOR, s, (double)chunk * (n_active * nd * 24.0 + nd * 4.0));
+            rc = launch_cg_persist(c, r32, p32[0], p32[1], e32, n_rhs, act_d, B.pq, B.dz[0],
+                                   B.dz[1], cur, cnt[cur], cnt[1 - cur], pp, first, chunk, 0, s);
+            if (rc) return rc;
+            timer_stop(c, KT_OPERATOR, s);
+            for (int j = 0; j < chunk; ++j) {
+                cnt[1 - cur] = nrun;
+                cur = 1 - cur;
+                pp = 1 - pp;
+            }
+            first = 0;
+        }
+        for (int j = 0; j < chunk && !persistent; ++j) {
             double* rr_dst = pc ? B.er : B.dz[1 - cur];
             if (mixed) {
                 // on the first step beta = 0 and p_old is not yet defined: pass z
-                timer_start(c, KT_OPERATOR, s);
+                timer_start(c, KT_OPERATOR, s, n_active * nd * 16.0 + nd * 4.0);
                 rc = launch_cg_mtm32(c, z32, first ? z32 : p32[pp], p32[1 - pp], q32, n_rhs, act_d,
                                      B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first, B.pq, s);
                 if (rc) return rc;
                 timer_stop(c, KT_OPERATOR, s);
                 pp = 1 - pp;
-                timer_start(c, KT_UPDATE, s);
+                timer_start(c, KT_UPDATE, s, n_active * nd * 24.0);
                 k_cg_update<float><<<g2, 256, 0, s>>>(e32, r32, p32[pp], q32, n, act_d, B.pq,
                                                       pstride, pq_n, B.dz[cur], dz_n, rr_dst);
             } else {
                 BetaSrc bs{B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first};
-                timer_start(c, KT_OPERATOR, s);
+                timer_start(c, KT_OPERATOR, s, n_active * nd * 48.0 + nd * 16.0);
                 rc = launch_M_upd64(c, z64, first ? z64 : p64[pp], p64[1 - pp], w64, n_rhs, act_d,
                                     bs, B.pq, s);
                 if (rc) return rc;
@@ -345,7 +366,7 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                 if (rc) return rc;
                 timer_stop(c, KT_OPERATOR, s);
                 pp = 1 - pp;
-                timer_start(c, KT_UPDATE, s);
+                timer_start(c, KT_UPDATE, s, n_active * nd * 48.0);
                 k_cg_update<double><<<g2, 256, 0, s>>>(v, r64, p64[pp], q64, n, act_d, B.pq,
                                                        pstride, pq_n, B.dz[cur], dz_n, rr_dst);
             }
@@ -356,7 +377,7 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
             first = 0;
         }
         k_it += chunk;
-        if ((rc = rows_to_host(c, est_bank(cur), nb2, n_rhs, hb, s))) return rc;
+        if ((rc = rows_to_host(c, est_bank(cur), pc ? nb2 : cnt[cur], n_rhs, hb, s))) return rc;
         int n_rel = 0;
         for (int k = 0; k < n_rhs; ++k) {
             rel_h[k] = 0;
@@ -387,6 +408,7 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
             k_recast<double><<<g2, 256, 0, s>>>(r64, r64, n, rel_d, B.tr, est_bank(cur));
         }
         HOL_CHECK_LAUNCH("k_recast");
+        if (!pc) cnt[cur] = nb2;   // k_recast wrote block partials into the current bank
         // the new r changes r.z: recompute z (all rhs; the unchanged ones get
         // the same z again)
         if (pc && (rc = apply_prec(cur))) return rc;

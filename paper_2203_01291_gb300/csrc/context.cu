@@ -15,21 +15,28 @@ static unsigned long long g_launches = 0;
 
 void count_launch() { __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED); }
 
-void timer_start(const hol_ctx* c, int k, cudaStream_t s)
+// A region is recorded when its running index is a multiple of the stride;
+// timer_stop pairs with the timer_start of the same region.
+void timer_start(const hol_ctx* c, int k, cudaStream_t s, double units)
 {
     KTimer* t = c->timer;
     if (!t || !t->on) return;
+    if (t->seen[k] % t->on != 0) return;
     if (t->used[k] >= t->cap) {
         t->dropped[k]++;
         return;
     }
     cudaEventRecord(t->ev[k][2 * t->used[k]], s);
+    t->units[k] += units;
 }
 
 void timer_stop(const hol_ctx* c, int k, cudaStream_t s)
 {
     KTimer* t = c->timer;
-    if (!t || !t->on || t->used[k] >= t->cap) return;
+    if (!t || !t->on) return;
+    const int rec = (t->seen[k] % t->on == 0);
+    t->seen[k]++;
+    if (!rec || t->used[k] >= t->cap) return;
     cudaEventRecord(t->ev[k][2 * t->used[k] + 1], s);
     t->used[k]++;
 }
@@ -179,6 +186,7 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     c->mv_warps = 4;
     c->mv_vec = 1;
     c->kpm_reg = 1;
+    c->persist = 0;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         free_ctx(c);
         return set_error(HOL_ECUDA, "hol_create: no CUDA device");
@@ -325,19 +333,25 @@ extern "C" int hol_timer_enable(hol_ctx* c, int on)
         c->timer = t;
     }
     if (c->timer) {
-        c->timer->on = on ? 1 : 0;
+        c->timer->on = on > 0 ? on : 0;
         if (on)
-            for (int k = 0; k < KT_COUNT; ++k) c->timer->used[k] = c->timer->dropped[k] = 0;
+            for (int k = 0; k < KT_COUNT; ++k)
+            {
+                c->timer->used[k] = c->timer->dropped[k] = c->timer->seen[k] = 0;
+                c->timer->units[k] = 0.0;
+            }
     }
     return HOL_OK;
 }
 
-extern "C" int hol_timer_read(hol_ctx* c, int klass, int* count, double* total_ms)
+extern "C" int hol_timer_read(hol_ctx* c, int klass, int* count, double* total_ms,
+                              double* units)
 {
     if (!c || !count || !total_ms || klass < 0 || klass >= KT_COUNT)
         return set_error(HOL_EINVAL, "hol_timer_read: bad argument");
     *count = 0;
     *total_ms = 0.0;
+    if (units) *units = 0.0;
     KTimer* t = c->timer;
     if (!t) return HOL_OK;
     double tot = 0.0;
@@ -349,5 +363,37 @@ extern "C" int hol_timer_read(hol_ctx* c, int klass, int* count, double* total_m
     }
     *count = t->used[klass];
     *total_ms = tot;
+    if (units) *units = t->units[klass];
+    return HOL_OK;
+}
+
+extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
+{
+    if (!c || !name) return set_error(HOL_EINVAL, "hol_set_option: null argument");
+    auto is = [&](const char* s) { return strcmp(name, s) == 0; };
+    if (is("slices_per_group")) {
+        if (value < 1 || c->T % value)
+            return set_error(HOL_EINVAL, "hol_set_option: slices_per_group must divide Ltau");
+        const int old = c->mv_k;
+        c->mv_k = value;
+        if ((long)matvec_pstride(c) * c->p.max_rhs > c->part_len) {
+            c->mv_k = old;
+            return set_error(HOL_EINVAL, "hol_set_option: slices_per_group too small");
+        }
+    } else if (is("warps_per_block")) {
+        if (value != 1 && value != 2 && value != 4)
+            return set_error(HOL_EINVAL, "hol_set_option: warps_per_block must be 1, 2 or 4");
+        c->mv_warps = value;
+    } else if (is("layout")) {
+        if (value < 0 || value > 2 || (value > 0 && c->L % 8))
+            return set_error(HOL_EINVAL, "hol_set_option: layout 0..2 (1, 2 need L % 8 == 0)");
+        c->mv_vec = value;
+    } else if (is("kpm_registers")) {
+        c->kpm_reg = value ? 1 : 0;
+    } else if (is("persistent_cg")) {
+        c->persist = value ? 1 : 0;
+    } else {
+        return set_error(HOL_EINVAL, "hol_set_option: unknown option '%s'", name);
+    }
     return HOL_OK;
 }

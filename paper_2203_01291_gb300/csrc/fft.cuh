@@ -43,15 +43,38 @@ struct RadixPlan {
     int r[16];
 };
 
-// twiddle w2[k] = exp(-i pi k / T), k < 2T
+// twiddle w2[k] = exp(-i pi k / T), 0 <= k < 2T (every caller's index is in
+// range: 2 r k T / (Ns RAD) < 2T and 2 e T / RAD < 2T)
 template <typename R>
 __device__ __forceinline__ typename Cx<R>::T2 tw(const typename Cx<R>::T2* __restrict__ w2, long k,
                                                  int T)
 {
-    return w2[k % (2 * T)];
+    (void)T;
+    return w2[k];
+}
+
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b)
+{
+    a.x -= b.x;
+    a.y -= b.y;
+    return a;
+}
+// multiply by -i
+template <typename C>
+__device__ __forceinline__ C cmi(C a)
+{
+    C r;
+    r.x = a.y;
+    r.y = -a.x;
+    return r;
 }
 
 // One Stockham pass of radix RAD over TS columns: in[tau][c] -> out[.][c].
+// Butterfly j (0 <= j < T/RAD) with k = j mod Ns reads in[j + r T/RAD],
+// scales input r by exp(-2 pi i r k / (Ns RAD)), takes the length-RAD DFT
+// and writes out[(j / Ns) Ns RAD + k + q Ns]. blockDim.x must be a multiple
+// of TS; (k, j / Ns) are advanced incrementally instead of divided.
 template <typename R, int RAD>
 __device__ void stockham_pass(const typename Cx<R>::T2* __restrict__ in,
                               typename Cx<R>::T2* __restrict__ out,
@@ -59,30 +82,55 @@ __device__ void stockham_pass(const typename Cx<R>::T2* __restrict__ in,
 {
     using C2 = typename Cx<R>::T2;
     const int nb = T / RAD;
-    for (int item = threadIdx.x; item < nb * TS; item += blockDim.x) {
-        const int c = item % TS, j = item / TS;
-        const int k = j % Ns;
+    const int c = threadIdx.x % TS;
+    const int sj = blockDim.x / TS;         // step of j per iteration
+    int j = threadIdx.x / TS;
+    int k = j % Ns, jb = j / Ns;
+    const int sk = sj % Ns, sjb = sj / Ns;
+    const int tstep = T / (Ns * RAD);       // twiddle index step per unit of k, halved
+    C2 root[RAD];                           // exp(-2 pi i e / RAD)
+#pragma unroll
+    for (int e = 0; e < RAD; ++e) root[e] = w2[2L * e * (T / RAD)];
+    for (; j < nb; j += sj) {
         C2 a[RAD];
-#pragma unroll
-        for (int r = 0; r < RAD; ++r) {
-            C2 v = in[(j + r * nb) * TS + c];
-            if (r > 0 && k > 0) {
-                // exp(-2 pi i r k / (Ns RAD)) = w2[2 r k T / (Ns RAD)]
-                v = cmul(v, tw<R>(w2, 2L * r * k * (T / (Ns * RAD)), T));
-            }
-            a[r] = v;
-        }
-        const int ob = (j / Ns) * Ns * RAD + k;
-#pragma unroll
-        for (int q = 0; q < RAD; ++q) {
-            C2 s = a[0];
+        a[0] = in[j * TS + c];
+        if (k > 0) {
+            const C2 w1 = w2[2L * k * tstep];
+            C2 wr = w1;
 #pragma unroll
             for (int r = 1; r < RAD; ++r) {
-                // exp(-2 pi i r q / RAD) = w2[2 (r q mod RAD) T / RAD]
-                const int e = (r * q) % RAD;
-                s = e == 0 ? cadd(s, a[r]) : cadd(s, cmul(a[r], tw<R>(w2, 2L * e * (T / RAD), T)));
+                a[r] = cmul(in[(j + r * nb) * TS + c], wr);
+                if (r + 1 < RAD) wr = cmul(wr, w1);
             }
-            out[(ob + q * Ns) * TS + c] = s;
+        } else {
+#pragma unroll
+            for (int r = 1; r < RAD; ++r) a[r] = in[(j + r * nb) * TS + c];
+        }
+        const int ob = jb * Ns * RAD + k;
+        if (RAD == 2) {
+            out[ob * TS + c] = cadd(a[0], a[1]);
+            out[(ob + Ns) * TS + c] = csub(a[0], a[1]);
+        } else if (RAD == 4) {
+            const C2 s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
+            const C2 s13 = cadd(a[1], a[3]), d13 = cmi(csub(a[1], a[3]));
+            out[ob * TS + c] = cadd(s02, s13);
+            out[(ob + Ns) * TS + c] = cadd(d02, d13);
+            out[(ob + 2 * Ns) * TS + c] = csub(s02, s13);
+            out[(ob + 3 * Ns) * TS + c] = csub(d02, d13);
+        } else {
+#pragma unroll
+            for (int q = 0; q < RAD; ++q) {
+                C2 s = a[0];
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) s = cadd(s, cmul(a[r], root[(r * q) % RAD]));
+                out[(ob + q * Ns) * TS + c] = s;
+            }
+        }
+        k += sk;
+        jb += sjb;
+        if (k >= Ns) {
+            k -= Ns;
+            jb += 1;
         }
     }
 }

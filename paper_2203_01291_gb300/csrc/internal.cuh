@@ -35,7 +35,9 @@ void count_launch();
 enum TimerClass { KT_OPERATOR = 0, KT_UPDATE = 1, KT_FORCE = 2, KT_PRECOND = 3, KT_OTHER = 4,
                   KT_COUNT = 5 };
 struct KTimer {
-    int on;
+    int on;                        // record one region in every `on` (0: off)
+    int seen[KT_COUNT];            // regions seen per class since enabling
+    double units[KT_COUNT];        // summed work units of the recorded regions
     int cap;                       // event pairs per class
     int used[KT_COUNT];
     int dropped[KT_COUNT];
@@ -43,7 +45,7 @@ struct KTimer {
 };
 // Record the start / stop of a timed region of class k on stream s (no-op
 // when timing is off or the pool is full).
-void timer_start(const hol_ctx* c, int k, cudaStream_t s);
+void timer_start(const hol_ctx* c, int k, cudaStream_t s, double units = 0.0);
 void timer_stop(const hol_ctx* c, int k, cudaStream_t s);
 
 // Largest supported lattice side (one lane per column, L values per lane).
@@ -130,6 +132,7 @@ struct hol_ctx {
     int mv_warps;        // warps per block in the matvec kernels
     int mv_vec;          // use the float4 layout of the fused FP32 M^T M (L % 8 == 0)
     int kpm_reg;         // use the register KPM kernel (FP32, L = 16 or 32)
+    int persist;         // use the persistent fused CG kernel when it fits
 };
 
 namespace hol {
@@ -167,6 +170,11 @@ int launch_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* 
                     float* q, int n_rhs, const int* mask, const double* rr_new,
                     const double* rr_old, int rr_stride, int rr_n, int first,
                     double* pq_part, cudaStream_t s);
+// Persistent fused CG chunk (persist.cu); HOL_EINVAL without launching when
+// unsupported (L % 8 != 0) or when the cooperative grid cannot be resident.
+int launch_cg_persist(const hol_ctx* c, float* r, float* p0, float* p1, float* e, int n_rhs,
+                      const int* mask, double* pq, double* rr0, double* rr1, int cur, int cnt_cur,
+                      int cnt_old, int pp, int first, int nit, int check_only, cudaStream_t s);
 int matvec_pstride(const hol_ctx* c);          // per-rhs stride of unit partials
 int matvec_units(const hol_ctx* c, int n_rhs); // upper bound of units per call
 

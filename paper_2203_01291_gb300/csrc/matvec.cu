@@ -38,22 +38,6 @@ __host__ MvGeom make_geom(const hol_ctx* c, int n_rhs)
     return g;
 }
 
-// Sum `acc` over the L lanes of each group and store it for valid units.
-template <int L>
-__device__ __forceinline__ void group_store_sum(double acc, bool valid, double* __restrict__ dst)
-{
-    __shared__ double red[32 * 8];   // up to 8 warps per block
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    red[w * 32 + lane] = valid ? acc : 0.0;
-    __syncwarp();
-    const LaneGeom<L> geo;
-    if (valid && geo.ix == 0) {
-        double s = 0.0;
-        for (int k = 0; k < L; ++k) s += red[w * 32 + geo.g * L + k];
-        *dst = s;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // out = M v. With UPD the loaded vector is p_new = r + beta p_old (the CG
 // direction update), whose own slices are also stored to pnew.
@@ -262,17 +246,16 @@ __global__ void __launch_bounds__(128) k_cg_mtm32(const float* __restrict__ r,
 // ---------------------------------------------------------------------------
 // Same fused FP32 CG step in the float4 layout of cb4.cuh (L % 8 == 0).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float4 ld4(const float* __restrict__ p, long o)
+// Ask L2 to fetch the 128-byte line of a slice that this lane covers
+// (32 lanes x 128 B = one 4 KB slice; smaller slices are covered by fewer
+// lanes), so that the later float4 loads of the slice hit L2.
+template <int L>
+__device__ __forceinline__ void prefetch_slice_l2(const float* base)
 {
-    return *reinterpret_cast<const float4*>(p + o);
-}
-__device__ __forceinline__ void st4(float* __restrict__ p, long o, const float4& v)
-{
-    *reinterpret_cast<float4*>(p + o) = v;
-}
-__device__ __forceinline__ float4 fma4s(float a, const float4& x, const float4& y)
-{
-    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+    constexpr int lines = (L * L * 4 + 127) / 128;
+    const int lane = threadIdx.x & 31;
+    for (int l = lane; l < lines; l += 32)
+        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(base + l * 32));
 }
 
 template <int L>
@@ -306,6 +289,15 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
         bt = (float)(rn / ro);
     }
 
+    // the unit's later slices t0+1 .. t0+K go to L2 while the first ones compute
+    if (geo.g == 0 || Geom4<L>::G == 1) {
+        for (int s = 1; s <= gm.K; ++s) {
+            int tq = t0 + s;
+            if (tq >= gm.T) tq -= gm.T;
+            prefetch_slice_l2<L>(r + base + (long)tq * N);
+            if (!first) prefetch_slice_l2<L>(pold + base + (long)tq * N);
+        }
+    }
     float4 W[RT], X[RT], P[RT], Y[RT];
     {
         const int tm = (t0 == 0) ? gm.T - 1 : t0 - 1;

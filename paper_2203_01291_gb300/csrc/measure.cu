@@ -225,6 +225,7 @@ struct Meas {
     hol_ctx* c;
     RadixPlan pt, ps;
     size_t sm_t, sm_s;
+    int ts_threads;   // threads of the spatial FFT: a multiple of L
     cudaStream_t s;
 
     int attrs()
@@ -243,7 +244,7 @@ struct Meas {
         const dim3 g(ceil_div(c->N, kMeasTS), nv);
         k_m_tau_fwd<<<g, 256, sm_t, s>>>(in, out, c->tw64, c->T, c->N, kMeasTS, pt, twist, nw);
         HOL_CHECK_LAUNCH("k_m_tau_fwd");
-        k_m_space<<<nv * nw, 256, sm_s, s>>>(out, c->twL64, c->L, ps, 0, 1.0);
+        k_m_space<<<nv * nw, ts_threads, sm_s, s>>>(out, c->twL64, c->L, ps, 0, 1.0);
         HOL_CHECK_LAUNCH("k_m_space");
         return HOL_OK;
     }
@@ -290,6 +291,7 @@ extern "C" int stochastic_measure(hol_ctx* c, const double* xi, int n_rv, const 
                          c->L, c->T);
     m.sm_t = 2 * (size_t)c->T * kMeasTS * sizeof(double2);
     m.sm_s = 2 * (size_t)c->N * sizeof(double2);
+    m.ts_threads = c->L * (256 / c->L);
     int rc = m.attrs();
     if (rc) return rc;
     cudaStream_t s = m.s;
@@ -329,7 +331,7 @@ extern "C" int stochastic_measure(hol_ctx* c, const double* xi, int n_rv, const 
             k_m_accum<<<g1((long)Th * N), 256, 0, s>>>(S2, A, B, nv, (long)Th * N);
             HOL_CHECK_LAUNCH("k_m_accum");
         }
-        k_m_space<<<Th, 256, m.sm_s, s>>>(S2, c->twL64, c->L, m.ps, 1, 1.0);
+        k_m_space<<<Th, m.ts_threads, m.sm_s, s>>>(S2, c->twL64, c->L, m.ps, 1, 1.0);
         HOL_CHECK_LAUNCH("k_m_space inv");
         double* tmp = c->v64a;
         const double sc = 2.0 / ((double)N * T * (double)N * T * n_rv);
@@ -390,7 +392,7 @@ extern "C" int stochastic_measure(hol_ctx* c, const double* xi, int n_rv, const 
             HOL_CUDA(cudaMemsetAsync(out, 0, 2 * n * sizeof(double), s));
             continue;
         }
-        k_m_space<<<T, 256, m.sm_s, s>>>(W + (long)k * n, c->twL64, c->L, m.ps, 1, 1.0);
+        k_m_space<<<T, m.ts_threads, m.sm_s, s>>>(W + (long)k * n, c->twL64, c->L, m.ps, 1, 1.0);
         HOL_CHECK_LAUNCH("k_m_space inv");
         double* tmp = c->v64a;
         k_m_tau_inv_full<<<ceil_div(N, kMeasTS), 256, m.sm_t, s>>>(W + (long)k * n, tmp, c->tw64, T,

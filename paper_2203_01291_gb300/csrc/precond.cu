@@ -286,7 +286,10 @@ __global__ void __launch_bounds__(256) k_kpm(const typename Cx<R>::T2* __restric
     const double db = bmax - bmin;
     const double a = 2.0 / db, c0 = -2.0 * bmin / db - 1.0;
     const int np = npv[w];
-    const double2* cw = coef + (long)w * ka.max_np;
+    // this omega's coefficients in shared memory (read once per Chebyshev step)
+    double2* cw = reinterpret_cast<double2*>(cur + N);
+    for (int m = threadIdx.x; m < np; m += blockDim.x) cw[m] = coef[(long)w * ka.max_np + m];
+    __syncthreads();
     if (ka.mode & 1) kpm_series<R>(cur, dbar, cw, np, true, true, a, c0, ka);
     if (ka.mode & 2) kpm_series<R>(cur, dbar, cw, np, false, false, a, c0, ka);
     for (int i = threadIdx.x; i < N; i += blockDim.x) vout[off + i] = cur[i];
@@ -454,7 +457,9 @@ __global__ void __launch_bounds__(32 * (L / (2 * (32 / (L / 4)))))
     const double db = bmax - bmin;
     const float a = (float)(2.0 / db), c0 = (float)(-2.0 * bmin / db - 1.0);
     const int np = npv[wq];
-    const double2* cw = coef + (long)wq * max_np;
+    extern __shared__ double2 cw[];   // this omega's coefficients
+    for (int m = threadIdx.x; m < np; m += blockDim.x) cw[m] = coef[(long)wq * max_np + m];
+    __syncthreads();
     int par = 0;
     for (int pass = 0; pass < 2; ++pass) {
         const bool trans = (pass == 0);
@@ -648,14 +653,20 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     if constexpr (sizeof(R) == 4) {
         if (c->kpm_reg && (c->L == 32 || c->L == 16)) {
             const float th = (float)c->th;
+            const size_t csm = (size_t)ka.max_np * sizeof(double2);
+            if (c->L == 32) {
+                if ((rc = set_smem_attr<R>((const void*)k_kpm_reg<32>, csm))) return rc;
+            } else if ((rc = set_smem_attr<R>((const void*)k_kpm_reg<16>, csm))) {
+                return rc;
+            }
             const float2* i2 = reinterpret_cast<const float2*>(h0);
             float2* o2 = reinterpret_cast<float2*>(h1);
             if (c->L == 32)
-                k_kpm_reg<32><<<ka.Th * n_rhs, 128, 0, s>>>(i2, o2, c->dbar, c->scal, c->kpm.np,
+                k_kpm_reg<32><<<ka.Th * n_rhs, 128, csm, s>>>(i2, o2, c->dbar, c->scal, c->kpm.np,
                                                              c->kpm.coef, n_rhs, ka.Th, ka.max_np,
                                                              mode, th);
             else
-                k_kpm_reg<16><<<ka.Th * n_rhs, 32, 0, s>>>(i2, o2, c->dbar, c->scal, c->kpm.np,
+                k_kpm_reg<16><<<ka.Th * n_rhs, 32, csm, s>>>(i2, o2, c->dbar, c->scal, c->kpm.np,
                                                             c->kpm.coef, n_rhs, ka.Th, ka.max_np,
                                                             mode, th);
             HOL_CHECK_LAUNCH("k_kpm_reg");
@@ -664,7 +675,7 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     }
     if (!done) {
         const int kt = kpm_threads(c);
-        const size_t ks = (size_t)c->N * sizeof(C2);
+        const size_t ks = ((size_t)c->N * sizeof(C2) + 15) / 16 * 16 + (size_t)ka.max_np * sizeof(double2);
         if ((rc = set_smem_attr<R>((const void*)k_kpm<R>, ks))) return rc;
         k_kpm<R><<<ka.Th * n_rhs, kt, ks, s>>>(h0, h1, c->dbar, c->scal, c->kpm.np, c->kpm.coef,
                                                n_rhs, ka);
