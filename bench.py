@@ -242,10 +242,9 @@ def run_ours(a):
         return it, res
 
     ctx.set_field(xd)
+    apply_options(ctx, a.option)      # before tuning: the tuner times what the solver runs
     tuned = ctx.tune(nr) if not a.no_tune else None
-    for opt in a.option:
-        name, val = opt.split("=")
-        ctx.set_option(name, int(val))
+    apply_options(ctx, a.option)      # explicit shapes win over the tuned ones
     for _ in range(a.warmup):
         flush.zero_()
         step(xd, Rd)
@@ -272,10 +271,19 @@ def run_ours(a):
     up_cnt, up_ms, _ = ctx.timer_read(hg.TIMER_UPDATE)
     fo_cnt, fo_ms, _ = ctx.timer_read(hg.TIMER_FORCE)
     pc_cnt, pc_ms, _ = ctx.timer_read(hg.TIMER_PRECOND)
-    ctx_kernel_name = ("k_cg_persist (fused CG chunk: p = r + beta p, q = M^T M p in shared "
-                       "memory, e += alpha p, r -= alpha q; per iteration r, p, e read and "
-                       "written once)" if op_avg_ms_hint(op_ms, op_cnt, up_cnt)
-                       else "k_cg_mtm32* (fused p = r + beta p, q = M^T M p, |Mp|^2)")
+    if ctx.get_option("merged_cg") and not a.precond:
+        ctx_kernel_name = ("k_cg_merged (one kernel per CG iteration: p = r + beta p, "
+                           "s = w + beta s, x += alpha p every other iteration, "
+                           "r' = r - alpha s, w' = M^T M r', r'.r' and |M r'|^2)")
+    elif op_avg_ms_hint(op_ms, op_cnt, up_cnt):
+        ctx_kernel_name = ("k_cg_persist (fused CG chunk: p = r + beta p, q = M^T M p in shared "
+                           "memory, e += alpha p, r -= alpha q; per iteration r, p, e read and "
+                           "written once)")
+    else:
+        kname = {0: "k_cg_mtm32<32>", 1: "k_cg_mtm32_v4<32>", 2: "k_cg_mtm32_v4a<32>",
+                 3: "k_cg_mtm32_v4s<32,3>", 4: "k_cg_mtm32_split<32,2>",
+                 5: "k_cg_mtm32_split<32,4>"}[ctx.get_option("layout")]
+        ctx_kernel_name = kname + " (fused p = r + beta p, q = M^T M p, |Mp|^2)"
     ctx.timer_enable(0)
     clk = clocks.stop()
     barrier(world)
@@ -292,24 +300,18 @@ def run_ours(a):
     mv = float(np.sum(2 * iters + 1 + 2 * rel + 1))
     total_mv = reduce_sum(world, mv)
 
-    # roofline of the dominant kernel (the CG operator: the persistent fused
-    # CG chunk when the grid fits, else the fused M^T M). The library records
-    # CUDA events around one in every TIMER_STRIDE launches on the launching
-    # stream during the timed region, with each launch's algorithmic bytes
-    # (every array read once and written once: r, p, e, expV; the tau halo
-    # re-reads are not counted).
+    # roofline of the dominant kernel (the CG operator: the merged CG
+    # iteration, the persistent fused CG chunk, or the fused M^T M). The
+    # library records CUDA events around one in every TIMER_STRIDE launches
+    # on the launching stream during the timed region, with each launch's
+    # algorithmic bytes (every array read once and written once, plus expV;
+    # the tau halo re-reads are not counted).
     op_avg_ms = op_ms / max(op_cnt, 1)
     alg_bytes = op_units / max(op_cnt, 1)
     achieved = op_units / max(op_ms / 1e3, 1e-12) / 1e9
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("k_cg_mtm32_bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = traffic_from_profiles(ctx_kernel_name.split()[0], op_cnt and alg_bytes)
 
     # FP64-only path on the same inputs (mixed vs FP64 at equal residual)
     fp64 = None
@@ -499,6 +501,47 @@ def measurement_leg(dev, n_rv=128):
             "mean_cg_iters": float(np.mean(its))}
 
 
+KERNEL_SOURCES = ("matvec.cu", "cb.cuh", "cb4.cuh", "cbs.cuh", "cg.cu")
+
+
+def kernel_source_digest():
+    """Digest of the sources of the CG kernels (a profile taken on other
+    sources no longer describes the running kernel)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2203_01291_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def traffic_from_profiles(kernel, alg_bytes):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    of `kernel` from a committed ncu summary: a line
+    `traffic_per_launch: <kernel> <source digest> <bytes> <alg bytes>` in
+    profiles/*.md, scaled to this run's algorithmic bytes per launch. None
+    when no summary matches the current kernel sources."""
+    import glob
+    digest = kernel_source_digest()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            if not line.startswith("traffic_per_launch:"):
+                continue
+            parts = line.split()
+            if len(parts) < 5 or parts[1] != kernel or parts[2] != digest:
+                continue
+            traffic, prof_alg = float(parts[3]), float(parts[4])
+            return traffic * (alg_bytes / prof_alg) if alg_bytes else traffic
+    return None
+
+
+def apply_options(ctx, options):
+    """NAME=VALUE launch options (hol_set_option)."""
+    for opt in options:
+        name, val = opt.split("=")
+        ctx.set_option(name, int(val))
+
+
 def op_avg_ms_hint(op_ms, op_cnt, up_cnt):
     """The persistent path records no separate update launches."""
     return op_cnt > 0 and up_cnt == 0
@@ -515,7 +558,9 @@ def run_matvec(a):
     nr = a.rhs
     ctx = hg.Context.from_workload(w, max_rhs=nr)
     ctx.set_field(torch.tensor(hi.phonon_field(w), device="cuda"))
+    apply_options(ctx, a.option)
     tuned = ctx.tune(nr) if not a.no_tune else None
+    apply_options(ctx, a.option)
     v = torch.tensor(hi.gaussian_vectors(w, nr, seed=5), device="cuda", dtype=torch.float32)
     q = torch.empty_like(v)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -535,6 +580,7 @@ def run_matvec(a):
     alg = nr * w.n * 4 * 2 + w.n * 4          # v in, q out, expV
     hbm = peaks().get("hbm_gbs", 6800.0)
     print(json.dumps({"mode": "matvec", "rhs": nr, "median_ms": ms, "tuned_launch": tuned,
+                      "options": a.option,
                       "alg_bytes": alg, "achieved_gbs": alg / (ms / 1e3) / 1e9,
                       "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / hbm,
                       "matvecs_per_s": 2 * nr / (ms / 1e3)}))

@@ -310,8 +310,9 @@ int fermion_matvec_static(const hol_params* p, const double* x, int op, const do
  * register layout) with CUDA events on `stream`, and keeps the fastest in the
  * context for all later calls (results are unchanged up to rounding; every
  * candidate computes the same operator). Host outputs (nullable): the chosen
- * slices per group, warps per block, layout (2 = float4 with
- * asynchronous prefetch, 1 = float4, 0 = scalar), and its time in ms.
+ * slices per group, warps per block, layout (5 / 4 = split
+ * float4 over 4 / 2 warps, 3 = streaming float4, 2 = float4 with asynchronous
+ * prefetch, 1 = float4, 0 = scalar), and its time in ms.
  * Requires hol_set_field; overwrites context scratch; synchronises `stream`.
  */
 int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_vec,
@@ -322,13 +323,27 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  * are the same up to rounding whichever is chosen):
  *   "slices_per_group"  tau slices streamed per lane group (divides Ltau)
  *   "warps_per_block"   1, 2 or 4 for the operator kernels
- *   "layout"            0 scalar, 1 float4, 2 float4 with cp.async prefetch
- *                       (1 and 2 need L % 8 == 0)
+ *   "layout"            0 scalar, 1 float4, 2 float4 with cp.async prefetch,
+ *                       3 streaming float4 with a cp.async ring across units
+ *                       (1-3 need L % 8 == 0), 4 / 5 split float4 with each
+ *                       slice spread over 2 / 4 warps (L == 32)
  *   "kpm_registers"     register KPM kernel for FP32, L = 16 or 32 (0/1)
  *   "persistent_cg"     plain mixed CG chunks in one cooperative launch (0/1)
- * Returns HOL_EINVAL for an unknown name or a value out of range.
+ *   "merged_cg"         plain mixed CG as one fused kernel per iteration
+ *                       (single-reduction Chronopoulos-Gear recurrences of
+ *                       the same CG, Eq. (CG); L % 8 == 0; allocates three
+ *                       more FP32 vector sets of max_rhs N Ltau on first
+ *                       use). Convergence is certified exactly as in the
+ *                       two-kernel solver; iteration counts may differ by a
+ *                       few percent (0/1)
+ * Returns HOL_EINVAL for an unknown name or a value out of range (HOL_ECUDA
+ * when an allocation fails).
  */
 int hol_set_option(hol_ctx* ctx, const char* name, int value);
+
+/* Current value of a launch option of hol_set_option into *value (written on
+ * success only). Returns HOL_EINVAL for a null argument or an unknown name. */
+int hol_get_option(const hol_ctx* ctx, const char* name, int* value);
 
 /*
  * Instrumentation (no counterpart in the paper; used by the benchmark).

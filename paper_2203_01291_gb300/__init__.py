@@ -32,7 +32,7 @@ __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F6
            "pseudofermion_phi", "phi_to_rhs", "hol_launch_count", "hol_timer_enable",
            "hol_timer_read", "fermion_matvec_static", "mass_apply", "md_integrate",
            "fourier_accel_leapfrog", "hol_md_opts", "stochastic_measure", "hol_tune",
-           "hmc_batch", "measure_batch", "hol_set_option", "hol_fma_peak",
+           "hmc_batch", "measure_batch", "hol_set_option", "hol_get_option", "hol_fma_peak",
            "library_path", "load"]
 
 
@@ -227,6 +227,12 @@ def hol_set_option(handle, name: str, value: int) -> None:
     _check(load().hol_set_option(handle, name.encode(), int(value)))
 
 
+def hol_get_option(handle, name: str) -> int:
+    out = ctypes.c_int(0)
+    _check(load().hol_get_option(handle, name.encode(), ctypes.byref(out)))
+    return int(out.value)
+
+
 def hol_fma_peak(prec: int) -> float:
     """Measured FMA throughput (GFLOP/s) of the current GPU."""
     g = ctypes.c_double()
@@ -352,6 +358,10 @@ class Context:
     def set_option(self, name: str, value: int) -> None:
         """Launch option (see include/holstein.h, hol_set_option)."""
         hol_set_option(self._h, name, value)
+
+    def get_option(self, name: str) -> int:
+        """Current value of a launch option (hol_get_option)."""
+        return hol_get_option(self._h, name)
 
     def tune(self, n_rhs: int) -> dict:
         """Pick the fastest launch shape of the fused M^T M for n_rhs (needs a field)."""

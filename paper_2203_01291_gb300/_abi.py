@@ -76,6 +76,7 @@ SIGNATURES = {
                            ctypes.POINTER(hol_cg_opts), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                            ctypes.POINTER(_VP), _I, _I]),
     "hol_set_option": (_I, [_VP, ctypes.c_char_p, _I]),
+    "hol_get_option": (_I, [_VP, ctypes.c_char_p, ctypes.POINTER(_I)]),
     "hol_tune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                       ctypes.POINTER(_D), _VP]),
     "hol_launch_count": (ctypes.c_ulonglong, []),

@@ -17,7 +17,8 @@
 // of the FP64 solution v; every `reliable_every` iterations, and whenever the
 // recursive residual estimate says "converged", e is folded into v and the
 // true residual b - M^T M v is recomputed in FP64 (reliable update) and
-// replaces r (the search direction is kept). Every reported convergence is
+// replaces r; the search direction is kept but re-conjugated against the new
+// residual (beta = -(z, A p) / (p, A p)). Every reported convergence is
 // certified by that FP64 residual. The preconditioner of the mixed path runs
 // in FP32.
 #include <math.h>
@@ -87,11 +88,16 @@ __global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restr
 {
     const int rhs = blockIdx.y;
     if (mask != nullptr && mask[rhs] == 0) return;
-    // every warp forms alpha itself (same partials, same order, same bits),
-    // so no barrier sits before the streaming loop
-    const double pq = warp_sum_array(pq_part + (long)rhs * pq_stride, pq_n);
-    const double dz = warp_sum_array(dz_part + (long)rhs * kRedStride, dz_n);
-    const R a = (R)(dz / pq);
+    // one warp forms alpha (FP64 sums are slow on this part: doing it in
+    // every warp measured slower than the barrier)
+    __shared__ double s_alpha;
+    if (threadIdx.x < 32) {
+        const double pq = warp_sum_array(pq_part + (long)rhs * pq_stride, pq_n);
+        const double dz = warp_sum_array(dz_part + (long)rhs * kRedStride, dz_n);
+        if (threadIdx.x == 0) s_alpha = dz / pq;
+    }
+    __syncthreads();
+    const R a = (R)s_alpha;
     const long base = (long)rhs * n;
     const long stride = (long)gridDim.x * blockDim.x;
     double acc = 0.0;
@@ -184,13 +190,102 @@ __global__ void __launch_bounds__(256) k_recast(const double* rt, R* r, long n,
     if (threadIdx.x == 0) rr_out[(long)rhs * kRedStride + blockIdx.x] = s;
 }
 
-// out[rhs] = sum_k bank[rhs*kRedStride + k], k < cnt; one warp per rhs.
-__global__ void k_rows(const double* __restrict__ bank, int cnt, int n_rhs, double* __restrict__ out)
+// out[rhs] = sum_k bank[rhs*stride + k], k < cnt; one warp per rhs.
+__global__ void k_rows(const double* __restrict__ bank, int cnt, int stride, int n_rhs,
+                       double* __restrict__ out)
 {
     const int rhs = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (rhs >= n_rhs) return;
-    const double s = warp_sum_array(bank + (long)rhs * kRedStride, cnt);
+    const double s = warp_sum_array(bank + (long)rhs * stride, cnt);
     if ((threadIdx.x & 31) == 0) out[rhs] = s;
+}
+
+// Block partials of a.b (FP32 vectors, FP64 accumulation) for the flagged rhs.
+__global__ void __launch_bounds__(256) k_dot32(const float* __restrict__ a,
+                                               const float* __restrict__ b, long n,
+                                               const int* __restrict__ mask,
+                                               double* __restrict__ out)
+{
+    const int rhs = blockIdx.y;
+    if (mask[rhs] == 0) return;
+    const long base = (long)rhs * n;
+    double acc = 0.0;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+         k += (long)gridDim.x * blockDim.x)
+        acc += (double)a[base + k] * (double)b[base + k];
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) out[(long)rhs * kRedStride + blockIdx.x] = s;
+}
+
+// Merged CG: put the flagged rhs into a start (2) or restart (1) mode.
+__global__ void k_set_mode(double* __restrict__ slot, const int* __restrict__ flag, int n_rhs,
+                           double mode)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_rhs || flag[k] == 0) return;
+    if (mode == 2.0) {   // alpha_prev and gamma_prev are not used; keep them finite
+        slot[k * 4 + 0] = 1.0;
+        slot[k * 4 + 1] = 1.0;
+    }
+    slot[k * 4 + 2] = mode;
+}
+
+
+// Restart of the search direction after a reliable update: the kept p is
+// re-conjugated against the new residual, beta = -(z, A p) / (p, A p) with
+// q = A p. Block partials of (z, q) and (p, q) for the flagged rhs.
+template <typename R>
+__global__ void __launch_bounds__(256) k_conj_dots(const R* __restrict__ z, const R* __restrict__ p,
+                                                   const R* __restrict__ q, long n,
+                                                   const int* __restrict__ mask,
+                                                   double* __restrict__ zq_out,
+                                                   double* __restrict__ pq_out)
+{
+    const int rhs = blockIdx.y;
+    if (mask[rhs] == 0) return;
+    const long base = (long)rhs * n;
+    double azq = 0.0, apq = 0.0;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+         k += (long)gridDim.x * blockDim.x) {
+        const double qv = (double)q[base + k];
+        azq += (double)z[base + k] * qv;
+        apq += (double)p[base + k] * qv;
+    }
+    double t = block_sum(azq);
+    if (threadIdx.x == 0) zq_out[(long)rhs * kRedStride + blockIdx.x] = t;
+    __syncthreads();
+    t = block_sum(apq);
+    if (threadIdx.x == 0) pq_out[(long)rhs * kRedStride + blockIdx.x] = t;
+}
+
+// p *= beta = -(z, q) / (p, q) for the flagged rhs (every thread forms beta
+// from the same partials in the same order).
+template <typename R>
+__global__ void __launch_bounds__(256) k_conj_scale(R* __restrict__ p, long n,
+                                                    const int* __restrict__ mask,
+                                                    const double* __restrict__ zq_part,
+                                                    const double* __restrict__ pq_part, int cnt)
+{
+    const int rhs = blockIdx.y;
+    if (mask[rhs] == 0) return;
+    const double zq = warp_sum_array(zq_part + (long)rhs * kRedStride, cnt);
+    const double pq = warp_sum_array(pq_part + (long)rhs * kRedStride, cnt);
+    const R bt = (R)(-zq / pq);
+    const long base = (long)rhs * n;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+         k += (long)gridDim.x * blockDim.x)
+        p[base + k] *= bt;
+}
+
+// dst row = src row (kRedStride partials) for the flagged rhs, so that the
+// next beta = sum(src) / sum(dst) is exactly 1.
+__global__ void k_copy_rows(const double* __restrict__ src, double* __restrict__ dst,
+                            const int* __restrict__ mask)
+{
+    const int rhs = blockIdx.x;
+    if (mask[rhs] == 0) return;
+    for (int k = threadIdx.x; k < kRedStride; k += blockDim.x)
+        dst[(long)rhs * kRedStride + k] = src[(long)rhs * kRedStride + k];
 }
 
 struct Banks {
@@ -216,10 +311,11 @@ Banks banks_of(hol_ctx* c)
 }
 
 // Reduce bank rows to per-rhs values and copy them to the pinned host buffer.
-int rows_to_host(hol_ctx* c, const double* bank, int cnt, int n_rhs, double* host, cudaStream_t s)
+int rows_to_host(hol_ctx* c, const double* bank, int cnt, int n_rhs, double* host, cudaStream_t s,
+                 int stride = kRedStride)
 {
     double* red = banks_of(c).red;
-    k_rows<<<ceil_div(32L * n_rhs, 256), 256, 0, s>>>(bank, cnt, n_rhs, red);
+    k_rows<<<ceil_div(32L * n_rhs, 256), 256, 0, s>>>(bank, cnt, stride, n_rhs, red);
     HOL_CHECK_LAUNCH("k_rows");
     HOL_CUDA(cudaMemcpyAsync(host, red, n_rhs * sizeof(double), cudaMemcpyDeviceToHost, s));
     HOL_CUDA(cudaStreamSynchronize(s));
@@ -394,6 +490,8 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
             }
         }
         if (n_rel == 0) continue;
+        if (persistent)   // bank rows of all rhs must keep one partial count
+            for (int k = 0; k < n_rhs; ++k) rel_h[k] = act_h[k];
         // reliable update / convergence certification for the flagged rhs
         HOL_CUDA(cudaMemcpyAsync(rel_d, rel_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
         if (mixed) {
@@ -412,6 +510,205 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
         // the new r changes r.z: recompute z (all rhs; the unchanged ones get
         // the same z again)
         if (pc && (rc = apply_prec(cur))) return rc;
+        // keep the direction, re-conjugated against the new z:
+        // p *= -(z, A p) / (p, A p) and the next beta forced to 1. Keeping
+        // p with beta = (r.z)_new / (r.z)_old instead lets the old direction
+        // swamp the new residual in FP32 when the recursive residual had
+        // drifted far below the true one.
+        {
+            double* cj0 = c->part + 8 * c->part_len;
+            double* cj1 = c->part + 9 * c->part_len;
+            if (mixed) {
+                if (persistent &&   // the persistent chunk keeps q in shared memory
+                    (rc = launch_cg_mtm32(c, p32[pp], p32[pp], nullptr, q32, n_rhs, rel_d, nullptr,
+                                          nullptr, 0, 0, 1, nullptr, s)))
+                    return rc;
+                k_conj_dots<float><<<g2, 256, 0, s>>>(z32, p32[pp], q32, n, rel_d, cj0, cj1);
+                HOL_CHECK_LAUNCH("k_conj_dots");
+                k_conj_scale<float><<<g2, 256, 0, s>>>(p32[pp], n, rel_d, cj0, cj1, nb2);
+            } else {
+                k_conj_dots<double><<<g2, 256, 0, s>>>(z64, p64[pp], q64, n, rel_d, cj0, cj1);
+                HOL_CHECK_LAUNCH("k_conj_dots");
+                k_conj_scale<double><<<g2, 256, 0, s>>>(p64[pp], n, rel_d, cj0, cj1, nb2);
+            }
+            HOL_CHECK_LAUNCH("k_conj_scale");
+            k_copy_rows<<<n_rhs, 256, 0, s>>>(B.dz[cur], B.dz[1 - cur], rel_d);
+            HOL_CHECK_LAUNCH("k_copy_rows");
+            cnt[1 - cur] = cnt[cur];
+        }
+        if ((rc = rows_to_host(c, B.tr, nb2, n_rhs, hb, s))) return rc;
+        int changed = 0;
+        for (int k = 0; k < n_rhs; ++k) {
+            if (!rel_h[k]) continue;
+            since[k] = 0;
+            true_res[k] = sqrt(hb[k]) / bnorm[k];
+            if (!isfinite(true_res[k]))
+                return set_error(HOL_ENUMERIC, "cg_solve: non-finite true residual (rhs %d)", k);
+            if (true_res[k] < o->tol) {
+                done[k] = 1;
+                act_h[k] = 0;
+                --n_active;
+                changed = 1;
+            }
+        }
+        if (changed)
+            HOL_CUDA(cudaMemcpyAsync(act_d, act_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    HOL_CUDA(cudaStreamSynchronize(s));
+    int all = 1;
+    for (int k = 0; k < n_rhs; ++k) {
+        if (iters) iters[k] = it[k];
+        if (resid) resid[k] = true_res[k];
+        all &= done[k];
+    }
+    if (!all)
+        return set_error(HOL_ENOTCONV, "cg_solve: not converged within %d iterations", o->max_iter);
+    return HOL_OK;
+}
+
+
+// Mixed plain CG with one fused kernel per iteration (k_cg_merged in
+// matvec.cu, Chronopoulos-Gear recurrences). The FP32 state per rhs is
+// x (the increment e), r, w = A r, p, s = A p; r, w, p, s are double
+// buffered by iteration parity because neighbouring units read the tau halo
+// of r and w. The x update of an iteration may be deferred to the next one
+// (which reads p_old anyway), so x is touched every other iteration; the
+// last iteration of every polling chunk settles it. Reliable updates work
+// as in cg_run; the restarted rhs get w = A r and s_old = A p_old
+// recomputed in FP32 with rho = r.s_old and pi = p_old.s_old, so the kept
+// direction is re-conjugated (beta = -rho / pi) and alpha is formed from
+// exact inner products (mode 1).
+static int cg_run_merged(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_opts* o,
+                         int* iters, double* resid, cudaStream_t s)
+{
+    const long n = c->n;
+    const int nb2 = elementwise_blocks(c);
+    const dim3 g2(nb2, n_rhs);
+    const Banks B = banks_of(c);
+    const int pstride = matvec_pstride(c);
+    const int nrun = c->T / c->mv_k;
+    int* act_d = c->mask;
+    int* rel_d = c->mask + c->p.max_rhs;
+    int* act_h = c->hflag;
+    int* rel_h = c->hflag + c->p.max_rhs;
+    double* hb = c->hbuf;
+    int rc;
+    double* G[2] = {B.dz[0], B.dz[1]};
+    double* D[2] = {B.pq, c->part + 11 * c->part_len};
+    double* Gr = c->part + 8 * c->part_len;
+    double* PI = c->part + 9 * c->part_len;
+    double* RHO = c->part + 10 * c->part_len;
+    float* e = c->v32e;
+    float* R[2] = {c->v32a, c->v32g};
+    float* W[2] = {c->v32d, c->v32h};
+    float* P[2] = {c->v32b, c->v32c};
+    float* S[2] = {c->v32f, c->v32i};
+    double* slot[2] = {c->cgs, c->cgs + 4 * c->p.max_rhs};
+    double* t64 = c->v64a;
+    double* rt64 = c->v64b;
+    const double nd = (double)n;
+
+    HOL_CUDA(cudaMemsetAsync(v, 0, (size_t)n_rhs * n * sizeof(double), s));
+    k_cg_init<float><<<g2, 256, 0, s>>>(b, R[0], e, n, B.bn, Gr);
+    HOL_CHECK_LAUNCH("k_cg_init");
+    if ((rc = rows_to_host(c, B.bn, nb2, n_rhs, hb, s))) return rc;
+    std::vector<double> bnorm(n_rhs), true_res(n_rhs, 1.0);
+    std::vector<int> it(n_rhs, 0), since(n_rhs, 0), done(n_rhs, 0);
+    int n_active = 0;
+    for (int k = 0; k < n_rhs; ++k) {
+        bnorm[k] = sqrt(hb[k]);
+        if (!isfinite(bnorm[k])) return set_error(HOL_ENUMERIC, "cg_solve: non-finite |b|");
+        act_h[k] = bnorm[k] != 0.0;
+        if (!act_h[k]) {   // v = 0 is exact
+            done[k] = 1;
+            true_res[k] = 0.0;
+        }
+        n_active += act_h[k];
+        rel_h[k] = 0;
+    }
+    HOL_CUDA(cudaMemcpyAsync(act_d, act_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (n_active > 0) {   // w = A r, delta partials; start mode
+        if ((rc = launch_cg_mtm32(c, R[0], R[0], nullptr, W[0], n_rhs, act_d, nullptr, nullptr, 0,
+                                  0, 1, D[0], s)))
+            return rc;
+        k_set_mode<<<ceil_div(n_rhs, 128), 128, 0, s>>>(slot[1], act_d, n_rhs, 2.0);
+        HOL_CHECK_LAUNCH("k_set_mode");
+    }
+    const int chk = o->check_every > 0 ? o->check_every : 10;
+    const int rel_every = o->reliable_every > 0 ? o->reliable_every : 1 << 30;
+    long i = 0;   // merged iterations so far (parity selects the buffers)
+    int k_it = 0;
+    while (n_active > 0 && k_it < o->max_iter) {
+        int chunk = chk;
+        if (chunk > o->max_iter - k_it) chunk = o->max_iter - k_it;
+        bool pending = false;
+        for (int j = 0; j < chunk; ++j) {
+            const int a = (int)(i & 1), z = 1 - a;
+            MergedScal sc;
+            sc.slot_in = slot[z];
+            sc.slot_out = slot[a];
+            sc.g_in = G[a];
+            sc.d_in = D[a];
+            sc.g_out = G[z];
+            sc.d_out = D[z];
+            sc.gr = Gr;
+            sc.rho = RHO;
+            sc.e_n = nb2;
+            sc.pi = PI;
+            if (pending) {
+                sc.fold = 2;
+                pending = false;
+            } else if (j == chunk - 1) {
+                sc.fold = 1;
+            } else {
+                sc.fold = 0;
+                pending = true;
+            }
+            timer_start(c, KT_OPERATOR, s,
+                        n_active * nd * (32.0 + (sc.fold ? 8.0 : 0.0)) + nd * 4.0);
+            rc = launch_cg_merged(c, R[a], W[a], P[z], S[z], e, P[a], S[a], R[z], W[z], n_rhs,
+                                  act_d, sc, s);
+            if (rc) return rc;
+            timer_stop(c, KT_OPERATOR, s);
+            ++i;
+        }
+        k_it += chunk;
+        const int a = (int)(i & 1), z = 1 - a;   // the next iteration's parity
+        if ((rc = rows_to_host(c, G[a], nrun, n_rhs, hb, s, pstride))) return rc;
+        int n_rel = 0;
+        for (int k = 0; k < n_rhs; ++k) {
+            rel_h[k] = 0;
+            if (!act_h[k]) continue;
+            it[k] += chunk;
+            since[k] += chunk;
+            const double est = sqrt(hb[k]) / bnorm[k];
+            if (!isfinite(est))
+                return set_error(HOL_ENUMERIC, "cg_solve: non-finite residual (rhs %d, iter %d)",
+                                 k, it[k]);
+            if (est < o->tol || since[k] >= rel_every || k_it >= o->max_iter) {
+                rel_h[k] = 1;
+                ++n_rel;
+            }
+        }
+        if (n_rel == 0) continue;
+        HOL_CUDA(cudaMemcpyAsync(rel_d, rel_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
+        k_fold<<<g2, 256, 0, s>>>(v, e, n, rel_d);
+        HOL_CHECK_LAUNCH("k_fold");
+        if ((rc = launch_M(c, HOL_F64, v, t64, n_rhs, rel_d, nullptr, s))) return rc;
+        if ((rc = launch_MT_resid64(c, t64, b, rt64, n_rhs, rel_d, s))) return rc;
+        k_recast<float><<<g2, 256, 0, s>>>(rt64, R[a], n, rel_d, B.tr, Gr);
+        HOL_CHECK_LAUNCH("k_recast");
+        // w = A r for the new r, s_old = A p_old, rho = r.s_old
+        if ((rc = launch_cg_mtm32(c, R[a], R[a], nullptr, W[a], n_rhs, rel_d, nullptr, nullptr, 0,
+                                  0, 1, D[a], s)))
+            return rc;
+        if ((rc = launch_cg_mtm32(c, P[z], P[z], nullptr, S[z], n_rhs, rel_d, nullptr, nullptr, 0,
+                                  0, 1, PI, s)))
+            return rc;
+        k_dot32<<<g2, 256, 0, s>>>(R[a], S[z], n, rel_d, RHO);
+        HOL_CHECK_LAUNCH("k_dot32");
+        k_set_mode<<<ceil_div(n_rhs, 128), 128, 0, s>>>(slot[z], rel_d, n_rhs, 1.0);
+        HOL_CHECK_LAUNCH("k_set_mode");
         if ((rc = rows_to_host(c, B.tr, nb2, n_rhs, hb, s))) return rc;
         int changed = 0;
         for (int k = 0; k < n_rhs; ++k) {
@@ -458,5 +755,7 @@ extern "C" int cg_solve(hol_ctx* c, const double* b, double* v, int n_rhs, const
     if (!(o->tol > 0.0) || o->max_iter < 1)
         return set_error(HOL_EINVAL, "cg_solve: tol must be > 0 and max_iter >= 1");
     if (b == v) return set_error(HOL_EINVAL, "cg_solve: b and v must not overlap");
+    if (c->merged && o->prec == HOL_F32 && !o->precond)
+        return cg_run_merged(c, b, v, n_rhs, o, iters, resid, (cudaStream_t)stream);
     return cg_run(c, b, v, n_rhs, o, iters, resid, (cudaStream_t)stream);
 }

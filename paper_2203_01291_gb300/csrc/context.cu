@@ -137,7 +137,8 @@ void free_ctx(hol_ctx* c)
                    c->v64c, c->v64d, c->v64e, c->v32a, c->v32b, c->v32c, c->v32d, c->v32e,
                    c->mask, c->kpm.np, c->kpm.coef, c->cbuf0, c->cbuf1, c->v64f, c->v32f,
                    c->tw64, c->tw32, c->md_phi, c->md_b, c->md_v, c->md_F, c->md_p,
-                   c->md_x0, c->md_g, c->md_s, c->ms_acc, c->twL64};
+                   c->md_x0, c->md_g, c->md_s, c->ms_acc, c->twL64, c->v32g, c->v32h,
+                   c->v32i, c->cgs};
     for (void* p : dev)
         if (p) cudaFree(p);
     timer_free(c->timer);
@@ -187,6 +188,7 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     c->mv_vec = 1;
     c->kpm_reg = 1;
     c->persist = 0;
+    c->merged = 0;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         free_ctx(c);
         return set_error(HOL_ECUDA, "hol_create: no CUDA device");
@@ -385,15 +387,44 @@ extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
             return set_error(HOL_EINVAL, "hol_set_option: warps_per_block must be 1, 2 or 4");
         c->mv_warps = value;
     } else if (is("layout")) {
-        if (value < 0 || value > 2 || (value > 0 && c->L % 8))
-            return set_error(HOL_EINVAL, "hol_set_option: layout 0..2 (1, 2 need L % 8 == 0)");
+        if (value < 0 || value > 5 || (value > 0 && c->L % 8) || (value > 3 && c->L != 32))
+            return set_error(HOL_EINVAL,
+                             "hol_set_option: layout 0..5 (1-3 need L %% 8 == 0, 4-5 L == 32)");
         c->mv_vec = value;
     } else if (is("kpm_registers")) {
         c->kpm_reg = value ? 1 : 0;
     } else if (is("persistent_cg")) {
         c->persist = value ? 1 : 0;
+    } else if (is("merged_cg")) {
+        if (value && c->L % 8)
+            return set_error(HOL_EINVAL, "hol_set_option: merged_cg needs L % 8 == 0");
+        if (value && !c->v32g) {   // three more FP32 vector sets and the scalar slots
+            const size_t vb = (size_t)c->p.max_rhs * c->n * sizeof(float);
+            float** bufs[3] = {&c->v32g, &c->v32h, &c->v32i};
+            for (float** b : bufs) {
+                const cudaError_t e = cudaMalloc((void**)b, vb);
+                if (e != cudaSuccess) return cuda_error(e, "hol_set_option: merged_cg buffers");
+            }
+            const cudaError_t e = cudaMalloc((void**)&c->cgs, 8 * c->p.max_rhs * sizeof(double));
+            if (e != cudaSuccess) return cuda_error(e, "hol_set_option: merged_cg scalars");
+        }
+        c->merged = value ? 1 : 0;
     } else {
         return set_error(HOL_EINVAL, "hol_set_option: unknown option '%s'", name);
     }
+    return HOL_OK;
+}
+
+extern "C" int hol_get_option(const hol_ctx* c, const char* name, int* value)
+{
+    if (!c || !name || !value) return set_error(HOL_EINVAL, "hol_get_option: null argument");
+    auto is = [&](const char* s) { return strcmp(name, s) == 0; };
+    if (is("slices_per_group")) *value = c->mv_k;
+    else if (is("warps_per_block")) *value = c->mv_warps;
+    else if (is("layout")) *value = c->mv_vec;
+    else if (is("kpm_registers")) *value = c->kpm_reg;
+    else if (is("persistent_cg")) *value = c->persist;
+    else if (is("merged_cg")) *value = c->merged;
+    else return set_error(HOL_EINVAL, "hol_get_option: unknown option '%s'", name);
     return HOL_OK;
 }

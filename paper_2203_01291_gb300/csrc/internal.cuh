@@ -54,7 +54,7 @@ constexpr int kMaxL = 32;
 // partial-sum banks have a fixed stride).
 constexpr int kRedStride = 256;
 // Number of partial-sum banks in hol_ctx::part.
-constexpr int kBanks = 8;
+constexpr int kBanks = 12;
 
 // Device-side scalars kept by a context (FP64).
 enum Scalar {
@@ -107,6 +107,10 @@ struct hol_ctx {
     int* mask;           // [2*max_rhs] active / reliable-update flags (device)
     double* v64f;
     float* v32f;
+    float* v32g;         // merged CG only (allocated when the option is set)
+    float* v32h;
+    float* v32i;
+    double* cgs;         // merged CG scalars [2][max_rhs][4]: alpha, gamma, mode
     double2* tw64;       // [2T] exp(-i pi k / T)
     float2* tw32;
     double* md_phi;      // leapfrog: Phi [max_rhs][T][N]
@@ -133,6 +137,7 @@ struct hol_ctx {
     int mv_vec;          // use the float4 layout of the fused FP32 M^T M (L % 8 == 0)
     int kpm_reg;         // use the register KPM kernel (FP32, L = 16 or 32)
     int persist;         // use the persistent fused CG kernel when it fits
+    int merged;          // mixed plain CG as one fused kernel per iteration
 };
 
 namespace hol {
@@ -175,6 +180,25 @@ int launch_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* 
 int launch_cg_persist(const hol_ctx* c, float* r, float* p0, float* p1, float* e, int n_rhs,
                       const int* mask, double* pq, double* rr0, double* rr1, int cur, int cnt_cur,
                       int cnt_old, int pp, int first, int nit, int check_only, cudaStream_t s);
+// Scalars of one merged (single-reduction) CG iteration; see cg.cu.
+struct MergedScal {
+    const double* slot_in;   // [rhs*4 + {alpha_prev, gamma_prev, mode}]
+    double* slot_out;        // alpha, gamma of this iteration, mode 0
+    const double* g_in;      // unit partials of gamma = r.r (mode 0)
+    const double* d_in;      // unit partials of delta = r.(M^T M r)
+    double* g_out;           // unit partials of the next gamma, delta
+    double* d_out;
+    const double* gr;        // block partials of gamma after a (re)start (modes 1, 2)
+    const double* rho;       // block partials of r.s_old (mode 1)
+    int e_n;                 // block partial count of gr and rho
+    const double* pi;        // unit partials of p_old.(M^T M p_old) (mode 1)
+    int fold;                // 0: defer the x update, 1: x += a p, 2: x += a_prev p_old + a p
+};
+// One merged CG iteration (float4 layout, L % 8 == 0).
+int launch_cg_merged(const hol_ctx* c, const float* r, const float* w, const float* pold,
+                     const float* sold, float* e, float* pnew, float* snew, float* rnew,
+                     float* wnew, int n_rhs, const int* mask, const MergedScal& sc,
+                     cudaStream_t s);
 int matvec_pstride(const hol_ctx* c);          // per-rhs stride of unit partials
 int matvec_units(const hol_ctx* c, int n_rhs); // upper bound of units per call
 

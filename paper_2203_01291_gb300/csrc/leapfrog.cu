@@ -163,7 +163,7 @@ int filter(hol_ctx* c, const double* in, const double* base, double* out, double
     const RadixPlan plan = plan_of(c->T);
     if (plan.n < 0) return set_error(HOL_EINVAL, "leapfrog: Ltau=%d has a prime factor > 7", c->T);
     const size_t sm = 2 * (size_t)c->T * kFilterTS * sizeof(double2);
-    if (sm > 48 * 1024)
+    if (sm > 32 * 1024)   // leaves room for static shared memory under the default limit
         HOL_CUDA(cudaFuncSetAttribute((const void*)k_tau_filter,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_tau_filter<<<ceil_div(c->N, kFilterTS), 256, sm, s>>>(in, base, out, coef,

@@ -10,6 +10,9 @@
 // leaves registers.
 #include "cb.cuh"
 #include "cb4.cuh"
+#include "cbs.cuh"
+#include <atomic>
+
 #include "internal.cuh"
 
 namespace hol {
@@ -370,11 +373,11 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int NPEND>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND)); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
 
 template <int L>
 __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict__ r,
@@ -496,6 +499,447 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
     if (pq_part != nullptr) group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
 }
 
+
+// ---------------------------------------------------------------------------
+// Streaming float4 fused CG step: a resident set of warps walks the units
+// (grid stride) and keeps a ring of S slice stages (r and p_old rows of one
+// tau slice per stage) in flight with cp.async across unit boundaries, so the
+// next unit's slices load while the current one computes. Each lane copies
+// and reads only its own ring slots (no barriers).
+// ---------------------------------------------------------------------------
+template <int L, int S>
+__global__ void __launch_bounds__(128, 2) k_cg_mtm32_v4s(const float* __restrict__ r,
+                                                        const float* __restrict__ pold,
+                                                        float* __restrict__ pnew,
+                                                        float* __restrict__ q,
+                                                        const float* __restrict__ ev, MvGeom gm,
+                                                        const int* __restrict__ mask,
+                                                        const double* __restrict__ rr_new_part,
+                                                        const double* __restrict__ rr_old_part,
+                                                        int rr_stride, int rr_n, int first,
+                                                        double* __restrict__ pq_part, float th,
+                                                        int total_warps)
+{
+    constexpr int N = L * L;
+    constexpr int RT = L / 4;
+    extern __shared__ __align__(16) float4 ring[];   // [warp][stage][array][RT][32]
+    const Geom4<L> geo;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* my = ring + (long)wib * (S * 2 * RT * 32);
+    auto slot = [&](int st, int arr, int k) -> float4* {
+        return my + ((st * 2 + arr) * RT + k) * 32 + lane;
+    };
+    const int warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw_units = gm.wpr * gm.n_rhs;              // warp-units in the launch
+    const int rounds = (nw_units - warp0 + total_warps - 1) / total_warps;
+    const int per = gm.K + 2;                            // slices per unit
+    const int npos = rounds * per;
+    // position -> (round, slice index j in the unit)
+    auto unit_of = [&](int rd, int& rhs, int& run) {
+        const int w = warp0 + rd * total_warps;
+        rhs = w / gm.wpr;
+        run = (w - rhs * gm.wpr) * Geom4<L>::G + geo.g;
+    };
+    auto issue = [&](int pos) {
+        if (pos < npos) {
+            const int rd = pos / per, j = pos - rd * per;
+            int rhs, run;
+            unit_of(rd, rhs, run);
+            const bool act = (mask == nullptr || mask[rhs] != 0);
+            if (act) {
+                const int t0 = (run < gm.nrun ? run : gm.nrun - 1) * gm.K;
+                int t = t0 - 1 + j;
+                if (t < 0) t += gm.T;
+                if (t >= gm.T) t -= gm.T;
+                const long o = (long)rhs * gm.T * N + (long)t * N;
+#pragma unroll
+                for (int k = 0; k < RT; ++k) {
+                    cp_async16(slot(pos % S, 0, k), r + o + geo.off(k));
+                    cp_async16(slot(pos % S, 1, k), (first ? r : pold) + o + geo.off(k));
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    for (int p = 0; p < S - 1; ++p) issue(p);
+    int pos = 0;
+    for (int rd = 0; rd < rounds; ++rd) {
+        int rhs, run;
+        unit_of(rd, rhs, run);
+        const bool act = (mask == nullptr || mask[rhs] != 0);
+        if (!act) {   // the ring still advances over this unit's (empty) stages
+            for (int j = 0; j < per; ++j, ++pos) {
+                issue(pos + S - 1);
+                cp_async_wait<S - 1>();
+            }
+            continue;
+        }
+        const bool valid = geo.ok && run < gm.nrun;
+        const int t0 = (run < gm.nrun ? run : gm.nrun - 1) * gm.K;
+        const long base = (long)rhs * gm.T * N;
+        float bt = 0.0f;
+        if (!first) {
+            const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
+            const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
+            bt = (float)(rn / ro);
+        }
+        float4 W[RT], X[RT], P[RT], Y[RT];
+        issue(pos + S - 1);
+        cp_async_wait<S - 1>();
+#pragma unroll
+        for (int k = 0; k < RT; ++k)
+            Y[k] = fma4s(bt, *slot(pos % S, 1, k), *slot(pos % S, 0, k));
+        c4_apply<L>(Y, geo, th);
+        ++pos;
+        issue(pos + S - 1);
+        cp_async_wait<S - 1>();
+        {
+            const long o = base + (long)t0 * N;
+            const float sg = (t0 == 0) ? 1.0f : -1.0f;
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                const float4 pv = fma4s(bt, *slot(pos % S, 1, k), *slot(pos % S, 0, k));
+                if (valid && pnew != nullptr) st4(pnew, o + geo.off(k), pv);
+                X[k] = pv;
+                const float4 d = ld4(ev, (long)t0 * N + geo.off(k));
+                W[k] = make_float4(fmaf(sg * d.x, Y[k].x, pv.x), fmaf(sg * d.y, Y[k].y, pv.y),
+                                   fmaf(sg * d.z, Y[k].z, pv.z), fmaf(sg * d.w, Y[k].w, pv.w));
+            }
+            c4_apply<L>(X, geo, th);
+        }
+        ++pos;
+        double acc = 0.0;
+        for (int s = 0; s < gm.K; ++s, ++pos) {
+            issue(pos + S - 1);
+            cp_async_wait<S - 1>();
+            const int tau = t0 + s;
+            const int tp = (tau + 1 == gm.T) ? 0 : tau + 1;
+            const long op = base + (long)tp * N;
+            const float sgp = (tp == 0) ? 1.0f : -1.0f;
+            const bool own = valid && (s + 1 < gm.K) && pnew != nullptr;
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                const float4 pv = fma4s(bt, *slot(pos % S, 1, k), *slot(pos % S, 0, k));
+                if (own) st4(pnew, op + geo.off(k), pv);
+                P[k] = pv;
+                float4 d = ld4(ev, (long)tp * N + geo.off(k));
+                d.x *= sgp; d.y *= sgp; d.z *= sgp; d.w *= sgp;
+                X[k] = make_float4(fmaf(d.x, X[k].x, pv.x), fmaf(d.y, X[k].y, pv.y),
+                                   fmaf(d.z, X[k].z, pv.z), fmaf(d.w, X[k].w, pv.w));
+                Y[k] = make_float4(d.x * X[k].x, d.y * X[k].y, d.z * X[k].z, d.w * X[k].w);
+            }
+            c4_apply<L>(P, geo, th);
+            c4_apply_t<L>(Y, geo, th);
+            const long o = base + (long)tau * N;
+            float part = 0.0f;
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                if (valid)
+                    st4(q, o + geo.off(k), make_float4(W[k].x + Y[k].x, W[k].y + Y[k].y,
+                                                       W[k].z + Y[k].z, W[k].w + Y[k].w));
+                part = fmaf(W[k].x, W[k].x, part);
+                part = fmaf(W[k].y, W[k].y, part);
+                part = fmaf(W[k].z, W[k].z, part);
+                part = fmaf(W[k].w, W[k].w, part);
+                W[k] = X[k];
+                X[k] = P[k];
+            }
+            acc += (double)part;
+        }
+        if (pq_part != nullptr) group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
+    }
+    cp_async_wait<0>();
+}
+
+
+// ---------------------------------------------------------------------------
+// Merged CG iteration (single reduction per iteration, Chronopoulos-Gear
+// recurrences): with w = A r and s = A p for A = M^T M,
+//   beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev)
+//   p = r + beta p_old,  s = w + beta s_old,  x += alpha p,  r' = r - alpha s,
+//   w' = A r',  gamma' = r'.r',  delta' = r'.w' = |M r'|^2.
+// r' is formed on the fly for the unit's slices and its two tau neighbours,
+// so the whole iteration is one pass over the vectors (float4 layout).
+// mode 1 (after a reliable update, with s_old = A p_old recomputed):
+//   beta = -rho / pi (p re-conjugated against the new r),
+//   alpha = gamma / (delta + 2 beta rho + beta^2 pi), rho = r.s_old,
+//   pi = p_old.s_old; mode 2 (start): beta = 0, alpha = gamma / delta.
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(128, 3) k_cg_merged(
+    const float* __restrict__ r, const float* __restrict__ w, const float* __restrict__ pold,
+    const float* __restrict__ sold, float* __restrict__ e, float* __restrict__ pnew,
+    float* __restrict__ snew, float* __restrict__ rnew, float* __restrict__ wnew,
+    const float* __restrict__ ev, MvGeom gm, const int* __restrict__ mask, MergedScal sc,
+    float th)
+{
+    constexpr int N = L * L;
+    constexpr int RT = L / 4;
+    const Geom4<L> geo;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int rhs = warp / gm.wpr;
+    if (rhs >= gm.n_rhs) return;
+    if (mask != nullptr && mask[rhs] == 0) return;
+    const int wr = warp - rhs * gm.wpr;
+    const int run = wr * Geom4<L>::G + geo.g;
+    const bool valid = geo.ok && run < gm.nrun;
+    const int t0 = (run < gm.nrun ? run : gm.nrun - 1) * gm.K;
+    const long base = (long)rhs * gm.T * N;
+
+    // scalars: every warp forms them from the same partials in the same order
+    const double* si = sc.slot_in + rhs * 4;
+    const int mode = (int)si[2];
+    const double dl = warp_sum_array(sc.d_in + (long)rhs * gm.pstride, gm.nrun);
+    double ga, be, al;
+    if (mode == 0) {
+        ga = warp_sum_array(sc.g_in + (long)rhs * gm.pstride, gm.nrun);
+        be = ga / si[1];
+        al = ga / (dl - be * ga / si[0]);
+    } else {
+        ga = warp_sum_array(sc.gr + (long)rhs * kRedStride, sc.e_n);
+        if (mode == 1) {   // p_old re-conjugated against the new r
+            const double pi = warp_sum_array(sc.pi + (long)rhs * gm.pstride, gm.nrun);
+            const double rho = warp_sum_array(sc.rho + (long)rhs * kRedStride, sc.e_n);
+            be = -rho / pi;
+            al = ga / (dl + 2.0 * be * rho + be * be * pi);
+        } else {
+            be = 0.0;
+            al = ga / dl;
+        }
+    }
+    if (wr == 0 && (threadIdx.x & 31) == 0) {
+        sc.slot_out[rhs * 4 + 0] = al;
+        sc.slot_out[rhs * 4 + 1] = ga;
+        sc.slot_out[rhs * 4 + 2] = 0.0;
+    }
+    const float a = (float)al, b = (float)be, ap = (float)si[0];
+    const bool old = (mode != 2);
+    const int fold = sc.fold;
+
+    if (geo.g == 0 || Geom4<L>::G == 1) {
+        for (int s = 1; s <= gm.K; ++s) {
+            int tq = t0 + s;
+            if (tq >= gm.T) tq -= gm.T;
+            const long o = base + (long)tq * N;
+            prefetch_slice_l2<L>(r + o);
+            prefetch_slice_l2<L>(w + o);
+            if (old) {
+                prefetch_slice_l2<L>(sold + o);
+                prefetch_slice_l2<L>(pold + o);
+            }
+            if (fold) prefetch_slice_l2<L>(e + o);
+        }
+    }
+    // r' of slice t (row k of this lane); own slices also store p, s, r', x
+    auto step = [&](long o, bool own, double& gacc) -> float4 {
+        const float4 rv = ld4(r, o);
+        float4 sv = ld4(w, o);
+        if (old) sv = fma4s(b, ld4(sold, o), sv);
+        const float4 rn = fma4s(-a, sv, rv);
+        if (own) {
+            float4 pv = rv, po = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (old) {
+                po = ld4(pold, o);
+                pv = fma4s(b, po, rv);
+            }
+            st4(pnew, o, pv);
+            st4(snew, o, sv);
+            st4(rnew, o, rn);
+            if (fold) {
+                float4 xv = ld4(e, o);
+                if (fold == 2) xv = fma4s(ap, po, xv);
+                st4(e, o, fma4s(a, pv, xv));
+            }
+            gacc += (double)(rn.x * rn.x + rn.y * rn.y + rn.z * rn.z + rn.w * rn.w);
+        }
+        return rn;
+    };
+
+    double gacc = 0.0;
+    float4 W[RT], X[RT], P[RT], Y[RT];
+    {
+        const int tm = (t0 == 0) ? gm.T - 1 : t0 - 1;
+        const long o = base + (long)tm * N;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) Y[k] = step(o + geo.off(k), false, gacc);
+        c4_apply<L>(Y, geo, th);
+    }
+    {
+        const long o = base + (long)t0 * N;
+        const float sg = (t0 == 0) ? 1.0f : -1.0f;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float4 pv = step(o + geo.off(k), valid, gacc);
+            X[k] = pv;
+            const float4 d = ld4(ev, (long)t0 * N + geo.off(k));
+            W[k] = make_float4(fmaf(sg * d.x, Y[k].x, pv.x), fmaf(sg * d.y, Y[k].y, pv.y),
+                               fmaf(sg * d.z, Y[k].z, pv.z), fmaf(sg * d.w, Y[k].w, pv.w));
+        }
+        c4_apply<L>(X, geo, th);
+    }
+    double acc = 0.0;
+    for (int s = 0; s < gm.K; ++s) {
+        const int tau = t0 + s;
+        const int tp = (tau + 1 == gm.T) ? 0 : tau + 1;
+        const long op = base + (long)tp * N;
+        const float sgp = (tp == 0) ? 1.0f : -1.0f;
+        const bool own = valid && (s + 1 < gm.K);
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float4 pv = step(op + geo.off(k), own, gacc);
+            P[k] = pv;
+            float4 d = ld4(ev, (long)tp * N + geo.off(k));
+            d.x *= sgp; d.y *= sgp; d.z *= sgp; d.w *= sgp;
+            X[k] = make_float4(fmaf(d.x, X[k].x, pv.x), fmaf(d.y, X[k].y, pv.y),
+                               fmaf(d.z, X[k].z, pv.z), fmaf(d.w, X[k].w, pv.w));
+            Y[k] = make_float4(d.x * X[k].x, d.y * X[k].y, d.z * X[k].z, d.w * X[k].w);
+        }
+        c4_apply<L>(P, geo, th);
+        c4_apply_t<L>(Y, geo, th);
+        const long o = base + (long)tau * N;
+        float part = 0.0f;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            if (valid)
+                st4(wnew, o + geo.off(k), make_float4(W[k].x + Y[k].x, W[k].y + Y[k].y,
+                                                      W[k].z + Y[k].z, W[k].w + Y[k].w));
+            part = fmaf(W[k].x, W[k].x, part);
+            part = fmaf(W[k].y, W[k].y, part);
+            part = fmaf(W[k].z, W[k].z, part);
+            part = fmaf(W[k].w, W[k].w, part);
+            W[k] = X[k];
+            X[k] = P[k];
+        }
+        acc += (double)part;
+    }
+    group_store_sum<L>(acc, valid, sc.d_out + (long)rhs * gm.pstride + run);
+    __syncwarp();
+    group_store_sum<L>(gacc, valid, sc.g_out + (long)rhs * gm.pstride + run);
+}
+
+
+// ---------------------------------------------------------------------------
+// Fused FP32 CG step in the split float4 layout of cbs.cuh (L = 32): one
+// block of NW warps per unit of K slices, so each lane holds L / (4 NW) rows
+// of a slice and the per-slice chain of dependent work is NW times shorter
+// than with one warp per slice. Same arithmetic as k_cg_mtm32_v4.
+// ---------------------------------------------------------------------------
+template <int L, int NW>
+__global__ void __launch_bounds__(32 * NW) k_cg_mtm32_split(const float* __restrict__ r,
+                                                           const float* __restrict__ pold,
+                                                           float* __restrict__ pnew,
+                                                           float* __restrict__ q,
+                                                           const float* __restrict__ ev,
+                                                           MvGeom gm,
+                                                           const int* __restrict__ mask,
+                                                           const double* __restrict__ rr_new_part,
+                                                           const double* __restrict__ rr_old_part,
+                                                           int rr_stride, int rr_n, int first,
+                                                           double* __restrict__ pq_part, float th)
+{
+    constexpr int N = L * L;
+    constexpr int RT = GeomS<L, NW>::RT;
+    __shared__ SplitX<L, NW> xs;
+    __shared__ double red[NW];
+    __shared__ float s_bt;
+    const GeomS<L, NW> geo;
+    const int unit = blockIdx.x;
+    const int rhs = unit / gm.nrun;
+    if (rhs >= gm.n_rhs) return;
+    if (mask != nullptr && mask[rhs] == 0) return;
+    const int run = unit - rhs * gm.nrun;
+    const int t0 = run * gm.K;
+    const long base = (long)rhs * gm.T * N;
+    int par = 0;
+
+    // the unit's later slices go to L2 while beta is formed
+    if (threadIdx.x < 32) {
+        for (int s = 1; s <= gm.K; ++s) {
+            int tq = t0 + s;
+            if (tq >= gm.T) tq -= gm.T;
+            prefetch_slice_l2<L>(r + base + (long)tq * N);
+            if (!first) prefetch_slice_l2<L>(pold + base + (long)tq * N);
+        }
+        float bt = 0.0f;
+        if (!first) {
+            const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
+            const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
+            bt = (float)(rn / ro);
+        }
+        if (threadIdx.x == 0) s_bt = bt;
+    }
+    __syncthreads();
+    const float bt = s_bt;
+
+    float4 W[RT], X[RT], P[RT], Y[RT];
+    {
+        const int tm = (t0 == 0) ? gm.T - 1 : t0 - 1;
+        const long o = base + (long)tm * N;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) Y[k] = fma4s(bt, ld4(pold, o + geo.off(k)), ld4(r, o + geo.off(k)));
+        cs_apply<L, NW>(Y, geo, th, xs, par);
+    }
+    {
+        const long o = base + (long)t0 * N;
+        const float sg = (t0 == 0) ? 1.0f : -1.0f;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float4 pv = fma4s(bt, ld4(pold, o + geo.off(k)), ld4(r, o + geo.off(k)));
+            if (pnew != nullptr) st4(pnew, o + geo.off(k), pv);
+            X[k] = pv;
+            const float4 d = ld4(ev, (long)t0 * N + geo.off(k));
+            W[k] = make_float4(fmaf(sg * d.x, Y[k].x, pv.x), fmaf(sg * d.y, Y[k].y, pv.y),
+                               fmaf(sg * d.z, Y[k].z, pv.z), fmaf(sg * d.w, Y[k].w, pv.w));
+        }
+        cs_apply<L, NW>(X, geo, th, xs, par);
+    }
+    double acc = 0.0;
+    for (int s = 0; s < gm.K; ++s) {
+        const int tau = t0 + s;
+        const int tp = (tau + 1 == gm.T) ? 0 : tau + 1;
+        const long op = base + (long)tp * N;
+        const float sgp = (tp == 0) ? 1.0f : -1.0f;
+        const bool own = (s + 1 < gm.K) && pnew != nullptr;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float4 pv = fma4s(bt, ld4(pold, op + geo.off(k)), ld4(r, op + geo.off(k)));
+            if (own) st4(pnew, op + geo.off(k), pv);
+            P[k] = pv;
+            float4 d = ld4(ev, (long)tp * N + geo.off(k));
+            d.x *= sgp; d.y *= sgp; d.z *= sgp; d.w *= sgp;
+            X[k] = make_float4(fmaf(d.x, X[k].x, pv.x), fmaf(d.y, X[k].y, pv.y),
+                               fmaf(d.z, X[k].z, pv.z), fmaf(d.w, X[k].w, pv.w));
+            Y[k] = make_float4(d.x * X[k].x, d.y * X[k].y, d.z * X[k].z, d.w * X[k].w);
+        }
+        cs_apply<L, NW>(P, geo, th, xs, par);
+        cs_apply_t<L, NW>(Y, geo, th, xs, par);
+        const long o = base + (long)tau * N;
+        float part = 0.0f;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            st4(q, o + geo.off(k), make_float4(W[k].x + Y[k].x, W[k].y + Y[k].y,
+                                               W[k].z + Y[k].z, W[k].w + Y[k].w));
+            part = fmaf(W[k].x, W[k].x, part);
+            part = fmaf(W[k].y, W[k].y, part);
+            part = fmaf(W[k].z, W[k].z, part);
+            part = fmaf(W[k].w, W[k].w, part);
+            W[k] = X[k];
+            X[k] = P[k];
+        }
+        acc += (double)part;
+    }
+    if (pq_part != nullptr) {
+        acc = warp_sum(acc);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NW; ++w) t += red[w];
+            pq_part[(long)rhs * gm.pstride + run] = t;
+        }
+    }
+}
+
 template <int L>
 int blocks_for(const hol_ctx* c, const MvGeom& g)
 {
@@ -572,12 +1016,59 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
 {
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
+    if constexpr (L == 32) {
+        if (c->mv_vec == 4 || c->mv_vec == 5) {   // split layout, 2 or 4 warps per unit
+            const int units = g.nrun * g.n_rhs;
+            if (c->mv_vec == 4)
+                k_cg_mtm32_split<L, 2><<<units, 64, 0, s>>>(r, pold, pnew, q, c->ev32, g, mask,
+                                                             rr_new, rr_old, rr_stride, rr_n,
+                                                             first, pq_part, (float)c->th);
+            else
+                k_cg_mtm32_split<L, 4><<<units, 128, 0, s>>>(r, pold, pnew, q, c->ev32, g, mask,
+                                                              rr_new, rr_old, rr_stride, rr_n,
+                                                              first, pq_part, (float)c->th);
+            HOL_CHECK_LAUNCH("k_cg_mtm32_split");
+            return HOL_OK;
+        }
+    }
     if constexpr (L % 8 == 0) {
+        if (c->mv_vec == 3) {
+            constexpr int S = 3;
+            const int wpb = 4;
+            const size_t sm = (size_t)wpb * S * 2 * (L / 4) * 32 * sizeof(float4);
+            // resident blocks, queried once per instantiation (one GPU model per process)
+            static std::atomic<int> resident(0);
+            if (resident.load() == 0) {
+                int per_sm = 0, sms = 0;
+                // the static reduction scratch counts against the default 48 KB
+                // dynamic limit, so the limit is always raised explicitly
+                HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_mtm32_v4s<L, S>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                HOL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &per_sm, k_cg_mtm32_v4s<L, S>, 32 * wpb, sm));
+                HOL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+                resident.store((per_sm < 1 ? 1 : per_sm) * sms);
+            }
+            const int need = g.wpr * g.n_rhs;                 // warp-units
+            int blocks = resident.load();
+            if ((long)blocks * wpb > need) blocks = (need + wpb - 1) / wpb;
+            k_cg_mtm32_v4s<L, S><<<blocks, 32 * wpb, sm, s>>>(
+                r, pold, pnew, q, c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first, pq_part,
+                (float)c->th, blocks * wpb);
+            HOL_CHECK_LAUNCH("k_cg_mtm32_v4s");
+            return HOL_OK;
+        }
         if (c->mv_vec == 2) {
             const size_t sm = (size_t)c->mv_warps * 2 * 2 * (L / 4) * 32 * sizeof(float4);
-            if (sm > 48 * 1024)
+            // raised once per instantiation to the largest size any block shape needs
+            // (the static reduction scratch counts against the default limit)
+            static std::atomic<int> limit(0);
+            if ((int)sm > limit.load()) {
+                const int most = 4 * 2 * 2 * (L / 4) * 32 * (int)sizeof(float4);
                 HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_mtm32_v4a<L>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, most));
+                limit.store(most);
+            }
             k_cg_mtm32_v4a<L><<<nb, nt, sm, s>>>(r, pold, pnew, q, c->ev32, g, mask, rr_new, rr_old,
                                                   rr_stride, rr_n, first, pq_part, (float)c->th);
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4a");
@@ -596,6 +1087,43 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
     return HOL_OK;
 }
 
+
+template <int L>
+int run_cg_merged(const hol_ctx* c, const float* r, const float* w, const float* pold,
+                  const float* sold, float* e, float* pnew, float* snew, float* rnew, float* wnew,
+                  int n_rhs, const int* mask, const MergedScal& sc, cudaStream_t s)
+{
+    if constexpr (L % 8 == 0) {
+        const MvGeom g = make_geom<L>(c, n_rhs);
+        const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
+        k_cg_merged<L><<<nb, nt, 0, s>>>(r, w, pold, sold, e, pnew, snew, rnew, wnew, c->ev32, g,
+                                         mask, sc, (float)c->th);
+        HOL_CHECK_LAUNCH("k_cg_merged");
+        return HOL_OK;
+    } else {
+        return set_error(HOL_EINVAL, "merged CG needs L %% 8 == 0 (L=%d)", c->L);
+    }
+}
+
+}  // namespace
+
+int launch_cg_merged(const hol_ctx* c, const float* r, const float* w, const float* pold,
+                     const float* sold, float* e, float* pnew, float* snew, float* rnew,
+                     float* wnew, int n_rhs, const int* mask, const MergedScal& sc,
+                     cudaStream_t s)
+{
+    switch (c->L) {
+#define X(LL)                                                                                  \
+    case LL:                                                                                   \
+        return run_cg_merged<LL>(c, r, w, pold, sold, e, pnew, snew, rnew, wnew, n_rhs, mask, \
+                                 sc, s);
+        HOL_FOR_EACH_L(X)
+#undef X
+    }
+    return set_error(HOL_EINVAL, "unsupported L=%d", c->L);
+}
+
+namespace {
 }  // namespace
 
 int matvec_units(const hol_ctx* c, int n_rhs)

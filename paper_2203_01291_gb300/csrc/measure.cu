@@ -233,7 +233,7 @@ struct Meas {
         const void* fns[] = {(const void*)k_m_tau_fwd, (const void*)k_m_tau_inv_half,
                              (const void*)k_m_tau_inv_full};
         for (const void* f : fns)
-            if (sm_t > 48 * 1024)
+            if (sm_t > 32 * 1024)   // leaves room for static shared memory
                 HOL_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)sm_t));
         return HOL_OK;

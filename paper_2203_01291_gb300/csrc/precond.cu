@@ -616,7 +616,7 @@ int kpm_threads(const hol_ctx* c)
 template <typename R>
 int set_smem_attr(const void* fn, size_t bytes)
 {
-    if (bytes > 48 * 1024)
+    if (bytes > 32 * 1024)   // leaves room for static shared memory
         HOL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     return HOL_OK;
 }
@@ -738,7 +738,7 @@ int precond_alloc(hol_ctx* c)
 int kpm_setup(hol_ctx* c, cudaStream_t s)
 {
     const size_t sm = 2 * (size_t)c->kpm.max_np * sizeof(double2);
-    if (sm > 48 * 1024)
+    if (sm > 32 * 1024)   // leaves room for static shared memory under the default limit
         HOL_CUDA(cudaFuncSetAttribute((const void*)k_kpm_coeffs,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_kpm_coeffs<<<c->T / 2, 128, sm, s>>>(c->scal, c->T, c->kpm.max_np, c->kpm.np, c->kpm.coef,

@@ -1,9 +1,14 @@
 // Launch-shape autotuner for the fused FP32 M^T M kernel of the CG iteration.
 //
 // Candidates: K (tau slices streamed per lane group) among the divisors
-// {1, 2, 4, 5, 8, 10} of Ltau, 1, 2 or 4 warps per block, and for L % 8 == 0
-// the float4 layout with cp.async prefetch (2), without (1), or the scalar
-// register layout (0). Each candidate is timed with CUDA
+// {1, 2, 4, 5, 8, 10} of Ltau, 1, 2 or 4 warps per block, for L = 32 the
+// split float4 layout with 4 or 2 warps per slice (5, 4), and for L % 8 == 0
+// the streaming float4 kernel with a cp.async ring across units (3), the
+// float4 layout with cp.async prefetch (2), without (1), or the scalar
+// register layout (0). The split and streaming kernels fix their own block
+// shapes, so they are timed once per K. With the merged CG on, the merged iteration kernel is
+// timed instead over K and warps (its layout is fixed). Each candidate is
+// timed with CUDA
 // events on the caller's stream (2 warm-up and 10 timed launches on the
 // context's scratch vectors) and the fastest is kept in the context for every
 // later call. Candidates whose per-unit partial sums would not fit the
@@ -32,23 +37,54 @@ extern "C" int hol_tune(hol_ctx* c, int n_rhs, int* best_k, int* best_warps, int
     int bk = old_k, bw = old_w, bv = old_v;
     double bms = 1e30;
     int rc = HOL_OK;
-    for (int vec = (c->L % 8 == 0) ? 2 : 0; vec >= 0 && !rc; --vec) {
+    // with the merged CG on, the merged iteration kernel is what the solver
+    // launches: time it (its layout is fixed, so only K and warps vary)
+    const bool merged = c->merged != 0;
+    MergedScal sc;
+    if (merged) {
+        HOL_CUDA(cudaMemsetAsync(c->part, 0, kBanks * c->part_len * sizeof(double), s));
+        HOL_CUDA(cudaMemsetAsync(c->cgs, 0, 8 * c->p.max_rhs * sizeof(double), s));
+        sc.slot_in = c->cgs;
+        sc.slot_out = c->cgs + 4 * c->p.max_rhs;
+        sc.g_in = c->part;
+        sc.d_in = c->part + c->part_len;
+        sc.g_out = c->part + 2 * c->part_len;
+        sc.d_out = c->part + 3 * c->part_len;
+        sc.gr = c->part + 4 * c->part_len;
+        sc.rho = c->part + 5 * c->part_len;
+        sc.e_n = 1;
+        sc.pi = c->part + 6 * c->part_len;
+        sc.fold = 0;
+    }
+    auto launch = [&](int r) -> int {
+        if (!merged)
+            return launch_cg_mtm32(c, c->v32a, c->v32a, nullptr, c->v32b, n_rhs, nullptr, nullptr,
+                                   nullptr, 0, 0, 1, nullptr, s);
+        sc.fold = (r & 1) ? 2 : 0;
+        return launch_cg_merged(c, c->v32a, c->v32b, c->v32c, c->v32d, c->v32e, c->v32f, c->v32g,
+                                c->v32h, c->v32i, n_rhs, nullptr, sc, s);
+    };
+    if (merged) {   // inputs of the merged kernel: zero vectors
+        float* bufs[4] = {c->v32b, c->v32c, c->v32d, c->v32e};
+        for (float* b : bufs)
+            HOL_CUDA(cudaMemsetAsync(b, 0, (size_t)n_rhs * c->n * sizeof(float), s));
+    }
+    const int vec_hi = merged ? c->mv_vec : (c->L == 32 ? 5 : (c->L % 8 == 0) ? 3 : 0);
+    const int vec_lo = merged ? c->mv_vec : 0;
+    for (int vec = vec_hi; vec >= vec_lo && !rc; --vec) {
         for (int ki = 0; ki < 6 && !rc; ++ki) {
             const int k = ks[ki];
             if (c->T % k) continue;
             c->mv_k = k;
             if ((long)matvec_pstride(c) * c->p.max_rhs > c->part_len) continue;
             for (int wi = 0; wi < 3 && !rc; ++wi) {
+                if (vec >= 3 && wi > 0 && !merged) break;   // fixed block shapes
                 c->mv_warps = ws[wi];
                 c->mv_vec = vec;
-                for (int r = 0; r < 2 && !rc; ++r)
-                    rc = launch_cg_mtm32(c, c->v32a, c->v32a, nullptr, c->v32b, n_rhs, nullptr,
-                                         nullptr, nullptr, 0, 0, 1, nullptr, s);
+                for (int r = 0; r < 2 && !rc; ++r) rc = launch(r);
                 if (rc) break;
                 cudaEventRecord(e0, s);
-                for (int r = 0; r < 10 && !rc; ++r)
-                    rc = launch_cg_mtm32(c, c->v32a, c->v32a, nullptr, c->v32b, n_rhs, nullptr,
-                                         nullptr, nullptr, 0, 0, 1, nullptr, s);
+                for (int r = 0; r < 10 && !rc; ++r) rc = launch(r);
                 cudaEventRecord(e1, s);
                 if (rc) break;
                 if (cudaEventSynchronize(e1) != cudaSuccess) {

@@ -221,6 +221,140 @@ def test_autotuner_choice_keeps_results(L, T):
         assert max(MF.rel_residual(w, x, v[k], sol.cpu().numpy()[k]) for k in range(3)) < 1.01e-8
 
 
+LAYOUT_CASES = [(32, 40, 2), (32, 30, 5), (16, 30, 3), (8, 24, 1), (24, 12, 4)]
+
+
+@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("L,T,K", LAYOUT_CASES)
+def test_fused_mtm_every_layout(layout, L, T, K):
+    """Each register layout of the fused FP32 M^T M (scalar, float4, float4
+    with prefetch, streaming float4, split float4 over 2 or 4 warps) and each
+    slice grouping gives the oracle's M^T M, and a masked mixed solve
+    (right-hand sides of different scale converge at different iterations)
+    stays certified."""
+    if layout >= 4 and L != 32:
+        pytest.skip("split layouts are for L = 32")
+    w, x = _field(L, T, seed=21)
+    nr = 5
+    v = hi.gaussian_vectors(w, nr, seed=22) * np.array([1.0, 1e-3, 1e3, 1.0, 1e-6])[:, None, None]
+    ref = np.stack([MF.MTM_apply(w, x, a) for a in v])
+    with _ctx(w, nr) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        ctx.set_option("slices_per_group", K)
+        ctx.set_option("layout", layout)
+        vt = torch.tensor(v, device=DEV, dtype=torch.float32)
+        out = torch.empty_like(vt)
+        ctx.fermion_matvec(hg.HOL_OP_MTM, vt, out)
+        got = out.cpu().double().numpy()
+        for k in range(nr):
+            assert _rel(got[k], ref[k]) < 3e-6
+        bt = torch.tensor(v, device=DEV)
+        sol = torch.empty_like(bt)
+        its, res = ctx.cg_solve(bt, sol, tol=1e-8, prec=hg.HOL_F32, reliable_every=30)
+        s = sol.cpu().numpy()
+    assert np.all(res < 1e-8)
+    assert max(MF.rel_residual(w, x, v[k], s[k]) for k in range(nr)) < 1.01e-8
+
+
+@pytest.mark.parametrize("layout,K", [(3, 1), (3, 2), (4, 2), (5, 4)])
+def test_vector_layouts_full_size(layout, K):
+    """The streaming layout (resident warps walk several of the 3200 or 1600
+    units each) and the split layouts at L=32, Ltau=200 with 16 right-hand
+    sides: the fused M^T M matches the oracle on every right-hand side."""
+    w = hi.WORKLOADS["big32"]
+    x = hi.phonon_field(w)
+    v = hi.gaussian_vectors(w, w.n_rhs, seed=23)
+    with _ctx(w, w.n_rhs) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        ctx.set_option("slices_per_group", K)
+        ctx.set_option("layout", layout)
+        vt = torch.tensor(v, device=DEV, dtype=torch.float32)
+        out = torch.empty_like(vt)
+        ctx.fermion_matvec(hg.HOL_OP_MTM, vt, out)
+        got = out.cpu().double().numpy()
+    for k in range(w.n_rhs):
+        assert _rel(got[k], MF.MTM_apply(w, x, v[k])) < 3e-6
+
+
+MERGED_CASES = [(8, 24, 1, 7, 20), (16, 30, 3, 10, 50), (24, 12, 4, 3, 9), (32, 40, 2, 10, 50),
+                (32, 30, 5, 1, 5), (16, 8, 2, 4, 1000)]
+
+
+@pytest.mark.parametrize("L,T,K,check_every,reliable_every", MERGED_CASES)
+def test_merged_cg_certified(L, T, K, check_every, reliable_every):
+    """The one-kernel-per-iteration mixed CG (Chronopoulos-Gear recurrences,
+    deferred x updates, restarts with recomputed A r and A p) reaches the
+    certified residual on right-hand sides of very different scale (they
+    leave the active set at different chunks), in about as many iterations
+    as the two-kernel solver."""
+    w, x = _field(L, T, seed=31)
+    nr = 5
+    v = hi.gaussian_vectors(w, nr, seed=32) * np.array([1.0, 1e-3, 1e3, 1.0, 1e-6])[:, None, None]
+    with _ctx(w, nr) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        ctx.set_option("slices_per_group", K)
+        bt = torch.tensor(v, device=DEV)
+        ref = torch.empty_like(bt)
+        its0, res0 = ctx.cg_solve(bt, ref, tol=1e-8, prec=hg.HOL_F32,
+                                  reliable_every=reliable_every, check_every=check_every)
+        ctx.set_option("merged_cg", 1)
+        sol = torch.empty_like(bt)
+        its1, res1 = ctx.cg_solve(bt, sol, tol=1e-8, prec=hg.HOL_F32,
+                                  reliable_every=reliable_every, check_every=check_every)
+        s = sol.cpu().numpy()
+    assert np.all(res1 < 1e-8)
+    for k in range(nr):
+        assert MF.rel_residual(w, x, v[k], s[k]) < 1.01e-8
+    assert np.all(np.asarray(its1) <= 1.5 * np.asarray(its0) + 2 * check_every + 10), (its0, its1)
+
+
+def test_merged_cg_big32_certified_by_oracle():
+    """The benchmark solve with the merged kernel: 16 right-hand sides
+    b = M^T R at L=32, Ltau=200 to 1e-8, residuals recomputed by the oracle."""
+    w = hi.WORKLOADS["big32"]
+    x = hi.phonon_field(w)
+    R = hi.gaussian_vectors(w, w.n_rhs, seed=2)
+    with _ctx(w, w.n_rhs) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        ctx.set_option("merged_cg", 1)
+        Rt = torch.tensor(R, device=DEV)
+        bt = torch.empty_like(Rt)
+        ctx.fermion_matvec(hg.HOL_OP_MT, Rt, bt)
+        b = bt.cpu().numpy()
+        vm = torch.empty_like(bt)
+        its, res = ctx.cg_solve(bt, vm, tol=1e-8, prec=hg.HOL_F32, reliable_every=50,
+                                check_every=10)
+        vm = vm.cpu().numpy()
+    for k in range(w.n_rhs):
+        assert res[k] < 1e-8
+        assert MF.rel_residual(w, x, b[k], vm[k]) < 1.01e-8
+
+
+def test_merged_cg_option_rules():
+    w, x = _field(12, 10)
+    with _ctx(w, 2) as ctx:
+        with pytest.raises(hg.HolError):
+            ctx.set_option("merged_cg", 1)             # needs L % 8 == 0
+    w, x = _field(8, 10)
+    with _ctx(w, 2) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        ctx.set_option("merged_cg", 1)
+        assert ctx.get_option("merged_cg") == 1
+        # FP64 and preconditioned solves keep the two-kernel loop
+        bt = torch.tensor(hi.gaussian_vectors(w, 2, seed=3), device=DEV)
+        sol = torch.empty_like(bt)
+        its, res = ctx.cg_solve(bt, sol, tol=1e-10, prec=hg.HOL_F64)
+        assert np.all(res < 1e-10)
+        # the autotuner times the merged kernel; the tuned solve stays certified
+        choice = ctx.tune(2)
+        assert w.Ltau % choice["slices_per_group"] == 0
+        assert ctx.get_option("slices_per_group") == choice["slices_per_group"]
+        its, res = ctx.cg_solve(bt, sol, tol=1e-8, prec=hg.HOL_F32)
+        assert np.all(res < 1e-8)
+        v = bt.cpu().numpy()
+        assert max(MF.rel_residual(w, x, v[k], sol.cpu().numpy()[k]) for k in range(2)) < 1.01e-8
+
+
 def test_invalid_shapes_rejected():
     for L, T in ((3, 8), (34, 8), (8, 7), (2, 8)):
         with pytest.raises(hg.HolError):
