@@ -43,7 +43,7 @@ METRIC = "CG solves/s (M^T M v = b, certified FP64 residual 1e-8) at L=32, Ltau=
 WORKLOAD = hi.WORKLOADS["big32"]
 TOL = 1e-8
 RELIABLE_EVERY = 50
-TIMER_STRIDE = 8          # CUDA events around one in every 8 launches of each kernel class
+TIMER_STRIDE = 32         # CUDA events around one in every 32 launches of each kernel class
 
 
 def peaks():

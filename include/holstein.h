@@ -329,6 +329,10 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  *                       slice spread over 2 / 4 warps (L == 32)
  *   "kpm_registers"     register KPM kernel for FP32, L = 16 or 32 (0/1)
  *   "persistent_cg"     plain mixed CG chunks in one cooperative launch (0/1)
+ *   "pdl"               programmatic dependent launch of the CG iteration
+ *                       kernels: each may be scheduled while its predecessor
+ *                       finishes and waits on the device for its results
+ *                       (0/1, default 1)
  *   "merged_cg"         plain mixed CG as one fused kernel per iteration
  *                       (single-reduction Chronopoulos-Gear recurrences of
  *                       the same CG, Eq. (CG); L % 8 == 0; allocates three

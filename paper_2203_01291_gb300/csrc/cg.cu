@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restr
                                                    int pq_n, const double* __restrict__ dz_part,
                                                    int dz_n, double* __restrict__ rr_out)
 {
+    pdl_wait();      // p, q and the partials come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     const int rhs = blockIdx.y;
     if (mask != nullptr && mask[rhs] == 0) return;
     // one warp forms alpha (FP64 sums are slow on this part: doing it in
@@ -322,6 +324,33 @@ int rows_to_host(hol_ctx* c, const double* bank, int cnt, int n_rhs, double* hos
     return HOL_OK;
 }
 
+// Enqueue per-rhs sums of a bank into a pinned host slot and record `ev`
+// when they have landed (the solver keeps the GPU one chunk ahead of these
+// reads, see cg_run).
+int rows_enqueue(const double* bank, int cnt, int stride, int n_rhs, double* red, double* host,
+                 cudaEvent_t ev, cudaStream_t s)
+{
+    k_rows<<<ceil_div(32L * n_rhs, 256), 256, 0, s>>>(bank, cnt, stride, n_rhs, red);
+    HOL_CHECK_LAUNCH("k_rows");
+    HOL_CUDA(cudaMemcpyAsync(host, red, n_rhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HOL_CUDA(cudaEventRecord(ev, s));
+    return HOL_OK;
+}
+
+struct EventPair {
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int create()
+    {
+        for (cudaEvent_t& e : ev) HOL_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        return HOL_OK;
+    }
+    ~EventPair()
+    {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
 }  // namespace
 
 int elementwise_blocks(const hol_ctx* c)
@@ -423,6 +452,11 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
         launch_cg_persist(c, r32, p32[0], p32[1], e32, n_rhs, act_d, B.pq, B.dz[0], B.dz[1], 0,
                           nb2, nb2, 0, 1, 1, 1, s) == HOL_OK;
     const int nrun = c->T / c->mv_k;
+    const long R = c->p.max_rhs;
+    EventPair evp;
+    if ((rc = evp.create())) return rc;
+    int q = 0;              // host slot of the estimate read of this chunk
+    bool have_prev = false; // an unexamined estimate of the previous chunk
     while (n_active > 0 && k_it < o->max_iter) {
         int chunk = chk;
         if (chunk > o->max_iter - k_it) chunk = o->max_iter - k_it;
@@ -450,8 +484,8 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                 timer_stop(c, KT_OPERATOR, s);
                 pp = 1 - pp;
                 timer_start(c, KT_UPDATE, s, n_active * nd * 24.0);
-                k_cg_update<float><<<g2, 256, 0, s>>>(e32, r32, p32[pp], q32, n, act_d, B.pq,
-                                                      pstride, pq_n, B.dz[cur], dz_n, rr_dst);
+                HOL_CUDA(launch_pdl(c->pdl, k_cg_update<float>, g2, 256, 0, s, e32, r32, p32[pp],
+                                    q32, n, act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst));
             } else {
                 BetaSrc bs{B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first};
                 timer_start(c, KT_OPERATOR, s, n_active * nd * 48.0 + nd * 16.0);
@@ -473,14 +507,47 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
             first = 0;
         }
         k_it += chunk;
-        if ((rc = rows_to_host(c, est_bank(cur), pc ? nb2 : cnt[cur], n_rhs, hb, s))) return rc;
+        // The recursive residual of this chunk is read asynchronously. Unless
+        // a reliable update is due by count, the next chunk is launched at
+        // once and this estimate is examined one chunk later (the GPU never
+        // waits for the host); an estimate below tol makes the end of the
+        // chunk then in flight a synchronisation point.
+        double* est_h = hb + (2 + q) * R;
+        if ((rc = rows_enqueue(est_bank(cur), pc ? nb2 : cnt[cur], kRedStride, n_rhs,
+                               B.red + (1 + q) * R, est_h, evp.ev[q], s)))
+            return rc;
+        bool sync = k_it >= o->max_iter;
+        for (int k = 0; k < n_rhs; ++k) {
+            if (!act_h[k]) continue;
+            it[k] += chunk;
+            since[k] += chunk;
+            if (since[k] >= rel_every) sync = true;
+        }
+        if (!sync && have_prev) {
+            HOL_CUDA(cudaEventSynchronize(evp.ev[1 - q]));
+            const double* prev = hb + (2 + (1 - q)) * R;
+            for (int k = 0; k < n_rhs; ++k) {
+                if (!act_h[k]) continue;
+                const double est = sqrt(prev[k]) / bnorm[k];
+                if (!isfinite(est))
+                    return set_error(HOL_ENUMERIC,
+                                     "cg_solve: non-finite residual (rhs %d, iter %d)", k,
+                                     it[k] - chunk);
+                if (est < o->tol) sync = true;
+            }
+        }
+        if (!sync) {
+            have_prev = true;
+            q = 1 - q;
+            continue;
+        }
+        HOL_CUDA(cudaEventSynchronize(evp.ev[q]));
+        have_prev = false;
         int n_rel = 0;
         for (int k = 0; k < n_rhs; ++k) {
             rel_h[k] = 0;
             if (!act_h[k]) continue;
-            it[k] += chunk;
-            since[k] += chunk;
-            const double est = sqrt(hb[k]) / bnorm[k];
+            const double est = sqrt(est_h[k]) / bnorm[k];
             if (!isfinite(est))
                 return set_error(HOL_ENUMERIC, "cg_solve: non-finite residual (rhs %d, iter %d)",
                                  k, it[k]);

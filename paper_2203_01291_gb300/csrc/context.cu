@@ -189,6 +189,7 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     c->kpm_reg = 1;
     c->persist = 0;
     c->merged = 0;
+    c->pdl = 1;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         free_ctx(c);
         return set_error(HOL_ECUDA, "hol_create: no CUDA device");
@@ -395,6 +396,8 @@ extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
         c->kpm_reg = value ? 1 : 0;
     } else if (is("persistent_cg")) {
         c->persist = value ? 1 : 0;
+    } else if (is("pdl")) {
+        c->pdl = value ? 1 : 0;
     } else if (is("merged_cg")) {
         if (value && c->L % 8)
             return set_error(HOL_EINVAL, "hol_set_option: merged_cg needs L % 8 == 0");
@@ -425,6 +428,7 @@ extern "C" int hol_get_option(const hol_ctx* c, const char* name, int* value)
     else if (is("kpm_registers")) *value = c->kpm_reg;
     else if (is("persistent_cg")) *value = c->persist;
     else if (is("merged_cg")) *value = c->merged;
+    else if (is("pdl")) *value = c->pdl;
     else return set_error(HOL_EINVAL, "hol_get_option: unknown option '%s'", name);
     return HOL_OK;
 }

@@ -31,6 +31,39 @@ int cuda_error(cudaError_t e, const char* what);
 
 void count_launch();
 
+// Programmatic dependent launch. A kernel launched with launch_pdl may be
+// scheduled while the previous kernel of its stream is still running; it
+// must call pdl_wait() before touching memory that kernel writes (the wait
+// returns once that kernel has completed and its writes are visible; it is
+// a no-op for a kernel launched normally). pdl_trigger() lets the next
+// PDL-launched kernel be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;\n" :::);
+}
+// Triggers the dependent launch when the thread leaves the kernel (at any
+// return), i.e. once this block's work is issued.
+struct PdlTriggerAtExit {
+    __device__ __forceinline__ ~PdlTriggerAtExit() { pdl_trigger(); }
+};
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t s, Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Optional CUDA-event timing of kernel classes (hol_timer_* entry points).
 enum TimerClass { KT_OPERATOR = 0, KT_UPDATE = 1, KT_FORCE = 2, KT_PRECOND = 3, KT_OTHER = 4,
                   KT_COUNT = 5 };
@@ -138,6 +171,7 @@ struct hol_ctx {
     int kpm_reg;         // use the register KPM kernel (FP32, L = 16 or 32)
     int persist;         // use the persistent fused CG kernel when it fits
     int merged;          // mixed plain CG as one fused kernel per iteration
+    int pdl;             // programmatic dependent launch of the CG kernels
 };
 
 namespace hol {

@@ -172,6 +172,8 @@ __global__ void __launch_bounds__(128) k_cg_mtm32(const float* __restrict__ r,
                                                   int rr_stride, int rr_n, int first,
                                                   double* __restrict__ pq_part, float th)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     constexpr int N = L * L;
     const LaneGeom<L> geo;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -273,6 +275,8 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
                                                      int rr_stride, int rr_n, int first,
                                                      double* __restrict__ pq_part, float th)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     constexpr int N = L * L;
     constexpr int RT = L / 4;
     const Geom4<L> geo;
@@ -391,6 +395,8 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
                                                          int rr_stride, int rr_n, int first,
                                                          double* __restrict__ pq_part, float th)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     constexpr int N = L * L;
     constexpr int RT = L / 4;
     extern __shared__ __align__(16) float4 ring[];   // [warp][slot][array][RT][32]
@@ -520,6 +526,8 @@ __global__ void __launch_bounds__(128, 2) k_cg_mtm32_v4s(const float* __restrict
                                                         double* __restrict__ pq_part, float th,
                                                         int total_warps)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     constexpr int N = L * L;
     constexpr int RT = L / 4;
     extern __shared__ __align__(16) float4 ring[];   // [warp][stage][array][RT][32]
@@ -673,6 +681,8 @@ __global__ void __launch_bounds__(128, 3) k_cg_merged(
     const float* __restrict__ ev, MvGeom gm, const int* __restrict__ mask, MergedScal sc,
     float th)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     constexpr int N = L * L;
     constexpr int RT = L / 4;
     const Geom4<L> geo;
@@ -837,6 +847,8 @@ __global__ void __launch_bounds__(32 * NW) k_cg_mtm32_split(const float* __restr
                                                            int rr_stride, int rr_n, int first,
                                                            double* __restrict__ pq_part, float th)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     constexpr int N = L * L;
     constexpr int RT = GeomS<L, NW>::RT;
     __shared__ SplitX<L, NW> xs;
@@ -1020,13 +1032,13 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
         if (c->mv_vec == 4 || c->mv_vec == 5) {   // split layout, 2 or 4 warps per unit
             const int units = g.nrun * g.n_rhs;
             if (c->mv_vec == 4)
-                k_cg_mtm32_split<L, 2><<<units, 64, 0, s>>>(r, pold, pnew, q, c->ev32, g, mask,
-                                                             rr_new, rr_old, rr_stride, rr_n,
-                                                             first, pq_part, (float)c->th);
+                HOL_CUDA(launch_pdl(c->pdl, k_cg_mtm32_split<L, 2>, units, 64, 0, s, r, pold, pnew,
+                                    q, c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first,
+                                    pq_part, (float)c->th));
             else
-                k_cg_mtm32_split<L, 4><<<units, 128, 0, s>>>(r, pold, pnew, q, c->ev32, g, mask,
-                                                              rr_new, rr_old, rr_stride, rr_n,
-                                                              first, pq_part, (float)c->th);
+                HOL_CUDA(launch_pdl(c->pdl, k_cg_mtm32_split<L, 4>, units, 128, 0, s, r, pold, pnew,
+                                    q, c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first,
+                                    pq_part, (float)c->th));
             HOL_CHECK_LAUNCH("k_cg_mtm32_split");
             return HOL_OK;
         }
@@ -1052,9 +1064,9 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
             const int need = g.wpr * g.n_rhs;                 // warp-units
             int blocks = resident.load();
             if ((long)blocks * wpb > need) blocks = (need + wpb - 1) / wpb;
-            k_cg_mtm32_v4s<L, S><<<blocks, 32 * wpb, sm, s>>>(
-                r, pold, pnew, q, c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first, pq_part,
-                (float)c->th, blocks * wpb);
+            HOL_CUDA(launch_pdl(c->pdl, k_cg_mtm32_v4s<L, S>, blocks, 32 * wpb, sm, s, r, pold,
+                                pnew, q, c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first,
+                                pq_part, (float)c->th, blocks * wpb));
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4s");
             return HOL_OK;
         }
@@ -1069,20 +1081,22 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, most));
                 limit.store(most);
             }
-            k_cg_mtm32_v4a<L><<<nb, nt, sm, s>>>(r, pold, pnew, q, c->ev32, g, mask, rr_new, rr_old,
-                                                  rr_stride, rr_n, first, pq_part, (float)c->th);
+            HOL_CUDA(launch_pdl(c->pdl, k_cg_mtm32_v4a<L>, nb, nt, sm, s, r, pold, pnew, q,
+                                c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first, pq_part,
+                                (float)c->th));
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4a");
             return HOL_OK;
         }
         if (c->mv_vec) {
-            k_cg_mtm32_v4<L><<<nb, nt, 0, s>>>(r, pold, pnew, q, c->ev32, g, mask, rr_new, rr_old,
-                                                rr_stride, rr_n, first, pq_part, (float)c->th);
+            HOL_CUDA(launch_pdl(c->pdl, k_cg_mtm32_v4<L>, nb, nt, 0, s, r, pold, pnew, q,
+                                c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first, pq_part,
+                                (float)c->th));
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4");
             return HOL_OK;
         }
     }
-    k_cg_mtm32<L><<<nb, nt, 0, s>>>(r, pold, pnew, q, c->ev32, g, mask, rr_new, rr_old, rr_stride,
-                                     rr_n, first, pq_part, (float)c->th);
+    HOL_CUDA(launch_pdl(c->pdl, k_cg_mtm32<L>, nb, nt, 0, s, r, pold, pnew, q, c->ev32, g, mask,
+                        rr_new, rr_old, rr_stride, rr_n, first, pq_part, (float)c->th));
     HOL_CHECK_LAUNCH("k_cg_mtm32");
     return HOL_OK;
 }
@@ -1096,8 +1110,8 @@ int run_cg_merged(const hol_ctx* c, const float* r, const float* w, const float*
     if constexpr (L % 8 == 0) {
         const MvGeom g = make_geom<L>(c, n_rhs);
         const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-        k_cg_merged<L><<<nb, nt, 0, s>>>(r, w, pold, sold, e, pnew, snew, rnew, wnew, c->ev32, g,
-                                         mask, sc, (float)c->th);
+        HOL_CUDA(launch_pdl(c->pdl, k_cg_merged<L>, nb, nt, 0, s, r, w, pold, sold, e, pnew,
+                            snew, rnew, wnew, c->ev32, g, mask, sc, (float)c->th));
         HOL_CHECK_LAUNCH("k_cg_merged");
         return HOL_OK;
     } else {
