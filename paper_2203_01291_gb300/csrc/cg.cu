@@ -77,14 +77,21 @@ __device__ __forceinline__ double block_sum(double v)
     return s;
 }
 
-// x += alpha p, r -= alpha q, new (r.r) partials; alpha = dz / pq from partials.
-template <typename R>
+// r -= alpha q with the new (r.r) partials; alpha = dz / pq from partials.
+// The x update may be deferred by one iteration (FOLD 0 stores alpha for
+// the next launch and leaves x alone; FOLD 2 then adds alpha_prev p_prev +
+// alpha p), so x is read and written every other iteration; FOLD 1 is the
+// plain x += alpha p.
+template <typename R, int FOLD>
 __global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restrict__ r,
-                                                   const R* __restrict__ p, const R* __restrict__ q,
-                                                   long n, const int* __restrict__ mask,
+                                                   const R* __restrict__ p,
+                                                   const R* __restrict__ pprev,
+                                                   const R* __restrict__ q, long n,
+                                                   const int* __restrict__ mask,
                                                    const double* __restrict__ pq_part, int pq_stride,
                                                    int pq_n, const double* __restrict__ dz_part,
-                                                   int dz_n, double* __restrict__ rr_out)
+                                                   int dz_n, double* __restrict__ rr_out,
+                                                   double* __restrict__ alpha_buf)
 {
     pdl_wait();      // p, q and the partials come from the previous kernel of the stream
     const PdlTriggerAtExit pdl_at_exit;
@@ -92,32 +99,48 @@ __global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restr
     if (mask != nullptr && mask[rhs] == 0) return;
     // one warp forms alpha (FP64 sums are slow on this part: doing it in
     // every warp measured slower than the barrier)
-    __shared__ double s_alpha;
+    __shared__ double s_alpha, s_alpha_prev;
     if (threadIdx.x < 32) {
         const double pq = warp_sum_array(pq_part + (long)rhs * pq_stride, pq_n);
         const double dz = warp_sum_array(dz_part + (long)rhs * kRedStride, dz_n);
-        if (threadIdx.x == 0) s_alpha = dz / pq;
+        if (threadIdx.x == 0) {
+            s_alpha = dz / pq;
+            if (FOLD == 2) s_alpha_prev = alpha_buf[rhs];
+        }
     }
     __syncthreads();
     const R a = (R)s_alpha;
+    R ap = R(0);
+    if (FOLD == 2) ap = (R)s_alpha_prev;
+    if (FOLD == 0 && blockIdx.x == 0 && threadIdx.x == 0) alpha_buf[rhs] = s_alpha;
     const long base = (long)rhs * n;
     const long stride = (long)gridDim.x * blockDim.x;
     double acc = 0.0;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n; k += stride) {
         const long o = base + 4 * k;
-        V4<R> xv, rv, pv, qv;
-        xv.ld(x + o);
+        V4<R> rv, qv;
         rv.ld(r + o);
-        pv.ld(p + o);
         qv.ld(q + o);
+        if (FOLD != 0) {
+            V4<R> xv, pv;
+            xv.ld(x + o);
+            pv.ld(p + o);
+            if (FOLD == 2) {
+                V4<R> pp;
+                pp.ld(pprev + o);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) xv.v[j] = fma(ap, pp.v[j], xv.v[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xv.v[j] = fma(a, pv.v[j], xv.v[j]);
+            xv.st(x + o);
+        }
         R part = R(0);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            xv.v[j] = fma(a, pv.v[j], xv.v[j]);
             rv.v[j] = fma(-a, qv.v[j], rv.v[j]);
             part = fma(rv.v[j], rv.v[j], part);
         }
-        xv.st(x + o);
         rv.st(r + o);
         acc += (double)part;
     }
@@ -473,8 +496,21 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
             }
             first = 0;
         }
+        bool pending = false;   // an x update deferred by the previous iteration
         for (int j = 0; j < chunk && !persistent; ++j) {
             double* rr_dst = pc ? B.er : B.dz[1 - cur];
+            // x is settled at the end of every chunk (reliable updates read it)
+            int fold;
+            if (pending) {
+                fold = 2;
+                pending = false;
+            } else if (j == chunk - 1) {
+                fold = 1;
+            } else {
+                fold = 0;
+                pending = true;
+            }
+            const double upd_bytes = fold == 0 ? 12.0 : fold == 1 ? 24.0 : 28.0;   // FP32
             if (mixed) {
                 // on the first step beta = 0 and p_old is not yet defined: pass z
                 timer_start(c, KT_OPERATOR, s, n_active * nd * 16.0 + nd * 4.0);
@@ -483,9 +519,12 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                 if (rc) return rc;
                 timer_stop(c, KT_OPERATOR, s);
                 pp = 1 - pp;
-                timer_start(c, KT_UPDATE, s, n_active * nd * 24.0);
-                HOL_CUDA(launch_pdl(c->pdl, k_cg_update<float>, g2, 256, 0, s, e32, r32, p32[pp],
-                                    q32, n, act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst));
+                timer_start(c, KT_UPDATE, s, n_active * nd * upd_bytes);
+                auto* upd = fold == 0 ? k_cg_update<float, 0>
+                                      : fold == 1 ? k_cg_update<float, 1> : k_cg_update<float, 2>;
+                HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, s, e32, r32, p32[pp], p32[1 - pp], q32, n,
+                                    act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst,
+                                    c->alpha_buf));
             } else {
                 BetaSrc bs{B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first};
                 timer_start(c, KT_OPERATOR, s, n_active * nd * 48.0 + nd * 16.0);
@@ -496,9 +535,12 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                 if (rc) return rc;
                 timer_stop(c, KT_OPERATOR, s);
                 pp = 1 - pp;
-                timer_start(c, KT_UPDATE, s, n_active * nd * 48.0);
-                k_cg_update<double><<<g2, 256, 0, s>>>(v, r64, p64[pp], q64, n, act_d, B.pq,
-                                                       pstride, pq_n, B.dz[cur], dz_n, rr_dst);
+                timer_start(c, KT_UPDATE, s, n_active * nd * 2.0 * upd_bytes);
+                auto* upd = fold == 0 ? k_cg_update<double, 0>
+                                      : fold == 1 ? k_cg_update<double, 1> : k_cg_update<double, 2>;
+                HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, s, v, r64, p64[pp], p64[1 - pp], q64, n,
+                                    act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst,
+                                    c->alpha_buf));
             }
             HOL_CHECK_LAUNCH("k_cg_update");
             timer_stop(c, KT_UPDATE, s);

@@ -134,11 +134,11 @@ void free_ctx(hol_ctx* c)
 {
     if (!c) return;
     void* dev[] = {c->x, c->ev64, c->ev32, c->dbar, c->scal, c->part, c->v64a, c->v64b,
-                   c->v64c, c->v64d, c->v64e, c->v32a, c->v32b, c->v32c, c->v32d, c->v32e,
-                   c->mask, c->kpm.np, c->kpm.coef, c->cbuf0, c->cbuf1, c->v64f, c->v32f,
+                   c->v64c, c->v64d, c->v64e, c->v32a,
+                   c->mask, c->kpm.np, c->kpm.coef, c->cbuf0, c->cbuf1, c->v64f,
                    c->tw64, c->tw32, c->md_phi, c->md_b, c->md_v, c->md_F, c->md_p,
                    c->md_x0, c->md_g, c->md_s, c->ms_acc, c->twL64, c->v32g, c->v32h,
-                   c->v32i, c->cgs};
+                   c->v32i, c->cgs, c->alpha_buf};
     for (void* p : dev)
         if (p) cudaFree(p);
     timer_free(c->timer);
@@ -220,14 +220,16 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     ALLOC(c->v64c, R * n * sizeof(double));
     ALLOC(c->v64d, R * n * sizeof(double));
     ALLOC(c->v64e, R * n * sizeof(double));
-    ALLOC(c->v32a, R * n * sizeof(float));
-    ALLOC(c->v32b, R * n * sizeof(float));
-    ALLOC(c->v32c, R * n * sizeof(float));
-    ALLOC(c->v32d, R * n * sizeof(float));
-    ALLOC(c->v32e, R * n * sizeof(float));
+    // the six FP32 vector sets of the solver are one arena (v32a is its base)
+    ALLOC(c->v32a, 6 * R * n * sizeof(float));
+    c->v32b = c->v32a + 1 * R * n;
+    c->v32c = c->v32a + 2 * R * n;
+    c->v32d = c->v32a + 3 * R * n;
+    c->v32e = c->v32a + 4 * R * n;
+    c->v32f = c->v32a + 5 * R * n;
     ALLOC(c->v64f, R * n * sizeof(double));
-    ALLOC(c->v32f, R * n * sizeof(float));
     ALLOC(c->mask, 2 * R * sizeof(int));
+    ALLOC(c->alpha_buf, R * sizeof(double));
     ALLOC(c->cbuf0, c->cbuf_len * sizeof(double2));
     ALLOC(c->cbuf1, c->cbuf_len * sizeof(double2));
 #undef ALLOC

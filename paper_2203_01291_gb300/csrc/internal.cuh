@@ -47,22 +47,12 @@ __device__ __forceinline__ void pdl_trigger()
 struct PdlTriggerAtExit {
     __device__ __forceinline__ ~PdlTriggerAtExit() { pdl_trigger(); }
 };
+// Launch of a CG-iteration kernel, with programmatic dependent launch when
+// the context enables it (hol_ctx::pdl).
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                       cudaStream_t s, Args&&... args)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
+cudaError_t launch_pdl(const hol_ctx* c, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                       size_t smem, cudaStream_t s, Args&&... args);
+
 
 // Optional CUDA-event timing of kernel classes (hol_timer_* entry points).
 enum TimerClass { KT_OPERATOR = 0, KT_UPDATE = 1, KT_FORCE = 2, KT_PRECOND = 3, KT_OTHER = 4,
@@ -144,6 +134,7 @@ struct hol_ctx {
     float* v32h;
     float* v32i;
     double* cgs;         // merged CG scalars [2][max_rhs][4]: alpha, gamma, mode
+    double* alpha_buf;   // CG: alpha of an iteration whose x update is deferred [max_rhs]
     double2* tw64;       // [2T] exp(-i pi k / T)
     float2* tw32;
     double* md_phi;      // leapfrog: Phi [max_rhs][T][N]
@@ -173,6 +164,25 @@ struct hol_ctx {
     int merged;          // mixed plain CG as one fused kernel per iteration
     int pdl;             // programmatic dependent launch of the CG kernels
 };
+
+namespace hol {
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(const hol_ctx* c, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                       size_t smem, cudaStream_t s, Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = c->pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+}  // namespace hol
 
 namespace hol {
 

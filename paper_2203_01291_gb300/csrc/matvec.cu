@@ -1032,11 +1032,11 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
         if (c->mv_vec == 4 || c->mv_vec == 5) {   // split layout, 2 or 4 warps per unit
             const int units = g.nrun * g.n_rhs;
             if (c->mv_vec == 4)
-                HOL_CUDA(launch_pdl(c->pdl, k_cg_mtm32_split<L, 2>, units, 64, 0, s, r, pold, pnew,
+                HOL_CUDA(launch_pdl(c, k_cg_mtm32_split<L, 2>, units, 64, 0, s, r, pold, pnew,
                                     q, c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first,
                                     pq_part, (float)c->th));
             else
-                HOL_CUDA(launch_pdl(c->pdl, k_cg_mtm32_split<L, 4>, units, 128, 0, s, r, pold, pnew,
+                HOL_CUDA(launch_pdl(c, k_cg_mtm32_split<L, 4>, units, 128, 0, s, r, pold, pnew,
                                     q, c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first,
                                     pq_part, (float)c->th));
             HOL_CHECK_LAUNCH("k_cg_mtm32_split");
@@ -1064,7 +1064,7 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
             const int need = g.wpr * g.n_rhs;                 // warp-units
             int blocks = resident.load();
             if ((long)blocks * wpb > need) blocks = (need + wpb - 1) / wpb;
-            HOL_CUDA(launch_pdl(c->pdl, k_cg_mtm32_v4s<L, S>, blocks, 32 * wpb, sm, s, r, pold,
+            HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4s<L, S>, blocks, 32 * wpb, sm, s, r, pold,
                                 pnew, q, c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first,
                                 pq_part, (float)c->th, blocks * wpb));
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4s");
@@ -1081,21 +1081,21 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, most));
                 limit.store(most);
             }
-            HOL_CUDA(launch_pdl(c->pdl, k_cg_mtm32_v4a<L>, nb, nt, sm, s, r, pold, pnew, q,
+            HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4a<L>, nb, nt, sm, s, r, pold, pnew, q,
                                 c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first, pq_part,
                                 (float)c->th));
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4a");
             return HOL_OK;
         }
         if (c->mv_vec) {
-            HOL_CUDA(launch_pdl(c->pdl, k_cg_mtm32_v4<L>, nb, nt, 0, s, r, pold, pnew, q,
+            HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4<L>, nb, nt, 0, s, r, pold, pnew, q,
                                 c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first, pq_part,
                                 (float)c->th));
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4");
             return HOL_OK;
         }
     }
-    HOL_CUDA(launch_pdl(c->pdl, k_cg_mtm32<L>, nb, nt, 0, s, r, pold, pnew, q, c->ev32, g, mask,
+    HOL_CUDA(launch_pdl(c, k_cg_mtm32<L>, nb, nt, 0, s, r, pold, pnew, q, c->ev32, g, mask,
                         rr_new, rr_old, rr_stride, rr_n, first, pq_part, (float)c->th));
     HOL_CHECK_LAUNCH("k_cg_mtm32");
     return HOL_OK;
@@ -1110,7 +1110,7 @@ int run_cg_merged(const hol_ctx* c, const float* r, const float* w, const float*
     if constexpr (L % 8 == 0) {
         const MvGeom g = make_geom<L>(c, n_rhs);
         const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-        HOL_CUDA(launch_pdl(c->pdl, k_cg_merged<L>, nb, nt, 0, s, r, w, pold, sold, e, pnew,
+        HOL_CUDA(launch_pdl(c, k_cg_merged<L>, nb, nt, 0, s, r, w, pold, sold, e, pnew,
                             snew, rnew, wnew, c->ev32, g, mask, sc, (float)c->th));
         HOL_CHECK_LAUNCH("k_cg_merged");
         return HOL_OK;
