@@ -181,15 +181,23 @@ __global__ void __launch_bounds__(256) k_fold(double* __restrict__ v, float* __r
     const int rhs = blockIdx.y;
     if (mask[rhs] == 0) return;
     const long base = (long)rhs * n;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n;
          k += (long)gridDim.x * blockDim.x) {
-        v[base + k] += (double)e[base + k];
-        e[base + k] = 0.0f;
+        const long o = base + 4 * k;
+        V4<double> vv;
+        V4<float> ev;
+        vv.ld(v + o);
+        ev.ld(e + o);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) vv.v[j] += (double)ev.v[j];
+        vv.st(v + o);
+        *reinterpret_cast<float4*>(e + o) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
 // Reliable update, part 3: r <- true residual rt (FP64; rounded to FP32 in
-// the mixed path); partials of |rt|^2 (true) and |r|^2 (recursion).
+// the mixed path); partials of |rt|^2 (true, FP64) and |r|^2 (recursion
+// estimate, accumulated in R per group of four).
 template <typename R>
 __global__ void __launch_bounds__(256) k_recast(const double* rt, R* r, long n,
                                                 const int* __restrict__ mask,
@@ -200,13 +208,21 @@ __global__ void __launch_bounds__(256) k_recast(const double* rt, R* r, long n,
     if (mask[rhs] == 0) return;
     const long base = (long)rhs * n;
     double at = 0.0, ar = 0.0;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n;
          k += (long)gridDim.x * blockDim.x) {
-        const double tv = rt[base + k];
-        const R rv = (R)tv;
-        if ((const void*)r != (const void*)rt) r[base + k] = rv;
-        at += tv * tv;
-        ar += (double)rv * (double)rv;
+        const long o = base + 4 * k;
+        V4<double> tv;
+        tv.ld(rt + o);
+        V4<R> rv;
+        R part = R(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            rv.v[j] = (R)tv.v[j];
+            at = fma(tv.v[j], tv.v[j], at);
+            part = fma(rv.v[j], rv.v[j], part);
+        }
+        if ((const void*)r != (const void*)rt) rv.st(r + o);
+        ar += (double)part;
     }
     double s = block_sum(at);
     if (threadIdx.x == 0) tr_out[(long)rhs * kRedStride + blockIdx.x] = s;
@@ -270,11 +286,21 @@ __global__ void __launch_bounds__(256) k_conj_dots(const R* __restrict__ z, cons
     if (mask[rhs] == 0) return;
     const long base = (long)rhs * n;
     double azq = 0.0, apq = 0.0;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n;
          k += (long)gridDim.x * blockDim.x) {
-        const double qv = (double)q[base + k];
-        azq += (double)z[base + k] * qv;
-        apq += (double)p[base + k] * qv;
+        const long o = base + 4 * k;
+        V4<R> zv, pv, qv;
+        zv.ld(z + o);
+        pv.ld(p + o);
+        qv.ld(q + o);
+        R szq = R(0), spq = R(0);   // a group of four in R, the sum in FP64
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            szq = fma(zv.v[j], qv.v[j], szq);
+            spq = fma(pv.v[j], qv.v[j], spq);
+        }
+        azq += (double)szq;
+        apq += (double)spq;
     }
     double t = block_sum(azq);
     if (threadIdx.x == 0) zq_out[(long)rhs * kRedStride + blockIdx.x] = t;
@@ -283,8 +309,7 @@ __global__ void __launch_bounds__(256) k_conj_dots(const R* __restrict__ z, cons
     if (threadIdx.x == 0) pq_out[(long)rhs * kRedStride + blockIdx.x] = t;
 }
 
-// p *= beta = -(z, q) / (p, q) for the flagged rhs (every thread forms beta
-// from the same partials in the same order).
+// p *= beta = -(z, q) / (p, q) for the flagged rhs (one warp forms beta).
 template <typename R>
 __global__ void __launch_bounds__(256) k_conj_scale(R* __restrict__ p, long n,
                                                     const int* __restrict__ mask,
@@ -293,13 +318,23 @@ __global__ void __launch_bounds__(256) k_conj_scale(R* __restrict__ p, long n,
 {
     const int rhs = blockIdx.y;
     if (mask[rhs] == 0) return;
-    const double zq = warp_sum_array(zq_part + (long)rhs * kRedStride, cnt);
-    const double pq = warp_sum_array(pq_part + (long)rhs * kRedStride, cnt);
-    const R bt = (R)(-zq / pq);
+    __shared__ double s_beta;
+    if (threadIdx.x < 32) {
+        const double zq = warp_sum_array(zq_part + (long)rhs * kRedStride, cnt);
+        const double pq = warp_sum_array(pq_part + (long)rhs * kRedStride, cnt);
+        if (threadIdx.x == 0) s_beta = -zq / pq;
+    }
+    __syncthreads();
+    const R bt = (R)s_beta;
     const long base = (long)rhs * n;
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
-         k += (long)gridDim.x * blockDim.x)
-        p[base + k] *= bt;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n;
+         k += (long)gridDim.x * blockDim.x) {
+        V4<R> pv;
+        pv.ld(p + base + 4 * k);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) pv.v[j] *= bt;
+        pv.st(p + base + 4 * k);
+    }
 }
 
 // dst row = src row (kRedStride partials) for the flagged rhs, so that the

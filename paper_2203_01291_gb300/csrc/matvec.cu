@@ -368,10 +368,10 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
 
 
 // ---------------------------------------------------------------------------
-// Float4 fused CG step with the r and p_old rows of the next tau slice
-// prefetched into a per-lane shared-memory ring by cp.async (16-byte async
-// copies, two stages), so the global loads of slice tau+1 are in flight
-// while slice tau is computed. Each lane copies and later reads only its own
+// Float4 fused CG step with the r, p_old and expV rows of the next tau
+// slice prefetched into a per-lane shared-memory ring by cp.async (16-byte
+// async copies, two stages), so the global loads of slice tau+1 are in
+// flight while slice tau is computed. Each lane copies and later reads only its own
 // slots, so cp.async.wait_group is the only synchronisation needed.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
@@ -399,12 +399,12 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
     const PdlTriggerAtExit pdl_at_exit;
     constexpr int N = L * L;
     constexpr int RT = L / 4;
-    extern __shared__ __align__(16) float4 ring[];   // [warp][slot][array][RT][32]
+    extern __shared__ __align__(16) float4 ring[];   // [warp][slot][array: r, p_old, expV][RT][32]
     const Geom4<L> geo;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* my = ring + (long)wib * (2 * 2 * RT * 32);
+    float4* my = ring + (long)wib * (2 * 3 * RT * 32);
     auto slot_ptr = [&](int slot, int arr, int k) -> float4* {
-        return my + ((slot * 2 + arr) * RT + k) * 32 + lane;
+        return my + ((slot * 3 + arr) * RT + k) * 32 + lane;
     };
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int rhs = warp / gm.wpr;
@@ -422,11 +422,13 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
         return t;
     };
     auto issue = [&](int j) {
-        const long o = base + (long)seq(j) * N;
+        const int t = seq(j);
+        const long o = base + (long)t * N;
 #pragma unroll
         for (int k = 0; k < RT; ++k) {
             cp_async16(slot_ptr(j & 1, 0, k), r + o + geo.off(k));
             cp_async16(slot_ptr(j & 1, 1, k), pold + o + geo.off(k));
+            if (j > 0) cp_async16(slot_ptr(j & 1, 2, k), ev + (long)t * N + geo.off(k));
         }
         cp_async_commit();
     };
@@ -456,7 +458,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
             const float4 pv = fma4s(bt, *slot_ptr(1, 1, k), *slot_ptr(1, 0, k));
             if (valid && pnew != nullptr) st4(pnew, o + geo.off(k), pv);
             X[k] = pv;
-            const float4 d = ld4(ev, (long)t0 * N + geo.off(k));
+            const float4 d = *slot_ptr(1, 2, k);
             W[k] = make_float4(fmaf(sg * d.x, Y[k].x, pv.x), fmaf(sg * d.y, Y[k].y, pv.y),
                                fmaf(sg * d.z, Y[k].z, pv.z), fmaf(sg * d.w, Y[k].w, pv.w));
         }
@@ -477,7 +479,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
             const float4 pv = fma4s(bt, *slot_ptr(j & 1, 1, k), *slot_ptr(j & 1, 0, k));
             if (own) st4(pnew, op + geo.off(k), pv);
             P[k] = pv;
-            float4 d = ld4(ev, (long)tp * N + geo.off(k));
+            float4 d = *slot_ptr(j & 1, 2, k);
             d.x *= sgp; d.y *= sgp; d.z *= sgp; d.w *= sgp;
             X[k] = make_float4(fmaf(d.x, X[k].x, pv.x), fmaf(d.y, X[k].y, pv.y),
                                fmaf(d.z, X[k].z, pv.z), fmaf(d.w, X[k].w, pv.w));
@@ -1071,12 +1073,12 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
             return HOL_OK;
         }
         if (c->mv_vec == 2) {
-            const size_t sm = (size_t)c->mv_warps * 2 * 2 * (L / 4) * 32 * sizeof(float4);
+            const size_t sm = (size_t)c->mv_warps * 2 * 3 * (L / 4) * 32 * sizeof(float4);
             // raised once per instantiation to the largest size any block shape needs
             // (the static reduction scratch counts against the default limit)
             static std::atomic<int> limit(0);
             if ((int)sm > limit.load()) {
-                const int most = 4 * 2 * 2 * (L / 4) * 32 * (int)sizeof(float4);
+                const int most = 4 * 2 * 3 * (L / 4) * 32 * (int)sizeof(float4);
                 HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_mtm32_v4a<L>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, most));
                 limit.store(most);
