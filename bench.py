@@ -280,9 +280,9 @@ def run_ours(a):
                            "memory, e += alpha p, r -= alpha q; per iteration r, p, e read and "
                            "written once)")
     else:
-        kname = {0: "k_cg_mtm32<32>", 1: "k_cg_mtm32_v4<32>", 2: "k_cg_mtm32_v4a<32>",
+        kname = {0: "k_cg_mtm32<32>", 1: "k_cg_mtm32_v4<32>", 2: "k_cg_mtm32_v4a<32,2>",
                  3: "k_cg_mtm32_v4s<32,3>", 4: "k_cg_mtm32_split<32,2>",
-                 5: "k_cg_mtm32_split<32,4>"}[ctx.get_option("layout")]
+                 5: "k_cg_mtm32_split<32,4>", 6: "k_cg_mtm32_v4a<32,3>"}[ctx.get_option("layout")]
         ctx_kernel_name = kname + " (fused p = r + beta p, q = M^T M p, |Mp|^2)"
     ctx.timer_enable(0)
     clk = clocks.stop()

@@ -310,9 +310,8 @@ int fermion_matvec_static(const hol_params* p, const double* x, int op, const do
  * register layout) with CUDA events on `stream`, and keeps the fastest in the
  * context for all later calls (results are unchanged up to rounding; every
  * candidate computes the same operator). Host outputs (nullable): the chosen
- * slices per group, warps per block, layout (5 / 4 = split
- * float4 over 4 / 2 warps, 3 = streaming float4, 2 = float4 with asynchronous
- * prefetch, 1 = float4, 0 = scalar), and its time in ms.
+ * slices per group, warps per block, layout (the "layout"
+ * values of hol_set_option), and its time in ms.
  * Requires hol_set_field; overwrites context scratch; synchronises `stream`.
  */
 int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_vec,
@@ -323,10 +322,11 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  * are the same up to rounding whichever is chosen):
  *   "slices_per_group"  tau slices streamed per lane group (divides Ltau)
  *   "warps_per_block"   1, 2 or 4 for the operator kernels
- *   "layout"            0 scalar, 1 float4, 2 float4 with cp.async prefetch,
- *                       3 streaming float4 with a cp.async ring across units
- *                       (1-3 need L % 8 == 0), 4 / 5 split float4 with each
- *                       slice spread over 2 / 4 warps (L == 32)
+ *   "layout"            0 scalar, 1 float4, 2 float4 with a two-slice cp.async
+ *                       ring, 6 the same with a three-slice ring, 3 streaming
+ *                       float4 with a cp.async ring across units (1-3 and 6
+ *                       need L % 8 == 0), 4 / 5 split float4 with each slice
+ *                       spread over 2 / 4 warps (L == 32)
  *   "kpm_registers"     register KPM kernel for FP32, L = 16 or 32 (0/1)
  *   "persistent_cg"     plain mixed CG chunks in one cooperative launch (0/1)
  *   "pdl"               programmatic dependent launch of the CG iteration

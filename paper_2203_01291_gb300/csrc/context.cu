@@ -390,9 +390,10 @@ extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
             return set_error(HOL_EINVAL, "hol_set_option: warps_per_block must be 1, 2 or 4");
         c->mv_warps = value;
     } else if (is("layout")) {
-        if (value < 0 || value > 5 || (value > 0 && c->L % 8) || (value > 3 && c->L != 32))
-            return set_error(HOL_EINVAL,
-                             "hol_set_option: layout 0..5 (1-3 need L %% 8 == 0, 4-5 L == 32)");
+        if (value < 0 || value > 6 || (value > 0 && c->L % 8) ||
+            ((value == 4 || value == 5) && c->L != 32))
+            return set_error(HOL_EINVAL, "hol_set_option: layout 0..6 (1-3, 6 need L %% 8 == 0, "
+                                         "4-5 L == 32)");
         c->mv_vec = value;
     } else if (is("kpm_registers")) {
         c->kpm_reg = value ? 1 : 0;

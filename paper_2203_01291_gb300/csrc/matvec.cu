@@ -383,7 +383,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int NPEND>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
 
-template <int L>
+template <int L, int S>
 __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict__ r,
                                                          const float* __restrict__ pold,
                                                          float* __restrict__ pnew,
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
     extern __shared__ __align__(16) float4 ring[];   // [warp][slot][array: r, p_old, expV][RT][32]
     const Geom4<L> geo;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* my = ring + (long)wib * (2 * 3 * RT * 32);
+    float4* my = ring + (long)wib * (S * 3 * RT * 32);
     auto slot_ptr = [&](int slot, int arr, int k) -> float4* {
         return my + ((slot * 3 + arr) * RT + k) * 32 + lane;
     };
@@ -421,20 +421,24 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
         if (t >= gm.T) t -= gm.T;
         return t;
     };
+    const int last = gm.K + 1;   // index of the last slice in the sequence
+    // slice j goes to slot j % S; the copy of slice j + S - 1 is issued just
+    // before slice j is waited for (its slot held slice j - 1, already read)
     auto issue = [&](int j) {
-        const int t = seq(j);
-        const long o = base + (long)t * N;
+        if (j <= last) {
+            const int t = seq(j);
+            const long o = base + (long)t * N;
 #pragma unroll
-        for (int k = 0; k < RT; ++k) {
-            cp_async16(slot_ptr(j & 1, 0, k), r + o + geo.off(k));
-            cp_async16(slot_ptr(j & 1, 1, k), pold + o + geo.off(k));
-            if (j > 0) cp_async16(slot_ptr(j & 1, 2, k), ev + (long)t * N + geo.off(k));
+            for (int k = 0; k < RT; ++k) {
+                cp_async16(slot_ptr(j % S, 0, k), r + o + geo.off(k));
+                cp_async16(slot_ptr(j % S, 1, k), pold + o + geo.off(k));
+                if (j > 0) cp_async16(slot_ptr(j % S, 2, k), ev + (long)t * N + geo.off(k));
+            }
         }
         cp_async_commit();
     };
-    const int last = gm.K + 1;   // index of the last slice in the sequence
-    issue(0);
-    issue(1);
+#pragma unroll
+    for (int j = 0; j < S - 1; ++j) issue(j);
 
     float bt = 0.0f;
     if (!first) {
@@ -444,21 +448,22 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
     }
 
     float4 W[RT], X[RT], P[RT], Y[RT];
-    cp_async_wait<1>();   // slice j = 0 has landed
+    issue(S - 1);
+    cp_async_wait<S - 1>();   // slice j = 0 has landed
 #pragma unroll
     for (int k = 0; k < RT; ++k) Y[k] = fma4s(bt, *slot_ptr(0, 1, k), *slot_ptr(0, 0, k));
     c4_apply<L>(Y, geo, th);
-    if (2 <= last) issue(2); else cp_async_commit();
-    cp_async_wait<1>();   // slice j = 1 (t0)
+    issue(S);
+    cp_async_wait<S - 1>();   // slice j = 1 (t0)
     {
         const long o = base + (long)t0 * N;
         const float sg = (t0 == 0) ? 1.0f : -1.0f;
 #pragma unroll
         for (int k = 0; k < RT; ++k) {
-            const float4 pv = fma4s(bt, *slot_ptr(1, 1, k), *slot_ptr(1, 0, k));
+            const float4 pv = fma4s(bt, *slot_ptr(1 % S, 1, k), *slot_ptr(1 % S, 0, k));
             if (valid && pnew != nullptr) st4(pnew, o + geo.off(k), pv);
             X[k] = pv;
-            const float4 d = *slot_ptr(1, 2, k);
+            const float4 d = *slot_ptr(1 % S, 2, k);
             W[k] = make_float4(fmaf(sg * d.x, Y[k].x, pv.x), fmaf(sg * d.y, Y[k].y, pv.y),
                                fmaf(sg * d.z, Y[k].z, pv.z), fmaf(sg * d.w, Y[k].w, pv.w));
         }
@@ -467,8 +472,8 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
     double acc = 0.0;
     for (int s = 0; s < gm.K; ++s) {
         const int j = s + 2;             // slice t0 + 1 + s
-        if (j + 1 <= last) issue(j + 1); else cp_async_commit();
-        cp_async_wait<1>();
+        issue(j + S - 1);
+        cp_async_wait<S - 1>();
         const int tau = t0 + s;
         const int tp = (tau + 1 == gm.T) ? 0 : tau + 1;
         const long op = base + (long)tp * N;
@@ -476,10 +481,10 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
         const bool own = valid && (s + 1 < gm.K) && pnew != nullptr;
 #pragma unroll
         for (int k = 0; k < RT; ++k) {
-            const float4 pv = fma4s(bt, *slot_ptr(j & 1, 1, k), *slot_ptr(j & 1, 0, k));
+            const float4 pv = fma4s(bt, *slot_ptr(j % S, 1, k), *slot_ptr(j % S, 0, k));
             if (own) st4(pnew, op + geo.off(k), pv);
             P[k] = pv;
-            float4 d = *slot_ptr(j & 1, 2, k);
+            float4 d = *slot_ptr(j % S, 2, k);
             d.x *= sgp; d.y *= sgp; d.z *= sgp; d.w *= sgp;
             X[k] = make_float4(fmaf(d.x, X[k].x, pv.x), fmaf(d.y, X[k].y, pv.y),
                                fmaf(d.z, X[k].z, pv.z), fmaf(d.w, X[k].w, pv.w));
@@ -1072,20 +1077,29 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4s");
             return HOL_OK;
         }
-        if (c->mv_vec == 2) {
-            const size_t sm = (size_t)c->mv_warps * 2 * 3 * (L / 4) * 32 * sizeof(float4);
+        if (c->mv_vec == 2 || c->mv_vec == 6) {   // cp.async ring of 2 or 3 slices
+            const bool deep = c->mv_vec == 6;
+            const size_t sm = (size_t)c->mv_warps * (deep ? 3 : 2) * 3 * (L / 4) * 32 * sizeof(float4);
             // raised once per instantiation to the largest size any block shape needs
             // (the static reduction scratch counts against the default limit)
             static std::atomic<int> limit(0);
             if ((int)sm > limit.load()) {
-                const int most = 4 * 2 * 3 * (L / 4) * 32 * (int)sizeof(float4);
-                HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_mtm32_v4a<L>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, most));
-                limit.store(most);
+                const int most2 = 4 * 2 * 3 * (L / 4) * 32 * (int)sizeof(float4);
+                const int most3 = 4 * 3 * 3 * (L / 4) * 32 * (int)sizeof(float4);
+                HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_mtm32_v4a<L, 2>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, most2));
+                HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_mtm32_v4a<L, 3>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, most3));
+                limit.store(most3);
             }
-            HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4a<L>, nb, nt, sm, s, r, pold, pnew, q,
-                                c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first, pq_part,
-                                (float)c->th));
+            if (deep)
+                HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4a<L, 3>, nb, nt, sm, s, r, pold, pnew, q,
+                                    c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first,
+                                    pq_part, (float)c->th));
+            else
+                HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4a<L, 2>, nb, nt, sm, s, r, pold, pnew, q,
+                                    c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first,
+                                    pq_part, (float)c->th));
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4a");
             return HOL_OK;
         }

@@ -3,9 +3,10 @@
 // Candidates: K (tau slices streamed per lane group) among the divisors
 // {1, 2, 4, 5, 8, 10} of Ltau, 1, 2 or 4 warps per block, for L = 32 the
 // split float4 layout with 4 or 2 warps per slice (5, 4), and for L % 8 == 0
-// the streaming float4 kernel with a cp.async ring across units (3), the
-// float4 layout with cp.async prefetch (2), without (1), or the scalar
-// register layout (0). The split and streaming kernels fix their own block
+// the float4 layout with a cp.async ring of three slices (6), the streaming
+// float4 kernel with a cp.async ring across units (3), the float4 layout
+// with a two-slice cp.async ring (2), without (1), or the scalar register
+// layout (0). The split and streaming kernels fix their own block
 // shapes, so they are timed once per K. With the merged CG on, the merged iteration kernel is
 // timed instead over K and warps (its layout is fixed). Each candidate is
 // timed with CUDA
@@ -69,16 +70,31 @@ extern "C" int hol_tune(hol_ctx* c, int n_rhs, int* best_k, int* best_warps, int
         for (float* b : bufs)
             HOL_CUDA(cudaMemsetAsync(b, 0, (size_t)n_rhs * c->n * sizeof(float), s));
     }
-    const int vec_hi = merged ? c->mv_vec : (c->L == 32 ? 5 : (c->L % 8 == 0) ? 3 : 0);
-    const int vec_lo = merged ? c->mv_vec : 0;
-    for (int vec = vec_hi; vec >= vec_lo && !rc; --vec) {
+    int vecs[8], nvec = 0;
+    if (merged) {
+        vecs[nvec++] = c->mv_vec;
+    } else {
+        if (c->L % 8 == 0) {
+            vecs[nvec++] = 6;
+            if (c->L == 32) {
+                vecs[nvec++] = 5;
+                vecs[nvec++] = 4;
+            }
+            vecs[nvec++] = 3;
+            vecs[nvec++] = 2;
+            vecs[nvec++] = 1;
+        }
+        vecs[nvec++] = 0;
+    }
+    for (int vi = 0; vi < nvec && !rc; ++vi) {
+        const int vec = vecs[vi];
         for (int ki = 0; ki < 6 && !rc; ++ki) {
             const int k = ks[ki];
             if (c->T % k) continue;
             c->mv_k = k;
             if ((long)matvec_pstride(c) * c->p.max_rhs > c->part_len) continue;
             for (int wi = 0; wi < 3 && !rc; ++wi) {
-                if (vec >= 3 && wi > 0 && !merged) break;   // fixed block shapes
+                if (vec >= 3 && vec <= 5 && wi > 0 && !merged) break;   // fixed block shapes
                 c->mv_warps = ws[wi];
                 c->mv_vec = vec;
                 for (int r = 0; r < 2 && !rc; ++r) rc = launch(r);

@@ -224,11 +224,12 @@ def test_autotuner_choice_keeps_results(L, T):
 LAYOUT_CASES = [(32, 40, 2), (32, 30, 5), (16, 30, 3), (8, 24, 1), (24, 12, 4)]
 
 
-@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("L,T,K", LAYOUT_CASES)
 def test_fused_mtm_every_layout(layout, L, T, K):
     """Each register layout of the fused FP32 M^T M (scalar, float4, float4
-    with prefetch, streaming float4, split float4 over 2 or 4 warps) and each
+    with a two- or three-slice prefetch ring, streaming float4, split float4
+    over 2 or 4 warps) and each
     slice grouping gives the oracle's M^T M, and a masked mixed solve
     (right-hand sides of different scale converge at different iterations)
     stays certified."""
@@ -256,7 +257,7 @@ def test_fused_mtm_every_layout(layout, L, T, K):
     assert max(MF.rel_residual(w, x, v[k], s[k]) for k in range(nr)) < 1.01e-8
 
 
-@pytest.mark.parametrize("layout,K", [(3, 1), (3, 2), (4, 2), (5, 4)])
+@pytest.mark.parametrize("layout,K", [(3, 1), (3, 2), (4, 2), (5, 4), (6, 4), (2, 8)])
 def test_vector_layouts_full_size(layout, K):
     """The streaming layout (resident warps walk several of the 3200 or 1600
     units each) and the split layouts at L=32, Ltau=200 with 16 right-hand
