@@ -162,6 +162,106 @@ __device__ typename Cx<R>::T2* fft_tau(typename Cx<R>::T2* a, typename Cx<R>::T2
 }
 
 
+// ---------------------------------------------------------------------------
+// The same transform with the length T, the tile width TS and the block size
+// NT known at compile time (the lengths of the configured workloads): the
+// plan, the butterfly loops and every index division are resolved by the
+// compiler. Same passes and twiddles as fft_tau.
+// ---------------------------------------------------------------------------
+struct PlanCT {
+    int n;
+    int r[16];
+};
+
+__host__ __device__ constexpr PlanCT plan_ct(int T)
+{
+    PlanCT p{0, {}};
+    int t = T;
+    const int rs[5] = {4, 2, 3, 5, 7};
+    for (int k = 0; k < 5; ++k)
+        while (t % rs[k] == 0 && p.n < 16) {
+            p.r[p.n++] = rs[k];
+            t /= rs[k];
+        }
+    if (t != 1) p.n = -1;
+    return p;
+}
+
+template <typename R, int RAD, int T, int TS, int NT, int Ns>
+__device__ __forceinline__ void stockham_pass_ct(const typename Cx<R>::T2* __restrict__ in,
+                                                 typename Cx<R>::T2* __restrict__ out,
+                                                 const typename Cx<R>::T2* __restrict__ w2)
+{
+    using C2 = typename Cx<R>::T2;
+    static_assert(NT % TS == 0, "block size must be a multiple of the tile width");
+    constexpr int nb = T / RAD;
+    constexpr int SJ = NT / TS;
+    constexpr int tstep = T / (Ns * RAD);
+    const int c = threadIdx.x % TS;
+    const int j0 = threadIdx.x / TS;
+    C2 root[RAD];
+#pragma unroll
+    for (int e = 0; e < RAD; ++e) root[e] = w2[2 * e * (T / RAD)];
+#pragma unroll
+    for (int jj = 0; jj < (nb + SJ - 1) / SJ; ++jj) {
+        const int j = j0 + jj * SJ;
+        if (nb % SJ != 0 && j >= nb) break;
+        const int k = j % Ns, jb = j / Ns;
+        C2 a[RAD];
+        a[0] = in[j * TS + c];
+        if (Ns > 1 && k > 0) {
+            const C2 w1 = w2[2 * k * tstep];
+            C2 wr = w1;
+#pragma unroll
+            for (int r = 1; r < RAD; ++r) {
+                a[r] = cmul(in[(j + r * nb) * TS + c], wr);
+                if (r + 1 < RAD) wr = cmul(wr, w1);
+            }
+        } else {
+#pragma unroll
+            for (int r = 1; r < RAD; ++r) a[r] = in[(j + r * nb) * TS + c];
+        }
+        const int ob = jb * Ns * RAD + k;
+        if constexpr (RAD == 2) {
+            out[ob * TS + c] = cadd(a[0], a[1]);
+            out[(ob + Ns) * TS + c] = csub(a[0], a[1]);
+        } else if constexpr (RAD == 4) {
+            const C2 s02 = cadd(a[0], a[2]), d02 = csub(a[0], a[2]);
+            const C2 s13 = cadd(a[1], a[3]), d13 = cmi(csub(a[1], a[3]));
+            out[ob * TS + c] = cadd(s02, s13);
+            out[(ob + Ns) * TS + c] = cadd(d02, d13);
+            out[(ob + 2 * Ns) * TS + c] = csub(s02, s13);
+            out[(ob + 3 * Ns) * TS + c] = csub(d02, d13);
+        } else {
+#pragma unroll
+            for (int q = 0; q < RAD; ++q) {
+                C2 sum = a[0];
+#pragma unroll
+                for (int r = 1; r < RAD; ++r) sum = cadd(sum, cmul(a[r], root[(r * q) % RAD]));
+                out[(ob + q * Ns) * TS + c] = sum;
+            }
+        }
+    }
+}
+
+template <typename R, int T, int TS, int NT, int S = 0, int Ns = 1>
+__device__ __forceinline__ typename Cx<R>::T2* fft_tau_ct(typename Cx<R>::T2* a,
+                                                          typename Cx<R>::T2* b,
+                                                          const typename Cx<R>::T2* __restrict__ w2)
+{
+    constexpr PlanCT P = plan_ct(T);
+    static_assert(P.n > 0, "length with a prime factor above 7");
+    if constexpr (S < P.n) {
+        constexpr int RAD = P.r[S];
+        __syncthreads();
+        stockham_pass_ct<R, RAD, T, TS, NT, Ns>(a, b, w2);
+        return fft_tau_ct<R, T, TS, NT, S + 1, Ns * RAD>(b, a, w2);
+    } else {
+        __syncthreads();
+        return a;
+    }
+}
+
 // radix plan of a length (host): factors 4 first, then 2, 3, 5, 7; n = -1 if
 // another prime factor remains
 inline RadixPlan plan_of(int T)

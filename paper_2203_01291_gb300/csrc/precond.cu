@@ -39,13 +39,17 @@ namespace {
 using namespace fft;
 
 // v (real [nr][T][N]) -> vh (complex [nr][T/2][N]) = U v restricted to omega < T/2
-template <typename R>
+// TC, TSC > 0: length and tile width fixed at compile time (fft_tau_ct);
+// 0: taken from the arguments (fft_tau).
+template <typename R, int TC = 0, int TSC = 0>
 __global__ void __launch_bounds__(256) k_tau_fwd(const R* __restrict__ v,
                                                  typename Cx<R>::T2* __restrict__ vh,
-                                                 const typename Cx<R>::T2* __restrict__ w2, int T,
-                                                 int N, int TS, RadixPlan plan, R scale)
+                                                 const typename Cx<R>::T2* __restrict__ w2, int T_,
+                                                 int N, int TS_, RadixPlan plan, R scale)
 {
     using C2 = typename Cx<R>::T2;
+    const int T = TC > 0 ? TC : T_;
+    const int TS = TSC > 0 ? TSC : TS_;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2* a = reinterpret_cast<C2*>(smem_raw);
     C2* b = a + (long)T * TS;
@@ -59,7 +63,11 @@ __global__ void __launch_bounds__(256) k_tau_fwd(const R* __restrict__ v,
         const C2 t = tw<R>(w2, tau, T);    // exp(-i pi tau / T)
         a[tau * TS + c] = Cx<R>::mk(x * t.x, x * t.y);
     }
-    C2* res = fft_tau<R>(a, b, w2, T, TS, plan);
+    C2* res;
+    if constexpr (TC > 0)
+        res = fft_tau_ct<R, TC, TSC, 256>(a, b, w2);
+    else
+        res = fft_tau<R>(a, b, w2, T, TS, plan);
     const int Th = T / 2;
     const long ob = (long)rhs * Th * N;
     for (int item = threadIdx.x; item < Th * TS; item += blockDim.x) {
@@ -76,15 +84,17 @@ __global__ void __launch_bounds__(256) k_tau_fwd(const R* __restrict__ v,
 
 // yh (complex [nr][T/2][N]) -> y (real [nr][T][N]) = U^dag of the conjugate-
 // symmetric extension; optional dot partials sum(y * rdot) per (rhs, tile).
-template <typename R>
+template <typename R, int TC = 0, int TSC = 0>
 __global__ void __launch_bounds__(256) k_tau_inv(const typename Cx<R>::T2* __restrict__ yh,
                                                  R* __restrict__ y,
-                                                 const typename Cx<R>::T2* __restrict__ w2, int T,
-                                                 int N, int TS, RadixPlan plan, R scale,
+                                                 const typename Cx<R>::T2* __restrict__ w2, int T_,
+                                                 int N, int TS_, RadixPlan plan, R scale,
                                                  const R* __restrict__ rdot,
                                                  double* __restrict__ dot_part)
 {
     using C2 = typename Cx<R>::T2;
+    const int T = TC > 0 ? TC : T_;
+    const int TS = TSC > 0 ? TSC : TS_;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2* a = reinterpret_cast<C2*>(smem_raw);
     C2* b = a + (long)T * TS;
@@ -102,7 +112,11 @@ __global__ void __launch_bounds__(256) k_tau_inv(const typename Cx<R>::T2* __res
         }
         a[w * TS + c] = z;
     }
-    C2* res = fft_tau<R>(a, b, w2, T, TS, plan);
+    C2* res;
+    if constexpr (TC > 0)
+        res = fft_tau_ct<R, TC, TSC, 256>(a, b, w2);
+    else
+        res = fft_tau<R>(a, b, w2, T, TS, plan);
     const long ob = (long)rhs * T * N;
     double acc = 0.0;
     for (int item = threadIdx.x; item < T * TS; item += blockDim.x) {
@@ -637,10 +651,23 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     C2* h0 = reinterpret_cast<C2*>(c->cbuf0);
     C2* h1 = reinterpret_cast<C2*>(c->cbuf1);
     int rc;
-    if ((rc = set_smem_attr<R>((const void*)k_tau_fwd<R>, sm))) return rc;
-    if ((rc = set_smem_attr<R>((const void*)k_tau_inv<R>, sm))) return rc;
+    // the configured lengths get transforms specialised at compile time
+    constexpr int TSW = sizeof(R) == 8 ? 16 : 32;   // tile_sites(prec)
+    using FwdK = void (*)(const R*, C2*, const C2*, int, int, int, RadixPlan, R);
+    using InvK = void (*)(const C2*, R*, const C2*, int, int, int, RadixPlan, R, const R*, double*);
+    FwdK fwd = k_tau_fwd<R>;
+    InvK inv = k_tau_inv<R>;
+    switch (c->T) {
+    case 40: fwd = k_tau_fwd<R, 40, TSW>; inv = k_tau_inv<R, 40, TSW>; break;
+    case 120: fwd = k_tau_fwd<R, 120, TSW>; inv = k_tau_inv<R, 120, TSW>; break;
+    case 160: fwd = k_tau_fwd<R, 160, TSW>; inv = k_tau_inv<R, 160, TSW>; break;
+    case 200: fwd = k_tau_fwd<R, 200, TSW>; inv = k_tau_inv<R, 200, TSW>; break;
+    default: break;
+    }
+    if ((rc = set_smem_attr<R>((const void*)fwd, sm))) return rc;
+    if ((rc = set_smem_attr<R>((const void*)inv, sm))) return rc;
     const R isq = (R)(1.0 / sqrt((double)c->T));
-    k_tau_fwd<R><<<gf, 256, sm, s>>>(v, h0, w2, c->T, c->N, TS, plan, isq);
+    fwd<<<gf, 256, sm, s>>>(v, h0, w2, c->T, c->N, TS, plan, isq);
     HOL_CHECK_LAUNCH("k_tau_fwd");
     KpmArgs ka;
     ka.L = c->L;
@@ -681,8 +708,7 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
                                                n_rhs, ka);
         HOL_CHECK_LAUNCH("k_kpm");
     }
-    k_tau_inv<R><<<gf, 256, sm, s>>>(h1, out, w2, c->T, c->N, TS, plan, (R)2 * isq, rdot,
-                                     dot_part);
+    inv<<<gf, 256, sm, s>>>(h1, out, w2, c->T, c->N, TS, plan, (R)2 * isq, rdot, dot_part);
     HOL_CHECK_LAUNCH("k_tau_inv");
     return HOL_OK;
 }
