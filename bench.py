@@ -271,7 +271,11 @@ def run_ours(a):
     up_cnt, up_ms, _ = ctx.timer_read(hg.TIMER_UPDATE)
     fo_cnt, fo_ms, _ = ctx.timer_read(hg.TIMER_FORCE)
     pc_cnt, pc_ms, _ = ctx.timer_read(hg.TIMER_PRECOND)
-    if ctx.get_option("merged_cg") and not a.precond:
+    if ctx.get_option("fused_cg") and not a.precond:
+        ctx_kernel_name = ("k_cg_fused<32> (one kernel per CG iteration: r' = r - alpha q, "
+                           "p' = r' + beta p, x += alpha p, q' = M^T M p', partials of "
+                           "r'.r', p'.q', r'.q', q'.q')")
+    elif ctx.get_option("merged_cg") and not a.precond:
         ctx_kernel_name = ("k_cg_merged (one kernel per CG iteration: p = r + beta p, "
                            "s = w + beta s, x += alpha p every other iteration, "
                            "r' = r - alpha s, w' = M^T M r', r'.r' and |M r'|^2)")

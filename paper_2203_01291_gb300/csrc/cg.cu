@@ -348,6 +348,7 @@ __global__ void k_copy_rows(const double* __restrict__ src, double* __restrict__
         dst[(long)rhs * kRedStride + k] = src[(long)rhs * kRedStride + k];
 }
 
+
 struct Banks {
     double* pq;      // matvec-unit partials of p.q
     double* dz[2];   // alternating partials of r.z (r.r without preconditioner)
@@ -711,6 +712,195 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
 }
 
 
+// Mixed plain CG with one fused kernel per iteration (k_cg_fused in
+// matvec.cu): the vector update of iteration i and the operator of
+// iteration i + 1 share one pass over the vectors, and beta comes from the
+// exact expansion |r - alpha q|^2 = r.r - 2 alpha r.q + alpha^2 q.q of
+// partials the previous pass accumulated. r, p and q are double buffered by
+// iteration parity (neighbouring units read the tau halo); x is updated in
+// place every iteration. Polling, reliable updates and certification work as
+// in cg_run; a reliable update replaces r by the true residual, builds the
+// direction from it and the previous direction (p = r + beta p_prev with
+// beta = -(r, A p_prev) / (p_prev, A p_prev)), recomputes q = A p and the
+// partials for the flagged rhs.
+static int cg_run_fused(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_opts* o,
+                        int* iters, double* resid, cudaStream_t s)
+{
+    const long n = c->n;
+    const int nb2 = elementwise_blocks(c);
+    const dim3 g2(nb2, n_rhs);
+    const Banks B = banks_of(c);
+    const int pstride = matvec_pstride(c);
+    const int nrun = c->T / c->mv_k;
+    int* act_d = c->mask;
+    int* rel_d = c->mask + c->p.max_rhs;
+    int* act_h = c->hflag;
+    int* rel_h = c->hflag + c->p.max_rhs;
+    double* hb = c->hbuf;
+    const long R = c->p.max_rhs;
+    int rc;
+    float* Rv[2] = {c->v32a, c->v32g};
+    float* Pv[2] = {c->v32b, c->v32c};
+    float* Qv[2] = {c->v32d, c->v32h};
+    float* X = c->v32e;
+    double* t64 = c->v64a;
+    double* rt64 = c->v64b;
+    auto bank = [&](int k) { return c->part + (long)k * c->part_len; };
+    double* GG[2] = {bank(12), bank(13)};
+    double* PQ[2] = {bank(14), bank(15)};
+    double* RQ[2] = {bank(16), bank(17)};
+    double* QQ[2] = {bank(18), bank(19)};
+    double* cj0 = bank(8);
+    double* cj1 = bank(9);
+    const double nd = (double)n;
+
+    HOL_CUDA(cudaMemsetAsync(v, 0, (size_t)n_rhs * n * sizeof(double), s));
+    k_cg_init<float><<<g2, 256, 0, s>>>(b, Rv[0], X, n, B.bn, cj1);
+    HOL_CHECK_LAUNCH("k_cg_init");
+    if ((rc = rows_to_host(c, B.bn, nb2, n_rhs, hb, s))) return rc;
+    std::vector<double> bnorm(n_rhs), true_res(n_rhs, 1.0);
+    std::vector<int> it(n_rhs, 0), since(n_rhs, 0), done(n_rhs, 0);
+    int n_active = 0;
+    for (int k = 0; k < n_rhs; ++k) {
+        bnorm[k] = sqrt(hb[k]);
+        if (!isfinite(bnorm[k])) return set_error(HOL_ENUMERIC, "cg_solve: non-finite |b|");
+        act_h[k] = bnorm[k] != 0.0;
+        if (!act_h[k]) {   // v = 0 is exact
+            done[k] = 1;
+            true_res[k] = 0.0;
+        }
+        n_active += act_h[k];
+        rel_h[k] = 0;
+    }
+    HOL_CUDA(cudaMemcpyAsync(act_d, act_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (n_active > 0) {   // p = r, q = A p and the partials of iteration 0
+        if ((rc = launch_cg_mtm32(c, Rv[0], Rv[0], Pv[0], Qv[0], n_rhs, act_d, nullptr, nullptr,
+                                  0, 0, 1, PQ[0], s)))
+            return rc;
+        if ((rc = launch_unit_dots(c, Rv[0], Qv[0], n_rhs, act_d, GG[0], RQ[0], QQ[0], s)))
+            return rc;
+    }
+    const int chk = o->check_every > 0 ? o->check_every : 10;
+    const int rel_every = o->reliable_every > 0 ? o->reliable_every : 1 << 30;
+    EventPair evp;
+    if ((rc = evp.create())) return rc;
+    int q = 0;
+    bool have_prev = false;
+    int a = 0;   // parity of the current r, p, q and partials
+    int k_it = 0;
+    while (n_active > 0 && k_it < o->max_iter) {
+        int chunk = chk;
+        if (chunk > o->max_iter - k_it) chunk = o->max_iter - k_it;
+        for (int j = 0; j < chunk; ++j) {
+            const int z = 1 - a;
+            FusedPartials fp{GG[a], PQ[a], RQ[a], QQ[a], GG[z], PQ[z], RQ[z], QQ[z]};
+            timer_start(c, KT_OPERATOR, s, n_active * nd * 32.0 + nd * 4.0);
+            rc = launch_cg_fused(c, Rv[a], Qv[a], Pv[a], X, Rv[z], Pv[z], Qv[z], n_rhs, act_d, fp,
+                                 s);
+            if (rc) return rc;
+            timer_stop(c, KT_OPERATOR, s);
+            a = z;
+        }
+        k_it += chunk;
+        // estimate read one chunk behind, as in cg_run
+        double* est_h = hb + (2 + q) * R;
+        if ((rc = rows_enqueue(GG[a], nrun, pstride, n_rhs, B.red + (1 + q) * R, est_h, evp.ev[q],
+                               s)))
+            return rc;
+        bool sync = k_it >= o->max_iter;
+        for (int k = 0; k < n_rhs; ++k) {
+            if (!act_h[k]) continue;
+            it[k] += chunk;
+            since[k] += chunk;
+            if (since[k] >= rel_every) sync = true;
+        }
+        if (!sync && have_prev) {
+            HOL_CUDA(cudaEventSynchronize(evp.ev[1 - q]));
+            const double* prev = hb + (2 + (1 - q)) * R;
+            for (int k = 0; k < n_rhs; ++k) {
+                if (!act_h[k]) continue;
+                const double est = sqrt(prev[k]) / bnorm[k];
+                if (!isfinite(est))
+                    return set_error(HOL_ENUMERIC,
+                                     "cg_solve: non-finite residual (rhs %d, iter %d)", k,
+                                     it[k] - chunk);
+                if (est < o->tol) sync = true;
+            }
+        }
+        if (!sync) {
+            have_prev = true;
+            q = 1 - q;
+            continue;
+        }
+        HOL_CUDA(cudaEventSynchronize(evp.ev[q]));
+        have_prev = false;
+        int n_rel = 0;
+        for (int k = 0; k < n_rhs; ++k) {
+            rel_h[k] = 0;
+            if (!act_h[k]) continue;
+            const double est = sqrt(est_h[k]) / bnorm[k];
+            if (!isfinite(est))
+                return set_error(HOL_ENUMERIC, "cg_solve: non-finite residual (rhs %d, iter %d)",
+                                 k, it[k]);
+            if (est < o->tol || since[k] >= rel_every || k_it >= o->max_iter) {
+                rel_h[k] = 1;
+                ++n_rel;
+            }
+        }
+        if (n_rel == 0) continue;
+        const int z = 1 - a;
+        HOL_CUDA(cudaMemcpyAsync(rel_d, rel_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
+        k_fold<<<g2, 256, 0, s>>>(v, X, n, rel_d);
+        HOL_CHECK_LAUNCH("k_fold");
+        if ((rc = launch_M(c, HOL_F64, v, t64, n_rhs, rel_d, nullptr, s))) return rc;
+        if ((rc = launch_MT_resid64(c, t64, b, rt64, n_rhs, rel_d, s))) return rc;
+        k_recast<float><<<g2, 256, 0, s>>>(rt64, Rv[a], n, rel_d, B.tr, cj1);
+        HOL_CHECK_LAUNCH("k_recast");
+        // The stored p (parity a) already contains the old r; the direction
+        // the last pass stepped along, p_prev with q_prev = A p_prev, is still
+        // in parity z. New direction: p = r + beta p_prev with
+        // beta = -(r, q_prev) / (p_prev, q_prev) (p_prev is scaled by beta,
+        // then p = r + p_prev from identical partial rows), q = A p and its
+        // p.q partials, written to parity a; then the r.r, r.q, q.q partials.
+        k_conj_dots<float><<<g2, 256, 0, s>>>(Rv[a], Pv[z], Qv[z], n, rel_d, cj0, cj1);
+        HOL_CHECK_LAUNCH("k_conj_dots");
+        k_conj_scale<float><<<g2, 256, 0, s>>>(Pv[z], n, rel_d, cj0, cj1, nb2);
+        HOL_CHECK_LAUNCH("k_conj_scale");
+        if ((rc = launch_cg_mtm32(c, Rv[a], Pv[z], Pv[a], Qv[a], n_rhs, rel_d, B.tr, B.tr,
+                                  kRedStride, nb2, 0, PQ[a], s)))
+            return rc;
+        if ((rc = launch_unit_dots(c, Rv[a], Qv[a], n_rhs, rel_d, GG[a], RQ[a], QQ[a], s)))
+            return rc;
+        if ((rc = rows_to_host(c, B.tr, nb2, n_rhs, hb, s))) return rc;
+        int changed = 0;
+        for (int k = 0; k < n_rhs; ++k) {
+            if (!rel_h[k]) continue;
+            since[k] = 0;
+            true_res[k] = sqrt(hb[k]) / bnorm[k];
+            if (!isfinite(true_res[k]))
+                return set_error(HOL_ENUMERIC, "cg_solve: non-finite true residual (rhs %d)", k);
+            if (true_res[k] < o->tol) {
+                done[k] = 1;
+                act_h[k] = 0;
+                --n_active;
+                changed = 1;
+            }
+        }
+        if (changed)
+            HOL_CUDA(cudaMemcpyAsync(act_d, act_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
+    }
+    HOL_CUDA(cudaStreamSynchronize(s));
+    int all = 1;
+    for (int k = 0; k < n_rhs; ++k) {
+        if (iters) iters[k] = it[k];
+        if (resid) resid[k] = true_res[k];
+        all &= done[k];
+    }
+    if (!all)
+        return set_error(HOL_ENOTCONV, "cg_solve: not converged within %d iterations", o->max_iter);
+    return HOL_OK;
+}
+
 // Mixed plain CG with one fused kernel per iteration (k_cg_merged in
 // matvec.cu, Chronopoulos-Gear recurrences). The FP32 state per rhs is
 // x (the increment e), r, w = A r, p, s = A p; r, w, p, s are double
@@ -899,6 +1089,8 @@ extern "C" int cg_solve(hol_ctx* c, const double* b, double* v, int n_rhs, const
     if (!(o->tol > 0.0) || o->max_iter < 1)
         return set_error(HOL_EINVAL, "cg_solve: tol must be > 0 and max_iter >= 1");
     if (b == v) return set_error(HOL_EINVAL, "cg_solve: b and v must not overlap");
+    if (c->fused && o->prec == HOL_F32 && !o->precond)
+        return cg_run_fused(c, b, v, n_rhs, o, iters, resid, (cudaStream_t)stream);
     if (c->merged && o->prec == HOL_F32 && !o->precond)
         return cg_run_merged(c, b, v, n_rhs, o, iters, resid, (cudaStream_t)stream);
     return cg_run(c, b, v, n_rhs, o, iters, resid, (cudaStream_t)stream);

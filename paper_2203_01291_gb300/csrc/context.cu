@@ -189,6 +189,7 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     c->kpm_reg = 1;
     c->persist = 0;
     c->merged = 0;
+    c->fused = 0;
     c->pdl = 1;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         free_ctx(c);
@@ -372,6 +373,22 @@ extern "C" int hol_timer_read(hol_ctx* c, int klass, int* count, double* total_m
     return HOL_OK;
 }
 
+// Three more FP32 vector sets and the merged solver's scalar slots, for the
+// merged and fused CG loops (allocated once, on first use).
+static int alloc_extra_vectors(hol_ctx* c)
+{
+    if (c->v32g) return HOL_OK;
+    const size_t vb = (size_t)c->p.max_rhs * c->n * sizeof(float);
+    float** bufs[3] = {&c->v32g, &c->v32h, &c->v32i};
+    for (float** b : bufs) {
+        const cudaError_t e = cudaMalloc((void**)b, vb);
+        if (e != cudaSuccess) return cuda_error(e, "hol_set_option: solver vector sets");
+    }
+    const cudaError_t e = cudaMalloc((void**)&c->cgs, 8 * c->p.max_rhs * sizeof(double));
+    if (e != cudaSuccess) return cuda_error(e, "hol_set_option: solver scalars");
+    return HOL_OK;
+}
+
 extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
 {
     if (!c || !name) return set_error(HOL_EINVAL, "hol_set_option: null argument");
@@ -401,20 +418,17 @@ extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
         c->persist = value ? 1 : 0;
     } else if (is("pdl")) {
         c->pdl = value ? 1 : 0;
-    } else if (is("merged_cg")) {
+    } else if (is("merged_cg") || is("fused_cg")) {
         if (value && c->L % 8)
-            return set_error(HOL_EINVAL, "hol_set_option: merged_cg needs L % 8 == 0");
-        if (value && !c->v32g) {   // three more FP32 vector sets and the scalar slots
-            const size_t vb = (size_t)c->p.max_rhs * c->n * sizeof(float);
-            float** bufs[3] = {&c->v32g, &c->v32h, &c->v32i};
-            for (float** b : bufs) {
-                const cudaError_t e = cudaMalloc((void**)b, vb);
-                if (e != cudaSuccess) return cuda_error(e, "hol_set_option: merged_cg buffers");
-            }
-            const cudaError_t e = cudaMalloc((void**)&c->cgs, 8 * c->p.max_rhs * sizeof(double));
-            if (e != cudaSuccess) return cuda_error(e, "hol_set_option: merged_cg scalars");
+            return set_error(HOL_EINVAL, "hol_set_option: %s needs L %% 8 == 0", name);
+        if (value) {
+            const int rc = alloc_extra_vectors(c);
+            if (rc) return rc;
         }
-        c->merged = value ? 1 : 0;
+        if (is("merged_cg"))
+            c->merged = value ? 1 : 0;
+        else
+            c->fused = value ? 1 : 0;
     } else {
         return set_error(HOL_EINVAL, "hol_set_option: unknown option '%s'", name);
     }
@@ -431,6 +445,7 @@ extern "C" int hol_get_option(const hol_ctx* c, const char* name, int* value)
     else if (is("kpm_registers")) *value = c->kpm_reg;
     else if (is("persistent_cg")) *value = c->persist;
     else if (is("merged_cg")) *value = c->merged;
+    else if (is("fused_cg")) *value = c->fused;
     else if (is("pdl")) *value = c->pdl;
     else return set_error(HOL_EINVAL, "hol_get_option: unknown option '%s'", name);
     return HOL_OK;

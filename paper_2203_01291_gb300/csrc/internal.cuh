@@ -77,7 +77,7 @@ constexpr int kMaxL = 32;
 // partial-sum banks have a fixed stride).
 constexpr int kRedStride = 256;
 // Number of partial-sum banks in hol_ctx::part.
-constexpr int kBanks = 12;
+constexpr int kBanks = 20;
 
 // Device-side scalars kept by a context (FP64).
 enum Scalar {
@@ -130,7 +130,7 @@ struct hol_ctx {
     int* mask;           // [2*max_rhs] active / reliable-update flags (device)
     double* v64f;
     float* v32f;
-    float* v32g;         // merged CG only (allocated when the option is set)
+    float* v32g;         // merged / fused CG only (allocated when an option needs them)
     float* v32h;
     float* v32i;
     double* cgs;         // merged CG scalars [2][max_rhs][4]: alpha, gamma, mode
@@ -161,7 +161,8 @@ struct hol_ctx {
     int mv_vec;          // use the float4 layout of the fused FP32 M^T M (L % 8 == 0)
     int kpm_reg;         // use the register KPM kernel (FP32, L = 16 or 32)
     int persist;         // use the persistent fused CG kernel when it fits
-    int merged;          // mixed plain CG as one fused kernel per iteration
+    int merged;          // mixed plain CG as one merged (Chronopoulos-Gear) kernel per iteration
+    int fused;           // mixed plain CG with the vector update fused into the operator
     int pdl;             // programmatic dependent launch of the CG kernels
 };
 
@@ -242,6 +243,25 @@ struct MergedScal {
 int launch_cg_merged(const hol_ctx* c, const float* r, const float* w, const float* pold,
                      const float* sold, float* e, float* pnew, float* snew, float* rnew,
                      float* wnew, int n_rhs, const int* mask, const MergedScal& sc,
+                     cudaStream_t s);
+// Unit partials of the fused CG iteration (layout of matvec_pstride / nrun).
+struct FusedPartials {
+    const double* g;    // r.r, p.q, r.q, q.q of the current iteration
+    const double* pq;
+    const double* rq;
+    const double* qq;
+    double* g_out;      // the same for the next iteration
+    double* pq_out;
+    double* rq_out;
+    double* qq_out;
+};
+// One fused CG iteration (vector update + next operator; float4 layout).
+int launch_cg_fused(const hol_ctx* c, const float* r, const float* q, const float* pold, float* x,
+                    float* rnew, float* pnew, float* qnew, int n_rhs, const int* mask,
+                    const FusedPartials& fp, cudaStream_t s);
+// Unit partials of r.r, r.q, q.q for the flagged rhs.
+int launch_unit_dots(const hol_ctx* c, const float* r, const float* q, int n_rhs,
+                     const int* mask, double* g_out, double* rq_out, double* qq_out,
                      cudaStream_t s);
 int matvec_pstride(const hol_ctx* c);          // per-rhs stride of unit partials
 int matvec_units(const hol_ctx* c, int n_rhs); // upper bound of units per call

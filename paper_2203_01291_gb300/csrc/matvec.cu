@@ -959,6 +959,248 @@ __global__ void __launch_bounds__(32 * NW) k_cg_mtm32_split(const float* __restr
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Fused CG iteration (float4 layout, cp.async ring of r, q, p, expV, x): the
+// vector update of iteration i and the operator of iteration i + 1 in one
+// pass. From the unit partials of the previous pass (g = r.r, pq = p.q,
+// rq = r.q, qq = q.q, all of iteration i):
+//   alpha = g / pq,  g' = |r - alpha q|^2 = g - 2 alpha rq + alpha^2 qq,
+//   beta = g' / g,   r' = r - alpha q,  p' = r' + beta p,  x += alpha p,
+//   q' = M^T M p',   and the new partials g' (of the stored r'), p'.q',
+//   r'.q', q'.q'.
+// g' is the exact expansion of |r'|^2, so no conjugacy is assumed; r' is
+// formed on the fly for the unit's slices and both tau neighbours.
+// ---------------------------------------------------------------------------
+struct FusedBanks {
+    const double* g;    // unit partials in (stride pstride, nrun per rhs)
+    const double* pq;
+    const double* rq;
+    const double* qq;
+    double* g_out;
+    double* pq_out;
+    double* rq_out;
+    double* qq_out;
+};
+
+template <int L>
+__global__ void __launch_bounds__(128, 2) k_cg_fused(const float* __restrict__ r,
+                                                     const float* __restrict__ q,
+                                                     const float* __restrict__ pold,
+                                                     float* __restrict__ x,
+                                                     float* __restrict__ rnew,
+                                                     float* __restrict__ pnew,
+                                                     float* __restrict__ qnew,
+                                                     const float* __restrict__ ev, MvGeom gm,
+                                                     const int* __restrict__ mask, FusedBanks bk,
+                                                     float th)
+{
+    pdl_wait();      // inputs come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
+    constexpr int N = L * L;
+    constexpr int RT = L / 4;
+    constexpr int S = 2;
+    constexpr int NA = 5;   // ring arrays: r, q, p, expV, x
+    // [warp][ring: slot][array][RT][32] then [warp][r' of the slice awaiting output][RT][32]
+    extern __shared__ __align__(16) float4 ring[];
+    const Geom4<L> geo;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* my = ring + (long)wib * ((S * NA + 1) * RT * 32);
+    auto slot_ptr = [&](int slot, int arr, int k) -> float4* {
+        return my + ((slot * NA + arr) * RT + k) * 32 + lane;
+    };
+    auto rbuf = [&](int k) -> float4* { return my + ((S * NA) * RT + k) * 32 + lane; };
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int rhs = warp / gm.wpr;
+    if (rhs >= gm.n_rhs) return;
+    if (mask != nullptr && mask[rhs] == 0) return;
+    const int run = (warp - rhs * gm.wpr) * Geom4<L>::G + geo.g;
+    const bool valid = geo.ok && run < gm.nrun;
+    const int t0 = (run < gm.nrun ? run : gm.nrun - 1) * gm.K;
+    const long base = (long)rhs * gm.T * N;
+    auto seq = [&](int j) -> int {
+        int t = t0 - 1 + j;
+        if (t < 0) t += gm.T;
+        if (t >= gm.T) t -= gm.T;
+        return t;
+    };
+    const int last = gm.K + 1;
+    auto issue = [&](int j) {
+        if (j <= last) {
+            const int t = seq(j);
+            const long o = base + (long)t * N;
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                cp_async16(slot_ptr(j % S, 0, k), r + o + geo.off(k));
+                cp_async16(slot_ptr(j % S, 1, k), q + o + geo.off(k));
+                cp_async16(slot_ptr(j % S, 2, k), pold + o + geo.off(k));
+                if (j > 0) cp_async16(slot_ptr(j % S, 3, k), ev + (long)t * N + geo.off(k));
+                if (j > 0 && j <= gm.K) cp_async16(slot_ptr(j % S, 4, k), x + o + geo.off(k));
+            }
+        }
+        cp_async_commit();
+    };
+    issue(0);
+
+    // scalars of iteration i (every warp forms them from the same partials)
+    const long pb = (long)rhs * gm.pstride;
+    const double g = warp_sum_array(bk.g + pb, gm.nrun);
+    const double pq = warp_sum_array(bk.pq + pb, gm.nrun);
+    const double rq = warp_sum_array(bk.rq + pb, gm.nrun);
+    const double qq = warp_sum_array(bk.qq + pb, gm.nrun);
+    const double ad = g / pq;
+    double gn = g - 2.0 * ad * rq + ad * ad * qq;
+    if (!(gn > 0.0)) gn = 0.0;   // roundoff below zero: restart the direction (beta = 0)
+    const float a = (float)ad, bt = (float)(gn / g);
+
+    // r' and p' of ring slot `sl` (row k)
+    auto rn_of = [&](int sl, int k) -> float4 {
+        return fma4s(-a, *slot_ptr(sl, 1, k), *slot_ptr(sl, 0, k));
+    };
+
+    double gacc = 0.0, pacc = 0.0, rqacc = 0.0, qqacc = 0.0;
+    float4 W[RT], X[RT], P[RT], Y[RT];
+    issue(1);
+    cp_async_wait<1>();   // slice j = 0 (halo t0 - 1)
+#pragma unroll
+    for (int k = 0; k < RT; ++k) Y[k] = fma4s(bt, *slot_ptr(0, 2, k), rn_of(0, k));
+    c4_apply<L>(Y, geo, th);
+    issue(2);
+    cp_async_wait<1>();   // slice j = 1 (t0)
+    {
+        const long o = base + (long)t0 * N;
+        const float sg = (t0 == 0) ? 1.0f : -1.0f;
+        float gp = 0.0f;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float4 rv = rn_of(1, k);
+            const float4 po = *slot_ptr(1, 2, k);
+            const float4 pv = fma4s(bt, po, rv);
+            if (valid) {
+                st4(rnew, o + geo.off(k), rv);
+                st4(pnew, o + geo.off(k), pv);
+                st4(x, o + geo.off(k), fma4s(a, po, *slot_ptr(1, 4, k)));
+            }
+            *rbuf(k) = rv;
+            gp = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, gp))));
+            X[k] = pv;
+            const float4 d = *slot_ptr(1, 3, k);
+            W[k] = make_float4(fmaf(sg * d.x, Y[k].x, pv.x), fmaf(sg * d.y, Y[k].y, pv.y),
+                               fmaf(sg * d.z, Y[k].z, pv.z), fmaf(sg * d.w, Y[k].w, pv.w));
+        }
+        gacc += (double)gp;
+        c4_apply<L>(X, geo, th);
+    }
+    for (int s = 0; s < gm.K; ++s) {
+        const int j = s + 2;             // slice t0 + 1 + s
+        issue(j + 1);
+        cp_async_wait<1>();
+        const int sl = j % S;
+        const int tau = t0 + s;
+        const int tp = (tau + 1 == gm.T) ? 0 : tau + 1;
+        const long op = base + (long)tp * N;
+        const float sgp = (tp == 0) ? 1.0f : -1.0f;
+        const bool own = valid && (s + 1 < gm.K);
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float4 rv = rn_of(sl, k);
+            const float4 po = *slot_ptr(sl, 2, k);
+            const float4 pv = fma4s(bt, po, rv);
+            if (own) {
+                st4(rnew, op + geo.off(k), rv);
+                st4(pnew, op + geo.off(k), pv);
+                st4(x, op + geo.off(k), fma4s(a, po, *slot_ptr(sl, 4, k)));
+            }
+            P[k] = pv;
+            float4 d = *slot_ptr(sl, 3, k);
+            d.x *= sgp; d.y *= sgp; d.z *= sgp; d.w *= sgp;
+            X[k] = make_float4(fmaf(d.x, X[k].x, pv.x), fmaf(d.y, X[k].y, pv.y),
+                               fmaf(d.z, X[k].z, pv.z), fmaf(d.w, X[k].w, pv.w));
+            Y[k] = make_float4(d.x * X[k].x, d.y * X[k].y, d.z * X[k].z, d.w * X[k].w);
+        }
+        c4_apply<L>(P, geo, th);
+        c4_apply_t<L>(Y, geo, th);
+        const long o = base + (long)tau * N;
+        float pp = 0.0f, rqp = 0.0f, qqp = 0.0f;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float4 qv = make_float4(W[k].x + Y[k].x, W[k].y + Y[k].y, W[k].z + Y[k].z,
+                                          W[k].w + Y[k].w);
+            if (valid) st4(qnew, o + geo.off(k), qv);
+            const float4 rv = *rbuf(k);   // r' of slice tau
+            pp = fmaf(W[k].x, W[k].x, fmaf(W[k].y, W[k].y, fmaf(W[k].z, W[k].z, fmaf(W[k].w, W[k].w, pp))));
+            rqp = fmaf(rv.x, qv.x, fmaf(rv.y, qv.y, fmaf(rv.z, qv.z, fmaf(rv.w, qv.w, rqp))));
+            qqp = fmaf(qv.x, qv.x, fmaf(qv.y, qv.y, fmaf(qv.z, qv.z, fmaf(qv.w, qv.w, qqp))));
+            W[k] = X[k];
+            X[k] = P[k];
+        }
+        pacc += (double)pp;
+        rqacc += (double)rqp;
+        qqacc += (double)qqp;
+        if (s + 1 < gm.K) {   // r' of slice tp waits for its output in the next step
+            float gp = 0.0f;
+#pragma unroll
+            for (int k = 0; k < RT; ++k) {
+                const float4 rv = rn_of(sl, k);
+                *rbuf(k) = rv;
+                gp = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, gp))));
+            }
+            gacc += (double)gp;
+        }
+    }
+    cp_async_wait<0>();
+    group_store_sum<L>(gacc, valid, bk.g_out + pb + run);
+    __syncwarp();
+    group_store_sum<L>(pacc, valid, bk.pq_out + pb + run);
+    __syncwarp();
+    group_store_sum<L>(rqacc, valid, bk.rq_out + pb + run);
+    __syncwarp();
+    group_store_sum<L>(qqacc, valid, bk.qq_out + pb + run);
+}
+
+// Unit partials of r.r, r.q and q.q (same units and layout as the operator
+// kernels' partials), for the flagged rhs: one block per (unit, rhs).
+__global__ void __launch_bounds__(256) k_unit_dots(const float* __restrict__ r,
+                                                   const float* __restrict__ q, MvGeom gm, int N,
+                                                   const int* __restrict__ mask,
+                                                   double* __restrict__ g_out,
+                                                   double* __restrict__ rq_out,
+                                                   double* __restrict__ qq_out)
+{
+    const int run = blockIdx.x, rhs = blockIdx.y;
+    if (mask[rhs] == 0) return;
+    const long o = (long)rhs * gm.T * N + (long)run * gm.K * N;
+    const long len = (long)gm.K * N;
+    double gg = 0.0, rqs = 0.0, qqs = 0.0;
+    for (long k = threadIdx.x; 4 * k < len; k += blockDim.x) {
+        const float4 rv = ld4(r, o + 4 * k);
+        const float4 qv = ld4(q, o + 4 * k);
+        gg += (double)fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, rv.w * rv.w)));
+        rqs += (double)fmaf(rv.x, qv.x, fmaf(rv.y, qv.y, fmaf(rv.z, qv.z, rv.w * qv.w)));
+        qqs += (double)fmaf(qv.x, qv.x, fmaf(qv.y, qv.y, fmaf(qv.z, qv.z, qv.w * qv.w)));
+    }
+    __shared__ double red[3][8];
+    gg = warp_sum(gg);
+    rqs = warp_sum(rqs);
+    qqs = warp_sum(qqs);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        red[0][w] = gg;
+        red[1][w] = rqs;
+        red[2][w] = qqs;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i)
+            for (int m = 0; m < 3; ++m) t[m] += red[m][i];
+        const long pbi = (long)rhs * gm.pstride + run;
+        g_out[pbi] = t[0];
+        rq_out[pbi] = t[1];
+        qq_out[pbi] = t[2];
+    }
+}
+
 template <int L>
 int blocks_for(const hol_ctx* c, const MvGeom& g)
 {
@@ -1135,6 +1377,74 @@ int run_cg_merged(const hol_ctx* c, const float* r, const float* w, const float*
     }
 }
 
+
+template <int L>
+int run_cg_fused(const hol_ctx* c, const float* r, const float* q, const float* pold, float* x,
+                 float* rnew, float* pnew, float* qnew, int n_rhs, const int* mask,
+                 const FusedPartials& fp, cudaStream_t s)
+{
+    if constexpr (L % 8 == 0) {
+        const MvGeom g = make_geom<L>(c, n_rhs);
+        const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
+        const size_t sm = (size_t)c->mv_warps * (2 * 5 + 1) * (L / 4) * 32 * sizeof(float4);
+        static std::atomic<int> limit(0);
+        if ((int)sm > limit.load()) {
+            const int most = 4 * (2 * 5 + 1) * (L / 4) * 32 * (int)sizeof(float4);
+            HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_fused<L>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, most));
+            limit.store(most);
+        }
+        FusedBanks bk{fp.g, fp.pq, fp.rq, fp.qq, fp.g_out, fp.pq_out, fp.rq_out, fp.qq_out};
+        HOL_CUDA(launch_pdl(c, k_cg_fused<L>, nb, nt, sm, s, r, q, pold, x, rnew, pnew, qnew,
+                            c->ev32, g, mask, bk, (float)c->th));
+        HOL_CHECK_LAUNCH("k_cg_fused");
+        return HOL_OK;
+    } else {
+        return set_error(HOL_EINVAL, "fused CG needs L %% 8 == 0 (L=%d)", c->L);
+    }
+}
+
+template <int L>
+int run_unit_dots(const hol_ctx* c, const float* r, const float* q, int n_rhs, const int* mask,
+                  double* g_out, double* rq_out, double* qq_out, cudaStream_t s)
+{
+    const MvGeom g = make_geom<L>(c, n_rhs);
+    k_unit_dots<<<dim3(g.nrun, n_rhs), 256, 0, s>>>(r, q, g, c->N, mask, g_out, rq_out, qq_out);
+    HOL_CHECK_LAUNCH("k_unit_dots");
+    return HOL_OK;
+}
+
+}  // namespace
+
+int launch_cg_fused(const hol_ctx* c, const float* r, const float* q, const float* pold, float* x,
+                    float* rnew, float* pnew, float* qnew, int n_rhs, const int* mask,
+                    const FusedPartials& fp, cudaStream_t s)
+{
+    switch (c->L) {
+#define X(LL)                                                                               \
+    case LL:                                                                                \
+        return run_cg_fused<LL>(c, r, q, pold, x, rnew, pnew, qnew, n_rhs, mask, fp, s);
+        HOL_FOR_EACH_L(X)
+#undef X
+    }
+    return set_error(HOL_EINVAL, "unsupported L=%d", c->L);
+}
+
+int launch_unit_dots(const hol_ctx* c, const float* r, const float* q, int n_rhs,
+                     const int* mask, double* g_out, double* rq_out, double* qq_out,
+                     cudaStream_t s)
+{
+    switch (c->L) {
+#define X(LL)                                                                                \
+    case LL:                                                                                 \
+        return run_unit_dots<LL>(c, r, q, n_rhs, mask, g_out, rq_out, qq_out, s);
+        HOL_FOR_EACH_L(X)
+#undef X
+    }
+    return set_error(HOL_EINVAL, "unsupported L=%d", c->L);
+}
+
+namespace {
 }  // namespace
 
 int launch_cg_merged(const hol_ctx* c, const float* r, const float* w, const float* pold,

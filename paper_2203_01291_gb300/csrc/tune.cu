@@ -1,4 +1,4 @@
-// Launch-shape autotuner for the fused FP32 M^T M kernel of the CG iteration.
+// Launch-shape autotuner for the CG iteration kernels.
 //
 // Candidates: K (tau slices streamed per lane group) among the divisors
 // {1, 2, 4, 5, 8, 10} of Ltau, 1, 2 or 4 warps per block, for L = 32 the
@@ -6,14 +6,13 @@
 // the float4 layout with a cp.async ring of three slices (6), the streaming
 // float4 kernel with a cp.async ring across units (3), the float4 layout
 // with a two-slice cp.async ring (2), without (1), or the scalar register
-// layout (0). The split and streaming kernels fix their own block
-// shapes, so they are timed once per K. With the merged CG on, the merged iteration kernel is
-// timed instead over K and warps (its layout is fixed). Each candidate is
-// timed with CUDA
-// events on the caller's stream (2 warm-up and 10 timed launches on the
-// context's scratch vectors) and the fastest is kept in the context for every
-// later call. Candidates whose per-unit partial sums would not fit the
-// context's partial-sum bank are skipped.
+// layout (0). The split and streaming kernels fix their own block shapes, so
+// they are timed once per K. With the fused or merged CG on, that iteration
+// kernel is timed instead, over K and warps (its layout is fixed). Each
+// candidate is timed with CUDA events on the caller's stream (2 warm-up and
+// 10 timed launches on the context's scratch vectors) and the fastest is
+// kept in the context for every later call. Candidates whose per-unit
+// partial sums would not fit the context's partial-sum bank are skipped.
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
@@ -40,8 +39,13 @@ extern "C" int hol_tune(hol_ctx* c, int n_rhs, int* best_k, int* best_warps, int
     int rc = HOL_OK;
     // with the merged CG on, the merged iteration kernel is what the solver
     // launches: time it (its layout is fixed, so only K and warps vary)
-    const bool merged = c->merged != 0;
+    const bool fused = c->fused != 0;
+    const bool merged = c->merged != 0 || fused;
     MergedScal sc;
+    FusedPartials fp{c->part, c->part + c->part_len, c->part + 2 * c->part_len,
+                     c->part + 3 * c->part_len, c->part + 4 * c->part_len,
+                     c->part + 5 * c->part_len, c->part + 6 * c->part_len,
+                     c->part + 7 * c->part_len};
     if (merged) {
         HOL_CUDA(cudaMemsetAsync(c->part, 0, kBanks * c->part_len * sizeof(double), s));
         HOL_CUDA(cudaMemsetAsync(c->cgs, 0, 8 * c->p.max_rhs * sizeof(double), s));
@@ -61,6 +65,9 @@ extern "C" int hol_tune(hol_ctx* c, int n_rhs, int* best_k, int* best_warps, int
         if (!merged)
             return launch_cg_mtm32(c, c->v32a, c->v32a, nullptr, c->v32b, n_rhs, nullptr, nullptr,
                                    nullptr, 0, 0, 1, nullptr, s);
+        if (fused)
+            return launch_cg_fused(c, c->v32a, c->v32b, c->v32c, c->v32e, c->v32f, c->v32g,
+                                   c->v32h, n_rhs, nullptr, fp, s);
         sc.fold = (r & 1) ? 2 : 0;
         return launch_cg_merged(c, c->v32a, c->v32b, c->v32c, c->v32d, c->v32e, c->v32f, c->v32g,
                                 c->v32h, c->v32i, n_rhs, nullptr, sc, s);

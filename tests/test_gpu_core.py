@@ -281,13 +281,16 @@ MERGED_CASES = [(8, 24, 1, 7, 20), (16, 30, 3, 10, 50), (24, 12, 4, 3, 9), (32, 
                 (32, 30, 5, 1, 5), (16, 8, 2, 4, 1000)]
 
 
+@pytest.mark.parametrize("solver", ["merged_cg", "fused_cg"])
 @pytest.mark.parametrize("L,T,K,check_every,reliable_every", MERGED_CASES)
-def test_merged_cg_certified(L, T, K, check_every, reliable_every):
-    """The one-kernel-per-iteration mixed CG (Chronopoulos-Gear recurrences,
-    deferred x updates, restarts with recomputed A r and A p) reaches the
-    certified residual on right-hand sides of very different scale (they
-    leave the active set at different chunks), in about as many iterations
-    as the two-kernel solver."""
+def test_merged_cg_certified(L, T, K, check_every, reliable_every, solver):
+    """The one-kernel-per-iteration mixed CG loops (merged: Chronopoulos-Gear
+    recurrences with deferred x updates; fused: the vector update folded into
+    the next operator pass, beta from the expansion of |r - alpha q|^2), with
+    restarts after reliable updates, reach the certified residual on
+    right-hand sides of very different scale (they leave the active set at
+    different chunks), in about as many iterations as the two-kernel
+    solver."""
     w, x = _field(L, T, seed=31)
     nr = 5
     v = hi.gaussian_vectors(w, nr, seed=32) * np.array([1.0, 1e-3, 1e3, 1.0, 1e-6])[:, None, None]
@@ -298,7 +301,7 @@ def test_merged_cg_certified(L, T, K, check_every, reliable_every):
         ref = torch.empty_like(bt)
         its0, res0 = ctx.cg_solve(bt, ref, tol=1e-8, prec=hg.HOL_F32,
                                   reliable_every=reliable_every, check_every=check_every)
-        ctx.set_option("merged_cg", 1)
+        ctx.set_option(solver, 1)
         sol = torch.empty_like(bt)
         its1, res1 = ctx.cg_solve(bt, sol, tol=1e-8, prec=hg.HOL_F32,
                                   reliable_every=reliable_every, check_every=check_every)
@@ -309,15 +312,19 @@ def test_merged_cg_certified(L, T, K, check_every, reliable_every):
     assert np.all(np.asarray(its1) <= 1.5 * np.asarray(its0) + 2 * check_every + 10), (its0, its1)
 
 
-def test_merged_cg_big32_certified_by_oracle():
-    """The benchmark solve with the merged kernel: 16 right-hand sides
-    b = M^T R at L=32, Ltau=200 to 1e-8, residuals recomputed by the oracle."""
+@pytest.mark.parametrize("solver", ["merged_cg", "fused_cg"])
+def test_merged_cg_big32_certified_by_oracle(solver):
+    """The benchmark solve with the merged or fused kernel: 16 right-hand
+    sides b = M^T R at L=32, Ltau=200 to 1e-8, residuals recomputed by the
+    oracle."""
     w = hi.WORKLOADS["big32"]
     x = hi.phonon_field(w)
     R = hi.gaussian_vectors(w, w.n_rhs, seed=2)
     with _ctx(w, w.n_rhs) as ctx:
         ctx.set_field(torch.tensor(x, device=DEV))
-        ctx.set_option("merged_cg", 1)
+        ctx.set_option(solver, 1)
+        if solver == "fused_cg":
+            ctx.tune(w.n_rhs)
         Rt = torch.tensor(R, device=DEV)
         bt = torch.empty_like(Rt)
         ctx.fermion_matvec(hg.HOL_OP_MT, Rt, bt)
@@ -331,22 +338,23 @@ def test_merged_cg_big32_certified_by_oracle():
         assert MF.rel_residual(w, x, b[k], vm[k]) < 1.01e-8
 
 
-def test_merged_cg_option_rules():
+@pytest.mark.parametrize("solver", ["merged_cg", "fused_cg"])
+def test_merged_cg_option_rules(solver):
     w, x = _field(12, 10)
     with _ctx(w, 2) as ctx:
         with pytest.raises(hg.HolError):
-            ctx.set_option("merged_cg", 1)             # needs L % 8 == 0
+            ctx.set_option(solver, 1)                  # needs L % 8 == 0
     w, x = _field(8, 10)
     with _ctx(w, 2) as ctx:
         ctx.set_field(torch.tensor(x, device=DEV))
-        ctx.set_option("merged_cg", 1)
-        assert ctx.get_option("merged_cg") == 1
+        ctx.set_option(solver, 1)
+        assert ctx.get_option(solver) == 1
         # FP64 and preconditioned solves keep the two-kernel loop
         bt = torch.tensor(hi.gaussian_vectors(w, 2, seed=3), device=DEV)
         sol = torch.empty_like(bt)
         its, res = ctx.cg_solve(bt, sol, tol=1e-10, prec=hg.HOL_F64)
         assert np.all(res < 1e-10)
-        # the autotuner times the merged kernel; the tuned solve stays certified
+        # the autotuner times the iteration kernel; the tuned solve stays certified
         choice = ctx.tune(2)
         assert w.Ltau % choice["slices_per_group"] == 0
         assert ctx.get_option("slices_per_group") == choice["slices_per_group"]
