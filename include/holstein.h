@@ -333,13 +333,22 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  *                       kernels: each may be scheduled while its predecessor
  *                       finishes and waits on the device for its results
  *                       (0/1, default 1)
- *   "merged_cg"         plain mixed CG as one fused kernel per iteration
- *                       (single-reduction Chronopoulos-Gear recurrences of
- *                       the same CG, Eq. (CG); L % 8 == 0; allocates three
- *                       more FP32 vector sets of max_rhs N Ltau on first
- *                       use). Convergence is certified exactly as in the
- *                       two-kernel solver; iteration counts may differ by a
- *                       few percent (0/1)
+ *   "fused_cg"          plain mixed CG (cg_solve with prec HOL_F32 and no
+ *                       preconditioner) with one kernel per iteration: the
+ *                       vector update of an iteration is done inside the next
+ *                       operator pass and beta comes from the exact expansion
+ *                       |r - alpha q|^2 = r.r - 2 alpha r.q + alpha^2 q.q
+ *                       (the CG of Eq. (CG), rearranged). Needs L % 8 == 0;
+ *                       allocates three more FP32 vector sets of max_rhs
+ *                       N Ltau on first use. Default 0: the two-kernel
+ *                       iteration (operator, then update), measured as fast
+ *                       at the benchmark size (0/1)
+ *   "merged_cg"         with fused_cg 0: plain mixed CG as one kernel per
+ *                       iteration with single-reduction Chronopoulos-Gear
+ *                       recurrences (L % 8 == 0; allocates the same three
+ *                       vector sets on first use) (0/1)
+ * Every solver variant certifies convergence by the FP64 true residual;
+ * iteration counts may differ by a few percent between them.
  * Returns HOL_EINVAL for an unknown name or a value out of range (HOL_ECUDA
  * when an allocation fails).
  */

@@ -243,6 +243,8 @@ def test_fused_mtm_every_layout(layout, L, T, K):
         ctx.set_field(torch.tensor(x, device=DEV))
         ctx.set_option("slices_per_group", K)
         ctx.set_option("layout", layout)
+        if L % 8 == 0:
+            ctx.set_option("fused_cg", 0)              # the solve below runs this layout's kernel
         vt = torch.tensor(v, device=DEV, dtype=torch.float32)
         out = torch.empty_like(vt)
         ctx.fermion_matvec(hg.HOL_OP_MTM, vt, out)
@@ -297,6 +299,7 @@ def test_merged_cg_certified(L, T, K, check_every, reliable_every, solver):
     with _ctx(w, nr) as ctx:
         ctx.set_field(torch.tensor(x, device=DEV))
         ctx.set_option("slices_per_group", K)
+        ctx.set_option("fused_cg", 0)                  # reference: the two-kernel iteration
         bt = torch.tensor(v, device=DEV)
         ref = torch.empty_like(bt)
         its0, res0 = ctx.cg_solve(bt, ref, tol=1e-8, prec=hg.HOL_F32,
@@ -322,9 +325,9 @@ def test_merged_cg_big32_certified_by_oracle(solver):
     R = hi.gaussian_vectors(w, w.n_rhs, seed=2)
     with _ctx(w, w.n_rhs) as ctx:
         ctx.set_field(torch.tensor(x, device=DEV))
+        ctx.set_option("fused_cg", 0)
         ctx.set_option(solver, 1)
-        if solver == "fused_cg":
-            ctx.tune(w.n_rhs)
+        ctx.tune(w.n_rhs)
         Rt = torch.tensor(R, device=DEV)
         bt = torch.empty_like(Rt)
         ctx.fermion_matvec(hg.HOL_OP_MT, Rt, bt)
@@ -347,6 +350,8 @@ def test_merged_cg_option_rules(solver):
     w, x = _field(8, 10)
     with _ctx(w, 2) as ctx:
         ctx.set_field(torch.tensor(x, device=DEV))
+        assert ctx.get_option("fused_cg") == 0         # the two-kernel iteration by default
+        ctx.set_option("fused_cg", 0)
         ctx.set_option(solver, 1)
         assert ctx.get_option(solver) == 1
         # FP64 and preconditioned solves keep the two-kernel loop
