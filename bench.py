@@ -505,18 +505,43 @@ def measurement_leg(dev, n_rv=128):
             "mean_cg_iters": float(np.mean(its))}
 
 
-KERNEL_SOURCES = ("matvec.cu", "cb.cuh", "cb4.cuh", "cbs.cuh", "cg.cu")
+KERNEL_HEADERS = ("cb.cuh", "cb4.cuh")   # device helpers of the operator kernels
 
 
-def kernel_source_digest():
-    """Digest of the sources of the CG kernels (a profile taken on other
-    sources no longer describes the running kernel)."""
+def kernel_source_digest(kernel):
+    """Digest of a kernel's own source text (its __global__ definition in
+    csrc/) and of the device helper headers it uses: a profile taken on other
+    sources no longer describes the running kernel."""
+    import glob
     import hashlib
+    import re
+    name = kernel.split("<")[0]
+    pat = re.compile(r"__global__ void(?: __launch_bounds__\([^)]*\))? " + re.escape(name) + r"\(")
+    csrc = os.path.join(ROOT, "paper_2203_01291_gb300", "csrc")
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_2203_01291_gb300", "csrc", name), "rb") as f:
+    for hname in KERNEL_HEADERS:
+        with open(os.path.join(csrc, hname), "rb") as f:
             h.update(f.read())
-    return h.hexdigest()[:12]
+    for path in sorted(glob.glob(os.path.join(csrc, "*.cu"))):
+        src = open(path).read()
+        m = pat.search(src)
+        if not m:
+            continue
+        start = src.rfind("template <", 0, m.start())
+        if start < 0 or src.find(";", start, m.start()) >= 0:
+            start = m.start()
+        depth, k = 0, src.index("{", m.end())
+        while True:
+            if src[k] == "{":
+                depth += 1
+            elif src[k] == "}":
+                depth -= 1
+                if depth == 0:
+                    break
+            k += 1
+        h.update(src[start:k + 1].encode())
+        return h.hexdigest()[:12]
+    return None
 
 
 def traffic_from_profiles(kernel, alg_bytes):
@@ -526,7 +551,7 @@ def traffic_from_profiles(kernel, alg_bytes):
     profiles/*.md, scaled to this run's algorithmic bytes per launch. None
     when no summary matches the current kernel sources."""
     import glob
-    digest = kernel_source_digest()
+    digest = kernel_source_digest(kernel)
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path):
             if not line.startswith("traffic_per_launch:"):
