@@ -98,111 +98,42 @@ def barrier(world):
         dist.barrier()
 
 
-def reduce_max(world, val):
+def reduce_max(world, val, device="cuda"):
+    """Maximum of a per-rank scalar over the ranks (the job's time)."""
     if world == 1:
         return val
     import torch
     import torch.distributed as dist
-    t = torch.tensor([val], device="cuda", dtype=torch.float64)
+    t = torch.tensor([val], device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
-def reduce_sum(world, val):
+def reduce_sum(world, val, device="cuda"):
+    """Sum of a per-rank scalar over the ranks (the job's work)."""
     if world == 1:
         return val
     import torch
     import torch.distributed as dist
-    t = torch.tensor([val], device="cuda", dtype=torch.float64)
+    t = torch.tensor([val], device=device, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 
-# ----------------------------------------------------------------------------
-# clocks sampled during the timed region
-# ----------------------------------------------------------------------------
-class Clocks:
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, index):
-        self.index = index
-        self.proc = None
-        self.path = None
-
-    def start(self):
-        try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
-        except Exception:
-            self.proc = None
-
-    def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
-            except ValueError:
-                continue
-            for nm, val in zip(names, f[5:9]):
-                if val.lower() == "active":
-                    reasons.add(nm)
-        os.unlink(self.path)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+def job_rate(world, units, ms, device="cuda"):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed over the slowest rank's time (units per second)."""
+    return reduce_sum(world, units, device) / (reduce_max(world, ms, device) / 1e3)
 
 
-# ----------------------------------------------------------------------------
-# CPU baseline: the oracle as it stands (matrix-free C, FP64, OpenMP)
-# ----------------------------------------------------------------------------
-def cpu_oracle_solves(n_solves, seed_offset=0, with_force=True):
-    """Time n_solves single-rhs oracle CG solves (+ force) of the benchmark
-    workload. Returns (seconds, iterations list, threads)."""
-    from oracle import matfree as MF
-    w = WORKLOAD
-    x = hi.phonon_field(w, seed=w.seed + seed_offset)
-    R = hi.gaussian_vectors(w, n_solves, seed=2 + seed_offset)
-    t0 = time.perf_counter()
-    its = []
-    for k in range(n_solves):
-        b = MF.MT_apply(w, x, R[k])
-        v, it, res = MF.cg(w, x, b, tol=TOL, max_iter=100000)
-        its.append(it)
-        if with_force:
-            MF.force_fermion(w, x, v, b)
-    return time.perf_counter() - t0, its, MF.num_threads()
-
-
-def cpu_baseline_block(target_s=15.0):
-    one, its, thr = cpu_oracle_solves(1)
-    n = max(1, min(16, int(target_s / max(one, 1e-3))))
-    if n > 1:
-        tt, its2, thr = cpu_oracle_solves(n, seed_offset=0)
+def replica_inputs(w, n_rhs, rank, field="iid"):
+    """The seeded inputs of one rank's replica (phonon field and pseudofermion
+    draws); every rank draws its own."""
+    if field == "ar1":
+        x = hi.phonon_field_ar1(w, corr=1.0 / w.omega0, seed=w.seed + 100 * rank)
     else:
-        tt, its2 = one, its
-    return {"value": n / tt, "unit": "CG solves/s", "cores": thr, "kind": "oracle",
-            "sample": f"{n} single-rhs FP64 textbook CG solves (+ force) of the L=32 Ltau=200 "
-                      f"workload to residual 1e-8 (matrix-free C oracle, OpenMP), mean "
-                      f"{float(np.mean(its2)):.0f} iterations"}
+        x = hi.phonon_field(w, seed=w.seed + 100 * rank)
+    return x, hi.gaussian_vectors(w, n_rhs, seed=2 + 100 * rank)
 
 
 # ----------------------------------------------------------------------------
@@ -219,11 +150,7 @@ def run_ours(a):
     dev = torch.device("cuda", torch.cuda.current_device())
     w = WORKLOAD
     nr = w.n_rhs
-    if a.field == "ar1":
-        x = hi.phonon_field_ar1(w, corr=1.0 / w.omega0, seed=w.seed + 100 * rank)
-    else:
-        x = hi.phonon_field(w, seed=w.seed + 100 * rank)
-    R = hi.gaussian_vectors(w, nr, seed=2 + 100 * rank)
+    x, R = replica_inputs(w, nr, rank, a.field)
     ctx = hg.Context.from_workload(w, max_rhs=nr)
     xd = torch.tensor(x, device=dev)
     Rd = torch.tensor(R, device=dev)
@@ -296,8 +223,7 @@ def run_ours(a):
     iters = np.array(stats["iters"])          # [steps][rhs]
     assert np.all(np.array(stats["resid"]) < TOL)
     solves = a.steps * nr
-    total_solves = reduce_sum(world, solves)
-    value = total_solves / (ms_max / 1e3)
+    value = job_rate(world, solves, ms_total)
     # matvec count: 2 per CG iteration per rhs, M^T for b, 2 per reliable update
     # (counted as one per 50 iterations plus the final certification), 1 in the force
     rel = np.ceil(iters / RELIABLE_EVERY) + 1
