@@ -195,7 +195,7 @@ def run_ours(a):
     launches = hg.hol_launch_count() - l0
     ms_total = e0.elapsed_time(e1)
     op_cnt, op_ms, op_units = ctx.timer_read(hg.TIMER_OPERATOR)
-    up_cnt, up_ms, _ = ctx.timer_read(hg.TIMER_UPDATE)
+    up_cnt, up_ms, up_units = ctx.timer_read(hg.TIMER_UPDATE)
     fo_cnt, fo_ms, _ = ctx.timer_read(hg.TIMER_FORCE)
     pc_cnt, pc_ms, _ = ctx.timer_read(hg.TIMER_PRECOND)
     if ctx.get_option("fused_cg") and not a.precond:
@@ -242,6 +242,19 @@ def run_ours(a):
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
     traffic = traffic_from_profiles(ctx_kernel_name.split()[0], op_cnt and alg_bytes)
+
+    # The whole CG iteration against the same peak: its algorithmic bytes
+    # (operator + vector update, every array once) over the wall time per
+    # iteration of the timed steps, which also carries the reliable updates,
+    # the polling, the set-up, b = M^T R and the force.
+    it_bytes = alg_bytes + (up_units / up_cnt if up_cnt else 0.0)
+    it_count = float(np.sum(np.max(iters, axis=1)))   # iterations the loop ran, per step
+    it_us = ms_total * 1e3 / it_count
+    cg_iteration = {"alg_bytes": it_bytes, "us_per_iteration": it_us,
+                    "achieved_gbs": it_bytes / (it_us * 1e-6) / 1e9,
+                    "frac": it_bytes / (it_us * 1e-6) / 1e9 / hbm,
+                    "note": "operator + update bytes per iteration over the step's wall time per "
+                            "iteration (reliable updates, polling, set-up and force included)"}
 
     # FP64-only path on the same inputs (mixed vs FP64 at equal residual)
     fp64 = None
@@ -347,6 +360,7 @@ def run_ours(a):
                          "alg_bytes_per_launch": alg_bytes,
                          "avg_launch_ms": op_avg_ms, "launches": op_cnt,
                          "peak_src": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "cg_iteration": cg_iteration,
             "kernel_ms": {"cg_operator": op_ms, "cg_update": up_ms, "force": fo_ms,
                           "precond": pc_ms, "timed_total": ms_total,
                           "timer_stride": TIMER_STRIDE,
