@@ -136,6 +136,90 @@ def replica_inputs(w, n_rhs, rank, field="iid"):
     return x, hi.gaussian_vectors(w, n_rhs, seed=2 + 100 * rank)
 
 
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands (matrix-free C, FP64, OpenMP)
+# ----------------------------------------------------------------------------
+def cpu_oracle_solves(n_solves, seed_offset=0, with_force=True):
+    """Time n_solves single-rhs oracle CG solves (+ force) of the benchmark
+    workload. Returns (seconds, iterations list, threads)."""
+    from oracle import matfree as MF
+    w = WORKLOAD
+    x = hi.phonon_field(w, seed=w.seed + seed_offset)
+    R = hi.gaussian_vectors(w, n_solves, seed=2 + seed_offset)
+    t0 = time.perf_counter()
+    its = []
+    for k in range(n_solves):
+        b = MF.MT_apply(w, x, R[k])
+        v, it, res = MF.cg(w, x, b, tol=TOL, max_iter=100000)
+        its.append(it)
+        if with_force:
+            MF.force_fermion(w, x, v, b)
+    return time.perf_counter() - t0, its, MF.num_threads()
+
+
+def cpu_baseline_block(target_s=15.0):
+    one, its, thr = cpu_oracle_solves(1)
+    n = max(1, min(16, int(target_s / max(one, 1e-3))))
+    if n > 1:
+        tt, its2, thr = cpu_oracle_solves(n, seed_offset=0)
+    else:
+        tt, its2 = one, its
+    return {"value": n / tt, "unit": "CG solves/s", "cores": thr, "kind": "oracle",
+            "sample": f"{n} single-rhs FP64 textbook CG solves (+ force) of the L=32 Ltau=200 "
+                      f"workload to residual 1e-8 (matrix-free C oracle, OpenMP), mean "
+                      f"{float(np.mean(its2)):.0f} iterations"}
+
+
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
@@ -325,7 +409,8 @@ def run_ours(a):
 
     extra = None
     if not a.no_extra:
-        extra = {"trajectory": trajectory_leg(dev), "measurement": measurement_leg(dev)}
+        extra = {"trajectory": trajectory_leg(dev), "measurement": measurement_leg(dev),
+                 "global_updates": global_update_leg(dev)}
 
     alu = {"fp64_fma_gflops": hg.hol_fma_peak(hg.HOL_F64),
            "fp32_fma_gflops": hg.hol_fma_peak(hg.HOL_F32),
@@ -443,6 +528,39 @@ def measurement_leg(dev, n_rv=128):
     return {"workload": "L=28 Ltau=120 chain, 128 Z2 probes, 2-point + type-2 Wick",
             "measurements_per_s": 1e3 / ms, "ms_per_measurement": ms,
             "mean_cg_iters": float(np.mean(its))}
+
+
+def global_update_leg(dev, n_moves=16):
+    """Reflection and swap updates (Sec. IV) on the hmc16 workload: L=16,
+    Ltau=160, alpha=1.5, x ~ N(0.5, 1), two pseudofermion fields, alternating
+    single-site reflections and nearest-neighbour swaps at random sites, each
+    with one tight action solve (mixed precision, certified 1e-10)."""
+    import torch
+    import paper_2203_01291_gb300 as hg
+    w = hi.WORKLOADS["hmc16"]
+    rng = np.random.default_rng(901)
+    with hg.Context.from_workload(w, max_rhs=2) as ctx:
+        x = torch.tensor(hi.phonon_field(w), device=dev)
+        R = torch.tensor(hi.gaussian_vectors(w, 2, seed=902), device=dev)
+        Phi = torch.empty_like(R)
+        ctx.set_field(x)
+        ctx.pseudofermion_phi(R, Phi)
+        moves = [(k % 2, int(rng.integers(0, w.N)), float(rng.random())) for k in range(n_moves)]
+        acc, dS, S = ctx.global_update(x, Phi, 0, 0, -1, u=0.0, tol=1e-10, prec=hg.HOL_F32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n_acc = 0
+        for kind, i, u in moves:
+            j = (i + 1) % w.L + (i // w.L) * w.L    # x-neighbour
+            acc, dS, S = ctx.global_update(x, Phi, kind, i, j, u=u, tol=1e-10, prec=hg.HOL_F32,
+                                           S_cur=S)
+            n_acc += int(acc)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    return {"workload": "hmc16 L=16 Ltau=160, 2 pseudofermions, alternating reflections and "
+                        "neighbour swaps, action solve mixed to 1e-10",
+            "updates_per_s": n_moves / dt, "ms_per_update": dt / n_moves * 1e3,
+            "accepted": n_acc, "of": n_moves}
 
 
 KERNEL_HEADERS = ("cb.cuh", "cb4.cuh")   # device helpers of the operator kernels

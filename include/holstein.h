@@ -233,6 +233,31 @@ int fourier_accel_leapfrog(hol_ctx* ctx, double* x, const double* R_pf, const do
                            double* dH, double* terms, void* stream);
 
 /*
+ * Reflection and swap updates (Sec. IV): one Metropolis move of the phonon
+ * field at fixed pseudofermion fields. kind HOL_REFLECT proposes
+ * x_{i,tau} -> -x_{i,tau} at every tau of site i; HOL_SWAP exchanges the
+ * lines of sites i and j (j != i; the paper uses neighbours, any pair is
+ * accepted here). The action is S = S_B + (1/2) sum_sigma |A^{-T} Phi_sigma|^2
+ * (Eq. (S_again)), evaluated with b = Lambda^{-T} Phi and one cg_solve(opts)
+ * of the n_pf right-hand sides M^T M v = b (the paper uses a tight tolerance,
+ * 1e-10, for such action differences, Sec. VI B). The move is accepted when
+ * u < exp(-(S(x') - S(x))) (Eq. (metropolis)) with the caller's uniform draw u.
+ * x (device, [T][N], in/out) holds the kept field on return, and the
+ * context's field is set to it. Phi: device [n_pf][T][N], unchanged.
+ * S_cur (host, nullable, in/out): the action at x; when null or not finite on
+ * entry it is computed (one more solve); on return it holds the action of the
+ * kept field, so a sequence of moves needs one solve each. accepted, dS (host,
+ * nullable): the decision and S(x') - S(x). Uses the context scratch (the
+ * leapfrog buffers); synchronises `stream`. Errors: HOL_EINVAL (bad kind,
+ * sites or n_pf), HOL_ENOTCONV from the solve, HOL_ENUMERIC.
+ */
+#define HOL_REFLECT 0
+#define HOL_SWAP    1
+int global_update(hol_ctx* ctx, double* x, const double* Phi, int n_pf, int kind, int i, int j,
+                  double u, const hol_cg_opts* opts, double* S_cur, int* accepted, double* dS,
+                  void* stream);
+
+/*
  * Stochastic Green's-function measurement with FFT averaging (Sec. V).
  * xi: n_rv probe vectors [n_rv][T][N] (FP64, device; e.g. Z2 draws, so that
  * <xi_i xi_j> = delta_ij, Eq. (Hutch_approx)). Gxi (device, caller-owned,

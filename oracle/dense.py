@@ -420,6 +420,39 @@ def hmc_update(m: Model, x, R_pf, R_p, dt, N_t, n_t, m_reg):
 
 
 # ----------------------------------------------------------------------------
+# Reflection and swap updates (Sec. IV)
+# ----------------------------------------------------------------------------
+REFLECT, SWAP = 0, 1
+
+
+def propose_global(x, kind: int, i: int, j: int = -1) -> np.ndarray:
+    """The proposed field of a global move (Sec. IV): reflection x_{i,tau} ->
+    -x_{i,tau} at every tau, or swap of the site lines x_{i,.} and x_{j,.}."""
+    y = np.array(x, dtype=np.float64, copy=True)
+    if kind == REFLECT:
+        y[:, i] = -y[:, i]
+    elif kind == SWAP:
+        y[:, [i, j]] = y[:, [j, i]]
+    else:
+        raise ValueError(kind)
+    return y
+
+
+def action(m: Model, x, Phi) -> float:
+    """S = S_B + S_F at fixed pseudofermion fields (Eq. (S_decompose))."""
+    return S_B(m, x) + S_F(m, x, Phi)
+
+
+def global_update(m: Model, x, Phi, kind: int, i: int, j: int, u: float):
+    """Metropolis test (Eq. (metropolis)) of a reflection or swap move at
+    fixed Phi: returns (accepted, dS, x_kept)."""
+    y = propose_global(x, kind, i, j)
+    dS = action(m, y, Phi) - action(m, x, Phi)
+    acc = bool(u < np.exp(-dS))
+    return acc, dS, (y if acc else np.array(x, dtype=np.float64, copy=True))
+
+
+# ----------------------------------------------------------------------------
 # Adiabatic preconditioner (Sec. VI A, App. C)
 # ----------------------------------------------------------------------------
 def dbar(m: Model, x) -> np.ndarray:

@@ -23,7 +23,7 @@ import torch
 
 from ._abi import (HOL_ECUDA, HOL_EINVAL, HOL_ENOMEM, HOL_ENOTCONV, HOL_ENUMERIC, HOL_ETIMEOUT,
                    HOL_F32, HOL_F64, HOL_OK, HOL_OP_M, HOL_OP_MT, HOL_OP_MTM, HOL_PINV,
-                   HOL_PINV_PINVT, HOL_PINVT, hol_cg_opts, hol_md_opts,
+                   HOL_PINV_PINVT, HOL_PINVT, HOL_REFLECT, HOL_SWAP, hol_cg_opts, hol_md_opts,
                    hol_params, load, library_path)
 
 __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F64", "HOL_F32",
@@ -33,6 +33,7 @@ __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F6
            "hol_timer_read", "fermion_matvec_static", "mass_apply", "md_integrate",
            "fourier_accel_leapfrog", "hol_md_opts", "stochastic_measure", "hol_tune",
            "hmc_batch", "measure_batch", "hol_set_option", "hol_get_option", "hol_fma_peak",
+           "global_update", "HOL_REFLECT", "HOL_SWAP",
            "library_path", "load"]
 
 
@@ -179,6 +180,19 @@ def stochastic_measure(handle, xi: torch.Tensor, n_rv: int, opts: hol_cg_opts, G
                                      _ptr(G2, torch.float64, 2 * n, "G2"), g4, int(four_point), it,
                                      _stream()))
     return np.array(it[:], dtype=np.int64)
+
+
+def global_update(handle, x: torch.Tensor, Phi: torch.Tensor, n_pf: int, kind: int, i: int,
+                  j: int, u: float, opts: hol_cg_opts, S_cur: float | None, n: int):
+    """Reflection / swap move (include/holstein.h); returns (accepted, dS, S)."""
+    S = ctypes.c_double(float("nan") if S_cur is None else float(S_cur))
+    acc = ctypes.c_int(0)
+    d = ctypes.c_double(0.0)
+    _check(load().global_update(handle, _ptr(x, torch.float64, n, "x"),
+                                _ptr(Phi, torch.float64, n_pf * n, "Phi"), n_pf, int(kind),
+                                int(i), int(j), float(u), ctypes.byref(opts), ctypes.byref(S),
+                                ctypes.byref(acc), ctypes.byref(d), _stream()))
+    return bool(acc.value), d.value, S.value
 
 
 def hol_tune(handle, n_rhs: int) -> dict:
@@ -346,6 +360,16 @@ class Context:
                                opts: hol_md_opts, u: float):
         """Algorithm 1; returns (accepted, dH, [S_B, S_F, K] at start and end)."""
         return fourier_accel_leapfrog(self._h, x, R_pf, R_p, self._nrhs(R_pf), opts, u, self.n)
+
+    def global_update(self, x: torch.Tensor, Phi: torch.Tensor, kind: int, i: int, j: int = -1,
+                      u: float = 0.5, tol: float = 1e-10, prec: int = HOL_F64,
+                      S_cur: float | None = None, max_iter: int = 100000):
+        """Reflection (kind HOL_REFLECT, site i) or swap (HOL_SWAP, sites i, j)
+        Metropolis move at fixed Phi; x is updated in place. Returns
+        (accepted, dS, S of the kept field)."""
+        opts = hol_cg_opts(tol, max_iter, 0, prec, 50, 10)
+        return global_update(self._h, x, Phi, self._nrhs(Phi), kind, i, j, u, opts, S_cur,
+                             self.n)
 
     def stochastic_measure(self, xi: torch.Tensor, Gxi: torch.Tensor, G2: torch.Tensor,
                            G4: torch.Tensor | None = None, four_point: int = 0,

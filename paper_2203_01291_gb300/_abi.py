@@ -14,6 +14,8 @@ HOL_ETIMEOUT = -4
 HOL_ECUDA = -5
 HOL_ENOMEM = -6
 
+HOL_REFLECT = 0
+HOL_SWAP = 1
 HOL_OP_M = 0
 HOL_OP_MT = 1
 HOL_OP_MTM = 2
@@ -64,6 +66,9 @@ SIGNATURES = {
     "fourier_accel_leapfrog": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.POINTER(hol_md_opts), _D,
                                     ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D),
                                     _VP]),
+    "global_update": (_I, [_VP, _VP, _VP, _I, _I, _I, _I, ctypes.c_double,
+                           ctypes.POINTER(hol_cg_opts), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), _VP]),
     "stochastic_measure": (_I, [_VP, _VP, _I, ctypes.POINTER(hol_cg_opts), _VP, _VP, _VP, _I,
                                 ctypes.POINTER(_I), _VP]),
     "pseudofermion_phi": (_I, [_VP, _VP, _VP, _I, _VP]),

@@ -271,6 +271,9 @@ int launch_lambda(const hol_ctx* c, bool transpose_forward, const double* w, dou
                   int nv, cudaStream_t s);
 int launch_force(hol_ctx* c, const double* v, const double* b, int n_pf, double* F,
                  int with_bos, double* S_F, cudaStream_t s);
+// out2[0] = S_B(x), out2[1] = (1/2) sum b . v over n_pf vectors (leapfrog.cu).
+int launch_action_terms(const hol_ctx* c, const double* x, const double* b, const double* v,
+                        int n_pf, double* out2, cudaStream_t s);
 int elementwise_blocks(const hol_ctx* c);
 
 // preconditioner (precond.cu). mode bit 0: P^{-T} part, bit 1: P^{-1} part

@@ -254,6 +254,17 @@ int leapfrog_alloc(hol_ctx* c)
     return HOL_OK;
 }
 
+int launch_action_terms(const hol_ctx* c, const double* x, const double* b, const double* v,
+                        int n_pf, double* out2, cudaStream_t s)
+{
+    const double w02 = c->p.omega0 * c->p.omega0;
+    k_sb1<<<1, 1024, 0, s>>>(x, c->N, c->T, c->p.dtau, w02, out2);
+    HOL_CHECK_LAUNCH("k_sb1");
+    k_dot1<<<1, 1024, 0, s>>>(b, v, (long)n_pf * c->n, 0.5, out2 + 1);
+    HOL_CHECK_LAUNCH("k_dot1");
+    return HOL_OK;
+}
+
 }  // namespace hol
 
 using namespace hol;

@@ -11,6 +11,7 @@ import os
 import numpy as np
 import pytest
 
+import holstein_inputs as hi
 from oracle import dense as D
 from oracle import matfree as MF
 
@@ -454,3 +455,55 @@ def test_matfree_cg_and_force_equal_dense():
     F = MF.force_fermion(m, x, vd, b) + MF.force_boson(m, x)
     Fd = D.dSF_dx(m, x, Phi) + D.dSB_dx(m, x)
     assert np.abs(F - Fd).max() < 1e-11 * np.abs(Fd).max()
+
+
+# ----------------------------------------------------------------------------
+# Reflection and swap updates (Sec. IV)
+# ----------------------------------------------------------------------------
+def test_global_moves_leave_S_B_invariant():
+    """S_B is a sum of per-site terms, each even in x: reflecting one site's
+    line or exchanging two lines does not change it (any x)."""
+    w = hi.WORKLOADS["tiny"]
+    m = D.model_of(w)
+    x = hi.phonon_field(w, seed=41)
+    for kind, i, j in ((D.REFLECT, 3, -1), (D.SWAP, 3, 7), (D.SWAP, 0, 15)):
+        y = D.propose_global(x, kind, i, j)
+        assert abs(D.S_B(m, y) - D.S_B(m, x)) < 1e-12 * D.S_B(m, x)
+    # two swaps of the same pair restore x; a reflection twice too
+    y = D.propose_global(D.propose_global(x, D.SWAP, 2, 9), D.SWAP, 2, 9)
+    assert np.array_equal(y, x)
+    y = D.propose_global(D.propose_global(x, D.REFLECT, 5), D.REFLECT, 5)
+    assert np.array_equal(y, x)
+
+
+def test_global_moves_free_without_coupling():
+    """alpha = 0: M and Lambda do not depend on x, so every reflection and
+    swap has dS = 0 and is accepted for any u < 1."""
+    w = hi.Workload("a0", L=4, Ltau=20, alpha=0.0, mu=0.2, omega0=1.0, x_std=1.0, seed=43)
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    R = hi.gaussian_vectors(w, 2, seed=44)
+    Phi = D.phi_from_R(m, x, R)
+    for kind, i, j in ((D.REFLECT, 6, -1), (D.SWAP, 1, 2)):
+        acc, dS, y = D.global_update(m, x, Phi, kind, i, j, 0.999)
+        assert acc and abs(dS) < 1e-10
+        assert np.array_equal(y, D.propose_global(x, kind, i, j))
+
+
+def test_single_site_reflection_is_free_for_constant_lines():
+    """Single-site limit (t = 0) at half filling with tau-constant fields
+    (App. B; the symmetry behind Eq. (Delta_S_sym)): S_F(-x, Phi) = S_F(x, Phi)
+    for any Phi, so reflecting a site costs nothing. With tau fluctuations the
+    move is no longer free (the pin is not vacuous)."""
+    w = hi.Workload("ss", L=4, Ltau=20, t=0.0, alpha=2.0, mu=0.0, omega0=1.0, x_std=1.0, seed=45)
+    m = D.model_of(w)
+    rng = np.random.default_rng(46)
+    xbar = rng.normal(0.0, 1.0, size=w.N)
+    x = np.tile(xbar, (w.Ltau, 1))
+    Phi = rng.normal(size=(2, w.Ltau, w.N))
+    for i in (0, 5, 11):
+        y = D.propose_global(x, D.REFLECT, i)
+        assert abs(D.S_F(m, y, Phi) - D.S_F(m, x, Phi)) < 1e-9 * D.S_F(m, x, Phi)
+    xf = x + 0.3 * rng.normal(size=x.shape)
+    y = D.propose_global(xf, D.REFLECT, 5)
+    assert abs(D.S_F(m, y, Phi) - D.S_F(m, xf, Phi)) > 1e-3
