@@ -83,7 +83,7 @@ __device__ __forceinline__ double block_sum(double v)
 // alpha p), so x is read and written every other iteration; FOLD 1 is the
 // plain x += alpha p.
 template <typename R, int FOLD>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 4) k_cg_update(R* __restrict__ x, R* __restrict__ r,
+__global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restrict__ r,
                                                    const R* __restrict__ p,
                                                    const R* __restrict__ pprev,
                                                    const R* __restrict__ q, long n,
@@ -97,23 +97,6 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 4) k_cg_update(R* __
     const PdlTriggerAtExit pdl_at_exit;
     const int rhs = blockIdx.y;
     if (mask != nullptr && mask[rhs] == 0) return;
-    const long base = (long)rhs * n;
-    const long stride = (long)gridDim.x * blockDim.x;
-    const long k0 = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    // FOLD 0 streams only r and q: the first U groups of four of this thread
-    // are loaded before alpha is known, so their latency overlaps its sums
-    constexpr int U = sizeof(R) == 4 ? 2 : 1;
-    V4<R> r0[U], q0[U];
-    if constexpr (FOLD == 0) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const long k = k0 + u * stride;
-            if (4 * k < n) {
-                r0[u].ld(r + base + 4 * k);
-                q0[u].ld(q + base + 4 * k);
-            }
-        }
-    }
     // one warp forms alpha (FP64 sums are slow on this part: doing it in
     // every warp measured slower than the barrier)
     __shared__ double s_alpha, s_alpha_prev;
@@ -130,26 +113,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 4) k_cg_update(R* __
     R ap = R(0);
     if (FOLD == 2) ap = (R)s_alpha_prev;
     if (FOLD == 0 && blockIdx.x == 0 && threadIdx.x == 0) alpha_buf[rhs] = s_alpha;
+    const long base = (long)rhs * n;
+    const long stride = (long)gridDim.x * blockDim.x;
     double acc = 0.0;
-    long kstart = k0;
-    if constexpr (FOLD == 0) {
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const long k = k0 + u * stride;
-            if (4 * k < n) {
-                R part = R(0);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    r0[u].v[j] = fma(-a, q0[u].v[j], r0[u].v[j]);
-                    part = fma(r0[u].v[j], r0[u].v[j], part);
-                }
-                r0[u].st(r + base + 4 * k);
-                acc += (double)part;
-            }
-        }
-        kstart = k0 + U * stride;
-    }
-    for (long k = kstart; 4 * k < n; k += stride) {
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n; k += stride) {
         const long o = base + 4 * k;
         V4<R> rv, qv;
         rv.ld(r + o);
