@@ -410,7 +410,7 @@ def run_ours(a):
     extra = None
     if not a.no_extra:
         extra = {"trajectory": trajectory_leg(dev), "measurement": measurement_leg(dev),
-                 "global_updates": global_update_leg(dev)}
+                 "global_updates": global_update_leg(dev), "chains": chains_leg(dev)}
 
     alu = {"fp64_fma_gflops": hg.hol_fma_peak(hg.HOL_F64),
            "fp32_fma_gflops": hg.hol_fma_peak(hg.HOL_F32),
@@ -528,6 +528,52 @@ def measurement_leg(dev, n_rv=128):
     return {"workload": "L=28 Ltau=120 chain, 128 Z2 probes, 2-point + type-2 Wick",
             "measurements_per_s": 1e3 / ms, "ms_per_measurement": ms,
             "mean_cg_iters": float(np.mean(its))}
+
+
+def chains_leg(dev, n_rv=128):
+    """The batching configuration: 48 independent chains of uneven size
+    (L in {8, 12, 16, 20, 24, 28}, 8 each, Ltau=120, beta=12, omega0=1,
+    alpha=1, x ~ N(0, 1) per chain seed). One HMC trajectory per chain
+    (Algorithm 1: N_t=20, n_t=4, dt=0.01, adiabatic PCG, mixed, forces to
+    1e-5, action to 1e-10) and one stochastic measurement per chain (128 Z2
+    probes, 2-point function, mixed CG to 1e-8), each chain on its own
+    stream, all chains concurrent (hmc_batch / measure_batch)."""
+    import torch
+    import paper_2203_01291_gb300 as hg
+    ws = hi.chain_workloads(8, 120)
+    ctxs = [hg.Context.from_workload(w, max_rhs=16) for w in ws]
+    try:
+        xs = [torch.tensor(hi.phonon_field(w), device=dev) for w in ws]
+        Rs = [torch.tensor(hi.gaussian_vectors(w, 2, seed=w.seed + 1), device=dev) for w in ws]
+        Rps = [torch.tensor(hi.gaussian_vectors(w, 1, seed=w.seed + 2)[0], device=dev)
+               for w in ws]
+        u = hi.uniforms(len(ws), seed=903)
+        o = hg.md_opts(0.01, 20, 4, 1.0, force_tol=1e-5, action_tol=1e-10, prec=hg.HOL_F32,
+                       precond=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        acc, dh = hg.hmc_batch(ctxs, xs, Rs, Rps, o, u, n_threads=8)
+        torch.cuda.synchronize()
+        t_traj = time.perf_counter() - t0
+        for c, x in zip(ctxs, xs):
+            c.set_field(x)
+        xis = [torch.tensor(hi.z2_vectors(w, n_rv, seed=w.seed + 3), device=dev) for w in ws]
+        Gxis = [torch.empty_like(xi) for xi in xis]
+        G2s = [torch.empty(2 * w.Ltau, w.L, w.L, dtype=torch.float64, device=dev) for w in ws]
+        mo = hg.hol_cg_opts(1e-8, 100000, 0, hg.HOL_F32, 50, 10)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hg.measure_batch(ctxs, xis, Gxis, G2s, mo, n_threads=8)
+        torch.cuda.synchronize()
+        t_meas = time.perf_counter() - t0
+    finally:
+        for c in ctxs:
+            c.close()
+    return {"workload": "48 chains, L in {8..28} x 8, Ltau=120; one trajectory (N_t=20, n_t=4, "
+                        "PCG mixed) and one 128-probe measurement per chain, chains concurrent",
+            "trajectories_per_s": len(ws) / t_traj, "ms_all_trajectories": t_traj * 1e3,
+            "accepted": int(np.sum(acc)), "of": len(ws),
+            "measurements_per_s": len(ws) / t_meas, "ms_all_measurements": t_meas * 1e3}
 
 
 def global_update_leg(dev, n_moves=16):

@@ -233,6 +233,24 @@ int fourier_accel_leapfrog(hol_ctx* ctx, double* x, const double* R_pf, const do
                            double* dH, double* terms, void* stream);
 
 /*
+ * Observables of one measurement (Eq. (Scdw) and the pair susceptibility P_s
+ * of Sec. II), contracted from the outputs of stochastic_measure run with
+ * four_point = 7: G2 (device, [2T][L][L]) and G4 (device, [3][2T][L][L]).
+ * Spins are independent and see the same field, so by Wick's theorem per
+ * spin, with g0 = G2[0][0][0] the averaged G_aa:
+ *   density <n> = 2 (1 - g0);
+ *   C(r) = (1/(N T)) sum <n_{i+r} n_i> (equal time) = 4 (1 - 2 g0 + G4[1][0][r])
+ *          + 2 (delta_{r,0} g0 - G4[2][0][r]), written to C (device, [L][L],
+ *          indexed [dy][dx]);
+ *   S_cdw = sum_r (-1)^(rx+ry) C(r);
+ *   P_s = dtau sum_{l < T} sum_r G4[0][l][r] (the tau integral as a sum over
+ *         slices of the averaged G^2).
+ * out3 (host, 3 doubles): density, S_cdw, P_s. Synchronises `stream`.
+ */
+int measure_observables(hol_ctx* ctx, const double* G2, const double* G4, double* C,
+                        double* out3, void* stream);
+
+/*
  * Reflection and swap updates (Sec. IV): one Metropolis move of the phonon
  * field at fixed pseudofermion fields. kind HOL_REFLECT proposes
  * x_{i,tau} -> -x_{i,tau} at every tau of site i; HOL_SWAP exchanges the

@@ -718,3 +718,85 @@ def four_point_pairs(m: Model, x, xi, Gxi=None) -> np.ndarray:
             out[2] += cross_corr_direct(a[n] * b[k], a[k] * b[n], m.L)
             npairs += 1
     return out / (2.0 * m.n * npairs)
+
+
+# ----------------------------------------------------------------------------
+# Observables from the Green function (Sec. II, Eq. (Scdw) and P_s)
+# ----------------------------------------------------------------------------
+def observables_exact(m: Model, x) -> dict:
+    """Per-configuration observables of the spin-degenerate model from the
+    dense equal- and unequal-time G = M^{-1} (G_{ab} = <c_a c_b^dag>), by Wick's
+    theorem for each spin (the two spins see the same x and are independent):
+      <n> = 2 (1 - mean_a G_aa);
+      C(r) = (1/(N T)) sum_{i, tau} <n_{i+r,tau} n_{i,tau}>, with
+      <n_a n_b> = 4 (1 - G_aa)(1 - G_bb) + 2 (delta_ab - G_ba) G_ab;
+      S_cdw = sum_r (-1)^(rx + ry) C(r)  (Eq. (Scdw));
+      P_s = (dtau / (N T)) sum_{tau'} sum_l sum_{r, r'} G_{(r, tau'+l), (r', tau')}^2,
+    the pair susceptibility with the imaginary-time integral as a sum over
+    the T slices (G squared removes the antiperiodic sign)."""
+    N, T, L = m.N, m.Ltau, m.L
+    G = green_matrix(m, x)
+    dG = np.diag(G).reshape(T, N)
+    out_C = np.zeros((L, L))
+    for tau in range(T):
+        for iy in range(L):
+            for ix in range(L):
+                a = tau * N + site(ix, iy, L)
+                for dy in range(L):
+                    for dx in range(L):
+                        b = tau * N + site(ix + dx, iy + dy, L)
+                        nn = 4.0 * (1.0 - G[a, a]) * (1.0 - G[b, b]) + \
+                            2.0 * ((1.0 if a == b else 0.0) - G[b, a]) * G[a, b]
+                        out_C[dy, dx] += nn
+    out_C /= N * T
+    sign = np.array([[(-1.0) ** (dx + dy) for dx in range(L)] for dy in range(L)])
+    ps = 0.0
+    for t1 in range(T):
+        for t0 in range(T):
+            blk = G[t1 * N:(t1 + 1) * N, t0 * N:(t0 + 1) * N]
+            ps += float(np.sum(blk * blk))
+    ps *= m.dtau / (N * T)
+    return {"density": 2.0 * (1.0 - float(np.mean(dG))), "C": out_C,
+            "S_cdw": float(np.sum(sign * out_C)), "P_s": ps}
+
+
+def observables_from_estimates(m: Model, G2, G4) -> dict:
+    """The same observables from the space-time averaged 2-point function
+    G2 [2T][L][L] and the pair-averaged Wick products G4 [3][2T][L][L]
+    (Sec. V; index [dl][dy][dx]): g0 = G2[0, 0, 0] estimates mean G_aa;
+    G4[1][0] (xi.Gxi star xi'.Gxi') estimates mean G_aa G_bb, G4[2][0]
+    (xi.Gxi' star xi'.Gxi) mean G_ab G_ba, G4[0][l] (xi.xi' star Gxi.Gxi')
+    mean G_{b,a}^2 at slice difference l."""
+    G2 = np.asarray(G2)
+    G4 = np.asarray(G4)
+    L, T = m.L, m.Ltau
+    g0 = float(G2[0, 0, 0])
+    delta = np.zeros((L, L))
+    delta[0, 0] = 1.0
+    C = 4.0 * (1.0 - 2.0 * g0 + G4[1, 0]) + 2.0 * (delta * g0 - G4[2, 0])
+    sign = np.array([[(-1.0) ** (dx + dy) for dx in range(L)] for dy in range(L)])
+    ps = m.dtau * float(np.sum(G4[0, :T]))
+    return {"density": 2.0 * (1.0 - g0), "C": C, "S_cdw": float(np.sum(sign * C)), "P_s": ps}
+
+
+def wick_products_exact(m: Model, x) -> np.ndarray:
+    """The expectations of the three pair estimators of four_point_pairs
+    from the dense G^ext (no probes): [0] mean G_{i+D,i}^2, [1] mean
+    G_{i,i} G_{i+D,i+D}, [2] mean G_{i,i+D} G_{i+D,i}, over the doubled
+    domain (the extension's signs cancel in each product). [3][2T][L][L]."""
+    N, T, L = m.N, m.Ltau, m.L
+    G = green_matrix(m, x)
+    Q = np.vstack([np.eye(N * T), -np.eye(N * T)])
+    Gx = Q @ G @ Q.T
+    out = np.zeros((3, 2 * T, L, L))
+    idx = np.arange(2 * T * N)
+    for dl in range(2 * T):
+        for dy in range(L):
+            for dx in range(L):
+                l, r = idx // N, idx % N
+                iy, ix = r // L, r % L
+                j = ((l + dl) % (2 * T)) * N + ((iy + dy) % L) * L + (ix + dx) % L
+                out[0, dl, dy, dx] = np.mean(Gx[j, idx] ** 2)
+                out[1, dl, dy, dx] = np.mean(Gx[idx, idx] * Gx[j, j])
+                out[2, dl, dy, dx] = np.mean(Gx[idx, j] * Gx[j, idx])
+    return out

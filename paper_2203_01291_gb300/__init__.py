@@ -33,7 +33,7 @@ __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F6
            "hol_timer_read", "fermion_matvec_static", "mass_apply", "md_integrate",
            "fourier_accel_leapfrog", "hol_md_opts", "stochastic_measure", "hol_tune",
            "hmc_batch", "measure_batch", "hol_set_option", "hol_get_option", "hol_fma_peak",
-           "global_update", "HOL_REFLECT", "HOL_SWAP",
+           "global_update", "HOL_REFLECT", "HOL_SWAP", "measure_observables",
            "library_path", "load"]
 
 
@@ -193,6 +193,16 @@ def global_update(handle, x: torch.Tensor, Phi: torch.Tensor, n_pf: int, kind: i
                                 int(i), int(j), float(u), ctypes.byref(opts), ctypes.byref(S),
                                 ctypes.byref(acc), ctypes.byref(d), _stream()))
     return bool(acc.value), d.value, S.value
+
+
+def measure_observables(handle, G2: torch.Tensor, G4: torch.Tensor, C: torch.Tensor, L: int,
+                        T: int) -> dict:
+    """density, S_cdw, P_s (host) and C(r) (device) from a measurement."""
+    out = (ctypes.c_double * 3)()
+    _check(load().measure_observables(handle, _ptr(G2, torch.float64, 2 * T * L * L, "G2"),
+                                      _ptr(G4, torch.float64, 6 * T * L * L, "G4"),
+                                      _ptr(C, torch.float64, L * L, "C"), out, _stream()))
+    return {"density": out[0], "S_cdw": out[1], "P_s": out[2]}
 
 
 def hol_tune(handle, n_rhs: int) -> dict:
@@ -360,6 +370,11 @@ class Context:
                                opts: hol_md_opts, u: float):
         """Algorithm 1; returns (accepted, dH, [S_B, S_F, K] at start and end)."""
         return fourier_accel_leapfrog(self._h, x, R_pf, R_p, self._nrhs(R_pf), opts, u, self.n)
+
+    def measure_observables(self, G2: torch.Tensor, G4: torch.Tensor, C: torch.Tensor) -> dict:
+        """<n>, S_cdw, P_s of one measurement (stochastic_measure with
+        four_point = 7); C(r) is written to C ([L][L], device)."""
+        return measure_observables(self._h, G2, G4, C, self.L, self.Ltau)
 
     def global_update(self, x: torch.Tensor, Phi: torch.Tensor, kind: int, i: int, j: int = -1,
                       u: float = 0.5, tol: float = 1e-10, prec: int = HOL_F64,

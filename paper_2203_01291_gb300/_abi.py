@@ -66,6 +66,7 @@ SIGNATURES = {
     "fourier_accel_leapfrog": (_I, [_VP, _VP, _VP, _VP, _I, ctypes.POINTER(hol_md_opts), _D,
                                     ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D),
                                     _VP]),
+    "measure_observables": (_I, [_VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double), _VP]),
     "global_update": (_I, [_VP, _VP, _VP, _I, _I, _I, _I, ctypes.c_double,
                            ctypes.POINTER(hol_cg_opts), ctypes.POINTER(ctypes.c_double),
                            ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double), _VP]),

@@ -403,3 +403,57 @@ extern "C" int stochastic_measure(hol_ctx* c, const double* xi, int n_rv, const 
     }
     return HOL_OK;
 }
+
+
+// ---------------------------------------------------------------------------
+// Observables from the averaged 2-point function and the Wick products
+// (Eq. (Scdw) and the pair susceptibility P_s), one block:
+//   g0 = G2[0][0][0] (mean G_aa), <n> = 2 (1 - g0),
+//   C(r) = 4 (1 - 2 g0 + G4[1][0][r]) + 2 (delta_{r,0} g0 - G4[2][0][r]),
+//   S_cdw = sum_r (-1)^(rx+ry) C(r),  P_s = dtau sum_{l < T} sum_r G4[0][l][r].
+// Every sum is taken in a fixed order by thread 0 of one warp (the arrays
+// hold a few thousand numbers).
+// ---------------------------------------------------------------------------
+namespace hol {
+namespace {
+__global__ void k_observables(const double* __restrict__ G2, const double* __restrict__ G4,
+                              int L, int T, double dtau, double* __restrict__ C,
+                              double* __restrict__ scal)
+{
+    const int LL = L * L;
+    const double g0 = G2[0];
+    const double* w0 = G4;                       // type 1 [2T][L][L]
+    const double* w1 = G4 + (long)2 * T * LL;    // type 2
+    const double* w2 = G4 + (long)4 * T * LL;    // type 3
+    for (int r = threadIdx.x; r < LL; r += blockDim.x)
+        C[r] = 4.0 * (1.0 - 2.0 * g0 + w1[r]) + 2.0 * ((r == 0 ? g0 : 0.0) - w2[r]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double scdw = 0.0;
+        for (int r = 0; r < LL; ++r) {
+            const int dx = r % L, dy = r / L;
+            scdw += ((dx + dy) & 1) ? -C[r] : C[r];
+        }
+        double ps = 0.0;
+        for (long k = 0; k < (long)T * LL; ++k) ps += w0[k];
+        scal[0] = 2.0 * (1.0 - g0);
+        scal[1] = scdw;
+        scal[2] = dtau * ps;
+    }
+}
+}  // namespace
+}  // namespace hol
+
+extern "C" int measure_observables(hol_ctx* c, const double* G2, const double* G4, double* C,
+                                   double* out3, void* stream)
+{
+    if (!c || !G2 || !G4 || !C || !out3)
+        return set_error(HOL_EINVAL, "measure_observables: null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    double* scal = c->md_s + 12;
+    k_observables<<<1, 256, 0, s>>>(G2, G4, c->L, c->T, c->p.dtau, C, scal);
+    HOL_CHECK_LAUNCH("k_observables");
+    HOL_CUDA(cudaMemcpyAsync(out3, scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HOL_CUDA(cudaStreamSynchronize(s));
+    return HOL_OK;
+}

@@ -88,3 +88,33 @@ def test_chain_size_two_point_and_type2():
     assert _rel(G2, D.green_average(m, x, xi, Gref)) < 1e-10
     assert _rel(G4[1], D.four_point_pairs(m, x, xi, Gref)[1]) < 1e-10
     assert float(np.abs(G4[0]).max()) == 0.0 and float(np.abs(G4[2]).max()) == 0.0
+
+
+@pytest.mark.parametrize("L,T,nrv", [(4, 10, 6), (6, 12, 4)])
+def test_observables_vs_oracle(L, T, nrv):
+    """<n>, C(r), S_cdw and P_s contracted on the GPU from its own 2-point
+    function and Wick products equal the oracle's contraction of the same
+    arrays, and of the oracle's direct-sum estimates with the same probes."""
+    w = hi.Workload("o", L=L, Ltau=T, alpha=1.1, mu=0.05)
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    xi = hi.z2_vectors(w, nrv, seed=5)
+    with hg.Context.from_workload(w, max_rhs=4) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        xt = torch.tensor(xi, device=DEV)
+        Gxi = torch.empty_like(xt)
+        G2 = torch.empty(2 * T, L, L, dtype=torch.float64, device=DEV)
+        G4 = torch.empty(3, 2 * T, L, L, dtype=torch.float64, device=DEV)
+        ctx.stochastic_measure(xt, Gxi, G2, G4, 7, tol=1e-13)
+        C = torch.empty(L, L, dtype=torch.float64, device=DEV)
+        obs = ctx.measure_observables(G2, G4, C)
+        Cg = C.cpu().numpy()
+        g2, g4 = G2.cpu().numpy(), G4.cpu().numpy()
+    same = D.observables_from_estimates(m, g2, g4)
+    for k in ("density", "S_cdw", "P_s"):
+        assert abs(obs[k] - same[k]) < 1e-12 * max(1.0, abs(same[k]))
+    assert np.abs(Cg - same["C"]).max() < 1e-12 * np.abs(same["C"]).max()
+    ref = D.observables_from_estimates(m, D.green_average(m, x, xi), D.four_point_pairs(m, x, xi))
+    for k in ("density", "S_cdw", "P_s"):
+        assert abs(obs[k] - ref[k]) < 1e-9 * max(1.0, abs(ref[k]))
+    assert np.abs(Cg - ref["C"]).max() < 1e-9 * np.abs(ref["C"]).max()

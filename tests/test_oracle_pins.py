@@ -507,3 +507,36 @@ def test_single_site_reflection_is_free_for_constant_lines():
     xf = x + 0.3 * rng.normal(size=x.shape)
     y = D.propose_global(xf, D.REFLECT, 5)
     assert abs(D.S_F(m, y, Phi) - D.S_F(m, xf, Phi)) > 1e-3
+
+
+# ----------------------------------------------------------------------------
+# Observables (Eq. (Scdw), P_s)
+# ----------------------------------------------------------------------------
+def test_observables_from_products_match_wick_definitions():
+    """The contraction of the space-time averaged G and the three Wick
+    products (what the stochastic measurement estimates) reproduces the
+    observables formed from the dense G by Wick's theorem for every pair of
+    sites (independent index sums)."""
+    w = hi.Workload("ob", L=4, Ltau=10, alpha=1.0, mu=0.1, omega0=1.0, x_std=0.7, seed=91)
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    ex = D.observables_exact(m, x)
+    es = D.observables_from_estimates(m, D.green_average_exact(m, x), D.wick_products_exact(m, x))
+    for k in ("density", "S_cdw", "P_s"):
+        assert abs(ex[k] - es[k]) < 1e-12 * max(1.0, abs(ex[k]))
+    assert np.abs(ex["C"] - es["C"]).max() < 1e-12
+
+
+def test_observables_particle_hole_at_half_filling():
+    """mu = 0 on the bipartite lattice: x -> -x maps n -> 2 - n, so
+    <n>(x) + <n>(-x) = 2 and C_{-x}(r) = C_x(r) + 4 - 4 <n>(x), for every
+    configuration (the same symmetry as the log det pin); free fermions are
+    exactly half filled."""
+    w = hi.Workload("ph", L=4, Ltau=10, alpha=1.3, mu=0.0, omega0=1.0, x_std=0.7, seed=92)
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    a = D.observables_exact(m, x)
+    b = D.observables_exact(m, -x)
+    assert abs(a["density"] + b["density"] - 2.0) < 1e-12
+    assert np.abs(b["C"] - (a["C"] + 4.0 - 4.0 * a["density"])).max() < 1e-12
+    assert abs(D.observables_exact(m, np.zeros_like(x))["density"] - 1.0) < 1e-12
