@@ -59,7 +59,9 @@ def args_parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["step", "matvec", "precond"], default="step")
+    ap.add_argument("--mode", choices=["step", "matvec", "precond", "leg"], default="step")
+    ap.add_argument("--leg", choices=["trajectory", "measurement", "global", "chains"],
+                    default="trajectory", help="with --mode leg: run one of the other rows alone")
     ap.add_argument("--rhs", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
@@ -795,6 +797,19 @@ def run_reference(a):
     print(json.dumps(out))
 
 
+def run_leg(a):
+    """One of the other rows of the JSON line alone (for profiling)."""
+    import torch
+    from paper_2203_01291_gb300 import build as hb
+    hb.build()
+    torch.cuda.set_device(0)
+    legs = {"trajectory": lambda: trajectory_leg("cuda", n_traj=1),
+            "measurement": lambda: measurement_leg("cuda", n_rv=32),
+            "global": lambda: global_update_leg("cuda"),
+            "chains": lambda: chains_leg("cuda")}
+    print(json.dumps({"mode": "leg", "leg": a.leg, **legs[a.leg]()}))
+
+
 def main():
     a = args_parse()
     if a.impl == "reference":
@@ -803,6 +818,8 @@ def main():
         run_matvec(a)
     elif a.mode == "precond":
         run_precond(a)
+    elif a.mode == "leg":
+        run_leg(a)
     else:
         run_ours(a)
 
