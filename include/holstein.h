@@ -119,7 +119,15 @@ typedef struct hol_cg_opts {
  * gradients from v = 0 (so v is a deterministic function of x and b), with
  * the preconditioner z = P^{-1} P^{-T} r when opts->precond (Eq. (CG_precon)).
  * b, v: FP64 [n_rhs][T][N] (device). Convergence of every right-hand side is
- * certified with an FP64 true residual |b - M^T M v| / |b| < tol.
+ * certified with an FP64 true residual |b - M^T M v| / |b| < tol. With
+ * opts->prec HOL_F32 the iterations run in FP32 (FP64 dot products) and
+ * every reliable_every iterations, and whenever the recursive residual
+ * estimate falls below tol, the FP32 increment is folded into the FP64 v and
+ * the residual is replaced by the FP64 true residual; the search direction
+ * is then re-conjugated against it, beta = -(z, A p) / (p, A p). The
+ * iteration kernels are chosen by the context's launch options (see
+ * hol_set_option: two kernels per iteration by default, fused_cg /
+ * merged_cg for one).
  * iters, resid: HOST arrays of n_rhs entries (nullable) receiving the
  * iterations and the final true relative residual of each right-hand side.
  * Returns HOL_ENOTCONV if some right-hand side did not converge (v then holds
