@@ -15,6 +15,8 @@ namespace {
 
 struct ForceArgs {
     int T, K, nrun, n_pf;
+    int pg;          // pseudofermions per group (blockIdx.y selects the group)
+    int groups;      // > 1: each group writes its partial force to Fp[group]
     long n;
     int with_bos;
     double th, da, dtau, w02;
@@ -35,6 +37,11 @@ __global__ void __launch_bounds__(128) k_force(const double* __restrict__ v,
     const int run = warp * LaneGeom<L>::G + geo.g;
     const bool valid = geo.ok && run < a.nrun;
     const int t0 = (run < a.nrun ? run : a.nrun - 1) * a.K;
+    const int grp = blockIdx.y;
+    const int sp0 = grp * a.pg;
+    const int sp1 = (sp0 + a.pg < a.n_pf) ? sp0 + a.pg : a.n_pf;
+    const bool bos = a.with_bos && a.groups == 1;   // else added by k_force_sum
+    double* Fout = F + (a.groups > 1 ? (long)grp * a.n : 0L);
     double acc = 0.0;
     for (int s = 0; s < a.K; ++s) {
         const int tau = t0 + s;
@@ -45,14 +52,14 @@ __global__ void __launch_bounds__(128) k_force(const double* __restrict__ v,
 #pragma unroll
         for (int iy = 0; iy < L; ++iy) {
             f[iy] = 0.0;
-            if (a.with_bos) {
+            if (bos) {
                 const long o = iy * L + geo.ix;
                 const double xc = x[(long)tau * N + o];
                 const double lap = x[(long)tp * N + o] - 2.0 * xc + x[(long)tm * N + o];
                 f[iy] = a.dtau * (a.w02 * xc - lap / (a.dtau * a.dtau));
             }
         }
-        for (int sp = 0; sp < a.n_pf; ++sp) {
+        for (int sp = sp0; sp < sp1; ++sp) {
             const long base = (long)sp * a.n + geo.ix;
             double c[L];
 #pragma unroll
@@ -74,7 +81,7 @@ __global__ void __launch_bounds__(128) k_force(const double* __restrict__ v,
         }
         if (valid) {
 #pragma unroll
-            for (int iy = 0; iy < L; ++iy) F[(long)tau * N + iy * L + geo.ix] = f[iy];
+            for (int iy = 0; iy < L; ++iy) Fout[(long)tau * N + iy * L + geo.ix] = f[iy];
         }
     }
     // per-unit sum of b.v over the slices tau-1 of the run
@@ -85,7 +92,29 @@ __global__ void __launch_bounds__(128) k_force(const double* __restrict__ v,
     if (valid && geo.ix == 0) {
         double ssum = 0.0;
         for (int k = 0; k < L; ++k) ssum += red[w * 32 + geo.g * L + k];
-        sf_part[run] = ssum;
+        sf_part[grp * a.nrun + run] = ssum;
+    }
+}
+
+// F = sum over pseudofermion groups of the partial forces (fixed order)
+// plus the bosonic force of Eq. (dSB_dx).
+__global__ void k_force_sum(const double* __restrict__ Fp, int groups, const double* __restrict__ x,
+                            int N, int T, int with_bos, double dtau, double w02,
+                            double* __restrict__ F)
+{
+    const long n = (long)N * T;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+         k += (long)gridDim.x * blockDim.x) {
+        double f = 0.0;
+        for (int g = 0; g < groups; ++g) f += Fp[(long)g * n + k];
+        if (with_bos) {
+            const int tau = (int)(k / N), i = (int)(k - (long)tau * N);
+            const int tp = tau + 1 == T ? 0 : tau + 1, tm = tau == 0 ? T - 1 : tau - 1;
+            const double xc = x[k];
+            const double lap = x[(long)tp * N + i] - 2.0 * xc + x[(long)tm * N + i];
+            f += dtau * (w02 * xc - lap / (dtau * dtau));
+        }
+        F[k] = f;
     }
 }
 
@@ -94,6 +123,22 @@ __global__ void k_sf_finish(const double* __restrict__ part, int cnt, double* __
 {
     const double s = warp_sum_array(part, cnt);
     if (threadIdx.x == 0) *out = 0.5 * s;
+}
+
+// Pseudofermion groups of the force kernel: up to 7 in one group, else
+// groups of about four (each group's blocks run independently).
+void force_groups(int n_pf, int* groups, int* pg)
+{
+    if (n_pf < 8) {
+        *groups = 1;
+        *pg = n_pf;
+        return;
+    }
+    int g = (n_pf + 3) / 4;
+    const int p = (n_pf + g - 1) / g;
+    g = (n_pf + p - 1) / p;
+    *groups = g;
+    *pg = p;
 }
 
 template <int L>
@@ -111,9 +156,19 @@ int run_force(hol_ctx* c, const double* v, const double* b, int n_pf, double* F,
     a.da = c->p.dtau * c->p.alpha;
     a.dtau = c->p.dtau;
     a.w02 = c->p.omega0 * c->p.omega0;
+    // many pseudofermions: split them into groups processed by separate
+    // blocks (partial forces in the solver scratch, summed afterwards)
+    force_groups(n_pf, &a.groups, &a.pg);
     const int warps = ceil_div(a.nrun, LaneGeom<L>::G);
-    k_force<L><<<ceil_div(warps, 4), 128, 0, s>>>(v, b, c->x, c->ev64, F, sf_part, a);
+    double* Fp = a.groups > 1 ? c->v64a : F;
+    k_force<L><<<dim3(ceil_div(warps, 4), a.groups), 128, 0, s>>>(v, b, c->x, c->ev64, Fp,
+                                                                 sf_part, a);
     HOL_CHECK_LAUNCH("k_force");
+    if (a.groups > 1) {
+        const int nb = ceil_div(c->n, 256) < 4096 ? ceil_div(c->n, 256) : 4096;
+        k_force_sum<<<nb, 256, 0, s>>>(Fp, a.groups, c->x, c->N, c->T, with_bos, a.dtau, a.w02, F);
+        HOL_CHECK_LAUNCH("k_force_sum");
+    }
     return HOL_OK;
 }
 
@@ -133,7 +188,9 @@ int launch_force(hol_ctx* c, const double* v, const double* b, int n_pf, double*
     }
     if (rc) return rc;
     if (S_F != nullptr) {
-        k_sf_finish<<<1, 32, 0, s>>>(sf_part, c->T / c->mv_k, S_F);
+        int groups, pg;
+        force_groups(n_pf, &groups, &pg);
+        k_sf_finish<<<1, 32, 0, s>>>(sf_part, groups * (c->T / c->mv_k), S_F);
         HOL_CHECK_LAUNCH("k_sf_finish");
     }
     return HOL_OK;

@@ -415,6 +415,32 @@ def test_force_vs_dense_definition(L, T):
         assert _rel(Fb.cpu().numpy(), D.dSF_dx(m, x, Phi)) < 1e-12
 
 
+@pytest.mark.parametrize("n_pf", [0, 7, 9, 16])
+def test_force_many_pseudofermions(n_pf):
+    """Many pseudofermions are split into groups of blocks whose partial
+    forces are summed in a fixed order: same force and S_F as the dense
+    definition (n_pf = 0 leaves the bosonic force alone)."""
+    w, x = _field(8, 12, seed=15)
+    m = D.model_of(w)
+    Phi = hi.gaussian_vectors(w, max(n_pf, 1), seed=16)[:n_pf]
+    with _ctx(w, 16) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        F = torch.empty(w.Ltau, w.N, device=DEV, dtype=torch.float64)
+        SF = torch.empty(1, device=DEV, dtype=torch.float64)
+        if n_pf == 0:
+            z = torch.zeros(1, w.Ltau, w.N, device=DEV, dtype=torch.float64)
+            from paper_2203_01291_gb300 import force as _force
+            _force(ctx._h, z, z, 0, F, True, SF, ctx.n)
+            assert _rel(F.cpu().numpy(), D.dSB_dx(m, x)) < 1e-13
+            assert float(SF) == 0.0
+            return
+        b = D.b_from_phi(m, x, Phi)
+        v = np.stack([D.solve_MTM(m, x, bb) for bb in b])
+        ctx.force(torch.tensor(v, device=DEV), torch.tensor(b, device=DEV), F, True, SF)
+        assert _rel(F.cpu().numpy(), D.dS_dx(m, x, Phi)) < 1e-12
+        assert abs(float(SF) - D.S_F(m, x, Phi)) < 1e-11 * abs(D.S_F(m, x, Phi))
+
+
 def test_force_full_size_grad24_vs_matrix_free():
     w = hi.WORKLOADS["grad24"]
     x = hi.phonon_field(w)
