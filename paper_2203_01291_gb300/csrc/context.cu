@@ -195,6 +195,12 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
         free_ctx(c);
         return set_error(HOL_ECUDA, "hol_create: no CUDA device");
     }
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) !=
+            cudaSuccess ||
+        c->sms < 1) {
+        free_ctx(c);
+        return set_error(HOL_ECUDA, "hol_create: multiprocessor count query failed");
+    }
 
     const long n = c->n, R = p->max_rhs;
     const long pstride = matvec_pstride(c);

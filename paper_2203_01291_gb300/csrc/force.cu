@@ -20,10 +20,11 @@ struct ForceArgs {
     long n;
     int with_bos;
     double th, da, dtau, w02;
+    double inv_dtau;   // 1 / dtau, so the stencil needs no division
 };
 
 template <int L>
-__global__ void __launch_bounds__(128) k_force(const double* __restrict__ v,
+__global__ void __launch_bounds__(32) k_force(const double* __restrict__ v,
                                                const double* __restrict__ b,
                                                const double* __restrict__ x,
                                                const double* __restrict__ ev,
@@ -48,17 +49,11 @@ __global__ void __launch_bounds__(128) k_force(const double* __restrict__ v,
         const int tm = (tau == 0) ? a.T - 1 : tau - 1;
         const int tp = (tau + 1 == a.T) ? 0 : tau + 1;
         const double sg = (tau == 0) ? 1.0 : -1.0;
+        // f accumulates the fermion force over the group divided by dtau alpha:
+        // sum_sigma y (y + s_tau v_tau) - b_{tau-1} v_{tau-1} / 2
         double f[L];
 #pragma unroll
-        for (int iy = 0; iy < L; ++iy) {
-            f[iy] = 0.0;
-            if (bos) {
-                const long o = iy * L + geo.ix;
-                const double xc = x[(long)tau * N + o];
-                const double lap = x[(long)tp * N + o] - 2.0 * xc + x[(long)tm * N + o];
-                f[iy] = a.dtau * (a.w02 * xc - lap / (a.dtau * a.dtau));
-            }
-        }
+        for (int iy = 0; iy < L; ++iy) f[iy] = 0.0;
         for (int sp = sp0; sp < sp1; ++sp) {
             const long base = (long)sp * a.n + geo.ix;
             double c[L];
@@ -68,7 +63,7 @@ __global__ void __launch_bounds__(128) k_force(const double* __restrict__ v,
                 const double vv = v[o];
                 const double bv = b[o] * vv;
                 acc += bv;
-                f[iy] -= 0.5 * a.da * bv;
+                f[iy] = fma(-0.5, bv, f[iy]);
                 c[iy] = vv;
             }
             cb_apply<double, L>(c, geo, a.th);
@@ -76,22 +71,31 @@ __global__ void __launch_bounds__(128) k_force(const double* __restrict__ v,
             for (int iy = 0; iy < L; ++iy) {
                 const double y = ev[(long)tau * N + iy * L + geo.ix] * c[iy];
                 const double vt = v[base + (long)tau * N + iy * L];
-                f[iy] += a.da * (sg * vt * y + y * y);
+                f[iy] = fma(y, fma(sg, vt, y), f[iy]);
             }
         }
         if (valid) {
 #pragma unroll
-            for (int iy = 0; iy < L; ++iy) Fout[(long)tau * N + iy * L + geo.ix] = f[iy];
+            for (int iy = 0; iy < L; ++iy) {
+                double fo = a.da * f[iy];
+                if (bos) {
+                    const long o = iy * L + geo.ix;
+                    const double xc = x[(long)tau * N + o];
+                    const double lap = x[(long)tp * N + o] - 2.0 * xc + x[(long)tm * N + o];
+                    fo += a.dtau * a.w02 * xc - lap * a.inv_dtau;
+                }
+                Fout[(long)tau * N + iy * L + geo.ix] = fo;
+            }
         }
     }
     // per-unit sum of b.v over the slices tau-1 of the run
-    __shared__ double red[32 * 4];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    red[w * 32 + lane] = valid ? acc : 0.0;
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31;
+    red[lane] = valid ? acc : 0.0;
     __syncwarp();
     if (valid && geo.ix == 0) {
         double ssum = 0.0;
-        for (int k = 0; k < L; ++k) ssum += red[w * 32 + geo.g * L + k];
+        for (int k = 0; k < L; ++k) ssum += red[geo.g * L + k];
         sf_part[grp * a.nrun + run] = ssum;
     }
 }
@@ -100,7 +104,7 @@ __global__ void __launch_bounds__(128) k_force(const double* __restrict__ v,
 // plus the bosonic force of Eq. (dSB_dx).
 __global__ void k_force_sum(const double* __restrict__ Fp, int groups, const double* __restrict__ x,
                             int N, int T, int with_bos, double dtau, double w02,
-                            double* __restrict__ F)
+                            double inv_dtau, double* __restrict__ F)
 {
     const long n = (long)N * T;
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
@@ -112,7 +116,7 @@ __global__ void k_force_sum(const double* __restrict__ Fp, int groups, const dou
             const int tp = tau + 1 == T ? 0 : tau + 1, tm = tau == 0 ? T - 1 : tau - 1;
             const double xc = x[k];
             const double lap = x[(long)tp * N + i] - 2.0 * xc + x[(long)tm * N + i];
-            f += dtau * (w02 * xc - lap / (dtau * dtau));
+            f += dtau * w02 * xc - lap * inv_dtau;
         }
         F[k] = f;
     }
@@ -125,48 +129,60 @@ __global__ void k_sf_finish(const double* __restrict__ part, int cnt, double* __
     if (threadIdx.x == 0) *out = 0.5 * s;
 }
 
-// Pseudofermion groups of the force kernel: up to 7 in one group, else
-// groups of about four (each group's blocks run independently).
-void force_groups(int n_pf, int* groups, int* pg)
+// Launch plan of the force kernel. Nothing is reused between the slices of
+// a run, so each run is one slice (K = 1) unless the per-run partial sums of
+// S_F would not fit the partial-sum bank. The pseudofermions are split into
+// groups run by separate blocks until about eight warps per multiprocessor
+// are resident; with more than one group the partial forces go to scratch
+// and k_force_sum adds them in a fixed order.
+struct ForcePlan {
+    int K, nrun, groups, pg;
+};
+
+ForcePlan force_plan(const hol_ctx* c, int n_pf)
 {
-    if (n_pf < 8) {
-        *groups = 1;
-        *pg = n_pf;
-        return;
-    }
-    int g = (n_pf + 3) / 4;
-    const int p = (n_pf + g - 1) / g;
-    g = (n_pf + p - 1) / p;
-    *groups = g;
-    *pg = p;
+    ForcePlan f;
+    f.K = (c->T <= c->part_len) ? 1 : c->mv_k;
+    f.nrun = c->T / f.K;
+    const int G = 32 / c->L;                       // runs per warp
+    const long warps = (f.nrun + G - 1) / G;      // warps per group
+    const long target = 8L * c->sms;
+    long g = (target + warps - 1) / warps;
+    if (g > n_pf) g = n_pf;
+    if (g * f.nrun > c->part_len) g = c->part_len / f.nrun;
+    if (g < 1) g = 1;
+    f.pg = n_pf > 0 ? (int)((n_pf + g - 1) / g) : 0;
+    f.groups = f.pg > 0 ? (n_pf + f.pg - 1) / f.pg : 1;
+    return f;
 }
 
 template <int L>
 int run_force(hol_ctx* c, const double* v, const double* b, int n_pf, double* F, int with_bos,
               double* sf_part, cudaStream_t s)
 {
+    const ForcePlan f = force_plan(c, n_pf);
     ForceArgs a;
     a.T = c->T;
-    a.K = c->mv_k;
-    a.nrun = c->T / c->mv_k;
+    a.K = f.K;
+    a.nrun = f.nrun;
     a.n_pf = n_pf;
+    a.pg = f.pg;
+    a.groups = f.groups;
     a.n = c->n;
     a.with_bos = with_bos;
     a.th = c->th;
     a.da = c->p.dtau * c->p.alpha;
     a.dtau = c->p.dtau;
     a.w02 = c->p.omega0 * c->p.omega0;
-    // many pseudofermions: split them into groups processed by separate
-    // blocks (partial forces in the solver scratch, summed afterwards)
-    force_groups(n_pf, &a.groups, &a.pg);
+    a.inv_dtau = 1.0 / c->p.dtau;
     const int warps = ceil_div(a.nrun, LaneGeom<L>::G);
     double* Fp = a.groups > 1 ? c->v64a : F;
-    k_force<L><<<dim3(ceil_div(warps, 4), a.groups), 128, 0, s>>>(v, b, c->x, c->ev64, Fp,
-                                                                 sf_part, a);
+    k_force<L><<<dim3(warps, a.groups), 32, 0, s>>>(v, b, c->x, c->ev64, Fp, sf_part, a);
     HOL_CHECK_LAUNCH("k_force");
     if (a.groups > 1) {
         const int nb = ceil_div(c->n, 256) < 4096 ? ceil_div(c->n, 256) : 4096;
-        k_force_sum<<<nb, 256, 0, s>>>(Fp, a.groups, c->x, c->N, c->T, with_bos, a.dtau, a.w02, F);
+        k_force_sum<<<nb, 256, 0, s>>>(Fp, a.groups, c->x, c->N, c->T, with_bos, a.dtau, a.w02,
+                                       a.inv_dtau, F);
         HOL_CHECK_LAUNCH("k_force_sum");
     }
     return HOL_OK;
@@ -188,9 +204,8 @@ int launch_force(hol_ctx* c, const double* v, const double* b, int n_pf, double*
     }
     if (rc) return rc;
     if (S_F != nullptr) {
-        int groups, pg;
-        force_groups(n_pf, &groups, &pg);
-        k_sf_finish<<<1, 32, 0, s>>>(sf_part, groups * (c->T / c->mv_k), S_F);
+        const ForcePlan f = force_plan(c, n_pf);
+        k_sf_finish<<<1, 32, 0, s>>>(sf_part, f.groups * f.nrun, S_F);
         HOL_CHECK_LAUNCH("k_sf_finish");
     }
     return HOL_OK;

@@ -101,6 +101,7 @@ struct hol_ctx {
     int L, N, T;
     long n;              // N * T
     int device;
+    int sms;             // streaming multiprocessors of the device
     double th;           // tanh(dtau t): checkerboard bond [[1, th], [th, 1]]
     double ch4;          // cosh(dtau t)^4, folded into the stored exp(-dtau V)
 

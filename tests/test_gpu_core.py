@@ -415,12 +415,14 @@ def test_force_vs_dense_definition(L, T):
         assert _rel(Fb.cpu().numpy(), D.dSF_dx(m, x, Phi)) < 1e-12
 
 
-@pytest.mark.parametrize("n_pf", [0, 7, 9, 16])
-def test_force_many_pseudofermions(n_pf):
-    """Many pseudofermions are split into groups of blocks whose partial
+@pytest.mark.parametrize("L,T,n_pf", [(8, 12, 0), (8, 12, 1), (8, 12, 2), (6, 10, 3),
+                                      (8, 12, 7), (10, 6, 9), (8, 12, 16)])
+def test_force_many_pseudofermions(L, T, n_pf):
+    """The pseudofermions are split into groups of blocks whose partial
     forces are summed in a fixed order: same force and S_F as the dense
-    definition (n_pf = 0 leaves the bosonic force alone)."""
-    w, x = _field(8, 12, seed=15)
+    definition for one to sixteen of them, including lattice sides that
+    leave idle lanes in a warp (n_pf = 0 leaves the bosonic force alone)."""
+    w, x = _field(L, T, seed=15)
     m = D.model_of(w)
     Phi = hi.gaussian_vectors(w, max(n_pf, 1), seed=16)[:n_pf]
     with _ctx(w, 16) as ctx:
@@ -428,9 +430,14 @@ def test_force_many_pseudofermions(n_pf):
         F = torch.empty(w.Ltau, w.N, device=DEV, dtype=torch.float64)
         SF = torch.empty(1, device=DEV, dtype=torch.float64)
         if n_pf == 0:
+            import ctypes
             z = torch.zeros(1, w.Ltau, w.N, device=DEV, dtype=torch.float64)
-            from paper_2203_01291_gb300 import force as _force
-            _force(ctx._h, z, z, 0, F, True, SF, ctx.n)
+            p = ctypes.c_void_p
+            rc = hg._abi.load().force(ctx._h, p(z.data_ptr()), p(z.data_ptr()), 0,
+                                      p(F.data_ptr()), 1, p(SF.data_ptr()),
+                                      p(torch.cuda.current_stream().cuda_stream))
+            assert rc == 0
+            torch.cuda.synchronize()
             assert _rel(F.cpu().numpy(), D.dSB_dx(m, x)) < 1e-13
             assert float(SF) == 0.0
             return
