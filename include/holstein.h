@@ -52,6 +52,20 @@ extern "C" {
 #define HOL_PINVT       1   /* out = P^{-T} v                                  */
 #define HOL_PINV_PINVT  2   /* out = P^{-1} P^{-T} v (the PCG preconditioner)  */
 
+/*
+ * kinetic propagator C ~ exp(-dtau K) inside B_tau = exp(-dtau V_tau) C
+ * (Sec. II D). CHECKERBOARD: the split product C4 C3 C2 C1 of two-site bond
+ * factors (colours 1, 2: x-bonds from even / odd x; 3, 4: y-bonds from even /
+ * odd y), the paper's discretisation. EXACT: exp(-dtau K) itself, applied as
+ * E (x) E with E = exp(dtau t A_ring) the exact factor of one lattice
+ * direction (a symmetric circulant whose taps are kept down to the rounding
+ * of the arithmetic). An EXACT context runs its operators in the scalar
+ * register layout only: hol_set_option refuses the other layouts and the
+ * one-kernel CG variants for it, and fermion_matvec_static refuses EXACT.
+ */
+#define HOL_KINETIC_CHECKERBOARD 0
+#define HOL_KINETIC_EXACT        1
+
 typedef struct hol_params {
     int L;            /* linear lattice size (even, 4..32)                      */
     int Ltau;         /* number of imaginary-time slices T = beta / dtau (even) */
@@ -61,6 +75,7 @@ typedef struct hol_params {
     double alpha;     /* electron-phonon coupling                               */
     double omega0;    /* phonon frequency (phonon mass is 1)                    */
     int max_rhs;      /* largest n_rhs any later call will pass (>= 1)          */
+    int kinetic;      /* HOL_KINETIC_CHECKERBOARD (0) or HOL_KINETIC_EXACT (1)  */
 } hol_params;
 
 typedef struct hol_ctx hol_ctx;
@@ -362,7 +377,8 @@ int fermion_matvec_static(const hol_params* p, const double* x, int op, const do
  * context for all later calls (results are unchanged up to rounding; every
  * candidate computes the same operator). Host outputs (nullable): the chosen
  * slices per group, warps per block, layout (the "layout"
- * values of hol_set_option), and its time in ms.
+ * values of hol_set_option), and its time in ms. A context with the exact
+ * propagator (HOL_KINETIC_EXACT) tunes the scalar layout 0 only.
  * Requires hol_set_field; overwrites context scratch; synchronises `stream`.
  */
 int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_vec,
@@ -400,6 +416,9 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  *                       vector sets on first use) (0/1)
  * Every solver variant certifies convergence by the FP64 true residual;
  * iteration counts may differ by a few percent between them.
+ * A context with the exact propagator (HOL_KINETIC_EXACT) keeps layout 0 and
+ * refuses any other layout and kpm_registers, persistent_cg, fused_cg and
+ * merged_cg set to 1 (those kernels are checkerboard only).
  * Returns HOL_EINVAL for an unknown name or a value out of range (HOL_ECUDA
  * when an allocation fails).
  */

@@ -198,6 +198,35 @@ def M_apply(m: Model, x, v):
     return (fermion_matrix(m, x) @ np.asarray(v).reshape(-1)).reshape(m.Ltau, m.N)
 
 
+def M_apply_blocks(m: Model, x, v, C=None):
+    """M v block by block from Eq. (M_def): (M v)_0 = v_0 + B_0 v_{T-1},
+    (M v)_tau = v_tau - B_tau v_{tau-1}, B_tau = diag(expV_tau) C with the
+    dense N x N propagator C (passed in to reuse it). For lattices whose
+    full M does not fit in memory."""
+    C = kinetic_propagator(m) if C is None else C
+    d = expV(m, x)
+    v = np.asarray(v).reshape(m.Ltau, m.N)
+    out = np.empty_like(v)
+    for tau in range(m.Ltau):
+        s = 1.0 if tau == 0 else -1.0
+        out[tau] = v[tau] + s * d[tau] * (C @ v[tau - 1])
+    return out
+
+
+def MT_apply_blocks(m: Model, x, u, C=None):
+    """M^T u block by block: (M^T u)_tau = u_tau + s_{tau+1} C^T diag(expV_{tau+1}) u_{tau+1}."""
+    C = kinetic_propagator(m) if C is None else C
+    d = expV(m, x)
+    u = np.asarray(u).reshape(m.Ltau, m.N)
+    T = m.Ltau
+    out = np.empty_like(u)
+    for tau in range(T):
+        tp = (tau + 1) % T
+        s = 1.0 if tp == 0 else -1.0
+        out[tau] = u[tau] + s * (C.T @ (d[tp] * u[tp]))
+    return out
+
+
 def MT_apply(m: Model, x, v):
     return (fermion_matrix(m, x).T @ np.asarray(v).reshape(-1)).reshape(m.Ltau, m.N)
 

@@ -22,7 +22,8 @@ import numpy as np
 import torch
 
 from ._abi import (HOL_ECUDA, HOL_EINVAL, HOL_ENOMEM, HOL_ENOTCONV, HOL_ENUMERIC, HOL_ETIMEOUT,
-                   HOL_F32, HOL_F64, HOL_OK, HOL_OP_M, HOL_OP_MT, HOL_OP_MTM, HOL_PINV,
+                   HOL_F32, HOL_F64, HOL_KINETIC_CHECKERBOARD, HOL_KINETIC_EXACT, HOL_OK,
+                   HOL_OP_M, HOL_OP_MT, HOL_OP_MTM, HOL_PINV,
                    HOL_PINV_PINVT, HOL_PINVT, HOL_REFLECT, HOL_SWAP, hol_cg_opts, hol_md_opts,
                    hol_params, load, library_path)
 
@@ -34,6 +35,7 @@ __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F6
            "fourier_accel_leapfrog", "hol_md_opts", "stochastic_measure", "hol_tune",
            "hmc_batch", "measure_batch", "hol_set_option", "hol_get_option", "hol_fma_peak",
            "global_update", "HOL_REFLECT", "HOL_SWAP", "measure_observables",
+           "HOL_KINETIC_CHECKERBOARD", "HOL_KINETIC_EXACT",
            "library_path", "load"]
 
 
@@ -291,13 +293,15 @@ class Context:
     """One lattice shape and set of couplings (owns the library context)."""
 
     def __init__(self, L: int, Ltau: int, dtau: float = 0.1, t: float = 1.0, mu: float = 0.0,
-                 alpha: float = 1.0, omega0: float = 1.0, max_rhs: int = 1):
+                 alpha: float = 1.0, omega0: float = 1.0, max_rhs: int = 1,
+                 kinetic: int = HOL_KINETIC_CHECKERBOARD):
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2203_01291_gb300 needs a CUDA GPU; there is no CPU fallback")
         self.L, self.Ltau, self.N = L, Ltau, L * L
         self.n = self.N * Ltau
         self.max_rhs = max_rhs
-        self.params = hol_params(L, Ltau, dtau, t, mu, alpha, omega0, max_rhs)
+        self.kinetic = kinetic
+        self.params = hol_params(L, Ltau, dtau, t, mu, alpha, omega0, max_rhs, kinetic)
         self._h = hol_create(self.params)
 
     @classmethod

@@ -27,11 +27,15 @@ HOL_PINV = 0
 HOL_PINVT = 1
 HOL_PINV_PINVT = 2
 
+HOL_KINETIC_CHECKERBOARD = 0
+HOL_KINETIC_EXACT = 1
+
 
 class hol_params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("Ltau", ctypes.c_int), ("dtau", ctypes.c_double),
                 ("t", ctypes.c_double), ("mu", ctypes.c_double), ("alpha", ctypes.c_double),
-                ("omega0", ctypes.c_double), ("max_rhs", ctypes.c_int)]
+                ("omega0", ctypes.c_double), ("max_rhs", ctypes.c_int),
+                ("kinetic", ctypes.c_int)]
 
 
 class hol_cg_opts(ctypes.Structure):

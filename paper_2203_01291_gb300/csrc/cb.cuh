@@ -87,6 +87,80 @@ __device__ __forceinline__ void cb_apply_t(R (&c)[L], const LaneGeom<L>& g, R th
     cb_xbond<R, L>(c, g.p1, th);
 }
 
+// ---------------------------------------------------------------------------
+// Exact kinetic propagator exp(-dtau K). On the periodic L x L lattice K is a
+// sum of commuting x and y hopping terms, so exp(-dtau K) = E (x) E with E =
+// exp(dtau t A) for the adjacency A of a ring of L sites: a symmetric
+// circulant, E[i][j] = e[d], d the ring distance of i and j (0..L/2). The
+// host computes e[d] from the ring's spectrum 2 cos(2 pi k / L) and keeps the
+// taps d <= D beyond which |e[d]| is below the rounding of the precision.
+// ---------------------------------------------------------------------------
+constexpr int kKinTaps = 17;   // L / 2 + 1 for L <= 32
+
+template <typename R>
+struct Kin {
+    R th;             // checkerboard bond tanh(dtau t)
+    int D;            // exact propagator: taps kept on each side of the centre
+    R e[kKinTaps];    // exact propagator: e[0..D]
+};
+
+// c <- exp(-dtau K) c for the slice held by a lane group (x along the lanes,
+// then y along the registers; E is symmetric, so this is also the transpose).
+template <typename R, int L>
+__device__ __forceinline__ void kin_exact(R (&c)[L], const LaneGeom<L>& g, const Kin<R>& k)
+{
+    const int base = g.g * L;
+    R o[L];
+#pragma unroll
+    for (int iy = 0; iy < L; ++iy) o[iy] = k.e[0] * c[iy];
+#pragma unroll
+    for (int d = 1; d <= L / 2; ++d) {
+        if (d <= k.D) {
+            const int jp = base + (g.ix + d) % L;
+            const int jm = base + (g.ix + L - d) % L;
+#pragma unroll
+            for (int iy = 0; iy < L; ++iy) {
+                R a = __shfl_sync(kFull, c[iy], jp);
+                if (2 * d != L) a += __shfl_sync(kFull, c[iy], jm);
+                o[iy] = fma(k.e[d], a, o[iy]);
+            }
+        }
+    }
+#pragma unroll
+    for (int iy = 0; iy < L; ++iy) c[iy] = k.e[0] * o[iy];
+#pragma unroll
+    for (int d = 1; d <= L / 2; ++d) {
+        if (d <= k.D) {
+#pragma unroll
+            for (int iy = 0; iy < L; ++iy) {
+                R a = o[(iy + d) % L];
+                if (2 * d != L) a += o[(iy + L - d) % L];
+                c[iy] = fma(k.e[d], a, c[iy]);
+            }
+        }
+    }
+}
+
+// c <- C c with the propagator the kernel was instantiated for.
+template <typename R, int L, bool EX>
+__device__ __forceinline__ void kin_apply(R (&c)[L], const LaneGeom<L>& g, const Kin<R>& k)
+{
+    if constexpr (EX)
+        kin_exact<R, L>(c, g, k);
+    else
+        cb_apply<R, L>(c, g, k.th);
+}
+
+// c <- C^T c.
+template <typename R, int L, bool EX>
+__device__ __forceinline__ void kin_apply_t(R (&c)[L], const LaneGeom<L>& g, const Kin<R>& k)
+{
+    if constexpr (EX)
+        kin_exact<R, L>(c, g, k);
+    else
+        cb_apply_t<R, L>(c, g, k.th);
+}
+
 // Warp-wide sum of a double, identical result in every lane (fixed order).
 __device__ __forceinline__ double warp_sum(double v)
 {

@@ -157,6 +157,52 @@ using namespace hol;
 
 extern "C" const char* hol_last_error(void) { return g_err; }
 
+// Modified Bessel function I_n(x) by its power series
+// sum_k (x/2)^(2k+n) / (k! (k+n)!) (all terms of one sign, no cancellation).
+static double bessel_i(int n, double x)
+{
+    const double h = 0.5 * x;
+    double term = 1.0;
+    for (int j = 1; j <= n; ++j) {
+        term *= h / j;
+        if (term == 0.0) return 0.0;
+    }
+    double sum = term;
+    for (int k = 1; k < 200; ++k) {
+        term *= h * h / ((double)k * (double)(k + n));
+        sum += term;
+        if (fabs(term) <= 1e-20 * fabs(sum)) break;
+    }
+    return sum;
+}
+
+// Taps of the exact one-direction factor E = exp(dtau t A_ring) on a ring of
+// L sites: exp(a A_line) has entries I_|i-j|(2a) on the infinite line, and
+// the ring sums the images, e[d] = sum_m I_|d + m L|(2 dtau t). Taps whose
+// magnitude is below 2^-60 (FP64) or 2^-30 (FP32) of e[0] are dropped: their
+// total is far below the rounding of that arithmetic.
+static void exact_taps(hol_ctx* c)
+{
+    const int L = c->L;
+    const double x = 2.0 * c->p.dtau * c->p.t;
+    for (int d = 0; d < kKinTaps; ++d) c->kin_e[d] = 0.0;
+    for (int d = 0; d <= L / 2; ++d) {
+        double e = 0.0;
+        for (int m = -64; m <= 64; ++m) {
+            const int k = abs(d + m * L);
+            if (k > 400) continue;
+            e += bessel_i(k, x);
+        }
+        c->kin_e[d] = e;
+    }
+    const double e0 = fabs(c->kin_e[0]);
+    int d64 = L / 2, d32 = L / 2;
+    while (d64 > 0 && fabs(c->kin_e[d64]) <= 0x1p-60 * e0) --d64;
+    while (d32 > 0 && fabs(c->kin_e[d32]) <= 0x1p-30 * e0) --d32;
+    c->kin_d64 = d64;
+    c->kin_d32 = d32;
+}
+
 extern "C" int hol_create(const hol_params* p, hol_ctx** out)
 {
     if (!p || !out) return set_error(HOL_EINVAL, "hol_create: null argument");
@@ -170,6 +216,12 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     if (!(p->dtau > 0.0) || !isfinite(p->t) || !isfinite(p->mu) || !isfinite(p->alpha) ||
         !isfinite(p->omega0))
         return set_error(HOL_EINVAL, "hol_create: non-finite or non-positive parameter");
+    if (p->kinetic != HOL_KINETIC_CHECKERBOARD && p->kinetic != HOL_KINETIC_EXACT)
+        return set_error(HOL_EINVAL, "hol_create: kinetic=%d must be %d (checkerboard) or %d "
+                                     "(exact)", p->kinetic, HOL_KINETIC_CHECKERBOARD,
+                         HOL_KINETIC_EXACT);
+    if (p->kinetic == HOL_KINETIC_EXACT && fabs(p->dtau * p->t) > 4.0)
+        return set_error(HOL_EINVAL, "hol_create: exact propagator needs |dtau t| <= 4");
 
     hol_ctx* c = (hol_ctx*)calloc(1, sizeof(hol_ctx));
     if (!c) return set_error(HOL_ENOMEM, "hol_create: host allocation failed");
@@ -179,14 +231,18 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     c->T = p->Ltau;
     c->n = (long)c->N * c->T;
     c->th = tanh(p->dtau * p->t);
-    {
+    c->exact = p->kinetic == HOL_KINETIC_EXACT;
+    if (c->exact) {
+        c->ch4 = 1.0;
+        exact_taps(c);
+    } else {
         const double ch = cosh(p->dtau * p->t);
         c->ch4 = ch * ch * ch * ch;
     }
     c->mv_k = (c->T % 4 == 0 && c->T >= 8) ? 2 : 1;
     c->mv_warps = 4;
-    c->mv_vec = 1;
-    c->kpm_reg = 1;
+    c->mv_vec = c->exact ? 0 : 1;
+    c->kpm_reg = c->exact ? 0 : 1;
     c->persist = 0;
     c->merged = 0;
     c->fused = 0;
@@ -413,18 +469,26 @@ extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
             return set_error(HOL_EINVAL, "hol_set_option: warps_per_block must be 1, 2 or 4");
         c->mv_warps = value;
     } else if (is("layout")) {
+        if (value != 0 && c->exact)
+            return set_error(HOL_EINVAL, "hol_set_option: the exact propagator runs in layout 0");
         if (value < 0 || value > 6 || (value > 0 && c->L % 8) ||
             ((value == 4 || value == 5) && c->L != 32))
             return set_error(HOL_EINVAL, "hol_set_option: layout 0..6 (1-3, 6 need L %% 8 == 0, "
                                          "4-5 L == 32)");
         c->mv_vec = value;
     } else if (is("kpm_registers")) {
+        if (value && c->exact)
+            return set_error(HOL_EINVAL, "hol_set_option: kpm_registers is checkerboard only");
         c->kpm_reg = value ? 1 : 0;
     } else if (is("persistent_cg")) {
+        if (value && c->exact)
+            return set_error(HOL_EINVAL, "hol_set_option: persistent_cg is checkerboard only");
         c->persist = value ? 1 : 0;
     } else if (is("pdl")) {
         c->pdl = value ? 1 : 0;
     } else if (is("merged_cg") || is("fused_cg")) {
+        if (value && c->exact)
+            return set_error(HOL_EINVAL, "hol_set_option: %s is checkerboard only", name);
         if (value && c->L % 8)
             return set_error(HOL_EINVAL, "hol_set_option: %s needs L %% 8 == 0", name);
         if (value) {

@@ -6,7 +6,8 @@
 //                     - (dtau alpha / 2) b_{i,tau-1} v_{i,tau-1},
 //   y_tau = exp(-dtau V_tau) C v_{tau-1},  u_tau = v_tau + s_tau y_tau,
 // so the kernel recomputes B_tau v_{tau-1} slice by slice (nothing of M is
-// stored) and adds the bosonic stencil of Eq. (dSB_dx).
+// stored) and adds the bosonic stencil of Eq. (dSB_dx). C is the checkerboard
+// product or, for a context with the exact propagator, exp(-dtau K).
 #include "cb.cuh"
 #include "internal.cuh"
 
@@ -19,11 +20,12 @@ struct ForceArgs {
     int groups;      // > 1: each group writes its partial force to Fp[group]
     long n;
     int with_bos;
-    double th, da, dtau, w02;
+    double da, dtau, w02;
     double inv_dtau;   // 1 / dtau, so the stencil needs no division
+    Kin<double> kin;   // propagator (checkerboard or exact)
 };
 
-template <int L>
+template <int L, bool EX>
 __global__ void __launch_bounds__(32) k_force(const double* __restrict__ v,
                                                const double* __restrict__ b,
                                                const double* __restrict__ x,
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(32) k_force(const double* __restrict__ v,
                 f[iy] = fma(-0.5, bv, f[iy]);
                 c[iy] = vv;
             }
-            cb_apply<double, L>(c, geo, a.th);
+            kin_apply<double, L, EX>(c, geo, a.kin);
 #pragma unroll
             for (int iy = 0; iy < L; ++iy) {
                 const double y = ev[(long)tau * N + iy * L + geo.ix] * c[iy];
@@ -170,14 +172,17 @@ int run_force(hol_ctx* c, const double* v, const double* b, int n_pf, double* F,
     a.groups = f.groups;
     a.n = c->n;
     a.with_bos = with_bos;
-    a.th = c->th;
+    a.kin = kin_of<double>(c);
     a.da = c->p.dtau * c->p.alpha;
     a.dtau = c->p.dtau;
     a.w02 = c->p.omega0 * c->p.omega0;
     a.inv_dtau = 1.0 / c->p.dtau;
     const int warps = ceil_div(a.nrun, LaneGeom<L>::G);
     double* Fp = a.groups > 1 ? c->v64a : F;
-    k_force<L><<<dim3(warps, a.groups), 32, 0, s>>>(v, b, c->x, c->ev64, Fp, sf_part, a);
+    if (c->exact)
+        k_force<L, true><<<dim3(warps, a.groups), 32, 0, s>>>(v, b, c->x, c->ev64, Fp, sf_part, a);
+    else
+        k_force<L, false><<<dim3(warps, a.groups), 32, 0, s>>>(v, b, c->x, c->ev64, Fp, sf_part, a);
     HOL_CHECK_LAUNCH("k_force");
     if (a.groups > 1) {
         const int nb = ceil_div(c->n, 256) < 4096 ? ceil_div(c->n, 256) : 4096;

@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include "../../include/holstein.h"
+#include "cb.cuh"
 
 namespace hol {
 
@@ -104,6 +105,10 @@ struct hol_ctx {
     int sms;             // streaming multiprocessors of the device
     double th;           // tanh(dtau t): checkerboard bond [[1, th], [th, 1]]
     double ch4;          // cosh(dtau t)^4, folded into the stored exp(-dtau V)
+                         // (1 with the exact propagator)
+    int exact;           // kinetic == HOL_KINETIC_EXACT
+    int kin_d64, kin_d32;            // exact propagator: taps kept in FP64 / FP32
+    double kin_e[hol::kKinTaps];     // exact propagator: ring factor taps e[0..L/2]
 
     // field-derived data (hol_set_field)
     double* x;           // [T][N] copy of the field
@@ -221,6 +226,32 @@ int launch_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* 
                     float* q, int n_rhs, const int* mask, const double* rr_new,
                     const double* rr_old, int rr_stride, int rr_n, int first,
                     double* pq_part, cudaStream_t s);
+// The same five operators with the exact propagator exp(-dtau K) (exact.cu;
+// scalar layout only). The launch_* calls above forward to these when the
+// context was created with HOL_KINETIC_EXACT.
+int launch_M_exact(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs,
+                   const int* mask, double* norm_part, cudaStream_t s);
+int launch_M_upd64_exact(const hol_ctx* c, const double* r, const double* pold, double* pnew,
+                         double* w, int n_rhs, const int* mask, BetaSrc beta,
+                         double* norm_part, cudaStream_t s);
+int launch_MT_exact(const hol_ctx* c, int prec, const void* u, void* out, int n_rhs,
+                    const int* mask, cudaStream_t s);
+int launch_MT_resid64_exact(const hol_ctx* c, const double* u, const double* b, double* out,
+                            int n_rhs, const int* mask, cudaStream_t s);
+int launch_cg_mtm32_exact(const hol_ctx* c, const float* r, const float* pold, float* pnew,
+                          float* q, int n_rhs, const int* mask, const double* rr_new,
+                          const double* rr_old, int rr_stride, int rr_n, int first,
+                          double* pq_part, cudaStream_t s);
+// Propagator parameters of a context for kernels computing in R.
+template <typename R>
+inline Kin<R> kin_of(const hol_ctx* c)
+{
+    Kin<R> k;
+    k.th = (R)c->th;
+    k.D = c->exact ? (sizeof(R) == 8 ? c->kin_d64 : c->kin_d32) : 0;
+    for (int d = 0; d < kKinTaps; ++d) k.e[d] = (R)c->kin_e[d];
+    return k;
+}
 // Persistent fused CG chunk (persist.cu); HOL_EINVAL without launching when
 // unsupported (L % 8 != 0) or when the cooperative grid cannot be resident.
 int launch_cg_persist(const hol_ctx* c, float* r, float* p0, float* p1, float* e, int n_rhs,

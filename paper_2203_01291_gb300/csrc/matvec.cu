@@ -1,252 +1,17 @@
-// Fermion-matrix kernels: M v, M^T u and the fused M^T M of the CG iteration
-// (Eq. (M_def), Sec. II D).
-//
-// Work decomposition. A "unit" is one right-hand side and a run of K
-// consecutive tau slices; one lane group (L lanes, see cb.cuh) streams the
-// run, holding one slice per register column. A warp holds G = 32/L groups
-// that always belong to the same right-hand side (the run index is padded to
-// a multiple of G), so per-rhs scalars are warp-uniform. Every global access
-// is a row of L consecutive sites (coalesced); the propagator itself never
-// leaves registers.
+// Fermion-matrix kernels in the float4, split and streaming layouts, the
+// merged and fused one-kernel CG iterations, and the launch dispatch of all
+// operator kernels (Eq. (M_def), Sec. II D). The scalar-layout kernels are
+// in mvscalar.cuh.
 #include "cb.cuh"
 #include "cb4.cuh"
 #include "cbs.cuh"
 #include <atomic>
 
 #include "internal.cuh"
+#include "mvscalar.cuh"
 
 namespace hol {
 namespace {
-
-struct MvGeom {
-    int T;              // slices
-    int K;              // slices per unit (divides T)
-    int nrun;           // T / K
-    int wpr;            // warps per right-hand side = ceil(nrun / G)
-    int n_rhs;
-    int pstride;        // stride of the per-unit partial sums (= wpr * G)
-};
-
-template <int L>
-__host__ MvGeom make_geom(const hol_ctx* c, int n_rhs)
-{
-    MvGeom g;
-    g.T = c->T;
-    g.K = c->mv_k;
-    g.nrun = c->T / c->mv_k;
-    constexpr int G = 32 / L;
-    g.wpr = (g.nrun + G - 1) / G;
-    g.n_rhs = n_rhs;
-    g.pstride = g.wpr * G;
-    return g;
-}
-
-// ---------------------------------------------------------------------------
-// out = M v. With UPD the loaded vector is p_new = r + beta p_old (the CG
-// direction update), whose own slices are also stored to pnew.
-// norm_part (nullable): |out|^2 summed over the unit's slices.
-// ---------------------------------------------------------------------------
-template <typename R, int L, bool UPD>
-__global__ void __launch_bounds__(128) k_M(const R* __restrict__ v, const R* __restrict__ pold,
-                                           R* __restrict__ pnew, R* __restrict__ out,
-                                           const R* __restrict__ ev, MvGeom gm,
-                                           const int* __restrict__ mask, BetaSrc bsrc,
-                                           double* __restrict__ norm_part, R th)
-{
-    constexpr int N = L * L;
-    const LaneGeom<L> geo;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int rhs = warp / gm.wpr;
-    if (rhs >= gm.n_rhs) return;
-    if (mask != nullptr && mask[rhs] == 0) return;
-    const int run = (warp - rhs * gm.wpr) * LaneGeom<L>::G + geo.g;
-    const bool valid = geo.ok && run < gm.nrun;
-    const int t0 = (run < gm.nrun ? run : gm.nrun - 1) * gm.K;
-    const long base = (long)rhs * gm.T * N + geo.ix;
-    R bt = R(0);
-    if (UPD && !bsrc.first) {
-        const double rn = warp_sum_array(bsrc.rn + (long)rhs * bsrc.stride, bsrc.n);
-        const double ro = warp_sum_array(bsrc.ro + (long)rhs * bsrc.stride, bsrc.n);
-        bt = (R)(rn / ro);
-    }
-
-    R a[L], c[L];
-    {
-        const int tm = (t0 == 0) ? gm.T - 1 : t0 - 1;
-        const long o = base + (long)tm * N;
-#pragma unroll
-        for (int iy = 0; iy < L; ++iy) {
-            R val = v[o + iy * L];
-            if (UPD) val = fma(bt, pold[o + iy * L], val);
-            a[iy] = val;
-        }
-    }
-    double acc = 0.0;
-    for (int s = 0; s < gm.K; ++s) {
-        const int tau = t0 + s;
-        const long o = base + (long)tau * N;
-        cb_apply<R, L>(a, geo, (R)th);
-#pragma unroll
-        for (int iy = 0; iy < L; ++iy) {
-            R val = v[o + iy * L];
-            if (UPD) {
-                val = fma(bt, pold[o + iy * L], val);
-                if (valid) pnew[o + iy * L] = val;
-            }
-            c[iy] = val;
-        }
-        const R sg = (tau == 0) ? R(1) : R(-1);
-        R part = R(0);
-#pragma unroll
-        for (int iy = 0; iy < L; ++iy) {
-            const R w = fma(sg * ev[(long)tau * N + iy * L + geo.ix], a[iy], c[iy]);
-            if (valid) out[o + iy * L] = w;
-            part = fma(w, w, part);
-            a[iy] = c[iy];
-        }
-        acc += (double)part;
-    }
-    if (norm_part != nullptr) group_store_sum<L>(acc, valid, norm_part + (long)rhs * gm.pstride + run);
-}
-
-// ---------------------------------------------------------------------------
-// out = M^T u (EPI = MT_PLAIN) or, FP64 only, out = b - M^T u (MT_RESID).
-// Streams the run downwards: (M^T u)_tau needs u_tau and u_{tau+1}.
-// ---------------------------------------------------------------------------
-template <typename R, int L, int EPI>
-__global__ void __launch_bounds__(128) k_MT(const R* __restrict__ u, const R* __restrict__ bvec,
-                                            R* __restrict__ out, const R* __restrict__ ev,
-                                            MvGeom gm, const int* __restrict__ mask, R th)
-{
-    constexpr int N = L * L;
-    const LaneGeom<L> geo;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int rhs = warp / gm.wpr;
-    if (rhs >= gm.n_rhs) return;
-    if (mask != nullptr && mask[rhs] == 0) return;
-    const int run = (warp - rhs * gm.wpr) * LaneGeom<L>::G + geo.g;
-    const bool valid = geo.ok && run < gm.nrun;
-    const int t0 = (run < gm.nrun ? run : gm.nrun - 1) * gm.K;
-    const long base = (long)rhs * gm.T * N + geo.ix;
-
-    R a[L], c[L];
-    {
-        int tp = t0 + gm.K;
-        if (tp == gm.T) tp = 0;
-        const long o = base + (long)tp * N;
-#pragma unroll
-        for (int iy = 0; iy < L; ++iy) a[iy] = u[o + iy * L];
-    }
-    for (int s = gm.K - 1; s >= 0; --s) {
-        const int tau = t0 + s;
-        const int tp = (tau + 1 == gm.T) ? 0 : tau + 1;
-#pragma unroll
-        for (int iy = 0; iy < L; ++iy) a[iy] *= ev[(long)tp * N + iy * L + geo.ix];
-        cb_apply_t<R, L>(a, geo, (R)th);
-        const long o = base + (long)tau * N;
-        const R sg = (tp == 0) ? R(1) : R(-1);
-#pragma unroll
-        for (int iy = 0; iy < L; ++iy) {
-            c[iy] = u[o + iy * L];
-            R w = fma(sg, a[iy], c[iy]);
-            if (EPI == MT_RESID) w = bvec[o + iy * L] - w;
-            if (valid) out[o + iy * L] = w;
-            a[iy] = c[iy];
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// FP32 fused CG step: p_new = r + beta p_old, q = M^T M p_new,
-// pq_part = |M p_new|^2 = p_new . q per unit. The run needs w = M p on
-// [t0, t0+K] and hence p on [t0-1, t0+K]; halo values are recomputed.
-// ---------------------------------------------------------------------------
-template <int L>
-__global__ void __launch_bounds__(128) k_cg_mtm32(const float* __restrict__ r,
-                                                  const float* __restrict__ pold,
-                                                  float* __restrict__ pnew, float* __restrict__ q,
-                                                  const float* __restrict__ ev, MvGeom gm,
-                                                  const int* __restrict__ mask,
-                                                  const double* __restrict__ rr_new_part,
-                                                  const double* __restrict__ rr_old_part,
-                                                  int rr_stride, int rr_n, int first,
-                                                  double* __restrict__ pq_part, float th)
-{
-    pdl_wait();      // inputs may come from the previous kernel of the stream
-    const PdlTriggerAtExit pdl_at_exit;
-    constexpr int N = L * L;
-    const LaneGeom<L> geo;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int rhs = warp / gm.wpr;
-    if (rhs >= gm.n_rhs) return;
-    if (mask != nullptr && mask[rhs] == 0) return;
-    const int run = (warp - rhs * gm.wpr) * LaneGeom<L>::G + geo.g;
-    const bool valid = geo.ok && run < gm.nrun;
-    const int t0 = (run < gm.nrun ? run : gm.nrun - 1) * gm.K;
-    const long base = (long)rhs * gm.T * N + geo.ix;
-
-    // beta = (r.r)_new / (r.r)_old, identical bits in every warp of this rhs
-    float bt = 0.0f;
-    if (!first) {
-        const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
-        const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
-        bt = (float)(rn / ro);
-    }
-
-    float W[L], X[L], P[L], Y[L];
-    // Y <- C p_{t0-1}
-    {
-        const int tm = (t0 == 0) ? gm.T - 1 : t0 - 1;
-        const long o = base + (long)tm * N;
-#pragma unroll
-        for (int iy = 0; iy < L; ++iy) Y[iy] = fmaf(bt, pold[o + iy * L], r[o + iy * L]);
-        cb_apply<float, L>(Y, geo, th);
-    }
-    // W <- w_{t0} = p_{t0} + s_{t0} D_{t0} C p_{t0-1};  X <- C p_{t0}
-    {
-        const long o = base + (long)t0 * N;
-        const float sg = (t0 == 0) ? 1.0f : -1.0f;
-#pragma unroll
-        for (int iy = 0; iy < L; ++iy) {
-            const float pv = fmaf(bt, pold[o + iy * L], r[o + iy * L]);
-            if (valid && pnew != nullptr) pnew[o + iy * L] = pv;
-            X[iy] = pv;
-            W[iy] = fmaf(sg * ev[(long)t0 * N + iy * L + geo.ix], Y[iy], pv);
-        }
-        cb_apply<float, L>(X, geo, th);
-    }
-    double acc = 0.0;
-    for (int s = 0; s < gm.K; ++s) {
-        const int tau = t0 + s;
-        const int tp = (tau + 1 == gm.T) ? 0 : tau + 1;
-        const long op = base + (long)tp * N;
-        const float sgp = (tp == 0) ? 1.0f : -1.0f;
-        const bool own = valid && (s + 1 < gm.K) && pnew != nullptr;
-#pragma unroll
-        for (int iy = 0; iy < L; ++iy) {
-            const float pv = fmaf(bt, pold[op + iy * L], r[op + iy * L]);
-            if (own) pnew[op + iy * L] = pv;
-            P[iy] = pv;
-            const float d = sgp * ev[(long)tp * N + iy * L + geo.ix];
-            X[iy] = fmaf(d, X[iy], pv);       // w_{tau+1}
-            Y[iy] = d * X[iy];
-        }
-        cb_apply<float, L>(P, geo, th);     // C p_{tau+1}
-        cb_apply_t<float, L>(Y, geo, th);   // C^T s D w_{tau+1}
-        const long o = base + (long)tau * N;
-        float part = 0.0f;
-#pragma unroll
-        for (int iy = 0; iy < L; ++iy) {
-            if (valid) q[o + iy * L] = W[iy] + Y[iy];
-            part = fmaf(W[iy], W[iy], part);
-            W[iy] = X[iy];
-            X[iy] = P[iy];
-        }
-        acc += (double)part;
-    }
-    if (pq_part != nullptr) group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
-}
-
 
 // ---------------------------------------------------------------------------
 // Same fused FP32 CG step in the float4 layout of cb4.cuh (L % 8 == 0).
@@ -1201,74 +966,10 @@ __global__ void __launch_bounds__(256) k_unit_dots(const float* __restrict__ r,
     }
 }
 
-template <int L>
-int blocks_for(const hol_ctx* c, const MvGeom& g)
-{
-    const long warps = (long)g.wpr * g.n_rhs;
-    return ceil_div(warps, c->mv_warps);
-}
 
 // ---------------------------------------------------------------------------
 // dispatch on L
 // ---------------------------------------------------------------------------
-#define HOL_FOR_EACH_L(X) \
-    X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32)
-
-template <int L>
-int run_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs, const int* mask,
-          double* norm_part, cudaStream_t s)
-{
-    const MvGeom g = make_geom<L>(c, n_rhs);
-    const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-    if (prec == HOL_F64)
-        k_M<double, L, false><<<nb, nt, 0, s>>>((const double*)v, nullptr, nullptr, (double*)out,
-                                                c->ev64, g, mask, BetaSrc{}, norm_part, c->th);
-    else
-        k_M<float, L, false><<<nb, nt, 0, s>>>((const float*)v, nullptr, nullptr, (float*)out,
-                                               c->ev32, g, mask, BetaSrc{}, norm_part,
-                                               (float)c->th);
-    HOL_CHECK_LAUNCH("k_M");
-    return HOL_OK;
-}
-
-template <int L>
-int run_M_upd64(const hol_ctx* c, const double* r, const double* pold, double* pnew, double* w,
-                int n_rhs, const int* mask, BetaSrc beta, double* norm_part, cudaStream_t s)
-{
-    const MvGeom g = make_geom<L>(c, n_rhs);
-    const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-    k_M<double, L, true><<<nb, nt, 0, s>>>(r, pold, pnew, w, c->ev64, g, mask, beta, norm_part,
-                                           c->th);
-    HOL_CHECK_LAUNCH("k_M upd");
-    return HOL_OK;
-}
-
-template <int L>
-int run_MT(const hol_ctx* c, int prec, const void* u, void* out, int n_rhs, const int* mask,
-           cudaStream_t s)
-{
-    const MvGeom g = make_geom<L>(c, n_rhs);
-    const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-    if (prec == HOL_F64)
-        k_MT<double, L, MT_PLAIN><<<nb, nt, 0, s>>>((const double*)u, nullptr, (double*)out,
-                                                    c->ev64, g, mask, c->th);
-    else
-        k_MT<float, L, MT_PLAIN><<<nb, nt, 0, s>>>((const float*)u, nullptr, (float*)out, c->ev32,
-                                                   g, mask, (float)c->th);
-    HOL_CHECK_LAUNCH("k_MT");
-    return HOL_OK;
-}
-
-template <int L>
-int run_MT_resid(const hol_ctx* c, const double* u, const double* b, double* out, int n_rhs,
-                 const int* mask, cudaStream_t s)
-{
-    const MvGeom g = make_geom<L>(c, n_rhs);
-    const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-    k_MT<double, L, MT_RESID><<<nb, nt, 0, s>>>(u, b, out, c->ev64, g, mask, c->th);
-    HOL_CHECK_LAUNCH("k_MT resid");
-    return HOL_OK;
-}
 
 template <int L>
 int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pnew, float* q,
@@ -1353,10 +1054,8 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
             return HOL_OK;
         }
     }
-    HOL_CUDA(launch_pdl(c, k_cg_mtm32<L>, nb, nt, 0, s, r, pold, pnew, q, c->ev32, g, mask,
-                        rr_new, rr_old, rr_stride, rr_n, first, pq_part, (float)c->th));
-    HOL_CHECK_LAUNCH("k_cg_mtm32");
-    return HOL_OK;
+    return run_cg_mtm32_scalar<L, false>(c, r, pold, pnew, q, n_rhs, mask, rr_new, rr_old,
+                                         rr_stride, rr_n, first, pq_part, s);
 }
 
 
@@ -1485,8 +1184,9 @@ int matvec_pstride(const hol_ctx* c)
 int launch_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs, const int* mask,
              double* norm_part, cudaStream_t s)
 {
+    if (c->exact) return launch_M_exact(c, prec, v, out, n_rhs, mask, norm_part, s);
     switch (c->L) {
-#define X(LL) case LL: return run_M<LL>(c, prec, v, out, n_rhs, mask, norm_part, s);
+#define X(LL) case LL: return run_M<LL, false>(c, prec, v, out, n_rhs, mask, norm_part, s);
         HOL_FOR_EACH_L(X)
 #undef X
     }
@@ -1496,8 +1196,10 @@ int launch_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs, co
 int launch_M_upd64(const hol_ctx* c, const double* r, const double* pold, double* pnew, double* w,
                    int n_rhs, const int* mask, BetaSrc beta, double* norm_part, cudaStream_t s)
 {
+    if (c->exact)
+        return launch_M_upd64_exact(c, r, pold, pnew, w, n_rhs, mask, beta, norm_part, s);
     switch (c->L) {
-#define X(LL) case LL: return run_M_upd64<LL>(c, r, pold, pnew, w, n_rhs, mask, beta, norm_part, s);
+#define X(LL) case LL: return run_M_upd64<LL, false>(c, r, pold, pnew, w, n_rhs, mask, beta, norm_part, s);
         HOL_FOR_EACH_L(X)
 #undef X
     }
@@ -1507,8 +1209,9 @@ int launch_M_upd64(const hol_ctx* c, const double* r, const double* pold, double
 int launch_MT(const hol_ctx* c, int prec, const void* u, void* out, int n_rhs, const int* mask,
               cudaStream_t s)
 {
+    if (c->exact) return launch_MT_exact(c, prec, u, out, n_rhs, mask, s);
     switch (c->L) {
-#define X(LL) case LL: return run_MT<LL>(c, prec, u, out, n_rhs, mask, s);
+#define X(LL) case LL: return run_MT<LL, false>(c, prec, u, out, n_rhs, mask, s);
         HOL_FOR_EACH_L(X)
 #undef X
     }
@@ -1518,8 +1221,9 @@ int launch_MT(const hol_ctx* c, int prec, const void* u, void* out, int n_rhs, c
 int launch_MT_resid64(const hol_ctx* c, const double* u, const double* b, double* out, int n_rhs,
                       const int* mask, cudaStream_t s)
 {
+    if (c->exact) return launch_MT_resid64_exact(c, u, b, out, n_rhs, mask, s);
     switch (c->L) {
-#define X(LL) case LL: return run_MT_resid<LL>(c, u, b, out, n_rhs, mask, s);
+#define X(LL) case LL: return run_MT_resid<LL, false>(c, u, b, out, n_rhs, mask, s);
         HOL_FOR_EACH_L(X)
 #undef X
     }
@@ -1530,6 +1234,9 @@ int launch_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* 
                     int n_rhs, const int* mask, const double* rr_new, const double* rr_old,
                     int rr_stride, int rr_n, int first, double* pq_part, cudaStream_t s)
 {
+    if (c->exact)
+        return launch_cg_mtm32_exact(c, r, pold, pnew, q, n_rhs, mask, rr_new, rr_old, rr_stride,
+                                     rr_n, first, pq_part, s);
     switch (c->L) {
 #define X(LL)                                                                                 \
     case LL:                                                                                  \

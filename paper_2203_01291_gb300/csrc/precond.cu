@@ -148,7 +148,59 @@ struct KpmArgs {
     int L, N, Th, max_np;
     int mode;         // bit 0: apply conj-coefficient series of A^T first; bit 1: then series of A
     double th;        // tanh(dtau t); dbar carries cosh^4 (see cb.cuh)
+    int ex;           // exact propagator exp(-dtau K) instead of the checkerboard
+    int D;            // exact: taps kept on each side
+    double e[kKinTaps];   // exact: ring factor taps
 };
+
+// v <- exp(-dtau K) v = (E (x) E) v on a complex slice in shared memory:
+// x direction into tmp, then y direction back into v.
+template <typename C2, typename R>
+__device__ __forceinline__ void kpm_exact(C2* v, C2* tmp, const KpmArgs& ka)
+{
+    const int L = ka.L, N = ka.N;
+    const R e0 = (R)ka.e[0];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int iy = i / L, ix = i - iy * L, row = iy * L;
+        const C2 a = v[i];
+        C2 o;
+        o.x = e0 * a.x;
+        o.y = e0 * a.y;
+        for (int d = 1; d <= ka.D; ++d) {
+            C2 u = v[row + (ix + d) % L];
+            if (2 * d != L) {
+                const C2 w = v[row + (ix + L - d) % L];
+                u.x += w.x;
+                u.y += w.y;
+            }
+            const R ed = (R)ka.e[d];
+            o.x = fma(ed, u.x, o.x);
+            o.y = fma(ed, u.y, o.y);
+        }
+        tmp[i] = o;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int iy = i / L, ix = i - iy * L;
+        const C2 a = tmp[i];
+        C2 o;
+        o.x = e0 * a.x;
+        o.y = e0 * a.y;
+        for (int d = 1; d <= ka.D; ++d) {
+            C2 u = tmp[((iy + d) % L) * L + ix];
+            if (2 * d != L) {
+                const C2 w = tmp[((iy + L - d) % L) * L + ix];
+                u.x += w.x;
+                u.y += w.y;
+            }
+            const R ed = (R)ka.e[d];
+            o.x = fma(ed, u.x, o.x);
+            o.y = fma(ed, u.y, o.y);
+        }
+        v[i] = o;
+    }
+    __syncthreads();
+}
 
 // In-place checkerboard colour (0: x-even, 1: x-odd, 2: y-even, 3: y-odd) on
 // a complex vector in shared memory; pairs are processed in parallel.
@@ -189,7 +241,8 @@ constexpr int kKpmMaxE = 8;   // elements per thread (N <= 8 * blockDim)
 // conjugated when conjc. u is in `cur` (shared) on entry; the result is left
 // in `cur` on exit. prev/acc/old are per-thread register arrays.
 template <typename R>
-__device__ void kpm_series(typename Cx<R>::T2* cur, const double* __restrict__ dbar,
+__device__ void kpm_series(typename Cx<R>::T2* cur, typename Cx<R>::T2* tmp,
+                           const double* __restrict__ dbar,
                            const double2* __restrict__ coef, int np, bool trans, bool conjc,
                            double a, double c0, const KpmArgs& ka)
 {
@@ -228,7 +281,9 @@ __device__ void kpm_series(typename Cx<R>::T2* cur, const double* __restrict__ d
             }
         }
         __syncthreads();
-        if (trans) {
+        if (ka.ex) {
+            kpm_exact<C2, R>(cur, tmp, ka);   // symmetric: same for Bop and its transpose
+        } else if (trans) {
             kpm_colour<C2, R>(cur, 3, ka.L, th);
             kpm_colour<C2, R>(cur, 2, ka.L, th);
             kpm_colour<C2, R>(cur, 1, ka.L, th);
@@ -300,12 +355,14 @@ __global__ void __launch_bounds__(256) k_kpm(const typename Cx<R>::T2* __restric
     const double db = bmax - bmin;
     const double a = 2.0 / db, c0 = -2.0 * bmin / db - 1.0;
     const int np = npv[w];
-    // this omega's coefficients in shared memory (read once per Chebyshev step)
-    double2* cw = reinterpret_cast<double2*>(cur + N);
+    // exact propagator: a second slice of scratch; then this omega's
+    // coefficients in shared memory (read once per Chebyshev step)
+    C2* tmp = cur + N;
+    double2* cw = reinterpret_cast<double2*>(cur + (ka.ex ? 2 * N : N));
     for (int m = threadIdx.x; m < np; m += blockDim.x) cw[m] = coef[(long)w * ka.max_np + m];
     __syncthreads();
-    if (ka.mode & 1) kpm_series<R>(cur, dbar, cw, np, true, true, a, c0, ka);
-    if (ka.mode & 2) kpm_series<R>(cur, dbar, cw, np, false, false, a, c0, ka);
+    if (ka.mode & 1) kpm_series<R>(cur, tmp, dbar, cw, np, true, true, a, c0, ka);
+    if (ka.mode & 2) kpm_series<R>(cur, tmp, dbar, cw, np, false, false, a, c0, ka);
     for (int i = threadIdx.x; i < N; i += blockDim.x) vout[off + i] = cur[i];
 }
 
@@ -676,9 +733,12 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     ka.max_np = c->kpm.max_np;
     ka.mode = mode;
     ka.th = c->th;
+    ka.ex = c->exact;
+    ka.D = c->exact ? (sizeof(R) == 8 ? c->kin_d64 : c->kin_d32) : 0;
+    for (int d = 0; d < kKinTaps; ++d) ka.e[d] = c->kin_e[d];
     bool done = false;
     if constexpr (sizeof(R) == 4) {
-        if (c->kpm_reg && (c->L == 32 || c->L == 16)) {
+        if (c->kpm_reg && !c->exact && (c->L == 32 || c->L == 16)) {
             const float th = (float)c->th;
             const size_t csm = (size_t)ka.max_np * sizeof(double2);
             if (c->L == 32) {
@@ -702,7 +762,8 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     }
     if (!done) {
         const int kt = kpm_threads(c);
-        const size_t ks = ((size_t)c->N * sizeof(C2) + 15) / 16 * 16 + (size_t)ka.max_np * sizeof(double2);
+        const size_t ks = ((size_t)c->N * sizeof(C2) * (c->exact ? 2 : 1) + 15) / 16 * 16 +
+                          (size_t)ka.max_np * sizeof(double2);
         if ((rc = set_smem_attr<R>((const void*)k_kpm<R>, ks))) return rc;
         k_kpm<R><<<ka.Th * n_rhs, kt, ks, s>>>(h0, h1, c->dbar, c->scal, c->kpm.np, c->kpm.coef,
                                                n_rhs, ka);

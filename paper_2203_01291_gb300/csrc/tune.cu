@@ -12,7 +12,8 @@
 // candidate is timed with CUDA events on the caller's stream (2 warm-up and
 // 10 timed launches on the context's scratch vectors) and the fastest is
 // kept in the context for every later call. Candidates whose per-unit
-// partial sums would not fit the context's partial-sum bank are skipped.
+// partial sums would not fit the context's partial-sum bank are skipped. A
+// context with the exact propagator has the scalar layout only.
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
@@ -81,7 +82,7 @@ extern "C" int hol_tune(hol_ctx* c, int n_rhs, int* best_k, int* best_warps, int
     if (merged) {
         vecs[nvec++] = c->mv_vec;
     } else {
-        if (c->L % 8 == 0) {
+        if (c->L % 8 == 0 && !c->exact) {   // the exact propagator runs in layout 0 only
             vecs[nvec++] = 6;
             if (c->L == 32) {
                 vecs[nvec++] = 5;

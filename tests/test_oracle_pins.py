@@ -65,6 +65,32 @@ def test_checkerboard_factors_spectrum_and_transpose():
     assert np.abs(D.kinetic_propagator(m).T - C1 @ C2 @ C3 @ C4).max() < 1e-14
 
 
+def test_exact_propagator_plane_waves():
+    """exp(-dtau K) acts on the plane wave e^{i k.r} as multiplication by
+    exp(2 dtau t (cos kx + cos ky)) (K = -t sum over nearest-neighbour bonds)."""
+    m = D.Model(L=6, Ltau=4, t=0.9, dtau=0.15, kinetic="exact")
+    C = D.kinetic_propagator(m)
+    L = m.L
+    ix, iy = np.meshgrid(np.arange(L), np.arange(L), indexing="xy")
+    for nx, ny in [(0, 0), (1, 0), (2, 3), (5, 1), (3, 3)]:
+        kx, ky = 2 * np.pi * nx / L, 2 * np.pi * ny / L
+        wave = np.exp(1j * (kx * ix + ky * iy)).reshape(-1)   # index ix + L*iy
+        lam = np.exp(2 * m.dtau * m.t * (np.cos(kx) + np.cos(ky)))
+        assert np.abs(C @ wave - lam * wave).max() < 1e-13
+
+
+@pytest.mark.parametrize("kinetic", ["checkerboard", "exact"])
+def test_blockwise_M_equals_dense_definition(kinetic):
+    """The block-by-block M and M^T used at large lattices are the dense
+    Eq. (M_def) matrix and its transpose (brute force on a small lattice)."""
+    m = D.Model(L=6, Ltau=5, alpha=1.1, mu=0.2, kinetic=kinetic)
+    x = rng(7).standard_normal((m.Ltau, m.N))
+    v = rng(8).standard_normal((m.Ltau, m.N))
+    Mx = D.fermion_matrix(m, x)
+    assert np.abs(D.M_apply_blocks(m, x, v).reshape(-1) - Mx @ v.reshape(-1)).max() < 1e-13
+    assert np.abs(D.MT_apply_blocks(m, x, v).reshape(-1) - Mx.T @ v.reshape(-1)).max() < 1e-13
+
+
 def test_free_fermion_checkerboard_close_to_exact():
     m = D.Model(L=8, Ltau=10)
     x = np.zeros((m.Ltau, m.N))
