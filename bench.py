@@ -489,6 +489,7 @@ def trajectory_leg(dev, n_traj=2):
             Rp = torch.tensor(hi.gaussian_vectors(w, 1, seed=400 + k)[0], device=dev)
             if k == 1:
                 torch.cuda.synchronize()
+                ctx.timer_enable(TIMER_STRIDE)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record()
@@ -499,9 +500,18 @@ def trajectory_leg(dev, n_traj=2):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / n_traj
+        # average launch durations of the solver's kernel classes (one launch in
+        # TIMER_STRIDE is bracketed by CUDA events on the launching stream)
+        avg_us = {}
+        for name, klass in (("cg_operator", hg.TIMER_OPERATOR), ("cg_update", hg.TIMER_UPDATE),
+                            ("precond", hg.TIMER_PRECOND), ("force", hg.TIMER_FORCE)):
+            cnt, tot, _ = ctx.timer_read(klass)
+            avg_us[name] = 1e3 * tot / cnt if cnt else None
+        ctx.timer_enable(0)
     return {"workload": "hmc16 L=16 Ltau=160, N_t=20 n_t=4 dt=0.01, PCG mixed",
             "trajectories_per_s": 1e3 / ms, "ms_per_trajectory": ms,
-            "accepted": int(sum(acc)), "of": n_traj, "mean_abs_dH": float(np.mean(np.abs(dhs)))}
+            "accepted": int(sum(acc)), "of": n_traj, "mean_abs_dH": float(np.mean(np.abs(dhs))),
+            "avg_launch_us": avg_us}
 
 
 def measurement_leg(dev, n_rv=128):

@@ -5,6 +5,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "cb.cuh"
 #include "internal.cuh"
 
@@ -156,6 +159,21 @@ int kpm_setup(hol_ctx* c, cudaStream_t s);   // precond.cu
 using namespace hol;
 
 extern "C" const char* hol_last_error(void) { return g_err; }
+
+namespace hol {
+int smem_raise(const void* fn, size_t bytes)
+{
+    if (bytes <= 32 * 1024) return HOL_OK;
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> limit;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = limit[fn];
+    if (bytes <= cur) return HOL_OK;
+    HOL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+    return HOL_OK;
+}
+}  // namespace hol
 
 // Modified Bessel function I_n(x) by its power series
 // sum_k (x/2)^(2k+n) / (k! (k+n)!) (all terms of one sign, no cancellation).

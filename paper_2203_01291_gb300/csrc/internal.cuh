@@ -32,6 +32,13 @@ int cuda_error(cudaError_t e, const char* what);
 
 void count_launch();
 
+// Raise the dynamic shared-memory limit of kernel `fn` to at least `bytes`
+// (a no-op up to 32 KB, which leaves room for static shared memory under the
+// default limit). The limit of a kernel only ever grows, under a lock, so
+// contexts of different shapes driven from several host threads never lower
+// it under one another's launches.
+int smem_raise(const void* fn, size_t bytes);
+
 // Programmatic dependent launch. A kernel launched with launch_pdl may be
 // scheduled while the previous kernel of its stream is still running; it
 // must call pdl_wait() before touching memory that kernel writes (the wait

@@ -149,7 +149,9 @@ __global__ void __launch_bounds__(1024) k_sb1(const double* __restrict__ x, int 
     }
 }
 
-constexpr int kFilterTS = 16;
+// Sites per tile of the tau filter: 16 on the largest lattice, 4 below it so
+// that small lattices still spread over many blocks.
+int filter_tile(const hol_ctx* c) { return c->N >= 1024 ? 16 : 4; }
 
 int grid_1d(long n)
 {
@@ -162,13 +164,12 @@ int filter(hol_ctx* c, const double* in, const double* base, double* out, double
 {
     const RadixPlan plan = plan_of(c->T);
     if (plan.n < 0) return set_error(HOL_EINVAL, "leapfrog: Ltau=%d has a prime factor > 7", c->T);
-    const size_t sm = 2 * (size_t)c->T * kFilterTS * sizeof(double2);
-    if (sm > 32 * 1024)   // leaves room for static shared memory under the default limit
-        HOL_CUDA(cudaFuncSetAttribute((const void*)k_tau_filter,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_tau_filter<<<ceil_div(c->N, kFilterTS), 256, sm, s>>>(in, base, out, coef,
-                                                             c->md_g + which * c->T, c->tw64,
-                                                             c->T, c->N, kFilterTS, plan);
+    const int ts = filter_tile(c);
+    const size_t sm = 2 * (size_t)c->T * ts * sizeof(double2);
+    if (int rc = smem_raise((const void*)k_tau_filter, sm)) return rc;
+    k_tau_filter<<<ceil_div(c->N, ts), 256, sm, s>>>(in, base, out, coef,
+                                                      c->md_g + which * c->T, c->tw64, c->T,
+                                                      c->N, ts, plan);
     HOL_CHECK_LAUNCH("k_tau_filter");
     return HOL_OK;
 }

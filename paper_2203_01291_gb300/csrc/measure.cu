@@ -233,9 +233,7 @@ struct Meas {
         const void* fns[] = {(const void*)k_m_tau_fwd, (const void*)k_m_tau_inv_half,
                              (const void*)k_m_tau_inv_full};
         for (const void* f : fns)
-            if (sm_t > 32 * 1024)   // leaves room for static shared memory
-                HOL_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)sm_t));
+            if (int rc = smem_raise(f, sm_t)) return rc;
         return HOL_OK;
     }
     // real vectors [nv][T][N] -> spectra [nv][nw][N] (tau then space)

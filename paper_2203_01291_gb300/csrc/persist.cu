@@ -203,9 +203,7 @@ int run_persist(const hol_ctx* c, PersistArgs a, int check_only, cudaStream_t s)
     int smem_max = 0;
     HOL_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     if (sm + 4096 > (size_t)smem_max) return HOL_EINVAL;   // does not fit: caller falls back
-    if (sm > 32 * 1024)   // leaves room for static shared memory
-        HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_persist<L>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (int rc = smem_raise((const void*)k_cg_persist<L>, sm)) return rc;
     int per_sm = 0, sms = 0;
     HOL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persist<L>, 32 * wpb, sm));
     HOL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));

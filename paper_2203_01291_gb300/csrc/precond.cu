@@ -667,12 +667,20 @@ __global__ void k_kpm_coeffs(const double* __restrict__ scal, int T, int max_np,
     }
 }
 
-int tile_sites(int prec) { return prec == HOL_F64 ? 16 : 32; }
+// Sites per tau-transform tile: 32 (FP32) / 16 (FP64) on the largest lattice;
+// 8 below it, so that a small lattice with few right-hand sides still spreads
+// over many blocks (N = 256 and 2 rhs: 64 blocks instead of 16).
+constexpr int kSmallTile = 8;
+int tile_sites(const hol_ctx* c, int prec)
+{
+    if (c->N < 1024) return kSmallTile;
+    return prec == HOL_F64 ? 16 : 32;
+}
 
 size_t fft_smem(const hol_ctx* c, int prec)
 {
     const size_t cs = prec == HOL_F64 ? sizeof(double2) : sizeof(float2);
-    return 2 * (size_t)c->T * tile_sites(prec) * cs;
+    return 2 * (size_t)c->T * tile_sites(c, prec) * cs;
 }
 
 int kpm_threads(const hol_ctx* c)
@@ -687,9 +695,7 @@ int kpm_threads(const hol_ctx* c)
 template <typename R>
 int set_smem_attr(const void* fn, size_t bytes)
 {
-    if (bytes > 32 * 1024)   // leaves room for static shared memory
-        HOL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    return HOL_OK;
+    return smem_raise(fn, bytes);
 }
 
 // fwd transform, KPM (mode), inverse transform (+ optional dot partials)
@@ -700,7 +706,7 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     using C2 = typename Cx<R>::T2;
     const int prec = sizeof(R) == 8 ? HOL_F64 : HOL_F32;
     const RadixPlan plan = plan_of(c->T);
-    const int TS = tile_sites(prec);
+    const int TS = tile_sites(c, prec);
     const size_t sm = fft_smem(c, prec);
     const dim3 gf(ceil_div(c->N, TS), n_rhs);
     const C2* w2 = reinterpret_cast<const C2*>(prec == HOL_F64 ? (const void*)c->tw64
@@ -709,18 +715,29 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     C2* h1 = reinterpret_cast<C2*>(c->cbuf1);
     int rc;
     // the configured lengths get transforms specialised at compile time
-    constexpr int TSW = sizeof(R) == 8 ? 16 : 32;   // tile_sites(prec)
+    constexpr int TSW = sizeof(R) == 8 ? 16 : 32;   // tile_sites on the largest lattice
     using FwdK = void (*)(const R*, C2*, const C2*, int, int, int, RadixPlan, R);
     using InvK = void (*)(const C2*, R*, const C2*, int, int, int, RadixPlan, R, const R*, double*);
     FwdK fwd = k_tau_fwd<R>;
     InvK inv = k_tau_inv<R>;
+#define HOL_TAU_CT(TT)                                    \
+    case TT:                                              \
+        if (TS == TSW) {                                  \
+            fwd = k_tau_fwd<R, TT, TSW>;                  \
+            inv = k_tau_inv<R, TT, TSW>;                  \
+        } else if (TS == kSmallTile) {                    \
+            fwd = k_tau_fwd<R, TT, kSmallTile>;           \
+            inv = k_tau_inv<R, TT, kSmallTile>;           \
+        }                                                 \
+        break;
     switch (c->T) {
-    case 40: fwd = k_tau_fwd<R, 40, TSW>; inv = k_tau_inv<R, 40, TSW>; break;
-    case 120: fwd = k_tau_fwd<R, 120, TSW>; inv = k_tau_inv<R, 120, TSW>; break;
-    case 160: fwd = k_tau_fwd<R, 160, TSW>; inv = k_tau_inv<R, 160, TSW>; break;
-    case 200: fwd = k_tau_fwd<R, 200, TSW>; inv = k_tau_inv<R, 200, TSW>; break;
+        HOL_TAU_CT(40)
+        HOL_TAU_CT(120)
+        HOL_TAU_CT(160)
+        HOL_TAU_CT(200)
     default: break;
     }
+#undef HOL_TAU_CT
     if ((rc = set_smem_attr<R>((const void*)fwd, sm))) return rc;
     if ((rc = set_smem_attr<R>((const void*)inv, sm))) return rc;
     const R isq = (R)(1.0 / sqrt((double)c->T));
@@ -776,7 +793,7 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
 
 }  // namespace
 
-int precond_tiles(const hol_ctx* c, int prec) { return ceil_div(c->N, tile_sites(prec)); }
+int precond_tiles(const hol_ctx* c, int prec) { return ceil_div(c->N, tile_sites(c, prec)); }
 
 int precond_check_shape(const hol_ctx* c)
 {
@@ -825,9 +842,7 @@ int precond_alloc(hol_ctx* c)
 int kpm_setup(hol_ctx* c, cudaStream_t s)
 {
     const size_t sm = 2 * (size_t)c->kpm.max_np * sizeof(double2);
-    if (sm > 32 * 1024)   // leaves room for static shared memory under the default limit
-        HOL_CUDA(cudaFuncSetAttribute((const void*)k_kpm_coeffs,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (int rc = smem_raise((const void*)k_kpm_coeffs, sm)) return rc;
     k_kpm_coeffs<<<c->T / 2, 128, sm, s>>>(c->scal, c->T, c->kpm.max_np, c->kpm.np, c->kpm.coef,
                                            c->kpm.np + c->T / 2);
     HOL_CHECK_LAUNCH("k_kpm_coeffs");
