@@ -470,7 +470,7 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
-def trajectory_leg(dev, n_traj=2):
+def trajectory_leg(dev, n_traj=2, options=()):
     """Algorithm 1 on the hmc16 workload: L=16, Ltau=160, alpha=1.5, omega0=1,
     x ~ N(0.5, 1), two pseudofermions, N_t=20, n_t=4, dt=0.01, m_reg=omega0,
     adiabatic preconditioner, mixed precision, force solves to 1e-5 and the
@@ -481,6 +481,7 @@ def trajectory_leg(dev, n_traj=2):
     o = hg.md_opts(0.01, 20, 4, w.omega0, force_tol=1e-5, action_tol=1e-10,
                    prec=hg.HOL_F32, precond=True)
     with hg.Context.from_workload(w, max_rhs=2) as ctx:
+        apply_options(ctx, options)
         x = torch.tensor(hi.phonon_field(w), device=dev)
         u = hi.uniforms(n_traj + 1, seed=77)
         acc, dhs = [], []
@@ -751,8 +752,9 @@ def run_precond(a):
     nr = a.rhs
     ctx = hg.Context.from_workload(w, max_rhs=nr)
     ctx.set_field(torch.tensor(hi.phonon_field(w), device="cuda"))
+    apply_options(ctx, a.option)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    res = {"mode": "precond", "rhs": nr}
+    res = {"mode": "precond", "rhs": nr, "options": list(a.option)}
     for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
         v = torch.tensor(hi.gaussian_vectors(w, nr, seed=5), device="cuda", dtype=dt)
         z = torch.empty_like(v)
@@ -813,7 +815,7 @@ def run_leg(a):
     from paper_2203_01291_gb300 import build as hb
     hb.build()
     torch.cuda.set_device(0)
-    legs = {"trajectory": lambda: trajectory_leg("cuda", n_traj=1),
+    legs = {"trajectory": lambda: trajectory_leg("cuda", n_traj=1, options=a.option),
             "measurement": lambda: measurement_leg("cuda", n_rv=32),
             "global": lambda: global_update_leg("cuda"),
             "chains": lambda: chains_leg("cuda")}

@@ -394,7 +394,11 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  *                       float4 with a cp.async ring across units (1-3 and 6
  *                       need L % 8 == 0), 4 / 5 split float4 with each slice
  *                       spread over 2 / 4 warps (L == 32)
- *   "kpm_registers"     register KPM kernel for FP32, L = 16 or 32 (0/1)
+ *   "kpm_registers"     FP32 KPM with the slice in registers, L = 16 or 32:
+ *                       0 off (shared-memory kernel), 1 four columns per
+ *                       lane, 2 two columns per lane (twice the warps per
+ *                       problem, half the work per lane on the chain of
+ *                       Bbar applies). Default 2 at L = 32, 1 otherwise
  *   "persistent_cg"     plain mixed CG chunks in one cooperative launch (0/1)
  *   "pdl"               programmatic dependent launch of the CG iteration
  *                       kernels: each may be scheduled while its predecessor

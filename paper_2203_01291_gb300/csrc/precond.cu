@@ -368,12 +368,16 @@ __global__ void __launch_bounds__(256) k_kpm(const typename Cx<R>::T2* __restric
 
 // ---------------------------------------------------------------- KPM, registers
 // FP32 KPM for L = 16 and 32 with the slice in registers. Lane (j, cx) of
-// warp w holds rows 2J, 2J+1 (J = w * PPW + j) and columns 4cx..4cx+3 of the
-// complex N-vector; x-bonds and in-warp y-bonds are shuffles, the colour-4
-// bond between the last row of one warp and the first row of the next goes
-// through shared memory (one barrier per Bbar apply, slots alternate).
+// warp w holds rows 2J, 2J+1 (J = w * PPW + j) and the CPL columns
+// CPL cx .. CPL cx + CPL - 1 (CPL = 4 or 2) of the complex N-vector; x-bonds
+// and in-warp y-bonds are register pairs or shuffles, the colour-4 bond
+// between the last row of one warp and the first row of the next goes through
+// shared memory (one barrier per Bbar apply, slots alternate). CPL = 2 spreads
+// a problem over twice the warps with half the work per lane on its chain of
+// dependent Bbar applies.
+template <int CPL>
 struct CV {
-    float4 re, im;
+    float re[CPL], im[CPL];
 };
 
 __device__ __forceinline__ void bond2(float& a, float& b, float th)
@@ -382,29 +386,10 @@ __device__ __forceinline__ void bond2(float& a, float& b, float th)
     a = fmaf(th, y, x);
     b = fmaf(th, x, y);
 }
-__device__ __forceinline__ void bond4(float4& a, float4& b, float th)
-{
-    bond2(a.x, b.x, th);
-    bond2(a.y, b.y, th);
-    bond2(a.z, b.z, th);
-    bond2(a.w, b.w, th);
-}
-__device__ __forceinline__ void addmul4(float4& a, const float4& b, float th)
-{
-    a.x = fmaf(th, b.x, a.x);
-    a.y = fmaf(th, b.y, a.y);
-    a.z = fmaf(th, b.z, a.z);
-    a.w = fmaf(th, b.w, a.w);
-}
-__device__ __forceinline__ float4 shf(const float4& v, int src)
-{
-    return make_float4(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src),
-                       __shfl_sync(kFull, v.z, src), __shfl_sync(kFull, v.w, src));
-}
 
-template <int L>
+template <int L, int CPL>
 struct KGeo {
-    static constexpr int LR = L / 4;          // lanes per row segment
+    static constexpr int LR = L / CPL;        // lanes per row segment
     static constexpr int PPW = 32 / LR;       // row pairs per warp
     static constexpr int W = L / (2 * PPW);   // warps per problem
     int lane, w, j, cx, right, left, down, up;
@@ -422,107 +407,144 @@ struct KGeo {
     __device__ __forceinline__ int row0() const { return 2 * (w * PPW + j); }
 };
 
-// colour 1 (x, even ix): inside the float4
-__device__ __forceinline__ void kc1(CV (&v)[2], float th)
+// colour 1 (x, even ix): column pairs inside the lane
+template <int CPL>
+__device__ __forceinline__ void kc1(CV<CPL> (&v)[2], float th)
 {
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        bond2(v[r].re.x, v[r].re.y, th);
-        bond2(v[r].re.z, v[r].re.w, th);
-        bond2(v[r].im.x, v[r].im.y, th);
-        bond2(v[r].im.z, v[r].im.w, th);
-    }
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int e = 0; e < CPL; e += 2) {
+            bond2(v[r].re[e], v[r].re[e + 1], th);
+            bond2(v[r].im[e], v[r].im[e + 1], th);
+        }
 }
-// colour 2 (x, odd ix): (.y,.z) inside, .w with right.x, .x with left.w
-template <int L>
-__device__ __forceinline__ void kc2(CV (&v)[2], const KGeo<L>& g, float th)
+// colour 2 (x, odd ix): inner pairs (1, 2), ..., the last column with the
+// right lane's first, the first with the left lane's last
+template <int L, int CPL>
+__device__ __forceinline__ void kc2(CV<CPL> (&v)[2], const KGeo<L, CPL>& g, float th)
 {
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const float rxr = __shfl_sync(kFull, v[r].re.x, g.right);
-        const float rxi = __shfl_sync(kFull, v[r].im.x, g.right);
-        const float lwr = __shfl_sync(kFull, v[r].re.w, g.left);
-        const float lwi = __shfl_sync(kFull, v[r].im.w, g.left);
-        bond2(v[r].re.y, v[r].re.z, th);
-        bond2(v[r].im.y, v[r].im.z, th);
-        v[r].re.w = fmaf(th, rxr, v[r].re.w);
-        v[r].im.w = fmaf(th, rxi, v[r].im.w);
-        v[r].re.x = fmaf(th, lwr, v[r].re.x);
-        v[r].im.x = fmaf(th, lwi, v[r].im.x);
+        const float rxr = __shfl_sync(kFull, v[r].re[0], g.right);
+        const float rxi = __shfl_sync(kFull, v[r].im[0], g.right);
+        const float lwr = __shfl_sync(kFull, v[r].re[CPL - 1], g.left);
+        const float lwi = __shfl_sync(kFull, v[r].im[CPL - 1], g.left);
+#pragma unroll
+        for (int e = 1; e + 1 < CPL; e += 2) {
+            bond2(v[r].re[e], v[r].re[e + 1], th);
+            bond2(v[r].im[e], v[r].im[e + 1], th);
+        }
+        v[r].re[CPL - 1] = fmaf(th, rxr, v[r].re[CPL - 1]);
+        v[r].im[CPL - 1] = fmaf(th, rxi, v[r].im[CPL - 1]);
+        v[r].re[0] = fmaf(th, lwr, v[r].re[0]);
+        v[r].im[0] = fmaf(th, lwi, v[r].im[0]);
     }
 }
 // colour 3 (y, even iy): rows 2J, 2J+1 of the same lane
-__device__ __forceinline__ void kc3(CV (&v)[2], float th)
+template <int CPL>
+__device__ __forceinline__ void kc3(CV<CPL> (&v)[2], float th)
 {
-    bond4(v[0].re, v[1].re, th);
-    bond4(v[0].im, v[1].im, th);
+#pragma unroll
+    for (int e = 0; e < CPL; ++e) {
+        bond2(v[0].re[e], v[1].re[e], th);
+        bond2(v[0].im[e], v[1].im[e], th);
+    }
 }
 // colour 4 (y, odd iy): row 2J+1 with row 2J+2 (next lane group / next warp)
-template <int L>
-__device__ __forceinline__ void kc4(CV (&v)[2], const KGeo<L>& g, float th, float4* xbuf, int par)
+template <int L, int CPL>
+__device__ __forceinline__ void kc4(CV<CPL> (&v)[2], const KGeo<L, CPL>& g, float th,
+                                    float* xbuf, int par)
 {
-    CV dn, upv;
-    dn.re = shf(v[0].re, g.down);
-    dn.im = shf(v[0].im, g.down);
-    upv.re = shf(v[1].re, g.up);
-    upv.im = shf(v[1].im, g.up);
-    if (KGeo<L>::W > 1) {
-        constexpr int LR = KGeo<L>::LR;
-        constexpr int PPW = KGeo<L>::PPW;
-        constexpr int W = KGeo<L>::W;
-        // slots: [par][w][0: first row of warp, 1: last row of warp][cx][re,im]
-        float4* sl = xbuf + par * (W * 2 * LR * 2);
+    CV<CPL> dn, upv;
+#pragma unroll
+    for (int e = 0; e < CPL; ++e) {
+        dn.re[e] = __shfl_sync(kFull, v[0].re[e], g.down);
+        dn.im[e] = __shfl_sync(kFull, v[0].im[e], g.down);
+        upv.re[e] = __shfl_sync(kFull, v[1].re[e], g.up);
+        upv.im[e] = __shfl_sync(kFull, v[1].im[e], g.up);
+    }
+    if constexpr (KGeo<L, CPL>::W > 1) {
+        constexpr int LR = KGeo<L, CPL>::LR;
+        constexpr int PPW = KGeo<L, CPL>::PPW;
+        constexpr int W = KGeo<L, CPL>::W;
+        // slot (par, warp, 0: first row of the warp / 1: last row, cx): CPL
+        // real parts then CPL imaginary parts
+        auto slot = [&](int wq, int which) {
+            return xbuf + ((((par * W + wq) * 2 + which) * LR + g.cx) * 2 * CPL);
+        };
         if (g.j == 0) {
-            sl[((g.w * 2 + 0) * LR + g.cx) * 2 + 0] = v[0].re;
-            sl[((g.w * 2 + 0) * LR + g.cx) * 2 + 1] = v[0].im;
+            float* sl = slot(g.w, 0);
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) {
+                sl[e] = v[0].re[e];
+                sl[CPL + e] = v[0].im[e];
+            }
         }
         if (g.j == PPW - 1) {
-            sl[((g.w * 2 + 1) * LR + g.cx) * 2 + 0] = v[1].re;
-            sl[((g.w * 2 + 1) * LR + g.cx) * 2 + 1] = v[1].im;
+            float* sl = slot(g.w, 1);
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) {
+                sl[e] = v[1].re[e];
+                sl[CPL + e] = v[1].im[e];
+            }
         }
         __syncthreads();
         if (g.j == PPW - 1) {
-            const int wn = (g.w + 1) % W;
-            dn.re = sl[((wn * 2 + 0) * LR + g.cx) * 2 + 0];
-            dn.im = sl[((wn * 2 + 0) * LR + g.cx) * 2 + 1];
+            const float* sl = slot((g.w + 1) % W, 0);
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) {
+                dn.re[e] = sl[e];
+                dn.im[e] = sl[CPL + e];
+            }
         }
         if (g.j == 0) {
-            const int wp = (g.w + W - 1) % W;
-            upv.re = sl[((wp * 2 + 1) * LR + g.cx) * 2 + 0];
-            upv.im = sl[((wp * 2 + 1) * LR + g.cx) * 2 + 1];
+            const float* sl = slot((g.w + W - 1) % W, 1);
+#pragma unroll
+            for (int e = 0; e < CPL; ++e) {
+                upv.re[e] = sl[e];
+                upv.im[e] = sl[CPL + e];
+            }
         }
     }
-    addmul4(v[1].re, dn.re, th);
-    addmul4(v[1].im, dn.im, th);
-    addmul4(v[0].re, upv.re, th);
-    addmul4(v[0].im, upv.im, th);
+#pragma unroll
+    for (int e = 0; e < CPL; ++e) {
+        v[1].re[e] = fmaf(th, dn.re[e], v[1].re[e]);
+        v[1].im[e] = fmaf(th, dn.im[e], v[1].im[e]);
+        v[0].re[e] = fmaf(th, upv.re[e], v[0].re[e]);
+        v[0].im[e] = fmaf(th, upv.im[e], v[0].im[e]);
+    }
 }
 
-template <int L>
-__global__ void __launch_bounds__(32 * (L / (2 * (32 / (L / 4)))))
+template <int L, int CPL>
+__global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
     k_kpm_reg(const float2* __restrict__ vin, float2* __restrict__ vout,
               const double* __restrict__ dbar, const double* __restrict__ scal,
               const int* __restrict__ npv, const double2* __restrict__ coef, int n_rhs, int Th,
               int max_np, int mode, float th)
 {
-    constexpr int N = L * L;
-    __shared__ float4 xbuf[2 * 2 * 4 * 8 * 2];
-    const KGeo<L> g;
+    using G = KGeo<L, CPL>;
+    __shared__ float xbuf[G::W > 1 ? 2 * G::W * 2 * G::LR * 2 * CPL : 1];
+    const G g;
     const int wq = blockIdx.x / n_rhs, rhs = blockIdx.x - wq * n_rhs;
-    const long off = ((long)rhs * Th + wq) * N;
+    const long off = ((long)rhs * Th + wq) * L * L;
     const int r0 = g.row0();
-    CV cur[2];
-    float4 d[2];
+    CV<CPL> cur[2];
+    float d[2][CPL];
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const long e = off + (long)(r0 + r) * L + 4 * g.cx;
-        const float4 a = *reinterpret_cast<const float4*>(vin + e);
-        const float4 b = *reinterpret_cast<const float4*>(vin + e + 2);
-        cur[r].re = make_float4(a.x, a.z, b.x, b.z);
-        cur[r].im = make_float4(a.y, a.w, b.y, b.w);
-        const int i = (r0 + r) * L + 4 * g.cx;
-        d[r] = make_float4((float)dbar[i], (float)dbar[i + 1], (float)dbar[i + 2],
-                           (float)dbar[i + 3]);
+        const long e = off + (long)(r0 + r) * L + CPL * g.cx;
+#pragma unroll
+        for (int q = 0; q < CPL; q += 2) {
+            const float4 a = *reinterpret_cast<const float4*>(vin + e + q);
+            cur[r].re[q] = a.x;
+            cur[r].im[q] = a.y;
+            cur[r].re[q + 1] = a.z;
+            cur[r].im[q + 1] = a.w;
+        }
+        const int i = (r0 + r) * L + CPL * g.cx;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) d[r][q] = (float)dbar[i + q];
     }
     const double bmin = scal[S_BMIN], bmax = scal[S_BMAX];
     const double db = bmax - bmin;
@@ -537,71 +559,66 @@ __global__ void __launch_bounds__(32 * (L / (2 * (32 / (L / 4)))))
         if (trans && !(mode & 1)) continue;
         if (!trans && !(mode & 2)) continue;
         const float sgn = trans ? -1.0f : 1.0f;    // conj coefficients for the transpose
-        CV acc[2], prev[2];
+        CV<CPL> acc[2], prev[2];
         {
             const double2 c = cw[0];
             const float cr = (float)c.x, ci = sgn * (float)c.y;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 prev[r] = cur[r];
-                acc[r].re = make_float4(cr * cur[r].re.x - ci * cur[r].im.x, cr * cur[r].re.y - ci * cur[r].im.y,
-                                        cr * cur[r].re.z - ci * cur[r].im.z, cr * cur[r].re.w - ci * cur[r].im.w);
-                acc[r].im = make_float4(cr * cur[r].im.x + ci * cur[r].re.x, cr * cur[r].im.y + ci * cur[r].re.y,
-                                        cr * cur[r].im.z + ci * cur[r].re.z, cr * cur[r].im.w + ci * cur[r].re.w);
+#pragma unroll
+                for (int e = 0; e < CPL; ++e) {
+                    acc[r].re[e] = cr * cur[r].re[e] - ci * cur[r].im[e];
+                    acc[r].im[e] = cr * cur[r].im[e] + ci * cur[r].re[e];
+                }
             }
         }
         for (int m = 1; m < np; ++m) {
-            CV old[2], b[2];
+            CV<CPL> old[2], b[2];
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 old[r] = cur[r];
                 b[r] = cur[r];
                 if (trans) {
-                    b[r].re.x *= d[r].x; b[r].re.y *= d[r].y; b[r].re.z *= d[r].z; b[r].re.w *= d[r].w;
-                    b[r].im.x *= d[r].x; b[r].im.y *= d[r].y; b[r].im.z *= d[r].z; b[r].im.w *= d[r].w;
+#pragma unroll
+                    for (int e = 0; e < CPL; ++e) {
+                        b[r].re[e] *= d[r][e];
+                        b[r].im[e] *= d[r][e];
+                    }
                 }
             }
             if (trans) {
-                kc4<L>(b, g, th, xbuf, par);
-                kc3(b, th);
-                kc2<L>(b, g, th);
-                kc1(b, th);
+                kc4<L, CPL>(b, g, th, xbuf, par);
+                kc3<CPL>(b, th);
+                kc2<L, CPL>(b, g, th);
+                kc1<CPL>(b, th);
             } else {
-                kc1(b, th);
-                kc2<L>(b, g, th);
-                kc3(b, th);
-                kc4<L>(b, g, th, xbuf, par);
+                kc1<CPL>(b, th);
+                kc2<L, CPL>(b, g, th);
+                kc3<CPL>(b, th);
+                kc4<L, CPL>(b, g, th, xbuf, par);
             }
             par ^= 1;
             const double2 c = cw[m];
             const float cr = (float)c.x, ci = sgn * (float)c.y;
+            // alpha_m = (m == 1 ? 1 : 2) (a B + c0) alpha_{m-1} - (m == 1 ? 0 : alpha_{m-2})
+            const float f2 = (m == 1) ? 1.0f : 2.0f;
+            const float pm = (m == 1) ? 0.0f : 1.0f;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
-                if (!trans) {
-                    b[r].re.x *= d[r].x; b[r].re.y *= d[r].y; b[r].re.z *= d[r].z; b[r].re.w *= d[r].w;
-                    b[r].im.x *= d[r].x; b[r].im.y *= d[r].y; b[r].im.z *= d[r].z; b[r].im.w *= d[r].w;
-                }
-                // alpha_m = (m == 1 ? 1 : 2) (a B + c0) alpha_{m-1} - (m == 1 ? 0 : alpha_{m-2})
-                const float f2 = (m == 1) ? 1.0f : 2.0f;
-                const float pm = (m == 1) ? 0.0f : 1.0f;
-                float* nre = &cur[r].re.x;
-                float* nim = &cur[r].im.x;
-                const float* bre = &b[r].re.x;
-                const float* bim = &b[r].im.x;
-                const float* ore = &old[r].re.x;
-                const float* oim = &old[r].im.x;
-                const float* pre = &prev[r].re.x;
-                const float* pim = &prev[r].im.x;
-                float* are = &acc[r].re.x;
-                float* aim = &acc[r].im.x;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float xr = f2 * fmaf(a, bre[e], c0 * ore[e]) - pm * pre[e];
-                    const float xi = f2 * fmaf(a, bim[e], c0 * oim[e]) - pm * pim[e];
-                    nre[e] = xr;
-                    nim[e] = xi;
-                    are[e] = fmaf(cr, xr, fmaf(-ci, xi, are[e]));
-                    aim[e] = fmaf(cr, xi, fmaf(ci, xr, aim[e]));
+                for (int e = 0; e < CPL; ++e) {
+                    float br = b[r].re[e], bi = b[r].im[e];
+                    if (!trans) {
+                        br *= d[r][e];
+                        bi *= d[r][e];
+                    }
+                    const float xr = f2 * fmaf(a, br, c0 * old[r].re[e]) - pm * prev[r].re[e];
+                    const float xi = f2 * fmaf(a, bi, c0 * old[r].im[e]) - pm * prev[r].im[e];
+                    cur[r].re[e] = xr;
+                    cur[r].im[e] = xi;
+                    acc[r].re[e] = fmaf(cr, xr, fmaf(-ci, xi, acc[r].re[e]));
+                    acc[r].im[e] = fmaf(cr, xi, fmaf(ci, xr, acc[r].im[e]));
                 }
                 prev[r] = old[r];
             }
@@ -611,9 +628,11 @@ __global__ void __launch_bounds__(32 * (L / (2 * (32 / (L / 4)))))
     }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const long e = off + (long)(r0 + r) * L + 4 * g.cx;
-        *reinterpret_cast<float4*>(vout + e) = make_float4(cur[r].re.x, cur[r].im.x, cur[r].re.y, cur[r].im.y);
-        *reinterpret_cast<float4*>(vout + e + 2) = make_float4(cur[r].re.z, cur[r].im.z, cur[r].re.w, cur[r].im.w);
+        const long e = off + (long)(r0 + r) * L + CPL * g.cx;
+#pragma unroll
+        for (int q = 0; q < CPL; q += 2)
+            *reinterpret_cast<float4*>(vout + e + q) =
+                make_float4(cur[r].re[q], cur[r].im[q], cur[r].re[q + 1], cur[r].im[q + 1]);
     }
 }
 
@@ -758,21 +777,23 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
         if (c->kpm_reg && !c->exact && (c->L == 32 || c->L == 16)) {
             const float th = (float)c->th;
             const size_t csm = (size_t)ka.max_np * sizeof(double2);
-            if (c->L == 32) {
-                if ((rc = set_smem_attr<R>((const void*)k_kpm_reg<32>, csm))) return rc;
-            } else if ((rc = set_smem_attr<R>((const void*)k_kpm_reg<16>, csm))) {
-                return rc;
-            }
             const float2* i2 = reinterpret_cast<const float2*>(h0);
             float2* o2 = reinterpret_cast<float2*>(h1);
+            auto run = [&](auto kern, int threads) -> int {
+                if (int e = set_smem_attr<R>((const void*)kern, csm)) return e;
+                kern<<<ka.Th * n_rhs, threads, csm, s>>>(i2, o2, c->dbar, c->scal, c->kpm.np,
+                                                         c->kpm.coef, n_rhs, ka.Th, ka.max_np,
+                                                         mode, th);
+                return HOL_OK;
+            };
+            const bool two = c->kpm_reg == 2;   // two columns per lane
             if (c->L == 32)
-                k_kpm_reg<32><<<ka.Th * n_rhs, 128, csm, s>>>(i2, o2, c->dbar, c->scal, c->kpm.np,
-                                                             c->kpm.coef, n_rhs, ka.Th, ka.max_np,
-                                                             mode, th);
+                rc = two ? run(k_kpm_reg<32, 2>, 32 * KGeo<32, 2>::W)
+                         : run(k_kpm_reg<32, 4>, 32 * KGeo<32, 4>::W);
             else
-                k_kpm_reg<16><<<ka.Th * n_rhs, 32, csm, s>>>(i2, o2, c->dbar, c->scal, c->kpm.np,
-                                                            c->kpm.coef, n_rhs, ka.Th, ka.max_np,
-                                                            mode, th);
+                rc = two ? run(k_kpm_reg<16, 2>, 32 * KGeo<16, 2>::W)
+                         : run(k_kpm_reg<16, 4>, 32 * KGeo<16, 4>::W);
+            if (rc) return rc;
             HOL_CHECK_LAUNCH("k_kpm_reg");
             done = true;
         }

@@ -63,6 +63,24 @@ def test_precond_apply_vs_oracle(L, T):
                 assert _rel(out.cpu().double().numpy(), ref) < tol, (which, dt)
 
 
+@pytest.mark.parametrize("kpm", [0, 1, 2])
+@pytest.mark.parametrize("L,T", [(16, 20), (32, 12), (16, 40)])
+def test_precond_fp32_kpm_variants(kpm, L, T):
+    """The FP32 KPM kernels (shared-memory, registers with four or two
+    columns per lane) all match the oracle's step-by-step KPM."""
+    w, x, ctx = _setup(L, T, seed=4)
+    m = D.model_of(w)
+    v = hi.gaussian_vectors(w, 2, seed=10)
+    ref = np.stack(
+        [D.precond_inverse_apply(m, x, D.precond_inverse_apply(m, x, a, trans=True)) for a in v])
+    with ctx:
+        ctx.set_option("kpm_registers", kpm)
+        vt = torch.tensor(v, device=DEV, dtype=torch.float32)
+        out = torch.empty_like(vt)
+        ctx.precond_apply(hg.HOL_PINV_PINVT, vt, out)
+        assert _rel(out.cpu().double().numpy(), ref) < 2e-5
+
+
 def test_precond_transpose_identity_and_spd():
     """<w, P^{-1} v> = <P^{-T} w, v> and <v, P^{-1} P^{-T} v> > 0 on the GPU."""
     w_, x, ctx = _setup(8, 40, std=1.5)
