@@ -122,6 +122,12 @@ def gaussian_vectors(w: Workload, count: int, seed: int) -> np.ndarray:
         g.standard_normal((count, w.Ltau, w.N)), dtype=np.float64)
 
 
+def site_vector(w: Workload, seed: int) -> np.ndarray:
+    """v[i] ~ N(0, 1), i.i.d. over the N sites of one slice (a random start
+    vector for the Arnoldi process)."""
+    return np.ascontiguousarray(_rng(seed).standard_normal(w.N), dtype=np.float64)
+
+
 def z2_vectors(w: Workload, count: int, seed: int) -> np.ndarray:
     """xi[k][tau][i] uniform in {-1, +1}, i.i.d. (stochastic probes)."""
     g = _rng(seed)

@@ -370,6 +370,30 @@ int fermion_matvec_static(const hol_params* p, const double* x, int op, const do
                           double* out, int n_rhs, void* stream);
 
 /*
+ * Arnoldi estimate of the spectral bounds of Bbar = exp(-dtau Vbar) C (App. C
+ * D): m steps (1 <= m <= 32, m <= N) of the Arnoldi process (modified
+ * Gram-Schmidt, FP64) on Bbar for the field of the last hol_set_field, from
+ * the start vector v0 (device, N doubles, any nonzero vector; the paper
+ * starts from a random one), then the eigenvalues of the Hessenberg matrix
+ * (shifted QR on the host). bmin = (1 - margin) min |Ritz value|, bmax =
+ * (1 + margin) max |Ritz value| (host outputs, nullable; the paper uses about
+ * twenty steps and a 5 % margin, margin in [0, 1)). steps (host, nullable)
+ * receives the steps done (fewer than m when an invariant subspace is found).
+ * install != 0 replaces the context's bounds (the deterministic norm bounds
+ * hol_set_field computes) by these and recomputes the Chebyshev orders N_P
+ * and coefficients, for every later precond_apply and preconditioned
+ * cg_solve until the next hol_set_field. Returns HOL_ENUMERIC if the QR
+ * iteration fails. Synchronises `stream`.
+ */
+int hol_arnoldi_bounds(hol_ctx* ctx, const double* v0, int m, double margin, int install,
+                       double* bmin, double* bmax, int* steps, void* stream);
+
+/* The spectral bounds of Bbar the preconditioner currently uses (host
+ * outputs): the deterministic norm bounds of hol_set_field, or those
+ * installed by hol_arnoldi_bounds. Synchronises `stream`. */
+int hol_get_bounds(hol_ctx* ctx, double* bmin, double* bmax, void* stream);
+
+/*
  * Launch-shape autotuner (no counterpart in the paper). Times the fused FP32
  * M^T M kernel of the CG iteration for n_rhs right-hand sides over its launch
  * candidates (tau slices per lane group, warps per block, vector or scalar

@@ -547,9 +547,44 @@ def chebyshev_coeffs(phi: float, bmin: float, bmax: float, NP: int, NQ: int | No
     return c
 
 
-def kpm_plan(m: Model, x, a1=1.0, a2=1.0):
-    """Per omega < T/2: (N_P, c_m); the mirrored half uses conj (App. C B)."""
-    bmin, bmax = spectral_bounds(m, x)
+def arnoldi_bounds(m: Model, x, v0, steps: int = 20, margin: float = 0.05):
+    """Spectral bounds of Bbar by the Arnoldi process (App. C D): `steps` steps
+    of Arnoldi on Bbar from v0 (modified Gram-Schmidt, each vector
+    orthogonalised twice so the basis stays orthonormal), the eigenvalues of the
+    square Hessenberg matrix (Ritz values, numpy's eigvals), and
+    ((1 - margin) min |ritz|, (1 + margin) max |ritz|). Stops early on an
+    invariant subspace (new vector below 1e-12 of |Bbar v_j|).
+    Returns (bmin, bmax, H, V, k) with k the steps done, H [k+1][k], V [k+1][N]."""
+    B = Bbar(m, x)
+    N = m.N
+    V = np.zeros((steps + 1, N))
+    H = np.zeros((steps + 1, steps))
+    v0 = np.asarray(v0, dtype=np.float64).reshape(N)
+    V[0] = v0 / np.linalg.norm(v0)
+    k = steps
+    for j in range(steps):
+        w = B @ V[j]
+        wn0 = np.linalg.norm(w)
+        for _ in range(2):               # Gram-Schmidt twice keeps V orthonormal
+            for i in range(j + 1):
+                c = V[i] @ w
+                H[i, j] += c
+                w = w - c * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        if not H[j + 1, j] > 1e-12 * wn0:
+            k = j + 1
+            break
+        V[j + 1] = w / H[j + 1, j]
+    ritz = np.linalg.eigvals(H[:k, :k])
+    mod = np.abs(ritz)
+    return (float((1.0 - margin) * mod.min()), float((1.0 + margin) * mod.max()),
+            H[:k + 1, :k], V[:k + 1], k)
+
+
+def kpm_plan(m: Model, x, a1=1.0, a2=1.0, bounds=None):
+    """Per omega < T/2: (N_P, c_m); the mirrored half uses conj (App. C B).
+    bounds: (bmin, bmax) to use instead of the deterministic spectral_bounds."""
+    bmin, bmax = spectral_bounds(m, x) if bounds is None else bounds
     T = m.Ltau
     plan = []
     for w in range(T // 2):
@@ -575,12 +610,12 @@ def kpm_block_apply(Amat: np.ndarray, coeffs, u: np.ndarray) -> np.ndarray:
     return acc
 
 
-def precond_inverse_apply(m: Model, x, v, trans: bool = False, a1=1.0, a2=1.0):
+def precond_inverse_apply(m: Model, x, v, trans: bool = False, a1=1.0, a2=1.0, bounds=None):
     """KPM approximation of P^{-1} v = U^dag Ptilde^{-1} U v (Eq. (P_change_basis), App. C D);
     with trans=True the exact transpose of that approximation,
-    U^dag diag(sum conj(c_m) T_m(A^T)) U v."""
+    U^dag diag(sum conj(c_m) T_m(A^T)) U v. bounds as in kpm_plan."""
     N, T = m.N, m.Ltau
-    bmin, bmax, plan = kpm_plan(m, x, a1, a2)
+    bmin, bmax, plan = kpm_plan(m, x, a1, a2, bounds)
     db = bmax - bmin
     Bb = Bbar(m, x)
     if trans:

@@ -35,7 +35,8 @@ __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F6
            "fourier_accel_leapfrog", "hol_md_opts", "stochastic_measure", "hol_tune",
            "hmc_batch", "measure_batch", "hol_set_option", "hol_get_option", "hol_fma_peak",
            "global_update", "HOL_REFLECT", "HOL_SWAP", "measure_observables",
-           "HOL_KINETIC_CHECKERBOARD", "HOL_KINETIC_EXACT",
+           "HOL_KINETIC_CHECKERBOARD", "HOL_KINETIC_EXACT", "hol_arnoldi_bounds",
+           "hol_get_bounds",
            "library_path", "load"]
 
 
@@ -214,6 +215,21 @@ def hol_tune(handle, n_rhs: int) -> dict:
                            ctypes.byref(ms), _stream()))
     return {"slices_per_group": k.value, "warps_per_block": w.value, "float4_layout": v.value,
             "ms": ms.value}
+
+
+def hol_arnoldi_bounds(handle, v0: torch.Tensor, N: int, m: int = 20, margin: float = 0.05,
+                       install: bool = False) -> dict:
+    lo, hi, st = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(load().hol_arnoldi_bounds(handle, _ptr(v0, torch.float64, N, "v0"), m, margin,
+                                     int(bool(install)), ctypes.byref(lo), ctypes.byref(hi),
+                                     ctypes.byref(st), _stream()))
+    return {"bmin": lo.value, "bmax": hi.value, "steps": st.value}
+
+
+def hol_get_bounds(handle) -> tuple:
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(load().hol_get_bounds(handle, ctypes.byref(lo), ctypes.byref(hi), _stream()))
+    return lo.value, hi.value
 
 
 def _ptrs(ts, dtype=torch.float64):
@@ -405,6 +421,16 @@ class Context:
     def get_option(self, name: str) -> int:
         """Current value of a launch option (hol_get_option)."""
         return hol_get_option(self._h, name)
+
+    def arnoldi_bounds(self, v0: torch.Tensor, m: int = 20, margin: float = 0.05,
+                       install: bool = False) -> dict:
+        """Spectral bounds of Bbar by m Arnoldi steps from v0 (hol_arnoldi_bounds);
+        install=True makes the preconditioner use them until the next set_field."""
+        return hol_arnoldi_bounds(self._h, v0, self.N, m, margin, install)
+
+    def bounds(self) -> tuple:
+        """(bmin, bmax) the preconditioner currently uses (hol_get_bounds)."""
+        return hol_get_bounds(self._h)
 
     def tune(self, n_rhs: int) -> dict:
         """Pick the fastest launch shape of the fused M^T M for n_rhs (needs a field)."""

@@ -87,6 +87,9 @@ SIGNATURES = {
                            ctypes.POINTER(_VP), _I, _I]),
     "hol_set_option": (_I, [_VP, ctypes.c_char_p, _I]),
     "hol_get_option": (_I, [_VP, ctypes.c_char_p, ctypes.POINTER(_I)]),
+    "hol_arnoldi_bounds": (_I, [_VP, _VP, _I, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                ctypes.POINTER(_I), _VP]),
+    "hol_get_bounds": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D), _VP]),
     "hol_tune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                       ctypes.POINTER(_D), _VP]),
     "hol_launch_count": (ctypes.c_ulonglong, []),

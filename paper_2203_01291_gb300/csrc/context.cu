@@ -141,7 +141,7 @@ void free_ctx(hol_ctx* c)
                    c->mask, c->kpm.np, c->kpm.coef, c->cbuf0, c->cbuf1, c->v64f,
                    c->tw64, c->tw32, c->md_phi, c->md_b, c->md_v, c->md_F, c->md_p,
                    c->md_x0, c->md_g, c->md_s, c->ms_acc, c->twL64, c->v32g, c->v32h,
-                   c->v32i, c->cgs, c->alpha_buf};
+                   c->v32i, c->cgs, c->alpha_buf, c->arn};
     for (void* p : dev)
         if (p) cudaFree(p);
     timer_free(c->timer);
@@ -314,6 +314,8 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     ALLOC(c->v64f, R * n * sizeof(double));
     ALLOC(c->mask, 2 * R * sizeof(int));
     ALLOC(c->alpha_buf, R * sizeof(double));
+    ALLOC(c->arn, ((size_t)(kArnoldiMax + 1) * c->N + (kArnoldiMax + 1) * kArnoldiMax + 1) *
+                      sizeof(double));
     ALLOC(c->cbuf0, c->cbuf_len * sizeof(double2));
     ALLOC(c->cbuf1, c->cbuf_len * sizeof(double2));
 #undef ALLOC

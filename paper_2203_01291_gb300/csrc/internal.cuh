@@ -81,6 +81,8 @@ void timer_stop(const hol_ctx* c, int k, cudaStream_t s);
 
 // Largest supported lattice side (one lane per column, L values per lane).
 constexpr int kMaxL = 32;
+// Most Arnoldi steps of hol_arnoldi_bounds.
+constexpr int kArnoldiMax = 32;
 // Blocks per right-hand side of the element-wise CG kernels (fixed, so the
 // partial-sum banks have a fixed stride).
 constexpr int kRedStride = 256;
@@ -148,6 +150,8 @@ struct hol_ctx {
     float* v32i;
     double* cgs;         // merged CG scalars [2][max_rhs][4]: alpha, gamma, mode
     double* alpha_buf;   // CG: alpha of an iteration whose x update is deferred [max_rhs]
+    double* arn;         // Arnoldi: basis [kArnoldiMax + 1][N], H [kArnoldiMax + 1][kArnoldiMax],
+                         // then one slot for the step count
     double2* tw64;       // [2T] exp(-i pi k / T)
     float2* tw32;
     double* md_phi;      // leapfrog: Phi [max_rhs][T][N]
