@@ -372,13 +372,16 @@ int fermion_matvec_static(const hol_params* p, const double* x, int op, const do
 /*
  * Arnoldi estimate of the spectral bounds of Bbar = exp(-dtau Vbar) C (App. C
  * D): m steps (1 <= m <= 32, m <= N) of the Arnoldi process (modified
- * Gram-Schmidt, FP64) on Bbar for the field of the last hol_set_field, from
- * the start vector v0 (device, N doubles, any nonzero vector; the paper
- * starts from a random one), then the eigenvalues of the Hessenberg matrix
- * (shifted QR on the host). bmin = (1 - margin) min |Ritz value|, bmax =
- * (1 + margin) max |Ritz value| (host outputs, nullable; the paper uses about
- * twenty steps and a 5 % margin, margin in [0, 1)). steps (host, nullable)
- * receives the steps done (fewer than m when an invariant subspace is found).
+ * Gram-Schmidt applied twice per step, FP64) for the field of the last
+ * hol_set_field, from the start vector v0 (device, N doubles, any nonzero
+ * vector; the paper starts from a random one), on Bbar and on
+ * Bbar^{-1} = C^{-1} exp(dtau Vbar); Ritz values are the eigenvalues of the
+ * Hessenberg matrices (shifted QR on the host). bmax = (1 + margin) times the
+ * largest Ritz modulus of Bbar, bmin = 1 / ((1 + margin) times the largest
+ * Ritz modulus of Bbar^{-1}) (host outputs, nullable; the paper uses about
+ * twenty steps and a 5 % margin; margin in [0, 1)). steps (host, nullable)
+ * receives the fewer of the two runs' steps (fewer than m when an invariant
+ * subspace is found).
  * install != 0 replaces the context's bounds (the deterministic norm bounds
  * hol_set_field computes) by these and recomputes the Chebyshev orders N_P
  * and coefficients, for every later precond_apply and preconditioned

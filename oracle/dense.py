@@ -547,25 +547,21 @@ def chebyshev_coeffs(phi: float, bmin: float, bmax: float, NP: int, NQ: int | No
     return c
 
 
-def arnoldi_bounds(m: Model, x, v0, steps: int = 20, margin: float = 0.05):
-    """Spectral bounds of Bbar by the Arnoldi process (App. C D): `steps` steps
-    of Arnoldi on Bbar from v0 (modified Gram-Schmidt, each vector
-    orthogonalised twice so the basis stays orthonormal), the eigenvalues of the
-    square Hessenberg matrix (Ritz values, numpy's eigvals), and
-    ((1 - margin) min |ritz|, (1 + margin) max |ritz|). Stops early on an
-    invariant subspace (new vector below 1e-12 of |Bbar v_j|).
-    Returns (bmin, bmax, H, V, k) with k the steps done, H [k+1][k], V [k+1][N]."""
-    B = Bbar(m, x)
-    N = m.N
+def arnoldi(A: np.ndarray, v0, steps: int):
+    """`steps` steps of the Arnoldi process on the dense matrix A from v0
+    (modified Gram-Schmidt, each new vector orthogonalised twice so the basis
+    stays orthonormal); stops early on an invariant subspace (new vector
+    below 1e-12 of |A v_j|). Returns (H [k+1][k], V [k+1][N], k)."""
+    N = A.shape[0]
     V = np.zeros((steps + 1, N))
     H = np.zeros((steps + 1, steps))
     v0 = np.asarray(v0, dtype=np.float64).reshape(N)
     V[0] = v0 / np.linalg.norm(v0)
     k = steps
     for j in range(steps):
-        w = B @ V[j]
+        w = A @ V[j]
         wn0 = np.linalg.norm(w)
-        for _ in range(2):               # Gram-Schmidt twice keeps V orthonormal
+        for _ in range(2):
             for i in range(j + 1):
                 c = V[i] @ w
                 H[i, j] += c
@@ -575,10 +571,23 @@ def arnoldi_bounds(m: Model, x, v0, steps: int = 20, margin: float = 0.05):
             k = j + 1
             break
         V[j + 1] = w / H[j + 1, j]
-    ritz = np.linalg.eigvals(H[:k, :k])
-    mod = np.abs(ritz)
-    return (float((1.0 - margin) * mod.min()), float((1.0 + margin) * mod.max()),
-            H[:k + 1, :k], V[:k + 1], k)
+    return H[:k + 1, :k], V[:k + 1], k
+
+
+def arnoldi_bounds(m: Model, x, v0, steps: int = 20, margin: float = 0.05):
+    """Spectral bounds of Bbar as App. C D estimates them: bmax from `steps`
+    Arnoldi steps on Bbar (largest Ritz modulus, increased by the margin),
+    bmin from the same on Bbar^{-1} = exp(dtau K) exp(dtau Vbar) (the inverse
+    of its largest Ritz modulus increased by the margin). Ritz values are
+    numpy's eigvals of the square Hessenberg matrix.
+    Returns (bmin, bmax, runs) with runs = {"B": (H, V, k), "Binv": (H, V, k)}."""
+    B = Bbar(m, x)
+    Binv = np.linalg.inv(kinetic_propagator(m)) / dbar(m, x)[None, :]
+    runs = {"B": arnoldi(B, v0, steps), "Binv": arnoldi(Binv, v0, steps)}
+    top = {}
+    for key, (H, _, k) in runs.items():
+        top[key] = float(np.abs(np.linalg.eigvals(H[:k, :k])).max())
+    return 1.0 / ((1.0 + margin) * top["Binv"]), (1.0 + margin) * top["B"], runs
 
 
 def kpm_plan(m: Model, x, a1=1.0, a2=1.0, bounds=None):

@@ -1,10 +1,13 @@
 // Arnoldi estimate of the spectral bounds of Bbar = exp(-dtau Vbar) C
-// (App. C D): m steps of the Arnoldi process on Bbar from a caller-given
-// start vector, the eigenvalues (Ritz values) of the m x m Hessenberg matrix
-// on the host, and bounds widened by a relative margin. The paper runs about
-// twenty steps from a random start and widens by 5 %. Optionally installs
-// the bounds in the context (Chebyshev orders and coefficients recomputed),
-// in place of the deterministic norm bounds that hol_set_field sets.
+// (App. C D): m steps of the Arnoldi process from a caller-given start
+// vector on Bbar, whose largest Ritz modulus (eigenvalue of the m x m
+// Hessenberg matrix, on the host) increased by a margin gives bmax, and on
+// Bbar^{-1} = C^{-1} exp(dtau Vbar), whose largest Ritz modulus increased by
+// the margin gives 1 / bmin (the paper's way to reach the small end stably).
+// The paper runs about twenty steps from a random start with a 5 % margin.
+// Optionally installs the bounds in the context (Chebyshev orders and
+// coefficients recomputed), in place of the deterministic norm bounds that
+// hol_set_field sets.
 //
 // The process runs in one block: Bbar v is the propagator (checkerboard
 // colours or the exact separable taps) on a slice in shared memory followed
@@ -25,9 +28,11 @@ namespace {
 
 struct ArnArgs {
     int N, L, m;
+    int inv;                  // 0: Bbar, 1: Bbar^{-1}
     int ex, D;                // exact propagator and its taps
-    double th;                // checkerboard bond tanh(dtau t)
-    double e[kKinTaps];
+    double th;                // checkerboard bond tanh(dtau t) (negated for the inverse)
+    double scale;             // inverse checkerboard: (1 - th^2)^-4, else 1
+    double e[kKinTaps];       // exact taps (sign-alternated for the inverse)
 };
 
 // Fixed-order block sum, the same value in every thread.
@@ -118,14 +123,22 @@ __global__ void __launch_bounds__(256) k_arnoldi(const double* __restrict__ v0,
         const double* vj = V + (long)j * N;
         for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] = vj[i];
         __syncthreads();
+        if (a.inv) {   // Bbar^{-1} v = C^{-1} (v / dbar)
+            for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] /= dbar[i];
+            __syncthreads();
+        }
         if (a.ex) {
-            arn_exact(w, tmp, a);
+            arn_exact(w, tmp, a);   // the inverse is exp(-dtau t A) per direction: taps (-1)^d e[d]
+        } else if (a.inv) {
+            // C^{-1} = C1^{-1} C2^{-1} C3^{-1} C4^{-1}; [[1, th], [th, 1]]^{-1} is
+            // [[1, -th], [-th, 1]] / (1 - th^2), and every site is in one bond per colour
+            for (int c = 3; c >= 0; --c) arn_colour(w, c, a.L, a.th);
         } else {
             for (int c = 0; c < 4; ++c) arn_colour(w, c, a.L, a.th);   // C4 C3 C2 C1
         }
         double q0 = 0.0;
         for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            w[i] *= dbar[i];
+            w[i] *= a.inv ? a.scale : dbar[i];
             q0 += w[i] * w[i];
         }
         const double wn0 = sqrt(block_total(q0, red));   // |Bbar v_j| (the barrier is inside)
@@ -241,44 +254,49 @@ extern "C" int hol_arnoldi_bounds(hol_ctx* c, const double* v0, int m, double ma
     if (!(margin >= 0.0 && margin < 1.0))
         return set_error(HOL_EINVAL, "hol_arnoldi_bounds: margin must be in [0, 1)");
     cudaStream_t s = (cudaStream_t)stream;
-    ArnArgs a;
-    a.N = c->N;
-    a.L = c->L;
-    a.m = m;
-    a.ex = c->exact;
-    a.D = c->exact ? c->kin_d64 : 0;
-    a.th = c->th;
-    for (int d = 0; d < kKinTaps; ++d) a.e[d] = c->kin_e[d];
     double* V = c->arn;
     double* H = c->arn + (size_t)(kArnoldiMax + 1) * c->N;
     int* info = reinterpret_cast<int*>(H + (kArnoldiMax + 1) * kArnoldiMax);
     const size_t sm = 2 * (size_t)c->N * sizeof(double);
     if (int rc = smem_raise((const void*)k_arnoldi, sm)) return rc;
-    k_arnoldi<<<1, 256, sm, s>>>(v0, c->dbar, a, V, H, info);
-    HOL_CHECK_LAUNCH("k_arnoldi");
-    std::vector<double> h((size_t)(m + 1) * m);
-    int done = 0;
-    HOL_CUDA(cudaMemcpyAsync(h.data(), H, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    HOL_CUDA(cudaMemcpyAsync(&done, info, sizeof(int), cudaMemcpyDeviceToHost, s));
-    HOL_CUDA(cudaStreamSynchronize(s));
-    if (done < 1 || done > m) return set_error(HOL_ENUMERIC, "hol_arnoldi_bounds: no step done");
-    std::vector<std::complex<double>> A((size_t)done * done), ev;
-    for (int i = 0; i < done; ++i)
-        for (int j = 0; j < done; ++j) A[(size_t)i * done + j] = h[(size_t)i * m + j];
-    if (!hessenberg_eigenvalues(done, A, ev))
-        return set_error(HOL_ENUMERIC, "hol_arnoldi_bounds: QR iteration did not converge");
-    double lo = INFINITY, hi = 0.0;
-    for (const auto& z : ev) {
-        const double r = std::abs(z);
-        lo = r < lo ? r : lo;
-        hi = r > hi ? r : hi;
+    double top[2] = {0.0, 0.0};   // largest Ritz modulus of Bbar, of Bbar^{-1}
+    int done_min = m;
+    for (int inv = 0; inv < 2; ++inv) {
+        ArnArgs a;
+        a.N = c->N;
+        a.L = c->L;
+        a.m = m;
+        a.inv = inv;
+        a.ex = c->exact;
+        a.D = c->exact ? c->kin_d64 : 0;
+        a.th = inv ? -c->th : c->th;
+        const double u = 1.0 - c->th * c->th;
+        a.scale = (inv && !c->exact) ? 1.0 / (u * u * u * u) : 1.0;
+        for (int d = 0; d < kKinTaps; ++d) a.e[d] = (inv && (d & 1)) ? -c->kin_e[d] : c->kin_e[d];
+        k_arnoldi<<<1, 256, sm, s>>>(v0, c->dbar, a, V, H, info);
+        HOL_CHECK_LAUNCH("k_arnoldi");
+        std::vector<double> h((size_t)(m + 1) * m);
+        int done = 0;
+        HOL_CUDA(cudaMemcpyAsync(h.data(), H, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                 s));
+        HOL_CUDA(cudaMemcpyAsync(&done, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+        HOL_CUDA(cudaStreamSynchronize(s));
+        if (done < 1 || done > m)
+            return set_error(HOL_ENUMERIC, "hol_arnoldi_bounds: no step done");
+        done_min = done < done_min ? done : done_min;
+        std::vector<std::complex<double>> A((size_t)done * done), ev;
+        for (int i = 0; i < done; ++i)
+            for (int j = 0; j < done; ++j) A[(size_t)i * done + j] = h[(size_t)i * m + j];
+        if (!hessenberg_eigenvalues(done, A, ev))
+            return set_error(HOL_ENUMERIC, "hol_arnoldi_bounds: QR iteration did not converge");
+        for (const auto& z : ev) top[inv] = std::abs(z) > top[inv] ? std::abs(z) : top[inv];
     }
-    if (!(lo > 0.0) || !isfinite(hi))
+    if (!(top[0] > 0.0) || !(top[1] > 0.0) || !isfinite(top[0]) || !isfinite(top[1]))
         return set_error(HOL_ENUMERIC, "hol_arnoldi_bounds: degenerate Ritz values");
-    const double b0 = (1.0 - margin) * lo, b1 = (1.0 + margin) * hi;
+    const double b0 = 1.0 / ((1.0 + margin) * top[1]), b1 = (1.0 + margin) * top[0];
     if (bmin) *bmin = b0;
     if (bmax) *bmax = b1;
-    if (steps) *steps = done;
+    if (steps) *steps = done_min;
     if (install) {
         static_assert(S_BMIN == 0 && S_BMAX == 1, "bounds are the first two scalars");
         const double b[2] = {b0, b1};

@@ -571,31 +571,34 @@ def test_observables_particle_hole_at_half_filling():
 # ---------------------------------------------------------------- Arnoldi bounds (App. C D)
 def test_arnoldi_full_dimension_gives_the_spectrum():
     """N steps of Arnoldi span the whole space: the Ritz values are the
-    eigenvalues of Bbar (checked against numpy's eigvals of the dense Bbar),
-    and with margin 0 the bounds are the extreme moduli."""
+    eigenvalues, so with margin 0 bmax is the largest eigenvalue modulus of
+    Bbar and bmin (from Bbar^{-1}) the smallest (numpy's eigvals of the dense
+    Bbar, a different route)."""
     w = hi.Workload("a", L=4, Ltau=10, alpha=1.3, mu=0.2, x_std=1.0, seed=5)
     m = D.model_of(w)
     x = hi.phonon_field(w)
-    v0 = hi.site_vector(w, seed=6)
-    lo, hi_, H, V, k = D.arnoldi_bounds(m, x, v0, steps=m.N, margin=0.0)
+    lo, hi_, runs = D.arnoldi_bounds(m, x, hi.site_vector(w, seed=6), steps=m.N, margin=0.0)
     ev = np.abs(np.linalg.eigvals(D.Bbar(m, x)))
-    assert k == m.N
+    assert runs["B"][2] == m.N and runs["Binv"][2] == m.N
     assert abs(lo - ev.min()) < 1e-10 * ev.max()
     assert abs(hi_ - ev.max()) < 1e-10 * ev.max()
 
 
 @pytest.mark.parametrize("kinetic", ["checkerboard", "exact"])
 def test_arnoldi_relation_and_orthonormal_basis(kinetic):
-    """Bbar V_k = V_{k+1} H (the Arnoldi relation) with orthonormal V, and the
-    20-step Ritz moduli lie inside the deterministic norm bounds."""
+    """A V_k = V_{k+1} H (the Arnoldi relation) with orthonormal V for Bbar
+    and Bbar^{-1}, and the 20-step bounds lie inside the deterministic norm
+    bounds; Bbar^{-1} is the inverse of Bbar."""
     w = hi.Workload("a", L=8, Ltau=12, alpha=1.1, x_std=1.0, seed=7)
     m = D.model_of(w, kinetic=kinetic)
     x = hi.phonon_field(w)
-    lo, hi_, H, V, k = D.arnoldi_bounds(m, x, hi.site_vector(w, seed=8), steps=20, margin=0.0)
+    lo, hi_, runs = D.arnoldi_bounds(m, x, hi.site_vector(w, seed=8), steps=20, margin=0.0)
     B = D.Bbar(m, x)
-    assert k == 20
-    assert np.abs(B @ V[:k].T - V.T @ H).max() < 1e-12
-    assert np.abs(V @ V.T - np.eye(k + 1)).max() < 1e-12
+    Binv = np.linalg.inv(B)
+    for key, A in (("B", B), ("Binv", Binv)):
+        H, V, k = runs[key]
+        assert k == 20
+        assert np.abs(A @ V[:k].T - V.T @ H).max() < 1e-11 * np.abs(A).max()
+        assert np.abs(V @ V.T - np.eye(k + 1)).max() < 1e-12
     dlo, dhi = D.spectral_bounds(m, x)
-    assert dlo <= lo and hi_ <= dhi
-
+    assert dlo <= lo <= hi_ <= dhi
