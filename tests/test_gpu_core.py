@@ -486,3 +486,63 @@ def test_end_to_end_force_matches_oracle_tiny():
         F = torch.empty(w.Ltau, w.N, device=DEV, dtype=torch.float64)
         ctx.force(v, b, F, True)
         assert _rel(F.cpu().numpy(), F_ref) < 1e-9
+
+
+@pytest.mark.parametrize("shape", ["tuned", (2, 4, 1), (2, 4, 2), (6, 4, 1), (0, 4, 1)])
+def test_big32_step_in_the_benchmark_launch_configuration(shape):
+    """The timed step of bench.py at full size (L=32, Ltau=200, 16 rhs), in
+    the launch shapes it runs (the autotuner's pick, and the shapes the
+    profiles were taken with): b = M^T R, mixed CG to 1e-8 with reliable
+    updates every 50 and polls every 10, then the force of the 16 solutions.
+    Every residual is recomputed by the matrix-free oracle, and the force is
+    compared with the oracle's on the same (v, b)."""
+    w = hi.WORKLOADS["big32"]
+    x = hi.phonon_field(w)
+    R = hi.gaussian_vectors(w, w.n_rhs, seed=2)
+    with _ctx(w, w.n_rhs) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        if shape == "tuned":
+            ctx.tune(w.n_rhs)
+        else:
+            layout, k, wpb = shape
+            ctx.set_option("layout", layout)
+            ctx.set_option("slices_per_group", k)
+            ctx.set_option("warps_per_block", wpb)
+        Rt = torch.tensor(R, device=DEV)
+        bt = torch.empty_like(Rt)
+        ctx.fermion_matvec(hg.HOL_OP_MT, Rt, bt)
+        vt = torch.empty_like(bt)
+        its, res = ctx.cg_solve(bt, vt, tol=1e-8, prec=hg.HOL_F32, reliable_every=50,
+                                check_every=10, max_iter=50000)
+        F = torch.empty(w.Ltau, w.N, device=DEV, dtype=torch.float64)
+        SF = torch.empty(1, device=DEV, dtype=torch.float64)
+        ctx.force(vt, bt, F, True, SF)
+        b, v, Fg = bt.cpu().numpy(), vt.cpu().numpy(), F.cpu().numpy()
+    Fref = MF.force_boson(w, x)
+    for k in range(w.n_rhs):
+        assert res[k] < 1e-8
+        assert MF.rel_residual(w, x, b[k], v[k]) < 1.01e-8
+        Fref = Fref + MF.force_fermion(w, x, v[k], b[k])
+    assert _rel(Fg, Fref) < 1e-12
+    sf = 0.5 * sum(float(np.dot(b[k].ravel(), v[k].ravel())) for k in range(w.n_rhs))
+    assert abs(float(SF) - sf) < 1e-11 * abs(sf)
+
+
+def test_big32_preconditioned_solve_certified():
+    """The preconditioned solve of the benchmark's comparison line at full
+    size (register KPM, default shapes): certified by the matrix-free oracle."""
+    w = hi.WORKLOADS["big32"]
+    x = hi.phonon_field(w)
+    R = hi.gaussian_vectors(w, 4, seed=3)
+    with _ctx(w, 4) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        Rt = torch.tensor(R, device=DEV)
+        bt = torch.empty_like(Rt)
+        ctx.fermion_matvec(hg.HOL_OP_MT, Rt, bt)
+        vt = torch.empty_like(bt)
+        its, res = ctx.cg_solve(bt, vt, tol=1e-8, prec=hg.HOL_F32, precond=True,
+                                max_iter=50000)
+        b, v = bt.cpu().numpy(), vt.cpu().numpy()
+    for k in range(4):
+        assert res[k] < 1e-8
+        assert MF.rel_residual(w, x, b[k], v[k]) < 1.01e-8
