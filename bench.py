@@ -303,7 +303,8 @@ def run_ours(a):
     else:
         kname = {0: "k_cg_mtm32<32>", 1: "k_cg_mtm32_v4<32>", 2: "k_cg_mtm32_v4a<32,2>",
                  3: "k_cg_mtm32_v4s<32,3>", 4: "k_cg_mtm32_split<32,2>",
-                 5: "k_cg_mtm32_split<32,4>", 6: "k_cg_mtm32_v4a<32,3>"}[ctx.get_option("layout")]
+                 5: "k_cg_mtm32_split<32,4>", 6: "k_cg_mtm32_v4a<32,3>",
+                 7: "k_cg_mtm32_tp<32>"}[ctx.get_option("layout")]
         ctx_kernel_name = kname + " (fused p = r + beta p, q = M^T M p, |Mp|^2)"
     ctx.timer_enable(0)
     clk = clocks.stop()

@@ -420,7 +420,10 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  *                       ring, 6 the same with a three-slice ring, 3 streaming
  *                       float4 with a cp.async ring across units (1-3 and 6
  *                       need L % 8 == 0), 4 / 5 split float4 with each slice
- *                       spread over 2 / 4 warps (L == 32)
+ *                       spread over 2 / 4 warps (L == 32), 7 float4 with one
+ *                       slice per warp and slices_per_group (<= 8) warps per
+ *                       block exchanging the tau neighbours in shared memory
+ *                       (L == 32)
  *   "kpm_registers"     FP32 KPM with the slice in registers, L = 16 or 32:
  *                       0 off (shared-memory kernel), 1 four columns per
  *                       lane, 2 two columns per lane (twice the warps per

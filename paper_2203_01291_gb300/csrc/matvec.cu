@@ -968,6 +968,140 @@ __global__ void __launch_bounds__(256) k_unit_dots(const float* __restrict__ r,
 
 
 // ---------------------------------------------------------------------------
+// The same fused FP32 CG step with the tau chain spread over the warps of a
+// block (float4 layout, L = 32): warp w of the block for unit u owns slice
+// tau = u K + w alone. The neighbour slices the step needs (C p_{tau-1} for
+// w_tau, s D w_{tau+1} for q_tau) come from the adjacent warps through
+// shared memory, two barriers per launch, instead of each warp walking a
+// chain of K slices with a recomputed halo: K times the warps of the chained
+// kernel on the same launch, for one extra C apply per block (the slice
+// before the block) and one extra slice load (the slice after it).
+// ---------------------------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(256, 2) k_cg_mtm32_tp(const float* __restrict__ r,
+                                                        const float* __restrict__ pold,
+                                                        float* __restrict__ pnew,
+                                                        float* __restrict__ q,
+                                                        const float* __restrict__ ev, MvGeom gm,
+                                                        const int* __restrict__ mask,
+                                                        const double* __restrict__ rr_new_part,
+                                                        const double* __restrict__ rr_old_part,
+                                                        int rr_stride, int rr_n, int first,
+                                                        double* __restrict__ pq_part, float th)
+{
+    static_assert(L == 32, "one slice per warp needs L = 32");
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
+    constexpr int N = L * L;
+    constexpr int RT = L / 4;
+    const Geom4<L> geo;
+    const int K = gm.K;                          // warps (slices) per block
+    const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rhs = blockIdx.x / gm.nrun;
+    if (rhs >= gm.n_rhs) return;                 // whole block: same rhs
+    if (mask != nullptr && mask[rhs] == 0) return;
+    const int unit = blockIdx.x - rhs * gm.nrun;
+    const int t0 = unit * K;
+    const int tau = t0 + wi;
+    const long base = (long)rhs * gm.T * N;
+    // shared: X slot j (0..K) = C p_{t0-1+j}; Z slot j (0..K) = s D w_{t0+j};
+    // each slot [RT][32] float4
+    extern __shared__ __align__(16) float4 xz[];
+    float4* Xs = xz;
+    float4* Zs = xz + (long)(K + 1) * RT * 32;
+    __shared__ double red[32];
+    auto at = [&](float4* a, int j, int k) -> float4* { return a + ((long)j * RT + k) * 32 + lane; };
+
+    float bt = 0.0f;
+    if (!first) {
+        const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
+        const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
+        bt = (float)(rn / ro);
+    }
+    auto load_p = [&](int t, float4 (&dst)[RT]) {
+        const long o = base + (long)t * N;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) dst[k] = fma4s(bt, ld4(pold, o + geo.off(k)), ld4(r, o + geo.off(k)));
+    };
+    float4 P[RT], X[RT];
+    load_p(tau, P);
+    if (pnew != nullptr) {
+        const long o = base + (long)tau * N;
+#pragma unroll
+        for (int k = 0; k < RT; ++k) st4(pnew, o + geo.off(k), P[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < RT; ++k) X[k] = P[k];
+    c4_apply<L>(X, geo, th);                     // C p_tau
+#pragma unroll
+    for (int k = 0; k < RT; ++k) *at(Xs, wi + 1, k) = X[k];
+    if (wi == 0) {                               // C p_{t0-1}: the slice before the block
+        load_p(t0 == 0 ? gm.T - 1 : t0 - 1, X);
+        c4_apply<L>(X, geo, th);
+#pragma unroll
+        for (int k = 0; k < RT; ++k) *at(Xs, 0, k) = X[k];
+    }
+    __syncthreads();
+    // w_tau = p_tau + s_tau D_tau C p_{tau-1};  Z_tau = s_tau D_tau w_tau
+    const float sg = (tau == 0) ? 1.0f : -1.0f;
+    float part = 0.0f;
+#pragma unroll
+    for (int k = 0; k < RT; ++k) {
+        const float4 d = ld4(ev, (long)tau * N + geo.off(k));
+        const float4 xm = *at(Xs, wi, k);
+        P[k].x = fmaf(sg * d.x, xm.x, P[k].x);
+        P[k].y = fmaf(sg * d.y, xm.y, P[k].y);
+        P[k].z = fmaf(sg * d.z, xm.z, P[k].z);
+        P[k].w = fmaf(sg * d.w, xm.w, P[k].w);
+        part = fmaf(P[k].x, P[k].x, part);
+        part = fmaf(P[k].y, P[k].y, part);
+        part = fmaf(P[k].z, P[k].z, part);
+        part = fmaf(P[k].w, P[k].w, part);
+        *at(Zs, wi, k) = make_float4(sg * d.x * P[k].x, sg * d.y * P[k].y, sg * d.z * P[k].z,
+                                     sg * d.w * P[k].w);
+    }
+    if (wi == K - 1) {                           // Z_{t0+K}: the slice after the block
+        const int tp = (t0 + K == gm.T) ? 0 : t0 + K;
+        const float sp = (tp == 0) ? 1.0f : -1.0f;
+        load_p(tp, X);
+#pragma unroll
+        for (int k = 0; k < RT; ++k) {
+            const float4 d = ld4(ev, (long)tp * N + geo.off(k));
+            const float4 xm = *at(Xs, K, k);     // C p_{t0+K-1}, written by this warp
+            float4 wv;
+            wv.x = fmaf(sp * d.x, xm.x, X[k].x);
+            wv.y = fmaf(sp * d.y, xm.y, X[k].y);
+            wv.z = fmaf(sp * d.z, xm.z, X[k].z);
+            wv.w = fmaf(sp * d.w, xm.w, X[k].w);
+            *at(Zs, K, k) = make_float4(sp * d.x * wv.x, sp * d.y * wv.y, sp * d.z * wv.z,
+                                        sp * d.w * wv.w);
+        }
+    }
+    __syncthreads();
+    // q_tau = w_tau + C^T Z_{tau+1}
+#pragma unroll
+    for (int k = 0; k < RT; ++k) X[k] = *at(Zs, wi + 1, k);
+    c4_apply_t<L>(X, geo, th);
+    {
+        const long o = base + (long)tau * N;
+#pragma unroll
+        for (int k = 0; k < RT; ++k)
+            st4(q, o + geo.off(k), make_float4(P[k].x + X[k].x, P[k].y + X[k].y,
+                                                P[k].z + X[k].z, P[k].w + X[k].w));
+    }
+    if (pq_part != nullptr) {                    // |M p|^2 over the block's slices
+        const double s = warp_sum((double)part);
+        if (lane == 0) red[wi] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int j = 0; j < K; ++j) t += red[j];
+            pq_part[(long)rhs * gm.pstride + unit] = t;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // dispatch on L
 // ---------------------------------------------------------------------------
 
@@ -979,6 +1113,17 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     if constexpr (L == 32) {
+        if (c->mv_vec == 7) {   // one slice per warp, K warps per block
+            const int K = c->mv_k;
+            if (K > 8) return set_error(HOL_EINVAL, "layout 7 needs slices_per_group <= 8");
+            const size_t sm = (size_t)2 * (K + 1) * (L / 4) * 32 * sizeof(float4);
+            if (int rc = smem_raise((const void*)k_cg_mtm32_tp<L>, sm)) return rc;
+            HOL_CUDA(launch_pdl(c, k_cg_mtm32_tp<L>, g.nrun * g.n_rhs, 32 * K, sm, s, r, pold,
+                                pnew, q, c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first,
+                                pq_part, (float)c->th));
+            HOL_CHECK_LAUNCH("k_cg_mtm32_tp");
+            return HOL_OK;
+        }
         if (c->mv_vec == 4 || c->mv_vec == 5) {   // split layout, 2 or 4 warps per unit
             const int units = g.nrun * g.n_rhs;
             if (c->mv_vec == 4)

@@ -2,7 +2,8 @@
 //
 // Candidates: K (tau slices streamed per lane group) among the divisors
 // {1, 2, 4, 5, 8, 10} of Ltau, 1, 2 or 4 warps per block, for L = 32 the
-// split float4 layout with 4 or 2 warps per slice (5, 4), and for L % 8 == 0
+// float4 layout with one slice per warp and K warps per block (7, K <= 8),
+// the split float4 layout with 4 or 2 warps per slice (5, 4), and for L % 8 == 0
 // the float4 layout with a cp.async ring of three slices (6), the streaming
 // float4 kernel with a cp.async ring across units (3), the float4 layout
 // with a two-slice cp.async ring (2), without (1), or the scalar register
@@ -85,6 +86,7 @@ extern "C" int hol_tune(hol_ctx* c, int n_rhs, int* best_k, int* best_warps, int
         if (c->L % 8 == 0 && !c->exact) {   // the exact propagator runs in layout 0 only
             vecs[nvec++] = 6;
             if (c->L == 32) {
+                vecs[nvec++] = 7;
                 vecs[nvec++] = 5;
                 vecs[nvec++] = 4;
             }
@@ -103,6 +105,7 @@ extern "C" int hol_tune(hol_ctx* c, int n_rhs, int* best_k, int* best_warps, int
             if ((long)matvec_pstride(c) * c->p.max_rhs > c->part_len) continue;
             for (int wi = 0; wi < 3 && !rc; ++wi) {
                 if (vec >= 3 && vec <= 5 && wi > 0 && !merged) break;   // fixed block shapes
+                if (vec == 7 && (wi > 0 || k > 8)) break;   // K warps per block, K <= 8
                 c->mv_warps = ws[wi];
                 c->mv_vec = vec;
                 for (int r = 0; r < 2 && !rc; ++r) rc = launch(r);

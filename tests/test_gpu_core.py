@@ -224,17 +224,17 @@ def test_autotuner_choice_keeps_results(L, T):
 LAYOUT_CASES = [(32, 40, 2), (32, 30, 5), (16, 30, 3), (8, 24, 1), (24, 12, 4)]
 
 
-@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("layout", [0, 1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("L,T,K", LAYOUT_CASES)
 def test_fused_mtm_every_layout(layout, L, T, K):
     """Each register layout of the fused FP32 M^T M (scalar, float4, float4
     with a two- or three-slice prefetch ring, streaming float4, split float4
-    over 2 or 4 warps) and each
-    slice grouping gives the oracle's M^T M, and a masked mixed solve
-    (right-hand sides of different scale converge at different iterations)
-    stays certified."""
-    if layout >= 4 and L != 32:
-        pytest.skip("split layouts are for L = 32")
+    over 2 or 4 warps, one slice per warp with the halos in shared memory)
+    and each slice grouping gives the oracle's M^T M, and a masked mixed
+    solve (right-hand sides of different scale converge at different
+    iterations) stays certified."""
+    if layout in (4, 5, 7) and L != 32:
+        pytest.skip("split and one-slice-per-warp layouts are for L = 32")
     w, x = _field(L, T, seed=21)
     nr = 5
     v = hi.gaussian_vectors(w, nr, seed=22) * np.array([1.0, 1e-3, 1e3, 1.0, 1e-6])[:, None, None]
@@ -259,7 +259,8 @@ def test_fused_mtm_every_layout(layout, L, T, K):
     assert max(MF.rel_residual(w, x, v[k], s[k]) for k in range(nr)) < 1.01e-8
 
 
-@pytest.mark.parametrize("layout,K", [(3, 1), (3, 2), (4, 2), (5, 4), (6, 4), (2, 8)])
+@pytest.mark.parametrize("layout,K", [(3, 1), (3, 2), (4, 2), (5, 4), (6, 4), (2, 8), (7, 1),
+                                      (7, 4), (7, 5), (7, 8)])
 def test_vector_layouts_full_size(layout, K):
     """The streaming layout (resident warps walk several of the 3200 or 1600
     units each) and the split layouts at L=32, Ltau=200 with 16 right-hand
@@ -488,7 +489,8 @@ def test_end_to_end_force_matches_oracle_tiny():
         assert _rel(F.cpu().numpy(), F_ref) < 1e-9
 
 
-@pytest.mark.parametrize("shape", ["tuned", (2, 4, 1), (2, 4, 2), (6, 4, 1), (0, 4, 1)])
+@pytest.mark.parametrize("shape", ["tuned", (2, 4, 1), (2, 4, 2), (6, 4, 1), (0, 4, 1),
+                                   (7, 4, 1), (7, 8, 1)])
 def test_big32_step_in_the_benchmark_launch_configuration(shape):
     """The timed step of bench.py at full size (L=32, Ltau=200, 16 rhs), in
     the launch shapes it runs (the autotuner's pick, and the shapes the
