@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restr
         const double pq = warp_sum_array(pq_part + (long)rhs * pq_stride, pq_n);
         const double dz = warp_sum_array(dz_part + (long)rhs * kRedStride, dz_n);
         if (threadIdx.x == 0) {
-            s_alpha = dz / pq;
+            s_alpha = cg_ratio(dz, pq);
             if (FOLD == 2) s_alpha_prev = alpha_buf[rhs];
         }
     }
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(256) k_conj_scale(R* __restrict__ p, long n,
     if (threadIdx.x < 32) {
         const double zq = warp_sum_array(zq_part + (long)rhs * kRedStride, cnt);
         const double pq = warp_sum_array(pq_part + (long)rhs * kRedStride, cnt);
-        if (threadIdx.x == 0) s_beta = -zq / pq;
+        if (threadIdx.x == 0) s_beta = cg_ratio(-zq, pq);
     }
     __syncthreads();
     const R bt = (R)s_beta;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 #include <stdio.h>
 
@@ -38,6 +39,16 @@ void count_launch();
 // contexts of different shapes driven from several host threads never lower
 // it under one another's launches.
 int smem_raise(const void* fn, size_t bytes);
+
+// A CG step ratio (alpha or beta) num / den, 0 when it is not finite. On a
+// small system the residual can reach exactly zero between two convergence
+// polls; the next step then has 0 / 0, and a zero step keeps the solution
+// instead of filling it with NaN.
+__host__ __device__ __forceinline__ double cg_ratio(double num, double den)
+{
+    const double q = num / den;
+    return isfinite(q) ? q : 0.0;
+}
 
 // Programmatic dependent launch. A kernel launched with launch_pdl may be
 // scheduled while the previous kernel of its stream is still running; it

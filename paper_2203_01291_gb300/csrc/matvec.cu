@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
     if (!first) {
         const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
         const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
-        bt = (float)(rn / ro);
+        bt = (float)cg_ratio(rn, ro);
     }
 
     // the unit's later slices t0+1 .. t0+K go to L2 while the first ones compute
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
     if (!first) {
         const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
         const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
-        bt = (float)(rn / ro);
+        bt = (float)cg_ratio(rn, ro);
     }
 
     float4 W[RT], X[RT], P[RT], Y[RT];
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(128, 2) k_cg_mtm32_v4s(const float* __restrict
         if (!first) {
             const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
             const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
-            bt = (float)(rn / ro);
+            bt = (float)cg_ratio(rn, ro);
         }
         float4 W[RT], X[RT], P[RT], Y[RT];
         issue(pos + S - 1);
@@ -475,18 +475,18 @@ __global__ void __launch_bounds__(128, 3) k_cg_merged(
     double ga, be, al;
     if (mode == 0) {
         ga = warp_sum_array(sc.g_in + (long)rhs * gm.pstride, gm.nrun);
-        be = ga / si[1];
-        al = ga / (dl - be * ga / si[0]);
+        be = cg_ratio(ga, si[1]);
+        al = cg_ratio(ga, dl - be * cg_ratio(ga, si[0]));
     } else {
         ga = warp_sum_array(sc.gr + (long)rhs * kRedStride, sc.e_n);
         if (mode == 1) {   // p_old re-conjugated against the new r
             const double pi = warp_sum_array(sc.pi + (long)rhs * gm.pstride, gm.nrun);
             const double rho = warp_sum_array(sc.rho + (long)rhs * kRedStride, sc.e_n);
-            be = -rho / pi;
-            al = ga / (dl + 2.0 * be * rho + be * be * pi);
+            be = cg_ratio(-rho, pi);
+            al = cg_ratio(ga, dl + 2.0 * be * rho + be * be * pi);
         } else {
             be = 0.0;
-            al = ga / dl;
+            al = cg_ratio(ga, dl);
         }
     }
     if (wr == 0 && (threadIdx.x & 31) == 0) {
@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(32 * NW) k_cg_mtm32_split(const float* __restr
         if (!first) {
             const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
             const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
-            bt = (float)(rn / ro);
+            bt = (float)cg_ratio(rn, ro);
         }
         if (threadIdx.x == 0) s_bt = bt;
     }
@@ -813,10 +813,10 @@ __global__ void __launch_bounds__(128, 2) k_cg_fused(const float* __restrict__ r
     const double pq = warp_sum_array(bk.pq + pb, gm.nrun);
     const double rq = warp_sum_array(bk.rq + pb, gm.nrun);
     const double qq = warp_sum_array(bk.qq + pb, gm.nrun);
-    const double ad = g / pq;
+    const double ad = cg_ratio(g, pq);
     double gn = g - 2.0 * ad * rq + ad * ad * qq;
     if (!(gn > 0.0)) gn = 0.0;   // roundoff below zero: restart the direction (beta = 0)
-    const float a = (float)ad, bt = (float)(gn / g);
+    const float a = (float)ad, bt = (float)cg_ratio(gn, g);
 
     // r' and p' of ring slot `sl` (row k)
     auto rn_of = [&](int sl, int k) -> float4 {
@@ -1016,7 +1016,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_mtm32_tp(const float* __restrict_
     if (!first) {
         const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
         const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
-        bt = (float)(rn / ro);
+        bt = (float)cg_ratio(rn, ro);
     }
     auto load_p = [&](int t, float4 (&dst)[RT]) {
         const long o = base + (long)t * N;

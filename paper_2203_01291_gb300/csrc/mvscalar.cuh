@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(128) k_M(const R* __restrict__ v, const R* __r
     if (UPD && !bsrc.first) {
         const double rn = warp_sum_array(bsrc.rn + (long)rhs * bsrc.stride, bsrc.n);
         const double ro = warp_sum_array(bsrc.ro + (long)rhs * bsrc.stride, bsrc.n);
-        bt = (R)(rn / ro);
+        bt = (R)cg_ratio(rn, ro);
     }
 
     R a[L], c[L];
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(128) k_cg_mtm32(const float* __restrict__ r,
     if (!first) {
         const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
         const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
-        bt = (float)(rn / ro);
+        bt = (float)cg_ratio(rn, ro);
     }
 
     float W[L], X[L], P[L], Y[L];

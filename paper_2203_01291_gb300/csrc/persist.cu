@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_persist(PersistArgs a)
             if (!first) {
                 const double rn = warp_sum_array(rr_now + (long)rhs * kRedStride, cnt_cur);
                 const double ro = warp_sum_array(rr_nxt + (long)rhs * kRedStride, cnt_old);
-                bt = (float)(rn / ro);
+                bt = (float)cg_ratio(rn, ro);
             }
             float4 W[RT], X[RT], P[RT], Y[RT];
             {
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_persist(PersistArgs a)
             // ---------------- phase B
             const double pqs = warp_sum_array(a.pq + (long)rhs * kRedStride, a.nrun);
             const double rz = warp_sum_array(rr_now + (long)rhs * kRedStride, cnt_cur);
-            const float al = (float)(rz / pqs);
+            const float al = (float)cg_ratio(rz, pqs);
             double acc = 0.0;
             for (int s = 0; s < a.K; ++s) {
                 const long o = base + (long)(t0 + s) * N;

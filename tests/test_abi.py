@@ -54,3 +54,45 @@ def test_context_refuses_without_gpu():
     import paper_2203_01291_gb300 as hg
     with pytest.raises(RuntimeError):
         hg.Context(L=4, Ltau=8)
+
+
+@pytest.mark.parametrize("field,value", [("L", 3), ("L", 34), ("L", 2), ("L", 7), ("Ltau", 3),
+                                         ("Ltau", 0), ("max_rhs", 0), ("max_rhs", 5000),
+                                         ("dtau", 0.0), ("dtau", -0.1), ("kinetic", 2),
+                                         ("kinetic", -1)])
+def test_create_refuses_bad_parameters_before_touching_a_device(field, value):
+    """hol_create validates the parameters on the host first: an unsupported
+    shape or value is HOL_EINVAL with a message, whether or not a GPU exists."""
+    from paper_2203_01291_gb300 import _abi
+    lib = _abi.load()
+    p = _abi.hol_params(8, 8, 0.1, 1.0, 0.0, 1.0, 1.0, 1, 0)
+    setattr(p, field, value)
+    h = ctypes.c_void_p()
+    rc = lib.hol_create(ctypes.byref(p), ctypes.byref(h))
+    assert rc == _abi.HOL_EINVAL
+    assert not h.value
+    assert lib.hol_last_error().decode()
+
+
+def test_create_refuses_exact_propagator_with_huge_hopping_step():
+    from paper_2203_01291_gb300 import _abi
+    lib = _abi.load()
+    p = _abi.hol_params(8, 8, 1.0, 5.0, 0.0, 1.0, 1.0, 1, _abi.HOL_KINETIC_EXACT)
+    h = ctypes.c_void_p()
+    assert lib.hol_create(ctypes.byref(p), ctypes.byref(h)) == _abi.HOL_EINVAL
+
+
+def test_null_arguments_are_refused():
+    """Every entry point taking a context refuses a null one with HOL_EINVAL."""
+    from paper_2203_01291_gb300 import _abi
+    lib = _abi.load()
+    v = ctypes.c_void_p()
+    assert lib.hol_set_field(None, None, None) == _abi.HOL_EINVAL
+    assert lib.fermion_matvec(None, 0, 0, None, None, 1, None) == _abi.HOL_EINVAL
+    assert lib.force(None, None, None, 1, None, 1, None, None) == _abi.HOL_EINVAL
+    assert lib.hol_destroy(None) == _abi.HOL_OK
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    assert lib.hol_get_bounds(None, ctypes.byref(lo), ctypes.byref(hi), None) == _abi.HOL_EINVAL
+    assert lib.hol_arnoldi_bounds(None, None, 20, 0.05, 0, None, None, None, None) == \
+        _abi.HOL_EINVAL
+    del v
