@@ -143,3 +143,47 @@ def test_many_right_hand_sides():
         s = sol.cpu().numpy()
     assert np.all(res < 1e-8)
     assert max(MF.rel_residual(w, x, v[k], s[k]) for k in range(nr)) < 1.01e-8
+
+
+@pytest.mark.parametrize("T", [2, 4])
+def test_trajectory_measurement_and_moves_on_the_shortest_tau_axis(T):
+    """Ltau = 2 and 4 (tau transforms of length 2 and 4, doubled domain of
+    length 4 and 8): an HMC trajectory, the stochastic Green's function with
+    its Wick products, and a reflection and a swap move match the oracle."""
+    w = hi.Workload("e", L=4, Ltau=T, alpha=1.1, mu=0.0, omega0=1.0, x_std=1.0, seed=10)
+    m = D.model_of(w)
+    x0 = hi.phonon_field(w)
+    R = hi.gaussian_vectors(w, 2, seed=11)
+    Rp = hi.gaussian_vectors(w, 1, seed=12)[0]
+    dt, Nt, nt, mreg = 0.05, 3, 2, 1.0
+    xf, pf, Hi, Hf = D.hmc_update(m, x0, R, Rp, dt, Nt, nt, mreg)
+    o = hg.md_opts(dt, Nt, nt, mreg, force_tol=1e-13, action_tol=1e-13, prec=hg.HOL_F64,
+                   precond=False, check_every=1)
+    xi = hi.z2_vectors(w, 3, seed=13)
+    Phi = D.phi_from_R(m, x0, R)
+    with _ctx(w, 4) as ctx:
+        x = torch.tensor(x0, device=DEV)
+        acc, dH, terms = ctx.fourier_accel_leapfrog(x, torch.tensor(R, device=DEV),
+                                                    torch.tensor(Rp, device=DEV), o, u=0.0)
+        assert acc
+        assert abs(terms[:3].sum() - Hi) < 1e-9 * abs(Hi)
+        assert abs(terms[3:].sum() - Hf) < 1e-9 * abs(Hf)
+        assert _rel(x.cpu().numpy(), xf) < 1e-8
+        ctx.set_field(torch.tensor(x0, device=DEV))
+        xt = torch.tensor(xi, device=DEV)
+        Gxi = torch.empty_like(xt)
+        G2 = torch.empty(2 * T, w.L, w.L, dtype=torch.float64, device=DEV)
+        G4 = torch.empty(3, 2 * T, w.L, w.L, dtype=torch.float64, device=DEV)
+        ctx.stochastic_measure(xt, Gxi, G2, G4, 7, tol=1e-13)
+        assert _rel(G2.cpu().numpy(), D.green_average(m, x0, xi)) < 1e-10
+        ref4 = D.four_point_pairs(m, x0, xi)
+        for k in range(3):
+            assert _rel(G4.cpu().numpy()[k], ref4[k]) < 1e-10
+        for kind, i, j in ((hg.HOL_REFLECT, 5, -1), (hg.HOL_SWAP, 1, 2)):
+            xg = torch.tensor(x0, device=DEV)
+            a_, dS, S = ctx.global_update(xg, torch.tensor(Phi, device=DEV), kind, i, j, u=0.5,
+                                          tol=1e-13)
+            a_o, dS_o, x_o = D.global_update(m, x0, Phi, kind, i, j, 0.5)
+            assert abs(dS - dS_o) < 1e-8 * D.action(m, x0, Phi)
+            if abs(np.log(0.5) + dS_o) > 1e-6:
+                assert a_ == a_o
