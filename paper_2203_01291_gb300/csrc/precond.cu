@@ -38,9 +38,18 @@ namespace {
 
 using namespace fft;
 
+// The tau transforms act on real site lines, two per complex transform: the
+// tile holds TS sites as TS / 2 columns, site 2c in the real and site 2c + 1
+// in the imaginary part of column c.
+//
+// Forward. With t_tau = exp(-i pi tau / T), X[w] = sum_tau t_tau x_tau
+// exp(-2 pi i w tau / T) of a real x has X[T-1-w] = conj(X[w]), so from
+// Z = X_a + i X_b: X_a = (Z[w] + conj Z[T-1-w]) / 2 and
+// X_b = (Z[w] - conj Z[T-1-w]) / (2 i).
+//
 // v (real [nr][T][N]) -> vh (complex [nr][T/2][N]) = U v restricted to omega < T/2
-// TC, TSC > 0: length and tile width fixed at compile time (fft_tau_ct);
-// 0: taken from the arguments (fft_tau).
+// TC, TSC > 0: length and tile width (sites) fixed at compile time
+// (fft_tau_ct); 0: taken from the arguments (fft_tau).
 template <typename R, int TC = 0, int TSC = 0>
 __global__ void __launch_bounds__(256) k_tau_fwd(const R* __restrict__ v,
                                                  typename Cx<R>::T2* __restrict__ vh,
@@ -50,40 +59,52 @@ __global__ void __launch_bounds__(256) k_tau_fwd(const R* __restrict__ v,
     using C2 = typename Cx<R>::T2;
     const int T = TC > 0 ? TC : T_;
     const int TS = TSC > 0 ? TSC : TS_;
+    const int TH = TS / 2;                 // transform columns
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2* a = reinterpret_cast<C2*>(smem_raw);
-    C2* b = a + (long)T * TS;
+    C2* b = a + (long)T * TH;
     const int rhs = blockIdx.y;
     const int i0 = blockIdx.x * TS;
     const long base = (long)rhs * T * N;
-    for (int item = threadIdx.x; item < T * TS; item += blockDim.x) {
-        const int c = item % TS, tau = item / TS;
-        const int i = i0 + c;
-        const R x = (i < N) ? v[base + (long)tau * N + i] : R(0);
+    for (int item = threadIdx.x; item < T * TH; item += blockDim.x) {
+        const int c = item % TH, tau = item / TH;
+        const int i = i0 + 2 * c;          // N is even, so i < N implies i + 1 < N
+        R xa = R(0), xb = R(0);
+        if (i < N) {
+            xa = v[base + (long)tau * N + i];
+            xb = v[base + (long)tau * N + i + 1];
+        }
         const C2 t = tw<R>(w2, tau, T);    // exp(-i pi tau / T)
-        a[tau * TS + c] = Cx<R>::mk(x * t.x, x * t.y);
+        a[tau * TH + c] = Cx<R>::mk(xa * t.x - xb * t.y, xa * t.y + xb * t.x);
     }
     C2* res;
     if constexpr (TC > 0)
-        res = fft_tau_ct<R, TC, TSC, 256>(a, b, w2);
+        res = fft_tau_ct<R, TC, TSC / 2, 256>(a, b, w2);
     else
-        res = fft_tau<R>(a, b, w2, T, TS, plan);
+        res = fft_tau<R>(a, b, w2, T, TH, plan);
     const int Th = T / 2;
     const long ob = (long)rhs * Th * N;
-    for (int item = threadIdx.x; item < Th * TS; item += blockDim.x) {
-        const int c = item % TS, w = item / TS;
-        const int i = i0 + c;
+    const R hs = R(0.5) * scale;
+    for (int item = threadIdx.x; item < Th * TH; item += blockDim.x) {
+        const int c = item % TH, w = item / TH;
+        const int i = i0 + 2 * c;
         if (i < N) {
-            C2 z = res[w * TS + c];
-            z.x *= scale;
-            z.y *= scale;
-            vh[ob + (long)w * N + i] = z;
+            const C2 z = res[w * TH + c];
+            const C2 zm = res[(T - 1 - w) * TH + c];
+            // X_a = (z + conj zm) / 2,  X_b = (z - conj zm) / (2 i)
+            vh[ob + (long)w * N + i] = Cx<R>::mk(hs * (z.x + zm.x), hs * (z.y - zm.y));
+            vh[ob + (long)w * N + i + 1] = Cx<R>::mk(hs * (z.y + zm.y), hs * (zm.x - z.x));
         }
     }
 }
 
-// yh (complex [nr][T/2][N]) -> y (real [nr][T][N]) = U^dag of the conjugate-
-// symmetric extension; optional dot partials sum(y * rdot) per (rhs, tile).
+// Inverse. y_tau = (2 / sqrt T) Re sum_{w < T/2} Y_w exp(2 pi i (w + 1/2) tau / T)
+// is the real inverse of the conjugate-symmetric extension Y_full (Y_w for
+// w < T/2, conj Y_{T-1-w} above), so two sites share one transform:
+// with Z = Y_full,a + i Y_full,b and F = FFT(conj Z),
+// y_a + i y_b = (1 / sqrt T) conj(t_tau F_tau).
+// yh (complex [nr][T/2][N]) -> y (real [nr][T][N]); optional dot partials
+// sum(y * rdot) per (rhs, tile). `scale` is 2 / sqrt T.
 template <typename R, int TC = 0, int TSC = 0>
 __global__ void __launch_bounds__(256) k_tau_inv(const typename Cx<R>::T2* __restrict__ yh,
                                                  R* __restrict__ y,
@@ -95,39 +116,51 @@ __global__ void __launch_bounds__(256) k_tau_inv(const typename Cx<R>::T2* __res
     using C2 = typename Cx<R>::T2;
     const int T = TC > 0 ? TC : T_;
     const int TS = TSC > 0 ? TSC : TS_;
+    const int TH = TS / 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2* a = reinterpret_cast<C2*>(smem_raw);
-    C2* b = a + (long)T * TS;
+    C2* b = a + (long)T * TH;
     const int rhs = blockIdx.y;
     const int i0 = blockIdx.x * TS;
     const int Th = T / 2;
     const long ib = (long)rhs * Th * N;
-    for (int item = threadIdx.x; item < T * TS; item += blockDim.x) {
-        const int c = item % TS, w = item / TS;
-        const int i = i0 + c;
+    for (int item = threadIdx.x; item < T * TH; item += blockDim.x) {
+        const int c = item % TH, w = item / TH;
+        const int i = i0 + 2 * c;
         C2 z = Cx<R>::mk(R(0), R(0));
-        if (w < Th && i < N) {
-            z = yh[ib + (long)w * N + i];
-            z.y = -z.y;   // conj
+        if (i < N) {
+            if (w < Th) {          // conj(Y_a + i Y_b)
+                const C2 ya = yh[ib + (long)w * N + i], yb = yh[ib + (long)w * N + i + 1];
+                z = Cx<R>::mk(ya.x - yb.y, -(ya.y + yb.x));
+            } else {               // conj(conj Y_a' + i conj Y_b'), ' = T-1-w
+                const long o = ib + (long)(T - 1 - w) * N + i;
+                const C2 ya = yh[o], yb = yh[o + 1];
+                z = Cx<R>::mk(ya.x + yb.y, ya.y - yb.x);
+            }
         }
-        a[w * TS + c] = z;
+        a[w * TH + c] = z;
     }
     C2* res;
     if constexpr (TC > 0)
-        res = fft_tau_ct<R, TC, TSC, 256>(a, b, w2);
+        res = fft_tau_ct<R, TC, TSC / 2, 256>(a, b, w2);
     else
-        res = fft_tau<R>(a, b, w2, T, TS, plan);
+        res = fft_tau<R>(a, b, w2, T, TH, plan);
     const long ob = (long)rhs * T * N;
+    const R hs = R(0.5) * scale;           // 1 / sqrt T
     double acc = 0.0;
-    for (int item = threadIdx.x; item < T * TS; item += blockDim.x) {
-        const int c = item % TS, tau = item / TS;
-        const int i = i0 + c;
+    for (int item = threadIdx.x; item < T * TH; item += blockDim.x) {
+        const int c = item % TH, tau = item / TH;
+        const int i = i0 + 2 * c;
         if (i < N) {
             const C2 t = tw<R>(w2, tau, T);
-            const C2 z = res[tau * TS + c];
-            const R val = scale * (t.x * z.x - t.y * z.y);   // 2/sqrt(T) Re(w2 * Y)
-            y[ob + (long)tau * N + i] = val;
-            if (rdot != nullptr) acc += (double)val * (double)rdot[ob + (long)tau * N + i];
+            const C2 f = res[tau * TH + c];
+            const R ya = hs * (t.x * f.x - t.y * f.y);     // Re(t F) / sqrt T
+            const R yb = -hs * (t.x * f.y + t.y * f.x);    // -Im(t F) / sqrt T
+            const long o = ob + (long)tau * N + i;
+            y[o] = ya;
+            y[o + 1] = yb;
+            if (rdot != nullptr)
+                acc += (double)ya * (double)rdot[o] + (double)yb * (double)rdot[o + 1];
         }
     }
     if (dot_part != nullptr) {
@@ -699,7 +732,7 @@ int tile_sites(const hol_ctx* c, int prec)
 size_t fft_smem(const hol_ctx* c, int prec)
 {
     const size_t cs = prec == HOL_F64 ? sizeof(double2) : sizeof(float2);
-    return 2 * (size_t)c->T * tile_sites(c, prec) * cs;
+    return 2 * (size_t)c->T * (tile_sites(c, prec) / 2) * cs;   // two sites per column
 }
 
 int kpm_threads(const hol_ctx* c)
