@@ -37,32 +37,46 @@ using namespace fft;
 constexpr int kMeasTS = 16;
 
 // real [nv][T][N] -> complex [nv][nw][N]: tau DFT of each site line,
-// optionally twisted by exp(-i pi tau / T), first nw frequencies kept.
+// optionally twisted by exp(-i pi tau / T), first nw frequencies kept. Two
+// real site lines share one complex transform (TS sites as TS / 2 columns):
+// the transform X of a real line has X[w'] = conj X[w] with w' = T-1-w
+// (twisted) or (T-w) mod T (plain), so Z = X_a + i X_b gives
+// X_a = (Z[w] + conj Z[w']) / 2 and X_b = (Z[w] - conj Z[w']) / (2 i).
 __global__ void __launch_bounds__(256) k_m_tau_fwd(const double* __restrict__ in,
                                                    double2* __restrict__ out,
                                                    const double2* __restrict__ w2, int T, int N,
                                                    int TS, RadixPlan plan, int twist, int nw)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TH = TS / 2;
     double2* a = reinterpret_cast<double2*>(smem_raw);
-    double2* b = a + (long)T * TS;
+    double2* b = a + (long)T * TH;
     const int vec = blockIdx.y, i0 = blockIdx.x * TS;
     const long ib = (long)vec * T * N;
-    for (int item = threadIdx.x; item < T * TS; item += blockDim.x) {
-        const int c = item % TS, tau = item / TS, i = i0 + c;
-        const double x = i < N ? in[ib + (long)tau * N + i] : 0.0;
-        double2 z = make_double2(x, 0.0);
+    for (int item = threadIdx.x; item < T * TH; item += blockDim.x) {
+        const int c = item % TH, tau = item / TH, i = i0 + 2 * c;   // N even: i + 1 < N too
+        double xa = 0.0, xb = 0.0;
+        if (i < N) {
+            xa = in[ib + (long)tau * N + i];
+            xb = in[ib + (long)tau * N + i + 1];
+        }
+        double2 z = make_double2(xa, xb);
         if (twist) {
             const double2 t = w2[tau];
-            z = make_double2(x * t.x, x * t.y);
+            z = make_double2(xa * t.x - xb * t.y, xa * t.y + xb * t.x);
         }
-        a[tau * TS + c] = z;
+        a[tau * TH + c] = z;
     }
-    double2* res = fft_tau<double>(a, b, w2, T, TS, plan);
+    double2* res = fft_tau<double>(a, b, w2, T, TH, plan);
     const long ob = (long)vec * nw * N;
-    for (int item = threadIdx.x; item < nw * TS; item += blockDim.x) {
-        const int c = item % TS, w = item / TS, i = i0 + c;
-        if (i < N) out[ob + (long)w * N + i] = res[w * TS + c];
+    for (int item = threadIdx.x; item < nw * TH; item += blockDim.x) {
+        const int c = item % TH, w = item / TH, i = i0 + 2 * c;
+        if (i < N) {
+            const int wp = twist ? T - 1 - w : (w == 0 ? 0 : T - w);
+            const double2 z = res[w * TH + c], zm = res[wp * TH + c];
+            out[ob + (long)w * N + i] = make_double2(0.5 * (z.x + zm.x), 0.5 * (z.y - zm.y));
+            out[ob + (long)w * N + i + 1] = make_double2(0.5 * (z.y + zm.y), 0.5 * (zm.x - z.x));
+        }
     }
 }
 
