@@ -13,6 +13,10 @@
  *   contiguous), length n = N*T per right-hand side.
  * - All array arguments are DEVICE pointers unless the comment says "host".
  *   The caller allocates and owns them; the library never frees them.
+ * - Device vector arguments are read and written with 8- and 16-byte vector
+ *   accesses and must be 16-byte aligned (cudaMalloc and PyTorch allocations
+ *   are, and so is a slice of one along the right-hand-side axis, since N is
+ *   even); a misaligned one is refused with HOL_EINVAL before any launch.
  * - The context owns its scratch memory (allocated in hol_create, released in
  *   hol_destroy) and is bound to the CUDA device current at hol_create.
  * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
@@ -34,7 +38,8 @@ extern "C" {
 #define HOL_EINVAL   -1   /* bad argument (size, null pointer, unsupported shape) */
 #define HOL_ENOTCONV -2   /* CG did not reach the tolerance within max_iter     */
 #define HOL_ENUMERIC -3   /* NaN / Inf met in a reduction                        */
-#define HOL_ETIMEOUT -4   /* a bounded device-side wait gave up                  */
+#define HOL_ETIMEOUT -4   /* reserved: a bounded device-side wait gave up (no
+                             call of this version waits on the device)          */
 #define HOL_ECUDA    -5   /* a CUDA runtime call failed                          */
 #define HOL_ENOMEM   -6   /* device allocation failed                            */
 

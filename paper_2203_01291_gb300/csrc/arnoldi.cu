@@ -247,6 +247,7 @@ extern "C" int hol_arnoldi_bounds(hol_ctx* c, const double* v0, int m, double ma
                                   double* bmin, double* bmax, int* steps, void* stream)
 {
     if (!c || !v0) return set_error(HOL_EINVAL, "hol_arnoldi_bounds: null argument");
+    if (int rc_ = require_aligned("hol_arnoldi_bounds", {v0})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "hol_arnoldi_bounds: hol_set_field not called");
     if (m < 1 || m > kArnoldiMax || m > c->N)
         return set_error(HOL_EINVAL, "hol_arnoldi_bounds: m=%d outside [1, min(%d, N)]", m,

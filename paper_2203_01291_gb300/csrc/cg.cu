@@ -1081,6 +1081,7 @@ extern "C" int cg_solve(hol_ctx* c, const double* b, double* v, int n_rhs, const
                         int* iters, double* resid, void* stream)
 {
     if (!c || !b || !v || !o) return set_error(HOL_EINVAL, "cg_solve: null argument");
+    if (int rc_ = require_aligned("cg_solve", {b, v})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "cg_solve: hol_set_field not called");
     if (n_rhs < 1 || n_rhs > c->p.max_rhs)
         return set_error(HOL_EINVAL, "cg_solve: n_rhs=%d outside [1, %d]", n_rhs, c->p.max_rhs);

@@ -352,6 +352,7 @@ extern "C" int hol_destroy(hol_ctx* c)
 extern "C" int hol_set_field(hol_ctx* c, const double* x, void* stream)
 {
     if (!c || !x) return set_error(HOL_EINVAL, "hol_set_field: null argument");
+    if (int rc_ = require_aligned("hol_set_field", {x})) return rc_;
     cudaStream_t s = (cudaStream_t)stream;
     const int nb = ceil_div(c->n, 256) < 4096 ? ceil_div(c->n, 256) : 4096;
     k_expv<<<nb, 256, 0, s>>>(x, c->x, c->ev64, c->ev32, c->n, c->p.dtau, c->p.alpha, c->p.mu,
@@ -372,6 +373,7 @@ extern "C" int fermion_matvec(hol_ctx* c, int op, int prec, const void* v, void*
                               void* stream)
 {
     if (!c || !v || !out) return set_error(HOL_EINVAL, "fermion_matvec: null argument");
+    if (int rc_ = require_aligned("fermion_matvec", {v, out})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "fermion_matvec: hol_set_field not called");
     if (n_rhs < 1 || n_rhs > c->p.max_rhs)
         return set_error(HOL_EINVAL, "fermion_matvec: n_rhs=%d outside [1, %d]", n_rhs,

@@ -224,6 +224,7 @@ extern "C" int force(hol_ctx* c, const double* v, const double* b, int n_pf, dou
                      int with_bosonic, double* S_F, void* stream)
 {
     if (!c || !v || !b || !dSdx) return set_error(HOL_EINVAL, "force: null argument");
+    if (int rc_ = require_aligned("force", {v, b, dSdx})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "force: hol_set_field not called");
     if (n_pf < 0 || n_pf > c->p.max_rhs)
         return set_error(HOL_EINVAL, "force: n_pf=%d outside [0, %d]", n_pf, c->p.max_rhs);

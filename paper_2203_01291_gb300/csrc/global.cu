@@ -62,6 +62,7 @@ extern "C" int global_update(hol_ctx* c, double* x, const double* Phi, int n_pf,
                              double* dS, void* stream)
 {
     if (!c || !x || !Phi || !o) return set_error(HOL_EINVAL, "global_update: null argument");
+    if (int rc_ = require_aligned("global_update", {x, Phi})) return rc_;
     if (n_pf < 1 || n_pf > c->p.max_rhs)
         return set_error(HOL_EINVAL, "global_update: n_pf=%d outside [1, %d]", n_pf,
                          c->p.max_rhs);

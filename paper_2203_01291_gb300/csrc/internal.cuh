@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <initializer_list>
 #include <stdio.h>
 
 #include "../../include/holstein.h"
@@ -39,6 +40,18 @@ void count_launch();
 // contexts of different shapes driven from several host threads never lower
 // it under one another's launches.
 int smem_raise(const void* fn, size_t bytes);
+
+// Device vectors are moved with 8- and 16-byte vector accesses, so every
+// device vector argument of the C ABI must be 16-byte aligned (cudaMalloc and
+// PyTorch allocations are, and so is a slice of one along the right-hand-side
+// axis, N being even). Checked on the host before any launch.
+inline int require_aligned(const char* fn, std::initializer_list<const void*> ptrs)
+{
+    for (const void* q : ptrs)
+        if (q != nullptr && (reinterpret_cast<uintptr_t>(q) & 15u) != 0)
+            return set_error(HOL_EINVAL, "%s: device vector %p is not 16-byte aligned", fn, q);
+    return HOL_OK;
+}
 
 // A CG step ratio (alpha or beta) num / den, 0 when it is not finite. On a
 // small system the residual can reach exactly zero between two convergence

@@ -47,7 +47,9 @@ __global__ void k_mass_tables(double* __restrict__ g, int T, double dtau, double
 }
 
 // out = base + coef * (F^{-1} diag(g) F in) along tau for TS sites per block
-// (base may be null; out may alias base).
+// (base may be null; out may alias base). g is real and symmetric
+// (g[w] = g[T-w]), so the filter maps real lines to real lines and two lines
+// share one complex transform: z = x_a + i x_b gives y_a + i y_b.
 __global__ void __launch_bounds__(256) k_tau_filter(const double* __restrict__ in, const double* base,
                                                     double* out, double coef,
                                                     const double* __restrict__ g,
@@ -55,33 +57,36 @@ __global__ void __launch_bounds__(256) k_tau_filter(const double* __restrict__ i
                                                     int TS, RadixPlan plan)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TH = TS / 2;
     double2* a = reinterpret_cast<double2*>(smem_raw);
-    double2* b = a + (long)T * TS;
+    double2* b = a + (long)T * TH;
     const int i0 = blockIdx.x * TS;
-    for (int item = threadIdx.x; item < T * TS; item += blockDim.x) {
-        const int c = item % TS, tau = item / TS;
-        const int i = i0 + c;
-        a[tau * TS + c] = make_double2(i < N ? in[(long)tau * N + i] : 0.0, 0.0);
+    for (int item = threadIdx.x; item < T * TH; item += blockDim.x) {
+        const int c = item % TH, tau = item / TH;
+        const int i = i0 + 2 * c;   // N is even, so i < N implies i + 1 < N
+        a[tau * TH + c] = i < N ? make_double2(in[(long)tau * N + i], in[(long)tau * N + i + 1])
+                                : make_double2(0.0, 0.0);
     }
-    double2* res = fft_tau<double>(a, b, w2, T, TS, plan);
+    double2* res = fft_tau<double>(a, b, w2, T, TH, plan);
     // conj(g X): the forward transform of it is T times the conjugate of the
     // inverse transform of g X
-    for (int item = threadIdx.x; item < T * TS; item += blockDim.x) {
-        const int c = item % TS, w = item / TS;
-        double2 z = res[w * TS + c];
+    for (int item = threadIdx.x; item < T * TH; item += blockDim.x) {
+        const int c = item % TH, w = item / TH;
+        double2 z = res[w * TH + c];
         const double gw = g[w];
-        res[w * TS + c] = make_double2(gw * z.x, -gw * z.y);
+        res[w * TH + c] = make_double2(gw * z.x, -gw * z.y);
     }
     double2* oth = (res == a) ? b : a;
-    double2* res2 = fft_tau<double>(res, oth, w2, T, TS, plan);
+    double2* res2 = fft_tau<double>(res, oth, w2, T, TH, plan);
     const double scale = coef / T;
-    for (int item = threadIdx.x; item < T * TS; item += blockDim.x) {
-        const int c = item % TS, tau = item / TS;
-        const int i = i0 + c;
+    for (int item = threadIdx.x; item < T * TH; item += blockDim.x) {
+        const int c = item % TH, tau = item / TH;
+        const int i = i0 + 2 * c;
         if (i < N) {
             const long k = (long)tau * N + i;
-            const double y = scale * res2[tau * TS + c].x;
-            out[k] = (base != nullptr ? base[k] : 0.0) + y;
+            const double2 z = res2[tau * TH + c];   // T conj(y_a + i y_b)
+            out[k] = (base != nullptr ? base[k] : 0.0) + scale * z.x;
+            out[k + 1] = (base != nullptr ? base[k + 1] : 0.0) - scale * z.y;
         }
     }
 }
@@ -165,7 +170,7 @@ int filter(hol_ctx* c, const double* in, const double* base, double* out, double
     const RadixPlan plan = plan_of(c->T);
     if (plan.n < 0) return set_error(HOL_EINVAL, "leapfrog: Ltau=%d has a prime factor > 7", c->T);
     const int ts = filter_tile(c);
-    const size_t sm = 2 * (size_t)c->T * ts * sizeof(double2);
+    const size_t sm = 2 * (size_t)c->T * (ts / 2) * sizeof(double2);   // two sites per column
     if (int rc = smem_raise((const void*)k_tau_filter, sm)) return rc;
     k_tau_filter<<<ceil_div(c->N, ts), 256, sm, s>>>(in, base, out, coef,
                                                       c->md_g + which * c->T, c->tw64, c->T,
@@ -274,6 +279,7 @@ extern "C" int mass_apply(hol_ctx* c, int which, double m_reg, const double* p, 
                           void* stream)
 {
     if (!c || !p || !out) return set_error(HOL_EINVAL, "mass_apply: null argument");
+    if (int rc_ = require_aligned("mass_apply", {p, out})) return rc_;
     if (which < 0 || which > 2) return set_error(HOL_EINVAL, "mass_apply: bad selector %d", which);
     if (!(m_reg >= 0.0)) return set_error(HOL_EINVAL, "mass_apply: m_reg must be >= 0 or inf");
     if (plan_of(c->T).n < 0) return set_error(HOL_EINVAL, "mass_apply: Ltau has a prime factor > 7");
@@ -288,6 +294,7 @@ extern "C" int md_integrate(hol_ctx* c, double* x, double* p, const double* Phi,
                             const hol_md_opts* o, void* stream)
 {
     if (!c || !x || !p || !Phi) return set_error(HOL_EINVAL, "md_integrate: null argument");
+    if (int rc_ = require_aligned("md_integrate", {x, p, Phi})) return rc_;
     int rc = check_md(c, o, n_pf);
     if (rc) return rc;
     return md_run(c, x, p, Phi, n_pf, o, (cudaStream_t)stream);
@@ -298,6 +305,7 @@ extern "C" int fourier_accel_leapfrog(hol_ctx* c, double* x, const double* R_pf,
                                       double* dH, double* terms, void* stream)
 {
     if (!c || !x || !R_pf || !R_p) return set_error(HOL_EINVAL, "fourier_accel_leapfrog: null argument");
+    if (int rc_ = require_aligned("fourier_accel_leapfrog", {x, R_pf, R_p})) return rc_;
     int rc = check_md(c, o, n_pf);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;

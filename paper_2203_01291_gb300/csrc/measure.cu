@@ -288,6 +288,7 @@ extern "C" int stochastic_measure(hol_ctx* c, const double* xi, int n_rv, const 
                                   void* stream)
 {
     if (!c || !xi || !opts || !Gxi || !G2) return set_error(HOL_EINVAL, "stochastic_measure: null argument");
+    if (int rc_ = require_aligned("stochastic_measure", {xi, Gxi, G2, G4})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "stochastic_measure: hol_set_field not called");
     if (n_rv < 1) return set_error(HOL_EINVAL, "stochastic_measure: n_rv=%d", n_rv);
     if (four_point & ~7) return set_error(HOL_EINVAL, "stochastic_measure: bad four_point mask");
@@ -461,6 +462,7 @@ extern "C" int measure_observables(hol_ctx* c, const double* G2, const double* G
 {
     if (!c || !G2 || !G4 || !C || !out3)
         return set_error(HOL_EINVAL, "measure_observables: null argument");
+    if (int rc_ = require_aligned("measure_observables", {G2, G4, C})) return rc_;
     cudaStream_t s = (cudaStream_t)stream;
     double* scal = c->md_s + 12;
     k_observables<<<1, 256, 0, s>>>(G2, G4, c->L, c->T, c->p.dtau, C, scal);

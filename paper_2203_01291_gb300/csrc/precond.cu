@@ -38,6 +38,49 @@ namespace {
 
 using namespace fft;
 
+// Two adjacent values (sites i, i + 1 with i even, so the pair is aligned to
+// its own size) as one vector access.
+__device__ __forceinline__ void ld_pair(const float* p, float& a, float& b)
+{
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ld_pair(const double* p, double& a, double& b)
+{
+    const double2 v = *reinterpret_cast<const double2*>(p);
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void st_pair(float* p, float a, float b)
+{
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+}
+__device__ __forceinline__ void st_pair(double* p, double a, double b)
+{
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+__device__ __forceinline__ void ld_cpair(const float2* p, float2& a, float2& b)
+{
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ld_cpair(const double2* p, double2& a, double2& b)
+{
+    a = p[0];
+    b = p[1];
+}
+__device__ __forceinline__ void st_cpair(float2* p, float2 a, float2 b)
+{
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_cpair(double2* p, double2 a, double2 b)
+{
+    p[0] = a;
+    p[1] = b;
+}
+
 // The tau transforms act on real site lines, two per complex transform: the
 // tile holds TS sites as TS / 2 columns, site 2c in the real and site 2c + 1
 // in the imaginary part of column c.
@@ -70,10 +113,7 @@ __global__ void __launch_bounds__(256) k_tau_fwd(const R* __restrict__ v,
         const int c = item % TH, tau = item / TH;
         const int i = i0 + 2 * c;          // N is even, so i < N implies i + 1 < N
         R xa = R(0), xb = R(0);
-        if (i < N) {
-            xa = v[base + (long)tau * N + i];
-            xb = v[base + (long)tau * N + i + 1];
-        }
+        if (i < N) ld_pair(v + base + (long)tau * N + i, xa, xb);
         const C2 t = tw<R>(w2, tau, T);    // exp(-i pi tau / T)
         a[tau * TH + c] = Cx<R>::mk(xa * t.x - xb * t.y, xa * t.y + xb * t.x);
     }
@@ -92,8 +132,8 @@ __global__ void __launch_bounds__(256) k_tau_fwd(const R* __restrict__ v,
             const C2 z = res[w * TH + c];
             const C2 zm = res[(T - 1 - w) * TH + c];
             // X_a = (z + conj zm) / 2,  X_b = (z - conj zm) / (2 i)
-            vh[ob + (long)w * N + i] = Cx<R>::mk(hs * (z.x + zm.x), hs * (z.y - zm.y));
-            vh[ob + (long)w * N + i + 1] = Cx<R>::mk(hs * (z.y + zm.y), hs * (zm.x - z.x));
+            st_cpair(vh + ob + (long)w * N + i, Cx<R>::mk(hs * (z.x + zm.x), hs * (z.y - zm.y)),
+                     Cx<R>::mk(hs * (z.y + zm.y), hs * (zm.x - z.x)));
         }
     }
 }
@@ -124,21 +164,19 @@ __global__ void __launch_bounds__(256) k_tau_inv(const typename Cx<R>::T2* __res
     const int i0 = blockIdx.x * TS;
     const int Th = T / 2;
     const long ib = (long)rhs * Th * N;
-    for (int item = threadIdx.x; item < T * TH; item += blockDim.x) {
+    // one load of (Y_a, Y_b)[w] fills rows w and T-1-w of conj Z
+    for (int item = threadIdx.x; item < Th * TH; item += blockDim.x) {
         const int c = item % TH, w = item / TH;
         const int i = i0 + 2 * c;
-        C2 z = Cx<R>::mk(R(0), R(0));
+        C2 lo = Cx<R>::mk(R(0), R(0)), hi = lo;
         if (i < N) {
-            if (w < Th) {          // conj(Y_a + i Y_b)
-                const C2 ya = yh[ib + (long)w * N + i], yb = yh[ib + (long)w * N + i + 1];
-                z = Cx<R>::mk(ya.x - yb.y, -(ya.y + yb.x));
-            } else {               // conj(conj Y_a' + i conj Y_b'), ' = T-1-w
-                const long o = ib + (long)(T - 1 - w) * N + i;
-                const C2 ya = yh[o], yb = yh[o + 1];
-                z = Cx<R>::mk(ya.x + yb.y, ya.y - yb.x);
-            }
+            C2 ya, yb;
+            ld_cpair(yh + ib + (long)w * N + i, ya, yb);
+            lo = Cx<R>::mk(ya.x - yb.y, -(ya.y + yb.x));   // conj(Y_a + i Y_b)
+            hi = Cx<R>::mk(ya.x + yb.y, ya.y - yb.x);      // conj(conj Y_a + i conj Y_b)
         }
-        a[w * TH + c] = z;
+        a[w * TH + c] = lo;
+        a[(T - 1 - w) * TH + c] = hi;
     }
     C2* res;
     if constexpr (TC > 0)
@@ -157,10 +195,14 @@ __global__ void __launch_bounds__(256) k_tau_inv(const typename Cx<R>::T2* __res
             const R ya = hs * (t.x * f.x - t.y * f.y);     // Re(t F) / sqrt T
             const R yb = -hs * (t.x * f.y + t.y * f.x);    // -Im(t F) / sqrt T
             const long o = ob + (long)tau * N + i;
-            y[o] = ya;
-            y[o + 1] = yb;
-            if (rdot != nullptr)
-                acc += (double)ya * (double)rdot[o] + (double)yb * (double)rdot[o + 1];
+            st_pair(y + o, ya, yb);
+            if (rdot != nullptr) {
+                R ra, rb;
+                ld_pair(rdot + o, ra, rb);
+                // the pair's two products in R, accumulated in FP64 (one
+                // conversion and one FP64 add per pair: the FP64 pipe is scarce)
+                acc += (double)fma(ya, ra, yb * rb);
+            }
         }
     }
     if (dot_part != nullptr) {
@@ -911,6 +953,7 @@ extern "C" int precond_apply(hol_ctx* c, int which, int prec, const void* v, voi
                              void* stream)
 {
     if (!c || !v || !out) return set_error(HOL_EINVAL, "precond_apply: null argument");
+    if (int rc_ = require_aligned("precond_apply", {v, out})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "precond_apply: hol_set_field not called");
     if (n_rhs < 1 || n_rhs > c->p.max_rhs)
         return set_error(HOL_EINVAL, "precond_apply: n_rhs=%d outside [1, %d]", n_rhs,

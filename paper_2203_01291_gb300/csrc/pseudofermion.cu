@@ -58,6 +58,7 @@ using namespace hol;
 extern "C" int pseudofermion_phi(hol_ctx* c, const double* R, double* Phi, int n_pf, void* stream)
 {
     if (!c || !R || !Phi) return set_error(HOL_EINVAL, "pseudofermion_phi: null argument");
+    if (int rc_ = require_aligned("pseudofermion_phi", {R, Phi})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "pseudofermion_phi: hol_set_field not called");
     if (n_pf < 1 || n_pf > c->p.max_rhs)
         return set_error(HOL_EINVAL, "pseudofermion_phi: n_pf=%d outside [1, %d]", n_pf,
@@ -71,6 +72,7 @@ extern "C" int pseudofermion_phi(hol_ctx* c, const double* R, double* Phi, int n
 extern "C" int phi_to_rhs(hol_ctx* c, const double* Phi, double* b, int n_pf, void* stream)
 {
     if (!c || !Phi || !b) return set_error(HOL_EINVAL, "phi_to_rhs: null argument");
+    if (int rc_ = require_aligned("phi_to_rhs", {Phi, b})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "phi_to_rhs: hol_set_field not called");
     if (n_pf < 1 || n_pf > c->p.max_rhs)
         return set_error(HOL_EINVAL, "phi_to_rhs: n_pf=%d outside [1, %d]", n_pf, c->p.max_rhs);

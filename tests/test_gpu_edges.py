@@ -187,3 +187,38 @@ def test_trajectory_measurement_and_moves_on_the_shortest_tau_axis(T):
             assert abs(dS - dS_o) < 1e-8 * D.action(m, x0, Phi)
             if abs(np.log(0.5) + dS_o) > 1e-6:
                 assert a_ == a_o
+
+
+def test_misaligned_device_vectors_are_refused_on_the_host():
+    """A device vector that is not 16-byte aligned (a view one element into an
+    allocation) is refused with HOL_EINVAL before anything is launched."""
+    w = hi.Workload("e", L=8, Ltau=8, seed=14)
+    x = hi.phonon_field(w)
+    n = w.n
+    with _ctx(w, 1) as ctx:
+        raw = torch.zeros(n + 1, dtype=torch.float64, device=DEV)
+        bad = raw[1:].view(1, w.Ltau, w.N)                 # 8 bytes past a 256-byte boundary
+        good = torch.zeros(1, w.Ltau, w.N, dtype=torch.float64, device=DEV)
+        with pytest.raises(hg.HolError) as e:
+            ctx.set_field(raw[1:].view(w.Ltau, w.N))
+        assert e.value.code == hg._abi.HOL_EINVAL
+        ctx.set_field(torch.tensor(x, device=DEV))
+        calls = [lambda: ctx.fermion_matvec(hg.HOL_OP_M, bad, good),
+                 lambda: ctx.fermion_matvec(hg.HOL_OP_M, good, bad),
+                 lambda: ctx.precond_apply(hg.HOL_PINV, bad, good),
+                 lambda: ctx.cg_solve(bad, good, tol=1e-8),
+                 lambda: ctx.force(good, bad, torch.empty(w.Ltau, w.N, dtype=torch.float64,
+                                                          device=DEV))]
+        for call in calls:
+            with pytest.raises(hg.HolError) as e:
+                call()
+            assert e.value.code == hg._abi.HOL_EINVAL
+        raw32 = torch.zeros(n + 2, dtype=torch.float32, device=DEV)
+        bad32 = raw32[2:].view(1, w.Ltau, w.N)             # 8 bytes off: float4 loads would fault
+        good32 = torch.zeros(1, w.Ltau, w.N, dtype=torch.float32, device=DEV)
+        with pytest.raises(hg.HolError):
+            ctx.fermion_matvec(hg.HOL_OP_MTM, bad32, good32)
+        # the context is still usable
+        out = torch.empty_like(good)
+        ctx.fermion_matvec(hg.HOL_OP_M, good, out)
+        torch.cuda.synchronize()
