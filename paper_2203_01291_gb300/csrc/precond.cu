@@ -625,8 +625,13 @@ __global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
     const double db = bmax - bmin;
     const float a = (float)(2.0 / db), c0 = (float)(-2.0 * bmin / db - 1.0);
     const int np = npv[wq];
-    extern __shared__ double2 cw[];   // this omega's coefficients
-    for (int m = threadIdx.x; m < np; m += blockDim.x) cw[m] = coef[(long)wq * max_np + m];
+    // this omega's coefficients, rounded to FP32 once (no conversion on the
+    // chain of dependent steps)
+    extern __shared__ float2 cw[];
+    for (int m = threadIdx.x; m < np; m += blockDim.x) {
+        const double2 c = coef[(long)wq * max_np + m];
+        cw[m] = make_float2((float)c.x, (float)c.y);
+    }
     __syncthreads();
     int par = 0;
     for (int pass = 0; pass < 2; ++pass) {
@@ -636,8 +641,8 @@ __global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
         const float sgn = trans ? -1.0f : 1.0f;    // conj coefficients for the transpose
         CV<CPL> acc[2], prev[2];
         {
-            const double2 c = cw[0];
-            const float cr = (float)c.x, ci = sgn * (float)c.y;
+            const float2 c = cw[0];
+            const float cr = c.x, ci = sgn * c.y;
 #pragma unroll
             for (int r = 0; r < 2; ++r) {
                 prev[r] = cur[r];
@@ -674,8 +679,8 @@ __global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
                 kc4<L, CPL>(b, g, th, xbuf, par);
             }
             par ^= 1;
-            const double2 c = cw[m];
-            const float cr = (float)c.x, ci = sgn * (float)c.y;
+            const float2 c = cw[m];
+            const float cr = c.x, ci = sgn * c.y;
             // alpha_m = (m == 1 ? 1 : 2) (a B + c0) alpha_{m-1} - (m == 1 ? 0 : alpha_{m-2})
             const float f2 = (m == 1) ? 1.0f : 2.0f;
             const float pm = (m == 1) ? 0.0f : 1.0f;
@@ -851,7 +856,7 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     if constexpr (sizeof(R) == 4) {
         if (c->kpm_reg && !c->exact && (c->L == 32 || c->L == 16)) {
             const float th = (float)c->th;
-            const size_t csm = (size_t)ka.max_np * sizeof(double2);
+            const size_t csm = (size_t)ka.max_np * sizeof(float2);
             const float2* i2 = reinterpret_cast<const float2*>(h0);
             float2* o2 = reinterpret_cast<float2*>(h1);
             auto run = [&](auto kern, int threads) -> int {
