@@ -99,6 +99,8 @@ __global__ void __launch_bounds__(256) k_tau_fwd(const R* __restrict__ v,
                                                  const typename Cx<R>::T2* __restrict__ w2, int T_,
                                                  int N, int TS_, RadixPlan plan, R scale)
 {
+    pdl_wait();      // the input comes from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     using C2 = typename Cx<R>::T2;
     const int T = TC > 0 ? TC : T_;
     const int TS = TSC > 0 ? TSC : TS_;
@@ -153,6 +155,8 @@ __global__ void __launch_bounds__(256) k_tau_inv(const typename Cx<R>::T2* __res
                                                  const R* __restrict__ rdot,
                                                  double* __restrict__ dot_part)
 {
+    pdl_wait();      // the input comes from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     using C2 = typename Cx<R>::T2;
     const int T = TC > 0 ? TC : T_;
     const int TS = TSC > 0 ? TSC : TS_;
@@ -417,6 +421,8 @@ __global__ void __launch_bounds__(256) k_kpm(const typename Cx<R>::T2* __restric
                                              const double2* __restrict__ coef, int n_rhs,
                                              KpmArgs ka)
 {
+    pdl_wait();      // the input comes from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     using C2 = typename Cx<R>::T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2* cur = reinterpret_cast<C2*>(smem_raw);
@@ -598,6 +604,8 @@ __global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
               const int* __restrict__ npv, const double2* __restrict__ coef, int n_rhs, int Th,
               int max_np, int mode, float th)
 {
+    pdl_wait();      // the input comes from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     using G = KGeo<L, CPL>;
     __shared__ float xbuf[G::W > 1 ? 2 * G::W * 2 * G::LR * 2 * CPL : 1];
     const G g;
@@ -840,7 +848,7 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     if ((rc = set_smem_attr<R>((const void*)fwd, sm))) return rc;
     if ((rc = set_smem_attr<R>((const void*)inv, sm))) return rc;
     const R isq = (R)(1.0 / sqrt((double)c->T));
-    fwd<<<gf, 256, sm, s>>>(v, h0, w2, c->T, c->N, TS, plan, isq);
+    HOL_CUDA(launch_pdl(c, fwd, gf, 256, sm, s, v, h0, w2, c->T, c->N, TS, plan, isq));
     HOL_CHECK_LAUNCH("k_tau_fwd");
     KpmArgs ka;
     ka.L = c->L;
@@ -861,9 +869,9 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
             float2* o2 = reinterpret_cast<float2*>(h1);
             auto run = [&](auto kern, int threads) -> int {
                 if (int e = set_smem_attr<R>((const void*)kern, csm)) return e;
-                kern<<<ka.Th * n_rhs, threads, csm, s>>>(i2, o2, c->dbar, c->scal, c->kpm.np,
-                                                         c->kpm.coef, n_rhs, ka.Th, ka.max_np,
-                                                         mode, th);
+                HOL_CUDA(launch_pdl(c, kern, ka.Th * n_rhs, threads, csm, s, i2, o2, c->dbar,
+                                    c->scal, c->kpm.np, c->kpm.coef, n_rhs, ka.Th, ka.max_np,
+                                    mode, th));
                 return HOL_OK;
             };
             const bool two = c->kpm_reg == 2;   // two columns per lane
@@ -883,11 +891,12 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
         const size_t ks = ((size_t)c->N * sizeof(C2) * (c->exact ? 2 : 1) + 15) / 16 * 16 +
                           (size_t)ka.max_np * sizeof(double2);
         if ((rc = set_smem_attr<R>((const void*)k_kpm<R>, ks))) return rc;
-        k_kpm<R><<<ka.Th * n_rhs, kt, ks, s>>>(h0, h1, c->dbar, c->scal, c->kpm.np, c->kpm.coef,
-                                               n_rhs, ka);
+        HOL_CUDA(launch_pdl(c, k_kpm<R>, ka.Th * n_rhs, kt, ks, s, h0, h1, c->dbar, c->scal,
+                            c->kpm.np, c->kpm.coef, n_rhs, ka));
         HOL_CHECK_LAUNCH("k_kpm");
     }
-    inv<<<gf, 256, sm, s>>>(h1, out, w2, c->T, c->N, TS, plan, (R)2 * isq, rdot, dot_part);
+    HOL_CUDA(launch_pdl(c, inv, gf, 256, sm, s, h1, out, w2, c->T, c->N, TS, plan, (R)2 * isq,
+                        rdot, dot_part));
     HOL_CHECK_LAUNCH("k_tau_inv");
     return HOL_OK;
 }
