@@ -178,6 +178,8 @@ __global__ void __launch_bounds__(256) k_cg_init(const double* __restrict__ b, R
 __global__ void __launch_bounds__(256) k_fold(double* __restrict__ v, float* __restrict__ e, long n,
                                               const int* __restrict__ mask)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     const int rhs = blockIdx.y;
     if (mask[rhs] == 0) return;
     const long base = (long)rhs * n;
@@ -204,6 +206,8 @@ __global__ void __launch_bounds__(256) k_recast(const double* rt, R* r, long n,
                                                 double* __restrict__ tr_out,
                                                 double* __restrict__ rr_out)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     const int rhs = blockIdx.y;
     if (mask[rhs] == 0) return;
     const long base = (long)rhs * n;
@@ -282,6 +286,8 @@ __global__ void __launch_bounds__(256) k_conj_dots(const R* __restrict__ z, cons
                                                    double* __restrict__ zq_out,
                                                    double* __restrict__ pq_out)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     const int rhs = blockIdx.y;
     if (mask[rhs] == 0) return;
     const long base = (long)rhs * n;
@@ -316,6 +322,8 @@ __global__ void __launch_bounds__(256) k_conj_scale(R* __restrict__ p, long n,
                                                     const double* __restrict__ zq_part,
                                                     const double* __restrict__ pq_part, int cnt)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     const int rhs = blockIdx.y;
     if (mask[rhs] == 0) return;
     __shared__ double s_beta;
@@ -342,6 +350,8 @@ __global__ void __launch_bounds__(256) k_conj_scale(R* __restrict__ p, long n,
 __global__ void k_copy_rows(const double* __restrict__ src, double* __restrict__ dst,
                             const int* __restrict__ mask)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     const int rhs = blockIdx.x;
     if (mask[rhs] == 0) return;
     for (int k = threadIdx.x; k < kRedStride; k += blockDim.x)
@@ -640,15 +650,15 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
         // reliable update / convergence certification for the flagged rhs
         HOL_CUDA(cudaMemcpyAsync(rel_d, rel_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
         if (mixed) {
-            k_fold<<<g2, 256, 0, s>>>(v, e32, n, rel_d);
+            HOL_CUDA(launch_pdl(c, k_fold, g2, 256, 0, s, v, e32, n, rel_d));
             HOL_CHECK_LAUNCH("k_fold");
             if ((rc = launch_M(c, HOL_F64, v, t64, n_rhs, rel_d, nullptr, s))) return rc;
             if ((rc = launch_MT_resid64(c, t64, b, rt64, n_rhs, rel_d, s))) return rc;
-            k_recast<float><<<g2, 256, 0, s>>>(rt64, r32, n, rel_d, B.tr, est_bank(cur));
+            HOL_CUDA(launch_pdl(c, k_recast<float>, g2, 256, 0, s, rt64, r32, n, rel_d, B.tr, est_bank(cur)));
         } else {
             if ((rc = launch_M(c, HOL_F64, v, w64, n_rhs, rel_d, nullptr, s))) return rc;
             if ((rc = launch_MT_resid64(c, w64, b, r64, n_rhs, rel_d, s))) return rc;
-            k_recast<double><<<g2, 256, 0, s>>>(r64, r64, n, rel_d, B.tr, est_bank(cur));
+            HOL_CUDA(launch_pdl(c, k_recast<double>, g2, 256, 0, s, r64, r64, n, rel_d, B.tr, est_bank(cur)));
         }
         HOL_CHECK_LAUNCH("k_recast");
         if (!pc) cnt[cur] = nb2;   // k_recast wrote block partials into the current bank
@@ -668,16 +678,16 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                     (rc = launch_cg_mtm32(c, p32[pp], p32[pp], nullptr, q32, n_rhs, rel_d, nullptr,
                                           nullptr, 0, 0, 1, nullptr, s)))
                     return rc;
-                k_conj_dots<float><<<g2, 256, 0, s>>>(z32, p32[pp], q32, n, rel_d, cj0, cj1);
+                HOL_CUDA(launch_pdl(c, k_conj_dots<float>, g2, 256, 0, s, z32, p32[pp], q32, n, rel_d, cj0, cj1));
                 HOL_CHECK_LAUNCH("k_conj_dots");
-                k_conj_scale<float><<<g2, 256, 0, s>>>(p32[pp], n, rel_d, cj0, cj1, nb2);
+                HOL_CUDA(launch_pdl(c, k_conj_scale<float>, g2, 256, 0, s, p32[pp], n, rel_d, cj0, cj1, nb2));
             } else {
-                k_conj_dots<double><<<g2, 256, 0, s>>>(z64, p64[pp], q64, n, rel_d, cj0, cj1);
+                HOL_CUDA(launch_pdl(c, k_conj_dots<double>, g2, 256, 0, s, z64, p64[pp], q64, n, rel_d, cj0, cj1));
                 HOL_CHECK_LAUNCH("k_conj_dots");
-                k_conj_scale<double><<<g2, 256, 0, s>>>(p64[pp], n, rel_d, cj0, cj1, nb2);
+                HOL_CUDA(launch_pdl(c, k_conj_scale<double>, g2, 256, 0, s, p64[pp], n, rel_d, cj0, cj1, nb2));
             }
             HOL_CHECK_LAUNCH("k_conj_scale");
-            k_copy_rows<<<n_rhs, 256, 0, s>>>(B.dz[cur], B.dz[1 - cur], rel_d);
+            HOL_CUDA(launch_pdl(c, k_copy_rows, n_rhs, 256, 0, s, B.dz[cur], B.dz[1 - cur], rel_d));
             HOL_CHECK_LAUNCH("k_copy_rows");
             cnt[1 - cur] = cnt[cur];
         }
@@ -850,11 +860,11 @@ static int cg_run_fused(hol_ctx* c, const double* b, double* v, int n_rhs, const
         if (n_rel == 0) continue;
         const int z = 1 - a;
         HOL_CUDA(cudaMemcpyAsync(rel_d, rel_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
-        k_fold<<<g2, 256, 0, s>>>(v, X, n, rel_d);
+        HOL_CUDA(launch_pdl(c, k_fold, g2, 256, 0, s, v, X, n, rel_d));
         HOL_CHECK_LAUNCH("k_fold");
         if ((rc = launch_M(c, HOL_F64, v, t64, n_rhs, rel_d, nullptr, s))) return rc;
         if ((rc = launch_MT_resid64(c, t64, b, rt64, n_rhs, rel_d, s))) return rc;
-        k_recast<float><<<g2, 256, 0, s>>>(rt64, Rv[a], n, rel_d, B.tr, cj1);
+        HOL_CUDA(launch_pdl(c, k_recast<float>, g2, 256, 0, s, rt64, Rv[a], n, rel_d, B.tr, cj1));
         HOL_CHECK_LAUNCH("k_recast");
         // The stored p (parity a) already contains the old r; the direction
         // the last pass stepped along, p_prev with q_prev = A p_prev, is still
@@ -862,9 +872,9 @@ static int cg_run_fused(hol_ctx* c, const double* b, double* v, int n_rhs, const
         // beta = -(r, q_prev) / (p_prev, q_prev) (p_prev is scaled by beta,
         // then p = r + p_prev from identical partial rows), q = A p and its
         // p.q partials, written to parity a; then the r.r, r.q, q.q partials.
-        k_conj_dots<float><<<g2, 256, 0, s>>>(Rv[a], Pv[z], Qv[z], n, rel_d, cj0, cj1);
+        HOL_CUDA(launch_pdl(c, k_conj_dots<float>, g2, 256, 0, s, Rv[a], Pv[z], Qv[z], n, rel_d, cj0, cj1));
         HOL_CHECK_LAUNCH("k_conj_dots");
-        k_conj_scale<float><<<g2, 256, 0, s>>>(Pv[z], n, rel_d, cj0, cj1, nb2);
+        HOL_CUDA(launch_pdl(c, k_conj_scale<float>, g2, 256, 0, s, Pv[z], n, rel_d, cj0, cj1, nb2));
         HOL_CHECK_LAUNCH("k_conj_scale");
         if ((rc = launch_cg_mtm32(c, Rv[a], Pv[z], Pv[a], Qv[a], n_rhs, rel_d, B.tr, B.tr,
                                   kRedStride, nb2, 0, PQ[a], s)))
@@ -1026,11 +1036,11 @@ static int cg_run_merged(hol_ctx* c, const double* b, double* v, int n_rhs, cons
         }
         if (n_rel == 0) continue;
         HOL_CUDA(cudaMemcpyAsync(rel_d, rel_h, n_rhs * sizeof(int), cudaMemcpyHostToDevice, s));
-        k_fold<<<g2, 256, 0, s>>>(v, e, n, rel_d);
+        HOL_CUDA(launch_pdl(c, k_fold, g2, 256, 0, s, v, e, n, rel_d));
         HOL_CHECK_LAUNCH("k_fold");
         if ((rc = launch_M(c, HOL_F64, v, t64, n_rhs, rel_d, nullptr, s))) return rc;
         if ((rc = launch_MT_resid64(c, t64, b, rt64, n_rhs, rel_d, s))) return rc;
-        k_recast<float><<<g2, 256, 0, s>>>(rt64, R[a], n, rel_d, B.tr, Gr);
+        HOL_CUDA(launch_pdl(c, k_recast<float>, g2, 256, 0, s, rt64, R[a], n, rel_d, B.tr, Gr));
         HOL_CHECK_LAUNCH("k_recast");
         // w = A r for the new r, s_old = A p_old, rho = r.s_old
         if ((rc = launch_cg_mtm32(c, R[a], R[a], nullptr, W[a], n_rhs, rel_d, nullptr, nullptr, 0,

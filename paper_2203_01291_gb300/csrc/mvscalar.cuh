@@ -55,6 +55,8 @@ __global__ void __launch_bounds__(128) k_M(const R* __restrict__ v, const R* __r
                                            const int* __restrict__ mask, BetaSrc bsrc,
                                            double* __restrict__ norm_part, Kin<R> kin)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     constexpr int N = L * L;
     const LaneGeom<L> geo;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -120,6 +122,8 @@ __global__ void __launch_bounds__(128) k_MT(const R* __restrict__ u, const R* __
                                             R* __restrict__ out, const R* __restrict__ ev,
                                             MvGeom gm, const int* __restrict__ mask, Kin<R> kin)
 {
+    pdl_wait();      // inputs may come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
     constexpr int N = L * L;
     const LaneGeom<L> geo;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -266,12 +270,9 @@ int run_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs, const
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     if (prec == HOL_F64)
-        k_M<double, L, false, EX><<<nb, nt, 0, s>>>((const double*)v, nullptr, nullptr, (double*)out,
-                                                c->ev64, g, mask, BetaSrc{}, norm_part, kin_of<double>(c));
+        HOL_CUDA(launch_pdl(c, k_M<double, L, false, EX>, nb, nt, 0, s, (const double*)v, nullptr, nullptr, (double*)out, c->ev64, g, mask, BetaSrc{}, norm_part, kin_of<double>(c)));
     else
-        k_M<float, L, false, EX><<<nb, nt, 0, s>>>((const float*)v, nullptr, nullptr, (float*)out,
-                                               c->ev32, g, mask, BetaSrc{}, norm_part,
-                                               kin_of<float>(c));
+        HOL_CUDA(launch_pdl(c, k_M<float, L, false, EX>, nb, nt, 0, s, (const float*)v, nullptr, nullptr, (float*)out, c->ev32, g, mask, BetaSrc{}, norm_part, kin_of<float>(c)));
     HOL_CHECK_LAUNCH("k_M");
     return HOL_OK;
 }
@@ -282,8 +283,7 @@ int run_M_upd64(const hol_ctx* c, const double* r, const double* pold, double* p
 {
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-    k_M<double, L, true, EX><<<nb, nt, 0, s>>>(r, pold, pnew, w, c->ev64, g, mask, beta, norm_part,
-                                           kin_of<double>(c));
+    HOL_CUDA(launch_pdl(c, k_M<double, L, true, EX>, nb, nt, 0, s, r, pold, pnew, w, c->ev64, g, mask, beta, norm_part, kin_of<double>(c)));
     HOL_CHECK_LAUNCH("k_M upd");
     return HOL_OK;
 }
@@ -295,11 +295,9 @@ int run_MT(const hol_ctx* c, int prec, const void* u, void* out, int n_rhs, cons
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     if (prec == HOL_F64)
-        k_MT<double, L, MT_PLAIN, EX><<<nb, nt, 0, s>>>((const double*)u, nullptr, (double*)out,
-                                                    c->ev64, g, mask, kin_of<double>(c));
+        HOL_CUDA(launch_pdl(c, k_MT<double, L, MT_PLAIN, EX>, nb, nt, 0, s, (const double*)u, nullptr, (double*)out, c->ev64, g, mask, kin_of<double>(c)));
     else
-        k_MT<float, L, MT_PLAIN, EX><<<nb, nt, 0, s>>>((const float*)u, nullptr, (float*)out, c->ev32,
-                                                   g, mask, kin_of<float>(c));
+        HOL_CUDA(launch_pdl(c, k_MT<float, L, MT_PLAIN, EX>, nb, nt, 0, s, (const float*)u, nullptr, (float*)out, c->ev32, g, mask, kin_of<float>(c)));
     HOL_CHECK_LAUNCH("k_MT");
     return HOL_OK;
 }
@@ -310,7 +308,7 @@ int run_MT_resid(const hol_ctx* c, const double* u, const double* b, double* out
 {
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-    k_MT<double, L, MT_RESID, EX><<<nb, nt, 0, s>>>(u, b, out, c->ev64, g, mask, kin_of<double>(c));
+    HOL_CUDA(launch_pdl(c, k_MT<double, L, MT_RESID, EX>, nb, nt, 0, s, u, b, out, c->ev64, g, mask, kin_of<double>(c)));
     HOL_CHECK_LAUNCH("k_MT resid");
     return HOL_OK;
 }
