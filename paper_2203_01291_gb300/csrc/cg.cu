@@ -654,11 +654,13 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
             HOL_CHECK_LAUNCH("k_fold");
             if ((rc = launch_M(c, HOL_F64, v, t64, n_rhs, rel_d, nullptr, s))) return rc;
             if ((rc = launch_MT_resid64(c, t64, b, rt64, n_rhs, rel_d, s))) return rc;
-            HOL_CUDA(launch_pdl(c, k_recast<float>, g2, 256, 0, s, rt64, r32, n, rel_d, B.tr, est_bank(cur)));
+            HOL_CUDA(launch_pdl(c, k_recast<float>, g2, 256, 0, s, rt64, r32, n, rel_d, B.tr,
+                                est_bank(cur)));
         } else {
             if ((rc = launch_M(c, HOL_F64, v, w64, n_rhs, rel_d, nullptr, s))) return rc;
             if ((rc = launch_MT_resid64(c, w64, b, r64, n_rhs, rel_d, s))) return rc;
-            HOL_CUDA(launch_pdl(c, k_recast<double>, g2, 256, 0, s, r64, r64, n, rel_d, B.tr, est_bank(cur)));
+            HOL_CUDA(launch_pdl(c, k_recast<double>, g2, 256, 0, s, r64, r64, n, rel_d, B.tr,
+                                est_bank(cur)));
         }
         HOL_CHECK_LAUNCH("k_recast");
         if (!pc) cnt[cur] = nb2;   // k_recast wrote block partials into the current bank
@@ -678,13 +680,17 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                     (rc = launch_cg_mtm32(c, p32[pp], p32[pp], nullptr, q32, n_rhs, rel_d, nullptr,
                                           nullptr, 0, 0, 1, nullptr, s)))
                     return rc;
-                HOL_CUDA(launch_pdl(c, k_conj_dots<float>, g2, 256, 0, s, z32, p32[pp], q32, n, rel_d, cj0, cj1));
+                HOL_CUDA(launch_pdl(c, k_conj_dots<float>, g2, 256, 0, s, z32, p32[pp], q32, n,
+                                    rel_d, cj0, cj1));
                 HOL_CHECK_LAUNCH("k_conj_dots");
-                HOL_CUDA(launch_pdl(c, k_conj_scale<float>, g2, 256, 0, s, p32[pp], n, rel_d, cj0, cj1, nb2));
+                HOL_CUDA(launch_pdl(c, k_conj_scale<float>, g2, 256, 0, s, p32[pp], n, rel_d, cj0,
+                                    cj1, nb2));
             } else {
-                HOL_CUDA(launch_pdl(c, k_conj_dots<double>, g2, 256, 0, s, z64, p64[pp], q64, n, rel_d, cj0, cj1));
+                HOL_CUDA(launch_pdl(c, k_conj_dots<double>, g2, 256, 0, s, z64, p64[pp], q64, n,
+                                    rel_d, cj0, cj1));
                 HOL_CHECK_LAUNCH("k_conj_dots");
-                HOL_CUDA(launch_pdl(c, k_conj_scale<double>, g2, 256, 0, s, p64[pp], n, rel_d, cj0, cj1, nb2));
+                HOL_CUDA(launch_pdl(c, k_conj_scale<double>, g2, 256, 0, s, p64[pp], n, rel_d, cj0,
+                                    cj1, nb2));
             }
             HOL_CHECK_LAUNCH("k_conj_scale");
             HOL_CUDA(launch_pdl(c, k_copy_rows, n_rhs, 256, 0, s, B.dz[cur], B.dz[1 - cur], rel_d));
@@ -872,7 +878,8 @@ static int cg_run_fused(hol_ctx* c, const double* b, double* v, int n_rhs, const
         // beta = -(r, q_prev) / (p_prev, q_prev) (p_prev is scaled by beta,
         // then p = r + p_prev from identical partial rows), q = A p and its
         // p.q partials, written to parity a; then the r.r, r.q, q.q partials.
-        HOL_CUDA(launch_pdl(c, k_conj_dots<float>, g2, 256, 0, s, Rv[a], Pv[z], Qv[z], n, rel_d, cj0, cj1));
+        HOL_CUDA(launch_pdl(c, k_conj_dots<float>, g2, 256, 0, s, Rv[a], Pv[z], Qv[z], n, rel_d,
+                            cj0, cj1));
         HOL_CHECK_LAUNCH("k_conj_dots");
         HOL_CUDA(launch_pdl(c, k_conj_scale<float>, g2, 256, 0, s, Pv[z], n, rel_d, cj0, cj1, nb2));
         HOL_CHECK_LAUNCH("k_conj_scale");

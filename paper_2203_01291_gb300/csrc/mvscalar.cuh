@@ -270,9 +270,13 @@ int run_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs, const
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     if (prec == HOL_F64)
-        HOL_CUDA(launch_pdl(c, k_M<double, L, false, EX>, nb, nt, 0, s, (const double*)v, nullptr, nullptr, (double*)out, c->ev64, g, mask, BetaSrc{}, norm_part, kin_of<double>(c)));
+        HOL_CUDA(launch_pdl(c, k_M<double, L, false, EX>, nb, nt, 0, s, (const double*)v,
+                            nullptr, nullptr, (double*)out, c->ev64, g, mask, BetaSrc{},
+                            norm_part, kin_of<double>(c)));
     else
-        HOL_CUDA(launch_pdl(c, k_M<float, L, false, EX>, nb, nt, 0, s, (const float*)v, nullptr, nullptr, (float*)out, c->ev32, g, mask, BetaSrc{}, norm_part, kin_of<float>(c)));
+        HOL_CUDA(launch_pdl(c, k_M<float, L, false, EX>, nb, nt, 0, s, (const float*)v, nullptr,
+                            nullptr, (float*)out, c->ev32, g, mask, BetaSrc{}, norm_part,
+                            kin_of<float>(c)));
     HOL_CHECK_LAUNCH("k_M");
     return HOL_OK;
 }
@@ -283,7 +287,8 @@ int run_M_upd64(const hol_ctx* c, const double* r, const double* pold, double* p
 {
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-    HOL_CUDA(launch_pdl(c, k_M<double, L, true, EX>, nb, nt, 0, s, r, pold, pnew, w, c->ev64, g, mask, beta, norm_part, kin_of<double>(c)));
+    HOL_CUDA(launch_pdl(c, k_M<double, L, true, EX>, nb, nt, 0, s, r, pold, pnew, w, c->ev64, g,
+                        mask, beta, norm_part, kin_of<double>(c)));
     HOL_CHECK_LAUNCH("k_M upd");
     return HOL_OK;
 }
@@ -295,9 +300,11 @@ int run_MT(const hol_ctx* c, int prec, const void* u, void* out, int n_rhs, cons
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     if (prec == HOL_F64)
-        HOL_CUDA(launch_pdl(c, k_MT<double, L, MT_PLAIN, EX>, nb, nt, 0, s, (const double*)u, nullptr, (double*)out, c->ev64, g, mask, kin_of<double>(c)));
+        HOL_CUDA(launch_pdl(c, k_MT<double, L, MT_PLAIN, EX>, nb, nt, 0, s, (const double*)u,
+                            nullptr, (double*)out, c->ev64, g, mask, kin_of<double>(c)));
     else
-        HOL_CUDA(launch_pdl(c, k_MT<float, L, MT_PLAIN, EX>, nb, nt, 0, s, (const float*)u, nullptr, (float*)out, c->ev32, g, mask, kin_of<float>(c)));
+        HOL_CUDA(launch_pdl(c, k_MT<float, L, MT_PLAIN, EX>, nb, nt, 0, s, (const float*)u,
+                            nullptr, (float*)out, c->ev32, g, mask, kin_of<float>(c)));
     HOL_CHECK_LAUNCH("k_MT");
     return HOL_OK;
 }
@@ -308,7 +315,8 @@ int run_MT_resid(const hol_ctx* c, const double* u, const double* b, double* out
 {
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-    HOL_CUDA(launch_pdl(c, k_MT<double, L, MT_RESID, EX>, nb, nt, 0, s, u, b, out, c->ev64, g, mask, kin_of<double>(c)));
+    HOL_CUDA(launch_pdl(c, k_MT<double, L, MT_RESID, EX>, nb, nt, 0, s, u, b, out, c->ev64, g,
+                        mask, kin_of<double>(c)));
     HOL_CHECK_LAUNCH("k_MT resid");
     return HOL_OK;
 }
