@@ -246,6 +246,7 @@ using namespace hol;
 extern "C" int hol_arnoldi_bounds(hol_ctx* c, const double* v0, int m, double margin, int install,
                                   double* bmin, double* bmax, int* steps, void* stream)
 {
+    HOL_TRACE("hol_arnoldi_bounds");
     if (!c || !v0) return set_error(HOL_EINVAL, "hol_arnoldi_bounds: null argument");
     if (int rc_ = require_aligned("hol_arnoldi_bounds", {v0})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "hol_arnoldi_bounds: hol_set_field not called");
@@ -310,6 +311,7 @@ extern "C" int hol_arnoldi_bounds(hol_ctx* c, const double* v0, int m, double ma
 
 extern "C" int hol_get_bounds(hol_ctx* c, double* bmin, double* bmax, void* stream)
 {
+    HOL_TRACE("hol_get_bounds");
     if (!c || !bmin || !bmax) return set_error(HOL_EINVAL, "hol_get_bounds: null argument");
     if (!c->field_set) return set_error(HOL_EINVAL, "hol_get_bounds: hol_set_field not called");
     cudaStream_t s = (cudaStream_t)stream;

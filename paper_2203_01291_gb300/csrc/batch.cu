@@ -70,6 +70,7 @@ extern "C" int hmc_batch(hol_ctx* const* ctxs, int n_chains, double* const* x,
                          const hol_md_opts* opts, const double* u, int* accepted, double* dH,
                          int n_threads)
 {
+    HOL_TRACE("hmc_batch");
     if (!ctxs || !x || !R_pf || !R_p || !opts || !u || n_chains < 1)
         return set_error(HOL_EINVAL, "hmc_batch: bad argument");
     for (int k = 0; k < n_chains; ++k)
@@ -90,6 +91,7 @@ extern "C" int measure_batch(hol_ctx* const* ctxs, int n_chains, const double* c
                              const hol_cg_opts* opts, double* const* Gxi, double* const* G2,
                              double* const* G4, int four_point, int n_threads)
 {
+    HOL_TRACE("measure_batch");
     if (!ctxs || !xi || !opts || !Gxi || !G2 || n_chains < 1)
         return set_error(HOL_EINVAL, "measure_batch: bad argument");
     return run_pool(n_chains, n_threads, [&](int k, cudaStream_t s) {

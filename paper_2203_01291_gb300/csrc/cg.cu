@@ -1097,6 +1097,7 @@ using namespace hol;
 extern "C" int cg_solve(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_opts* o,
                         int* iters, double* resid, void* stream)
 {
+    HOL_TRACE("cg_solve");
     if (!c || !b || !v || !o) return set_error(HOL_EINVAL, "cg_solve: null argument");
     if (int rc_ = require_aligned("cg_solve", {b, v})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "cg_solve: hol_set_field not called");

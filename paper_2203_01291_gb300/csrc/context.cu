@@ -223,6 +223,7 @@ static void exact_taps(hol_ctx* c)
 
 extern "C" int hol_create(const hol_params* p, hol_ctx** out)
 {
+    HOL_TRACE("hol_create");
     if (!p || !out) return set_error(HOL_EINVAL, "hol_create: null argument");
     *out = nullptr;
     if (p->L < 4 || p->L > kMaxL || (p->L & 1))
@@ -343,6 +344,7 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
 
 extern "C" int hol_destroy(hol_ctx* c)
 {
+    HOL_TRACE("hol_destroy");
     if (!c) return HOL_OK;
     cudaDeviceSynchronize();
     free_ctx(c);
@@ -351,6 +353,7 @@ extern "C" int hol_destroy(hol_ctx* c)
 
 extern "C" int hol_set_field(hol_ctx* c, const double* x, void* stream)
 {
+    HOL_TRACE("hol_set_field");
     if (!c || !x) return set_error(HOL_EINVAL, "hol_set_field: null argument");
     if (int rc_ = require_aligned("hol_set_field", {x})) return rc_;
     cudaStream_t s = (cudaStream_t)stream;
@@ -372,6 +375,7 @@ extern "C" int hol_set_field(hol_ctx* c, const double* x, void* stream)
 extern "C" int fermion_matvec(hol_ctx* c, int op, int prec, const void* v, void* out, int n_rhs,
                               void* stream)
 {
+    HOL_TRACE("fermion_matvec");
     if (!c || !v || !out) return set_error(HOL_EINVAL, "fermion_matvec: null argument");
     if (int rc_ = require_aligned("fermion_matvec", {v, out})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "fermion_matvec: hol_set_field not called");
@@ -404,6 +408,7 @@ extern "C" unsigned long long hol_launch_count(void) { return __atomic_load_n(&g
 
 extern "C" int hol_timer_enable(hol_ctx* c, int on)
 {
+    HOL_TRACE("hol_timer_enable");
     if (!c) return set_error(HOL_EINVAL, "hol_timer_enable: null context");
     if (on && !c->timer) {
         KTimer* t = (KTimer*)calloc(1, sizeof(KTimer));
@@ -440,6 +445,7 @@ extern "C" int hol_timer_enable(hol_ctx* c, int on)
 extern "C" int hol_timer_read(hol_ctx* c, int klass, int* count, double* total_ms,
                               double* units)
 {
+    HOL_TRACE("hol_timer_read");
     if (!c || !count || !total_ms || klass < 0 || klass >= KT_COUNT)
         return set_error(HOL_EINVAL, "hol_timer_read: bad argument");
     *count = 0;
@@ -478,6 +484,7 @@ static int alloc_extra_vectors(hol_ctx* c)
 
 extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
 {
+    HOL_TRACE("hol_set_option");
     if (!c || !name) return set_error(HOL_EINVAL, "hol_set_option: null argument");
     auto is = [&](const char* s) { return strcmp(name, s) == 0; };
     if (is("slices_per_group")) {
@@ -534,6 +541,7 @@ extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
 
 extern "C" int hol_get_option(const hol_ctx* c, const char* name, int* value)
 {
+    HOL_TRACE("hol_get_option");
     if (!c || !name || !value) return set_error(HOL_EINVAL, "hol_get_option: null argument");
     auto is = [&](const char* s) { return strcmp(name, s) == 0; };
     if (is("slices_per_group")) *value = c->mv_k;

@@ -223,6 +223,7 @@ using namespace hol;
 extern "C" int force(hol_ctx* c, const double* v, const double* b, int n_pf, double* dSdx,
                      int with_bosonic, double* S_F, void* stream)
 {
+    HOL_TRACE("force");
     if (!c || !v || !b || !dSdx) return set_error(HOL_EINVAL, "force: null argument");
     if (int rc_ = require_aligned("force", {v, b, dSdx})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "force: hol_set_field not called");

@@ -61,6 +61,7 @@ extern "C" int global_update(hol_ctx* c, double* x, const double* Phi, int n_pf,
                              int j, double u, const hol_cg_opts* o, double* S_cur, int* accepted,
                              double* dS, void* stream)
 {
+    HOL_TRACE("global_update");
     if (!c || !x || !Phi || !o) return set_error(HOL_EINVAL, "global_update: null argument");
     if (int rc_ = require_aligned("global_update", {x, Phi})) return rc_;
     if (n_pf < 1 || n_pf > c->p.max_rhs)

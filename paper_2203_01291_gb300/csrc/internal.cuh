@@ -7,6 +7,8 @@
 #include <initializer_list>
 #include <stdio.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/holstein.h"
 #include "cb.cuh"
 
@@ -33,6 +35,16 @@ int cuda_error(cudaError_t e, const char* what);
     } while (0)
 
 void count_launch();
+
+// An NVTX range around each C-ABI call, named after it, so that a profiler's
+// timeline shows the library's calls (a no-op unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define HOL_TRACE(name) const hol::NvtxRange hol_trace_range_(name)
 
 // Raise the dynamic shared-memory limit of kernel `fn` to at least `bytes`
 // (a no-op up to 32 KB, which leaves room for static shared memory under the

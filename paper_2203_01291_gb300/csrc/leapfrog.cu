@@ -278,6 +278,7 @@ using namespace hol;
 extern "C" int mass_apply(hol_ctx* c, int which, double m_reg, const double* p, double* out,
                           void* stream)
 {
+    HOL_TRACE("mass_apply");
     if (!c || !p || !out) return set_error(HOL_EINVAL, "mass_apply: null argument");
     if (int rc_ = require_aligned("mass_apply", {p, out})) return rc_;
     if (which < 0 || which > 2) return set_error(HOL_EINVAL, "mass_apply: bad selector %d", which);
@@ -293,6 +294,7 @@ extern "C" int mass_apply(hol_ctx* c, int which, double m_reg, const double* p, 
 extern "C" int md_integrate(hol_ctx* c, double* x, double* p, const double* Phi, int n_pf,
                             const hol_md_opts* o, void* stream)
 {
+    HOL_TRACE("md_integrate");
     if (!c || !x || !p || !Phi) return set_error(HOL_EINVAL, "md_integrate: null argument");
     if (int rc_ = require_aligned("md_integrate", {x, p, Phi})) return rc_;
     int rc = check_md(c, o, n_pf);
@@ -304,6 +306,7 @@ extern "C" int fourier_accel_leapfrog(hol_ctx* c, double* x, const double* R_pf,
                                       int n_pf, const hol_md_opts* o, double u, int* accepted,
                                       double* dH, double* terms, void* stream)
 {
+    HOL_TRACE("fourier_accel_leapfrog");
     if (!c || !x || !R_pf || !R_p) return set_error(HOL_EINVAL, "fourier_accel_leapfrog: null argument");
     if (int rc_ = require_aligned("fourier_accel_leapfrog", {x, R_pf, R_p})) return rc_;
     int rc = check_md(c, o, n_pf);

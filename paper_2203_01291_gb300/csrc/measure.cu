@@ -287,6 +287,7 @@ extern "C" int stochastic_measure(hol_ctx* c, const double* xi, int n_rv, const 
                                   double* Gxi, double* G2, double* G4, int four_point, int* iters,
                                   void* stream)
 {
+    HOL_TRACE("stochastic_measure");
     if (!c || !xi || !opts || !Gxi || !G2) return set_error(HOL_EINVAL, "stochastic_measure: null argument");
     if (int rc_ = require_aligned("stochastic_measure", {xi, Gxi, G2, G4})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "stochastic_measure: hol_set_field not called");
@@ -460,6 +461,7 @@ __global__ void k_observables(const double* __restrict__ G2, const double* __res
 extern "C" int measure_observables(hol_ctx* c, const double* G2, const double* G4, double* C,
                                    double* out3, void* stream)
 {
+    HOL_TRACE("measure_observables");
     if (!c || !G2 || !G4 || !C || !out3)
         return set_error(HOL_EINVAL, "measure_observables: null argument");
     if (int rc_ = require_aligned("measure_observables", {G2, G4, C})) return rc_;

@@ -62,6 +62,7 @@ using namespace hol;
 extern "C" int fermion_matvec_static(const hol_params* p, const double* x, int op, const double* v,
                                      double* out, int n_rhs, void* stream)
 {
+    HOL_TRACE("fermion_matvec_static");
     if (!p || !x || !v || !out) return set_error(HOL_EINVAL, "fermion_matvec_static: null argument");
     if (int rc_ = require_aligned("fermion_matvec_static", {x, v, out})) return rc_;
     if (p->L < 4 || p->L > kMaxL || (p->L & 1) || p->Ltau < 2 || (p->Ltau & 1))

@@ -31,6 +31,7 @@ using namespace hol;
 
 extern "C" int hol_fma_peak(int prec, double* gflops, void* stream)
 {
+    HOL_TRACE("hol_fma_peak");
     if (!gflops || (prec != HOL_F64 && prec != HOL_F32))
         return set_error(HOL_EINVAL, "hol_fma_peak: bad argument");
     cudaStream_t s = (cudaStream_t)stream;

@@ -966,6 +966,7 @@ using namespace hol;
 extern "C" int precond_apply(hol_ctx* c, int which, int prec, const void* v, void* out, int n_rhs,
                              void* stream)
 {
+    HOL_TRACE("precond_apply");
     if (!c || !v || !out) return set_error(HOL_EINVAL, "precond_apply: null argument");
     if (int rc_ = require_aligned("precond_apply", {v, out})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "precond_apply: hol_set_field not called");

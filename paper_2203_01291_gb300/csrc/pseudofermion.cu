@@ -57,6 +57,7 @@ using namespace hol;
 
 extern "C" int pseudofermion_phi(hol_ctx* c, const double* R, double* Phi, int n_pf, void* stream)
 {
+    HOL_TRACE("pseudofermion_phi");
     if (!c || !R || !Phi) return set_error(HOL_EINVAL, "pseudofermion_phi: null argument");
     if (int rc_ = require_aligned("pseudofermion_phi", {R, Phi})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "pseudofermion_phi: hol_set_field not called");
@@ -71,6 +72,7 @@ extern "C" int pseudofermion_phi(hol_ctx* c, const double* R, double* Phi, int n
 
 extern "C" int phi_to_rhs(hol_ctx* c, const double* Phi, double* b, int n_pf, void* stream)
 {
+    HOL_TRACE("phi_to_rhs");
     if (!c || !Phi || !b) return set_error(HOL_EINVAL, "phi_to_rhs: null argument");
     if (int rc_ = require_aligned("phi_to_rhs", {Phi, b})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "phi_to_rhs: hol_set_field not called");

@@ -24,6 +24,7 @@ using namespace hol;
 extern "C" int hol_tune(hol_ctx* c, int n_rhs, int* best_k, int* best_warps, int* best_vec,
                         double* best_ms, void* stream)
 {
+    HOL_TRACE("hol_tune");
     if (!c) return set_error(HOL_EINVAL, "hol_tune: null context");
     if (!c->field_set) return set_error(HOL_EINVAL, "hol_tune: hol_set_field not called");
     if (n_rhs < 1 || n_rhs > c->p.max_rhs)
