@@ -11,7 +11,7 @@ Conventions
 * a space-time vector is laid out [tau][i]; flattened index tau*N + i;
 * s_0 = +1 (the antiperiodic corner block), s_tau = -1 for tau >= 1.
 
-Readings of the paper taken here (each also listed in the design doc):
+Readings of the paper taken here:
 
 * B_tau = exp(-dtau V_tau) exp(-dtau K): the diagonal acts last (Eq. (B_def)).
 * The "minimal split checkerboard" exp(-dtau K) (Sec. II D) is the product
