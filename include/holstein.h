@@ -90,10 +90,13 @@ typedef struct hol_ctx hol_ctx;
  * unsupported shape, HOL_ENOMEM if the scratch does not fit. */
 int hol_create(const hol_params* p, hol_ctx** out);
 
-/* Release the context and its scratch. NULL is accepted. */
+/* Release the context and its scratch (no counterpart in the paper). Waits
+ * for the device to finish the context's work first. NULL is accepted. */
 int hol_destroy(hol_ctx* ctx);
 
-/* Message describing the last error on the calling thread (static storage). */
+/* Message describing the last error on the calling thread (thread-local
+ * static storage, valid until that thread's next failing call; no
+ * counterpart in the paper). */
 const char* hol_last_error(void);
 
 /*
@@ -396,9 +399,10 @@ int fermion_matvec_static(const hol_params* p, const double* x, int op, const do
 int hol_arnoldi_bounds(hol_ctx* ctx, const double* v0, int m, double margin, int install,
                        double* bmin, double* bmax, int* steps, void* stream);
 
-/* The spectral bounds of Bbar the preconditioner currently uses (host
- * outputs): the deterministic norm bounds of hol_set_field, or those
- * installed by hol_arnoldi_bounds. Synchronises `stream`. */
+/* The spectral bounds of Bbar (App. C D) the preconditioner currently uses
+ * (host outputs): the deterministic norm bounds of hol_set_field, or those
+ * installed by hol_arnoldi_bounds. HOL_EINVAL before hol_set_field or for a
+ * null argument. Synchronises `stream`. */
 int hol_get_bounds(hol_ctx* ctx, double* bmin, double* bmax, void* stream);
 
 /*
@@ -464,7 +468,8 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
 int hol_set_option(hol_ctx* ctx, const char* name, int value);
 
 /* Current value of a launch option of hol_set_option into *value (written on
- * success only). Returns HOL_EINVAL for a null argument or an unknown name. */
+ * success only; no counterpart in the paper). Returns HOL_EINVAL for a null
+ * argument or an unknown name. */
 int hol_get_option(const hol_ctx* ctx, const char* name, int* value);
 
 /*
@@ -481,7 +486,8 @@ int hol_get_option(const hol_ctx* ctx, const char* name, int* value);
  */
 unsigned long long hol_launch_count(void);
 /* Measured FMA throughput of the current GPU in GFLOP/s (prec HOL_F64 or
- * HOL_F32; 2 flops per FMA): the ALU roofline of the FP64 path. */
+ * HOL_F32; 2 flops per FMA): the ALU roofline of the FP64 path (no
+ * counterpart in the paper). gflops: host output. Synchronises `stream`. */
 int hol_fma_peak(int prec, double* gflops, void* stream);
 int hol_timer_enable(hol_ctx* ctx, int on);
 int hol_timer_read(hol_ctx* ctx, int klass, int* count, double* total_ms, double* units);
