@@ -22,7 +22,7 @@ def rng(seed=0):
     return np.random.default_rng(seed)
 
 
-# ---------------------------------------------------------------- P1 free fermions
+# ---------------------------------------------------------------- free fermions
 @pytest.mark.parametrize("L", [4, 6])
 @pytest.mark.parametrize("mu", [0.0, 0.3])
 def test_free_fermion_logdet_exact_kinetic(L, mu):
@@ -98,7 +98,7 @@ def test_free_fermion_checkerboard_close_to_exact():
     assert abs(D.logdet_M(m, x) - D.logdet_M(me, x)) < 0.05
 
 
-# ---------------------------------------------------------------- P2 particle-hole
+# ---------------------------------------------------------------- particle-hole
 @pytest.mark.parametrize("kinetic", ["exact", "checkerboard"])
 def test_particle_hole_logdet(kinetic):
     """mu = 0, bipartite lattice: log det M(-x) - log det M(x) = dtau alpha sum x,
@@ -124,7 +124,7 @@ def test_lambda_determinant_and_inverse():
     assert abs(2 * ld - m.dtau * m.alpha * x.sum()) < 1e-11
 
 
-# ---------------------------------------------------------------- P3 t = 0
+# ---------------------------------------------------------------- t = 0
 def test_atomic_limit_logdet():
     """t = 0: det M = prod_i (1 + exp(-dtau sum_tau (alpha x_{i,tau} - mu)))
     (single-site form of Sec. IV, Eq. (detM_alt))."""
@@ -144,7 +144,7 @@ def test_single_site_adiabatic_reflection_symmetry():
     assert abs(D.S_F(m, x, Phi) - D.S_F(m, -x, Phi)) < 1e-11 * abs(D.S_F(m, x, Phi))
 
 
-# ---------------------------------------------------------------- P4 S_F at x0
+# ---------------------------------------------------------------- S_F at x0
 def test_SF_at_sampling_point_and_solution():
     """Phi = A(x0)^T R gives S_F(x0, Phi) = |R|^2 / 2 (Sec. II D) and
     v = (M^T M)^{-1} Lambda^{-T} Phi = M^{-1} R."""
@@ -159,7 +159,7 @@ def test_SF_at_sampling_point_and_solution():
     assert np.abs(D.M_apply(m, x, v) - R[0]).max() < 1e-12
 
 
-# ---------------------------------------------------------------- P5 forces
+# ---------------------------------------------------------------- forces
 def test_force_matches_finite_differences():
     """dS_F/dx (Eq. (dSF_dx)) against central differences of S_F at fixed Phi."""
     m = D.Model(L=4, Ltau=8, alpha=1.2)
@@ -220,7 +220,7 @@ def test_bosonic_force_finite_differences():
         assert abs((D.S_B(m, xp) - D.S_B(m, xm)) / (2 * h) - F[tau, i]) < 1e-6
 
 
-# ---------------------------------------------------------------- P6 / P7 Fourier
+# ---------------------------------------------------------------- Fourier
 def test_Q_fourier_equals_stencil():
     """Qx = F^{-1} Qtilde F x equals the stencil of Eq. (dSB_dx)."""
     m = D.Model(L=4, Ltau=20, omega0=0.8)
@@ -261,7 +261,7 @@ def test_mass_operator_powers():
     assert np.abs(D.mass_apply(m, p, np.inf, 1.0) - m.dtau * p).max() < 1e-14
 
 
-# ---------------------------------------------------------------- P12 leapfrog
+# ---------------------------------------------------------------- leapfrog
 def test_leapfrog_reversible():
     m = D.Model(L=4, Ltau=8, alpha=1.0)
     g = rng(14)
@@ -304,7 +304,7 @@ def test_harmonic_modes_without_fermions():
     assert np.abs(x1 - ref).max() < 5e-3 * np.abs(x0).max()
 
 
-# ---------------------------------------------------------------- P8-P10 preconditioner
+# ---------------------------------------------------------------- preconditioner
 def test_precond_block_diagonal_in_U_basis():
     """U P U^dag is block diagonal with blocks I - e^{-i phi_omega} Bbar
     (Eqs. (Mww), (P_block))."""
@@ -413,7 +413,7 @@ def test_matvec_count_worked_example():
     assert abs(D.n_matvec_bound(T, g2["delta_b"]) / T - g2["value"]) < 0.01
 
 
-# ---------------------------------------------------------------- P11 measurements
+# ---------------------------------------------------------------- measurements
 def test_cross_correlation_direct_equals_fft():
     g = rng(40)
     a, b = g.standard_normal((2, 8, 16))
@@ -602,3 +602,49 @@ def test_arnoldi_relation_and_orthonormal_basis(kinetic):
         assert np.abs(V @ V.T - np.eye(k + 1)).max() < 1e-12
     dlo, dhi = D.spectral_bounds(m, x)
     assert dlo <= lo <= hi_ <= dhi
+
+
+# ---------------------------------------------------------------- further pins
+def test_leapfrog_is_symplectic():
+    """Algorithm 1's map (x, p) -> (x', p') at fixed Phi is symplectic: its
+    Jacobian J (central differences, h = 1e-6) satisfies J^T Omega J = Omega
+    for the canonical form Omega. A force that is not the gradient of the
+    action (a dropped or mis-signed term) breaks this."""
+    w = hi.Workload("s", L=4, Ltau=2, alpha=1.1, mu=0.2, omega0=1.0, x_std=1.0, seed=5)
+    m = D.model_of(w)
+    x0 = hi.phonon_field(w)
+    R = hi.gaussian_vectors(w, 1, seed=6)
+    Phi = D.phi_from_R(m, x0, R)
+    p0 = hi.gaussian_vectors(w, 1, seed=7)[0]
+    n = m.n
+    dt, Nt, nt, mreg = 0.05, 2, 2, 1.0
+
+    def flow(z):
+        xf, pf = D.leapfrog_split(m, z[:n].reshape(m.Ltau, m.N), z[n:].reshape(m.Ltau, m.N),
+                                  Phi, dt, Nt, nt, mreg)
+        return np.concatenate([xf.ravel(), pf.ravel()])
+
+    z0 = np.concatenate([x0.ravel(), p0.ravel()])
+    h = 1e-6
+    J = np.empty((2 * n, 2 * n))
+    for k in range(2 * n):
+        e = np.zeros(2 * n)
+        e[k] = h
+        J[:, k] = (flow(z0 + e) - flow(z0 - e)) / (2 * h)
+    Om = np.block([[np.zeros((n, n)), np.eye(n)], [-np.eye(n), np.zeros((n, n))]])
+    # the Fourier-accelerated kinetic term p M^{-1} p / 2 is a constant metric,
+    # so the flow preserves the canonical form of (x, p) itself
+    assert np.abs(J.T @ Om @ J - Om).max() < 1e-6
+    assert abs(np.linalg.det(J) - 1.0) < 1e-6
+
+
+def test_atomic_limit_density():
+    """t = 0: every site decouples and its occupation per spin is
+    1 / (1 + exp(dtau sum_tau (alpha x_tau - mu))) (det M factorises over sites
+    at t = 0, Eq. (M_def)), so <n> is twice its site average."""
+    w = hi.Workload("a", L=4, Ltau=6, t=0.0, alpha=0.9, mu=0.3, x_std=1.0, seed=8)
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    occ = 1.0 / (1.0 + np.exp(m.dtau * (m.alpha * x - m.mu).sum(axis=0)))
+    obs = D.observables_exact(m, x)
+    assert abs(obs["density"] - 2.0 * occ.mean()) < 1e-12
