@@ -25,3 +25,43 @@ def test_bench_uses_no_undefined_names():
             defined.add(node.name)
     used = {n.id for n in ast.walk(tree) if isinstance(n, ast.Name) and isinstance(n.ctx, ast.Load)}
     assert sorted(used - defined) == []
+
+
+def _bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_traffic_line_is_ignored_once_the_kernel_sources_change(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from a committed ncu line only while
+    the digest of the kernel's sources matches it; it is scaled to the run's
+    algorithmic bytes; a stale digest gives None."""
+    b = _bench()
+    digest = b.kernel_source_digest("k_cg_mtm32_v4a<32,2>")
+    assert len(digest) == 12
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "x.md").write_text(
+        "traffic_per_launch: k_cg_mtm32_v4a<32,2> %s 1000 2000\n" % digest)
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    monkeypatch.setattr(b, "kernel_source_digest", lambda k: digest)
+    assert b.traffic_from_profiles("k_cg_mtm32_v4a<32,2>", 4000) == 2000.0
+    monkeypatch.setattr(b, "kernel_source_digest", lambda k: "0" * 12)
+    assert b.traffic_from_profiles("k_cg_mtm32_v4a<32,2>", 4000) is None
+
+
+def test_single_rank_job_rate_and_replica_inputs():
+    """At N = 1 the job rate is units over the rank's time; each rank draws
+    its own seeded inputs (replicas, no shared data)."""
+    import holstein_inputs as hi
+    b = _bench()
+    assert b.job_rate(1, 32, 500.0) == 64.0
+    w = hi.Workload("r", L=4, Ltau=4, seed=3)
+    x0, r0 = b.replica_inputs(w, 2, 0)
+    x1, r1 = b.replica_inputs(w, 2, 1)
+    xa, ra = b.replica_inputs(w, 2, 0)
+    assert (x0 == xa).all() and (r0 == ra).all()
+    assert not (x0 == x1).all() and not (r0 == r1).all()
