@@ -441,8 +441,16 @@ def run_ours(a):
 
     extra = None
     if not a.no_extra:
-        extra = {"trajectory": trajectory_leg(dev), "measurement": measurement_leg(dev),
-                 "global_updates": global_update_leg(dev), "chains": chains_leg(dev)}
+        # the other rows are reported beside the headline; a row that fails
+        # reports its error instead of taking the headline line down with it
+        extra = {}
+        for name, leg in (("trajectory", trajectory_leg), ("measurement", measurement_leg),
+                          ("global_updates", global_update_leg), ("chains", chains_leg)):
+            try:
+                extra[name] = leg(dev)
+            except Exception as e:   # noqa: BLE001
+                extra[name] = {"error": f"{type(e).__name__}: {e}"}
+                torch.cuda.synchronize()
 
     alu = {"fp64_fma_gflops": hg.hol_fma_peak(hg.HOL_F64),
            "fp32_fma_gflops": hg.hol_fma_peak(hg.HOL_F32),
