@@ -450,7 +450,6 @@ def run_ours(a):
                 extra[name] = leg(dev)
             except Exception as e:   # noqa: BLE001
                 extra[name] = {"error": f"{type(e).__name__}: {e}"}
-                torch.cuda.synchronize()
 
     alu = {"fp64_fma_gflops": hg.hol_fma_peak(hg.HOL_F64),
            "fp32_fma_gflops": hg.hol_fma_peak(hg.HOL_F32),
