@@ -399,6 +399,14 @@ int fermion_matvec_static(const hol_params* p, const double* x, int op, const do
 int hol_arnoldi_bounds(hol_ctx* ctx, const double* v0, int m, double margin, int install,
                        double* bmin, double* bmax, int* steps, void* stream);
 
+/* Eigenvalues of an n x n real upper Hessenberg matrix H (HOST, row-major;
+ * entries below the first subdiagonal must be zero) by the shifted QR
+ * iteration hol_arnoldi_bounds uses for its Ritz values (host code, no GPU
+ * needed). re, im: HOST arrays of n, in no particular order. HOL_EINVAL for a
+ * bad argument or a matrix that is not Hessenberg, HOL_ENUMERIC if the
+ * iteration does not converge. */
+int hol_hessenberg_eigenvalues(int n, const double* H, double* re, double* im);
+
 /* The spectral bounds of Bbar (App. C D) the preconditioner currently uses
  * (host outputs): the deterministic norm bounds of hol_set_field, or those
  * installed by hol_arnoldi_bounds. HOL_EINVAL before hol_set_field or for a

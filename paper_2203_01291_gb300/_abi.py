@@ -90,6 +90,7 @@ SIGNATURES = {
     "hol_arnoldi_bounds": (_I, [_VP, _VP, _I, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D),
                                 ctypes.POINTER(_I), _VP]),
     "hol_get_bounds": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D), _VP]),
+    "hol_hessenberg_eigenvalues": (_I, [_I, _VP, _VP, _VP]),
     "hol_tune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                       ctypes.POINTER(_D), _VP]),
     "hol_launch_count": (ctypes.c_ulonglong, []),

@@ -322,3 +322,24 @@ extern "C" int hol_get_bounds(hol_ctx* c, double* bmin, double* bmax, void* stre
     *bmax = b[S_BMAX];
     return HOL_OK;
 }
+
+extern "C" int hol_hessenberg_eigenvalues(int n, const double* H, double* re, double* im)
+{
+    HOL_TRACE("hol_hessenberg_eigenvalues");
+    if (n < 1 || !H || !re || !im)
+        return set_error(HOL_EINVAL, "hol_hessenberg_eigenvalues: bad argument");
+    for (int i = 2; i < n; ++i)
+        for (int j = 0; j + 1 < i; ++j)
+            if (H[(size_t)i * n + j] != 0.0)
+                return set_error(HOL_EINVAL, "hol_hessenberg_eigenvalues: not upper Hessenberg");
+    std::vector<std::complex<double>> A((size_t)n * n), ev;
+    for (size_t k = 0; k < A.size(); ++k) A[k] = H[k];
+    if (!hessenberg_eigenvalues(n, A, ev))
+        return set_error(HOL_ENUMERIC, "hol_hessenberg_eigenvalues: QR iteration did not converge");
+    for (int k = 0; k < n; ++k) {
+        re[k] = ev[k].real();
+        im[k] = ev[k].imag();
+    }
+    return HOL_OK;
+}
+

@@ -96,3 +96,39 @@ def test_null_arguments_are_refused():
     assert lib.hol_arnoldi_bounds(None, None, 20, 0.05, 0, None, None, None, None) == \
         _abi.HOL_EINVAL
     del v
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (5, 2), (12, 3), (20, 4), (32, 5)])
+def test_host_hessenberg_eigenvalues_match_numpy(n, seed):
+    """The host shifted-QR eigen-solver behind the Arnoldi bounds (no GPU):
+    random upper Hessenberg matrices, including ones with complex pairs,
+    against numpy's eigvals (matched as multisets)."""
+    import numpy as np
+    from paper_2203_01291_gb300 import _abi
+    lib = _abi.load()
+    rng = np.random.default_rng(seed)
+    H = np.triu(rng.standard_normal((n, n)), -1)
+    if n > 3:
+        H[:3, :3] += np.eye(3) * 2.0                  # a well separated block too
+    re = np.zeros(n)
+    im = np.zeros(n)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)   # noqa: E731
+    Hc = np.ascontiguousarray(H)
+    assert lib.hol_hessenberg_eigenvalues(n, p(Hc), p(re), p(im)) == _abi.HOL_OK
+    got = np.sort_complex(re + 1j * im)
+    ref = np.sort_complex(np.linalg.eigvals(H))
+    # match each reference eigenvalue to the nearest computed one
+    for z in ref:
+        assert np.min(np.abs(got - z)) < 1e-9 * max(1.0, np.abs(ref).max())
+    assert abs(got.sum() - np.trace(H)) < 1e-9 * max(1.0, np.abs(H).sum())
+
+
+def test_host_hessenberg_eigenvalues_refuses_a_full_matrix():
+    import numpy as np
+    from paper_2203_01291_gb300 import _abi
+    lib = _abi.load()
+    H = np.ones((4, 4))
+    re = np.zeros(4)
+    im = np.zeros(4)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)   # noqa: E731
+    assert lib.hol_hessenberg_eigenvalues(4, p(H), p(re), p(im)) == _abi.HOL_EINVAL
