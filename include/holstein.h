@@ -71,6 +71,18 @@ extern "C" {
 #define HOL_KINETIC_CHECKERBOARD 0
 #define HOL_KINETIC_EXACT        1
 
+/*
+ * The taps of the exact one-direction factor E = exp(dtau t A_ring) on a ring
+ * of L sites that HOL_KINETIC_EXACT applies (host code, no GPU needed):
+ * e[d], d = 0 .. L/2, the entry of E for ring distance d (HOST array of 17
+ * doubles; entries past L/2 are zero), summed over the periodic images from
+ * the power series of the modified Bessel functions I_k(2 dtau t). d64 / d32
+ * (host): the largest d kept by the FP64 / FP32 kernels (|e[d]| above 2^-60
+ * / 2^-30 of e[0]). HOL_EINVAL for an unsupported L, dtau <= 0 or
+ * |dtau t| > 4.
+ */
+int hol_exact_taps(int L, double dtau, double t, double* e, int* d64, int* d32);
+
 typedef struct hol_params {
     int L;            /* linear lattice size (even, 4..32)                      */
     int Ltau;         /* number of imaginary-time slices T = beta / dtau (even) */

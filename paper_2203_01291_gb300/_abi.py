@@ -91,6 +91,7 @@ SIGNATURES = {
                                 ctypes.POINTER(_I), _VP]),
     "hol_get_bounds": (_I, [_VP, ctypes.POINTER(_D), ctypes.POINTER(_D), _VP]),
     "hol_hessenberg_eigenvalues": (_I, [_I, _VP, _VP, _VP]),
+    "hol_exact_taps": (_I, [_I, _D, _D, _VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "hol_tune": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                       ctypes.POINTER(_D), _VP]),
     "hol_launch_count": (ctypes.c_ulonglong, []),

@@ -199,11 +199,11 @@ static double bessel_i(int n, double x)
 // the ring sums the images, e[d] = sum_m I_|d + m L|(2 dtau t). Taps whose
 // magnitude is below 2^-60 (FP64) or 2^-30 (FP32) of e[0] are dropped: their
 // total is far below the rounding of that arithmetic.
-static void exact_taps(hol_ctx* c)
+static void compute_exact_taps(int L, double dtau, double t, double* e_out, int* d64_out,
+                               int* d32_out)
 {
-    const int L = c->L;
-    const double x = 2.0 * c->p.dtau * c->p.t;
-    for (int d = 0; d < kKinTaps; ++d) c->kin_e[d] = 0.0;
+    const double x = 2.0 * dtau * t;
+    for (int d = 0; d < kKinTaps; ++d) e_out[d] = 0.0;
     for (int d = 0; d <= L / 2; ++d) {
         double e = 0.0;
         for (int m = -64; m <= 64; ++m) {
@@ -211,14 +211,29 @@ static void exact_taps(hol_ctx* c)
             if (k > 400) continue;
             e += bessel_i(k, x);
         }
-        c->kin_e[d] = e;
+        e_out[d] = e;
     }
-    const double e0 = fabs(c->kin_e[0]);
+    const double e0 = fabs(e_out[0]);
     int d64 = L / 2, d32 = L / 2;
-    while (d64 > 0 && fabs(c->kin_e[d64]) <= 0x1p-60 * e0) --d64;
-    while (d32 > 0 && fabs(c->kin_e[d32]) <= 0x1p-30 * e0) --d32;
-    c->kin_d64 = d64;
-    c->kin_d32 = d32;
+    while (d64 > 0 && fabs(e_out[d64]) <= 0x1p-60 * e0) --d64;
+    while (d32 > 0 && fabs(e_out[d32]) <= 0x1p-30 * e0) --d32;
+    *d64_out = d64;
+    *d32_out = d32;
+}
+
+static void exact_taps(hol_ctx* c)
+{
+    compute_exact_taps(c->L, c->p.dtau, c->p.t, c->kin_e, &c->kin_d64, &c->kin_d32);
+}
+
+extern "C" int hol_exact_taps(int L, double dtau, double t, double* e, int* d64, int* d32)
+{
+    HOL_TRACE("hol_exact_taps");
+    if (!e || !d64 || !d32 || L < 4 || L > kMaxL || (L & 1) || !(dtau > 0.0) ||
+        !(fabs(dtau * t) <= 4.0))
+        return set_error(HOL_EINVAL, "hol_exact_taps: bad argument");
+    compute_exact_taps(L, dtau, t, e, d64, d32);
+    return HOL_OK;
 }
 
 extern "C" int hol_create(const hol_params* p, hol_ctx** out)

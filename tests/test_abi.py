@@ -132,3 +132,28 @@ def test_host_hessenberg_eigenvalues_refuses_a_full_matrix():
     im = np.zeros(4)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)   # noqa: E731
     assert lib.hol_hessenberg_eigenvalues(4, p(H), p(re), p(im)) == _abi.HOL_EINVAL
+
+
+@pytest.mark.parametrize("L", [4, 6, 8, 16, 32])
+@pytest.mark.parametrize("dtau,t", [(0.1, 1.0), (0.1, 3.0), (0.2, -1.0), (1.0, 1.0)])
+def test_host_exact_propagator_taps(L, dtau, t):
+    """The taps of the exact kinetic propagator (no GPU): the first row of
+    scipy's matrix exponential of dtau t times the ring adjacency, and the
+    taps the FP64 / FP32 kernels drop are below 2^-60 / 2^-30 of e[0]."""
+    import numpy as np
+    import scipy.linalg
+    from paper_2203_01291_gb300 import _abi
+    lib = _abi.load()
+    e = np.zeros(17)
+    d64, d32 = ctypes.c_int(), ctypes.c_int()
+    assert lib.hol_exact_taps(L, dtau, t, e.ctypes.data_as(ctypes.c_void_p), ctypes.byref(d64),
+                              ctypes.byref(d32)) == _abi.HOL_OK
+    A = np.zeros((L, L))
+    for i in range(L):
+        A[i, (i + 1) % L] = A[(i + 1) % L, i] = 1.0
+    ref = scipy.linalg.expm(dtau * t * A)[0, : L // 2 + 1]
+    assert np.abs(e[: L // 2 + 1] - ref).max() < 1e-14 * abs(ref[0])
+    assert np.all(e[L // 2 + 1:] == 0.0)
+    assert np.all(np.abs(ref[d64.value + 1:]) <= 2.0 ** -60 * abs(ref[0]) * 1.01)
+    assert np.all(np.abs(ref[d32.value + 1:]) <= 2.0 ** -30 * abs(ref[0]) * 1.01)
+    assert 0 <= d32.value <= d64.value <= L // 2
