@@ -157,3 +157,19 @@ def test_host_exact_propagator_taps(L, dtau, t):
     assert np.all(np.abs(ref[d64.value + 1:]) <= 2.0 ** -60 * abs(ref[0]) * 1.01)
     assert np.all(np.abs(ref[d32.value + 1:]) <= 2.0 ** -30 * abs(ref[0]) * 1.01)
     assert 0 <= d32.value <= d64.value <= L // 2
+
+
+@pytest.mark.parametrize("kinetic", [0, 1])
+def test_create_without_a_device_fails_cleanly(kinetic):
+    """Valid parameters on a host without a GPU: HOL_ECUDA with a message and
+    no context (the partly built context is released)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    from paper_2203_01291_gb300 import _abi
+    lib = _abi.load()
+    p = _abi.hol_params(8, 8, 0.1, 1.0, 0.0, 1.0, 1.0, 2, kinetic)
+    h = ctypes.c_void_p()
+    assert lib.hol_create(ctypes.byref(p), ctypes.byref(h)) == _abi.HOL_ECUDA
+    assert not h.value
+    assert "device" in lib.hol_last_error().decode()
