@@ -9,7 +9,7 @@
  *   B_tau = exp(-dtau V_tau) exp(-dtau K) (Eq. (B_def)), exp(-dtau K) the
  *   checkerboard product C4 C3 C2 C1 of two-site bond factors
  *   [[cosh, sinh], [sinh, cosh]](dtau t) over four bond colours (x-even,
- *   x-odd, y-even, y-odd);
+ *   x-odd, y-even, y-odd), or (kinetic = 1) exp(-dtau K) itself;
  *   M^T is the transpose of that matrix, (M^T u)_tau = u_tau +
  *   s_{tau+1} C^T D_{tau+1} u_{tau+1}, C^T = C1 C2 C3 C4;
  *   CG on M^T M v = b (Eq. (CG)), stopped on |b - M^T M v| / |b| (Sec. VI B);
@@ -29,6 +29,7 @@
 typedef struct {
     int L, T;
     double dtau, t, mu, alpha, omega0;
+    int kinetic;   /* 0: checkerboard C4 C3 C2 C1; 1: exact exp(-dtau K) */
 } orc_model;
 
 static int idx(int ix, int iy, int L) { return ((ix + L) % L) + L * ((iy + L) % L); }
@@ -54,9 +55,47 @@ static void bond_colour(const orc_model* m, int colour, double* v)
         }
 }
 
-/* v <- C v (C = C4 C3 C2 C1, so C1 acts first) or v <- C^T v */
+/* v <- exp(-dtau K) v exactly. K = -t (nearest-neighbour hopping) on the
+ * periodic lattice is the sum of commuting x and y parts, so exp(-dtau K) is
+ * E (x) E with E = exp(dtau t A) for the adjacency A of a ring of L sites;
+ * E[i][j] = e[(i - j) mod L] with e[d] = (1/L) sum_k exp(2 dtau t
+ * cos(2 pi k / L)) cos(2 pi k d / L), from the ring's Fourier modes. */
+static void exact_kinetic(const orc_model* m, double* v)
+{
+    const int L = m->L, N = L * L;
+    const double pi = acos(-1.0);
+    double* e = (double*)malloc(sizeof(double) * L);
+    double* tmp = (double*)malloc(sizeof(double) * N);
+    for (int d = 0; d < L; ++d) {
+        double s = 0.0;
+        for (int k = 0; k < L; ++k)
+            s += exp(2.0 * m->dtau * m->t * cos(2.0 * pi * k / L)) * cos(2.0 * pi * k * d / L);
+        e[d] = s / L;
+    }
+    for (int iy = 0; iy < L; ++iy)          /* x direction */
+        for (int ix = 0; ix < L; ++ix) {
+            double s = 0.0;
+            for (int jx = 0; jx < L; ++jx) s += e[(ix - jx + L) % L] * v[jx + L * iy];
+            tmp[ix + L * iy] = s;
+        }
+    for (int iy = 0; iy < L; ++iy)          /* y direction */
+        for (int ix = 0; ix < L; ++ix) {
+            double s = 0.0;
+            for (int jy = 0; jy < L; ++jy) s += e[(iy - jy + L) % L] * tmp[ix + L * jy];
+            v[ix + L * iy] = s;
+        }
+    free(tmp);
+    free(e);
+}
+
+/* v <- C v (C = C4 C3 C2 C1, so C1 acts first) or v <- C^T v; with the exact
+ * propagator (symmetric) both are exp(-dtau K) v */
 void orc_kinetic(const orc_model* m, double* v, int transpose)
 {
+    if (m->kinetic == 1) {
+        exact_kinetic(m, v);
+        return;
+    }
     if (!transpose)
         for (int c = 0; c < 4; ++c) bond_colour(m, c, v);
     else

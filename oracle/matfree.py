@@ -18,7 +18,8 @@ LIB = os.path.join(OUT_DIR, "libholstein_oracle.so")
 class _Model(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("T", ctypes.c_int), ("dtau", ctypes.c_double),
                 ("t", ctypes.c_double), ("mu", ctypes.c_double),
-                ("alpha", ctypes.c_double), ("omega0", ctypes.c_double)]
+                ("alpha", ctypes.c_double), ("omega0", ctypes.c_double),
+                ("kinetic", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -51,7 +52,11 @@ def lib():
 
 
 def _m(model) -> _Model:
-    return _Model(model.L, model.Ltau, model.dtau, model.t, model.mu, model.alpha, model.omega0)
+    """A workload or a dense-oracle Model (its `kinetic`, "checkerboard" by
+    default, selects the propagator)."""
+    exact = getattr(model, "kinetic", "checkerboard") == "exact"
+    return _Model(model.L, model.Ltau, model.dtau, model.t, model.mu, model.alpha, model.omega0,
+                  1 if exact else 0)
 
 
 def _p(a: np.ndarray):

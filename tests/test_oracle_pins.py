@@ -467,6 +467,26 @@ def test_matfree_operators_equal_dense():
     assert np.abs(MF.MT_apply(m, x, v) - D.MT_apply(m, x, v)).max() < 1e-13
 
 
+@pytest.mark.parametrize("L,T", [(6, 4), (8, 6), (4, 10)])
+def test_matfree_exact_propagator_equals_dense(L, T):
+    """The C oracle's exact exp(-dtau K) (ring Fourier modes) against the
+    dense oracle's (scipy's matrix exponential of the hopping matrix):
+    M, M^T and the fermion force."""
+    m = D.Model(L=L, Ltau=T, alpha=1.1, mu=0.2, kinetic="exact")
+    g = rng(52)
+    x = g.standard_normal((m.Ltau, m.N))
+    v = g.standard_normal((m.Ltau, m.N))
+    assert np.abs(MF.M_apply(m, x, v) - D.M_apply(m, x, v)).max() < 1e-13
+    assert np.abs(MF.MT_apply(m, x, v) - D.MT_apply(m, x, v)).max() < 1e-13
+    R = g.standard_normal((1, m.Ltau, m.N))
+    Phi = D.phi_from_R(m, x + 0.1, R)
+    b = D.b_from_phi(m, x, Phi[0])
+    vd = D.solve_MTM(m, x, b)
+    F = MF.force_fermion(m, x, vd, b)
+    Fd = D.dSF_dx(m, x, Phi)
+    assert np.abs(F - Fd).max() < 1e-11 * np.abs(Fd).max()
+
+
 def test_matfree_cg_and_force_equal_dense():
     m = D.Model(L=4, Ltau=10, alpha=1.2)
     g = rng(51)
