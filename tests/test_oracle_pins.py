@@ -668,3 +668,36 @@ def test_atomic_limit_density():
     occ = 1.0 / (1.0 + np.exp(m.dtau * (m.alpha * x - m.mu).sum(axis=0)))
     obs = D.observables_exact(m, x)
     assert abs(obs["density"] - 2.0 * occ.mean()) < 1e-12
+
+
+def test_stochastic_estimators_are_unbiased_over_z2_probes():
+    """Sec. V B-C: with Z2 probes (<xi_i xi_j> = delta_ij) the 2-point average
+    and the pair-averaged Wick products are unbiased estimates of the exact
+    space-time averages: their mean over many independent probe sets lies
+    within a few standard errors of the dense-G values, and the spread of a
+    single set shrinks as the probe count grows."""
+    w = hi.Workload("u", L=4, Ltau=4, alpha=1.0, mu=0.1, x_std=1.0, seed=21)
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    G = D.green_matrix(m, x)
+    exact2 = D.green_average_exact(m, x)
+    exact4 = D.wick_products_exact(m, x)
+    sets, nrv = 200, 4
+    e2, e4 = [], []
+    for k in range(sets):
+        xi = hi.z2_vectors(w, nrv, seed=1000 + k)
+        Gxi = np.array([(G @ v.reshape(-1)).reshape(m.Ltau, m.N) for v in xi])
+        e2.append(D.green_average(m, x, xi, Gxi))
+        e4.append(D.four_point_pairs(m, x, xi, Gxi))
+    e2, e4 = np.array(e2), np.array(e4)
+    for est, exact in ((e2, exact2), (e4, exact4)):
+        mean = est.mean(axis=0)
+        se = est.std(axis=0, ddof=1) / np.sqrt(sets) + 1e-12
+        z = np.abs(mean - exact) / se
+        assert np.median(z) < 1.5 and z.max() < 6.0
+    # a set of 16 probes is closer to the exact value than a set of 4, on average
+    err4 = np.mean([np.abs(D.green_average(m, x, hi.z2_vectors(w, 4, seed=5000 + k)) - exact2).mean()
+                    for k in range(20)])
+    err16 = np.mean([np.abs(D.green_average(m, x, hi.z2_vectors(w, 16, seed=6000 + k)) - exact2).mean()
+                     for k in range(20)])
+    assert err16 < 0.75 * err4
