@@ -173,3 +173,25 @@ def test_create_without_a_device_fails_cleanly(kinetic):
     assert lib.hol_create(ctypes.byref(p), ctypes.byref(h)) == _abi.HOL_ECUDA
     assert not h.value
     assert "device" in lib.hol_last_error().decode()
+
+
+@pytest.mark.parametrize("lang,std", [("c", "c99"), ("c++", "c++11")])
+def test_header_is_plain_c_and_cxx(tmp_path, lang, std):
+    """include/holstein.h is a C ABI: it compiles as C99 and as C++11 with all
+    warnings as errors, and declares everything a caller needs (the types and
+    every entry point) without CUDA or torch headers."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / ("use." + ("c" if lang == "c" else "cpp"))
+    calls = "\n".join(f"    (void){name};" for name in declared_functions())
+    src.write_text('#include "holstein.h"\nint main(void)\n{\n    hol_params p = {0};\n'
+                   '    hol_cg_opts o = {0};\n    hol_md_opts m = {0};\n'
+                   '    (void)p; (void)o; (void)m;\n' + calls + "\n    return 0;\n}\n")
+    r = subprocess.run([cc, "-std=" + std, "-Wall", "-Wextra", "-Werror",
+                        "-Wno-missing-field-initializers", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
