@@ -188,11 +188,12 @@ def test_force_structured_equals_fully_dense():
     assert np.abs(ref - np.array([F[c] for c in comps])).max() < 1e-12
 
 
-def test_force_phi_average_is_logdet_derivative():
+@pytest.mark.parametrize("L,kinetic", [(4, "checkerboard"), (6, "exact")])
+def test_force_phi_average_is_logdet_derivative(L, kinetic):
     """Phi ~ N(0, A^T A): E[dS_F,sigma/dx] = -d ln|det M|/dx - dtau alpha / 2.
     Exact (no sampling): sum over Phi_k = A^T e_k for all unit vectors e_k,
     since sum_k e_k e_k^T = I; right side by central differences of slogdet."""
-    m = D.Model(L=4, Ltau=4, alpha=1.1)
+    m = D.Model(L=L, Ltau=4, alpha=1.1, kinetic=kinetic)
     g = rng(10)
     x = g.standard_normal((m.Ltau, m.N))
     A = D.A_matrix(m, x)
@@ -205,7 +206,7 @@ def test_force_phi_average_is_logdet_derivative():
         xp[tau, i] += h
         xm[tau, i] -= h
         dld = (D.logdet_M(m, xp) - D.logdet_M(m, xm)) / (2 * h)
-        assert abs(F[tau, i] - (-dld - 0.5 * m.dtau * m.alpha)) < 1e-7
+        assert abs(F[tau, i] - (-dld - 0.5 * m.dtau * m.alpha)) < 1e-7, (tau, i)
 
 
 def test_bosonic_force_finite_differences():
