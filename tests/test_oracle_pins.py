@@ -589,6 +589,52 @@ def test_observables_particle_hole_at_half_filling():
     assert abs(D.observables_exact(m, np.zeros_like(x))["density"] - 1.0) < 1e-12
 
 
+@pytest.mark.parametrize("L,T,mu", [(4, 10, 0.3), (6, 8, -0.45)])
+def test_observables_free_fermion_closed_form(L, T, mu):
+    """Free fermions (x = 0) with the exact propagator: B = exp(-dtau (K - mu))
+    is diagonal in momentum with b_k = exp(-dtau (eps_k - mu)), so G = M^{-1}
+    splits into one T x T matrix per k, G_k(l, l') = b^(l-l') / (1 + b^T) for
+    l >= l' and -b^(T+l-l') / (1 + b^T) for l < l' (the inverse of the
+    antiperiodic bidiagonal matrix of Eq. (M_def)). Written from that:
+      <n>  = 2 (1 - (1/N) sum_k 1/(1 + b_k^T));
+      C(r) = 4 (1 - g(0))^2 + 2 (delta_r0 - g(r)) g(r),
+             g(r) = (1/N) sum_k e^{i k.r} / (1 + b_k^T) (equal-time G, even in r);
+      P_s  = dtau / (N T) sum_{l, l'} sum_{r, r'} G^2 = dtau / (N T) sum_k
+             sum_{l, l'} G_k(l, l')^2 (the Fourier transform keeps the
+             Frobenius norm of every N x N block).
+    A wrong dtau, 1/N or slice range in P_s, or a wrong sign or index in the
+    C(r) contraction, fails it."""
+    m = D.Model(L=L, Ltau=T, mu=mu, kinetic="exact")
+    x = np.zeros((T, m.N))
+    ks = 2 * np.pi * np.arange(L) / L
+    kx, ky = np.meshgrid(ks, ks, indexing="xy")         # [iky][ikx]
+    eps = -2 * m.t * (np.cos(kx) + np.cos(ky))
+    b = np.exp(-m.dtau * (eps - mu))
+    occ = 1.0 / (1.0 + b ** T)                            # G_k(l, l)
+    dens = 2.0 * (1.0 - occ.mean())
+    g = np.real(np.fft.ifft2(occ))                        # g(r) at [dy][dx]
+    delta = np.zeros((L, L))
+    delta[0, 0] = 1.0
+    C = 4.0 * (1.0 - g[0, 0]) ** 2 + 2.0 * (delta - g) * g
+    ps = 0.0
+    for bk in b.ravel():
+        for d in range(T):                                # l - l' = d >= 0: T - d pairs
+            ps += (T - d) * (bk ** d / (1.0 + bk ** T)) ** 2
+        for d in range(1, T):                             # l' - l = d > 0: T - d pairs
+            ps += (T - d) * (bk ** (T - d) / (1.0 + bk ** T)) ** 2
+    ps *= m.dtau / (m.N * T)
+    ex = D.observables_exact(m, x)
+    assert abs(ex["density"] - dens) < 1e-12
+    assert np.abs(ex["C"] - C).max() < 1e-12
+    assert abs(ex["P_s"] - ps) < 1e-12 * ps
+    S = float(np.sum(np.array([[(-1.0) ** (dx + dy) for dx in range(L)] for dy in range(L)]) * C))
+    assert abs(ex["S_cdw"] - S) < 1e-12 * max(1.0, abs(S))
+    # the contraction of the estimators' expectations gives the same P_s
+    es = D.observables_from_estimates(m, D.green_average_exact(m, x), D.wick_products_exact(m, x))
+    assert abs(es["P_s"] - ps) < 1e-12 * ps
+    assert np.abs(es["C"] - C).max() < 1e-12
+
+
 # ---------------------------------------------------------------- Arnoldi bounds (App. C D)
 def test_arnoldi_full_dimension_gives_the_spectrum():
     """N steps of Arnoldi span the whole space: the Ritz values are the
