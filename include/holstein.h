@@ -369,10 +369,13 @@ int measure_batch(hol_ctx* const* ctxs, int n_chains, const double* const* xi, i
  * entirely by another allocator (a framework's caching allocator, or a budget
  * fixed at start-up), and code that must not trigger the device-wide
  * synchronisation that cudaMalloc / cudaFree can imply. It needs no context:
- * out = M v, M^T v or M^T M v (op = HOL_OP_M, HOL_OP_MT, HOL_OP_MTM; same
- * operator and same kernels as fermion_matvec with HOL_F64) for the field x
- * and the couplings in p (p->max_rhs is ignored). x: FP64 [T][N]; v, out: FP64
- * [n_rhs][T][N], device, must not overlap.
+ * out = M v, M^T v or M^T M v (op = HOL_OP_M, HOL_OP_MT, HOL_OP_MTM; the
+ * operator and kernels of fermion_matvec with HOL_F64 in a checkerboard
+ * context) for the field x and the couplings in p (p->max_rhs and p->omega0
+ * are ignored). Only the checkerboard propagator is supported: p->kinetic must
+ * be HOL_KINETIC_CHECKERBOARD, else HOL_EINVAL. The couplings are checked as
+ * hol_create checks them (dtau > 0; t, mu and alpha finite). x: FP64 [T][N];
+ * v, out: FP64 [n_rhs][T][N], device; their address ranges must not overlap.
  *
  * Scratch: one file-scope device array of 2^20 doubles (8 MiB) that every GPU
  * loading this library holds until the process exits. A call needs N*T

@@ -734,6 +734,42 @@ def cross_corr_direct(a2: np.ndarray, b2: np.ndarray, L: int) -> np.ndarray:
     return out
 
 
+def cross_corr_at(a2: np.ndarray, b2: np.ndarray, L: int, deltas) -> np.ndarray:
+    """(a star b)_Delta = sum_i a_i b_{i+Delta} (Eq. (cross_corr)) over the
+    periodic doubled domain, by direct summation at the listed offsets only.
+    deltas: sequence of (dl, dy, dx). Returns one value per offset."""
+    return np.array([np.sum(a2.reshape(-1) * _shift(b2, L, dl, dy, dx).reshape(-1))
+                     for dl, dy, dx in deltas])
+
+
+def green_average_at(m: Model, xi, Gxi, deltas) -> np.ndarray:
+    """green_average at the listed offsets (dl, dy, dx) only:
+    (1/N_rv) sum_n (1/(2 N T)) (Q xi_n star Q G xi_n)_Delta (Eqs. (G_avg-1),
+    (G_def-1), (cross_corr), (G_approx_better))."""
+    out = np.zeros(len(deltas))
+    for v, gv in zip(xi, Gxi):
+        out += cross_corr_at(extend(v), extend(gv), m.L, deltas)
+    return out / (2.0 * m.n * len(xi))
+
+
+def four_point_pairs_at(m: Model, xi, Gxi, deltas) -> np.ndarray:
+    """four_point_pairs at the listed offsets only: the three pair-averaged
+    Wick products of Sec. V C (Eq. (GG_approx_better)) over all pairs n < k,
+    each by direct summation. Returns [3][len(deltas)]."""
+    a = [extend(v) for v in xi]
+    b = [extend(v) for v in Gxi]
+    R = len(xi)
+    out = np.zeros((3, len(deltas)))
+    npairs = 0
+    for n in range(R):
+        for k in range(n + 1, R):
+            out[0] += cross_corr_at(a[n] * a[k], b[n] * b[k], m.L, deltas)
+            out[1] += cross_corr_at(a[n] * b[n], a[k] * b[k], m.L, deltas)
+            out[2] += cross_corr_at(a[n] * b[k], a[k] * b[n], m.L, deltas)
+            npairs += 1
+    return out / (2.0 * m.n * npairs)
+
+
 def green_average(m: Model, x, xi, Gxi=None) -> np.ndarray:
     """Space-time averaged Green function estimate, Eqs. (G_avg-1), (G_def-1), (cross_corr), averaged
     over the probe vectors (Eq. (G_approx_better)): (1/N_rv) sum_n (1/(2 N T)) (a_n star b_n)

@@ -65,6 +65,14 @@ inline int require_aligned(const char* fn, std::initializer_list<const void*> pt
     return HOL_OK;
 }
 
+// True when the byte ranges [a, a + na) and [b, b + nb) share an address
+// (host-side aliasing check of two device arrays of the C ABI).
+inline bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb)
+{
+    const uintptr_t pa = reinterpret_cast<uintptr_t>(a), pb = reinterpret_cast<uintptr_t>(b);
+    return pa < pb + nb && pb < pa + na;
+}
+
 // A CG step ratio (alpha or beta) num / den, 0 when it is not finite. On a
 // small system the residual can reach exactly zero between two convergence
 // polls; the next step then has 0 / 0, and a zero step keeps the solution

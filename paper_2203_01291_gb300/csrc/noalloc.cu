@@ -71,10 +71,15 @@ extern "C" int fermion_matvec_static(const hol_params* p, const double* x, int o
     if (op != HOL_OP_M && op != HOL_OP_MT && op != HOL_OP_MTM)
         return set_error(HOL_EINVAL, "fermion_matvec_static: bad op %d", op);
     if (n_rhs < 1) return set_error(HOL_EINVAL, "fermion_matvec_static: n_rhs=%d", n_rhs);
+    if (!(p->dtau > 0.0) || !isfinite(p->t) || !isfinite(p->mu) || !isfinite(p->alpha))
+        return set_error(HOL_EINVAL, "fermion_matvec_static: dtau must be > 0 and t, mu, alpha "
+                                     "finite");
     if (p->kinetic != HOL_KINETIC_CHECKERBOARD)
         return set_error(HOL_EINVAL, "fermion_matvec_static: checkerboard propagator only");
-    if (v == out) return set_error(HOL_EINVAL, "fermion_matvec_static: v and out must not overlap");
     const long n = (long)p->L * p->L * p->Ltau;
+    const size_t vbytes = (size_t)n_rhs * (size_t)n * sizeof(double);
+    if (ranges_overlap(v, vbytes, out, vbytes))
+        return set_error(HOL_EINVAL, "fermion_matvec_static: v and out must not overlap");
     const long need = n + (op == HOL_OP_MTM ? (long)n_rhs * n : 0);
     if (need > kStaticDoubles)
         return set_error(HOL_EINVAL,

@@ -195,3 +195,45 @@ def test_header_is_plain_c_and_cxx(tmp_path, lang, std):
                         "-I", os.path.join(ROOT, "include"), str(src)],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+@pytest.mark.parametrize("case", ["dtau0", "t_nan", "mu_nan", "alpha_inf", "exact", "overlap",
+                                  "overlap_tail", "oversize"])
+def test_static_operator_refuses_bad_arguments_on_the_host(case):
+    """fermion_matvec_static validates couplings, propagator, aliasing (by
+    address range, not only equal pointers) and the static scratch limit on
+    the host before it looks at a device; the fake device addresses below
+    are never dereferenced."""
+    from paper_2203_01291_gb300 import _abi
+    lib = _abi.load()
+    L, T, nr = 8, 8, 2
+    p = _abi.hol_params(L, T, 0.1, 1.0, 0.2, 1.0, 1.0, 1, 0)
+    nbytes = nr * L * L * T * 8
+    x, v, out = 0x100000, 0x200000, 0x200000 + nbytes
+    if case == "dtau0":
+        p.dtau = 0.0
+    elif case == "t_nan":
+        p.t = float("nan")
+    elif case == "mu_nan":
+        p.mu = float("nan")
+    elif case == "alpha_inf":
+        p.alpha = float("inf")
+    elif case == "exact":
+        p.kinetic = _abi.HOL_KINETIC_EXACT
+    elif case == "overlap":
+        out = v + 16 * 64                 # inside v's range, different pointer
+    elif case == "overlap_tail":
+        out = v - nbytes + 16             # ends inside v's range
+    elif case == "oversize":
+        p.L, p.Ltau = 32, 400             # 409600 doubles per rhs: 3 rhs of M^T M exceed 2^20
+        nr = 3
+        out = 0x40000000                  # far from v: only the size is wrong
+    rc = lib.fermion_matvec_static(ctypes.byref(p), ctypes.c_void_p(x), _abi.HOL_OP_MTM,
+                                   ctypes.c_void_p(v), ctypes.c_void_p(out), nr, None)
+    assert rc == _abi.HOL_EINVAL, case
+    msg = lib.hol_last_error().decode()
+    assert msg
+    if case == "oversize":
+        assert "scratch" in msg
+    if case.startswith("overlap"):
+        assert "overlap" in msg

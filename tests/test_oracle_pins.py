@@ -424,6 +424,32 @@ def test_cross_correlation_direct_equals_fft():
     assert np.abs(out - ref).max() < 1e-12
 
 
+def test_cross_correlation_at_offsets_equals_fft_and_full_estimators():
+    """The selected-offset sums equal the FFT cross-correlation (numpy's
+    fftn, a different route) at those offsets, and the selected-offset 2-
+    and 4-point estimators equal the full-array ones there (probes and
+    stand-in solutions random; the estimators are bilinear in them)."""
+    g = rng(43)
+    L, T2 = 6, 10
+    a, b = g.standard_normal((2, T2, L * L))
+    deltas = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (3, 2, 5), (9, 5, 1), (5, 3, 3),
+              (7, 0, 4)]
+    fa, fb = np.fft.fftn(a.reshape(T2, L, L)), np.fft.fftn(b.reshape(T2, L, L))
+    full = np.fft.ifftn(np.conj(fa) * fb).real
+    out = D.cross_corr_at(a, b, L, deltas)
+    assert np.abs(out - np.array([full[d] for d in deltas])).max() < 1e-12
+    m = D.Model(L=L, Ltau=T2 // 2)
+    xi = np.sign(g.standard_normal((4, m.Ltau, m.N)))
+    gx = g.standard_normal((4, m.Ltau, m.N))
+    G2 = D.green_average(m, None, xi, gx)
+    G4 = D.four_point_pairs(m, None, xi, gx)
+    assert np.abs(D.green_average_at(m, xi, gx, deltas) - np.array([G2[d] for d in deltas])).max() \
+        < 1e-13
+    at4 = D.four_point_pairs_at(m, xi, gx, deltas)
+    for k in range(3):
+        assert np.abs(at4[k] - np.array([G4[k][d] for d in deltas])).max() < 1e-13
+
+
 def test_green_average_complete_probe_sets_are_exact():
     """sum_k (G xi_k) xi_k^T = G for the unit vectors and (times n) for the
     rows of a Hadamard matrix, so the stochastic average (Eq. (G_approx_better))

@@ -43,6 +43,32 @@ def test_static_scratch_operator_matches_context_operator():
             assert _rel(out.cpu().numpy(), ref.cpu().numpy()) < 1e-13, (call, op)
 
 
+def test_static_scratch_operator_with_chemical_potential():
+    """mu != 0 and a coupling other than 1: a sign or factor error in the
+    exp(-dtau (alpha x - mu)) table of the static path would show here (the
+    hmc16 workload above has mu = 0). Two calls in a row, all three ops."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    hg.build.build()
+    torch.cuda.set_device(0)
+    w = hi.Workload("static_mu", L=12, Ltau=24, alpha=0.8, mu=0.35, omega0=1.0, x_std=1.0,
+                    seed=61)
+    params = hg.hol_params(w.L, w.Ltau, w.dtau, w.t, w.mu, w.alpha, w.omega0, 3)
+    with hg.Context.from_workload(w, max_rhs=3) as ctx:
+        x = torch.tensor(hi.phonon_field(w), device="cuda")
+        ctx.set_field(x)
+        for call in range(2):
+            for op in (hg.HOL_OP_M, hg.HOL_OP_MT, hg.HOL_OP_MTM):
+                v = torch.tensor(hi.gaussian_vectors(w, 3, seed=70 + 3 * call + op),
+                                 device="cuda")
+                ref = torch.empty_like(v)
+                ctx.fermion_matvec(op, v, ref)
+                out = torch.full_like(v, float("nan"))
+                hg.fermion_matvec_static(params, x, op, v, out, 3)
+                torch.cuda.synchronize()
+                assert _rel(out.cpu().numpy(), ref.cpu().numpy()) < 1e-13, (call, op)
+
+
 def test_static_scratch_rejects_oversize():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
