@@ -115,6 +115,22 @@ def phonon_field_ar1(w: Workload, corr: float, seed: int | None = None) -> np.nd
     return np.ascontiguousarray(x * w.x_std + w.x_shift, dtype=np.float64)
 
 
+def phonon_field_prior(w: Workload, seed: int | None = None) -> np.ndarray:
+    """x[tau][i] drawn from the free-phonon law exp(-S_B): per site, the
+    Gaussian whose inverse covariance is the quadratic form of the discrete
+    harmonic-oscillator action S_B = (dtau/2) sum_tau [omega0^2 x_tau^2 +
+    ((x_{tau+1} - x_tau)/dtau)^2] (periodic in tau). That form is circulant
+    in tau with eigenvalues q_k = dtau (omega0^2 + (2 - 2 cos(2 pi k/T))/dtau^2),
+    so x = F^{-1} q^{-1/2} F R with R ~ N(0, 1) i.i.d. (numpy's FFT along
+    tau), plus x_shift. tau-smooth, unlike phonon_field."""
+    g = _rng(w.seed if seed is None else seed)
+    R = g.standard_normal((w.Ltau, w.N))
+    k = np.arange(w.Ltau)
+    q = w.dtau * (w.omega0 ** 2 + (2.0 - 2.0 * np.cos(2.0 * np.pi * k / w.Ltau)) / w.dtau ** 2)
+    x = np.fft.ifft(np.fft.fft(R, axis=0) / np.sqrt(q)[:, None], axis=0).real
+    return np.ascontiguousarray(x + w.x_shift, dtype=np.float64)
+
+
 def gaussian_vectors(w: Workload, count: int, seed: int) -> np.ndarray:
     """R[k][tau][i] ~ N(0, 1), i.i.d. (pseudofermion / momentum draws)."""
     g = _rng(seed)

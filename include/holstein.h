@@ -184,6 +184,8 @@ int cg_solve(hol_ctx* ctx, const double* b, double* v, int n_rhs,
  * with_bosonic != 0 adds dS_B/dx of Eq. (dSB_dx) for the field of the last
  * hol_set_field. S_F (device, nullable, one double) receives
  * (1/2) sum_sigma b_sigma . v_sigma (Eq. (Sf_Psi)). dSdx is overwritten.
+ * With dSdx null (and S_F not null) only the action S_F is computed: no
+ * force, no B_tau sweep. HOL_EINVAL when both are null.
  */
 int force(hol_ctx* ctx, const double* v, const double* b, int n_pf,
           double* dSdx, int with_bosonic, double* S_F, void* stream);

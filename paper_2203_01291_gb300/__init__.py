@@ -101,13 +101,14 @@ def cg_solve(handle, b: torch.Tensor, v: torch.Tensor, n_rhs: int, n: int, opts:
     return np.array(it[:], dtype=np.int64), np.array(rs[:], dtype=np.float64)
 
 
-def force(handle, v: torch.Tensor, b: torch.Tensor, n_pf: int, dSdx: torch.Tensor,
+def force(handle, v: torch.Tensor, b: torch.Tensor, n_pf: int, dSdx: torch.Tensor | None,
           with_bosonic: bool, S_F: torch.Tensor | None, n: int) -> None:
+    """Phonon force into dSdx and/or the action into S_F (dSdx None: action only)."""
     sf = _ptr(S_F, torch.float64, 1, "S_F") if S_F is not None else None
+    f = _ptr(dSdx, torch.float64, n, "dSdx") if dSdx is not None else None
     _check(load().force(handle, _ptr(v, torch.float64, n_pf * n, "v"),
-                        _ptr(b, torch.float64, n_pf * n, "b"), n_pf,
-                        _ptr(dSdx, torch.float64, n, "dSdx"), int(bool(with_bosonic)), sf,
-                        _stream()))
+                        _ptr(b, torch.float64, n_pf * n, "b"), n_pf, f,
+                        int(bool(with_bosonic)), sf, _stream()))
 
 
 def precond_apply(handle, which: int, prec: int, v: torch.Tensor, out: torch.Tensor, n_rhs: int,
@@ -365,7 +366,7 @@ class Context:
         opts = hol_cg_opts(tol, max_iter, int(bool(precond)), prec, reliable_every, check_every)
         return cg_solve(self._h, b, v, self._nrhs(b), self.n, opts, raise_on_nonconv)
 
-    def force(self, v: torch.Tensor, b: torch.Tensor, dSdx: torch.Tensor,
+    def force(self, v: torch.Tensor, b: torch.Tensor, dSdx: torch.Tensor | None,
               with_bosonic: bool = True, S_F: torch.Tensor | None = None) -> None:
         force(self._h, v, b, self._nrhs(v), dSdx, with_bosonic, S_F, self.n)
 

@@ -131,6 +131,27 @@ __global__ void k_sf_finish(const double* __restrict__ part, int cnt, double* __
     if (threadIdx.x == 0) *out = 0.5 * s;
 }
 
+// Partial sums of b . v over all pseudofermions, one per block in a fixed
+// order (the action alone, Eq. (Sf_Psi), without the force).
+__global__ void k_sf_dot(const double* __restrict__ v, const double* __restrict__ b, long len,
+                         double* __restrict__ part)
+{
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < len;
+         k += (long)gridDim.x * blockDim.x)
+        acc = fma(b[k], v[k], acc);
+    acc = warp_sum(acc);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = acc;
+    __syncthreads();
+    if (wid == 0) {
+        acc = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+        acc = warp_sum(acc);
+        if (lane == 0) part[blockIdx.x] = acc;
+    }
+}
+
 // Launch plan of the force kernel. Nothing is reused between the slices of
 // a run, so each run is one slice (K = 1) unless the per-run partial sums of
 // S_F would not fit the partial-sum bank. The pseudofermions are split into
@@ -224,11 +245,25 @@ extern "C" int force(hol_ctx* c, const double* v, const double* b, int n_pf, dou
                      int with_bosonic, double* S_F, void* stream)
 {
     HOL_TRACE("force");
-    if (!c || !v || !b || !dSdx) return set_error(HOL_EINVAL, "force: null argument");
+    if (!c || !v || !b || (!dSdx && !S_F)) return set_error(HOL_EINVAL, "force: null argument");
     if (int rc_ = require_aligned("force", {v, b, dSdx})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "force: hol_set_field not called");
     if (n_pf < 0 || n_pf > c->p.max_rhs)
         return set_error(HOL_EINVAL, "force: n_pf=%d outside [0, %d]", n_pf, c->p.max_rhs);
+    if (!dSdx) {   // the action alone
+        cudaStream_t s = (cudaStream_t)stream;
+        double* part = c->part + 6 * c->part_len;
+        const long len = (long)n_pf * c->n;
+        long nb = (len + 255) / 256;
+        if (nb > 1024) nb = 1024;
+        if (nb > c->part_len) nb = c->part_len;
+        if (nb < 1) nb = 1;
+        k_sf_dot<<<(int)nb, 256, 0, s>>>(v, b, len, part);
+        HOL_CHECK_LAUNCH("k_sf_dot");
+        k_sf_finish<<<1, 32, 0, s>>>(part, (int)nb, S_F);
+        HOL_CHECK_LAUNCH("k_sf_finish");
+        return HOL_OK;
+    }
     timer_start(c, KT_FORCE, (cudaStream_t)stream);
     int rc = launch_force(c, v, b, n_pf, dSdx, with_bosonic, S_F, (cudaStream_t)stream);
     timer_stop(c, KT_FORCE, (cudaStream_t)stream);

@@ -548,3 +548,24 @@ def test_big32_preconditioned_solve_certified():
     for k in range(4):
         assert res[k] < 1e-8
         assert MF.rel_residual(w, x, b[k], v[k]) < 1.01e-8
+
+
+def test_force_action_only_mode():
+    """force with a null dSdx computes the action alone: the same S_F as the
+    full call, and HOL_EINVAL when both outputs are null."""
+    import ctypes
+    w, x = _field(8, 12, seed=17)
+    m = D.model_of(w)
+    Phi = hi.gaussian_vectors(w, 3, seed=18)
+    b = D.b_from_phi(m, x, Phi)
+    v = np.stack([D.solve_MTM(m, x, bb) for bb in b])
+    with _ctx(w, 3) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        vt, bt = torch.tensor(v, device=DEV), torch.tensor(b, device=DEV)
+        SF = torch.empty(1, device=DEV, dtype=torch.float64)
+        ctx.force(vt, bt, None, False, SF)
+        assert abs(float(SF) - D.S_F(m, x, Phi)) < 1e-11 * abs(D.S_F(m, x, Phi))
+        p = ctypes.c_void_p
+        rc = hg._abi.load().force(ctx._h, p(vt.data_ptr()), p(bt.data_ptr()), 3, None, 0, None,
+                                  p(torch.cuda.current_stream().cuda_stream))
+        assert rc == hg._abi.HOL_EINVAL

@@ -146,3 +146,20 @@ def test_hmc16_trajectory_energy_error_scales_as_dt2():
             out.append(dH)
     assert abs(out[1]) < 1.0
     assert 2.5 < abs(out[0]) / abs(out[1]) < 6.0
+
+
+@pytest.mark.parametrize("m_reg", [1.0, float("inf")])
+def test_mass_operators_vs_dense_hmc16_shape(m_reg):
+    """The Fourier-acceleration mass at the trajectory workload's own shape
+    (L=16, Ltau=160: the tau transform specialised for 160) against the
+    dense-DFT oracle."""
+    w = hi.WORKLOADS["hmc16"]
+    m = D.model_of(w)
+    p = hi.gaussian_vectors(w, 1, seed=31)[0]
+    with hg.Context.from_workload(w) as ctx:
+        pt = torch.tensor(p, device=DEV)
+        out = torch.empty_like(pt)
+        for which, power in ((0, -1.0), (1, 0.5), (2, 1.0)):
+            ctx.mass_apply(which, m_reg, pt, out)
+            ref = D.mass_apply(m, p, m_reg, power)
+            assert _rel(out.cpu().numpy(), ref) < 1e-12, (which, m_reg)

@@ -164,3 +164,44 @@ def test_pcg_hmc16_certified_by_oracle():
         assert res_p[k] < 1e-8
         assert MF.rel_residual(w, x, b[k], vp[k]) < 1.01e-8
     assert np.mean(its_p) < np.mean(its_0)
+
+
+FULL_SIZE = {
+    # the fields the benchmark rows precondition: the L=32 CG workload, the
+    # hmc16 trajectory workload, and the L=28 chain of the batching workload;
+    # Ltau = 200, 160 and 120 run the tau transforms specialised for them
+    "big32": hi.WORKLOADS["big32"],
+    "hmc16": hi.WORKLOADS["hmc16"],
+    "chain28": hi.chain_workloads(8, 120)[-1],
+}
+
+
+@pytest.mark.parametrize("name", sorted(FULL_SIZE))
+def test_precond_full_size_vs_oracle(name):
+    """P^{-1}, P^{-T} and P^{-1} P^{-T} at the workloads' own shapes, with the
+    launch dispatch the benchmark takes (default options, tuned operator
+    shapes), element by element against the oracle's step-by-step KPM in
+    FP64 (1e-11) and FP32 (2e-5), 2 right-hand sides. A wrong twiddle in a
+    length-specialised transform would give a preconditioner that is still
+    SPD (so PCG still converges) but not this one."""
+    w = FULL_SIZE[name]
+    assert w.Ltau in (120, 160, 200)
+    m = D.model_of(w)
+    x = hi.phonon_field(w)
+    v = hi.gaussian_vectors(w, 2, seed=19)
+    refs = {
+        hg.HOL_PINV: np.stack([D.precond_inverse_apply(m, x, a) for a in v]),
+        hg.HOL_PINVT: np.stack([D.precond_inverse_apply(m, x, a, trans=True) for a in v]),
+    }
+    refs[hg.HOL_PINV_PINVT] = np.stack(
+        [D.precond_inverse_apply(m, x, D.precond_inverse_apply(m, x, a, trans=True)) for a in v])
+    with hg.Context.from_workload(w, max_rhs=2) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        ctx.tune(2)
+        for which, ref in refs.items():
+            for dt, tol in ((torch.float64, 1e-11), (torch.float32, 2e-5)):
+                vt = torch.tensor(v, device=DEV, dtype=dt)
+                out = torch.empty_like(vt)
+                ctx.precond_apply(which, vt, out)
+                err = _rel(out.cpu().double().numpy(), ref)
+                assert err < tol, (name, which, dt, err)

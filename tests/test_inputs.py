@@ -52,3 +52,23 @@ def test_chain_batch_layout():
     assert len(ws) == 48
     assert sorted({w.L for w in ws}) == list(hi.CHAIN_SIZES)
     assert len({w.seed for w in ws}) == 48 and all(w.Ltau == 120 for w in ws)
+
+
+def test_prior_field_has_the_free_phonon_covariance():
+    """phonon_field_prior samples exp(-S_B): the sample covariance along tau
+    matches the inverse of the action's quadratic form (built densely here
+    from the stencil), and S_B averages N T / 2 (equipartition)."""
+    w = hi.Workload("p", L=32, Ltau=20, omega0=0.7, dtau=0.1, seed=12)
+    x = hi.phonon_field_prior(w)
+    assert x.shape == (w.Ltau, w.N) and np.array_equal(x, hi.phonon_field_prior(w))
+    T, dt = w.Ltau, w.dtau
+    A = np.zeros((T, T))
+    for t in range(T):
+        A[t, t] += dt * w.omega0 ** 2 + 2.0 / dt
+        A[t, (t + 1) % T] -= 1.0 / dt
+        A[(t + 1) % T, t] -= 1.0 / dt
+    C = np.linalg.inv(A)
+    emp = x @ x.T / w.N
+    assert np.abs(emp - C).max() < 6 * C.max() * np.sqrt(2.0 / w.N)
+    SB = 0.5 * dt * np.sum(w.omega0 ** 2 * x * x + ((np.roll(x, -1, axis=0) - x) / dt) ** 2)
+    assert abs(SB / (w.N * T / 2) - 1.0) < 5 * np.sqrt(2.0 / (w.N * T))
