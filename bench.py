@@ -720,9 +720,9 @@ def chains_leg(dev, n_rv=128, precs=None, repeats=3):
     # blocks of 16; the concurrent chains already fill the GPU)
     ctxs = [hg.Context.from_workload(w, max_rhs=64) for w in ws]
     out = {"workload": "48 chains, L in {8..28} x 8, Ltau=120; one trajectory (N_t=20, n_t=4, "
-                       "PCG, forces 1e-5, action 1e-10) per chain in each precision, and one "
-                       "128-probe measurement per chain (mixed, 1e-8), chains concurrent on "
-                       "host-driven streams"}
+                       "PCG, forces 1e-5, action 1e-10) per chain in each precision (graph "
+                       "path; the host-thread path for comparison), and one 128-probe "
+                       "measurement per chain (mixed, 1e-8, host-thread path)"}
     try:
         x0 = [hi.phonon_field(w) for w in ws]
         xs = [torch.tensor(x, device=dev) for x in x0]
@@ -733,7 +733,8 @@ def chains_leg(dev, n_rv=128, precs=None, repeats=3):
         Rps = [torch.tensor(hi.gaussian_vectors(w, 1, seed=w.seed + 2)[0], device=dev)
                for w in ws]
         u = hi.uniforms(len(ws), seed=903)
-        for prec in precs:
+        runs = [("graph", p) for p in precs] + [("threads", hg.HOL_F32)]
+        for path, prec in runs:
             o = hg.md_opts(0.01, 20, 4, 1.0, force_tol=1e-5, action_tol=1e-10, prec=prec,
                            precond=True)
             times, accs = [], []
@@ -742,17 +743,24 @@ def chains_leg(dev, n_rv=128, precs=None, repeats=3):
                     x.copy_(torch.from_numpy(xh))
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                acc, dh = hg.hmc_batch(ctxs, xs, Rs, Rps, o, u, n_threads=8)
+                if path == "graph":
+                    acc, dh = hg.hmc_batch_graph(ctxs, xs, Rs, Rps, o, u)
+                else:
+                    acc, dh = hg.hmc_batch(ctxs, xs, Rs, Rps, o, u, n_threads=8)
                 torch.cuda.synchronize()
                 if rep:
                     times.append(time.perf_counter() - t0)
                     accs.append(int(np.sum(acc)))
-            key = "mixed" if prec == hg.HOL_F32 else "fp64"
+            key = ("mixed" if prec == hg.HOL_F32 else "fp64") + \
+                ("" if path == "graph" else "_host_threads")
             t = float(np.mean(times))
             out[key] = {"trajectories_per_s": len(ws) / t, "ms_all_trajectories": t * 1e3,
                         "ms_min": float(np.min(times)) * 1e3, "ms_max": float(np.max(times)) * 1e3,
                         "repeats": repeats, "accepted": accs[-1], "of": len(ws),
-                        "mean_abs_dH": float(np.mean(np.abs(dh)))}
+                        "mean_abs_dH": float(np.mean(np.abs(dh))),
+                        "path": "one captured CUDA graph per leapfrog step over all 48 chains, "
+                                "solves device-driven (hmc_batch_graph)" if path == "graph" else
+                                "one stream per chain, driven by 8 host threads (hmc_batch)"}
         if "mixed" in out and "fp64" in out:
             out["mixed_over_fp64"] = out["mixed"]["trajectories_per_s"] / \
                 out["fp64"]["trajectories_per_s"]

@@ -365,6 +365,46 @@ int measure_batch(hol_ctx* const* ctxs, int n_chains, const double* const* xi, i
                   double* const* G4, int four_point, int n_threads);
 
 /*
+ * Graph-launched solve and batched trajectories (no counterpart in the paper:
+ * the paper's solver and HMC driver are host loops).
+ *
+ * cg_solve_graph: the solve of cg_solve -- the same kernels, the same
+ * decisions, so bitwise the same v, iterations and residuals -- with every
+ * decision of its loop taken on the device: the loop over chunks of
+ * check_every iterations is a conditional WHILE node of a CUDA graph, the
+ * reliable update (and the certification by the FP64 true residual) a
+ * conditional IF node inside it; the host launches the graph once and waits
+ * for it. Requires an even check_every and the two-kernel CG iteration
+ * (options fused_cg, merged_cg and persistent_cg off), else HOL_EINVAL. The
+ * loop runs whole chunks: with max_iter not a multiple of check_every it can
+ * run up to check_every - 1 iterations past max_iter before HOL_ENOTCONV; the
+ * number of chunks is bounded by max_iter / check_every + 2 in every case (no
+ * device-side wait exists that could hang). Arguments and results as
+ * cg_solve; uses the context's scratch and internal streams; synchronises
+ * `stream`.
+ *
+ * hmc_batch_graph: one HMC trajectory (Algorithm 1, as fourier_accel_leapfrog)
+ * for each of n_chains independent chains with their own contexts (any mix
+ * of lattice sizes; no context repeated). The start of all chains, one
+ * leapfrog step of all chains and the end of all chains are each captured
+ * once into one CUDA graph (each chain on its own branch, its solves
+ * graph-driven as in cg_solve_graph); the step graph is launched n_steps
+ * times; the host reads the energies at the end and takes the Metropolis
+ * decisions with u[k] (host array). x[k], R_pf[k] ([n_pf][T_k][N_k]), R_p[k]
+ * as in fourier_accel_leapfrog; accepted, dH (host arrays of n_chains,
+ * nullable). Each chain's result is bitwise the one fourier_accel_leapfrog
+ * gives it. Both solver option sets need what cg_solve_graph needs. On a
+ * failed solve (HOL_ENOTCONV or HOL_ENUMERIC, naming the chain) the fields of
+ * all chains are left at the end of the trajectory. Synchronises `stream`.
+ */
+int cg_solve_graph(hol_ctx* ctx, const double* b, double* v, int n_rhs, const hol_cg_opts* opts,
+                   int* iters, double* resid, void* stream);
+int hmc_batch_graph(hol_ctx* const* ctxs, int n_chains, double* const* x,
+                    const double* const* R_pf, const double* const* R_p, int n_pf,
+                    const hol_md_opts* opts, const double* u, int* accepted, double* dH,
+                    void* stream);
+
+/*
  * Allocation-free FP64 fermion operator (no counterpart in the paper).
  *
  * For callers that cannot call cudaMalloc: code whose device memory is owned

@@ -33,7 +33,7 @@ __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F6
            "pseudofermion_phi", "phi_to_rhs", "hol_launch_count", "hol_timer_enable",
            "hol_timer_read", "fermion_matvec_static", "mass_apply", "md_integrate",
            "fourier_accel_leapfrog", "hol_md_opts", "stochastic_measure", "hol_tune",
-           "hmc_batch", "measure_batch", "hol_set_option", "hol_get_option", "hol_fma_peak",
+           "hmc_batch", "hmc_batch_graph", "cg_solve_graph", "measure_batch", "hol_set_option", "hol_get_option", "hol_fma_peak",
            "global_update", "HOL_REFLECT", "HOL_SWAP", "measure_observables",
            "HOL_KINETIC_CHECKERBOARD", "HOL_KINETIC_EXACT", "hol_arnoldi_bounds",
            "hol_get_bounds",
@@ -96,6 +96,19 @@ def cg_solve(handle, b: torch.Tensor, v: torch.Tensor, n_rhs: int, n: int, opts:
     rc = load().cg_solve(handle, _ptr(b, torch.float64, n_rhs * n, "b"),
                          _ptr(v, torch.float64, n_rhs * n, "v"), n_rhs, ctypes.byref(opts), it,
                          rs, _stream())
+    if rc != HOL_OK and (rc != HOL_ENOTCONV or raise_on_nonconv):
+        _check(rc)
+    return np.array(it[:], dtype=np.int64), np.array(rs[:], dtype=np.float64)
+
+
+def cg_solve_graph(handle, b: torch.Tensor, v: torch.Tensor, n_rhs: int, n: int,
+                   opts: hol_cg_opts, raise_on_nonconv: bool = True):
+    """cg_solve as one CUDA graph launch (include/holstein.h, cg_solve_graph)."""
+    it = (ctypes.c_int * n_rhs)()
+    rs = (ctypes.c_double * n_rhs)()
+    rc = load().cg_solve_graph(handle, _ptr(b, torch.float64, n_rhs * n, "b"),
+                               _ptr(v, torch.float64, n_rhs * n, "v"), n_rhs, ctypes.byref(opts),
+                               it, rs, _stream())
     if rc != HOL_OK and (rc != HOL_ENOTCONV or raise_on_nonconv):
         _check(rc)
     return np.array(it[:], dtype=np.int64), np.array(rs[:], dtype=np.float64)
@@ -255,6 +268,21 @@ def hmc_batch(contexts, xs, R_pfs, R_ps, opts: hol_md_opts, us, n_threads: int =
     return np.array(acc[:], dtype=bool), np.array(dh[:])
 
 
+def hmc_batch_graph(contexts, xs, R_pfs, R_ps, opts: hol_md_opts, us):
+    """Algorithm 1 once for every chain, all chains in one captured CUDA graph
+    per leapfrog step (include/holstein.h, hmc_batch_graph); returns
+    (accepted[n], dH[n])."""
+    n = len(contexts)
+    hs = (ctypes.c_void_p * n)(*[c.handle.value for c in contexts])
+    n_pf = R_pfs[0].numel() // contexts[0].n
+    acc = (ctypes.c_int * n)()
+    dh = (ctypes.c_double * n)()
+    u = (ctypes.c_double * n)(*[float(v) for v in us])
+    _check(load().hmc_batch_graph(hs, n, _ptrs(xs), _ptrs(R_pfs), _ptrs(R_ps), n_pf,
+                                  ctypes.byref(opts), u, acc, dh, _stream()))
+    return np.array(acc[:], dtype=bool), np.array(dh[:])
+
+
 def measure_batch(contexts, xis, Gxis, G2s, opts: hol_cg_opts, G4s=None, four_point: int = 0,
                   n_threads: int = 8) -> None:
     n = len(contexts)
@@ -365,6 +393,14 @@ class Context:
                  raise_on_nonconv: bool = True):
         opts = hol_cg_opts(tol, max_iter, int(bool(precond)), prec, reliable_every, check_every)
         return cg_solve(self._h, b, v, self._nrhs(b), self.n, opts, raise_on_nonconv)
+
+    def cg_solve_graph(self, b: torch.Tensor, v: torch.Tensor, tol: float = 1e-10,
+                       max_iter: int = 10000, precond: bool = False, prec: int = HOL_F64,
+                       reliable_every: int = 50, check_every: int = 10,
+                       raise_on_nonconv: bool = True):
+        """The solve of cg_solve as one graph launch (device-side control)."""
+        opts = hol_cg_opts(tol, max_iter, int(bool(precond)), prec, reliable_every, check_every)
+        return cg_solve_graph(self._h, b, v, self._nrhs(b), self.n, opts, raise_on_nonconv)
 
     def force(self, v: torch.Tensor, b: torch.Tensor, dSdx: torch.Tensor | None,
               with_bosonic: bool = True, S_F: torch.Tensor | None = None) -> None:

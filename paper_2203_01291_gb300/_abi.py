@@ -63,6 +63,8 @@ SIGNATURES = {
     "fermion_matvec": (_I, [_VP, _I, _I, _VP, _VP, _I, _VP]),
     "cg_solve": (_I, [_VP, _VP, _VP, _I, ctypes.POINTER(hol_cg_opts),
                       ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
+    "cg_solve_graph": (_I, [_VP, _VP, _VP, _I, ctypes.POINTER(hol_cg_opts),
+                            ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
     "force": (_I, [_VP, _VP, _VP, _I, _VP, _I, _VP, _VP]),
     "precond_apply": (_I, [_VP, _I, _I, _VP, _VP, _I, _VP]),
     "mass_apply": (_I, [_VP, _I, _D, _VP, _VP, _VP]),
@@ -82,6 +84,9 @@ SIGNATURES = {
     "hmc_batch": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                        ctypes.POINTER(_VP), _I, ctypes.POINTER(hol_md_opts),
                        ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D), _I]),
+    "hmc_batch_graph": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
+                             ctypes.POINTER(_VP), _I, ctypes.POINTER(hol_md_opts),
+                             ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
     "measure_batch": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), _I,
                            ctypes.POINTER(hol_cg_opts), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                            ctypes.POINTER(_VP), _I, _I]),

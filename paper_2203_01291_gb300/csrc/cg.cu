@@ -1090,6 +1090,414 @@ static int cg_run_merged(hol_ctx* c, const double* b, double* v, int n_rhs, cons
     return HOL_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Graph-captured CG: the decisions cg_run takes on the host after every chunk
+// of check_every iterations (the one-chunk-late look at the recursive
+// residual, reliable updates by count and by estimate, certification by the
+// FP64 true residual) are taken by one-block kernels on the device instead,
+// in the same order and with the same reductions (warp_sum_array of the same
+// partial-sum rows), so the kernel sequence and the result are the same as
+// cg_run's. The chunk loop is a conditional WHILE node of the graph and the
+// reliable update a conditional IF node inside it; nothing waits on the host.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kDcgThreads = 1024;
+
+__global__ void __launch_bounds__(kDcgThreads) k_dcg_start(const double* __restrict__ bn, int cnt,
+                                                           int n_rhs, int* __restrict__ act,
+                                                           int* __restrict__ rel, DcgState d)
+{
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        d.g[DCG_KIT] = 0;
+        d.g[DCG_HAVE_PREV] = 0;
+        d.g[DCG_ERR] = 0;
+        d.g[DCG_ERR_RHS] = -1;
+        d.g[DCG_LOOPS] = 0;
+    }
+    __syncthreads();
+    for (int k = wid; k < n_rhs; k += kDcgThreads / 32) {
+        const double s = warp_sum_array(bn + (long)k * kRedStride, cnt);
+        if (lane == 0) {
+            const double nb = sqrt(s);
+            d.bnorm[k] = nb;
+            if (!isfinite(nb)) atomicExch(&d.g[DCG_ERR], HOL_ENUMERIC);
+            const int z = nb == 0.0;   // v = 0 is exact
+            d.done[k] = z;
+            d.tres[k] = z ? 0.0 : 1.0;
+            act[k] = z ? 0 : 1;
+            rel[k] = 0;
+            d.it[k] = 0;
+            d.since[k] = 0;
+            d.prev[k] = 0.0;
+        }
+    }
+}
+
+// End of a chunk: the iteration counts, then whether this chunk is a
+// synchronisation point (a reliable update due by count, the iteration cap,
+// or the previous chunk's estimate below tol); if it is, the rhs to update
+// are flagged from this chunk's estimate, else the estimate is kept for the
+// next chunk. Sets the IF condition of the reliable update.
+__global__ void __launch_bounds__(kDcgThreads) k_dcg_decide(const double* __restrict__ est_bank,
+                                                            int cnt, int n_rhs, int chunk, double tol,
+                                                            int rel_every, int max_iter,
+                                                            const int* __restrict__ act,
+                                                            int* __restrict__ rel, DcgState d,
+                                                            cudaGraphConditionalHandle h_if)
+{
+    __shared__ int s_sync, s_nrel, s_err;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kit = d.g[DCG_KIT] + chunk;
+    const int have_prev = d.g[DCG_HAVE_PREV];
+    if (threadIdx.x == 0) {
+        s_sync = kit >= max_iter;
+        s_nrel = 0;
+        s_err = 0;
+    }
+    __syncthreads();
+    for (int k = wid; k < n_rhs; k += kDcgThreads / 32) {
+        const double s = warp_sum_array(est_bank + (long)k * kRedStride, cnt);
+        if (lane == 0) {
+            d.cur[k] = s;
+            if (act[k]) {
+                d.it[k] += chunk;
+                d.since[k] += chunk;
+                if (d.since[k] >= rel_every) s_sync = 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (!s_sync && have_prev) {
+        for (int k = threadIdx.x; k < n_rhs; k += kDcgThreads) {
+            if (!act[k]) continue;
+            const double est = sqrt(d.prev[k]) / d.bnorm[k];
+            if (!isfinite(est)) {
+                s_err = 1;
+                d.g[DCG_ERR_RHS] = k;   // one failing rhs (any); reported only
+            } else if (est < tol) {
+                s_sync = 1;
+            }
+        }
+    }
+    __syncthreads();
+    if (s_err) {
+        if (threadIdx.x == 0) {
+            d.g[DCG_ERR] = HOL_ENUMERIC;
+            d.g[DCG_KIT] = kit;
+            cudaGraphSetConditional(h_if, 0u);
+        }
+        return;
+    }
+    if (!s_sync) {
+        for (int k = threadIdx.x; k < n_rhs; k += kDcgThreads) {
+            d.prev[k] = d.cur[k];
+            rel[k] = 0;
+        }
+        if (threadIdx.x == 0) {
+            d.g[DCG_HAVE_PREV] = 1;
+            d.g[DCG_KIT] = kit;
+            cudaGraphSetConditional(h_if, 0u);
+        }
+        return;
+    }
+    for (int k = threadIdx.x; k < n_rhs; k += kDcgThreads) {
+        int flag = 0;
+        if (act[k]) {
+            const double est = sqrt(d.cur[k]) / d.bnorm[k];
+            if (!isfinite(est)) {
+                s_err = 1;
+            } else if (est < tol || d.since[k] >= rel_every || kit >= max_iter) {
+                flag = 1;
+                atomicAdd(&s_nrel, 1);
+            }
+        }
+        rel[k] = flag;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        d.g[DCG_HAVE_PREV] = 0;
+        d.g[DCG_KIT] = kit;
+        if (s_err) d.g[DCG_ERR] = HOL_ENUMERIC;
+        cudaGraphSetConditional(h_if, (s_nrel > 0 && !s_err) ? 1u : 0u);
+    }
+}
+
+// After a reliable update: the true residual of the flagged rhs; converged
+// ones leave the active set.
+__global__ void __launch_bounds__(kDcgThreads) k_dcg_finish(const double* __restrict__ tr, int cnt,
+                                                            int n_rhs, double tol,
+                                                            int* __restrict__ act,
+                                                            const int* __restrict__ rel,
+                                                            DcgState d)
+{
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = wid; k < n_rhs; k += kDcgThreads / 32) {
+        if (!rel[k]) continue;
+        const double s = warp_sum_array(tr + (long)k * kRedStride, cnt);
+        if (lane == 0) {
+            d.since[k] = 0;
+            const double t = sqrt(s) / d.bnorm[k];
+            d.tres[k] = t;
+            if (!isfinite(t)) {
+                atomicExch(&d.g[DCG_ERR], HOL_ENUMERIC);
+            } else if (t < tol) {
+                d.done[k] = 1;
+                act[k] = 0;
+            }
+        }
+    }
+}
+
+// Loop condition: rhs still active, iterations below the cap, no error, and
+// a hard bound on the number of chunks (so the loop ends whatever happens).
+// When the loop ends unconverged or with an error, the sticky failure flag
+// is raised.
+__global__ void __launch_bounds__(kDcgThreads) k_dcg_cond(const int* __restrict__ act, int n_rhs,
+                                                          int max_iter, int max_loops, DcgState d,
+                                                          cudaGraphConditionalHandle h_while)
+{
+    __shared__ int s_act;
+    if (threadIdx.x == 0) s_act = 0;
+    __syncthreads();
+    int a = 0;
+    for (int k = threadIdx.x; k < n_rhs; k += kDcgThreads) a |= act[k];
+    if (a) s_act = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int loops = d.g[DCG_LOOPS] + 1;
+        d.g[DCG_LOOPS] = loops;
+        const int err = d.g[DCG_ERR];
+        const int go = s_act && d.g[DCG_KIT] < max_iter && !err && loops <= max_loops;
+        if (!go && (s_act || err)) d.g[DCG_STICKY] = err ? err : HOL_ENOTCONV;
+        cudaGraphSetConditional(h_while, go ? 1u : 0u);
+    }
+}
+
+}  // namespace
+
+int cond_handle(cudaStream_t s, cudaGraphConditionalHandle* h)
+{
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    HOL_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
+    if (st != cudaStreamCaptureStatusActive || !g)
+        return set_error(HOL_EINVAL, "graph solve: stream is not capturing");
+    HOL_CUDA(cudaGraphConditionalHandleCreate(h, g, 0u, cudaGraphCondAssignDefault));
+    return HOL_OK;
+}
+
+int cond_node(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+              cudaGraph_t* body)
+{
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    HOL_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, &edges, &nd));
+    if (st != cudaStreamCaptureStatusActive || !g)
+        return set_error(HOL_EINVAL, "graph solve: stream is not capturing");
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    HOL_CUDA(cudaGraphAddNode(&node, g, deps, edges, nd, &np));
+    *body = np.conditional.phGraph_out[0];
+    HOL_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                                 cudaStreamSetCaptureDependencies));
+    return HOL_OK;
+}
+
+int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_opts* o,
+               cudaStream_t s)
+{
+    const bool mixed = (o->prec == HOL_F32);
+    const bool pc = o->precond != 0;
+    const long n = c->n;
+    const int nb2 = elementwise_blocks(c);
+    const dim3 g2(nb2, n_rhs);
+    const Banks B = banks_of(c);
+    const int pstride = matvec_pstride(c);
+    const int pq_n = c->T / c->mv_k;
+    const int dz_n = pc ? precond_tiles(c, mixed ? HOL_F32 : HOL_F64) : nb2;
+    int* act_d = c->mask;
+    int* rel_d = c->mask + c->p.max_rhs;
+    const DcgState d = dcg_state(c);
+    const int chk = o->check_every > 0 ? o->check_every : 10;
+    const int rel_every = (mixed && o->reliable_every > 0) ? o->reliable_every : 1 << 30;
+    int rc;
+    if (!c->capturing) return set_error(HOL_EINVAL, "graph solve: context is not being captured");
+    if (chk & 1) return set_error(HOL_EINVAL, "graph solve: check_every must be even (%d)", chk);
+    if (c->fused || c->merged || c->persist)
+        return set_error(HOL_EINVAL, "graph solve: needs the two-kernel CG iteration (fused_cg, "
+                                     "merged_cg and persistent_cg off)");
+    if (pc && (rc = precond_check_shape(c))) return rc;
+
+    double* r64 = c->v64a;
+    double* p64[2] = {c->v64b, c->v64c};
+    double* q64 = c->v64d;
+    double* w64 = c->v64e;
+    double* z64 = pc ? c->v64f : r64;
+    float* r32 = c->v32a;
+    float* p32[2] = {c->v32b, c->v32c};
+    float* q32 = c->v32d;
+    float* e32 = c->v32e;
+    float* z32 = pc ? c->v32f : r32;
+    double* t64 = c->v64a;
+    double* rt64 = c->v64b;
+    auto est_bank = [&](int cur) { return pc ? B.er : B.dz[cur]; };
+    auto apply_prec = [&](int bank, cudaStream_t cs) -> int {
+        return mixed ? precond_apply_impl(c, HOL_F32, r32, z32, n_rhs, 3, r32, B.dz[bank], cs)
+                     : precond_apply_impl(c, HOL_F64, r64, z64, n_rhs, 3, r64, B.dz[bank], cs);
+    };
+
+    HOL_CUDA(cudaMemsetAsync(v, 0, (size_t)n_rhs * n * sizeof(double), s));
+    if (mixed)
+        k_cg_init<float><<<g2, 256, 0, s>>>(b, r32, e32, n, B.bn, est_bank(0));
+    else
+        k_cg_init<double><<<g2, 256, 0, s>>>(b, r64, nullptr, n, B.bn, est_bank(0));
+    HOL_CHECK_LAUNCH("k_cg_init");
+    if (pc && (rc = apply_prec(0, s))) return rc;
+    k_dcg_start<<<1, kDcgThreads, 0, s>>>(B.bn, nb2, n_rhs, act_d, rel_d, d);
+    HOL_CHECK_LAUNCH("k_dcg_start");
+
+    // One chunk of chk iterations on stream cs, then the decision and the
+    // conditional reliable update. chk is even, so the bank and direction
+    // parities are back at 0 at every chunk end and the loop body is the same
+    // for every chunk.
+    auto chunk = [&](cudaStream_t cs, int first) -> int {
+        int cur = 0, pp = 0;
+        bool pending = false;
+        for (int j = 0; j < chk; ++j) {
+            double* rr_dst = pc ? B.er : B.dz[1 - cur];
+            int fold;
+            if (pending) {
+                fold = 2;
+                pending = false;
+            } else if (j == chk - 1) {
+                fold = 1;
+            } else {
+                fold = 0;
+                pending = true;
+            }
+            int r2;
+            if (mixed) {
+                r2 = launch_cg_mtm32(c, z32, first ? z32 : p32[pp], p32[1 - pp], q32, n_rhs, act_d,
+                                     B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first, B.pq, cs);
+                if (r2) return r2;
+                pp = 1 - pp;
+                auto* upd = fold == 0 ? k_cg_update<float, 0>
+                                      : fold == 1 ? k_cg_update<float, 1> : k_cg_update<float, 2>;
+                HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, cs, e32, r32, p32[pp], p32[1 - pp], q32, n,
+                                    act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst,
+                                    c->alpha_buf));
+            } else {
+                BetaSrc bs{B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first};
+                r2 = launch_M_upd64(c, z64, first ? z64 : p64[pp], p64[1 - pp], w64, n_rhs, act_d,
+                                    bs, B.pq, cs);
+                if (r2) return r2;
+                r2 = launch_MT(c, HOL_F64, w64, q64, n_rhs, act_d, cs);
+                if (r2) return r2;
+                pp = 1 - pp;
+                auto* upd = fold == 0 ? k_cg_update<double, 0>
+                                      : fold == 1 ? k_cg_update<double, 1> : k_cg_update<double, 2>;
+                HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, cs, v, r64, p64[pp], p64[1 - pp], q64, n,
+                                    act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst,
+                                    c->alpha_buf));
+            }
+            HOL_CHECK_LAUNCH("k_cg_update");
+            if (pc && (r2 = apply_prec(1 - cur, cs))) return r2;
+            cur = 1 - cur;
+            first = 0;
+        }
+        // cur == 0 and pp == 0 here (chk even)
+        cudaGraphConditionalHandle h_if;
+        int r2 = cond_handle(cs, &h_if);
+        if (r2) return r2;
+        k_dcg_decide<<<1, kDcgThreads, 0, cs>>>(est_bank(cur), nb2, n_rhs, chk, o->tol, rel_every,
+                                                o->max_iter, act_d, rel_d, d, h_if);
+        HOL_CHECK_LAUNCH("k_dcg_decide");
+        cudaGraph_t body;
+        if ((r2 = cond_node(cs, h_if, cudaGraphCondTypeIf, &body))) return r2;
+        cudaStream_t is = c->cap_s[1];
+        HOL_CUDA(cudaStreamBeginCaptureToGraph(is, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
+        r2 = [&]() -> int {
+            // reliable update / certification of the flagged rhs (as in cg_run)
+            int r3;
+            if (mixed) {
+                HOL_CUDA(launch_pdl(c, k_fold, g2, 256, 0, is, v, e32, n, rel_d));
+                HOL_CHECK_LAUNCH("k_fold");
+                if ((r3 = launch_M(c, HOL_F64, v, t64, n_rhs, rel_d, nullptr, is))) return r3;
+                if ((r3 = launch_MT_resid64(c, t64, b, rt64, n_rhs, rel_d, is))) return r3;
+                HOL_CUDA(launch_pdl(c, k_recast<float>, g2, 256, 0, is, rt64, r32, n, rel_d, B.tr,
+                                    est_bank(cur)));
+            } else {
+                if ((r3 = launch_M(c, HOL_F64, v, w64, n_rhs, rel_d, nullptr, is))) return r3;
+                if ((r3 = launch_MT_resid64(c, w64, b, r64, n_rhs, rel_d, is))) return r3;
+                HOL_CUDA(launch_pdl(c, k_recast<double>, g2, 256, 0, is, r64, r64, n, rel_d, B.tr,
+                                    est_bank(cur)));
+            }
+            HOL_CHECK_LAUNCH("k_recast");
+            if (pc && (r3 = apply_prec(cur, is))) return r3;
+            double* cj0 = c->part + 8 * c->part_len;
+            double* cj1 = c->part + 9 * c->part_len;
+            if (mixed) {
+                HOL_CUDA(launch_pdl(c, k_conj_dots<float>, g2, 256, 0, is, z32, p32[pp], q32, n,
+                                    rel_d, cj0, cj1));
+                HOL_CHECK_LAUNCH("k_conj_dots");
+                HOL_CUDA(launch_pdl(c, k_conj_scale<float>, g2, 256, 0, is, p32[pp], n, rel_d, cj0,
+                                    cj1, nb2));
+            } else {
+                HOL_CUDA(launch_pdl(c, k_conj_dots<double>, g2, 256, 0, is, z64, p64[pp], q64, n,
+                                    rel_d, cj0, cj1));
+                HOL_CHECK_LAUNCH("k_conj_dots");
+                HOL_CUDA(launch_pdl(c, k_conj_scale<double>, g2, 256, 0, is, p64[pp], n, rel_d, cj0,
+                                    cj1, nb2));
+            }
+            HOL_CHECK_LAUNCH("k_conj_scale");
+            HOL_CUDA(launch_pdl(c, k_copy_rows, n_rhs, 256, 0, is, B.dz[cur], B.dz[1 - cur], rel_d));
+            HOL_CHECK_LAUNCH("k_copy_rows");
+            k_dcg_finish<<<1, kDcgThreads, 0, is>>>(B.tr, nb2, n_rhs, o->tol, act_d, rel_d, d);
+            HOL_CHECK_LAUNCH("k_dcg_finish");
+            return HOL_OK;
+        }();
+        cudaGraph_t done_body = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(is, &done_body);
+        if (r2) return r2;
+        if (ee != cudaSuccess) return cuda_error(ee, "graph solve: reliable-update body");
+        return HOL_OK;
+    };
+
+    const int max_loops = (o->max_iter + chk - 1) / chk + 2;
+    if ((rc = chunk(s, 1))) return rc;
+    cudaGraphConditionalHandle h_while;
+    if ((rc = cond_handle(s, &h_while))) return rc;
+    k_dcg_cond<<<1, kDcgThreads, 0, s>>>(act_d, n_rhs, o->max_iter, max_loops, d, h_while);
+    HOL_CHECK_LAUNCH("k_dcg_cond");
+    cudaGraph_t body;
+    if ((rc = cond_node(s, h_while, cudaGraphCondTypeWhile, &body))) return rc;
+    cudaStream_t ws = c->cap_s[0];
+    HOL_CUDA(cudaStreamBeginCaptureToGraph(ws, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+    rc = chunk(ws, 0);
+    if (!rc) {
+        k_dcg_cond<<<1, kDcgThreads, 0, ws>>>(act_d, n_rhs, o->max_iter, max_loops, d, h_while);
+        rc = cudaGetLastError() == cudaSuccess ? HOL_OK : set_error(HOL_ECUDA, "k_dcg_cond");
+        count_launch();
+    }
+    cudaGraph_t wb = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(ws, &wb);
+    if (rc) return rc;
+    if (ee != cudaSuccess) return cuda_error(ee, "graph solve: loop body");
+    return HOL_OK;
+}
+
 }  // namespace hol
 
 using namespace hol;

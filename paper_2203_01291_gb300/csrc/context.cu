@@ -144,6 +144,9 @@ void free_ctx(hol_ctx* c)
                    c->v32i, c->cgs, c->alpha_buf, c->arn};
     for (void* p : dev)
         if (p) cudaFree(p);
+    if (c->dcg) cudaFree(c->dcg);
+    for (cudaStream_t cs : c->cap_s)
+        if (cs) cudaStreamDestroy(cs);
     timer_free(c->timer);
     if (c->hbuf) cudaFreeHost(c->hbuf);
     if (c->hflag) cudaFreeHost(c->hflag);
@@ -332,6 +335,12 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     ALLOC(c->alpha_buf, R * sizeof(double));
     ALLOC(c->arn, ((size_t)(kArnoldiMax + 1) * c->N + (kArnoldiMax + 1) * kArnoldiMax + 1) *
                       sizeof(double));
+    ALLOC(c->dcg, dcg_bytes(R));
+    for (cudaStream_t& cs : c->cap_s)
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            free_ctx(c);
+            return set_error(HOL_ECUDA, "hol_create: stream creation failed");
+        }
     ALLOC(c->cbuf0, c->cbuf_len * sizeof(double2));
     ALLOC(c->cbuf1, c->cbuf_len * sizeof(double2));
 #undef ALLOC

@@ -225,6 +225,12 @@ struct hol_ctx {
     int merged;          // mixed plain CG as one merged (Chronopoulos-Gear) kernel per iteration
     int fused;           // mixed plain CG with the vector update fused into the operator
     int pdl;             // programmatic dependent launch of the CG kernels
+
+    // graph-captured (device-driven) solves: device-side decision state and
+    // the side streams that capture the bodies of conditional graph nodes
+    double* dcg;         // hol::DcgState storage (see dcg_state)
+    cudaStream_t cap_s[3];
+    int capturing;       // set while the context's work is being captured
 };
 
 namespace hol {
@@ -297,6 +303,78 @@ int launch_cg_mtm32_exact(const hol_ctx* c, const float* r, const float* pold, f
                           float* q, int n_rhs, const int* mask, const double* rr_new,
                           const double* rr_old, int rr_stride, int rr_n, int first,
                           double* pq_part, cudaStream_t s);
+// Device-side state of a graph-captured CG solve (one context): per right-hand
+// side its |b|, the previous and the current chunk's residual sums, the true
+// residual, iteration and since-last-reliable-update counts and the converged
+// flag; plus solve-wide counters g[DCG_*] (DCG_STICKY collects failures of
+// every solve since it was last cleared).
+enum DcgSlot { DCG_KIT = 0, DCG_HAVE_PREV = 1, DCG_ERR = 2, DCG_ERR_RHS = 3, DCG_LOOPS = 4,
+               DCG_STICKY = 5, DCG_COUNT = 8 };
+struct DcgState {
+    double* bnorm;
+    double* prev;
+    double* cur;
+    double* tres;
+    int* it;
+    int* since;
+    int* done;
+    int* g;
+};
+inline size_t dcg_bytes(long R)
+{
+    return (size_t)(4 * R) * sizeof(double) + (size_t)(3 * R + DCG_COUNT) * sizeof(int);
+}
+inline DcgState dcg_state(const hol_ctx* c)
+{
+    const long R = c->p.max_rhs;
+    DcgState d;
+    d.bnorm = c->dcg;
+    d.prev = c->dcg + R;
+    d.cur = c->dcg + 2 * R;
+    d.tres = c->dcg + 3 * R;
+    int* ib = reinterpret_cast<int*>(c->dcg + 4 * R);
+    d.it = ib;
+    d.since = ib + R;
+    d.done = ib + 2 * R;
+    d.g = ib + 3 * R;
+    return d;
+}
+// Graph-capturable CG: the solve of cg_solve (the same kernels and the same
+// decisions, so bitwise the same result) with every decision taken on the
+// device: the chunk loop is a WHILE node and the reliable update an IF node.
+// `s` must be capturing in thread-local mode, inside a CaptureScope; needs an
+// even check_every and the default two-kernel iteration. Per-rhs results stay
+// in dcg_state(c) and v.
+int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_opts* o,
+               cudaStream_t s);
+// Conditional nodes in a capturing stream: cond_handle creates a handle in the
+// graph being captured on s (capture the kernel that sets it next);
+// cond_node appends the node after the stream's current dependencies, makes
+// it the new dependency and returns its (first) body graph.
+int cond_handle(cudaStream_t s, cudaGraphConditionalHandle* h);
+int cond_node(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+              cudaGraph_t* body);
+// While a context's work is captured: no programmatic launches and no timer
+// events (neither may sit in a conditional body), and solves device-driven.
+struct CaptureScope {
+    hol_ctx* c;
+    int pdl;
+    KTimer* timer;
+    explicit CaptureScope(hol_ctx* ctx) : c(ctx), pdl(ctx->pdl), timer(ctx->timer)
+    {
+        c->pdl = 0;
+        c->timer = nullptr;
+        c->capturing = 1;
+    }
+    ~CaptureScope()
+    {
+        c->pdl = pdl;
+        c->timer = timer;
+        c->capturing = 0;
+    }
+    CaptureScope(const CaptureScope&) = delete;
+    CaptureScope& operator=(const CaptureScope&) = delete;
+};
 // Propagator parameters of a context for kernels computing in R.
 template <typename R>
 inline Kin<R> kin_of(const hol_ctx* c)
@@ -368,6 +446,19 @@ int elementwise_blocks(const hol_ctx* c);
 // per (rhs, tile) at stride kRedStride, precond_tiles(c, prec) per rhs.
 int precond_alloc(hol_ctx* c);
 int leapfrog_alloc(hol_ctx* c);
+// Parts of one HMC trajectory (leapfrog.cu) replayed by the captured batch
+// (graph.cu): md_start (Phi, p, the initial energies in md_s[0..2], the first
+// force and half kick, the kick coefficient for the next step), md_step (one
+// leapfrog step ending with the kick by md_s[kKickSlot]), md_set_kick, md_end
+// (tight action solve, final energies in md_s[3..5]); md_check validates the
+// options as fourier_accel_leapfrog does.
+constexpr int kKickSlot = 12;
+int md_start(hol_ctx* c, double* x, const double* R_pf, const double* R_p, int n_pf,
+             const hol_md_opts* o, cudaStream_t s);
+int md_set_kick(hol_ctx* c, double kick, cudaStream_t s);
+int md_step(hol_ctx* c, double* x, int n_pf, const hol_md_opts* o, cudaStream_t s);
+int md_end(hol_ctx* c, double* x, int n_pf, const hol_md_opts* o, cudaStream_t s);
+int md_check(const hol_ctx* c, const hol_md_opts* o, int n_pf);
 int measure_alloc(hol_ctx* c);
 int precond_check_shape(const hol_ctx* c);
 int precond_tiles(const hol_ctx* c, int prec);

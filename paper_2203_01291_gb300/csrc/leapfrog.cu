@@ -113,6 +113,19 @@ __global__ void k_axpy(double* __restrict__ y, const double* __restrict__ x, dou
         y[k] = fma(a, x[k], y[k]);
 }
 
+// y += -(*coef) x: the kick of k_axpy with its coefficient read on the
+// device (a captured step graph serves every step of a trajectory)
+__global__ void k_axpy_dev(double* __restrict__ y, const double* __restrict__ x,
+                           const double* __restrict__ coef, long n)
+{
+    const double a = -coef[0];
+    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < n;
+         k += (long)gridDim.x * blockDim.x)
+        y[k] = fma(a, x[k], y[k]);
+}
+
+__global__ void k_set1(double* __restrict__ dst, double value) { *dst = value; }
+
 // out[0] = scale * sum_k a[k] b[k] (one block, fixed order)
 __global__ void __launch_bounds__(1024) k_dot1(const double* __restrict__ a,
                                                const double* __restrict__ b, long n, double scale,
@@ -201,7 +214,10 @@ int fermion_force(hol_ctx* c, const double* x, const double* Phi, int n_pf,
     int rc;
     if ((rc = hol_set_field(c, x, s))) return rc;
     if ((rc = launch_lambda(c, false, Phi, c->md_b, n_pf, s))) return rc;
-    if ((rc = cg_solve(c, c->md_b, c->md_v, n_pf, cg, nullptr, nullptr, s))) return rc;
+    // inside a graph capture the solve is device-driven (same result)
+    rc = c->capturing ? cg_run_dev(c, c->md_b, c->md_v, n_pf, cg, s)
+                      : cg_solve(c, c->md_b, c->md_v, n_pf, cg, nullptr, nullptr, s);
+    if (rc) return rc;
     timer_start(c, KT_FORCE, s);
     rc = launch_force(c, c->md_v, c->md_b, n_pf, c->md_F, 0, nullptr, s);
     timer_stop(c, KT_FORCE, s);
@@ -245,6 +261,80 @@ int md_run(hol_ctx* c, double* x, double* p, const double* Phi, int n_pf, const 
 }
 
 }  // namespace
+
+// The three parts of fourier_accel_leapfrog that a captured batch replays
+// (graph.cu), with the kernel sequence of fourier_accel_leapfrog / md_run:
+// the start (Phi, p, H_i, the first force and half kick), one leapfrog step
+// (n_sub bosonic sub-steps, the force, the kick by the device-side
+// coefficient md_s[kKickSlot]) and the end (the tight action solve and H_f).
+int md_start(hol_ctx* c, double* x, const double* R_pf, const double* R_p, int n_pf,
+             const hol_md_opts* o, cudaStream_t s)
+{
+    int rc;
+    const long n = c->n;
+    double* sc = c->md_s;
+    if ((rc = hol_set_field(c, x, s))) return rc;
+    if ((rc = launch_MT(c, HOL_F64, R_pf, c->v64e, n_pf, nullptr, s))) return rc;
+    if ((rc = launch_lambda(c, true, c->v64e, c->md_phi, n_pf, s))) return rc;
+    if ((rc = mass_tables(c, o->m_reg, s))) return rc;
+    if ((rc = filter(c, R_p, nullptr, c->md_p, 1.0, 1, s))) return rc;
+    HOL_CUDA(cudaMemcpyAsync(c->md_x0, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    const double w02 = c->p.omega0 * c->p.omega0;
+    k_sb1<<<1, 1024, 0, s>>>(x, c->N, c->T, c->p.dtau, w02, sc + 0);
+    k_dot1<<<1, 1024, 0, s>>>(R_pf, R_pf, (long)n_pf * n, 0.5, sc + 1);
+    if ((rc = filter(c, c->md_p, nullptr, c->md_F, 1.0, 0, s))) return rc;
+    k_dot1<<<1, 1024, 0, s>>>(c->md_p, c->md_F, n, 0.5, sc + 2);
+    HOL_CHECK_LAUNCH("initial energies");
+    // md_run up to its first half kick
+    if ((rc = mass_tables(c, o->m_reg, s))) return rc;
+    if ((rc = fermion_force(c, x, c->md_phi, n_pf, &o->cg_force, s))) return rc;
+    k_axpy<<<grid_1d(c->n), 256, 0, s>>>(c->md_p, c->md_F, -0.5 * o->dt, c->n);
+    HOL_CHECK_LAUNCH("k_axpy");
+    return md_set_kick(c, o->n_steps == 1 ? 0.5 * o->dt : o->dt, s);
+}
+
+int md_set_kick(hol_ctx* c, double kick, cudaStream_t s)
+{
+    k_set1<<<1, 1, 0, s>>>(c->md_s + kKickSlot, kick);
+    HOL_CHECK_LAUNCH("k_set1");
+    return HOL_OK;
+}
+
+int md_step(hol_ctx* c, double* x, int n_pf, const hol_md_opts* o, cudaStream_t s)
+{
+    int rc;
+    const double dts = o->dt / o->n_sub;
+    for (int k = 0; k < o->n_sub; ++k) {
+        if ((rc = boson_kick(c, c->md_p, x, 0.5 * dts, s))) return rc;
+        if ((rc = filter(c, c->md_p, x, x, dts, 0, s))) return rc;
+        if ((rc = boson_kick(c, c->md_p, x, 0.5 * dts, s))) return rc;
+    }
+    if ((rc = fermion_force(c, x, c->md_phi, n_pf, &o->cg_force, s))) return rc;
+    k_axpy_dev<<<grid_1d(c->n), 256, 0, s>>>(c->md_p, c->md_F, c->md_s + kKickSlot, c->n);
+    HOL_CHECK_LAUNCH("k_axpy_dev");
+    return HOL_OK;
+}
+
+int md_end(hol_ctx* c, double* x, int n_pf, const hol_md_opts* o, cudaStream_t s)
+{
+    int rc;
+    const long n = c->n;
+    double* sc = c->md_s;
+    const double w02 = c->p.omega0 * c->p.omega0;
+    if ((rc = hol_set_field(c, x, s))) return rc;
+    if ((rc = launch_lambda(c, false, c->md_phi, c->md_b, n_pf, s))) return rc;
+    rc = c->capturing ? cg_run_dev(c, c->md_b, c->md_v, n_pf, &o->cg_action, s)
+                      : cg_solve(c, c->md_b, c->md_v, n_pf, &o->cg_action, nullptr, nullptr, s);
+    if (rc) return rc;
+    k_sb1<<<1, 1024, 0, s>>>(x, c->N, c->T, c->p.dtau, w02, sc + 3);
+    k_dot1<<<1, 1024, 0, s>>>(c->md_b, c->md_v, (long)n_pf * n, 0.5, sc + 4);
+    if ((rc = filter(c, c->md_p, nullptr, c->md_F, 1.0, 0, s))) return rc;
+    k_dot1<<<1, 1024, 0, s>>>(c->md_p, c->md_F, n, 0.5, sc + 5);
+    HOL_CHECK_LAUNCH("final energies");
+    return HOL_OK;
+}
+
+int md_check(const hol_ctx* c, const hol_md_opts* o, int n_pf) { return check_md(c, o, n_pf); }
 
 int leapfrog_alloc(hol_ctx* c)
 {

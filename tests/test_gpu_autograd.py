@@ -121,7 +121,8 @@ def test_mixed_force_after_refinement_matches_fp64_oracle(name, tol):
     products and reliable updates, convergence certified by the FP64 true
     residual) refined to `tol`, then the FP64 force kernel: the force of two
     pseudofermions within 1e-7 relative (max norm over all x components) of
-    the FP64 oracle's (matrix-free C, textbook CG to 1e-14, its own force).
+    the FP64 oracle's (matrix-free C, textbook CG to 1e-13, the smallest
+    residual its FP64 recursion certifies on these shapes, and its own force).
     The force is quadratic in v, so its relative error is about twice that
     of v, bounded by kappa(M^T M) times the residual; the measured condition
     numbers (Lanczos on the oracle's operator) are recorded in the DESIGN
@@ -133,8 +134,8 @@ def test_mixed_force_after_refinement_matches_fp64_oracle(name, tol):
     Fo = np.zeros((w.Ltau, w.N))
     for r in R:
         b = MF.MT_apply(w, x, r)
-        v, _, res = MF.cg(w, x, b, tol=1e-14, max_iter=200000)
-        assert res < 1e-14
+        v, _, res = MF.cg(w, x, b, tol=1e-13, max_iter=60000)
+        assert res < 1e-13
         Fo += MF.force_fermion(w, x, v, b)
     with hg.Context.from_workload(w, max_rhs=2) as ctx:
         ctx.set_field(torch.tensor(x, device=DEV))
