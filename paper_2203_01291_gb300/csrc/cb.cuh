@@ -178,6 +178,52 @@ __device__ __forceinline__ double warp_sum_array(const double* __restrict__ a, i
     return warp_sum(s);
 }
 
+// Compensated float pair (a double-float): the value hi + lo with lo the
+// rounding error of hi, kept by Knuth's TwoSum at every addition, so sums of
+// FP32 terms keep about 48 significant bits while running on the FP32 pipes
+// (on this GPU an FP64 instruction costs sixty-four times an FP32 one). The
+// order of additions is fixed, so results are reproducible bit for bit.
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 f2_two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return F2{s, e};
+}
+// x + y, renormalised so that |lo| stays below half an ulp of hi
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y)
+{
+    const F2 s = f2_two_sum(x.hi, y.hi);
+    const float lo = s.lo + (x.lo + y.lo);
+    const float hi = s.hi + lo;
+    return F2{hi, lo - (hi - s.hi)};
+}
+__device__ __forceinline__ F2 f2_add(F2 x, float y) { return f2_add(x, F2{y, 0.0f}); }
+// Warp-wide sum, identical in every lane (fixed butterfly order).
+__device__ __forceinline__ F2 f2_warp_sum(F2 v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const F2 y{__shfl_xor_sync(kFull, v.hi, o), __shfl_xor_sync(kFull, v.lo, o)};
+        v = f2_add(v, y);
+    }
+    return v;
+}
+__device__ __forceinline__ double f2_to_double(F2 v) { return (double)v.hi + (double)v.lo; }
+
+// Sum of a[0..n) by one full warp as warp_sum_array (same order, same bits),
+// loading through L2 only: for partials written by other blocks of the same
+// launch.
+__device__ __forceinline__ double warp_sum_array_cg(const double* __restrict__ a, int n)
+{
+    double s = 0.0;
+    for (int k = (threadIdx.x & 31); k < n; k += 32) s += __ldcg(a + k);
+    return warp_sum(s);
+}
+
 // Sum `acc` over the L lanes of each group and store it for valid units.
 template <int L>
 __device__ __forceinline__ void group_store_sum(double acc, bool valid, double* __restrict__ dst)
@@ -191,6 +237,38 @@ __device__ __forceinline__ void group_store_sum(double acc, bool valid, double* 
         double s = 0.0;
         for (int k = 0; k < L; ++k) s += red[w * 32 + geo.g * L + k];
         *dst = s;
+    }
+}
+
+// The same for a compensated float pair: the sum over each group's L lanes
+// (a butterfly when L is a power of two, else one lane summing the group in
+// a fixed order), converted to FP64 once for the stored value.
+template <int L>
+__device__ __forceinline__ void group_store_sum(F2 acc, bool valid, double* __restrict__ dst)
+{
+    const LaneGeom<L> geo;
+    if constexpr ((L & (L - 1)) == 0) {
+        if (!valid) acc = F2{0.0f, 0.0f};
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) {
+            const F2 y{__shfl_xor_sync(kFull, acc.hi, o), __shfl_xor_sync(kFull, acc.lo, o)};
+            acc = f2_add(acc, y);
+        }
+        if (valid && geo.ix == 0) *dst = f2_to_double(acc);
+    } else {
+        __shared__ float red_h[32 * 8], red_l[32 * 8];   // up to 8 warps per block
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        red_h[w * 32 + lane] = valid ? acc.hi : 0.0f;
+        red_l[w * 32 + lane] = valid ? acc.lo : 0.0f;
+        __syncwarp();
+        if (valid && geo.ix == 0) {
+            F2 t{0.0f, 0.0f};
+            for (int k = 0; k < L; ++k) {
+                const int j = w * 32 + geo.g * L + k;
+                t = f2_add(t, F2{red_h[j], red_l[j]});
+            }
+            *dst = f2_to_double(t);
+        }
     }
 }
 

@@ -77,6 +77,26 @@ __device__ __forceinline__ double block_sum(double v)
     return s;
 }
 
+// Block sum of a compensated float pair, converted to FP64 once (thread 0).
+__device__ __forceinline__ double block_sum_f2(F2 v)
+{
+    __shared__ float red_hi[32], red_lo[32];
+    v = f2_warp_sum(v);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red_hi[w] = v.hi;
+        red_lo[w] = v.lo;
+    }
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+        F2 t{0.0f, 0.0f};
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = f2_add(t, F2{red_hi[k], red_lo[k]});
+        s = f2_to_double(t);
+    }
+    return s;
+}
+
 // r -= alpha q with the new (r.r) partials; alpha = dz / pq from partials.
 // The x update may be deferred by one iteration (FOLD 0 stores alpha for
 // the next launch and leaves x alone; FOLD 2 then adds alpha_prev p_prev +
@@ -91,31 +111,46 @@ __global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restr
                                                    const double* __restrict__ pq_part, int pq_stride,
                                                    int pq_n, const double* __restrict__ dz_part,
                                                    int dz_n, double* __restrict__ rr_out,
-                                                   double* __restrict__ alpha_buf)
+                                                   double* __restrict__ alpha_buf,
+                                                   const double* __restrict__ alpha_in,
+                                                   double* __restrict__ beta_out,
+                                                   int* __restrict__ beta_cnt)
 {
     pdl_wait();      // p, q and the partials come from the previous kernel of the stream
     const PdlTriggerAtExit pdl_at_exit;
     const int rhs = blockIdx.y;
     if (mask != nullptr && mask[rhs] == 0) return;
-    // one warp forms alpha (FP64 sums are slow on this part: doing it in
-    // every warp measured slower than the barrier)
-    __shared__ double s_alpha, s_alpha_prev;
-    if (threadIdx.x < 32) {
-        const double pq = warp_sum_array(pq_part + (long)rhs * pq_stride, pq_n);
-        const double dz = warp_sum_array(dz_part + (long)rhs * kRedStride, dz_n);
-        if (threadIdx.x == 0) {
-            s_alpha = cg_ratio(dz, pq);
-            if (FOLD == 2) s_alpha_prev = alpha_buf[rhs];
+    double alpha, alpha_prev = 0.0;
+    if (alpha_in != nullptr) {
+        // formed once per rhs by the operator's last warp (cg_alpha_epilogue)
+        alpha = alpha_in[rhs];
+        if (FOLD == 2) alpha_prev = alpha_buf[rhs];
+    } else {
+        // one warp forms alpha (FP64 sums are slow on this part: doing it
+        // in every warp measured slower than the barrier)
+        __shared__ double s_alpha, s_alpha_prev;
+        if (threadIdx.x < 32) {
+            const double pq = warp_sum_array(pq_part + (long)rhs * pq_stride, pq_n);
+            const double dz = warp_sum_array(dz_part + (long)rhs * kRedStride, dz_n);
+            if (threadIdx.x == 0) {
+                s_alpha = cg_ratio(dz, pq);
+                if (FOLD == 2) s_alpha_prev = alpha_buf[rhs];
+            }
         }
+        __syncthreads();
+        alpha = s_alpha;
+        alpha_prev = s_alpha_prev;
     }
-    __syncthreads();
-    const R a = (R)s_alpha;
+    const R a = (R)alpha;
     R ap = R(0);
-    if (FOLD == 2) ap = (R)s_alpha_prev;
-    if (FOLD == 0 && blockIdx.x == 0 && threadIdx.x == 0) alpha_buf[rhs] = s_alpha;
+    if (FOLD == 2) ap = (R)alpha_prev;
+    if (FOLD == 0 && blockIdx.x == 0 && threadIdx.x == 0) alpha_buf[rhs] = alpha;
     const long base = (long)rhs * n;
     const long stride = (long)gridDim.x * blockDim.x;
+    // the partial of the new r.r: a compensated float pair in the FP32 path
+    // (one FP64 conversion per block), FP64 in the FP64 path
     double acc = 0.0;
+    F2 acc2{0.0f, 0.0f};
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n; k += stride) {
         const long o = base + 4 * k;
         V4<R> rv, qv;
@@ -142,10 +177,36 @@ __global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restr
             part = fma(rv.v[j], rv.v[j], part);
         }
         rv.st(r + o);
-        acc += (double)part;
+        if constexpr (sizeof(R) == 4)
+            acc2 = f2_add(acc2, (float)part);
+        else
+            acc += (double)part;
     }
-    const double s = block_sum(acc);
+    double s;
+    if constexpr (sizeof(R) == 4)
+        s = block_sum_f2(acc2);
+    else
+        s = block_sum(acc);
     if (threadIdx.x == 0) rr_out[(long)rhs * kRedStride + blockIdx.x] = s;
+    if (beta_out != nullptr) {
+        // the last block of this rhs forms the next beta = (r.r)_new / (r.r)_old
+        // from the partial rows, summed as the operator kernel would sum them
+        __shared__ int s_last;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(beta_cnt + rhs, 1) == (int)gridDim.x - 1;
+        }
+        __syncthreads();
+        if (s_last && threadIdx.x < 32) {
+            __threadfence();
+            const double rn = warp_sum_array_cg(rr_out + (long)rhs * kRedStride, gridDim.x);
+            const double ro = warp_sum_array_cg(dz_part + (long)rhs * kRedStride, dz_n);
+            if (threadIdx.x == 0) {
+                beta_out[rhs] = cg_ratio(rn, ro);
+                beta_cnt[rhs] = 0;
+            }
+        }
+    }
 }
 
 // Start: r = b (FP64 or rounded to FP32), x = 0; partials of |b|^2 and |r|^2.
@@ -348,7 +409,8 @@ __global__ void __launch_bounds__(256) k_conj_scale(R* __restrict__ p, long n,
 // dst row = src row (kRedStride partials) for the flagged rhs, so that the
 // next beta = sum(src) / sum(dst) is exactly 1.
 __global__ void k_copy_rows(const double* __restrict__ src, double* __restrict__ dst,
-                            const int* __restrict__ mask)
+                            const int* __restrict__ mask, double* __restrict__ beta_out,
+                            int beta_n)
 {
     pdl_wait();      // inputs may come from the previous kernel of the stream
     const PdlTriggerAtExit pdl_at_exit;
@@ -356,6 +418,15 @@ __global__ void k_copy_rows(const double* __restrict__ src, double* __restrict__
     if (mask[rhs] == 0) return;
     for (int k = threadIdx.x; k < kRedStride; k += blockDim.x)
         dst[(long)rhs * kRedStride + k] = src[(long)rhs * kRedStride + k];
+    if (beta_out != nullptr) {
+        // both rows now hold the same partials: the next beta is their ratio,
+        // formed as the operator kernel would form it
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const double v = warp_sum_array(dst + (long)rhs * kRedStride, beta_n);
+            if (threadIdx.x == 0) beta_out[rhs] = cg_ratio(v, v);
+        }
+    }
 }
 
 
@@ -560,8 +631,10 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
             if (mixed) {
                 // on the first step beta = 0 and p_old is not yet defined: pass z
                 timer_start(c, KT_OPERATOR, s, n_active * nd * 16.0 + nd * 4.0);
+                int adone = 0;   // alpha formed by the operator's last warp
                 rc = launch_cg_mtm32(c, z32, first ? z32 : p32[pp], p32[1 - pp], q32, n_rhs, act_d,
-                                     B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first, B.pq, s);
+                                     B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first, B.pq, s,
+                                     c->alpha_now, &adone, pc ? nullptr : c->beta_now);
                 if (rc) return rc;
                 timer_stop(c, KT_OPERATOR, s);
                 pp = 1 - pp;
@@ -570,7 +643,8 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                                       : fold == 1 ? k_cg_update<float, 1> : k_cg_update<float, 2>;
                 HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, s, e32, r32, p32[pp], p32[1 - pp], q32, n,
                                     act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst,
-                                    c->alpha_buf));
+                                    c->alpha_buf, adone ? (const double*)c->alpha_now : nullptr,
+                                    pc ? nullptr : c->beta_now, c->beta_cnt));
             } else {
                 BetaSrc bs{B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first};
                 timer_start(c, KT_OPERATOR, s, n_active * nd * 48.0 + nd * 16.0);
@@ -586,7 +660,8 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                                       : fold == 1 ? k_cg_update<double, 1> : k_cg_update<double, 2>;
                 HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, s, v, r64, p64[pp], p64[1 - pp], q64, n,
                                     act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst,
-                                    c->alpha_buf));
+                                    c->alpha_buf, (const double*)nullptr, (double*)nullptr,
+                                    (int*)nullptr));
             }
             HOL_CHECK_LAUNCH("k_cg_update");
             timer_stop(c, KT_UPDATE, s);
@@ -693,7 +768,8 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                                     cj1, nb2));
             }
             HOL_CHECK_LAUNCH("k_conj_scale");
-            HOL_CUDA(launch_pdl(c, k_copy_rows, n_rhs, 256, 0, s, B.dz[cur], B.dz[1 - cur], rel_d));
+            HOL_CUDA(launch_pdl(c, k_copy_rows, n_rhs, 256, 0, s, B.dz[cur], B.dz[1 - cur], rel_d,
+                                (mixed && !pc) ? c->beta_now : nullptr, dz_n));
             HOL_CHECK_LAUNCH("k_copy_rows");
             cnt[1 - cur] = cnt[cur];
         }
@@ -1387,15 +1463,18 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
             }
             int r2;
             if (mixed) {
+                int adone = 0;
                 r2 = launch_cg_mtm32(c, z32, first ? z32 : p32[pp], p32[1 - pp], q32, n_rhs, act_d,
-                                     B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first, B.pq, cs);
+                                     B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first, B.pq, cs,
+                                     c->alpha_now, &adone, pc ? nullptr : c->beta_now);
                 if (r2) return r2;
                 pp = 1 - pp;
                 auto* upd = fold == 0 ? k_cg_update<float, 0>
                                       : fold == 1 ? k_cg_update<float, 1> : k_cg_update<float, 2>;
                 HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, cs, e32, r32, p32[pp], p32[1 - pp], q32, n,
                                     act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst,
-                                    c->alpha_buf));
+                                    c->alpha_buf, adone ? (const double*)c->alpha_now : nullptr,
+                                    pc ? nullptr : c->beta_now, c->beta_cnt));
             } else {
                 BetaSrc bs{B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first};
                 r2 = launch_M_upd64(c, z64, first ? z64 : p64[pp], p64[1 - pp], w64, n_rhs, act_d,
@@ -1408,7 +1487,8 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
                                       : fold == 1 ? k_cg_update<double, 1> : k_cg_update<double, 2>;
                 HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, cs, v, r64, p64[pp], p64[1 - pp], q64, n,
                                     act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst,
-                                    c->alpha_buf));
+                                    c->alpha_buf, (const double*)nullptr, (double*)nullptr,
+                                    (int*)nullptr));
             }
             HOL_CHECK_LAUNCH("k_cg_update");
             if (pc && (r2 = apply_prec(1 - cur, cs))) return r2;
@@ -1461,7 +1541,8 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
                                     cj1, nb2));
             }
             HOL_CHECK_LAUNCH("k_conj_scale");
-            HOL_CUDA(launch_pdl(c, k_copy_rows, n_rhs, 256, 0, is, B.dz[cur], B.dz[1 - cur], rel_d));
+            HOL_CUDA(launch_pdl(c, k_copy_rows, n_rhs, 256, 0, is, B.dz[cur], B.dz[1 - cur], rel_d,
+                                (mixed && !pc) ? c->beta_now : nullptr, dz_n));
             HOL_CHECK_LAUNCH("k_copy_rows");
             k_dcg_finish<<<1, kDcgThreads, 0, is>>>(B.tr, nb2, n_rhs, o->tol, act_d, rel_d, d);
             HOL_CHECK_LAUNCH("k_dcg_finish");

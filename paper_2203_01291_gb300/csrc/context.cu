@@ -145,6 +145,10 @@ void free_ctx(hol_ctx* c)
     for (void* p : dev)
         if (p) cudaFree(p);
     if (c->dcg) cudaFree(c->dcg);
+    if (c->alpha_now) cudaFree(c->alpha_now);
+    if (c->alpha_cnt) cudaFree(c->alpha_cnt);
+    if (c->beta_now) cudaFree(c->beta_now);
+    if (c->beta_cnt) cudaFree(c->beta_cnt);
     for (cudaStream_t cs : c->cap_s)
         if (cs) cudaStreamDestroy(cs);
     timer_free(c->timer);
@@ -336,6 +340,15 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     ALLOC(c->arn, ((size_t)(kArnoldiMax + 1) * c->N + (kArnoldiMax + 1) * kArnoldiMax + 1) *
                       sizeof(double));
     ALLOC(c->dcg, dcg_bytes(R));
+    ALLOC(c->alpha_now, R * sizeof(double));
+    ALLOC(c->alpha_cnt, R * sizeof(int));
+    ALLOC(c->beta_now, R * sizeof(double));
+    ALLOC(c->beta_cnt, R * sizeof(int));
+    if (cudaMemset(c->alpha_cnt, 0, R * sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->beta_cnt, 0, R * sizeof(int)) != cudaSuccess) {
+        free_ctx(c);
+        return set_error(HOL_ECUDA, "hol_create: memset");
+    }
     for (cudaStream_t& cs : c->cap_s)
         if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
             free_ctx(c);

@@ -231,6 +231,16 @@ struct hol_ctx {
     double* dcg;         // hol::DcgState storage (see dcg_state)
     cudaStream_t cap_s[3];
     int capturing;       // set while the context's work is being captured
+
+    // alpha of the current mixed CG iteration per rhs, formed by the last warp
+    // of the operator kernel (cg_alpha_epilogue), and that kernel's per-rhs
+    // count of finished warps (zero between launches)
+    double* alpha_now;
+    int* alpha_cnt;
+    // beta of the next plain mixed CG iteration per rhs, formed by the last
+    // block of the update kernel, and that kernel's per-rhs block count
+    double* beta_now;
+    int* beta_cnt;
 };
 
 namespace hol {
@@ -286,7 +296,9 @@ int launch_MT_resid64(const hol_ctx* c, const double* u, const double* b, double
 int launch_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pnew,
                     float* q, int n_rhs, const int* mask, const double* rr_new,
                     const double* rr_old, int rr_stride, int rr_n, int first,
-                    double* pq_part, cudaStream_t s);
+                    double* pq_part, cudaStream_t s,
+                    double* alpha_out = nullptr, int* alpha_done = nullptr,
+                    const double* beta_in = nullptr);
 // The same five operators with the exact propagator exp(-dtau K) (exact.cu;
 // scalar layout only). The launch_* calls above forward to these when the
 // context was created with HOL_KINETIC_EXACT.

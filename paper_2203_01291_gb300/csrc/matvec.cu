@@ -54,12 +54,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
     const int t0 = (run < gm.nrun ? run : gm.nrun - 1) * gm.K;
     const long base = (long)rhs * gm.T * N;
 
-    float bt = 0.0f;
-    if (!first) {
-        const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
-        const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
-        bt = (float)cg_ratio(rn, ro);
-    }
+    const float bt = cg_beta(gm, rhs, first, rr_new_part, rr_old_part, rr_stride, rr_n);
 
     // the unit's later slices t0+1 .. t0+K go to L2 while the first ones compute
     if (geo.g == 0 || Geom4<L>::G == 1) {
@@ -92,7 +87,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
         }
         c4_apply<L>(X, geo, th);
     }
-    double acc = 0.0;
+    F2 acc{0.0f, 0.0f};   // compensated float pair (see cb.cuh)
     for (int s = 0; s < gm.K; ++s) {
         const int tau = t0 + s;
         const int tp = (tau + 1 == gm.T) ? 0 : tau + 1;
@@ -126,9 +121,12 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
             W[k] = X[k];
             X[k] = P[k];
         }
-        acc += (double)part;
+        acc = f2_add(acc, part);
     }
-    if (pq_part != nullptr) group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
+    if (pq_part != nullptr) {
+        group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
+        cg_alpha_epilogue(gm, rhs, pq_part, rr_new_part, rr_stride, rr_n);
+    }
 }
 
 
@@ -205,12 +203,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
 #pragma unroll
     for (int j = 0; j < S - 1; ++j) issue(j);
 
-    float bt = 0.0f;
-    if (!first) {
-        const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
-        const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
-        bt = (float)cg_ratio(rn, ro);
-    }
+    const float bt = cg_beta(gm, rhs, first, rr_new_part, rr_old_part, rr_stride, rr_n);
 
     float4 W[RT], X[RT], P[RT], Y[RT];
     issue(S - 1);
@@ -234,7 +227,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
         }
         c4_apply<L>(X, geo, th);
     }
-    double acc = 0.0;
+    F2 acc{0.0f, 0.0f};   // compensated float pair (see cb.cuh)
     for (int s = 0; s < gm.K; ++s) {
         const int j = s + 2;             // slice t0 + 1 + s
         issue(j + S - 1);
@@ -271,10 +264,13 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
             W[k] = X[k];
             X[k] = P[k];
         }
-        acc += (double)part;
+        acc = f2_add(acc, part);
     }
     cp_async_wait<0>();
-    if (pq_part != nullptr) group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
+    if (pq_part != nullptr) {
+        group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
+        cg_alpha_epilogue(gm, rhs, pq_part, rr_new_part, rr_stride, rr_n);
+    }
 }
 
 
@@ -388,7 +384,7 @@ __global__ void __launch_bounds__(128, 2) k_cg_mtm32_v4s(const float* __restrict
             c4_apply<L>(X, geo, th);
         }
         ++pos;
-        double acc = 0.0;
+        F2 acc{0.0f, 0.0f};   // compensated float pair (see cb.cuh)
         for (int s = 0; s < gm.K; ++s, ++pos) {
             issue(pos + S - 1);
             cp_async_wait<S - 1>();
@@ -424,7 +420,7 @@ __global__ void __launch_bounds__(128, 2) k_cg_mtm32_v4s(const float* __restrict
                 W[k] = X[k];
                 X[k] = P[k];
             }
-            acc += (double)part;
+            acc = f2_add(acc, part);
         }
         if (pq_part != nullptr) group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
     }
@@ -1012,12 +1008,7 @@ __global__ void __launch_bounds__(256, 2) k_cg_mtm32_tp(const float* __restrict_
     __shared__ double red[32];
     auto at = [&](float4* a, int j, int k) -> float4* { return a + ((long)j * RT + k) * 32 + lane; };
 
-    float bt = 0.0f;
-    if (!first) {
-        const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
-        const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
-        bt = (float)cg_ratio(rn, ro);
-    }
+    const float bt = cg_beta(gm, rhs, first, rr_new_part, rr_old_part, rr_stride, rr_n);
     auto load_p = [&](int t, float4 (&dst)[RT]) {
         const long o = base + (long)t * N;
 #pragma unroll
@@ -1108,9 +1099,22 @@ __global__ void __launch_bounds__(256, 2) k_cg_mtm32_tp(const float* __restrict_
 template <int L>
 int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pnew, float* q,
                  int n_rhs, const int* mask, const double* rr_new, const double* rr_old,
-                 int rr_stride, int rr_n, int first, double* pq_part, cudaStream_t s)
+                 int rr_stride, int rr_n, int first, double* pq_part, cudaStream_t s,
+                 double* alpha_out, int* alpha_done, const double* beta_in)
 {
     const MvGeom g = make_geom<L>(c, n_rhs);
+    // the layouts whose kernels run cg_alpha_epilogue (scalar, float4, float4
+    // with a cp.async ring) form alpha when asked; the others leave it to the
+    // update kernel
+    MvGeom ga = g;
+    if (alpha_out != nullptr) {
+        ga.alpha_out = alpha_out;
+        ga.alpha_cnt = c->alpha_cnt;
+    }
+    ga.beta_in = beta_in;   // (the other layouts sum the partials: the same value)
+    auto mark = [&]() {
+        if (alpha_out != nullptr && alpha_done != nullptr) *alpha_done = 1;
+    };
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     if constexpr (L == 32) {
         if (c->mv_vec == 7) {   // one slice per warp, K warps per block
@@ -1182,25 +1186,30 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
             }
             if (deep)
                 HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4a<L, 3>, nb, nt, sm, s, r, pold, pnew, q,
-                                    c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first,
+                                    c->ev32, ga, mask, rr_new, rr_old, rr_stride, rr_n, first,
                                     pq_part, (float)c->th));
             else
                 HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4a<L, 2>, nb, nt, sm, s, r, pold, pnew, q,
-                                    c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first,
+                                    c->ev32, ga, mask, rr_new, rr_old, rr_stride, rr_n, first,
                                     pq_part, (float)c->th));
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4a");
+            mark();
             return HOL_OK;
         }
         if (c->mv_vec) {
             HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4<L>, nb, nt, 0, s, r, pold, pnew, q,
-                                c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first, pq_part,
+                                c->ev32, ga, mask, rr_new, rr_old, rr_stride, rr_n, first, pq_part,
                                 (float)c->th));
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4");
+            mark();
             return HOL_OK;
         }
     }
-    return run_cg_mtm32_scalar<L, false>(c, r, pold, pnew, q, n_rhs, mask, rr_new, rr_old,
-                                         rr_stride, rr_n, first, pq_part, s);
+    const int rc = run_cg_mtm32_scalar<L, false>(c, r, pold, pnew, q, n_rhs, mask, rr_new, rr_old,
+                                                 rr_stride, rr_n, first, pq_part, s,
+                                                 ga.alpha_out, beta_in);
+    if (rc == HOL_OK) mark();
+    return rc;
 }
 
 
@@ -1377,8 +1386,12 @@ int launch_MT_resid64(const hol_ctx* c, const double* u, const double* b, double
 
 int launch_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pnew, float* q,
                     int n_rhs, const int* mask, const double* rr_new, const double* rr_old,
-                    int rr_stride, int rr_n, int first, double* pq_part, cudaStream_t s)
+                    int rr_stride, int rr_n, int first, double* pq_part, cudaStream_t s,
+                    double* alpha_out, int* alpha_done, const double* beta_in)
 {
+    if (alpha_done) *alpha_done = 0;
+    if (first) beta_in = nullptr;
+    if (pq_part == nullptr) alpha_out = nullptr;
     if (c->exact)
         return launch_cg_mtm32_exact(c, r, pold, pnew, q, n_rhs, mask, rr_new, rr_old, rr_stride,
                                      rr_n, first, pq_part, s);
@@ -1386,7 +1399,7 @@ int launch_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* 
 #define X(LL)                                                                                 \
     case LL:                                                                                  \
         return run_cg_mtm32<LL>(c, r, pold, pnew, q, n_rhs, mask, rr_new, rr_old, rr_stride, \
-                                rr_n, first, pq_part, s);
+                                rr_n, first, pq_part, s, alpha_out, alpha_done, beta_in);
         HOL_FOR_EACH_L(X)
 #undef X
     }

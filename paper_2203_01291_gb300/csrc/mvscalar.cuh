@@ -27,6 +27,9 @@ struct MvGeom {
     int wpr;            // warps per right-hand side = ceil(nrun / G)
     int n_rhs;
     int pstride;        // stride of the per-unit partial sums (= wpr * G)
+    double* alpha_out;  // CG operator only (nullable): alpha per rhs, formed by the last warp
+    int* alpha_cnt;     // warps of each rhs that have finished (reset by the last one)
+    const double* beta_in;   // CG operator only (nullable): beta per rhs, formed by the update
 };
 
 template <int L>
@@ -40,7 +43,53 @@ __host__ MvGeom make_geom(const hol_ctx* c, int n_rhs)
     g.wpr = (g.nrun + G - 1) / G;
     g.n_rhs = n_rhs;
     g.pstride = g.wpr * G;
+    g.alpha_out = nullptr;
+    g.alpha_cnt = nullptr;
+    g.beta_in = nullptr;
     return g;
+}
+
+// beta of a CG step: 0 on the first, else the value the update kernel formed
+// for this rhs (when given), else (r.r)_new / (r.r)_old from the partial rows
+// (the same sums, so the same bits either way).
+__device__ __forceinline__ float cg_beta(const MvGeom& gm, int rhs, int first,
+                                         const double* __restrict__ rr_new_part,
+                                         const double* __restrict__ rr_old_part, int rr_stride,
+                                         int rr_n)
+{
+    if (first) return 0.0f;
+    if (gm.beta_in != nullptr) return (float)gm.beta_in[rhs];
+    const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
+    const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
+    return (float)cg_ratio(rn, ro);
+}
+
+// CG operator epilogue: once every warp of a right-hand side has stored its
+// partial sums of p.q, the last warp to finish forms alpha = (r.z) / (p.q)
+// of that right-hand side from the partial rows, in the order the update
+// kernel would sum them (so the same bits), and resets the count. The update
+// kernel then reads one number instead of reducing partials in every block
+// (FP64 sums cost sixty-four FP32 operations each on this GPU). The count is
+// an atomic; no warp waits for another.
+__device__ __forceinline__ void cg_alpha_epilogue(const MvGeom& gm, int rhs,
+                                                  const double* __restrict__ pq_part,
+                                                  const double* __restrict__ dz_part,
+                                                  int dz_stride, int dz_n)
+{
+    if (gm.alpha_out == nullptr) return;
+    __syncwarp();
+    __threadfence();
+    int prev = 0;
+    if ((threadIdx.x & 31) == 0) prev = atomicAdd(gm.alpha_cnt + rhs, 1);
+    prev = __shfl_sync(kFull, prev, 0);
+    if (prev != gm.wpr - 1) return;
+    __threadfence();
+    const double pq = warp_sum_array_cg(pq_part + (long)rhs * gm.pstride, gm.nrun);
+    const double dz = warp_sum_array_cg(dz_part + (long)rhs * dz_stride, dz_n);
+    if ((threadIdx.x & 31) == 0) {
+        gm.alpha_out[rhs] = cg_ratio(dz, pq);
+        gm.alpha_cnt[rhs] = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -192,12 +241,7 @@ __global__ void __launch_bounds__(128) k_cg_mtm32(const float* __restrict__ r,
     const long base = (long)rhs * gm.T * N + geo.ix;
 
     // beta = (r.r)_new / (r.r)_old, identical bits in every warp of this rhs
-    float bt = 0.0f;
-    if (!first) {
-        const double rn = warp_sum_array(rr_new_part + (long)rhs * rr_stride, rr_n);
-        const double ro = warp_sum_array(rr_old_part + (long)rhs * rr_stride, rr_n);
-        bt = (float)cg_ratio(rn, ro);
-    }
+    const float bt = cg_beta(gm, rhs, first, rr_new_part, rr_old_part, rr_stride, rr_n);
 
     float W[L], X[L], P[L], Y[L];
     // Y <- C p_{t0-1}
@@ -221,7 +265,7 @@ __global__ void __launch_bounds__(128) k_cg_mtm32(const float* __restrict__ r,
         }
         kin_apply<float, L, EX>(X, geo, kin);
     }
-    double acc = 0.0;
+    F2 acc{0.0f, 0.0f};   // compensated float pair (see cb.cuh)
     for (int s = 0; s < gm.K; ++s) {
         const int tau = t0 + s;
         const int tp = (tau + 1 == gm.T) ? 0 : tau + 1;
@@ -248,9 +292,12 @@ __global__ void __launch_bounds__(128) k_cg_mtm32(const float* __restrict__ r,
             W[iy] = X[iy];
             X[iy] = P[iy];
         }
-        acc += (double)part;
+        acc = f2_add(acc, part);
     }
-    if (pq_part != nullptr) group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
+    if (pq_part != nullptr) {
+        group_store_sum<L>(acc, valid, pq_part + (long)rhs * gm.pstride + run);
+        cg_alpha_epilogue(gm, rhs, pq_part, rr_new_part, rr_stride, rr_n);
+    }
 }
 
 template <int L>
@@ -326,9 +373,15 @@ template <int L, bool EX>
 int run_cg_mtm32_scalar(const hol_ctx* c, const float* r, const float* pold, float* pnew,
                         float* q, int n_rhs, const int* mask, const double* rr_new,
                         const double* rr_old, int rr_stride, int rr_n, int first,
-                        double* pq_part, cudaStream_t s)
+                        double* pq_part, cudaStream_t s, double* alpha_out = nullptr,
+                        const double* beta_in = nullptr)
 {
-    const MvGeom g = make_geom<L>(c, n_rhs);
+    MvGeom g = make_geom<L>(c, n_rhs);
+    if (alpha_out != nullptr && pq_part != nullptr) {   // see cg_alpha_epilogue
+        g.alpha_out = alpha_out;
+        g.alpha_cnt = c->alpha_cnt;
+    }
+    g.beta_in = beta_in;
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     HOL_CUDA(launch_pdl(c, k_cg_mtm32<L, EX>, nb, nt, 0, s, r, pold, pnew, q, c->ev32, g, mask,
                         rr_new, rr_old, rr_stride, rr_n, first, pq_part, kin_of<float>(c)));
