@@ -33,7 +33,8 @@ __all__ = ["Context", "HolError", "HOL_OP_M", "HOL_OP_MT", "HOL_OP_MTM", "HOL_F6
            "pseudofermion_phi", "phi_to_rhs", "hol_launch_count", "hol_timer_enable",
            "hol_timer_read", "fermion_matvec_static", "mass_apply", "md_integrate",
            "fourier_accel_leapfrog", "hol_md_opts", "stochastic_measure", "hol_tune",
-           "hmc_batch", "hmc_batch_graph", "cg_solve_graph", "measure_batch", "hol_set_option", "hol_get_option", "hol_fma_peak",
+           "hmc_batch", "hmc_batch_graph", "cg_solve_graph", "measure_batch",
+           "measure_batch_graph", "hol_set_option", "hol_get_option", "hol_fma_peak",
            "global_update", "HOL_REFLECT", "HOL_SWAP", "measure_observables",
            "HOL_KINETIC_CHECKERBOARD", "HOL_KINETIC_EXACT", "hol_arnoldi_bounds",
            "hol_get_bounds",
@@ -281,6 +282,18 @@ def hmc_batch_graph(contexts, xs, R_pfs, R_ps, opts: hol_md_opts, us):
     _check(load().hmc_batch_graph(hs, n, _ptrs(xs), _ptrs(R_pfs), _ptrs(R_ps), n_pf,
                                   ctypes.byref(opts), u, acc, dh, _stream()))
     return np.array(acc[:], dtype=bool), np.array(dh[:])
+
+
+def measure_batch_graph(contexts, xis, Gxis, G2s, opts: hol_cg_opts, G4s=None,
+                        four_point: int = 0) -> None:
+    """stochastic_measure for every chain, all chains in one captured CUDA
+    graph (include/holstein.h, measure_batch_graph)."""
+    n = len(contexts)
+    hs = (ctypes.c_void_p * n)(*[c.handle.value for c in contexts])
+    n_rv = xis[0].numel() // contexts[0].n
+    g4 = _ptrs(G4s) if G4s is not None else None
+    _check(load().measure_batch_graph(hs, n, _ptrs(xis), n_rv, ctypes.byref(opts), _ptrs(Gxis),
+                                      _ptrs(G2s), g4, int(four_point), _stream()))
 
 
 def measure_batch(contexts, xis, Gxis, G2s, opts: hol_cg_opts, G4s=None, four_point: int = 0,

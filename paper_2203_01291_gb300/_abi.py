@@ -87,6 +87,9 @@ SIGNATURES = {
     "hmc_batch_graph": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                              ctypes.POINTER(_VP), _I, ctypes.POINTER(hol_md_opts),
                              ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
+    "measure_batch_graph": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), _I,
+                                 ctypes.POINTER(hol_cg_opts), ctypes.POINTER(_VP),
+                                 ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP]),
     "measure_batch": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), _I,
                            ctypes.POINTER(hol_cg_opts), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                            ctypes.POINTER(_VP), _I, _I]),

@@ -634,7 +634,8 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                 int adone = 0;   // alpha formed by the operator's last warp
                 rc = launch_cg_mtm32(c, z32, first ? z32 : p32[pp], p32[1 - pp], q32, n_rhs, act_d,
                                      B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first, B.pq, s,
-                                     c->alpha_now, &adone, pc ? nullptr : c->beta_now);
+                                     (c->handoff & 1) ? c->alpha_now : nullptr, &adone,
+                                     (!pc && (c->handoff & 2)) ? c->beta_now : nullptr);
                 if (rc) return rc;
                 timer_stop(c, KT_OPERATOR, s);
                 pp = 1 - pp;
@@ -644,7 +645,7 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                 HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, s, e32, r32, p32[pp], p32[1 - pp], q32, n,
                                     act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst,
                                     c->alpha_buf, adone ? (const double*)c->alpha_now : nullptr,
-                                    pc ? nullptr : c->beta_now, c->beta_cnt));
+                                    (!pc && (c->handoff & 2)) ? c->beta_now : nullptr, c->beta_cnt));
             } else {
                 BetaSrc bs{B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first};
                 timer_start(c, KT_OPERATOR, s, n_active * nd * 48.0 + nd * 16.0);
@@ -769,7 +770,7 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
             }
             HOL_CHECK_LAUNCH("k_conj_scale");
             HOL_CUDA(launch_pdl(c, k_copy_rows, n_rhs, 256, 0, s, B.dz[cur], B.dz[1 - cur], rel_d,
-                                (mixed && !pc) ? c->beta_now : nullptr, dz_n));
+                                (mixed && !pc && (c->handoff & 2)) ? c->beta_now : nullptr, dz_n));
             HOL_CHECK_LAUNCH("k_copy_rows");
             cnt[1 - cur] = cnt[cur];
         }
@@ -1466,7 +1467,8 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
                 int adone = 0;
                 r2 = launch_cg_mtm32(c, z32, first ? z32 : p32[pp], p32[1 - pp], q32, n_rhs, act_d,
                                      B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first, B.pq, cs,
-                                     c->alpha_now, &adone, pc ? nullptr : c->beta_now);
+                                     (c->handoff & 1) ? c->alpha_now : nullptr, &adone,
+                                     (!pc && (c->handoff & 2)) ? c->beta_now : nullptr);
                 if (r2) return r2;
                 pp = 1 - pp;
                 auto* upd = fold == 0 ? k_cg_update<float, 0>
@@ -1474,7 +1476,7 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
                 HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, cs, e32, r32, p32[pp], p32[1 - pp], q32, n,
                                     act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst,
                                     c->alpha_buf, adone ? (const double*)c->alpha_now : nullptr,
-                                    pc ? nullptr : c->beta_now, c->beta_cnt));
+                                    (!pc && (c->handoff & 2)) ? c->beta_now : nullptr, c->beta_cnt));
             } else {
                 BetaSrc bs{B.dz[cur], B.dz[1 - cur], kRedStride, dz_n, first};
                 r2 = launch_M_upd64(c, z64, first ? z64 : p64[pp], p64[1 - pp], w64, n_rhs, act_d,
@@ -1542,7 +1544,7 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
             }
             HOL_CHECK_LAUNCH("k_conj_scale");
             HOL_CUDA(launch_pdl(c, k_copy_rows, n_rhs, 256, 0, is, B.dz[cur], B.dz[1 - cur], rel_d,
-                                (mixed && !pc) ? c->beta_now : nullptr, dz_n));
+                                (mixed && !pc && (c->handoff & 2)) ? c->beta_now : nullptr, dz_n));
             HOL_CHECK_LAUNCH("k_copy_rows");
             k_dcg_finish<<<1, kDcgThreads, 0, is>>>(B.tr, nb2, n_rhs, o->tol, act_d, rel_d, d);
             HOL_CHECK_LAUNCH("k_dcg_finish");

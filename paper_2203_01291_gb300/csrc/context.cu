@@ -557,6 +557,10 @@ extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
         c->persist = value ? 1 : 0;
     } else if (is("pdl")) {
         c->pdl = value ? 1 : 0;
+    } else if (is("scalar_handoff")) {
+        if (value < 0 || value > 3)
+            return set_error(HOL_EINVAL, "hol_set_option: scalar_handoff must be 0..3");
+        c->handoff = value;
     } else if (is("merged_cg") || is("fused_cg")) {
         if (value && c->exact)
             return set_error(HOL_EINVAL, "hol_set_option: %s is checkerboard only", name);
@@ -589,6 +593,7 @@ extern "C" int hol_get_option(const hol_ctx* c, const char* name, int* value)
     else if (is("merged_cg")) *value = c->merged;
     else if (is("fused_cg")) *value = c->fused;
     else if (is("pdl")) *value = c->pdl;
+    else if (is("scalar_handoff")) *value = c->handoff;
     else return set_error(HOL_EINVAL, "hol_get_option: unknown option '%s'", name);
     return HOL_OK;
 }

@@ -11,7 +11,9 @@
 // the capture), and the step graph is launched N_t times. The host only reads
 // the energies at the end for the Metropolis decisions. Each chain computes
 // exactly what fourier_accel_leapfrog computes for it (same kernels, same
-// decisions, bitwise the same numbers).
+// decisions, bitwise the same numbers). measure_batch_graph captures every
+// chain's stochastic measurement (probe solves and FFT accumulation) into one
+// graph the same way.
 #include <math.h>
 
 #include <vector>
@@ -263,5 +265,65 @@ extern "C" int hmc_batch_graph(hol_ctx* const* ctxs, int n_chains, double* const
     HOL_CUDA(cudaStreamSynchronize(os));
     HOL_CUDA(cudaEventRecord(st.e[0], os));
     HOL_CUDA(cudaStreamWaitEvent(user, st.e[0], 0));
+    return HOL_OK;
+}
+
+extern "C" int measure_batch_graph(hol_ctx* const* ctxs, int n_chains, const double* const* xi,
+                                   int n_rv, const hol_cg_opts* opts, double* const* Gxi,
+                                   double* const* G2, double* const* G4, int four_point,
+                                   void* stream)
+{
+    HOL_TRACE("measure_batch_graph");
+    if (!ctxs || !xi || !opts || !Gxi || !G2 || n_chains < 1)
+        return set_error(HOL_EINVAL, "measure_batch_graph: null argument or no chains");
+    if (four_point && !G4)
+        return set_error(HOL_EINVAL, "measure_batch_graph: four-point products need G4");
+    for (int k = 0; k < n_chains; ++k) {
+        hol_ctx* c = ctxs[k];
+        if (!c || !xi[k] || !Gxi[k] || !G2[k] || (four_point && !G4[k]))
+            return set_error(HOL_EINVAL, "measure_batch_graph: null argument (chain %d)", k);
+        if (int rc_ = check_graph_solver(c, opts, "measure_batch_graph")) return rc_;
+        if (int rc_ = measure_prepare(c)) return rc_;
+        for (int j = 0; j < k; ++j)
+            if (ctxs[j] == c)
+                return set_error(HOL_EINVAL, "measure_batch_graph: context of chain %d repeated",
+                                 k);
+    }
+    cudaStream_t user = (cudaStream_t)stream;
+    Streams st;
+    if (int rc_ = st.create(n_chains + 1, n_chains + 2)) return rc_;
+    cudaStream_t os = st.s[n_chains];
+    HOL_CUDA(cudaEventRecord(st.e[n_chains + 1], user));
+    HOL_CUDA(cudaStreamWaitEvent(os, st.e[n_chains + 1], 0));
+    for (int k = 0; k < n_chains; ++k)
+        HOL_CUDA(cudaMemsetAsync(dcg_state(ctxs[k]).g, 0, DCG_COUNT * sizeof(int), os));
+    Graph g;
+    int rc;
+    {
+        std::vector<CaptureScope*> scopes;
+        for (int k = 0; k < n_chains; ++k) scopes.push_back(new CaptureScope(ctxs[k]));
+        rc = capture(os, g, [&]() {
+            return fork_join(os, st, n_chains, [&](int k, cudaStream_t sk) {
+                return measure_run(ctxs[k], xi[k], n_rv, opts, Gxi[k], G2[k],
+                                   four_point ? G4[k] : nullptr, four_point, nullptr, sk);
+            });
+        });
+        for (CaptureScope* p : scopes) delete p;
+    }
+    if (rc) return rc;
+    HOL_CUDA(cudaGraphLaunch(g.e, os));
+    std::vector<int> gs(DCG_COUNT * (size_t)n_chains);
+    for (int k = 0; k < n_chains; ++k)
+        HOL_CUDA(cudaMemcpyAsync(gs.data() + DCG_COUNT * k, dcg_state(ctxs[k]).g,
+                                 DCG_COUNT * sizeof(int), cudaMemcpyDeviceToHost, os));
+    HOL_CUDA(cudaStreamSynchronize(os));
+    HOL_CUDA(cudaEventRecord(st.e[0], os));
+    HOL_CUDA(cudaStreamWaitEvent(user, st.e[0], 0));
+    for (int k = 0; k < n_chains; ++k) {
+        const int bad = gs[DCG_COUNT * k + DCG_STICKY];
+        if (bad)
+            return set_error(bad, "measure_batch_graph: a probe solve of chain %d %s", k,
+                             bad == HOL_ENUMERIC ? "met a non-finite residual" : "did not converge");
+    }
     return HOL_OK;
 }

@@ -241,6 +241,7 @@ struct hol_ctx {
     // block of the update kernel, and that kernel's per-rhs block count
     double* beta_now;
     int* beta_cnt;
+    int handoff;         // launch option "scalar_handoff": bit 0 alpha_now, bit 1 beta_now in use
 };
 
 namespace hol {
@@ -471,6 +472,12 @@ int md_set_kick(hol_ctx* c, double kick, cudaStream_t s);
 int md_step(hol_ctx* c, double* x, int n_pf, const hol_md_opts* o, cudaStream_t s);
 int md_end(hol_ctx* c, double* x, int n_pf, const hol_md_opts* o, cudaStream_t s);
 int md_check(const hol_ctx* c, const hol_md_opts* o, int n_pf);
+// The measurement of stochastic_measure on stream s (measure.cu): inside a
+// graph capture its solves are device-driven and `iters` must be null;
+// measure_prepare raises the kernels' shared-memory limits beforehand.
+int measure_run(hol_ctx* c, const double* xi, int n_rv, const hol_cg_opts* opts, double* Gxi,
+                double* G2, double* G4, int four_point, int* iters, cudaStream_t s);
+int measure_prepare(hol_ctx* c);
 int measure_alloc(hol_ctx* c);
 int precond_check_shape(const hol_ctx* c);
 int precond_tiles(const hol_ctx* c, int prec);

@@ -279,6 +279,24 @@ int measure_alloc(hol_ctx* c)
     return HOL_OK;
 }
 
+// Shared-memory limits of the measurement kernels for this context's shape,
+// raised outside any stream capture.
+int measure_prepare(hol_ctx* c)
+{
+    Meas m;
+    m.c = c;
+    m.pt = plan_of(c->T);
+    m.ps = plan_of(c->L);
+    if (m.pt.n < 0 || m.ps.n < 0)
+        return set_error(HOL_EINVAL, "stochastic_measure: L=%d and Ltau=%d need prime factors in {2,3,5,7}",
+                         c->L, c->T);
+    m.sm_t = 2 * (size_t)c->T * kMeasTS * sizeof(double2);
+    return m.attrs();
+}
+
+int measure_run(hol_ctx* c, const double* xi, int n_rv, const hol_cg_opts* opts, double* Gxi,
+                double* G2, double* G4, int four_point, int* iters, cudaStream_t stream);
+
 }  // namespace hol
 
 using namespace hol;
@@ -288,6 +306,14 @@ extern "C" int stochastic_measure(hol_ctx* c, const double* xi, int n_rv, const 
                                   void* stream)
 {
     HOL_TRACE("stochastic_measure");
+    return measure_run(c, xi, n_rv, opts, Gxi, G2, G4, four_point, iters, (cudaStream_t)stream);
+}
+
+// The measurement of stochastic_measure; inside a graph capture its probe
+// solves are device-driven (cg_run_dev) and no iteration counts are returned.
+int hol::measure_run(hol_ctx* c, const double* xi, int n_rv, const hol_cg_opts* opts, double* Gxi,
+                     double* G2, double* G4, int four_point, int* iters, cudaStream_t stream)
+{
     if (!c || !xi || !opts || !Gxi || !G2) return set_error(HOL_EINVAL, "stochastic_measure: null argument");
     if (int rc_ = require_aligned("stochastic_measure", {xi, Gxi, G2, G4})) return rc_;
     if (!c->field_set) return set_error(HOL_EINVAL, "stochastic_measure: hol_set_field not called");
@@ -317,6 +343,10 @@ extern "C" int stochastic_measure(hol_ctx* c, const double* xi, int n_rv, const 
     for (int v0 = 0; v0 < n_rv; v0 += R) {
         const int nv = (n_rv - v0) < R ? (n_rv - v0) : R;
         if ((rc = launch_MT(c, HOL_F64, xi + (long)v0 * n, c->md_b, nv, nullptr, s))) return rc;
+        if (c->capturing) {
+            if ((rc = cg_run_dev(c, c->md_b, Gxi + (long)v0 * n, nv, opts, s))) return rc;
+            continue;
+        }
         std::vector<int> it(nv);
         if ((rc = cg_solve(c, c->md_b, Gxi + (long)v0 * n, nv, opts, it.data(), nullptr, s)))
             return rc;

@@ -119,3 +119,35 @@ def test_hmc_batch_graph_equals_sequential(prec, precond, n_steps):
     finally:
         for c in ctxs:
             c.close()
+
+
+def test_measure_batch_graph_equals_stochastic_measure():
+    """Every chain's 2-point function, Wick products and probe solutions from
+    the one-graph batched measurement are bitwise those of stochastic_measure
+    run chain by chain (mixed precision, probes in blocks of max_rhs)."""
+    ws = _chains()[:4]
+    opts = hg.hol_cg_opts(1e-10, 100000, 0, hg.HOL_F32, 50, 10)
+    ctxs = [hg.Context.from_workload(w, max_rhs=4) for w in ws]
+    try:
+        xis, G2s, G4s, Gxis, refs = [], [], [], [], []
+        for w, c in zip(ws, ctxs):
+            c.set_field(torch.tensor(hi.phonon_field(w), device=DEV))
+            xi = torch.tensor(hi.z2_vectors(w, 6, seed=w.seed + 3), device=DEV)
+            Gxi = torch.empty_like(xi)
+            G2 = torch.empty(2 * w.Ltau, w.L, w.L, dtype=torch.float64, device=DEV)
+            G4 = torch.empty(3, 2 * w.Ltau, w.L, w.L, dtype=torch.float64, device=DEV)
+            c.stochastic_measure(xi, Gxi, G2, G4, 7, tol=1e-10, prec=hg.HOL_F32)
+            refs.append((Gxi.cpu().numpy(), G2.cpu().numpy(), G4.cpu().numpy()))
+            xis.append(xi)
+            Gxis.append(torch.full_like(xi, float("nan")))
+            G2s.append(torch.full_like(G2, float("nan")))
+            G4s.append(torch.full_like(G4, float("nan")))
+        hg.measure_batch_graph(ctxs, xis, Gxis, G2s, opts, G4s=G4s, four_point=7)
+        torch.cuda.synchronize()
+        for k in range(len(ws)):
+            assert np.array_equal(Gxis[k].cpu().numpy(), refs[k][0])
+            assert np.array_equal(G2s[k].cpu().numpy(), refs[k][1])
+            assert np.array_equal(G4s[k].cpu().numpy(), refs[k][2])
+    finally:
+        for c in ctxs:
+            c.close()
