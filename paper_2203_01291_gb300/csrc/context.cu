@@ -149,6 +149,7 @@ void free_ctx(hol_ctx* c)
     if (c->alpha_cnt) cudaFree(c->alpha_cnt);
     if (c->beta_now) cudaFree(c->beta_now);
     if (c->beta_cnt) cudaFree(c->beta_cnt);
+    if (c->kpm_q) cudaFree(c->kpm_q);
     for (cudaStream_t cs : c->cap_s)
         if (cs) cudaStreamDestroy(cs);
     timer_free(c->timer);
@@ -344,8 +345,10 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     ALLOC(c->alpha_cnt, R * sizeof(int));
     ALLOC(c->beta_now, R * sizeof(double));
     ALLOC(c->beta_cnt, R * sizeof(int));
+    ALLOC(c->kpm_q, 2 * sizeof(int));
     if (cudaMemset(c->alpha_cnt, 0, R * sizeof(int)) != cudaSuccess ||
-        cudaMemset(c->beta_cnt, 0, R * sizeof(int)) != cudaSuccess) {
+        cudaMemset(c->beta_cnt, 0, R * sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->kpm_q, 0, 2 * sizeof(int)) != cudaSuccess) {
         free_ctx(c);
         return set_error(HOL_ECUDA, "hol_create: memset");
     }
@@ -557,6 +560,10 @@ extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
         c->persist = value ? 1 : 0;
     } else if (is("pdl")) {
         c->pdl = value ? 1 : 0;
+    } else if (is("kpm_queue")) {
+        if (value < 0 || value > 8)
+            return set_error(HOL_EINVAL, "hol_set_option: kpm_queue must be 0..8");
+        c->kpm_queue = value;
     } else if (is("scalar_handoff")) {
         if (value < 0 || value > 3)
             return set_error(HOL_EINVAL, "hol_set_option: scalar_handoff must be 0..3");
@@ -594,6 +601,7 @@ extern "C" int hol_get_option(const hol_ctx* c, const char* name, int* value)
     else if (is("fused_cg")) *value = c->fused;
     else if (is("pdl")) *value = c->pdl;
     else if (is("scalar_handoff")) *value = c->handoff;
+    else if (is("kpm_queue")) *value = c->kpm_queue;
     else return set_error(HOL_EINVAL, "hol_get_option: unknown option '%s'", name);
     return HOL_OK;
 }

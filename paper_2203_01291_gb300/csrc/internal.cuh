@@ -242,6 +242,9 @@ struct hol_ctx {
     double* beta_now;
     int* beta_cnt;
     int handoff;         // launch option "scalar_handoff": bit 0 alpha_now, bit 1 beta_now in use
+    int kpm_queue;       // launch option "kpm_queue": persistent register-KPM grid of this many
+                         // blocks per multiprocessor (0: one block per problem)
+    int* kpm_q;          // its work queue [2] (next problem, finished blocks; zero between launches)
 };
 
 namespace hol {

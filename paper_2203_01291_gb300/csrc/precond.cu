@@ -597,130 +597,157 @@ __device__ __forceinline__ void kc4(CV<CPL> (&v)[2], const KGeo<L, CPL>& g, floa
     }
 }
 
+// One block per (omega, rhs) problem (queue null), or a persistent grid of a
+// few blocks per multiprocessor taking problems from an atomic queue in the
+// order omega = 0, 1, ... (the longest Chebyshev series first, since N_P
+// falls with omega): the long series then run on multiprocessors shared with
+// few other blocks while the short ones fill the rest. queue[0] is the next
+// problem, queue[1] counts finished blocks; the last block resets both for
+// the next launch (no block waits for another). Which block runs a problem
+// does not change its arithmetic.
 template <int L, int CPL>
 __global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
     k_kpm_reg(const float2* __restrict__ vin, float2* __restrict__ vout,
               const double* __restrict__ dbar, const double* __restrict__ scal,
               const int* __restrict__ npv, const double2* __restrict__ coef, int n_rhs, int Th,
-              int max_np, int mode, float th)
+              int max_np, int mode, float th, int* __restrict__ queue)
 {
     pdl_wait();      // the input comes from the previous kernel of the stream
     const PdlTriggerAtExit pdl_at_exit;
     using G = KGeo<L, CPL>;
     __shared__ float xbuf[G::W > 1 ? 2 * G::W * 2 * G::LR * 2 * CPL : 1];
+    __shared__ int s_item;
     const G g;
-    const int wq = blockIdx.x / n_rhs, rhs = blockIdx.x - wq * n_rhs;
-    const long off = ((long)rhs * Th + wq) * L * L;
-    const int r0 = g.row0();
-    CV<CPL> cur[2];
-    float d[2][CPL];
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const long e = off + (long)(r0 + r) * L + CPL * g.cx;
-#pragma unroll
-        for (int q = 0; q < CPL; q += 2) {
-            const float4 a = *reinterpret_cast<const float4*>(vin + e + q);
-            cur[r].re[q] = a.x;
-            cur[r].im[q] = a.y;
-            cur[r].re[q + 1] = a.z;
-            cur[r].im[q + 1] = a.w;
+    const int n_items = n_rhs * Th;
+    for (int item = blockIdx.x;;) {
+        if (queue != nullptr) {
+            __syncthreads();   // the previous problem's shared data is no longer read
+            if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+            __syncthreads();
+            item = s_item;
+            if (item >= n_items) break;
         }
-        const int i = (r0 + r) * L + CPL * g.cx;
+        const int wq = item / n_rhs, rhs = item - wq * n_rhs;
+        const long off = ((long)rhs * Th + wq) * L * L;
+        const int r0 = g.row0();
+        CV<CPL> cur[2];
+        float d[2][CPL];
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) d[r][q] = (float)dbar[i + q];
-    }
-    const double bmin = scal[S_BMIN], bmax = scal[S_BMAX];
-    const double db = bmax - bmin;
-    const float a = (float)(2.0 / db), c0 = (float)(-2.0 * bmin / db - 1.0);
-    const int np = npv[wq];
-    // this omega's coefficients, rounded to FP32 once (no conversion on the
-    // chain of dependent steps)
-    extern __shared__ float2 cw[];
-    for (int m = threadIdx.x; m < np; m += blockDim.x) {
-        const double2 c = coef[(long)wq * max_np + m];
-        cw[m] = make_float2((float)c.x, (float)c.y);
-    }
-    __syncthreads();
-    int par = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool trans = (pass == 0);
-        if (trans && !(mode & 1)) continue;
-        if (!trans && !(mode & 2)) continue;
-        const float sgn = trans ? -1.0f : 1.0f;    // conj coefficients for the transpose
-        CV<CPL> acc[2], prev[2];
-        {
-            const float2 c = cw[0];
-            const float cr = c.x, ci = sgn * c.y;
+        for (int r = 0; r < 2; ++r) {
+            const long e = off + (long)(r0 + r) * L + CPL * g.cx;
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                prev[r] = cur[r];
-#pragma unroll
-                for (int e = 0; e < CPL; ++e) {
-                    acc[r].re[e] = cr * cur[r].re[e] - ci * cur[r].im[e];
-                    acc[r].im[e] = cr * cur[r].im[e] + ci * cur[r].re[e];
-                }
+            for (int q = 0; q < CPL; q += 2) {
+                const float4 a = *reinterpret_cast<const float4*>(vin + e + q);
+                cur[r].re[q] = a.x;
+                cur[r].im[q] = a.y;
+                cur[r].re[q + 1] = a.z;
+                cur[r].im[q + 1] = a.w;
             }
-        }
-        for (int m = 1; m < np; ++m) {
-            CV<CPL> old[2], b[2];
+            const int i = (r0 + r) * L + CPL * g.cx;
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                old[r] = cur[r];
-                b[r] = cur[r];
-                if (trans) {
+            for (int q = 0; q < CPL; ++q) d[r][q] = (float)dbar[i + q];
+        }
+        const double bmin = scal[S_BMIN], bmax = scal[S_BMAX];
+        const double db = bmax - bmin;
+        const float a = (float)(2.0 / db), c0 = (float)(-2.0 * bmin / db - 1.0);
+        const int np = npv[wq];
+        // this omega's coefficients, rounded to FP32 once (no conversion on the
+        // chain of dependent steps)
+        extern __shared__ float2 cw[];
+        for (int m = threadIdx.x; m < np; m += blockDim.x) {
+            const double2 c = coef[(long)wq * max_np + m];
+            cw[m] = make_float2((float)c.x, (float)c.y);
+        }
+        __syncthreads();
+        int par = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            const bool trans = (pass == 0);
+            if (trans && !(mode & 1)) continue;
+            if (!trans && !(mode & 2)) continue;
+            const float sgn = trans ? -1.0f : 1.0f;    // conj coefficients for the transpose
+            CV<CPL> acc[2], prev[2];
+            {
+                const float2 c = cw[0];
+                const float cr = c.x, ci = sgn * c.y;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    prev[r] = cur[r];
 #pragma unroll
                     for (int e = 0; e < CPL; ++e) {
-                        b[r].re[e] *= d[r][e];
-                        b[r].im[e] *= d[r][e];
+                        acc[r].re[e] = cr * cur[r].re[e] - ci * cur[r].im[e];
+                        acc[r].im[e] = cr * cur[r].im[e] + ci * cur[r].re[e];
                     }
                 }
             }
-            if (trans) {
-                kc4<L, CPL>(b, g, th, xbuf, par);
-                kc3<CPL>(b, th);
-                kc2<L, CPL>(b, g, th);
-                kc1<CPL>(b, th);
-            } else {
-                kc1<CPL>(b, th);
-                kc2<L, CPL>(b, g, th);
-                kc3<CPL>(b, th);
-                kc4<L, CPL>(b, g, th, xbuf, par);
-            }
-            par ^= 1;
-            const float2 c = cw[m];
-            const float cr = c.x, ci = sgn * c.y;
-            // alpha_m = (m == 1 ? 1 : 2) (a B + c0) alpha_{m-1} - (m == 1 ? 0 : alpha_{m-2})
-            const float f2 = (m == 1) ? 1.0f : 2.0f;
-            const float pm = (m == 1) ? 0.0f : 1.0f;
+            for (int m = 1; m < np; ++m) {
+                CV<CPL> old[2], b[2];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
+                for (int r = 0; r < 2; ++r) {
+                    old[r] = cur[r];
+                    b[r] = cur[r];
+                    if (trans) {
 #pragma unroll
-                for (int e = 0; e < CPL; ++e) {
-                    float br = b[r].re[e], bi = b[r].im[e];
-                    if (!trans) {
-                        br *= d[r][e];
-                        bi *= d[r][e];
+                        for (int e = 0; e < CPL; ++e) {
+                            b[r].re[e] *= d[r][e];
+                            b[r].im[e] *= d[r][e];
+                        }
                     }
-                    const float xr = f2 * fmaf(a, br, c0 * old[r].re[e]) - pm * prev[r].re[e];
-                    const float xi = f2 * fmaf(a, bi, c0 * old[r].im[e]) - pm * prev[r].im[e];
-                    cur[r].re[e] = xr;
-                    cur[r].im[e] = xi;
-                    acc[r].re[e] = fmaf(cr, xr, fmaf(-ci, xi, acc[r].re[e]));
-                    acc[r].im[e] = fmaf(cr, xi, fmaf(ci, xr, acc[r].im[e]));
                 }
-                prev[r] = old[r];
+                if (trans) {
+                    kc4<L, CPL>(b, g, th, xbuf, par);
+                    kc3<CPL>(b, th);
+                    kc2<L, CPL>(b, g, th);
+                    kc1<CPL>(b, th);
+                } else {
+                    kc1<CPL>(b, th);
+                    kc2<L, CPL>(b, g, th);
+                    kc3<CPL>(b, th);
+                    kc4<L, CPL>(b, g, th, xbuf, par);
+                }
+                par ^= 1;
+                const float2 c = cw[m];
+                const float cr = c.x, ci = sgn * c.y;
+                // alpha_m = (m == 1 ? 1 : 2) (a B + c0) alpha_{m-1} - (m == 1 ? 0 : alpha_{m-2})
+                const float f2 = (m == 1) ? 1.0f : 2.0f;
+                const float pm = (m == 1) ? 0.0f : 1.0f;
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+#pragma unroll
+                    for (int e = 0; e < CPL; ++e) {
+                        float br = b[r].re[e], bi = b[r].im[e];
+                        if (!trans) {
+                            br *= d[r][e];
+                            bi *= d[r][e];
+                        }
+                        const float xr = f2 * fmaf(a, br, c0 * old[r].re[e]) - pm * prev[r].re[e];
+                        const float xi = f2 * fmaf(a, bi, c0 * old[r].im[e]) - pm * prev[r].im[e];
+                        cur[r].re[e] = xr;
+                        cur[r].im[e] = xi;
+                        acc[r].re[e] = fmaf(cr, xr, fmaf(-ci, xi, acc[r].re[e]));
+                        acc[r].im[e] = fmaf(cr, xi, fmaf(ci, xr, acc[r].im[e]));
+                    }
+                    prev[r] = old[r];
+                }
             }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) cur[r] = acc[r];
         }
 #pragma unroll
-        for (int r = 0; r < 2; ++r) cur[r] = acc[r];
+        for (int r = 0; r < 2; ++r) {
+            const long e = off + (long)(r0 + r) * L + CPL * g.cx;
+#pragma unroll
+            for (int q = 0; q < CPL; q += 2)
+                *reinterpret_cast<float4*>(vout + e + q) =
+                    make_float4(cur[r].re[q], cur[r].im[q], cur[r].re[q + 1], cur[r].im[q + 1]);
+        }
+        if (queue == nullptr) break;
     }
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const long e = off + (long)(r0 + r) * L + CPL * g.cx;
-#pragma unroll
-        for (int q = 0; q < CPL; q += 2)
-            *reinterpret_cast<float4*>(vout + e + q) =
-                make_float4(cur[r].re[q], cur[r].im[q], cur[r].re[q + 1], cur[r].im[q + 1]);
+    if (queue != nullptr && threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(queue + 1, 1) == (int)gridDim.x - 1) {
+            queue[0] = 0;
+            queue[1] = 0;
+        }
     }
 }
 
@@ -869,9 +896,16 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
             float2* o2 = reinterpret_cast<float2*>(h1);
             auto run = [&](auto kern, int threads) -> int {
                 if (int e = set_smem_attr<R>((const void*)kern, csm)) return e;
-                HOL_CUDA(launch_pdl(c, kern, ka.Th * n_rhs, threads, csm, s, i2, o2, c->dbar,
-                                    c->scal, c->kpm.np, c->kpm.coef, n_rhs, ka.Th, ka.max_np,
-                                    mode, th));
+                const int items = ka.Th * n_rhs;
+                int grid = items;
+                int* q = nullptr;
+                if (c->kpm_queue > 0 && items > c->kpm_queue * c->sms) {
+                    grid = c->kpm_queue * c->sms;   // persistent: problems from the queue
+                    q = c->kpm_q;
+                }
+                HOL_CUDA(launch_pdl(c, kern, grid, threads, csm, s, i2, o2, c->dbar, c->scal,
+                                    c->kpm.np, c->kpm.coef, n_rhs, ka.Th, ka.max_np, mode, th,
+                                    q));
                 return HOL_OK;
             };
             const bool two = c->kpm_reg == 2;   // two columns per lane

@@ -63,11 +63,13 @@ def test_precond_apply_vs_oracle(L, T):
                 assert _rel(out.cpu().double().numpy(), ref) < tol, (which, dt)
 
 
-@pytest.mark.parametrize("kpm", [0, 1, 2])
-@pytest.mark.parametrize("L,T", [(16, 20), (32, 12), (16, 40)])
-def test_precond_fp32_kpm_variants(kpm, L, T):
+@pytest.mark.parametrize("kpm,queue", [(0, 0), (1, 0), (2, 0), (1, 1), (2, 1), (2, 3)])
+@pytest.mark.parametrize("L,T", [(16, 20), (32, 12), (16, 40), (32, 200)])
+def test_precond_fp32_kpm_variants(kpm, queue, L, T):
     """The FP32 KPM kernels (shared-memory, registers with four or two
-    columns per lane) all match the oracle's step-by-step KPM."""
+    columns per lane, one block per problem or a persistent grid taking
+    problems from a queue) all match the oracle's step-by-step KPM, also
+    twice in a row (the queue resets itself)."""
     w, x, ctx = _setup(L, T, seed=4)
     m = D.model_of(w)
     v = hi.gaussian_vectors(w, 2, seed=10)
@@ -75,10 +77,12 @@ def test_precond_fp32_kpm_variants(kpm, L, T):
         [D.precond_inverse_apply(m, x, D.precond_inverse_apply(m, x, a, trans=True)) for a in v])
     with ctx:
         ctx.set_option("kpm_registers", kpm)
+        ctx.set_option("kpm_queue", queue)
         vt = torch.tensor(v, device=DEV, dtype=torch.float32)
-        out = torch.empty_like(vt)
-        ctx.precond_apply(hg.HOL_PINV_PINVT, vt, out)
-        assert _rel(out.cpu().double().numpy(), ref) < 2e-5
+        for _ in range(2):
+            out = torch.full_like(vt, float("nan"))
+            ctx.precond_apply(hg.HOL_PINV_PINVT, vt, out)
+            assert _rel(out.cpu().double().numpy(), ref) < 2e-5
 
 
 def test_precond_transpose_identity_and_spd():
