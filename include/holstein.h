@@ -532,6 +532,20 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  *                       N Ltau on first use. Default 0: the two-kernel
  *                       iteration (operator, then update), measured as fast
  *                       at the benchmark size (0/1)
+ *   "scalar_handoff"    mixed CG (two-kernel iteration): bit 0 set, alpha is
+ *                       formed once per right-hand side by the last warp of
+ *                       the operator kernel to finish (layouts 0, 1, 2, 6) and
+ *                       read by the update kernel; bit 1 set (plain CG), beta
+ *                       is formed by the last block of the update kernel and
+ *                       read by the operator. Default 0: every block and warp
+ *                       forms them from the partial sums (measured faster:
+ *                       the last-block step lengthens the producer's tail).
+ *                       The values are the same either way (0..3)
+ *   "kpm_queue"         FP32 register KPM (kpm_registers 1 or 2): 0 one block
+ *                       per (omega, rhs) problem; k in 1..8 a persistent grid
+ *                       of k blocks per multiprocessor taking the problems
+ *                       from a queue, longest Chebyshev series first (used
+ *                       when there are more problems than blocks)
  *   "merged_cg"         with fused_cg 0: plain mixed CG as one kernel per
  *                       iteration with single-reduction Chronopoulos-Gear
  *                       recurrences (L % 8 == 0; allocates the same three

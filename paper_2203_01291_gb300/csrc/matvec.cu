@@ -819,7 +819,7 @@ __global__ void __launch_bounds__(128, 2) k_cg_fused(const float* __restrict__ r
         return fma4s(-a, *slot_ptr(sl, 1, k), *slot_ptr(sl, 0, k));
     };
 
-    double gacc = 0.0, pacc = 0.0, rqacc = 0.0, qqacc = 0.0;
+    F2 gacc{0.0f, 0.0f}, pacc{0.0f, 0.0f}, rqacc{0.0f, 0.0f}, qqacc{0.0f, 0.0f};   // see cb.cuh
     float4 W[RT], X[RT], P[RT], Y[RT];
     issue(1);
     cp_async_wait<1>();   // slice j = 0 (halo t0 - 1)
@@ -849,7 +849,7 @@ __global__ void __launch_bounds__(128, 2) k_cg_fused(const float* __restrict__ r
             W[k] = make_float4(fmaf(sg * d.x, Y[k].x, pv.x), fmaf(sg * d.y, Y[k].y, pv.y),
                                fmaf(sg * d.z, Y[k].z, pv.z), fmaf(sg * d.w, Y[k].w, pv.w));
         }
-        gacc += (double)gp;
+        gacc = f2_add(gacc, gp);
         c4_apply<L>(X, geo, th);
     }
     for (int s = 0; s < gm.K; ++s) {
@@ -895,9 +895,9 @@ __global__ void __launch_bounds__(128, 2) k_cg_fused(const float* __restrict__ r
             W[k] = X[k];
             X[k] = P[k];
         }
-        pacc += (double)pp;
-        rqacc += (double)rqp;
-        qqacc += (double)qqp;
+        pacc = f2_add(pacc, pp);
+        rqacc = f2_add(rqacc, rqp);
+        qqacc = f2_add(qqacc, qqp);
         if (s + 1 < gm.K) {   // r' of slice tp waits for its output in the next step
             float gp = 0.0f;
 #pragma unroll
@@ -906,7 +906,7 @@ __global__ void __launch_bounds__(128, 2) k_cg_fused(const float* __restrict__ r
                 *rbuf(k) = rv;
                 gp = fmaf(rv.x, rv.x, fmaf(rv.y, rv.y, fmaf(rv.z, rv.z, fmaf(rv.w, rv.w, gp))));
             }
-            gacc += (double)gp;
+            gacc = f2_add(gacc, gp);
         }
     }
     cp_async_wait<0>();
