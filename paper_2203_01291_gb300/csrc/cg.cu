@@ -77,6 +77,24 @@ __device__ __forceinline__ double block_sum(double v)
     return s;
 }
 
+// The operands of one float4 element of the update kernel (x, p, p_prev
+// only when the x update is folded in).
+template <typename R>
+struct Ops {
+    V4<R> r, q, x, p, pp;
+    __device__ __forceinline__ void load(const R* rr, const R* qq, const R* xx, const R* ppv,
+                                         const R* ppr, long o, int fold)
+    {
+        r.ld(rr + o);
+        q.ld(qq + o);
+        if (fold != 0) {
+            x.ld(xx + o);
+            p.ld(ppv + o);
+            if (fold == 2) pp.ld(ppr + o);
+        }
+    }
+};
+
 // Block sum of a compensated float pair, converted to FP64 once (thread 0).
 __device__ __forceinline__ double block_sum_f2(F2 v)
 {
@@ -103,7 +121,7 @@ __device__ __forceinline__ double block_sum_f2(F2 v)
 // alpha p), so x is read and written every other iteration; FOLD 1 is the
 // plain x += alpha p.
 template <typename R, int FOLD>
-__global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restrict__ r,
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2) k_cg_update(R* __restrict__ x, R* __restrict__ r,
                                                    const R* __restrict__ p,
                                                    const R* __restrict__ pprev,
                                                    const R* __restrict__ q, long n,
@@ -120,6 +138,12 @@ __global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restr
     const PdlTriggerAtExit pdl_at_exit;
     const int rhs = blockIdx.y;
     if (mask != nullptr && mask[rhs] == 0) return;
+    const long base = (long)rhs * n;
+    const long stride = (long)gridDim.x * blockDim.x;
+    // the first element's operands are loaded while alpha is formed
+    long k = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    Ops<R> cur;
+    if (4 * k < n) cur.load(r, q, x, p, pprev, base + 4 * k, FOLD);
     double alpha, alpha_prev = 0.0;
     if (alpha_in != nullptr) {
         // formed once per rhs by the operator's last warp (cg_alpha_epilogue)
@@ -145,42 +169,39 @@ __global__ void __launch_bounds__(256) k_cg_update(R* __restrict__ x, R* __restr
     R ap = R(0);
     if (FOLD == 2) ap = (R)alpha_prev;
     if (FOLD == 0 && blockIdx.x == 0 && threadIdx.x == 0) alpha_buf[rhs] = alpha;
-    const long base = (long)rhs * n;
-    const long stride = (long)gridDim.x * blockDim.x;
     // the partial of the new r.r: a compensated float pair in the FP32 path
     // (one FP64 conversion per block), FP64 in the FP64 path
     double acc = 0.0;
     F2 acc2{0.0f, 0.0f};
-    for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n; k += stride) {
+    // the next element's operands are loaded before the current one is
+    // computed (two in flight per thread)
+    while (4 * k < n) {
+        const long kn = k + stride;
+        Ops<R> nxt;
+        if (4 * kn < n) nxt.load(r, q, x, p, pprev, base + 4 * kn, FOLD);
         const long o = base + 4 * k;
-        V4<R> rv, qv;
-        rv.ld(r + o);
-        qv.ld(q + o);
         if (FOLD != 0) {
-            V4<R> xv, pv;
-            xv.ld(x + o);
-            pv.ld(p + o);
             if (FOLD == 2) {
-                V4<R> pp;
-                pp.ld(pprev + o);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) xv.v[j] = fma(ap, pp.v[j], xv.v[j]);
+                for (int j = 0; j < 4; ++j) cur.x.v[j] = fma(ap, cur.pp.v[j], cur.x.v[j]);
             }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) xv.v[j] = fma(a, pv.v[j], xv.v[j]);
-            xv.st(x + o);
+            for (int j = 0; j < 4; ++j) cur.x.v[j] = fma(a, cur.p.v[j], cur.x.v[j]);
+            cur.x.st(x + o);
         }
         R part = R(0);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            rv.v[j] = fma(-a, qv.v[j], rv.v[j]);
-            part = fma(rv.v[j], rv.v[j], part);
+            cur.r.v[j] = fma(-a, cur.q.v[j], cur.r.v[j]);
+            part = fma(cur.r.v[j], cur.r.v[j], part);
         }
-        rv.st(r + o);
+        cur.r.st(r + o);
         if constexpr (sizeof(R) == 4)
             acc2 = f2_add(acc2, (float)part);
         else
             acc += (double)part;
+        cur = nxt;
+        k = kn;
     }
     double s;
     if constexpr (sizeof(R) == 4)
@@ -493,10 +514,17 @@ struct EventPair {
 
 }  // namespace
 
-int elementwise_blocks(const hol_ctx* c)
+// Blocks per right-hand side of the element-wise CG kernels (256 threads
+// each): about four blocks per multiprocessor over all right-hand sides, so
+// the update kernel (its two iterations in flight take some 60 registers)
+// runs as one resident wave; at least one float4 per thread, at most
+// kRedStride blocks (the stride of the partial-sum banks).
+int elementwise_blocks(const hol_ctx* c, int n_rhs)
 {
     const long v4 = c->n / 4;
-    long nb = (v4 + 1023) / 1024;   // about four vec4 per thread
+    const long most = (v4 + 255) / 256;
+    long nb = (4L * c->sms + n_rhs - 1) / (n_rhs > 0 ? n_rhs : 1);
+    if (nb > most) nb = most;
     if (nb < 1) nb = 1;
     if (nb > kRedStride) nb = kRedStride;
     return (int)nb;
@@ -510,7 +538,7 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
     const bool pc = o->precond != 0;
     const int prec = mixed ? HOL_F32 : HOL_F64;
     const long n = c->n;
-    const int nb2 = elementwise_blocks(c);
+    const int nb2 = elementwise_blocks(c, n_rhs);
     const dim3 g2(nb2, n_rhs);
     const Banks B = banks_of(c);
     const int pstride = matvec_pstride(c);
@@ -820,7 +848,7 @@ static int cg_run_fused(hol_ctx* c, const double* b, double* v, int n_rhs, const
                         int* iters, double* resid, cudaStream_t s)
 {
     const long n = c->n;
-    const int nb2 = elementwise_blocks(c);
+    const int nb2 = elementwise_blocks(c, n_rhs);
     const dim3 g2(nb2, n_rhs);
     const Banks B = banks_of(c);
     const int pstride = matvec_pstride(c);
@@ -1010,7 +1038,7 @@ static int cg_run_merged(hol_ctx* c, const double* b, double* v, int n_rhs, cons
                          int* iters, double* resid, cudaStream_t s)
 {
     const long n = c->n;
-    const int nb2 = elementwise_blocks(c);
+    const int nb2 = elementwise_blocks(c, n_rhs);
     const dim3 g2(nb2, n_rhs);
     const Banks B = banks_of(c);
     const int pstride = matvec_pstride(c);
@@ -1396,7 +1424,7 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
     const bool mixed = (o->prec == HOL_F32);
     const bool pc = o->precond != 0;
     const long n = c->n;
-    const int nb2 = elementwise_blocks(c);
+    const int nb2 = elementwise_blocks(c, n_rhs);
     const dim3 g2(nb2, n_rhs);
     const Banks B = banks_of(c);
     const int pstride = matvec_pstride(c);

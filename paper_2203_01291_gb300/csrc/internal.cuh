@@ -455,7 +455,7 @@ int launch_force(hol_ctx* c, const double* v, const double* b, int n_pf, double*
 // out2[0] = S_B(x), out2[1] = (1/2) sum b . v over n_pf vectors (leapfrog.cu).
 int launch_action_terms(const hol_ctx* c, const double* x, const double* b, const double* v,
                         int n_pf, double* out2, cudaStream_t s);
-int elementwise_blocks(const hol_ctx* c);
+int elementwise_blocks(const hol_ctx* c, int n_rhs);
 
 // preconditioner (precond.cu). mode bit 0: P^{-T} part, bit 1: P^{-1} part
 // (both: P^{-1} P^{-T}). rdot/dot_part (nullable): partial sums of out . rdot
