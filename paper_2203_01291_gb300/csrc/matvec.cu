@@ -143,12 +143,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) of this GPU's
-// global memory into L2: a hint, no data moves to the SM.
-__device__ __forceinline__ void prefetch_l2(const void* gmem, unsigned bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
-}
 template <int NPEND>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory"); }
 
@@ -191,19 +185,6 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
         return t;
     };
     const int last = gm.K + 1;   // index of the last slice in the sequence
-    // the whole run (its slices of r, p_old and expV) is requested from DRAM
-    // into L2 at once, so that a cold launch streams at full bandwidth while
-    // the ring below works through the slices (in the CG loop the vectors
-    // are already in L2 and the hints cost a few instructions)
-    if (valid && geo.cx == 0 && geo.rc == 0) {
-        for (int j = 0; j <= last; ++j) {
-            const int t = seq(j);
-            const long o = base + (long)t * N;
-            prefetch_l2(r + o, N * sizeof(float));
-            if (pold != r) prefetch_l2(pold + o, N * sizeof(float));
-            if (j > 0) prefetch_l2(ev + (long)t * N, N * sizeof(float));
-        }
-    }
     // slice j goes to slot j % S; the copy of slice j + S - 1 is issued just
     // before slice j is waited for (its slot held slice j - 1, already read)
     auto issue = [&](int j) {
