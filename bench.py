@@ -838,7 +838,7 @@ def prior_field_leg(dev, n_rhs=16):
     return out
 
 
-def split_sweep_leg(dev, n_traj=4, dts=(0.01, 0.35)):
+def split_sweep_leg(dev, n_traj=4, dts=(0.01, 0.1, 0.2, 0.35)):
     """Acceptance against the number n_t of bosonic sub-steps (Sec. III B,
     time-step splitting): omega0=1, lambda = alpha^2/(omega0^2 W) = 0.25
     (W = 8 t, so alpha = sqrt(2)), beta=4 (Ltau=40), L=16, Fourier
@@ -847,9 +847,10 @@ def split_sweep_leg(dev, n_traj=4, dts=(0.01, 0.35)):
     from exp(-S_B) (a fresh one per trajectory). The paper's dt for this
     sweep is not stated: dt = 0.01 is its default; with the constant mass
     the fastest bosonic mode has frequency sqrt(omega0^2 + 4/dtau^2) ~ 20,
-    so the leapfrog sub-step dt/n_t is stable for dt/n_t < 0.1, and dt =
-    0.35 puts that edge between n_t = 3 and 4 where the paper sees it. The
-    acceptance estimate is the mean of min(1, exp(-dH))."""
+    so the leapfrog sub-step dt/n_t is stable for dt/n_t < 0.1: dt = 0.1
+    and 0.2 put that edge at n_t = 1 and 2, dt = 0.35 between n_t = 3 and 4
+    where the paper sees it. The acceptance estimate is the mean of
+    min(1, exp(-dH)); a trajectory whose solves fail counts as rejected."""
     import torch
     import paper_2203_01291_gb300 as hg
     w = hi.Workload("split16", L=16, Ltau=40, omega0=1.0, alpha=float(np.sqrt(2.0)), seed=511)

@@ -293,7 +293,10 @@ __global__ void __launch_bounds__(256) k_recast(const double* rt, R* r, long n,
     const int rhs = blockIdx.y;
     if (mask[rhs] == 0) return;
     const long base = (long)rhs * n;
+    // |b - M^T M v|^2 in FP64 (the certified true residual); the recast
+    // vector's r.r as a compensated float pair in the FP32 path
     double at = 0.0, ar = 0.0;
+    F2 ar2{0.0f, 0.0f};
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n;
          k += (long)gridDim.x * blockDim.x) {
         const long o = base + 4 * k;
@@ -308,12 +311,18 @@ __global__ void __launch_bounds__(256) k_recast(const double* rt, R* r, long n,
             part = fma(rv.v[j], rv.v[j], part);
         }
         if ((const void*)r != (const void*)rt) rv.st(r + o);
-        ar += (double)part;
+        if constexpr (sizeof(R) == 4)
+            ar2 = f2_add(ar2, (float)part);
+        else
+            ar += (double)part;
     }
     double s = block_sum(at);
     if (threadIdx.x == 0) tr_out[(long)rhs * kRedStride + blockIdx.x] = s;
     __syncthreads();
-    s = block_sum(ar);
+    if constexpr (sizeof(R) == 4)
+        s = block_sum_f2(ar2);
+    else
+        s = block_sum(ar);
     if (threadIdx.x == 0) rr_out[(long)rhs * kRedStride + blockIdx.x] = s;
 }
 
@@ -373,7 +382,10 @@ __global__ void __launch_bounds__(256) k_conj_dots(const R* __restrict__ z, cons
     const int rhs = blockIdx.y;
     if (mask[rhs] == 0) return;
     const long base = (long)rhs * n;
+    // a group of four in R; the sums as compensated float pairs in the FP32
+    // path, FP64 in the FP64 path
     double azq = 0.0, apq = 0.0;
+    F2 azq2{0.0f, 0.0f}, apq2{0.0f, 0.0f};
     for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; 4 * k < n;
          k += (long)gridDim.x * blockDim.x) {
         const long o = base + 4 * k;
@@ -381,19 +393,24 @@ __global__ void __launch_bounds__(256) k_conj_dots(const R* __restrict__ z, cons
         zv.ld(z + o);
         pv.ld(p + o);
         qv.ld(q + o);
-        R szq = R(0), spq = R(0);   // a group of four in R, the sum in FP64
+        R szq = R(0), spq = R(0);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             szq = fma(zv.v[j], qv.v[j], szq);
             spq = fma(pv.v[j], qv.v[j], spq);
         }
-        azq += (double)szq;
-        apq += (double)spq;
+        if constexpr (sizeof(R) == 4) {
+            azq2 = f2_add(azq2, (float)szq);
+            apq2 = f2_add(apq2, (float)spq);
+        } else {
+            azq += (double)szq;
+            apq += (double)spq;
+        }
     }
-    double t = block_sum(azq);
+    double t = sizeof(R) == 4 ? block_sum_f2(azq2) : block_sum(azq);
     if (threadIdx.x == 0) zq_out[(long)rhs * kRedStride + blockIdx.x] = t;
     __syncthreads();
-    t = block_sum(apq);
+    t = sizeof(R) == 4 ? block_sum_f2(apq2) : block_sum(apq);
     if (threadIdx.x == 0) pq_out[(long)rhs * kRedStride + blockIdx.x] = t;
 }
 
