@@ -555,12 +555,39 @@ def cold_operator_block(ctx, nr, flush, hbm, launches=20):
     ms = statistics.median(times)
     unit = nr * n * 8.0 + n * 4.0
     cg_bytes = nr * n * 16.0 + n * 4.0
+    # the floor of one event-bracketed launch of the same kernel: the fused
+    # M^T M on a 1-rhs L=8, Ltau=2 lattice (64 sites) after the same flush
+    tiny = hg.Context(L=8, Ltau=2, max_rhs=1)
+    try:
+        tiny.set_field(torch.zeros(2, 64, dtype=torch.float64, device="cuda"))
+        tv = torch.ones(1, 2, 64, dtype=torch.float32, device="cuda")
+        tq = torch.empty_like(tv)
+        for _ in range(3):
+            tiny.fermion_matvec(hg.HOL_OP_MTM, tv, tq)
+        floor = []
+        for _ in range(launches):
+            flush_l2(flush)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            tiny.fermion_matvec(hg.HOL_OP_MTM, tv, tq)
+            e1.record()
+            torch.cuda.synchronize()
+            floor.append(e0.elapsed_time(e1))
+    finally:
+        tiny.close()
+    floor_ms = statistics.median(floor)
+    ceiling = unit / ((floor_ms / 1e3 + unit / (hbm * 1e9))) / 1e9 / hbm
     return {"rhs": nr, "median_us": ms * 1e3, "min_us": min(times) * 1e3,
             "unit_bytes": unit, "achieved_gbs": unit / (ms / 1e3) / 1e9,
             "frac": unit / (ms / 1e3) / 1e9 / hbm,
             "cg_launch_bytes": cg_bytes,
+            "launch_floor_us": floor_ms * 1e3,
+            "frac_ceiling": ceiling,
             "note": "median of single launches after a 256 MB L2 flush; frac by the operator's "
-                    "algorithmic bytes (v in, q out, expV), of measured HBM"}
+                    "algorithmic bytes (v in, q out, expV), of measured HBM; launch_floor_us: "
+                    "the same kernel on 64 sites, timed the same way; frac_ceiling: the "
+                    "fraction a launch with that floor would reach moving the bytes at peak"}
 
 
 def precision_error_block(ctx, xd, Rd, nr):

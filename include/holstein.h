@@ -197,8 +197,9 @@ int force(hol_ctx* ctx, const double* v, const double* b, int n_pf,
  * along tau of Eq. (U_omega), each block (I - e^{-i phi_omega} Bbar)^{-1}
  * replaced by its Chebyshev series sum_{m<N_P} c_m T_m(A),
  * A = 2 (Bbar - bmin)/(bmax - bmin) - 1 (App. C, Eqs. (A_def), (Minv_KPM),
- * (alpha_recur)), N_P(omega) = max(1, floor((bmax-bmin)(1/phi_omega + 1)))
- * (Eq. (NP_heuristic) with a1 = a2 = 1), c_m by Chebyshev-Gauss quadrature
+ * (alpha_recur)), N_P(omega) = max(1, floor((bmax-bmin)(a1/phi_omega + a2)))
+ * (Eq. (NP_heuristic); a1 = a2 = 1 unless the launch options kpm_a1_percent /
+ * kpm_a2_percent say otherwise), c_m by Chebyshev-Gauss quadrature
  * with 2 N_P points (Eq. (Cheby-Gauss)); bmin, bmax are the norm bounds set by
  * hol_set_field. HOL_PINVT applies the exact transpose of that approximation,
  * U^dag diag(sum conj(c_m) T_m(A^T)) U. which: HOL_PINV, HOL_PINVT or
@@ -541,6 +542,12 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  *                       forms them from the partial sums (measured faster:
  *                       the last-block step lengthens the producer's tail).
  *                       The values are the same either way (0..3)
+ *   "kpm_a1_percent",   100 a1 and 100 a2 of the Chebyshev order N_P(omega) =
+ *   "kpm_a2_percent"    max(1, floor((bmax - bmin)(a1 / phi_omega + a2)))
+ *                       (Eq. (NP_heuristic)); the paper's a1 = a2 = 1 (100) by
+ *                       default; smaller values shorten the series (a cheaper,
+ *                       less exact P^{-1}). 1..400; takes effect at the next
+ *                       hol_set_field or installed Arnoldi bounds
  *   "kpm_queue"         FP32 register KPM (kpm_registers 1 or 2): 0 one block
  *                       per (omega, rhs) problem; k in 1..8 a persistent grid
  *                       of k blocks per multiprocessor taking the problems

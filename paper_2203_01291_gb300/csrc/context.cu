@@ -292,6 +292,8 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     c->merged = 0;
     c->fused = 0;
     c->pdl = 1;
+    c->kpm_a1 = 1.0;
+    c->kpm_a2 = 1.0;
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         free_ctx(c);
         return set_error(HOL_ECUDA, "hol_create: no CUDA device");
@@ -560,6 +562,13 @@ extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
         c->persist = value ? 1 : 0;
     } else if (is("pdl")) {
         c->pdl = value ? 1 : 0;
+    } else if (is("kpm_a1_percent") || is("kpm_a2_percent")) {
+        if (value < 1 || value > 400)
+            return set_error(HOL_EINVAL, "hol_set_option: %s must be in [1, 400]", name);
+        if (is("kpm_a1_percent"))
+            c->kpm_a1 = value / 100.0;
+        else
+            c->kpm_a2 = value / 100.0;
     } else if (is("kpm_queue")) {
         if (value < 0 || value > 8)
             return set_error(HOL_EINVAL, "hol_set_option: kpm_queue must be 0..8");
@@ -602,6 +611,8 @@ extern "C" int hol_get_option(const hol_ctx* c, const char* name, int* value)
     else if (is("pdl")) *value = c->pdl;
     else if (is("scalar_handoff")) *value = c->handoff;
     else if (is("kpm_queue")) *value = c->kpm_queue;
+    else if (is("kpm_a1_percent")) *value = (int)lround(c->kpm_a1 * 100.0);
+    else if (is("kpm_a2_percent")) *value = (int)lround(c->kpm_a2 * 100.0);
     else return set_error(HOL_EINVAL, "hol_get_option: unknown option '%s'", name);
     return HOL_OK;
 }

@@ -245,6 +245,7 @@ struct hol_ctx {
     int kpm_queue;       // launch option "kpm_queue": persistent register-KPM grid of this many
                          // blocks per multiprocessor (0: one block per problem)
     int* kpm_q;          // its work queue [2] (next problem, finished blocks; zero between launches)
+    double kpm_a1, kpm_a2;   // constants of the Chebyshev order heuristic (1, 1 by default)
 };
 
 namespace hol {

@@ -757,14 +757,14 @@ __global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
 // coefficient sums cost FMAs only (FP64 throughput is scarce on this part).
 __global__ void k_kpm_coeffs(const double* __restrict__ scal, int T, int max_np,
                              int* __restrict__ npv, double2* __restrict__ coef,
-                             int* __restrict__ clamped)
+                             int* __restrict__ clamped, double a1, double a2)
 {
     extern __shared__ double2 fq[];              // [2 max_np]
     const int w = blockIdx.x;
     const double bmin = scal[S_BMIN], bmax = scal[S_BMAX];
     const double db = bmax - bmin;
     const double phi = 2.0 * M_PI / T * (w + 0.5);
-    const double npd = floor(db * (1.0 / phi + 1.0));
+    const double npd = floor(db * (a1 / phi + a2));   // Eq. (NP_heuristic)
     const int np = npd < 1.0 ? 1 : (npd > (double)max_np ? max_np : (int)npd);
     if (threadIdx.x == 0) {
         npv[w] = np;
@@ -988,7 +988,7 @@ int kpm_setup(hol_ctx* c, cudaStream_t s)
     const size_t sm = 2 * (size_t)c->kpm.max_np * sizeof(double2);
     if (int rc = smem_raise((const void*)k_kpm_coeffs, sm)) return rc;
     k_kpm_coeffs<<<c->T / 2, 128, sm, s>>>(c->scal, c->T, c->kpm.max_np, c->kpm.np, c->kpm.coef,
-                                           c->kpm.np + c->T / 2);
+                                           c->kpm.np + c->T / 2, c->kpm_a1, c->kpm_a2);
     HOL_CHECK_LAUNCH("k_kpm_coeffs");
     return HOL_OK;
 }

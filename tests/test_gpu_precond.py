@@ -209,3 +209,27 @@ def test_precond_full_size_vs_oracle(name):
                 ctx.precond_apply(which, vt, out)
                 err = _rel(out.cpu().double().numpy(), ref)
                 assert err < tol, (name, which, dt, err)
+
+
+@pytest.mark.parametrize("a1,a2", [(50, 100), (150, 50), (25, 200)])
+def test_precond_order_constants_vs_oracle(a1, a2):
+    """The Chebyshev orders N_P(omega) = max(1, floor(db (a1/phi + a2))) of
+    Eq. (NP_heuristic) with other constants than the paper's a1 = a2 = 1
+    (launch options, in percent): P^{-1} P^{-T} against the oracle's KPM with
+    the same constants, FP64 and FP32."""
+    w, x, ctx = _setup(16, 40, seed=8, std=1.2)
+    m = D.model_of(w)
+    v = hi.gaussian_vectors(w, 2, seed=11)
+    ref = np.stack([D.precond_inverse_apply(
+        m, x, D.precond_inverse_apply(m, x, a, trans=True, a1=a1 / 100, a2=a2 / 100),
+        a1=a1 / 100, a2=a2 / 100) for a in v])
+    with ctx:
+        ctx.set_option("kpm_a1_percent", a1)
+        ctx.set_option("kpm_a2_percent", a2)
+        assert ctx.get_option("kpm_a1_percent") == a1
+        ctx.set_field(torch.tensor(x, device=DEV))       # the plan is formed here
+        for dt, tol in ((torch.float64, 1e-11), (torch.float32, 2e-5)):
+            vt = torch.tensor(v, device=DEV, dtype=dt)
+            out = torch.empty_like(vt)
+            ctx.precond_apply(hg.HOL_PINV_PINVT, vt, out)
+            assert _rel(out.cpu().double().numpy(), ref) < tol, dt
