@@ -377,7 +377,7 @@ def run_ours(a):
                 "mixed_over_fp64": (solves / (ms_total / 1e3)) / (nr / (ms64 / 1e3))}
 
     # the dominant kernel cold: one fused M^T M launch after an L2 flush
-    cold = cold_operator_block(ctx, nr, flush, hbm)
+    cold = cold_operator_block(ctx, xd, nr, flush, hbm)
 
     # precision of the mixed path against the FP64 path on the same inputs
     prec_err = None if a.no_fp64 else precision_error_block(ctx, xd, Rd, nr)
@@ -426,6 +426,12 @@ def run_ours(a):
             "norm_bounds": list(ctx.bounds()),
             "solves_per_s": nr / (msb / 1e3), "ms_per_step": msb,
             "mean_iters": float(np.mean(itsb))}
+        # shorter Chebyshev series (a1 < 1 in Eq. (NP_heuristic)), same inputs
+        ctx.set_field(xd)
+        bs = torch.empty_like(Rd)
+        ctx.fermion_matvec(hg.HOL_OP_MT, Rd, bs)
+        alt["pcg_short_series"] = short_series_rows(ctx, xd, bs, torch.empty_like(Rd))
+        apply_options(ctx, a.option)   # an explicit kpm_a1_percent stays in force
 
     # end to end through the public API: host (pinned) inputs -> device,
     # solve + force, solutions and force back to host, every step
@@ -519,21 +525,43 @@ def run_ours(a):
             "clocks": clk,
             "cpu_baseline": cpu,
         }
-        print(json.dumps(out))
+        print(json.dumps(strict_json(out)))
     ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
-def cold_operator_block(ctx, nr, flush, hbm, launches=20):
+def event_times(fn, flush, launches):
+    """Device times (ms) of `fn`, each call alone between two CUDA events on
+    the current stream, after an L2 flush (flush=None: no flush, warm)."""
+    import torch
+    times = []
+    for _ in range(launches):
+        if flush is not None:
+            flush_l2(flush)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times
+
+
+def cold_operator_block(ctx, xd, nr, flush, hbm, launches=20):
     """The fused FP32 M^T M (the CG operator kernel, here without the
     direction update) on nr right-hand sides, each launch timed alone with
     CUDA events after an L2 flush (cold). Two units of algorithmic bytes:
     the operator's own (v in, q out, expV: nr n 8 B + n 4 B, which is also
     the matvec unit of one M apply on nr rhs), and the bytes the CG
     iteration's launch moves (r and p_old in, p_new and q out: nr n 16 B +
-    n 4 B)."""
+    n 4 B). Beside it: the floor of such a measurement (the same kernel on
+    64 sites after the same flush, the same without the flush, and a
+    128-element torch kernel after the flush) and the same operator on 64
+    right-hand sides (launch shapes tuned for 64), where the floor weighs
+    four times less."""
     import torch
     import paper_2203_01291_gb300 as hg
     n = ctx.n
@@ -542,21 +570,12 @@ def cold_operator_block(ctx, nr, flush, hbm, launches=20):
     q = torch.empty_like(v)
     for _ in range(3):
         ctx.fermion_matvec(hg.HOL_OP_MTM, v, q)
-    times = []
-    for _ in range(launches):
-        flush_l2(flush)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        ctx.fermion_matvec(hg.HOL_OP_MTM, v, q)
-        e1.record()
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
+    times = event_times(lambda: ctx.fermion_matvec(hg.HOL_OP_MTM, v, q), flush, launches)
     ms = statistics.median(times)
     unit = nr * n * 8.0 + n * 4.0
     cg_bytes = nr * n * 16.0 + n * 4.0
     # the floor of one event-bracketed launch of the same kernel: the fused
-    # M^T M on a 1-rhs L=8, Ltau=2 lattice (64 sites) after the same flush
+    # M^T M on a 1-rhs L=8, Ltau=2 lattice (64 sites)
     tiny = hg.Context(L=8, Ltau=2, max_rhs=1)
     try:
         tiny.set_field(torch.zeros(2, 64, dtype=torch.float64, device="cuda"))
@@ -564,30 +583,57 @@ def cold_operator_block(ctx, nr, flush, hbm, launches=20):
         tq = torch.empty_like(tv)
         for _ in range(3):
             tiny.fermion_matvec(hg.HOL_OP_MTM, tv, tq)
-        floor = []
-        for _ in range(launches):
-            flush_l2(flush)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            tiny.fermion_matvec(hg.HOL_OP_MTM, tv, tq)
-            e1.record()
-            torch.cuda.synchronize()
-            floor.append(e0.elapsed_time(e1))
+        floor = event_times(lambda: tiny.fermion_matvec(hg.HOL_OP_MTM, tv, tq), flush, launches)
+        floor_warm = event_times(lambda: tiny.fermion_matvec(hg.HOL_OP_MTM, tv, tq), None,
+                                 launches)
     finally:
         tiny.close()
+    small = torch.zeros(128, dtype=torch.float32, device="cuda")
+    floor_torch = event_times(lambda: small.add_(1.0), flush, launches)
     floor_ms = statistics.median(floor)
-    ceiling = unit / ((floor_ms / 1e3 + unit / (hbm * 1e9))) / 1e9 / hbm
+
+    def ceiling(unit_bytes):
+        return unit_bytes / (floor_ms / 1e3 + unit_bytes / (hbm * 1e9)) / 1e9 / hbm
+
+    rhs64 = None
+    if nr < 64:
+        nr64 = 64
+        v64 = torch.tensor(hi.gaussian_vectors(WORKLOAD, nr64, seed=6), device="cuda",
+                           dtype=torch.float32)
+        q64 = torch.empty_like(v64)
+        with hg.Context.from_workload(WORKLOAD, max_rhs=nr64) as c64:
+            c64.set_field(xd)
+            tuned64 = c64.tune(nr64)
+            for _ in range(3):
+                c64.fermion_matvec(hg.HOL_OP_MTM, v64, q64)
+            t64 = event_times(lambda: c64.fermion_matvec(hg.HOL_OP_MTM, v64, q64), flush,
+                              launches)
+        ms64 = statistics.median(t64)
+        unit64 = nr64 * n * 8.0 + n * 4.0
+        rhs64 = {"rhs": nr64, "median_us": ms64 * 1e3, "unit_bytes": unit64,
+                 "achieved_gbs": unit64 / (ms64 / 1e3) / 1e9,
+                 "frac": unit64 / (ms64 / 1e3) / 1e9 / hbm, "frac_ceiling": ceiling(unit64),
+                 "tuned_launch": tuned64}
+        del v64, q64
     return {"rhs": nr, "median_us": ms * 1e3, "min_us": min(times) * 1e3,
             "unit_bytes": unit, "achieved_gbs": unit / (ms / 1e3) / 1e9,
             "frac": unit / (ms / 1e3) / 1e9 / hbm,
             "cg_launch_bytes": cg_bytes,
             "launch_floor_us": floor_ms * 1e3,
-            "frac_ceiling": ceiling,
+            "launch_floor_warm_us": statistics.median(floor_warm) * 1e3,
+            "torch_kernel_floor_us": statistics.median(floor_torch) * 1e3,
+            "frac_ceiling": ceiling(unit),
+            "rhs64": rhs64,
             "note": "median of single launches after a 256 MB L2 flush; frac by the operator's "
                     "algorithmic bytes (v in, q out, expV), of measured HBM; launch_floor_us: "
-                    "the same kernel on 64 sites, timed the same way; frac_ceiling: the "
-                    "fraction a launch with that floor would reach moving the bytes at peak"}
+                    "the same kernel on 64 sites, timed the same way; torch_kernel_floor_us: a "
+                    "128-element torch add after the same flush (the floor is the platform's, "
+                    "not the kernel's); launch_floor_warm_us: the 64-site kernel without the "
+                    "flush, where the GPU is idle when the first event is recorded and waits "
+                    "for the host's launch call (so it measures the host path; with the flush "
+                    "queued first the kernel is already queued when the event fires); "
+                    "frac_ceiling: the fraction a launch with that floor would reach moving "
+                    "the bytes at peak"}
 
 
 def precision_error_block(ctx, xd, Rd, nr):
@@ -860,9 +906,45 @@ def prior_field_leg(dev, n_rhs=16):
             ms = e0.elapsed_time(e1)
             out["pcg" if pc else "cg"] = {"solves_per_s": n_rhs / (ms / 1e3), "ms": ms,
                                           "mean_iters": float(np.mean(its))}
+        out["pcg_short_series"] = short_series_rows(ctx, xd, b, v)
     out["iteration_ratio"] = out["cg"]["mean_iters"] / out["pcg"]["mean_iters"]
     out["speedup"] = out["pcg"]["solves_per_s"] / out["cg"]["solves_per_s"]
     return out
+
+
+def short_series_rows(ctx, x, b, v, a1_percents=(50, 25)):
+    """The preconditioned solve with the first Chebyshev order constant of
+    Eq. (NP_heuristic) below the paper's a1 = 1 (a2 = 1 kept): a shorter
+    series is a cheaper P^-1 and, on these fields, also the better
+    preconditioner. The constants take effect at the next set_field (which
+    recomputes the Chebyshev plan for x). Each row: one warm solve, then one
+    timed; the context's a1 is put back to 1 afterwards."""
+    import torch
+    import paper_2203_01291_gb300 as hg
+    rows = {}
+    n_rhs = b.shape[0]
+    try:
+        for a1 in a1_percents:
+            ctx.set_option("kpm_a1_percent", a1)
+            ctx.set_field(x)
+            ctx.cg_solve(b, v, tol=TOL, prec=hg.HOL_F32, reliable_every=RELIABLE_EVERY,
+                         max_iter=50000, precond=True)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            its, res = ctx.cg_solve(b, v, tol=TOL, prec=hg.HOL_F32,
+                                    reliable_every=RELIABLE_EVERY, max_iter=50000, precond=True)
+            e1.record()
+            torch.cuda.synchronize()
+            assert np.all(res < TOL)
+            ms = e0.elapsed_time(e1)
+            rows[f"a1={a1 / 100:g}"] = {"solves_per_s": n_rhs / (ms / 1e3), "ms": ms,
+                                        "mean_iters": float(np.mean(its))}
+    finally:
+        ctx.set_option("kpm_a1_percent", 100)
+        ctx.set_field(x)
+    return rows
 
 
 def split_sweep_leg(dev, n_traj=4, dts=(0.01, 0.1, 0.2, 0.35)):
@@ -906,8 +988,12 @@ def split_sweep_leg(dev, n_traj=4, dts=(0.01, 0.1, 0.2, 0.35)):
                         dh = float("inf")
                     dhs.append(dh)
                     pacc.append(float(min(1.0, np.exp(-dh))) if np.isfinite(dh) else 0.0)
+                med = float(np.median(np.abs(dhs)))
+                # failed trajectories count as dH = infinity; strict JSON has
+                # no infinity, so an infinite median is reported as null
                 rows.append({"n_t": n_t, "acceptance": float(np.mean(pacc)),
-                             "median_abs_dH": float(np.median(np.abs(dhs)))})
+                             "median_abs_dH": med if np.isfinite(med) else None,
+                             "failed": int(sum(not np.isfinite(d) for d in dhs))})
             res[f"dt={dt:g}"] = rows
     res["seconds"] = time.perf_counter() - t0
     return res
@@ -958,7 +1044,9 @@ def kernel_source_digest(kernel):
     import hashlib
     import re
     name = kernel.split("<")[0]
-    pat = re.compile(r"__global__ void(?: __launch_bounds__\([^)]*\))? " + re.escape(name) + r"\(")
+    # (launch bounds may hold one level of parentheses: sizeof(R) == 4 ? 4 : 2)
+    pat = re.compile(r"__global__ void(?: __launch_bounds__\((?:[^()]|\([^()]*\))*\))? "
+                     + re.escape(name) + r"\(")
     csrc = os.path.join(ROOT, "paper_2203_01291_gb300", "csrc")
     h = hashlib.sha256()
     for hname in KERNEL_HEADERS:
@@ -1004,6 +1092,18 @@ def traffic_from_profiles(kernel, alg_bytes):
             traffic, prof_alg = float(parts[3]), float(parts[4])
             return traffic * (alg_bytes / prof_alg) if alg_bytes else traffic
     return None
+
+
+def strict_json(obj):
+    """A copy of obj with every non-finite float replaced by None: the line
+    must parse as strict JSON, which has no NaN or infinity."""
+    if isinstance(obj, float):
+        return obj if np.isfinite(obj) else None
+    if isinstance(obj, dict):
+        return {k: strict_json(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [strict_json(v) for v in obj]
+    return obj
 
 
 def flush_l2(buf):
@@ -1096,7 +1196,7 @@ def run_precond(a):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         res[name + "_median_ms"] = statistics.median(times)
-    print(json.dumps(res))
+    print(json.dumps(strict_json(res)))
     ctx.close()
 
 
@@ -1131,7 +1231,7 @@ def run_reference(a):
                                       f"{float(np.mean(its)):.0f} iterations"},
            "e2e": {"value": value, "unit": "CG solves/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(out))
+    print(json.dumps(strict_json(out)))
 
 
 def run_leg(a):
@@ -1148,7 +1248,7 @@ def run_leg(a):
             "chains": lambda: chains_leg("cuda", repeats=1),
             "prior": lambda: prior_field_leg("cuda"),
             "split": lambda: split_sweep_leg("cuda")}
-    print(json.dumps({"mode": "leg", "leg": a.leg, **legs[a.leg]()}))
+    print(json.dumps(strict_json({"mode": "leg", "leg": a.leg, **legs[a.leg]()})))
 
 
 def main():

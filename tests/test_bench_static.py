@@ -53,6 +53,23 @@ def test_traffic_line_is_ignored_once_the_kernel_sources_change(tmp_path, monkey
     assert b.traffic_from_profiles("k_cg_mtm32_v4a<32,2>", 4000) is None
 
 
+def test_every_profiled_kernel_has_a_source_digest():
+    """Each kernel named on a committed traffic line is found in csrc/
+    (including kernels whose launch bounds hold parentheses), so a stale
+    line is detected instead of silently matching nothing."""
+    import glob
+    b = _bench()
+    names = set()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(path):
+            if line.startswith("traffic_per_launch:"):
+                names.add(line.split()[1])
+    assert names
+    for k in sorted(names):
+        assert b.kernel_source_digest(k) is not None, k
+    assert b.kernel_source_digest("k_cg_update<float,0>") is not None
+
+
 def test_single_rank_job_rate_and_replica_inputs():
     """At N = 1 the job rate is units over the rank's time; each rank draws
     its own seeded inputs (replicas, no shared data)."""
@@ -65,3 +82,14 @@ def test_single_rank_job_rate_and_replica_inputs():
     xa, ra = b.replica_inputs(w, 2, 0)
     assert (x0 == xa).all() and (r0 == ra).all()
     assert not (x0 == x1).all() and not (r0 == r1).all()
+
+
+def test_bench_line_is_strict_json():
+    """Non-finite numbers (a failed trajectory's dH) become null, so the
+    printed line parses as strict JSON."""
+    import json
+    b = _bench()
+    obj = {"a": float("inf"), "b": [1.5, float("nan"), {"c": -float("inf")}], "d": 2, "e": "x"}
+    out = b.strict_json(obj)
+    assert out == {"a": None, "b": [1.5, None, {"c": None}], "d": 2, "e": "x"}
+    json.loads(json.dumps(out, allow_nan=False))
