@@ -506,9 +506,12 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  *   "slices_per_group"  tau slices streamed per lane group (divides Ltau)
  *   "warps_per_block"   1, 2 or 4 for the operator kernels
  *   "layout"            0 scalar, 1 float4, 2 float4 with a two-slice cp.async
- *                       ring, 6 the same with a three-slice ring, 3 streaming
- *                       float4 with a cp.async ring across units (1-3 and 6
- *                       need L % 8 == 0), 4 / 5 split float4 with each slice
+ *                       ring, 6 the same with a three-slice ring (2 and 6
+ *                       need L % 4 == 0, L >= 8; for L % 8 == 4 the row
+ *                       chunks of a lane alternate L/4 + 1 and L/4 - 1
+ *                       rows), 3 streaming float4 with a cp.async ring
+ *                       across units (1 and 3 need L % 8 == 0), 4 / 5 split
+ *                       float4 with each slice
  *                       spread over 2 / 4 warps (L == 32), 7 float4 with one
  *                       slice per warp and slices_per_group (<= 8) warps per
  *                       block exchanging the tau neighbours in shared memory

@@ -1,9 +1,16 @@
-// Vectorised register layout of one tau slice for L divisible by 8.
+// Vectorised register layout of one tau slice for L divisible by 4 (L >= 8).
 //
 // A group of L lanes holds the slice: lane (cx, rc) of the group holds the
-// four columns 4cx..4cx+3 (one float4) of the L/4 rows rc*L/4 ..
-// rc*L/4 + L/4 - 1 (cx < L/4, rc < 4). Every global access is a float4 of a
-// row, so a slice costs L/4 vector loads per lane instead of L scalar ones.
+// four columns 4cx..4cx+3 (one float4) of a chunk of consecutive rows
+// (cx < L/4, rc < 4). Every global access is a float4 of a row, so a slice
+// costs about L/4 vector loads per lane instead of L scalar ones.
+// Chunks: for L % 8 == 0 chunk rc holds the L/4 rows rc*L/4 .. rc*L/4 + L/4 - 1.
+// For L % 8 == 4 (L/4 odd) an equal split would start every other chunk on an
+// odd row; there the chunks alternate L/4 + 1 and L/4 - 1 rows (12: 4,2,4,2;
+// 20: 6,4,6,4; 28: 8,6,8,6), so every chunk starts on an even row and holds an
+// even number of rows. A lane keeps RT = L/4 + 1 register rows; a short chunk
+// leaves its last two unused (never loaded or stored, and no lattice row
+// ever reads them).
 // Checkerboard colours (C = C4 C3 C2 C1):
 //   colour 1, x-bonds (even ix, ix+1): inside the float4;
 //   colour 2, x-bonds (odd ix, ix+1):  (.y,.z) inside, (.w, right.x) and
@@ -19,11 +26,14 @@ namespace hol {
 
 template <int L>
 struct Geom4 {
-    static_assert(L % 8 == 0, "vector layout needs L divisible by 8");
-    static constexpr int LR = L / 4;   // lanes per row segment
-    static constexpr int RT = L / 4;   // rows per lane
-    static constexpr int G = 32 / L;   // slices per warp
+    static_assert(L % 4 == 0 && L >= 8 && L <= 32, "vector layout needs L % 4 == 0, 8 <= L <= 32");
+    static constexpr int LR = L / 4;                  // lanes per row segment
+    static constexpr bool kUneven = (L / 4) % 2 == 1;   // chunks of L/4 +- 1 rows
+    static constexpr int RT = L / 4 + (kUneven ? 1 : 0);   // register rows per lane
+    static constexpr int G = 32 / L;                  // slices per warp
     int g, cx, rc, left, right, down, up;
+    int row0;      // first lattice row of this lane's chunk
+    bool shortc;   // the chunk holds RT - 2 rows (L % 8 == 4, odd rc)
     bool ok;
     __device__ __forceinline__ Geom4()
     {
@@ -42,9 +52,22 @@ struct Geom4 {
         left = b + rc * LR + (cx == 0 ? LR - 1 : cx - 1);
         down = b + ((rc + 1) & 3) * LR + cx;
         up = b + ((rc + 3) & 3) * LR + cx;
+        if constexpr (kUneven) {
+            row0 = (rc >> 1) * (L / 2) + (rc & 1) * (L / 4 + 1);
+            shortc = (rc & 1) != 0;
+        } else {
+            row0 = rc * RT;
+            shortc = false;
+        }
     }
-    // float offset of row k of this lane inside a slice
-    __device__ __forceinline__ int off(int k) const { return (rc * RT + k) * L + 4 * cx; }
+    // float offset of register row k of this lane inside a slice
+    __device__ __forceinline__ int off(int k) const { return (row0 + k) * L + 4 * cx; }
+    // register row k holds a lattice row (always, unless L % 8 == 4)
+    __device__ __forceinline__ bool has(int k) const
+    {
+        if constexpr (kUneven) return k < RT - 2 || !shortc;
+        return true;
+    }
 };
 
 // bond [[1, th], [th, 1]] (cosh folded into the diagonal, see cb.cuh)
@@ -66,20 +89,20 @@ __device__ __forceinline__ float4 shfl4(const float4& v, int src)
 }
 
 template <int L>
-__device__ __forceinline__ void c4_colour1(float4 (&c)[L / 4], float th)
+__device__ __forceinline__ void c4_colour1(float4 (&c)[Geom4<L>::RT], float th)
 {
 #pragma unroll
-    for (int k = 0; k < L / 4; ++k) {
+    for (int k = 0; k < Geom4<L>::RT; ++k) {
         bond(c[k].x, c[k].y, th);
         bond(c[k].z, c[k].w, th);
     }
 }
 
 template <int L>
-__device__ __forceinline__ void c4_colour2(float4 (&c)[L / 4], const Geom4<L>& g, float th)
+__device__ __forceinline__ void c4_colour2(float4 (&c)[Geom4<L>::RT], const Geom4<L>& g, float th)
 {
 #pragma unroll
-    for (int k = 0; k < L / 4; ++k) {
+    for (int k = 0; k < Geom4<L>::RT; ++k) {
         const float rx = __shfl_sync(kFull, c[k].x, g.right);
         const float lw = __shfl_sync(kFull, c[k].w, g.left);
         bond(c[k].y, c[k].z, th);
@@ -89,10 +112,10 @@ __device__ __forceinline__ void c4_colour2(float4 (&c)[L / 4], const Geom4<L>& g
 }
 
 template <int L>
-__device__ __forceinline__ void c4_colour3(float4 (&c)[L / 4], float th)
+__device__ __forceinline__ void c4_colour3(float4 (&c)[Geom4<L>::RT], float th)
 {
 #pragma unroll
-    for (int k = 0; k < L / 4; k += 2) {
+    for (int k = 0; k < Geom4<L>::RT; k += 2) {
         bond(c[k].x, c[k + 1].x, th);
         bond(c[k].y, c[k + 1].y, th);
         bond(c[k].z, c[k + 1].z, th);
@@ -100,32 +123,61 @@ __device__ __forceinline__ void c4_colour3(float4 (&c)[L / 4], float th)
     }
 }
 
-template <int L>
-__device__ __forceinline__ void c4_colour4(float4 (&c)[L / 4], const Geom4<L>& g, float th)
+__device__ __forceinline__ void fma4_into(float4& a, float th, const float4& b)
 {
-    constexpr int RT = L / 4;
-    const float4 dn = shfl4(c[0], g.down);        // partner of my last row
-    const float4 upv = shfl4(c[RT - 1], g.up);    // partner of my first row
+    a.x = fmaf(th, b.x, a.x);
+    a.y = fmaf(th, b.y, a.y);
+    a.z = fmaf(th, b.z, a.z);
+    a.w = fmaf(th, b.w, a.w);
+}
+
+__device__ __forceinline__ float4 sel4(bool p, const float4& a, const float4& b)
+{
+    return make_float4(p ? a.x : b.x, p ? a.y : b.y, p ? a.z : b.z, p ? a.w : b.w);
+}
+
+template <int L>
+__device__ __forceinline__ void c4_colour4(float4 (&c)[Geom4<L>::RT], const Geom4<L>& g, float th)
+{
+    constexpr int RT = Geom4<L>::RT;
+    if constexpr (!Geom4<L>::kUneven) {
+        const float4 dn = shfl4(c[0], g.down);        // partner of my last row
+        const float4 upv = shfl4(c[RT - 1], g.up);    // partner of my first row
 #pragma unroll
-    for (int k = 1; k + 1 < RT; k += 2) {
-        bond(c[k].x, c[k + 1].x, th);
-        bond(c[k].y, c[k + 1].y, th);
-        bond(c[k].z, c[k + 1].z, th);
-        bond(c[k].w, c[k + 1].w, th);
+        for (int k = 1; k + 1 < RT; k += 2) {
+            bond(c[k].x, c[k + 1].x, th);
+            bond(c[k].y, c[k + 1].y, th);
+            bond(c[k].z, c[k + 1].z, th);
+            bond(c[k].w, c[k + 1].w, th);
+        }
+        fma4_into(c[RT - 1], th, dn);
+        fma4_into(c[0], th, upv);
+    } else {
+        // a long chunk's last row is register RT - 1, a short one's RT - 3;
+        // the pairs below RT - 3 are interior in both
+        const float4 dn = shfl4(c[0], g.down);
+        const float4 upv = shfl4(sel4(g.shortc, c[RT - 3], c[RT - 1]), g.up);
+#pragma unroll
+        for (int k = 1; k + 1 < RT - 3; k += 2) {
+            bond(c[k].x, c[k + 1].x, th);
+            bond(c[k].y, c[k + 1].y, th);
+            bond(c[k].z, c[k + 1].z, th);
+            bond(c[k].w, c[k + 1].w, th);
+        }
+        // rows RT - 3 and RT - 2: a bond in a long chunk; in a short one
+        // RT - 3 is the last row and pairs with the next chunk instead
+        // (register RT - 2 is unused there)
+        const float4 a = c[RT - 3];
+        fma4_into(c[RT - 3], th, sel4(g.shortc, dn, c[RT - 2]));
+        fma4_into(c[RT - 2], th, a);
+        fma4_into(c[RT - 1], th, dn);   // (unused register in a short chunk)
+        fma4_into(c[0], th, upv);
     }
-    c[RT - 1].x = fmaf(th, dn.x, c[RT - 1].x);
-    c[RT - 1].y = fmaf(th, dn.y, c[RT - 1].y);
-    c[RT - 1].z = fmaf(th, dn.z, c[RT - 1].z);
-    c[RT - 1].w = fmaf(th, dn.w, c[RT - 1].w);
-    c[0].x = fmaf(th, upv.x, c[0].x);
-    c[0].y = fmaf(th, upv.y, c[0].y);
-    c[0].z = fmaf(th, upv.z, c[0].z);
-    c[0].w = fmaf(th, upv.w, c[0].w);
 }
 
 // c <- C c (colour 1 first)
 template <int L>
-__device__ __forceinline__ void c4_apply(float4 (&c)[L / 4], const Geom4<L>& g, float th)
+__device__ __forceinline__ void c4_apply(float4 (&c)[Geom4<L>::RT], const Geom4<L>& g, float th)
 {
     c4_colour1<L>(c, th);
     c4_colour2<L>(c, g, th);
@@ -135,7 +187,7 @@ __device__ __forceinline__ void c4_apply(float4 (&c)[L / 4], const Geom4<L>& g, 
 
 // c <- C^T c (colour 4 first)
 template <int L>
-__device__ __forceinline__ void c4_apply_t(float4 (&c)[L / 4], const Geom4<L>& g, float th)
+__device__ __forceinline__ void c4_apply_t(float4 (&c)[Geom4<L>::RT], const Geom4<L>& g, float th)
 {
     c4_colour4<L>(c, g, th);
     c4_colour3<L>(c, th);

@@ -545,10 +545,12 @@ extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
     } else if (is("layout")) {
         if (value != 0 && c->exact)
             return set_error(HOL_EINVAL, "hol_set_option: the exact propagator runs in layout 0");
-        if (value < 0 || value > 7 || (value > 0 && c->L % 8) ||
+        const bool ring = value == 2 || value == 6;   // float4 with a cp.async ring
+        if (value < 0 || value > 7 || (ring && (c->L % 4 || c->L < 8)) ||
+            (value > 0 && !ring && c->L % 8) ||
             ((value == 4 || value == 5 || value == 7) && c->L != 32))
-            return set_error(HOL_EINVAL, "hol_set_option: layout 0..7 (1-3, 6 need L %% 8 == 0, "
-                                         "4, 5, 7 L == 32)");
+            return set_error(HOL_EINVAL, "hol_set_option: layout 0..7 (2, 6 need L %% 4 == 0 "
+                                         "and L >= 8; 1, 3 L %% 8 == 0; 4, 5, 7 L == 32)");
         c->mv_vec = value;
     } else if (is("kpm_registers")) {
         if (value && c->exact)

@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
     pdl_wait();      // inputs may come from the previous kernel of the stream
     const PdlTriggerAtExit pdl_at_exit;
     constexpr int N = L * L;
-    constexpr int RT = L / 4;
+    constexpr int RT = Geom4<L>::RT;   // L/4 rows, L/4 + 1 for L % 8 == 4 (see cb4.cuh)
     extern __shared__ __align__(16) float4 ring[];   // [warp][slot][array: r, p_old, expV][RT][32]
     const Geom4<L> geo;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
             const long o = base + (long)t * N;
 #pragma unroll
             for (int k = 0; k < RT; ++k) {
+                if (!geo.has(k)) continue;   // unused register row (short chunk)
                 cp_async16(slot_ptr(j % S, 0, k), r + o + geo.off(k));
                 cp_async16(slot_ptr(j % S, 1, k), pold + o + geo.off(k));
                 if (j > 0) cp_async16(slot_ptr(j % S, 2, k), ev + (long)t * N + geo.off(k));
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
 #pragma unroll
         for (int k = 0; k < RT; ++k) {
             const float4 pv = fma4s(bt, *slot_ptr(1 % S, 1, k), *slot_ptr(1 % S, 0, k));
-            if (valid && pnew != nullptr) st4(pnew, o + geo.off(k), pv);
+            if (valid && pnew != nullptr && geo.has(k)) st4(pnew, o + geo.off(k), pv);
             X[k] = pv;
             const float4 d = *slot_ptr(1 % S, 2, k);
             W[k] = make_float4(fmaf(sg * d.x, Y[k].x, pv.x), fmaf(sg * d.y, Y[k].y, pv.y),
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
 #pragma unroll
         for (int k = 0; k < RT; ++k) {
             const float4 pv = fma4s(bt, *slot_ptr(j % S, 1, k), *slot_ptr(j % S, 0, k));
-            if (own) st4(pnew, op + geo.off(k), pv);
+            if (own && geo.has(k)) st4(pnew, op + geo.off(k), pv);
             P[k] = pv;
             float4 d = *slot_ptr(j % S, 2, k);
             d.x *= sgp; d.y *= sgp; d.z *= sgp; d.w *= sgp;
@@ -254,13 +255,15 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4a(const float* __restrict
         float part = 0.0f;
 #pragma unroll
         for (int k = 0; k < RT; ++k) {
-            if (valid)
+            if (valid && geo.has(k))
                 st4(q, o + geo.off(k), make_float4(W[k].x + Y[k].x, W[k].y + Y[k].y,
                                                    W[k].z + Y[k].z, W[k].w + Y[k].w));
-            part = fmaf(W[k].x, W[k].x, part);
-            part = fmaf(W[k].y, W[k].y, part);
-            part = fmaf(W[k].z, W[k].z, part);
-            part = fmaf(W[k].w, W[k].w, part);
+            if (geo.has(k)) {
+                part = fmaf(W[k].x, W[k].x, part);
+                part = fmaf(W[k].y, W[k].y, part);
+                part = fmaf(W[k].z, W[k].z, part);
+                part = fmaf(W[k].w, W[k].w, part);
+            }
             W[k] = X[k];
             X[k] = P[k];
         }
@@ -1142,6 +1145,36 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
             return HOL_OK;
         }
     }
+    if constexpr (L % 4 == 0 && L >= 8) {   // float4 layout with a cp.async ring (cb4.cuh)
+        if (c->mv_vec == 2 || c->mv_vec == 6) {   // cp.async ring of 2 or 3 slices
+            const bool deep = c->mv_vec == 6;
+            const size_t sm =
+                (size_t)c->mv_warps * (deep ? 3 : 2) * 3 * Geom4<L>::RT * 32 * sizeof(float4);
+            // raised once per instantiation to the largest size any block shape needs
+            // (the static reduction scratch counts against the default limit)
+            static std::atomic<int> limit(0);
+            if ((int)sm > limit.load()) {
+                const int most2 = 4 * 2 * 3 * Geom4<L>::RT * 32 * (int)sizeof(float4);
+                const int most3 = 4 * 3 * 3 * Geom4<L>::RT * 32 * (int)sizeof(float4);
+                HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_mtm32_v4a<L, 2>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, most2));
+                HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_mtm32_v4a<L, 3>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, most3));
+                limit.store(most3);
+            }
+            if (deep)
+                HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4a<L, 3>, nb, nt, sm, s, r, pold, pnew, q,
+                                    c->ev32, ga, mask, rr_new, rr_old, rr_stride, rr_n, first,
+                                    pq_part, (float)c->th));
+            else
+                HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4a<L, 2>, nb, nt, sm, s, r, pold, pnew, q,
+                                    c->ev32, ga, mask, rr_new, rr_old, rr_stride, rr_n, first,
+                                    pq_part, (float)c->th));
+            HOL_CHECK_LAUNCH("k_cg_mtm32_v4a");
+            mark();
+            return HOL_OK;
+        }
+    }
     if constexpr (L % 8 == 0) {
         if (c->mv_vec == 3) {
             constexpr int S = 3;
@@ -1167,33 +1200,6 @@ int run_cg_mtm32(const hol_ctx* c, const float* r, const float* pold, float* pne
                                 pnew, q, c->ev32, g, mask, rr_new, rr_old, rr_stride, rr_n, first,
                                 pq_part, (float)c->th, blocks * wpb));
             HOL_CHECK_LAUNCH("k_cg_mtm32_v4s");
-            return HOL_OK;
-        }
-        if (c->mv_vec == 2 || c->mv_vec == 6) {   // cp.async ring of 2 or 3 slices
-            const bool deep = c->mv_vec == 6;
-            const size_t sm = (size_t)c->mv_warps * (deep ? 3 : 2) * 3 * (L / 4) * 32 * sizeof(float4);
-            // raised once per instantiation to the largest size any block shape needs
-            // (the static reduction scratch counts against the default limit)
-            static std::atomic<int> limit(0);
-            if ((int)sm > limit.load()) {
-                const int most2 = 4 * 2 * 3 * (L / 4) * 32 * (int)sizeof(float4);
-                const int most3 = 4 * 3 * 3 * (L / 4) * 32 * (int)sizeof(float4);
-                HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_mtm32_v4a<L, 2>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, most2));
-                HOL_CUDA(cudaFuncSetAttribute((const void*)k_cg_mtm32_v4a<L, 3>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, most3));
-                limit.store(most3);
-            }
-            if (deep)
-                HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4a<L, 3>, nb, nt, sm, s, r, pold, pnew, q,
-                                    c->ev32, ga, mask, rr_new, rr_old, rr_stride, rr_n, first,
-                                    pq_part, (float)c->th));
-            else
-                HOL_CUDA(launch_pdl(c, k_cg_mtm32_v4a<L, 2>, nb, nt, sm, s, r, pold, pnew, q,
-                                    c->ev32, ga, mask, rr_new, rr_old, rr_stride, rr_n, first,
-                                    pq_part, (float)c->th));
-            HOL_CHECK_LAUNCH("k_cg_mtm32_v4a");
-            mark();
             return HOL_OK;
         }
         if (c->mv_vec) {

@@ -7,7 +7,8 @@
 // the float4 layout with a cp.async ring of three slices (6), the streaming
 // float4 kernel with a cp.async ring across units (3), the float4 layout
 // with a two-slice cp.async ring (2), without (1), or the scalar register
-// layout (0). The split and streaming kernels fix their own block shapes, so
+// layout (0); for L % 8 == 4 (uneven row chunks, cb4.cuh) the two ring
+// kernels (6, 2) or the scalar layout. The split and streaming kernels fix their own block shapes, so
 // they are timed once per K. With the fused or merged CG on, that iteration
 // kernel is timed instead, over K and warps (its layout is fixed). Each
 // candidate is timed with CUDA events on the caller's stream (2 warm-up and
@@ -94,6 +95,9 @@ extern "C" int hol_tune(hol_ctx* c, int n_rhs, int* best_k, int* best_warps, int
             vecs[nvec++] = 3;
             vecs[nvec++] = 2;
             vecs[nvec++] = 1;
+        } else if (c->L % 4 == 0 && c->L >= 8 && !c->exact) {   // L % 8 == 4: the ring kernels
+            vecs[nvec++] = 6;
+            vecs[nvec++] = 2;
         }
         vecs[nvec++] = 0;
     }

@@ -259,6 +259,68 @@ def test_fused_mtm_every_layout(layout, L, T, K):
     assert max(MF.rel_residual(w, x, v[k], s[k]) for k in range(nr)) < 1.01e-8
 
 
+UNEVEN_CASES = [(12, 20, 2), (12, 8, 8), (20, 10, 5), (28, 24, 4), (28, 30, 3)]
+
+
+@pytest.mark.parametrize("layout", [2, 6])
+@pytest.mark.parametrize("L,T,K", UNEVEN_CASES)
+def test_fused_mtm_uneven_row_chunks(layout, L, T, K):
+    """L % 8 == 4: the float4 ring kernels hold row chunks of L/4 + 1 and
+    L/4 - 1 rows (the y-bond at each chunk edge crosses lanes, the two unused
+    registers of a short chunk are never loaded, stored or summed). The fused
+    M^T M matches the oracle on right-hand sides of very different scale, and
+    the masked mixed solve through the same kernel is certified."""
+    w, x = _field(L, T, seed=24)
+    nr = 5
+    v = hi.gaussian_vectors(w, nr, seed=25) * np.array([1.0, 1e-3, 1e3, 1.0, 1e-6])[:, None, None]
+    ref = np.stack([MF.MTM_apply(w, x, a) for a in v])
+    with _ctx(w, nr) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        ctx.set_option("slices_per_group", K)
+        ctx.set_option("layout", layout)
+        vt = torch.tensor(v, device=DEV, dtype=torch.float32)
+        out = torch.full_like(vt, float("nan"))
+        ctx.fermion_matvec(hg.HOL_OP_MTM, vt, out)
+        got = out.cpu().double().numpy()
+        for k in range(nr):
+            assert _rel(got[k], ref[k]) < 3e-6
+        bt = torch.tensor(v, device=DEV)
+        sol = torch.empty_like(bt)
+        its, res = ctx.cg_solve(bt, sol, tol=1e-8, prec=hg.HOL_F32, reliable_every=30)
+        s = sol.cpu().numpy()
+    assert np.all(res < 1e-8)
+    assert max(MF.rel_residual(w, x, v[k], s[k]) for k in range(nr)) < 1.01e-8
+
+
+def test_uneven_row_chunks_full_size_and_layout_limits():
+    """The measurement lattice (L = 28, Ltau = 120) with 64 right-hand sides in
+    the three-slice ring layout: every right-hand side matches the oracle.
+    Layouts 1 and 3 (equal chunks only) are refused for L % 8 == 4; the ring
+    layouts are refused where L % 4 != 0."""
+    w = hi.Workload("chain28", L=28, Ltau=120, omega0=1.0, alpha=1.0, seed=1047)
+    x = hi.phonon_field(w)
+    nr = 64
+    v = hi.gaussian_vectors(w, nr, seed=26)
+    with _ctx(w, nr) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        ctx.set_option("layout", 6)
+        vt = torch.tensor(v, device=DEV, dtype=torch.float32)
+        out = torch.full_like(vt, float("nan"))
+        ctx.fermion_matvec(hg.HOL_OP_MTM, vt, out)
+        got = out.cpu().double().numpy()
+        for lay in (1, 3):
+            with pytest.raises(hg.HolError):
+                ctx.set_option("layout", lay)
+        assert ctx.get_option("layout") == 6
+    for k in (0, 1, 31, 62, 63):
+        assert _rel(got[k], MF.MTM_apply(w, x, v[k])) < 3e-6
+    w6 = hi.Workload("l6", L=6, Ltau=8, seed=27)
+    with _ctx(w6, 1) as ctx:
+        for lay in (2, 6):
+            with pytest.raises(hg.HolError):
+                ctx.set_option("layout", lay)
+
+
 @pytest.mark.parametrize("layout,K", [(3, 1), (3, 2), (4, 2), (5, 4), (6, 4), (2, 8), (7, 1),
                                       (7, 4), (7, 5), (7, 8)])
 def test_vector_layouts_full_size(layout, K):
