@@ -135,7 +135,10 @@ __global__ void __launch_bounds__(128, 3) k_cg_mtm32_v4(const float* __restrict_
 // slice prefetched into a per-lane shared-memory ring by cp.async (16-byte
 // async copies, two stages), so the global loads of slice tau+1 are in
 // flight while slice tau is computed. Each lane copies and later reads only its own
-// slots, so cp.async.wait_group is the only synchronisation needed.
+// slots, so cp.async.wait_group is the only synchronisation needed. Also
+// built for L % 8 == 4, where a lane's row chunk may leave its last two
+// register rows unused (cb4.cuh): those rows are never copied, stored or
+// summed.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
 {
