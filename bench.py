@@ -70,6 +70,8 @@ def args_parse():
                                       "chains", "prior", "split"],
                     default="trajectory", help="with --mode leg: run one of the other rows alone")
     ap.add_argument("--rhs", type=int, default=16)
+    ap.add_argument("--prec", choices=["f32", "f64"], default="f32",
+                    help="--mode matvec: the fused FP32 M^T M (f32) or FP64 M and M^T (f64)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape")
@@ -755,7 +757,7 @@ def measurement_leg(dev, n_rv=128):
     # all probes in one block solve (127 ms against 244 ms in blocks of 16)
     with hg.Context.from_workload(w, max_rhs=n_rv) as ctx:
         ctx.set_field(torch.tensor(hi.phonon_field(w), device=dev))
-        ctx.tune(n_rv)                # launch shapes for the probe block (outside the timing)
+        tuned = ctx.tune(n_rv)        # launch shapes for the probe block (outside the timing)
         xi = torch.tensor(hi.z2_vectors(w, n_rv, seed=5), device=dev)
         Gxi = torch.empty_like(xi)
         G2 = torch.empty(2 * w.Ltau, w.L, w.L, dtype=torch.float64, device=dev)
@@ -772,7 +774,7 @@ def measurement_leg(dev, n_rv=128):
         ms = e0.elapsed_time(e1)
     return {"workload": "L=28 Ltau=120 chain, 128 Z2 probes, 2-point + type-2 Wick",
             "measurements_per_s": 1e3 / ms, "ms_per_measurement": ms,
-            "mean_cg_iters": float(np.mean(its))}
+            "mean_cg_iters": float(np.mean(its)), "tuned_launch": tuned}
 
 
 def chains_leg(dev, n_rv=128, precs=None, repeats=3):
@@ -1140,9 +1142,12 @@ def run_matvec(a):
     apply_options(ctx, a.option)
     tuned = ctx.tune(nr) if not a.no_tune else None
     apply_options(ctx, a.option)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    if a.prec == "f64":
+        run_matvec64(a, ctx, w, nr, flush, tuned)
+        return
     v = torch.tensor(hi.gaussian_vectors(w, nr, seed=5), device="cuda", dtype=torch.float32)
     q = torch.empty_like(v)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for _ in range(a.warmup):
         ctx.fermion_matvec(hg.HOL_OP_MTM, v, q)
     times = []
@@ -1163,6 +1168,30 @@ def run_matvec(a):
                       "alg_bytes": alg, "achieved_gbs": alg / (ms / 1e3) / 1e9,
                       "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / hbm,
                       "matvecs_per_s": 2 * nr / (ms / 1e3)}))
+    ctx.close()
+
+
+def run_matvec64(a, ctx, w, nr, flush, tuned):
+    """FP64 M and M^T alone on nr right-hand sides (the operators of the FP64
+    solver and of the mixed solver's reliable updates), each launch timed
+    alone after an L2 flush. ALU-bound on this part: algorithmic flops per
+    element 10 for either (C: 4 colours x one FMA per site; D and the sign
+    term: one multiply and one add), against the measured FP64 FMA rate."""
+    import torch
+    import paper_2203_01291_gb300 as hg
+    v = torch.tensor(hi.gaussian_vectors(w, nr, seed=5), device="cuda")
+    out = torch.empty_like(v)
+    peak = hg.hol_fma_peak(hg.HOL_F64)
+    res = {"mode": "matvec", "prec": "f64", "rhs": nr, "tuned_launch": tuned,
+           "options": a.option, "flops_per_element": 10, "fp64_fma_gflops": peak}
+    for name, op in (("M", hg.HOL_OP_M), ("MT", hg.HOL_OP_MT)):
+        for _ in range(a.warmup):
+            ctx.fermion_matvec(op, v, out)
+        ms = statistics.median(event_times(lambda: ctx.fermion_matvec(op, v, out), flush,
+                                           a.steps))
+        gf = 10.0 * nr * w.n / (ms / 1e3) / 1e9
+        res[name] = {"median_us": ms * 1e3, "gflops": gf, "frac_of_fp64_fma": gf / peak}
+    print(json.dumps(strict_json(res)))
     ctx.close()
 
 

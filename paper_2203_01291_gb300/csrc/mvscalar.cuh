@@ -92,12 +92,25 @@ __device__ __forceinline__ void cg_alpha_epilogue(const MvGeom& gm, int rhs,
     }
 }
 
+// -x when neg, else x: a sign-bit flip on the integer pipe (the FP64 pipe,
+// 1/64 of the FP32 rate on this part, is not spent on a multiplication by -1)
+__device__ __forceinline__ double neg_if(bool neg, double x)
+{
+    const unsigned long long m = neg ? 0x8000000000000000ULL : 0ULL;
+    return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(x) ^ m));
+}
+__device__ __forceinline__ float neg_if(bool neg, float x)
+{
+    return __int_as_float(__float_as_int(x) ^ (neg ? (int)0x80000000 : 0));
+}
+
 // ---------------------------------------------------------------------------
 // out = M v. With UPD the loaded vector is p_new = r + beta p_old (the CG
 // direction update), whose own slices are also stored to pnew.
-// norm_part (nullable): |out|^2 summed over the unit's slices.
+// norm_part (used when NORM, else ignored): |out|^2 summed over the unit's
+// slices.
 // ---------------------------------------------------------------------------
-template <typename R, int L, bool UPD, bool EX>
+template <typename R, int L, bool UPD, bool EX, bool NORM = true>
 __global__ void __launch_bounds__(128) k_M(const R* __restrict__ v, const R* __restrict__ pold,
                                            R* __restrict__ pnew, R* __restrict__ out,
                                            const R* __restrict__ ev, MvGeom gm,
@@ -148,18 +161,21 @@ __global__ void __launch_bounds__(128) k_M(const R* __restrict__ v, const R* __r
             }
             c[iy] = val;
         }
-        const R sg = (tau == 0) ? R(1) : R(-1);
+        const bool neg = tau != 0;   // s_tau = -1 except at tau = 0
         R part = R(0);
 #pragma unroll
         for (int iy = 0; iy < L; ++iy) {
-            const R w = fma(sg * ev[(long)tau * N + iy * L + geo.ix], a[iy], c[iy]);
+            const R w = fma(neg_if(neg, ev[(long)tau * N + iy * L + geo.ix]), a[iy], c[iy]);
             if (valid) out[o + iy * L] = w;
-            part = fma(w, w, part);
+            if constexpr (NORM) part = fma(w, w, part);
             a[iy] = c[iy];
         }
-        acc += (double)part;
+        if constexpr (NORM) acc += (double)part;
     }
-    if (norm_part != nullptr) group_store_sum<L>(acc, valid, norm_part + (long)rhs * gm.pstride + run);
+    if constexpr (NORM) {
+        if (norm_part != nullptr)
+            group_store_sum<L>(acc, valid, norm_part + (long)rhs * gm.pstride + run);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -316,7 +332,11 @@ int run_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs, const
 {
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-    if (prec == HOL_F64)
+    if (prec == HOL_F64 && norm_part == nullptr)
+        HOL_CUDA(launch_pdl(c, k_M<double, L, false, EX, false>, nb, nt, 0, s, (const double*)v,
+                            nullptr, nullptr, (double*)out, c->ev64, g, mask, BetaSrc{},
+                            nullptr, kin_of<double>(c)));
+    else if (prec == HOL_F64)
         HOL_CUDA(launch_pdl(c, k_M<double, L, false, EX>, nb, nt, 0, s, (const double*)v,
                             nullptr, nullptr, (double*)out, c->ev64, g, mask, BetaSrc{},
                             norm_part, kin_of<double>(c)));
