@@ -66,7 +66,8 @@ def args_parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["step", "matvec", "precond", "leg"], default="step")
-    ap.add_argument("--leg", choices=["trajectory", "trajectory64", "measurement", "global",
+    ap.add_argument("--leg", choices=["trajectory", "trajectory64", "measurement",
+                                      "measurement32", "global",
                                       "chains", "prior", "split"],
                     default="trajectory", help="with --mode leg: run one of the other rows alone")
     ap.add_argument("--rhs", type=int, default=16)
@@ -772,8 +773,8 @@ def measurement_leg(dev, n_rv=128):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-    return {"workload": "L=28 Ltau=120 chain, 128 Z2 probes, 2-point + type-2 Wick",
-            "measurements_per_s": 1e3 / ms, "ms_per_measurement": ms,
+    return {"workload": f"L=28 Ltau=120 chain, {n_rv} Z2 probes, 2-point + type-2 Wick",
+            "probes": n_rv, "measurements_per_s": 1e3 / ms, "ms_per_measurement": ms,
             "mean_cg_iters": float(np.mean(its)), "tuned_launch": tuned}
 
 
@@ -1272,7 +1273,8 @@ def run_leg(a):
     legs = {"trajectory": lambda: trajectory_leg("cuda", n_traj=1, options=a.option),
             "trajectory64": lambda: trajectory_leg("cuda", n_traj=1, options=a.option,
                                                    prec=0),
-            "measurement": lambda: measurement_leg("cuda", n_rv=32),
+            "measurement": lambda: measurement_leg("cuda"),
+            "measurement32": lambda: measurement_leg("cuda", n_rv=32),
             "global": lambda: global_update_leg("cuda"),
             "chains": lambda: chains_leg("cuda", repeats=1),
             "prior": lambda: prior_field_leg("cuda"),
