@@ -15,6 +15,7 @@ namespace hol {
 
 static thread_local char g_err[512] = "no error";
 static unsigned long long g_launches = 0;
+std::atomic<int> g_occ64[2][3][33][5];
 
 void count_launch() { __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED); }
 
@@ -304,6 +305,10 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
         free_ctx(c);
         return set_error(HOL_ECUDA, "hol_create: multiprocessor count query failed");
     }
+    if (c->exact)
+        occ64_warm_exact(c);
+    else
+        occ64_warm(c);
 
     const long n = c->n, R = p->max_rhs;
     const long pstride = matvec_pstride(c);

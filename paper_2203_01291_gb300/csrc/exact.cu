@@ -3,11 +3,21 @@
 // the scalar-layout kernels of mvscalar.cuh instantiated with EX = true.
 // This file: M v and M^T u; exact_cg.cu: the CG-step variants.
 // Every other launch shape is refused for such a context (context.cu), so
-// these five calls carry all its operator work.
+// these five calls carry all its operator work (and occ64_warm_exact fills
+// the occupancy caches of their FP64 kernels).
 #include "internal.cuh"
 #include "mvscalar.cuh"
 
 namespace hol {
+
+void occ64_warm_exact(const hol_ctx* c)
+{
+    switch (c->L) {
+#define X(LL) case LL: occ64_warm_l<LL, true>(); return;
+        HOL_FOR_EACH_L(X)
+#undef X
+    }
+}
 
 int launch_M_exact(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs,
                    const int* mask, double* norm_part, cudaStream_t s)

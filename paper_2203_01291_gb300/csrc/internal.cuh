@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <atomic>
 #include <initializer_list>
 #include <stdio.h>
 
@@ -274,6 +275,13 @@ enum MtEpilogue { MT_PLAIN = 0, MT_RESID = 1 };
 
 // out = M v (double or float per prec). norm_part (nullable): per-unit
 // sums of |out|^2 at stride matvec_pstride(c) per right-hand side.
+// Resident blocks per SM of the partial-free FP64 operator kernels, by
+// [exact propagator][M, M^T, residual M^T][L][warps per block] (0: not yet
+// queried); filled by occ64_warm at context creation.
+extern std::atomic<int> g_occ64[2][3][33][5];
+void occ64_warm(const hol_ctx* c);         // matvec.cu (checkerboard)
+void occ64_warm_exact(const hol_ctx* c);   // exact.cu
+
 int launch_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs,
              const int* mask, double* norm_part, cudaStream_t s);
 // Where the CG beta = rr_new / rr_old of each right-hand side comes from:

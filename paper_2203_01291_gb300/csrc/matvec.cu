@@ -1344,6 +1344,15 @@ int matvec_pstride(const hol_ctx* c)
     return 0;
 }
 
+void occ64_warm(const hol_ctx* c)
+{
+    switch (c->L) {
+#define X(LL) case LL: occ64_warm_l<LL, false>(); return;
+        HOL_FOR_EACH_L(X)
+#undef X
+    }
+}
+
 int launch_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs, const int* mask,
              double* norm_part, cudaStream_t s)
 {

@@ -14,6 +14,8 @@
 // ones), so each translation unit compiles only its own half.
 #pragma once
 
+#include <atomic>
+
 #include "cb.cuh"
 #include "internal.cuh"
 
@@ -323,8 +325,66 @@ int blocks_for(const hol_ctx* c, const MvGeom& g)
     return ceil_div(warps, c->mv_warps);
 }
 
+// Resident blocks per SM of `kern` at wpb warps per block, cached per kernel
+// in `cache` (indexed by wpb). The occupancy query is not a stream operation;
+// it is made once, before any capture (occ64_warm, from hol_create). The
+// caches are process-wide (g_occ64, shared by the translation units that
+// instantiate the same kernel).
+inline int occ_blocks(const void* kern, int wpb, std::atomic<int> (&cache)[5])
+{
+    int rb = cache[wpb].load();
+    if (rb == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rb, kern, 32 * wpb, 0) != cudaSuccess ||
+            rb < 1)
+            rb = 1;
+        cache[wpb].store(rb);
+    }
+    return rb;
+}
+
+// Geometry of an FP64 operator launch that keeps no per-unit partial sums
+// (M without |Mv|^2, M^T, the residual M^T): these kernels are bound by the
+// FP64 pipe (1/64 of the FP32 rate on this part) and need every resident
+// warp slot filled to hide its latency, while the CG's FP32 shape (few long
+// slice runs) suits bandwidth. K is the smallest divisor of T, at most the
+// context's K, whose warps fit one resident wave (rb blocks per SM); a halo
+// slice is re-read per run, no slice is computed twice, so the results do
+// not depend on K.
+template <int L>
+__host__ MvGeom make_geom64(const hol_ctx* c, int n_rhs, int rb)
+{
+    const long wave = (long)rb * c->mv_warps * c->sms;
+    constexpr int G = 32 / L;
+    int k = c->mv_k;
+    for (int kk = 1; kk < c->mv_k; ++kk) {
+        if (c->T % kk) continue;
+        if ((long)((c->T / kk + G - 1) / G) * n_rhs <= wave) {
+            k = kk;
+            break;
+        }
+    }
+    MvGeom g = make_geom<L>(c, n_rhs);
+    g.K = k;
+    g.nrun = c->T / k;
+    g.wpr = (g.nrun + G - 1) / G;
+    g.pstride = g.wpr * G;
+    return g;
+}
+
 #define HOL_FOR_EACH_L(X) \
     X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32)
+
+// warm the occupancy caches of the partial-free FP64 operator kernels
+// (make_geom64) for every block size, outside any stream capture
+template <int L, bool EX>
+void occ64_warm_l()
+{
+    for (int w : {1, 2, 4}) {
+        occ_blocks((const void*)k_M<double, L, false, EX, false>, w, g_occ64[EX][0][L]);
+        occ_blocks((const void*)k_MT<double, L, MT_PLAIN, EX>, w, g_occ64[EX][1][L]);
+        occ_blocks((const void*)k_MT<double, L, MT_RESID, EX>, w, g_occ64[EX][2][L]);
+    }
+}
 
 template <int L, bool EX>
 int run_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs, const int* mask,
@@ -332,11 +392,14 @@ int run_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs, const
 {
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-    if (prec == HOL_F64 && norm_part == nullptr)
-        HOL_CUDA(launch_pdl(c, k_M<double, L, false, EX, false>, nb, nt, 0, s, (const double*)v,
-                            nullptr, nullptr, (double*)out, c->ev64, g, mask, BetaSrc{},
-                            nullptr, kin_of<double>(c)));
-    else if (prec == HOL_F64)
+    if (prec == HOL_F64 && norm_part == nullptr) {
+        const int rb = occ_blocks((const void*)k_M<double, L, false, EX, false>, c->mv_warps,
+                                  g_occ64[EX][0][L]);
+        const MvGeom g64 = make_geom64<L>(c, n_rhs, rb);
+        HOL_CUDA(launch_pdl(c, k_M<double, L, false, EX, false>, blocks_for<L>(c, g64), nt, 0, s,
+                            (const double*)v, nullptr, nullptr, (double*)out, c->ev64, g64, mask,
+                            BetaSrc{}, nullptr, kin_of<double>(c)));
+    } else if (prec == HOL_F64)
         HOL_CUDA(launch_pdl(c, k_M<double, L, false, EX>, nb, nt, 0, s, (const double*)v,
                             nullptr, nullptr, (double*)out, c->ev64, g, mask, BetaSrc{},
                             norm_part, kin_of<double>(c)));
@@ -366,10 +429,14 @@ int run_MT(const hol_ctx* c, int prec, const void* u, void* out, int n_rhs, cons
 {
     const MvGeom g = make_geom<L>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
-    if (prec == HOL_F64)
-        HOL_CUDA(launch_pdl(c, k_MT<double, L, MT_PLAIN, EX>, nb, nt, 0, s, (const double*)u,
-                            nullptr, (double*)out, c->ev64, g, mask, kin_of<double>(c)));
-    else
+    if (prec == HOL_F64) {
+        const int rb = occ_blocks((const void*)k_MT<double, L, MT_PLAIN, EX>, c->mv_warps,
+                                  g_occ64[EX][1][L]);
+        const MvGeom g64 = make_geom64<L>(c, n_rhs, rb);
+        HOL_CUDA(launch_pdl(c, k_MT<double, L, MT_PLAIN, EX>, blocks_for<L>(c, g64), nt, 0, s,
+                            (const double*)u, nullptr, (double*)out, c->ev64, g64, mask,
+                            kin_of<double>(c)));
+    } else
         HOL_CUDA(launch_pdl(c, k_MT<float, L, MT_PLAIN, EX>, nb, nt, 0, s, (const float*)u,
                             nullptr, (float*)out, c->ev32, g, mask, kin_of<float>(c)));
     HOL_CHECK_LAUNCH("k_MT");
@@ -380,7 +447,9 @@ template <int L, bool EX>
 int run_MT_resid(const hol_ctx* c, const double* u, const double* b, double* out, int n_rhs,
                  const int* mask, cudaStream_t s)
 {
-    const MvGeom g = make_geom<L>(c, n_rhs);
+    const int rb = occ_blocks((const void*)k_MT<double, L, MT_RESID, EX>, c->mv_warps,
+                              g_occ64[EX][2][L]);
+    const MvGeom g = make_geom64<L>(c, n_rhs, rb);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     HOL_CUDA(launch_pdl(c, k_MT<double, L, MT_RESID, EX>, nb, nt, 0, s, u, b, out, c->ev64, g,
                         mask, kin_of<double>(c)));

@@ -259,6 +259,40 @@ def test_fused_mtm_every_layout(layout, L, T, K):
     assert max(MF.rel_residual(w, x, v[k], s[k]) for k in range(nr)) < 1.01e-8
 
 
+@pytest.mark.parametrize("L,T", [(16, 40), (32, 20)])
+def test_fp64_operators_do_not_depend_on_the_slice_grouping(L, T):
+    """The FP64 M and M^T launches without partial sums pick their own slice
+    grouping (as many warps as fit one resident wave); every element is the
+    same arithmetic whatever the grouping, so the results are bitwise those
+    of every slices_per_group and of the context-free static operator, and
+    within 1e-13 of the oracle."""
+    w, x = _field(L, T, seed=28)
+    nr = 3
+    v = hi.gaussian_vectors(w, nr, seed=29)
+    vt = torch.tensor(v, device=DEV)
+    got = {}
+    with _ctx(w, nr) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        for k in (1, 2, 4, 5):
+            ctx.set_option("slices_per_group", k)
+            for op in (hg.HOL_OP_M, hg.HOL_OP_MT):
+                out = torch.full_like(vt, float("nan"))
+                ctx.fermion_matvec(op, vt, out)
+                got[(k, op)] = out.cpu().numpy()
+    for op in (hg.HOL_OP_M, hg.HOL_OP_MT):
+        for k in (2, 4, 5):
+            assert np.array_equal(got[(k, op)], got[(1, op)])
+        st = torch.full_like(vt, float("nan"))
+        hg.fermion_matvec_static(hg.hol_params(L=L, Ltau=T, dtau=w.dtau, t=w.t, mu=w.mu,
+                                               alpha=w.alpha, omega0=w.omega0, max_rhs=nr),
+                                 torch.tensor(x, device=DEV), op, vt, st, nr)
+        assert np.array_equal(st.cpu().numpy(), got[(1, op)])
+    ref_m = np.stack([MF.M_apply(w, x, a) for a in v])
+    ref_mt = np.stack([MF.MT_apply(w, x, a) for a in v])
+    assert _rel(got[(1, hg.HOL_OP_M)], ref_m) < 1e-13
+    assert _rel(got[(1, hg.HOL_OP_MT)], ref_mt) < 1e-13
+
+
 UNEVEN_CASES = [(12, 20, 2), (12, 8, 8), (20, 10, 5), (28, 24, 4), (28, 30, 3)]
 
 
