@@ -616,6 +616,8 @@ def cold_operator_block(ctx, xd, nr, flush, hbm, launches=20):
         rhs64 = {"rhs": nr64, "median_us": ms64 * 1e3, "unit_bytes": unit64,
                  "achieved_gbs": unit64 / (ms64 / 1e3) / 1e9,
                  "frac": unit64 / (ms64 / 1e3) / 1e9 / hbm, "frac_ceiling": ceiling(unit64),
+                 "frac_beyond_floor": (unit64 / ((ms64 - floor_ms) / 1e3) / 1e9 / hbm
+                                       if ms64 > floor_ms else None),
                  "tuned_launch": tuned64}
         del v64, q64
     return {"rhs": nr, "median_us": ms * 1e3, "min_us": min(times) * 1e3,
@@ -626,6 +628,8 @@ def cold_operator_block(ctx, xd, nr, flush, hbm, launches=20):
             "launch_floor_warm_us": statistics.median(floor_warm) * 1e3,
             "torch_kernel_floor_us": statistics.median(floor_torch) * 1e3,
             "frac_ceiling": ceiling(unit),
+            "frac_beyond_floor": (unit / ((ms - floor_ms) / 1e3) / 1e9 / hbm
+                                  if ms > floor_ms else None),
             "rhs64": rhs64,
             "note": "median of single launches after a 256 MB L2 flush; frac by the operator's "
                     "algorithmic bytes (v in, q out, expV), of measured HBM; launch_floor_us: "
@@ -636,7 +640,8 @@ def cold_operator_block(ctx, xd, nr, flush, hbm, launches=20):
                     "for the host's launch call (so it measures the host path; with the flush "
                     "queued first the kernel is already queued when the event fires); "
                     "frac_ceiling: the fraction a launch with that floor would reach moving "
-                    "the bytes at peak"}
+                    "the bytes at peak; frac_beyond_floor: the bytes over the launch's time "
+                    "beyond the floor"}
 
 
 def precision_error_block(ctx, xd, Rd, nr):
@@ -748,10 +753,11 @@ def trajectory_pair(dev, n_traj=5):
             "mixed_over_fp64": mixed["trajectories_per_s"] / fp64["trajectories_per_s"]}
 
 
-def measurement_leg(dev, n_rv=128):
+def measurement_leg(dev, n_rv=128, repeats=3):
     """Stochastic Green's function (2-point and the type-2 Wick product) of one
     L=28, Ltau=120 chain (beta=12, omega0=1, alpha=1, x ~ N(0, 1)) with 128
-    Z2 probes solved in mixed precision to 1e-8."""
+    Z2 probes solved in mixed precision to 1e-8 (`repeats` timed measurements
+    of the same probes, mean and spread)."""
     import torch
     import paper_2203_01291_gb300 as hg
     w = hi.Workload("chain28", L=28, Ltau=120, omega0=1.0, alpha=1.0, seed=1047)
@@ -766,15 +772,19 @@ def measurement_leg(dev, n_rv=128):
         ctx.stochastic_measure(xi[:16].contiguous(), Gxi[:16], G2, G4, 2, tol=1e-8,
                                prec=hg.HOL_F32)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        its = ctx.stochastic_measure(xi, Gxi, G2, G4, 2, tol=1e-8, prec=hg.HOL_F32)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        times = []
+        for _ in range(repeats):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            its = ctx.stochastic_measure(xi, Gxi, G2, G4, 2, tol=1e-8, prec=hg.HOL_F32)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = float(np.mean(times))
     return {"workload": f"L=28 Ltau=120 chain, {n_rv} Z2 probes, 2-point + type-2 Wick",
             "probes": n_rv, "measurements_per_s": 1e3 / ms, "ms_per_measurement": ms,
+            "ms_min": float(np.min(times)), "ms_max": float(np.max(times)), "repeats": repeats,
             "mean_cg_iters": float(np.mean(its)), "tuned_launch": tuned}
 
 
@@ -873,7 +883,7 @@ def chains_leg(dev, n_rv=128, precs=None, repeats=3):
     return out
 
 
-def prior_field_leg(dev, n_rhs=16):
+def prior_field_leg(dev, n_rhs=16, repeats=3):
     """The L=32, Ltau=200 workload (omega0=0.5, alpha=1, 16 rhs, mixed CG to
     a certified 1e-8) on a tau-smooth field drawn from the free-phonon law
     exp(-S_B) (holstein_inputs.phonon_field_prior) instead of the i.i.d.
@@ -898,16 +908,22 @@ def prior_field_leg(dev, n_rhs=16):
             ctx.cg_solve(b, v, tol=TOL, prec=hg.HOL_F32, reliable_every=RELIABLE_EVERY,
                          max_iter=50000, precond=pc)
             torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            its, res = ctx.cg_solve(b, v, tol=TOL, prec=hg.HOL_F32,
-                                    reliable_every=RELIABLE_EVERY, max_iter=50000, precond=pc)
-            e1.record()
-            torch.cuda.synchronize()
-            assert np.all(res < TOL)
-            ms = e0.elapsed_time(e1)
+            times = []
+            for _ in range(repeats):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                its, res = ctx.cg_solve(b, v, tol=TOL, prec=hg.HOL_F32,
+                                        reliable_every=RELIABLE_EVERY, max_iter=50000,
+                                        precond=pc)
+                e1.record()
+                torch.cuda.synchronize()
+                assert np.all(res < TOL)
+                times.append(e0.elapsed_time(e1))
+            ms = float(np.mean(times))
             out["pcg" if pc else "cg"] = {"solves_per_s": n_rhs / (ms / 1e3), "ms": ms,
+                                          "ms_min": float(np.min(times)),
+                                          "ms_max": float(np.max(times)), "repeats": repeats,
                                           "mean_iters": float(np.mean(its))}
         out["pcg_short_series"] = short_series_rows(ctx, xd, b, v)
     out["iteration_ratio"] = out["cg"]["mean_iters"] / out["pcg"]["mean_iters"]

@@ -560,6 +560,8 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
     const Banks B = banks_of(c);
     const int pstride = matvec_pstride(c);
     const int pq_n = c->T / c->mv_k;
+    int pstride64 = 0, pq_n64 = 0;   // the FP64 CG's M keeps its own grouping
+    fp64_cg_geom(c, n_rhs, &pstride64, &pq_n64);
     const int dz_n = pc ? precond_tiles(c, prec) : nb2;   // partial count of r.z
     int* act_d = c->mask;
     int* rel_d = c->mask + c->p.max_rhs;
@@ -705,7 +707,7 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                 auto* upd = fold == 0 ? k_cg_update<double, 0>
                                       : fold == 1 ? k_cg_update<double, 1> : k_cg_update<double, 2>;
                 HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, s, v, r64, p64[pp], p64[1 - pp], q64, n,
-                                    act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst,
+                                    act_d, B.pq, pstride64, pq_n64, B.dz[cur], dz_n, rr_dst,
                                     c->alpha_buf, (const double*)nullptr, (double*)nullptr,
                                     (int*)nullptr));
             }
@@ -1446,6 +1448,8 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
     const Banks B = banks_of(c);
     const int pstride = matvec_pstride(c);
     const int pq_n = c->T / c->mv_k;
+    int pstride64 = 0, pq_n64 = 0;   // the FP64 CG's M keeps its own grouping
+    fp64_cg_geom(c, n_rhs, &pstride64, &pq_n64);
     const int dz_n = pc ? precond_tiles(c, mixed ? HOL_F32 : HOL_F64) : nb2;
     int* act_d = c->mask;
     int* rel_d = c->mask + c->p.max_rhs;
@@ -1533,7 +1537,7 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
                 auto* upd = fold == 0 ? k_cg_update<double, 0>
                                       : fold == 1 ? k_cg_update<double, 1> : k_cg_update<double, 2>;
                 HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, cs, v, r64, p64[pp], p64[1 - pp], q64, n,
-                                    act_d, B.pq, pstride, pq_n, B.dz[cur], dz_n, rr_dst,
+                                    act_d, B.pq, pstride64, pq_n64, B.dz[cur], dz_n, rr_dst,
                                     c->alpha_buf, (const double*)nullptr, (double*)nullptr,
                                     (int*)nullptr));
             }

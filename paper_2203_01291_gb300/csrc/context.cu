@@ -15,7 +15,7 @@ namespace hol {
 
 static thread_local char g_err[512] = "no error";
 static unsigned long long g_launches = 0;
-std::atomic<int> g_occ64[2][3][33][5];
+std::atomic<int> g_occ64[2][4][33][5];
 
 void count_launch() { __atomic_add_fetch(&g_launches, 1ULL, __ATOMIC_RELAXED); }
 

@@ -10,6 +10,21 @@
 
 namespace hol {
 
+void fp64_cg_geom_exact(const hol_ctx* c, int n_rhs, int* pstride, int* nrun)
+{
+    switch (c->L) {
+#define X(LL)                                                \
+    case LL: {                                               \
+        const MvGeom g = geom_m_upd64<LL, true>(c, n_rhs);   \
+        *pstride = g.pstride;                                \
+        *nrun = g.nrun;                                      \
+        return;                                              \
+    }
+        HOL_FOR_EACH_L(X)
+#undef X
+    }
+}
+
 int launch_M_upd64_exact(const hol_ctx* c, const double* r, const double* pold, double* pnew,
                          double* w, int n_rhs, const int* mask, BetaSrc beta,
                          double* norm_part, cudaStream_t s)

@@ -275,12 +275,16 @@ enum MtEpilogue { MT_PLAIN = 0, MT_RESID = 1 };
 
 // out = M v (double or float per prec). norm_part (nullable): per-unit
 // sums of |out|^2 at stride matvec_pstride(c) per right-hand side.
-// Resident blocks per SM of the partial-free FP64 operator kernels, by
-// [exact propagator][M, M^T, residual M^T][L][warps per block] (0: not yet
-// queried); filled by occ64_warm at context creation.
-extern std::atomic<int> g_occ64[2][3][33][5];
+// Resident blocks per SM of the FP64 operator kernels that take their own
+// slice grouping, by [exact propagator][M, M^T, residual M^T, the FP64 CG's
+// M][L][warps per block] (0: not yet queried); filled by occ64_warm at
+// context creation.
+extern std::atomic<int> g_occ64[2][4][33][5];
 void occ64_warm(const hol_ctx* c);         // matvec.cu (checkerboard)
 void occ64_warm_exact(const hol_ctx* c);   // exact.cu
+// Stride and count of the |Mp|^2 unit partials that the FP64 CG's M
+// (launch_M_upd64) writes for n_rhs right-hand sides.
+void fp64_cg_geom(const hol_ctx* c, int n_rhs, int* pstride, int* nrun);
 
 int launch_M(const hol_ctx* c, int prec, const void* v, void* out, int n_rhs,
              const int* mask, double* norm_part, cudaStream_t s);

@@ -1344,6 +1344,29 @@ int matvec_pstride(const hol_ctx* c)
     return 0;
 }
 
+void fp64_cg_geom_exact(const hol_ctx* c, int n_rhs, int* pstride, int* nrun);   // exact_cg.cu
+
+void fp64_cg_geom(const hol_ctx* c, int n_rhs, int* pstride, int* nrun)
+{
+    *pstride = matvec_pstride(c);
+    *nrun = c->T / c->mv_k;
+    if (c->exact) {
+        fp64_cg_geom_exact(c, n_rhs, pstride, nrun);
+        return;
+    }
+    switch (c->L) {
+#define X(LL)                                                 \
+    case LL: {                                                \
+        const MvGeom g = geom_m_upd64<LL, false>(c, n_rhs);   \
+        *pstride = g.pstride;                                 \
+        *nrun = g.nrun;                                       \
+        return;                                               \
+    }
+        HOL_FOR_EACH_L(X)
+#undef X
+    }
+}
+
 void occ64_warm(const hol_ctx* c)
 {
     switch (c->L) {

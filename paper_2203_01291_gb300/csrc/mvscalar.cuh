@@ -351,14 +351,16 @@ inline int occ_blocks(const void* kern, int wpb, std::atomic<int> (&cache)[5])
 // slice is re-read per run, no slice is computed twice, so the results do
 // not depend on K.
 template <int L>
-__host__ MvGeom make_geom64(const hol_ctx* c, int n_rhs, int rb)
+__host__ MvGeom make_geom64(const hol_ctx* c, int n_rhs, int rb, long max_pstride = 1L << 30)
 {
     const long wave = (long)rb * c->mv_warps * c->sms;
     constexpr int G = 32 / L;
     int k = c->mv_k;
     for (int kk = 1; kk < c->mv_k; ++kk) {
         if (c->T % kk) continue;
-        if ((long)((c->T / kk + G - 1) / G) * n_rhs <= wave) {
+        const long wpr = (c->T / kk + G - 1) / G;
+        if (wpr * G > max_pstride) continue;   // the per-unit partial sums must fit their bank
+        if (wpr * n_rhs <= wave) {
             k = kk;
             break;
         }
@@ -383,7 +385,20 @@ void occ64_warm_l()
         occ_blocks((const void*)k_M<double, L, false, EX, false>, w, g_occ64[EX][0][L]);
         occ_blocks((const void*)k_MT<double, L, MT_PLAIN, EX>, w, g_occ64[EX][1][L]);
         occ_blocks((const void*)k_MT<double, L, MT_RESID, EX>, w, g_occ64[EX][2][L]);
+        occ_blocks((const void*)k_M<double, L, true, EX, true>, w, g_occ64[EX][3][L]);
     }
+}
+
+// Geometry of the FP64 CG's M (p = z + beta p_old, w = M p, |w|^2 partials
+// per unit): the FP64 grouping of make_geom64, limited so that its partial
+// sums fit the bank; the update kernel reads them with this geometry's
+// stride and count (fp64_cg_geom).
+template <int L, bool EX>
+MvGeom geom_m_upd64(const hol_ctx* c, int n_rhs)
+{
+    const int rb = occ_blocks((const void*)k_M<double, L, true, EX, true>, c->mv_warps,
+                              g_occ64[EX][3][L]);
+    return make_geom64<L>(c, n_rhs, rb, c->part_len / c->p.max_rhs);
 }
 
 template <int L, bool EX>
@@ -415,7 +430,7 @@ template <int L, bool EX>
 int run_M_upd64(const hol_ctx* c, const double* r, const double* pold, double* pnew, double* w,
                 int n_rhs, const int* mask, BetaSrc beta, double* norm_part, cudaStream_t s)
 {
-    const MvGeom g = make_geom<L>(c, n_rhs);
+    const MvGeom g = geom_m_upd64<L, EX>(c, n_rhs);
     const int nb = blocks_for<L>(c, g), nt = 32 * c->mv_warps;
     HOL_CUDA(launch_pdl(c, k_M<double, L, true, EX>, nb, nt, 0, s, r, pold, pnew, w, c->ev64, g,
                         mask, beta, norm_part, kin_of<double>(c)));
