@@ -745,12 +745,18 @@ def trajectory_leg(dev, n_traj=5, options=(), prec=None):
 
 def trajectory_pair(dev, n_traj=5):
     """The hmc16 trajectory row in both precisions at equal final residual,
-    and their rate ratio (mixed over FP64)."""
+    and their rate ratio (mixed over FP64); beside them the mixed trajectory
+    with the first Chebyshev order constant a1 = 0.5 instead of the paper's
+    1 (Eq. (NP_heuristic): a shorter series, a cheaper P^-1)."""
     import paper_2203_01291_gb300 as hg
     mixed = trajectory_leg(dev, n_traj, prec=hg.HOL_F32)
     fp64 = trajectory_leg(dev, n_traj, prec=hg.HOL_F64)
+    short = trajectory_leg(dev, n_traj, options=("kpm_a1_percent=50",), prec=hg.HOL_F32)
     return {"mixed": mixed, "fp64": fp64,
-            "mixed_over_fp64": mixed["trajectories_per_s"] / fp64["trajectories_per_s"]}
+            "mixed_over_fp64": mixed["trajectories_per_s"] / fp64["trajectories_per_s"],
+            "mixed_a1_0.5": {k: short[k] for k in ("trajectories_per_s", "ms_per_trajectory",
+                                                   "ms_min", "ms_max", "accepted", "of",
+                                                   "mean_abs_dH", "avg_launch_us")}}
 
 
 def measurement_leg(dev, n_rv=128, repeats=3):

@@ -32,8 +32,7 @@ struct Geom4 {
     static constexpr int RT = L / 4 + (kUneven ? 1 : 0);   // register rows per lane
     static constexpr int G = 32 / L;                  // slices per warp
     int g, cx, rc, left, right, down, up;
-    int row0;      // first lattice row of this lane's chunk
-    bool shortc;   // the chunk holds RT - 2 rows (L % 8 == 4, odd rc)
+    bool shortc;   // the chunk holds RT - 2 rows (L % 8 == 4, odd rc; else false)
     bool ok;
     __device__ __forceinline__ Geom4()
     {
@@ -52,16 +51,16 @@ struct Geom4 {
         left = b + rc * LR + (cx == 0 ? LR - 1 : cx - 1);
         down = b + ((rc + 1) & 3) * LR + cx;
         up = b + ((rc + 3) & 3) * LR + cx;
-        if constexpr (kUneven) {
-            row0 = (rc >> 1) * (L / 2) + (rc & 1) * (L / 4 + 1);
-            shortc = (rc & 1) != 0;
-        } else {
-            row0 = rc * RT;
-            shortc = false;
-        }
+        shortc = kUneven && (rc & 1) != 0;
+    }
+    // first lattice row of this lane's chunk
+    __device__ __forceinline__ int row0() const
+    {
+        if constexpr (kUneven) return (rc >> 1) * (L / 2) + (rc & 1) * (L / 4 + 1);
+        return rc * RT;
     }
     // float offset of register row k of this lane inside a slice
-    __device__ __forceinline__ int off(int k) const { return (row0 + k) * L + 4 * cx; }
+    __device__ __forceinline__ int off(int k) const { return (row0() + k) * L + 4 * cx; }
     // register row k holds a lattice row (always, unless L % 8 == 4)
     __device__ __forceinline__ bool has(int k) const
     {
