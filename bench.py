@@ -575,6 +575,18 @@ def cold_operator_block(ctx, xd, nr, flush, hbm, launches=20):
         ctx.fermion_matvec(hg.HOL_OP_MTM, v, q)
     times = event_times(lambda: ctx.fermion_matvec(hg.HOL_OP_MTM, v, q), flush, launches)
     ms = statistics.median(times)
+    # two launches on different inputs after the flush: the second one meets
+    # cold data (its own v, q and the evicted expV rows are not in L2) but
+    # not the cold start of the first (kernel code, parameters, TLB)
+    v2 = torch.tensor(hi.gaussian_vectors(WORKLOAD, nr, seed=7), device="cuda",
+                      dtype=torch.float32)
+    q2 = torch.empty_like(v2)
+
+    def pair():
+        ctx.fermion_matvec(hg.HOL_OP_MTM, v, q)
+        ctx.fermion_matvec(hg.HOL_OP_MTM, v2, q2)
+
+    ms_pair = statistics.median(event_times(pair, flush, launches))
     unit = nr * n * 8.0 + n * 4.0
     cg_bytes = nr * n * 16.0 + n * 4.0
     # the floor of one event-bracketed launch of the same kernel: the fused
@@ -630,6 +642,9 @@ def cold_operator_block(ctx, xd, nr, flush, hbm, launches=20):
             "frac_ceiling": ceiling(unit),
             "frac_beyond_floor": (unit / ((ms - floor_ms) / 1e3) / 1e9 / hbm
                                   if ms > floor_ms else None),
+            "second_launch_us": (ms_pair - ms) * 1e3,
+            "second_launch_frac": (unit / ((ms_pair - ms) / 1e3) / 1e9 / hbm
+                                   if ms_pair > ms else None),
             "rhs64": rhs64,
             "note": "median of single launches after a 256 MB L2 flush; frac by the operator's "
                     "algorithmic bytes (v in, q out, expV), of measured HBM; launch_floor_us: "
@@ -641,7 +656,9 @@ def cold_operator_block(ctx, xd, nr, flush, hbm, launches=20):
                     "queued first the kernel is already queued when the event fires); "
                     "frac_ceiling: the fraction a launch with that floor would reach moving "
                     "the bytes at peak; frac_beyond_floor: the bytes over the launch's time "
-                    "beyond the floor"}
+                    "beyond the floor; second_launch_*: a second launch on other inputs right "
+                    "after the first, from the same flush (cold data, warm start), timed as "
+                    "the difference of the pair and the single launch"}
 
 
 def precision_error_block(ctx, xd, Rd, nr):
