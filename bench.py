@@ -381,6 +381,7 @@ def run_ours(a):
 
     # the dominant kernel cold: one fused M^T M launch after an L2 flush
     cold = cold_operator_block(ctx, xd, nr, flush, hbm)
+    rates = unit_rates_block(ctx, xd, vd, bd, Fd, nr, flush, cold)
 
     # precision of the mixed path against the FP64 path on the same inputs
     prec_err = None if a.no_fp64 else precision_error_block(ctx, xd, Rd, nr)
@@ -512,6 +513,7 @@ def run_ours(a):
                          "peak_src": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                          "cold": cold},
             "cg_iteration": cg_iteration,
+            "unit_rates": rates,
             "kernel_ms": {"cg_operator": op_ms, "cg_update": up_ms, "force": fo_ms,
                           "precond": pc_ms, "timed_total": ms_total,
                           "timer_stride": TIMER_STRIDE,
@@ -553,6 +555,35 @@ def event_times(fn, flush, launches):
     return times
 
 
+def unit_rates_block(ctx, xd, vd, bd, Fd, nr, flush, cold, launches=10):
+    """The per-unit rates asked beside the solve rate, each launch timed alone
+    after an L2 flush: fermion matvecs/s (one M or M^T on one right-hand
+    side; the fused FP32 M^T M counts two) in FP32 and FP64, and forces/s
+    (the force of one pseudofermion; one call computes nr of them plus the
+    bosonic term, with the solutions of the last benchmark step)."""
+    import torch
+    import paper_2203_01291_gb300 as hg
+    ctx.set_field(xd)
+    v64 = torch.tensor(hi.gaussian_vectors(WORKLOAD, nr, seed=5), device="cuda")
+    o64 = torch.empty_like(v64)
+    out = {"fp32_fused_mtm_matvecs_per_s": 2 * nr / (cold["median_us"] / 1e6),
+           "fp32_fused_mtm_matvecs_per_s_streaming": 2 * nr / (cold["stream_us"] / 1e6)}
+    for name, op in (("fp64_M", hg.HOL_OP_M), ("fp64_MT", hg.HOL_OP_MT)):
+        ctx.fermion_matvec(op, v64, o64)
+        ms = statistics.median(event_times(lambda: ctx.fermion_matvec(op, v64, o64), flush,
+                                           launches))
+        out[name + "_us"] = ms * 1e3
+        out[name + "_matvecs_per_s"] = nr / (ms / 1e3)
+    ctx.force(vd, bd, Fd, with_bosonic=True)
+    ms = statistics.median(event_times(lambda: ctx.force(vd, bd, Fd, with_bosonic=True),
+                                       flush, launches))
+    out["force_us"] = ms * 1e3
+    out["forces_per_s"] = nr / (ms / 1e3)
+    out["note"] = ("cold single launches (L2 flushed before each); the FP32 figures are the "
+                   "cold operator block's, single and streaming")
+    return out
+
+
 def cold_operator_block(ctx, xd, nr, flush, hbm, launches=20):
     """The fused FP32 M^T M (the CG operator kernel, here without the
     direction update) on nr right-hand sides, each launch timed alone with
@@ -587,6 +618,21 @@ def cold_operator_block(ctx, xd, nr, flush, hbm, launches=20):
         ctx.fermion_matvec(hg.HOL_OP_MTM, v2, q2)
 
     ms_pair = statistics.median(event_times(pair, flush, launches))
+    # a run of launches over eight different input sets after the flush
+    # (216 MB of inputs and outputs, more than L2): every launch streams cold
+    # data; the run's time over its launches is not limited by the event
+    # resolution (about 0.5 us) as a single short launch is
+    n_set = 8
+    vs = [torch.tensor(hi.gaussian_vectors(WORKLOAD, nr, seed=20 + j), device="cuda",
+                       dtype=torch.float32) for j in range(n_set)]
+    qs = [torch.empty_like(vj) for vj in vs]
+
+    def run():
+        for vj, qj in zip(vs, qs):
+            ctx.fermion_matvec(hg.HOL_OP_MTM, vj, qj)
+
+    ms_run = statistics.median(event_times(run, flush, max(5, launches // 4))) / n_set
+    del vs, qs
     unit = nr * n * 8.0 + n * 4.0
     cg_bytes = nr * n * 16.0 + n * 4.0
     # the floor of one event-bracketed launch of the same kernel: the fused
@@ -642,6 +688,7 @@ def cold_operator_block(ctx, xd, nr, flush, hbm, launches=20):
             "frac_ceiling": ceiling(unit),
             "frac_beyond_floor": (unit / ((ms - floor_ms) / 1e3) / 1e9 / hbm
                                   if ms > floor_ms else None),
+            "stream_us": ms_run * 1e3, "stream_frac": unit / (ms_run / 1e3) / 1e9 / hbm,
             "second_launch_us": (ms_pair - ms) * 1e3,
             "second_launch_frac": (unit / ((ms_pair - ms) / 1e3) / 1e9 / hbm
                                    if ms_pair > ms else None),
@@ -658,7 +705,9 @@ def cold_operator_block(ctx, xd, nr, flush, hbm, launches=20):
                     "the bytes at peak; frac_beyond_floor: the bytes over the launch's time "
                     "beyond the floor; second_launch_*: a second launch on other inputs right "
                     "after the first, from the same flush (cold data, warm start), timed as "
-                    "the difference of the pair and the single launch"}
+                    "the difference of the pair and the single launch; stream_*: eight "
+                    "launches on eight different input sets after the flush (216 MB, more "
+                    "than L2), per launch: every launch streams cold data"}
 
 
 def precision_error_block(ctx, xd, Rd, nr):
