@@ -516,11 +516,16 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  *                       slice per warp and slices_per_group (<= 8) warps per
  *                       block exchanging the tau neighbours in shared memory
  *                       (L == 32)
- *   "kpm_registers"     FP32 KPM with the slice in registers, L = 16 or 32:
- *                       0 off (shared-memory kernel), 1 four columns per
- *                       lane, 2 two columns per lane (twice the warps per
- *                       problem, half the work per lane on the chain of
- *                       Bbar applies). Default 2 at L = 32, 1 otherwise
+ *   "kpm_registers"     FP32 KPM with the slice in registers: 0 off
+ *                       (shared-memory kernel), 1 four columns per lane
+ *                       (L = 16 or 32), 2 two columns per lane (L = 16 or
+ *                       32: twice the warps per problem, half the work per
+ *                       lane on the chain of Bbar applies), 3 the lane
+ *                       layout (any L: one lane per column, the rows in
+ *                       registers, the real and imaginary parts in two lane
+ *                       groups). 1 and 2 fall back to the shared-memory
+ *                       kernel for other L. Default 2 at L = 32, 1 at
+ *                       L = 16, 3 otherwise
  *   "persistent_cg"     plain mixed CG chunks in one cooperative launch (0/1)
  *   "pdl"               programmatic dependent launch of the CG iteration
  *                       kernels: each may be scheduled while its predecessor

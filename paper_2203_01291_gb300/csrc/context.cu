@@ -286,9 +286,11 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     c->mv_warps = 4;
     c->mv_vec = c->exact ? 0 : 1;
     // register KPM: two columns per lane at L = 32 (measured 0.126 against
-    // 0.149 ms for P^{-1} P^{-T} on 16 rhs), four below (one warp per problem
-    // at L = 16 beats two warps and their barrier per Bbar apply)
-    c->kpm_reg = c->exact ? 0 : (c->L == 32 ? 2 : 1);
+    // 0.149 ms for P^{-1} P^{-T} on 16 rhs), four at L = 16 (one warp per
+    // problem beats two warps and their barrier per Bbar apply), the lane
+    // layout (one lane per column, real and imaginary parts in two lane
+    // groups) for every other L
+    c->kpm_reg = c->exact ? 0 : (c->L == 32 ? 2 : c->L == 16 ? 1 : 3);
     c->persist = 0;
     c->merged = 0;
     c->fused = 0;
@@ -560,8 +562,8 @@ extern "C" int hol_set_option(hol_ctx* c, const char* name, int value)
     } else if (is("kpm_registers")) {
         if (value && c->exact)
             return set_error(HOL_EINVAL, "hol_set_option: kpm_registers is checkerboard only");
-        if (value < 0 || value > 2)
-            return set_error(HOL_EINVAL, "hol_set_option: kpm_registers must be 0, 1 or 2");
+        if (value < 0 || value > 3)
+            return set_error(HOL_EINVAL, "hol_set_option: kpm_registers must be 0, 1, 2 or 3");
         c->kpm_reg = value;
     } else if (is("persistent_cg")) {
         if (value && c->exact)

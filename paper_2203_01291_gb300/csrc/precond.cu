@@ -751,6 +751,134 @@ __global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
     }
 }
 
+// ---------------------------------------------------------- KPM, lane layout
+// FP32 KPM for any even L <= 32 in the scalar register layout of cb.cuh: a
+// lane group of L lanes holds one real N-vector (lane = column, registers =
+// rows; x-bonds by shuffles, y-bonds on register pairs). Bbar is real, so
+// T_m(A) acts on the real and imaginary parts of a problem's complex vector
+// independently: lane group 2s + p holds part p (0: real, 1: imaginary) of
+// problem s of the block, and the two recurrences meet only in the complex
+// coefficient sum. Each group accumulates A_p = sum c_m.re x_p and
+// B_p = sum c_m.im x_p; at the end of a series acc.re = A_0 - s B_1 and
+// acc.im = A_1 + s B_0 (s = -1 for the conjugate coefficients of the
+// transpose), one exchange per series instead of one per step. With
+// G = 32 / L >= 2 groups per warp a block is one warp holding G / 2 problems
+// (an odd last group shadows and never stores); with G = 1 a block is two
+// warps, one per part, exchanging through shared memory. The problems of a
+// block share omega (consecutive right-hand sides), so every group runs the
+// same N_P(omega) steps and the warp-wide shuffles stay converged.
+template <int L>
+struct KLane {
+    static constexpr int G = 32 / L;                  // lane groups per warp
+    static constexpr int PPB = G >= 2 ? G / 2 : 1;    // problems per block
+    static constexpr int THREADS = G >= 2 ? 32 : 64;
+};
+
+template <int L>
+__global__ void __launch_bounds__(KLane<L>::THREADS)
+    k_kpm_lane(const float2* __restrict__ vin, float2* __restrict__ vout,
+               const double* __restrict__ dbar, const double* __restrict__ scal,
+               const int* __restrict__ npv, const double2* __restrict__ coef, int n_rhs, int Th,
+               int max_np, int mode, float th)
+{
+    pdl_wait();      // the input comes from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
+    using K = KLane<L>;
+    constexpr int N = L * L;
+    const LaneGeom<L> geo;
+    // this lane's group within the block: part and problem slot
+    const int grp = (K::G >= 2) ? geo.g : (int)(threadIdx.x >> 5);
+    const int part = grp & 1, slot = grp >> 1;
+    const bool live = geo.ok && slot < K::PPB;
+    const int rpb = (n_rhs + K::PPB - 1) / K::PPB;   // blocks per omega
+    const int wq = blockIdx.x / rpb;
+    const int rhs_raw = (blockIdx.x - wq * rpb) * K::PPB + (slot < K::PPB ? slot : 0);
+    const bool own = live && rhs_raw < n_rhs;        // stores its results
+    const int rhs = rhs_raw < n_rhs ? rhs_raw : n_rhs - 1;
+    const long off = ((long)rhs * Th + wq) * N + geo.ix;
+    const float* vin_f = reinterpret_cast<const float*>(vin);
+    float t[L], d[L];
+#pragma unroll
+    for (int iy = 0; iy < L; ++iy) {
+        t[iy] = vin_f[2 * (off + iy * L) + part];
+        d[iy] = (float)dbar[geo.ix + iy * L];
+    }
+    const double bmin = scal[S_BMIN], bmax = scal[S_BMAX];
+    const double db = bmax - bmin;
+    const float a = (float)(2.0 / db), c0 = (float)(-2.0 * bmin / db - 1.0);
+    const int np = npv[wq];
+    extern __shared__ float2 kl_cw[];   // this omega's coefficients, then (G = 1) the exchange
+    for (int m = threadIdx.x; m < np; m += blockDim.x) {
+        const double2 cm = coef[(long)wq * max_np + m];
+        kl_cw[m] = make_float2((float)cm.x, (float)cm.y);
+    }
+    float* xbuf = reinterpret_cast<float*>(kl_cw + max_np);   // [2][32][L]
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool trans = (pass == 0);
+        if (trans && !(mode & 1)) continue;
+        if (!trans && !(mode & 2)) continue;
+        const float sgn = trans ? -1.0f : 1.0f;   // conj coefficients for the transpose
+        float A[L], B[L], prev[L];
+        {
+            const float2 cm = kl_cw[0];
+#pragma unroll
+            for (int iy = 0; iy < L; ++iy) {
+                A[iy] = cm.x * t[iy];
+                B[iy] = cm.y * t[iy];
+                prev[iy] = t[iy];
+            }
+        }
+        for (int m = 1; m < np; ++m) {
+            float b[L];
+#pragma unroll
+            for (int iy = 0; iy < L; ++iy) b[iy] = trans ? t[iy] * d[iy] : t[iy];
+            if (trans)
+                cb_apply_t<float, L>(b, geo, th);
+            else
+                cb_apply<float, L>(b, geo, th);
+            const float2 cm = kl_cw[m];
+            // alpha_m = (m == 1 ? 1 : 2) (a Bbar + c0) alpha_{m-1} - (m == 1 ? 0 : alpha_{m-2})
+            const float f2 = (m == 1) ? 1.0f : 2.0f;
+            const float pm = (m == 1) ? 0.0f : 1.0f;
+#pragma unroll
+            for (int iy = 0; iy < L; ++iy) {
+                const float bv = trans ? b[iy] : b[iy] * d[iy];
+                const float x = f2 * fmaf(a, bv, c0 * t[iy]) - pm * prev[iy];
+                prev[iy] = t[iy];
+                t[iy] = x;
+                A[iy] = fmaf(cm.x, x, A[iy]);
+                B[iy] = fmaf(cm.y, x, B[iy]);
+            }
+        }
+        // acc.re = A_0 - sgn B_1, acc.im = A_1 + sgn B_0: swap B with the other part
+        float Bo[L];
+        if constexpr (K::G >= 2) {
+            const int lane = threadIdx.x & 31;
+            const int src = part == 0 ? lane + L : lane - L;   // the other part's lane
+            const int srcc = (src >= 0 && src < 32) ? src : lane;
+#pragma unroll
+            for (int iy = 0; iy < L; ++iy) Bo[iy] = __shfl_sync(kFull, B[iy], srcc);
+        } else {
+            const int lane = threadIdx.x & 31;
+            // (the previous series' reads of xbuf ended at its third barrier)
+#pragma unroll
+            for (int iy = 0; iy < L; ++iy) xbuf[(part * 32 + lane) * L + iy] = B[iy];
+            __syncthreads();
+#pragma unroll
+            for (int iy = 0; iy < L; ++iy) Bo[iy] = xbuf[((1 - part) * 32 + lane) * L + iy];
+            __syncthreads();
+        }
+#pragma unroll
+        for (int iy = 0; iy < L; ++iy) t[iy] = part == 0 ? A[iy] - sgn * Bo[iy] : A[iy] + sgn * Bo[iy];
+    }
+    if (own) {
+        float* vout_f = reinterpret_cast<float*>(vout);
+#pragma unroll
+        for (int iy = 0; iy < L; ++iy) vout_f[2 * (off + iy * L) + part] = t[iy];
+    }
+}
+
 // N_P(omega) and c_m(omega), m < N_P, one block per omega < T/2.
 // f(cos theta_n) is evaluated once per quadrature node into shared memory;
 // cos(m theta_n) follows from a rotation by m pi / N_Q per node, so the
@@ -815,6 +943,38 @@ size_t fft_smem(const hol_ctx* c, int prec)
 {
     const size_t cs = prec == HOL_F64 ? sizeof(double2) : sizeof(float2);
     return 2 * (size_t)c->T * (tile_sites(c, prec) / 2) * cs;   // two sites per column
+}
+
+template <int L>
+int run_kpm_lane_l(const hol_ctx* c, const float2* in, float2* out, int n_rhs, int Th,
+                   int max_np, int mode, cudaStream_t s)
+{
+    using K = KLane<L>;
+    const size_t sm = (size_t)max_np * sizeof(float2) +
+                      (K::G >= 2 ? 0 : (size_t)2 * 32 * L * sizeof(float));
+    static std::atomic<int> limit(0);   // raised once per instantiation (not a stream call)
+    if ((int)sm > limit.load()) {
+        HOL_CUDA(cudaFuncSetAttribute((const void*)k_kpm_lane<L>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        limit.store((int)sm);
+    }
+    const int grid = Th * ((n_rhs + K::PPB - 1) / K::PPB);
+    HOL_CUDA(launch_pdl(c, k_kpm_lane<L>, grid, K::THREADS, sm, s, in, out, c->dbar, c->scal,
+                        c->kpm.np, c->kpm.coef, n_rhs, Th, max_np, mode, (float)c->th));
+    HOL_CHECK_LAUNCH("k_kpm_lane");
+    return HOL_OK;
+}
+
+// FP32 KPM in the lane layout (any even L; option kpm_registers = 3)
+int run_kpm_lane(const hol_ctx* c, const float2* in, float2* out, int n_rhs, int Th, int max_np,
+                 int mode, cudaStream_t s)
+{
+    switch (c->L) {
+#define X(LL) case LL: return run_kpm_lane_l<LL>(c, in, out, n_rhs, Th, max_np, mode, s);
+        X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32)
+#undef X
+    }
+    return set_error(HOL_EINVAL, "kpm lane layout: unsupported L=%d", c->L);
 }
 
 int kpm_threads(const hol_ctx* c)
@@ -917,6 +1077,11 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
                          : run(k_kpm_reg<16, 4>, 32 * KGeo<16, 4>::W);
             if (rc) return rc;
             HOL_CHECK_LAUNCH("k_kpm_reg");
+            done = true;
+        } else if (c->kpm_reg == 3 && !c->exact) {
+            rc = run_kpm_lane(c, reinterpret_cast<const float2*>(h0),
+                              reinterpret_cast<float2*>(h1), n_rhs, ka.Th, ka.max_np, mode, s);
+            if (rc) return rc;
             done = true;
         }
     }

@@ -85,6 +85,35 @@ def test_precond_fp32_kpm_variants(kpm, queue, L, T):
             assert _rel(out.cpu().double().numpy(), ref) < 2e-5
 
 
+@pytest.mark.parametrize("L,T,nr", [(4, 12, 3), (6, 10, 3), (8, 12, 3), (10, 8, 2), (12, 12, 3),
+                                    (14, 6, 1), (16, 8, 3), (20, 8, 1), (24, 6, 2), (28, 6, 3),
+                                    (30, 4, 1), (32, 6, 2)])
+def test_precond_fp32_lane_layout_vs_oracle(L, T, nr):
+    """The lane-layout FP32 KPM (kpm_registers 3: lane = column, rows in
+    registers, real and imaginary parts in two lane groups whose recurrences
+    meet only in the coefficient sums) for every lattice shape it has to
+    cover: several problems per warp (L <= 16, with an idle lane group when
+    32 / L is odd), two warps per problem (L > 16), right-hand side counts
+    that leave a block's last slot empty. P^{-1}, P^{-T} and P^{-1} P^{-T}
+    against the oracle's step-by-step KPM."""
+    w, x, ctx = _setup(L, T, seed=5, nr=nr)
+    m = D.model_of(w)
+    v = hi.gaussian_vectors(w, nr, seed=11)
+    refs = {
+        hg.HOL_PINV: np.stack([D.precond_inverse_apply(m, x, a) for a in v]),
+        hg.HOL_PINVT: np.stack([D.precond_inverse_apply(m, x, a, trans=True) for a in v]),
+    }
+    refs[hg.HOL_PINV_PINVT] = np.stack(
+        [D.precond_inverse_apply(m, x, D.precond_inverse_apply(m, x, a, trans=True)) for a in v])
+    with ctx:
+        ctx.set_option("kpm_registers", 3)
+        vt = torch.tensor(v, device=DEV, dtype=torch.float32)
+        for which, ref in refs.items():
+            out = torch.full_like(vt, float("nan"))
+            ctx.precond_apply(which, vt, out)
+            assert _rel(out.cpu().double().numpy(), ref) < 2e-5, (L, which)
+
+
 def test_precond_transpose_identity_and_spd():
     """<w, P^{-1} v> = <P^{-T} w, v> and <v, P^{-1} P^{-T} v> > 0 on the GPU."""
     w_, x, ctx = _setup(8, 40, std=1.5)
