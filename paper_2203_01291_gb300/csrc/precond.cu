@@ -1049,7 +1049,7 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     for (int d = 0; d < kKinTaps; ++d) ka.e[d] = c->kin_e[d];
     bool done = false;
     if constexpr (sizeof(R) == 4) {
-        if (c->kpm_reg && !c->exact && (c->L == 32 || c->L == 16)) {
+        if ((c->kpm_reg == 1 || c->kpm_reg == 2) && !c->exact && (c->L == 32 || c->L == 16)) {
             const float th = (float)c->th;
             const size_t csm = (size_t)ka.max_np * sizeof(float2);
             const float2* i2 = reinterpret_cast<const float2*>(h0);
