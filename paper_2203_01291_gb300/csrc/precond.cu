@@ -774,13 +774,14 @@ struct KLane {
     static constexpr int THREADS = G >= 2 ? 32 : 64;
 };
 
-template <int L>
+template <typename R, int L>
 __global__ void __launch_bounds__(KLane<L>::THREADS)
-    k_kpm_lane(const float2* __restrict__ vin, float2* __restrict__ vout,
+    k_kpm_lane(const typename Cx<R>::T2* __restrict__ vin, typename Cx<R>::T2* __restrict__ vout,
                const double* __restrict__ dbar, const double* __restrict__ scal,
                const int* __restrict__ npv, const double2* __restrict__ coef, int n_rhs, int Th,
-               int max_np, int mode, float th)
+               int max_np, int mode, R th)
 {
+    using C2 = typename Cx<R>::T2;
     pdl_wait();      // the input comes from the previous kernel of the stream
     const PdlTriggerAtExit pdl_at_exit;
     using K = KLane<L>;
@@ -796,32 +797,37 @@ __global__ void __launch_bounds__(KLane<L>::THREADS)
     const bool own = live && rhs_raw < n_rhs;        // stores its results
     const int rhs = rhs_raw < n_rhs ? rhs_raw : n_rhs - 1;
     const long off = ((long)rhs * Th + wq) * N + geo.ix;
-    const float* vin_f = reinterpret_cast<const float*>(vin);
-    float t[L], d[L];
+    const R* vin_f = reinterpret_cast<const R*>(vin);
+    R t[L], d[L];
 #pragma unroll
     for (int iy = 0; iy < L; ++iy) {
         t[iy] = vin_f[2 * (off + iy * L) + part];
-        d[iy] = (float)dbar[geo.ix + iy * L];
+        d[iy] = (R)dbar[geo.ix + iy * L];
     }
     const double bmin = scal[S_BMIN], bmax = scal[S_BMAX];
     const double db = bmax - bmin;
-    const float a = (float)(2.0 / db), c0 = (float)(-2.0 * bmin / db - 1.0);
+    const R a = (R)(2.0 / db), c0 = (R)(-2.0 * bmin / db - 1.0);
     const int np = npv[wq];
-    extern __shared__ float2 kl_cw[];   // this omega's coefficients, then (G = 1) the exchange
+    // this omega's coefficients (rounded to R once), then (G = 1) the exchange
+    extern __shared__ __align__(16) unsigned char kl_smem[];
+    C2* cw = reinterpret_cast<C2*>(kl_smem);
     for (int m = threadIdx.x; m < np; m += blockDim.x) {
         const double2 cm = coef[(long)wq * max_np + m];
-        kl_cw[m] = make_float2((float)cm.x, (float)cm.y);
+        C2 cr;
+        cr.x = (R)cm.x;
+        cr.y = (R)cm.y;
+        cw[m] = cr;
     }
-    float* xbuf = reinterpret_cast<float*>(kl_cw + max_np);   // [2][32][L]
+    R* xbuf = reinterpret_cast<R*>(cw + max_np);   // [2][32][L]
     __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
         const bool trans = (pass == 0);
         if (trans && !(mode & 1)) continue;
         if (!trans && !(mode & 2)) continue;
-        const float sgn = trans ? -1.0f : 1.0f;   // conj coefficients for the transpose
-        float A[L], B[L], prev[L];
+        const R sgn = trans ? R(-1) : R(1);   // conj coefficients for the transpose
+        R A[L], B[L], prev[L];
         {
-            const float2 cm = kl_cw[0];
+            const C2 cm = cw[0];
 #pragma unroll
             for (int iy = 0; iy < L; ++iy) {
                 A[iy] = cm.x * t[iy];
@@ -830,29 +836,29 @@ __global__ void __launch_bounds__(KLane<L>::THREADS)
             }
         }
         for (int m = 1; m < np; ++m) {
-            float b[L];
+            R b[L];
 #pragma unroll
             for (int iy = 0; iy < L; ++iy) b[iy] = trans ? t[iy] * d[iy] : t[iy];
             if (trans)
-                cb_apply_t<float, L>(b, geo, th);
+                cb_apply_t<R, L>(b, geo, th);
             else
-                cb_apply<float, L>(b, geo, th);
-            const float2 cm = kl_cw[m];
+                cb_apply<R, L>(b, geo, th);
+            const C2 cm = cw[m];
             // alpha_m = (m == 1 ? 1 : 2) (a Bbar + c0) alpha_{m-1} - (m == 1 ? 0 : alpha_{m-2})
-            const float f2 = (m == 1) ? 1.0f : 2.0f;
-            const float pm = (m == 1) ? 0.0f : 1.0f;
+            const R f2 = (m == 1) ? R(1) : R(2);
+            const R pm = (m == 1) ? R(0) : R(1);
 #pragma unroll
             for (int iy = 0; iy < L; ++iy) {
-                const float bv = trans ? b[iy] : b[iy] * d[iy];
-                const float x = f2 * fmaf(a, bv, c0 * t[iy]) - pm * prev[iy];
+                const R bv = trans ? b[iy] : b[iy] * d[iy];
+                const R x = f2 * fma(a, bv, c0 * t[iy]) - pm * prev[iy];
                 prev[iy] = t[iy];
                 t[iy] = x;
-                A[iy] = fmaf(cm.x, x, A[iy]);
-                B[iy] = fmaf(cm.y, x, B[iy]);
+                A[iy] = fma(cm.x, x, A[iy]);
+                B[iy] = fma(cm.y, x, B[iy]);
             }
         }
         // acc.re = A_0 - sgn B_1, acc.im = A_1 + sgn B_0: swap B with the other part
-        float Bo[L];
+        R Bo[L];
         if constexpr (K::G >= 2) {
             const int lane = threadIdx.x & 31;
             const int src = part == 0 ? lane + L : lane - L;   // the other part's lane
@@ -873,7 +879,7 @@ __global__ void __launch_bounds__(KLane<L>::THREADS)
         for (int iy = 0; iy < L; ++iy) t[iy] = part == 0 ? A[iy] - sgn * Bo[iy] : A[iy] + sgn * Bo[iy];
     }
     if (own) {
-        float* vout_f = reinterpret_cast<float*>(vout);
+        R* vout_f = reinterpret_cast<R*>(vout);
 #pragma unroll
         for (int iy = 0; iy < L; ++iy) vout_f[2 * (off + iy * L) + part] = t[iy];
     }
@@ -945,36 +951,40 @@ size_t fft_smem(const hol_ctx* c, int prec)
     return 2 * (size_t)c->T * (tile_sites(c, prec) / 2) * cs;   // two sites per column
 }
 
-template <int L>
-int run_kpm_lane_l(const hol_ctx* c, const float2* in, float2* out, int n_rhs, int Th,
-                   int max_np, int mode, cudaStream_t s)
+template <typename R, int L>
+int run_kpm_lane_l(const hol_ctx* c, const typename Cx<R>::T2* in, typename Cx<R>::T2* out,
+                   int n_rhs, int Th, int max_np, int mode, cudaStream_t s)
 {
     using K = KLane<L>;
-    const size_t sm = (size_t)max_np * sizeof(float2) +
-                      (K::G >= 2 ? 0 : (size_t)2 * 32 * L * sizeof(float));
+    const size_t sm = (size_t)max_np * sizeof(typename Cx<R>::T2) +
+                      (K::G >= 2 ? 0 : (size_t)2 * 32 * L * sizeof(R));
     static std::atomic<int> limit(0);   // raised once per instantiation (not a stream call)
     if ((int)sm > limit.load()) {
-        HOL_CUDA(cudaFuncSetAttribute((const void*)k_kpm_lane<L>,
+        HOL_CUDA(cudaFuncSetAttribute((const void*)k_kpm_lane<R, L>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         limit.store((int)sm);
     }
     const int grid = Th * ((n_rhs + K::PPB - 1) / K::PPB);
-    HOL_CUDA(launch_pdl(c, k_kpm_lane<L>, grid, K::THREADS, sm, s, in, out, c->dbar, c->scal,
-                        c->kpm.np, c->kpm.coef, n_rhs, Th, max_np, mode, (float)c->th));
+    HOL_CUDA(launch_pdl(c, k_kpm_lane<R, L>, grid, K::THREADS, sm, s, in, out, c->dbar, c->scal,
+                        c->kpm.np, c->kpm.coef, n_rhs, Th, max_np, mode, (R)c->th));
     HOL_CHECK_LAUNCH("k_kpm_lane");
     return HOL_OK;
 }
 
-// FP32 KPM in the lane layout (any even L; option kpm_registers = 3)
-int run_kpm_lane(const hol_ctx* c, const float2* in, float2* out, int n_rhs, int Th, int max_np,
-                 int mode, cudaStream_t s)
+// KPM in the lane layout: FP32, any even L
+template <typename R>
+int run_kpm_lane(const hol_ctx* c, const typename Cx<R>::T2* in, typename Cx<R>::T2* out,
+                 int n_rhs, int Th, int max_np, int mode, cudaStream_t s)
 {
-    switch (c->L) {
-#define X(LL) case LL: return run_kpm_lane_l<LL>(c, in, out, n_rhs, Th, max_np, mode, s);
-        X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32)
+    if constexpr (sizeof(R) == 4) {
+        switch (c->L) {
+#define X(LL) case LL: return run_kpm_lane_l<R, LL>(c, in, out, n_rhs, Th, max_np, mode, s);
+            X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30)
+            X(32)
 #undef X
+        }
     }
-    return set_error(HOL_EINVAL, "kpm lane layout: unsupported L=%d", c->L);
+    return set_error(HOL_EINVAL, "kpm lane layout: FP32 only (L=%d)", c->L);
 }
 
 int kpm_threads(const hol_ctx* c)
@@ -1079,12 +1089,17 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
             HOL_CHECK_LAUNCH("k_kpm_reg");
             done = true;
         } else if (c->kpm_reg == 3 && !c->exact) {
-            rc = run_kpm_lane(c, reinterpret_cast<const float2*>(h0),
-                              reinterpret_cast<float2*>(h1), n_rhs, ka.Th, ka.max_np, mode, s);
+            rc = run_kpm_lane<float>(c, reinterpret_cast<const float2*>(h0),
+                                     reinterpret_cast<float2*>(h1), n_rhs, ka.Th, ka.max_np,
+                                     mode, s);
             if (rc) return rc;
             done = true;
         }
     }
+    // (FP64 stays on the shared-memory kernel: the lane layout puts a
+    // problem's critical chain of FP64 steps on one warp, i.e. one SMSP's
+    // share of the FP64 pipe, and measured slower: 602 against 325 us per
+    // P^{-1} P^{-T} on the L = 16, Ltau = 160 trajectory's 2 rhs)
     if (!done) {
         const int kt = kpm_threads(c);
         const size_t ks = ((size_t)c->N * sizeof(C2) * (c->exact ? 2 : 1) + 15) / 16 * 16 +
