@@ -71,6 +71,9 @@ def args_parse():
                                       "chains", "prior", "split"],
                     default="trajectory", help="with --mode leg: run one of the other rows alone")
     ap.add_argument("--rhs", type=int, default=16)
+    ap.add_argument("--lattice", default=None,
+                    help="--mode precond: LxLtau of a chain lattice of the batching workload "
+                         "(omega0=1, alpha=1, x ~ N(0, 1)) instead of the L=32, Ltau=200 one")
     ap.add_argument("--prec", choices=["f32", "f64"], default="f32",
                     help="--mode matvec: the fused FP32 M^T M (f32) or FP64 M and M^T (f64)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
@@ -1292,12 +1295,16 @@ def run_precond(a):
     hb.build()
     torch.cuda.set_device(0)
     w = WORKLOAD
+    if a.lattice:
+        L, T = (int(t) for t in a.lattice.lower().split("x"))
+        w = hi.Workload(f"chain{L}", L=L, Ltau=T, omega0=1.0, alpha=1.0, x_std=1.0, seed=1000 + L)
     nr = a.rhs
     ctx = hg.Context.from_workload(w, max_rhs=nr)
     ctx.set_field(torch.tensor(hi.phonon_field(w), device="cuda"))
     apply_options(ctx, a.option)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    res = {"mode": "precond", "rhs": nr, "options": list(a.option)}
+    res = {"mode": "precond", "lattice": f"L={w.L} Ltau={w.Ltau}", "rhs": nr,
+           "options": list(a.option), "kpm_registers": ctx.get_option("kpm_registers")}
     for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
         v = torch.tensor(hi.gaussian_vectors(w, nr, seed=5), device="cuda", dtype=dt)
         z = torch.empty_like(v)
