@@ -557,6 +557,13 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  *                       default; smaller values shorten the series (a cheaper,
  *                       less exact P^{-1}). 1..400; takes effect at the next
  *                       hol_set_field or installed Arnoldi bounds
+ *   "fused_pc_update"   preconditioned CG (both precisions): the vector update
+ *                       of each iteration (r -= alpha q, the deferred x
+ *                       update, the r.r partials) runs inside the forward
+ *                       tau transform of the preconditioner applied to the
+ *                       new r, one kernel and one pass over r fewer per
+ *                       iteration (0/1, default 1). The iteration is the
+ *                       same up to the grouping of the r.r partials
  *   "kpm_queue"         FP32 register KPM (kpm_registers 1 or 2): 0 one block
  *                       per (omega, rhs) problem; k in 1..8 a persistent grid
  *                       of k blocks per multiprocessor taking the problems

@@ -28,6 +28,7 @@
 
 #include "cb.cuh"
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace hol {
 namespace {
@@ -63,20 +64,6 @@ struct V4<double> {
     }
 };
 
-// Block sum of a double (blockDim a multiple of 32, <= 1024); valid in thread 0.
-__device__ __forceinline__ double block_sum(double v)
-{
-    __shared__ double red[32];
-    v = warp_sum(v);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
-    return s;
-}
-
 // The operands of one float4 element of the update kernel (x, p, p_prev
 // only when the x update is folded in).
 template <typename R>
@@ -95,25 +82,6 @@ struct Ops {
     }
 };
 
-// Block sum of a compensated float pair, converted to FP64 once (thread 0).
-__device__ __forceinline__ double block_sum_f2(F2 v)
-{
-    __shared__ float red_hi[32], red_lo[32];
-    v = f2_warp_sum(v);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        red_hi[w] = v.hi;
-        red_lo[w] = v.lo;
-    }
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0) {
-        F2 t{0.0f, 0.0f};
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = f2_add(t, F2{red_hi[k], red_lo[k]});
-        s = f2_to_double(t);
-    }
-    return s;
-}
 
 // r -= alpha q with the new (r.r) partials; alpha = dz / pq from partials.
 // The x update may be deferred by one iteration (FOLD 0 stores alpha for
@@ -563,6 +531,10 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
     int pstride64 = 0, pq_n64 = 0;   // the FP64 CG's M keeps its own grouping
     fp64_cg_geom(c, n_rhs, &pstride64, &pq_n64);
     const int dz_n = pc ? precond_tiles(c, prec) : nb2;   // partial count of r.z
+    // PCG: the vector update inside the preconditioner's forward transform;
+    // the r.r estimate then has one partial per transform tile
+    const bool fuse_pc = pc && c->pc_fuse;
+    const int est_n = fuse_pc ? dz_n : nb2;
     int* act_d = c->mask;
     int* rel_d = c->mask + c->p.max_rhs;
     int* act_h = c->hflag;
@@ -686,6 +658,17 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                 if (rc) return rc;
                 timer_stop(c, KT_OPERATOR, s);
                 pp = 1 - pp;
+                if (fuse_pc) {   // the update runs inside the preconditioner's forward transform
+                    const PcUpd u{e32, p32[pp], p32[1 - pp], q32, act_d, B.pq, pstride, pq_n,
+                                  B.dz[cur], dz_n, rr_dst, c->alpha_buf, fold};
+                    timer_start(c, KT_PRECOND, s, (double)n_rhs);
+                    rc = precond_apply_upd(c, HOL_F32, r32, z32, n_rhs, &u, B.dz[1 - cur], s);
+                    timer_stop(c, KT_PRECOND, s);
+                    if (rc) return rc;
+                    cur = 1 - cur;
+                    first = 0;
+                    continue;
+                }
                 timer_start(c, KT_UPDATE, s, n_active * nd * upd_bytes);
                 auto* upd = fold == 0 ? k_cg_update<float, 0>
                                       : fold == 1 ? k_cg_update<float, 1> : k_cg_update<float, 2>;
@@ -703,6 +686,17 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
                 if (rc) return rc;
                 timer_stop(c, KT_OPERATOR, s);
                 pp = 1 - pp;
+                if (fuse_pc) {
+                    const PcUpd u{v, p64[pp], p64[1 - pp], q64, act_d, B.pq, pstride64, pq_n64,
+                                  B.dz[cur], dz_n, rr_dst, c->alpha_buf, fold};
+                    timer_start(c, KT_PRECOND, s, (double)n_rhs);
+                    rc = precond_apply_upd(c, HOL_F64, r64, z64, n_rhs, &u, B.dz[1 - cur], s);
+                    timer_stop(c, KT_PRECOND, s);
+                    if (rc) return rc;
+                    cur = 1 - cur;
+                    first = 0;
+                    continue;
+                }
                 timer_start(c, KT_UPDATE, s, n_active * nd * 2.0 * upd_bytes);
                 auto* upd = fold == 0 ? k_cg_update<double, 0>
                                       : fold == 1 ? k_cg_update<double, 1> : k_cg_update<double, 2>;
@@ -724,7 +718,7 @@ static int cg_run(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_c
         // waits for the host); an estimate below tol makes the end of the
         // chunk then in flight a synchronisation point.
         double* est_h = hb + (2 + q) * R;
-        if ((rc = rows_enqueue(est_bank(cur), pc ? nb2 : cnt[cur], kRedStride, n_rhs,
+        if ((rc = rows_enqueue(est_bank(cur), pc ? est_n : cnt[cur], kRedStride, n_rhs,
                                B.red + (1 + q) * R, est_h, evp.ev[q], s)))
             return rc;
         bool sync = k_it >= o->max_iter;
@@ -1451,6 +1445,8 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
     int pstride64 = 0, pq_n64 = 0;   // the FP64 CG's M keeps its own grouping
     fp64_cg_geom(c, n_rhs, &pstride64, &pq_n64);
     const int dz_n = pc ? precond_tiles(c, mixed ? HOL_F32 : HOL_F64) : nb2;
+    const bool fuse_pc = pc && c->pc_fuse;   // as in cg_run
+    const int est_n = fuse_pc ? dz_n : nb2;
     int* act_d = c->mask;
     int* rel_d = c->mask + c->p.max_rhs;
     const DcgState d = dcg_state(c);
@@ -1520,6 +1516,16 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
                                      (!pc && (c->handoff & 2)) ? c->beta_now : nullptr);
                 if (r2) return r2;
                 pp = 1 - pp;
+                if (fuse_pc) {
+                    const PcUpd u{e32, p32[pp], p32[1 - pp], q32, act_d, B.pq, pstride, pq_n,
+                                  B.dz[cur], dz_n, rr_dst, c->alpha_buf, fold};
+                    if ((r2 = precond_apply_upd(c, HOL_F32, r32, z32, n_rhs, &u, B.dz[1 - cur],
+                                                cs)))
+                        return r2;
+                    cur = 1 - cur;
+                    first = 0;
+                    continue;
+                }
                 auto* upd = fold == 0 ? k_cg_update<float, 0>
                                       : fold == 1 ? k_cg_update<float, 1> : k_cg_update<float, 2>;
                 HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, cs, e32, r32, p32[pp], p32[1 - pp], q32, n,
@@ -1534,6 +1540,16 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
                 r2 = launch_MT(c, HOL_F64, w64, q64, n_rhs, act_d, cs);
                 if (r2) return r2;
                 pp = 1 - pp;
+                if (fuse_pc) {
+                    const PcUpd u{v, p64[pp], p64[1 - pp], q64, act_d, B.pq, pstride64, pq_n64,
+                                  B.dz[cur], dz_n, rr_dst, c->alpha_buf, fold};
+                    if ((r2 = precond_apply_upd(c, HOL_F64, r64, z64, n_rhs, &u, B.dz[1 - cur],
+                                                cs)))
+                        return r2;
+                    cur = 1 - cur;
+                    first = 0;
+                    continue;
+                }
                 auto* upd = fold == 0 ? k_cg_update<double, 0>
                                       : fold == 1 ? k_cg_update<double, 1> : k_cg_update<double, 2>;
                 HOL_CUDA(launch_pdl(c, upd, g2, 256, 0, cs, v, r64, p64[pp], p64[1 - pp], q64, n,
@@ -1550,8 +1566,9 @@ int cg_run_dev(hol_ctx* c, const double* b, double* v, int n_rhs, const hol_cg_o
         cudaGraphConditionalHandle h_if;
         int r2 = cond_handle(cs, &h_if);
         if (r2) return r2;
-        k_dcg_decide<<<1, kDcgThreads, 0, cs>>>(est_bank(cur), nb2, n_rhs, chk, o->tol, rel_every,
-                                                o->max_iter, act_d, rel_d, d, h_if);
+        k_dcg_decide<<<1, kDcgThreads, 0, cs>>>(est_bank(cur), pc ? est_n : nb2, n_rhs, chk,
+                                                o->tol, rel_every, o->max_iter, act_d, rel_d, d,
+                                                h_if);
         HOL_CHECK_LAUNCH("k_dcg_decide");
         cudaGraph_t body;
         if ((r2 = cond_node(cs, h_if, cudaGraphCondTypeIf, &body))) return r2;

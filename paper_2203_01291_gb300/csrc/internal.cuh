@@ -247,6 +247,7 @@ struct hol_ctx {
                          // blocks per multiprocessor (0: one block per problem)
     int* kpm_q;          // its work queue [2] (next problem, finished blocks; zero between launches)
     double kpm_a1, kpm_a2;   // constants of the Chebyshev order heuristic (1, 1 by default)
+    int pc_fuse;             // PCG: vector update fused into the preconditioner's transform
 };
 
 namespace hol {
@@ -282,7 +283,30 @@ enum MtEpilogue { MT_PLAIN = 0, MT_RESID = 1 };
 extern std::atomic<int> g_occ64[2][4][33][5];
 void occ64_warm(const hol_ctx* c);         // matvec.cu (checkerboard)
 void occ64_warm_exact(const hol_ctx* c);   // exact.cu
-// Stride and count of the |Mp|^2 unit partials that the FP64 CG's M
+// PCG: the CG vector update (r -= alpha q with alpha = (r.z) / (p.q) from
+// the partials, the deferred x update of k_cg_update's FOLD modes, the
+// partials of the new r.r) fused into the forward tau transform of the
+// preconditioner application that follows it (precond_apply_upd).
+struct PcUpd {
+    void* x;               // solution accumulator (FP32 e or FP64 x)
+    const void* p;         // this iteration's direction
+    const void* pprev;     // the previous one (fold 2)
+    const void* q;         // A p
+    const int* mask;       // active right-hand sides
+    const double* pq_part; // p.q unit partials
+    int pq_stride, pq_n;
+    const double* dz_part; // r.z partials (kRedStride per rhs)
+    int dz_n;
+    double* rr_out;        // new r.r partials, one per transform tile
+    double* alpha_buf;     // alpha of the previous iteration (fold 0 writes, 2 reads)
+    int fold;              // 0, 1 or 2 as k_cg_update's FOLD
+};
+// z = P^{-1} P^{-T} r after r has been updated in place as `u` says; dot_part
+// receives the r.z partials (precond_tiles per rhs). prec HOL_F32 or HOL_F64.
+int precond_apply_upd(hol_ctx* c, int prec, void* r, void* z, int n_rhs, const PcUpd* u,
+                      double* dot_part, cudaStream_t s);
+
+// Stride and count of the |Mp|^2 unit partials that the FP64 CG's M// Stride and count of the |Mp|^2 unit partials that the FP64 CG's M
 // (launch_M_upd64) writes for n_rhs right-hand sides.
 void fp64_cg_geom(const hol_ctx* c, int n_rhs, int* pstride, int* nrun);
 

@@ -32,6 +32,7 @@
 #include "cb.cuh"
 #include "fft.cuh"
 #include "internal.cuh"
+#include "reduce.cuh"
 
 namespace hol {
 namespace {
@@ -134,6 +135,132 @@ __global__ void __launch_bounds__(256) k_tau_fwd(const R* __restrict__ v,
             const C2 z = res[w * TH + c];
             const C2 zm = res[(T - 1 - w) * TH + c];
             // X_a = (z + conj zm) / 2,  X_b = (z - conj zm) / (2 i)
+            st_cpair(vh + ob + (long)w * N + i, Cx<R>::mk(hs * (z.x + zm.x), hs * (z.y - zm.y)),
+                     Cx<R>::mk(hs * (z.y + zm.y), hs * (zm.x - z.x)));
+        }
+    }
+}
+
+// The forward transform with the CG update of the PCG iteration fused into
+// its load phase (PcUpd): each element of r is read once, updated
+// (r -= alpha q, and the x accumulator by the fold mode's terms), written
+// back, summed into this tile's r.r partial and transformed. alpha is formed
+// by one warp per block from the partials, as k_cg_update forms it. Masked
+// right-hand sides are transformed without an update.
+template <typename R>
+struct PcUpdK {
+    R* x;
+    const R* p;
+    const R* pp;
+    const R* q;
+    const int* mask;
+    const double* pq_part;
+    int pq_stride, pq_n;
+    const double* dz_part;
+    int dz_n;
+    double* rr_out;
+    double* alpha_buf;
+    int fold;
+};
+
+template <typename R, int TC = 0, int TSC = 0>
+__global__ void __launch_bounds__(256) k_tau_fwd_upd(R* __restrict__ v,
+                                                     typename Cx<R>::T2* __restrict__ vh,
+                                                     const typename Cx<R>::T2* __restrict__ w2,
+                                                     int T_, int N, int TS_, RadixPlan plan,
+                                                     R scale, PcUpdK<R> u)
+{
+    pdl_wait();      // p, q and the partials come from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
+    using C2 = typename Cx<R>::T2;
+    const int T = TC > 0 ? TC : T_;
+    const int TS = TSC > 0 ? TSC : TS_;
+    const int TH = TS / 2;                 // transform columns
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C2* a = reinterpret_cast<C2*>(smem_raw);
+    C2* b = a + (long)T * TH;
+    const int rhs = blockIdx.y;
+    const int i0 = blockIdx.x * TS;
+    const long base = (long)rhs * T * N;
+    const bool act = u.mask == nullptr || u.mask[rhs] != 0;
+    __shared__ double s_alpha, s_alpha_prev;
+    if (threadIdx.x < 32) {
+        double al = 0.0, alp = 0.0;
+        if (act) {
+            const double pq = warp_sum_array(u.pq_part + (long)rhs * u.pq_stride, u.pq_n);
+            const double dz = warp_sum_array(u.dz_part + (long)rhs * kRedStride, u.dz_n);
+            al = cg_ratio(dz, pq);
+            if (u.fold == 2) alp = u.alpha_buf[rhs];
+        }
+        if (threadIdx.x == 0) {
+            s_alpha = al;
+            s_alpha_prev = alp;
+        }
+    }
+    __syncthreads();
+    const R al = (R)s_alpha, ap = (R)s_alpha_prev;
+    if (act && u.fold == 0 && blockIdx.x == 0 && threadIdx.x == 0) u.alpha_buf[rhs] = s_alpha;
+    double acc = 0.0;
+    F2 acc2{0.0f, 0.0f};
+    for (int item = threadIdx.x; item < T * TH; item += blockDim.x) {
+        const int c = item % TH, tau = item / TH;
+        const int i = i0 + 2 * c;          // N is even, so i < N implies i + 1 < N
+        R xa = R(0), xb = R(0);
+        if (i < N) {
+            const long o = base + (long)tau * N + i;
+            ld_pair(v + o, xa, xb);
+            if (act) {
+                R qa, qb;
+                ld_pair(u.q + o, qa, qb);
+                if (u.fold != 0) {
+                    R ea, eb, pa, pb;
+                    ld_pair(u.x + o, ea, eb);
+                    ld_pair(u.p + o, pa, pb);
+                    if (u.fold == 2) {
+                        R qa2, qb2;
+                        ld_pair(u.pp + o, qa2, qb2);
+                        ea = fma(ap, qa2, ea);
+                        eb = fma(ap, qb2, eb);
+                    }
+                    ea = fma(al, pa, ea);
+                    eb = fma(al, pb, eb);
+                    st_pair(u.x + o, ea, eb);
+                }
+                xa = fma(-al, qa, xa);
+                xb = fma(-al, qb, xb);
+                st_pair(v + o, xa, xb);
+                const R part = fma(xa, xa, xb * xb);
+                if constexpr (sizeof(R) == 4)
+                    acc2 = f2_add(acc2, (float)part);
+                else
+                    acc += (double)part;
+            }
+        }
+        const C2 t = tw<R>(w2, tau, T);    // exp(-i pi tau / T)
+        a[tau * TH + c] = Cx<R>::mk(xa * t.x - xb * t.y, xa * t.y + xb * t.x);
+    }
+    {
+        double sum;
+        if constexpr (sizeof(R) == 4)
+            sum = block_sum_f2(acc2);
+        else
+            sum = block_sum(acc);
+        if (act && threadIdx.x == 0) u.rr_out[(long)rhs * kRedStride + blockIdx.x] = sum;
+    }
+    C2* res;
+    if constexpr (TC > 0)
+        res = fft_tau_ct<R, TC, TSC / 2, 256>(a, b, w2);
+    else
+        res = fft_tau<R>(a, b, w2, T, TH, plan);
+    const int Th = T / 2;
+    const long ob = (long)rhs * Th * N;
+    const R hs = R(0.5) * scale;
+    for (int item = threadIdx.x; item < Th * TH; item += blockDim.x) {
+        const int c = item % TH, w = item / TH;
+        const int i = i0 + 2 * c;
+        if (i < N) {
+            const C2 z = res[w * TH + c];
+            const C2 zm = res[(T - 1 - w) * TH + c];
             st_cpair(vh + ob + (long)w * N + i, Cx<R>::mk(hs * (z.x + zm.x), hs * (z.y - zm.y)),
                      Cx<R>::mk(hs * (z.y + zm.y), hs * (zm.x - z.x)));
         }
@@ -1002,10 +1129,11 @@ int set_smem_attr(const void* fn, size_t bytes)
     return smem_raise(fn, bytes);
 }
 
-// fwd transform, KPM (mode), inverse transform (+ optional dot partials)
+// fwd transform, KPM (mode), inverse transform (+ optional dot partials);
+// with `up`, the CG update of v (in place) is fused into the fwd transform
 template <typename R>
 int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rdot,
-                double* dot_part, cudaStream_t s)
+                double* dot_part, cudaStream_t s, const PcUpd* up = nullptr)
 {
     using C2 = typename Cx<R>::T2;
     const int prec = sizeof(R) == 8 ? HOL_F64 : HOL_F32;
@@ -1021,16 +1149,20 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     // the configured lengths get transforms specialised at compile time
     constexpr int TSW = sizeof(R) == 8 ? 16 : 32;   // tile_sites on the largest lattice
     using FwdK = void (*)(const R*, C2*, const C2*, int, int, int, RadixPlan, R);
+    using FwdU = void (*)(R*, C2*, const C2*, int, int, int, RadixPlan, R, PcUpdK<R>);
     using InvK = void (*)(const C2*, R*, const C2*, int, int, int, RadixPlan, R, const R*, double*);
     FwdK fwd = k_tau_fwd<R>;
+    FwdU fwdu = k_tau_fwd_upd<R>;
     InvK inv = k_tau_inv<R>;
 #define HOL_TAU_CT(TT)                                    \
     case TT:                                              \
         if (TS == TSW) {                                  \
             fwd = k_tau_fwd<R, TT, TSW>;                  \
+            fwdu = k_tau_fwd_upd<R, TT, TSW>;             \
             inv = k_tau_inv<R, TT, TSW>;                  \
         } else if (TS == kSmallTile) {                    \
             fwd = k_tau_fwd<R, TT, kSmallTile>;           \
+            fwdu = k_tau_fwd_upd<R, TT, kSmallTile>;      \
             inv = k_tau_inv<R, TT, kSmallTile>;           \
         }                                                 \
         break;
@@ -1042,11 +1174,20 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
     default: break;
     }
 #undef HOL_TAU_CT
-    if ((rc = set_smem_attr<R>((const void*)fwd, sm))) return rc;
+    if ((rc = set_smem_attr<R>(up ? (const void*)fwdu : (const void*)fwd, sm))) return rc;
     if ((rc = set_smem_attr<R>((const void*)inv, sm))) return rc;
     const R isq = (R)(1.0 / sqrt((double)c->T));
-    HOL_CUDA(launch_pdl(c, fwd, gf, 256, sm, s, v, h0, w2, c->T, c->N, TS, plan, isq));
-    HOL_CHECK_LAUNCH("k_tau_fwd");
+    if (up) {
+        PcUpdK<R> uk{(R*)up->x, (const R*)up->p, (const R*)up->pprev, (const R*)up->q, up->mask,
+                     up->pq_part, up->pq_stride, up->pq_n, up->dz_part, up->dz_n, up->rr_out,
+                     up->alpha_buf, up->fold};
+        HOL_CUDA(launch_pdl(c, fwdu, gf, 256, sm, s, const_cast<R*>(v), h0, w2, c->T, c->N, TS,
+                            plan, isq, uk));
+        HOL_CHECK_LAUNCH("k_tau_fwd_upd");
+    } else {
+        HOL_CUDA(launch_pdl(c, fwd, gf, 256, sm, s, v, h0, w2, c->T, c->N, TS, plan, isq));
+        HOL_CHECK_LAUNCH("k_tau_fwd");
+    }
     KpmArgs ka;
     ka.L = c->L;
     ka.N = c->N;
@@ -1137,6 +1278,16 @@ int precond_apply_impl(hol_ctx* c, int prec, const void* v, void* out, int n_rhs
                                    (const double*)rdot, dot_part, s);
     return precond_run<float>(c, (const float*)v, (float*)out, n_rhs, mode, (const float*)rdot,
                               dot_part, s);
+}
+
+int precond_apply_upd(hol_ctx* c, int prec, void* r, void* z, int n_rhs, const PcUpd* u,
+                      double* dot_part, cudaStream_t s)
+{
+    if (prec == HOL_F64)
+        return precond_run<double>(c, (const double*)r, (double*)z, n_rhs, 3, (const double*)r,
+                                   dot_part, s, u);
+    return precond_run<float>(c, (const float*)r, (float*)z, n_rhs, 3, (const float*)r, dot_part,
+                              s, u);
 }
 
 // Twiddles w2[k] = exp(-i pi k / T) (long double on the host) and the

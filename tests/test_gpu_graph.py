@@ -24,11 +24,13 @@ def _built():
 DEV = "cuda"
 
 
-def _both(w, nr, **kw):
+def _both(w, nr, options=None, **kw):
     x = torch.tensor(hi.phonon_field(w), device=DEV)
     R = torch.tensor(hi.gaussian_vectors(w, nr, seed=w.seed + 1), device=DEV)
     with hg.Context.from_workload(w, max_rhs=nr) as ctx:
         ctx.set_field(x)
+        for name, value in (options or {}).items():
+            ctx.set_option(name, value)
         b = torch.empty_like(R)
         ctx.fermion_matvec(hg.HOL_OP_MT, R, b)
         v0 = torch.empty_like(b)
@@ -40,11 +42,12 @@ def _both(w, nr, **kw):
 
 
 @pytest.mark.parametrize("prec", [hg.HOL_F64, hg.HOL_F32])
-@pytest.mark.parametrize("precond", [False, True])
-def test_graph_solve_equals_host_solve(prec, precond):
+@pytest.mark.parametrize("precond,fused", [(False, 0), (True, 0), (True, 1)])
+def test_graph_solve_equals_host_solve(prec, precond, fused):
     w = hi.Workload("g", L=8, Ltau=24, alpha=1.2, omega0=1.0, x_std=1.0, seed=71)
     it0, r0, v0, it1, r1, v1 = _both(w, 3, tol=1e-10, prec=prec, precond=precond,
-                                     reliable_every=20, check_every=4)
+                                     reliable_every=20, check_every=4,
+                                     options={"fused_pc_update": fused})
     assert np.array_equal(it0, it1) and np.array_equal(r0, r1)
     assert np.array_equal(v0, v1)
     assert np.all(r1 < 1e-10)

@@ -152,8 +152,44 @@ def test_precond_exact_when_x_constant_in_tau():
         assert D.rel_residual(m, xc, b[0], v.cpu().numpy()[0]) < 1e-10
 
 
+@pytest.mark.parametrize("prec", [hg.HOL_F32, hg.HOL_F64])
+@pytest.mark.parametrize("L,T", [(12, 40), (16, 160), (28, 24)])
+def test_pcg_fused_update_matches_unfused(prec, L, T):
+    """PCG with the vector update fused into the preconditioner's forward
+    transform (fused_pc_update) runs the same iteration as the separate
+    update kernel: the same iteration counts (up to the regrouped r.r
+    partials of the convergence estimate, which can move a chunk decision by
+    one chunk), certified residuals, and solutions within the residual's
+    bound of each other and of the oracle's residual check."""
+    w = hi.Workload("f", L=L, Ltau=T, alpha=1.0, omega0=1.0, x_std=1.0, seed=40 + L)
+    x = hi.phonon_field(w)
+    R = hi.gaussian_vectors(w, 3, seed=41)
+    tol = 1e-8 if prec == hg.HOL_F32 else 1e-10
+    out = {}
+    with hg.Context.from_workload(w, max_rhs=3) as ctx:
+        ctx.set_field(torch.tensor(x, device=DEV))
+        Rt = torch.tensor(R, device=DEV)
+        bt = torch.empty_like(Rt)
+        ctx.fermion_matvec(hg.HOL_OP_MT, Rt, bt)
+        for fused in (0, 1):
+            ctx.set_option("fused_pc_update", fused)
+            v = torch.empty_like(bt)
+            its, res = ctx.cg_solve(bt, v, tol=tol, prec=prec, precond=True, check_every=2,
+                                    reliable_every=20)
+            out[fused] = (its, res, v.cpu().numpy())
+        b = bt.cpu().numpy()
+    for fused in (0, 1):
+        assert np.all(out[fused][1] < tol)
+    assert np.all(np.abs(out[0][0] - out[1][0]) <= 2)
+    d = np.abs(out[0][2] - out[1][2]).max() / np.abs(out[0][2]).max()
+    assert d < 1e-4 if prec == hg.HOL_F32 else d < 1e-6
+    for k in range(3):
+        assert MF.rel_residual(w, x, b[k], out[1][2][k]) < 1.01 * tol
+
+
+@pytest.mark.parametrize("fused", [0, 1])
 @pytest.mark.parametrize("prec,tol", [(hg.HOL_F64, 1e-12), (hg.HOL_F32, 1e-8)])
-def test_pcg_tiny_vs_lu(prec, tol):
+def test_pcg_tiny_vs_lu(prec, tol, fused):
     w = hi.WORKLOADS["tiny"]
     m = D.model_of(w)
     x = hi.phonon_field(w)
@@ -165,6 +201,7 @@ def test_pcg_tiny_vs_lu(prec, tol):
     _, it_ref = D.pcg(m, x, b[0], tol=tol, precond=True)
     with hg.Context.from_workload(w, max_rhs=2) as ctx:
         ctx.set_field(torch.tensor(x, device=DEV))
+        ctx.set_option("fused_pc_update", fused)   # the update inside the forward transform
         bt = torch.tensor(b, device=DEV)
         v = torch.empty_like(bt)
         its, res = ctx.cg_solve(bt, v, tol=tol, precond=True, prec=prec, check_every=1,
