@@ -1012,6 +1012,173 @@ __global__ void __launch_bounds__(KLane<L>::THREADS)
     }
 }
 
+// ------------------------------------------------ KPM, banded lane layout
+// FP64 KPM in the scalar lane layout with each problem spread over several
+// warps: lane = column; the rows are cut into NB bands of RB = L / NB rows
+// (RB even, so the even y-bonds stay inside a band); lane group (p, b) holds
+// band b of part p (0: real, 1: imaginary). FP64 work is bound by the SM's
+// FP64 pipe, which one warp can only use a quarter of (its SMSP's share), so
+// a problem's chain of dependent Bbar applies needs its work on several
+// warps: 2 NB lane groups over at least four warps. The odd y-bonds across
+// band edges are exchanged through shared memory, one barrier per colour-4
+// application (two alternating slot sets); the x-bonds are shuffles within
+// the lane group; the two parts meet once per series as in k_kpm_lane.
+template <int L>
+struct KBand {
+    // bands per part: RB = L / NB even, 2 NB lane groups over as many warps
+    // as that gives. Measured (P^{-1} P^{-T}, 2 rhs, against the
+    // shared-memory kernel): L = 8 82 / 215 us, 12 114 / 222, 16 173 / 309
+    // (Ltau = 160; 191 with NB = 4), 24 386 / 454, 28 454 / 544, 32 849 /
+    // 985 (Ltau = 200; 862 with NB = 8); L = 20 was slower (320 / 304) and
+    // keeps the shared-memory kernel, as do the sizes not listed
+    static constexpr int NB = L == 4 ? 2 : L == 6 ? 3 : L == 8 ? 4 : L == 10 ? 5 : L == 12 ? 6
+                            : L == 14 ? 7 : L == 16 ? 8 : L == 18 ? 3 : L == 24 ? 6 : L == 28 ? 7
+                            : L == 32 ? 4 : 0;
+    static constexpr int RB = NB > 0 ? L / NB : 0;
+    static constexpr int G = 32 / L;                           // lane groups per warp
+    static constexpr int GROUPS = 2 * NB;
+    static constexpr int WARPS = (GROUPS + G - 1) / G;
+    static constexpr int THREADS = 32 * WARPS;
+    static constexpr bool OK = NB > 0 && RB % 2 == 0;
+};
+
+template <int L>
+__global__ void __launch_bounds__(KBand<L>::THREADS > 0 ? KBand<L>::THREADS : 32)
+    k_kpm_band(const double2* __restrict__ vin, double2* __restrict__ vout,
+               const double* __restrict__ dbar, const double* __restrict__ scal,
+               const int* __restrict__ npv, const double2* __restrict__ coef, int n_rhs, int Th,
+               int max_np, int mode, double th)
+{
+    pdl_wait();      // the input comes from the previous kernel of the stream
+    const PdlTriggerAtExit pdl_at_exit;
+    using K = KBand<L>;
+    constexpr int N = L * L, RB = K::RB, NB = K::NB;
+    const LaneGeom<L> geo;
+    const int gi = (int)(threadIdx.x >> 5) * K::G + geo.g;     // lane group of the block
+    const bool live = geo.ok && gi < K::GROUPS;
+    const int gs = live ? gi : 0;                              // idle groups shadow group 0
+    const int part = gs / NB, band = gs - part * NB;
+    const int wq = blockIdx.x / n_rhs, rhs = blockIdx.x - wq * n_rhs;
+    const long off = ((long)rhs * Th + wq) * N + geo.ix;
+    const int row0 = band * RB;
+    const double* vin_f = reinterpret_cast<const double*>(vin);
+    double t[RB], d[RB];
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        t[k] = vin_f[2 * (off + (row0 + k) * L) + part];
+        d[k] = dbar[geo.ix + (row0 + k) * L];
+    }
+    const double bmin = scal[S_BMIN], bmax = scal[S_BMAX];
+    const double db = bmax - bmin;
+    const double a = 2.0 / db, c0 = -2.0 * bmin / db - 1.0;
+    const int np = npv[wq];
+    extern __shared__ __align__(16) unsigned char kb_smem[];
+    double2* cw = reinterpret_cast<double2*>(kb_smem);
+    for (int m = threadIdx.x; m < np; m += blockDim.x) cw[m] = coef[(long)wq * max_np + m];
+    // band-edge slots [par][part][band][first / last row][column], then the B exchange
+    double* eb = reinterpret_cast<double*>(cw + max_np);
+    double* xb = eb + 2 * 2 * NB * 2 * L;                      // [part][band][RB][column]
+    __syncthreads();
+    auto edge = [&](int par, int p, int b, int which) -> double* {
+        return eb + ((((par * 2 + p) * NB + b) * 2 + which) * L);
+    };
+    int par = 0;
+    // colour 4 (odd y-bonds): pairs (1, 2), ..., inside the band; the band's
+    // last row with the next band's first, its first with the previous
+    // band's last (through shared memory)
+    auto colour4 = [&](double (&c)[RB]) {
+        if (live) {
+            edge(par, part, band, 0)[geo.ix] = c[0];
+            edge(par, part, band, 1)[geo.ix] = c[RB - 1];
+        }
+        __syncthreads();
+        const int bn = band + 1 == NB ? 0 : band + 1, bp = band == 0 ? NB - 1 : band - 1;
+        const double dn = edge(par, part, bn, 0)[geo.ix];
+        const double upv = edge(par, part, bp, 1)[geo.ix];
+        par ^= 1;   // the next exchange writes the other slot set
+#pragma unroll
+        for (int k = 1; k + 1 < RB; k += 2) {
+            const double x = c[k], y = c[k + 1];
+            c[k] = fma(th, y, x);
+            c[k + 1] = fma(th, x, y);
+        }
+        c[RB - 1] = fma(th, dn, c[RB - 1]);
+        c[0] = fma(th, upv, c[0]);
+    };
+    auto colour3 = [&](double (&c)[RB]) {
+#pragma unroll
+        for (int k = 0; k < RB; k += 2) {
+            const double x = c[k], y = c[k + 1];
+            c[k] = fma(th, y, x);
+            c[k + 1] = fma(th, x, y);
+        }
+    };
+    auto xbond = [&](double (&c)[RB], int partner) {
+#pragma unroll
+        for (int k = 0; k < RB; ++k) c[k] = fma(th, __shfl_sync(kFull, c[k], partner), c[k]);
+    };
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool trans = (pass == 0);
+        if (trans && !(mode & 1)) continue;
+        if (!trans && !(mode & 2)) continue;
+        const double sgn = trans ? -1.0 : 1.0;   // conj coefficients for the transpose
+        double A[RB], B[RB], prev[RB];
+        {
+            const double2 cm = cw[0];
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                A[k] = cm.x * t[k];
+                B[k] = cm.y * t[k];
+                prev[k] = t[k];
+            }
+        }
+        for (int m = 1; m < np; ++m) {
+            double b[RB];
+#pragma unroll
+            for (int k = 0; k < RB; ++k) b[k] = trans ? t[k] * d[k] : t[k];
+            if (trans) {   // C^T: colour 4 first
+                colour4(b);
+                colour3(b);
+                xbond(b, geo.p2);
+                xbond(b, geo.p1);
+            } else {
+                xbond(b, geo.p1);
+                xbond(b, geo.p2);
+                colour3(b);
+                colour4(b);
+            }
+            const double2 cm = cw[m];
+            const double f2 = (m == 1) ? 1.0 : 2.0;
+            const double pm = (m == 1) ? 0.0 : 1.0;
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                const double bv = trans ? b[k] : b[k] * d[k];
+                const double x = f2 * fma(a, bv, c0 * t[k]) - pm * prev[k];
+                prev[k] = t[k];
+                t[k] = x;
+                A[k] = fma(cm.x, x, A[k]);
+                B[k] = fma(cm.y, x, B[k]);
+            }
+        }
+        // acc.re = A_0 - sgn B_1, acc.im = A_1 + sgn B_0
+        if (live)
+#pragma unroll
+            for (int k = 0; k < RB; ++k) xb[((part * NB + band) * RB + k) * L + geo.ix] = B[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            const double bo = xb[(((1 - part) * NB + band) * RB + k) * L + geo.ix];
+            t[k] = part == 0 ? A[k] - sgn * bo : A[k] + sgn * bo;
+        }
+        __syncthreads();   // xb is rewritten by the next series
+    }
+    if (live) {
+        double* vout_f = reinterpret_cast<double*>(vout);
+#pragma unroll
+        for (int k = 0; k < RB; ++k) vout_f[2 * (off + (row0 + k) * L) + part] = t[k];
+    }
+}
+
 // N_P(omega) and c_m(omega), m < N_P, one block per omega < T/2.
 // f(cos theta_n) is evaluated once per quadrature node into shared memory;
 // cos(m theta_n) follows from a rotation by m pi / N_Q per node, so the
@@ -1096,6 +1263,51 @@ int run_kpm_lane_l(const hol_ctx* c, const typename Cx<R>::T2* in, typename Cx<R
                         c->kpm.np, c->kpm.coef, n_rhs, Th, max_np, mode, (R)c->th));
     HOL_CHECK_LAUNCH("k_kpm_lane");
     return HOL_OK;
+}
+
+template <int L>
+int run_kpm_band_l(const hol_ctx* c, const double2* in, double2* out, int n_rhs, int Th,
+                   int max_np, int mode, cudaStream_t s)
+{
+    using K = KBand<L>;
+    if constexpr (!K::OK) {
+        return set_error(HOL_EINVAL, "kpm banded layout: unsupported L=%d", L);
+    } else {
+        const size_t sm = (size_t)max_np * sizeof(double2) +
+                          (size_t)(2 * 2 * K::NB * 2 * L + 2 * L * L) * sizeof(double);
+        static std::atomic<int> limit(0);   // raised once per instantiation (not a stream call)
+        if ((int)sm > limit.load()) {
+            HOL_CUDA(cudaFuncSetAttribute((const void*)k_kpm_band<L>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            limit.store((int)sm);
+        }
+        HOL_CUDA(launch_pdl(c, k_kpm_band<L>, Th * n_rhs, K::THREADS, sm, s, in, out, c->dbar,
+                            c->scal, c->kpm.np, c->kpm.coef, n_rhs, Th, max_np, mode, c->th));
+        HOL_CHECK_LAUNCH("k_kpm_band");
+        return HOL_OK;
+    }
+}
+
+// FP64 KPM in the banded lane layout, for the L that KBand covers
+bool kpm_band_ok(int L)
+{
+    switch (L) {
+#define X(LL) case LL: return KBand<LL>::OK;
+        X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(24) X(28) X(32)
+#undef X
+    }
+    return false;
+}
+
+int run_kpm_band(const hol_ctx* c, const double2* in, double2* out, int n_rhs, int Th, int max_np,
+                 int mode, cudaStream_t s)
+{
+    switch (c->L) {
+#define X(LL) case LL: return run_kpm_band_l<LL>(c, in, out, n_rhs, Th, max_np, mode, s);
+        X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(24) X(28) X(32)
+#undef X
+    }
+    return set_error(HOL_EINVAL, "kpm banded layout: unsupported L=%d", c->L);
 }
 
 // KPM in the lane layout: FP32, any even L
@@ -1236,11 +1448,19 @@ int precond_run(hol_ctx* c, const R* v, R* out, int n_rhs, int mode, const R* rd
             if (rc) return rc;
             done = true;
         }
+    } else {
+        // FP64: the banded lane layout (each problem over several warps: the
+        // one-warp lane layout put a problem's chain of FP64 steps on one
+        // SMSP's share of the FP64 pipe and measured slower than the
+        // shared-memory kernel, 602 against 325 us on the L = 16,
+        // Ltau = 160 trajectory's 2 rhs)
+        if (c->kpm_reg != 0 && !c->exact && kpm_band_ok(c->L)) {
+            rc = run_kpm_band(c, reinterpret_cast<const double2*>(h0),
+                              reinterpret_cast<double2*>(h1), n_rhs, ka.Th, ka.max_np, mode, s);
+            if (rc) return rc;
+            done = true;
+        }
     }
-    // (FP64 stays on the shared-memory kernel: the lane layout puts a
-    // problem's critical chain of FP64 steps on one warp, i.e. one SMSP's
-    // share of the FP64 pipe, and measured slower: 602 against 325 us per
-    // P^{-1} P^{-T} on the L = 16, Ltau = 160 trajectory's 2 rhs)
     if (!done) {
         const int kt = kpm_threads(c);
         const size_t ks = ((size_t)c->N * sizeof(C2) * (c->exact ? 2 : 1) + 15) / 16 * 16 +
