@@ -27,6 +27,7 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "cb.cuh"
@@ -787,10 +788,10 @@ __global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
         }
         __syncthreads();
         int par = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            const bool trans = (pass == 0);
-            if (trans && !(mode & 1)) continue;
-            if (!trans && !(mode & 2)) continue;
+        // one series; the direction is a compile-time constant, so the chain
+        // of dependent steps carries no branch on it
+        auto series = [&](auto trans_c) {
+            constexpr bool trans = decltype(trans_c)::value;
             const float sgn = trans ? -1.0f : 1.0f;    // conj coefficients for the transpose
             CV<CPL> acc[2], prev[2];
             {
@@ -812,7 +813,7 @@ __global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
                 for (int r = 0; r < 2; ++r) {
                     old[r] = cur[r];
                     b[r] = cur[r];
-                    if (trans) {
+                    if constexpr (trans) {
 #pragma unroll
                         for (int e = 0; e < CPL; ++e) {
                             b[r].re[e] *= d[r][e];
@@ -820,7 +821,7 @@ __global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
                         }
                     }
                 }
-                if (trans) {
+                if constexpr (trans) {
                     kc4<L, CPL>(b, g, th, xbuf, par);
                     kc3<CPL>(b, th);
                     kc2<L, CPL>(b, g, th);
@@ -842,7 +843,7 @@ __global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
 #pragma unroll
                     for (int e = 0; e < CPL; ++e) {
                         float br = b[r].re[e], bi = b[r].im[e];
-                        if (!trans) {
+                        if constexpr (!trans) {
                             br *= d[r][e];
                             bi *= d[r][e];
                         }
@@ -858,7 +859,9 @@ __global__ void __launch_bounds__(32 * KGeo<L, CPL>::W)
             }
 #pragma unroll
             for (int r = 0; r < 2; ++r) cur[r] = acc[r];
-        }
+        };
+        if (mode & 1) series(std::true_type{});
+        if (mode & 2) series(std::false_type{});
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const long e = off + (long)(r0 + r) * L + CPL * g.cx;
@@ -947,10 +950,9 @@ __global__ void __launch_bounds__(KLane<L>::THREADS)
     }
     R* xbuf = reinterpret_cast<R*>(cw + max_np);   // [2][32][L]
     __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool trans = (pass == 0);
-        if (trans && !(mode & 1)) continue;
-        if (!trans && !(mode & 2)) continue;
+    // one series; the direction is a compile-time constant
+    auto series = [&](auto trans_c) {
+        constexpr bool trans = decltype(trans_c)::value;
         const R sgn = trans ? R(-1) : R(1);   // conj coefficients for the transpose
         R A[L], B[L], prev[L];
         {
@@ -966,7 +968,7 @@ __global__ void __launch_bounds__(KLane<L>::THREADS)
             R b[L];
 #pragma unroll
             for (int iy = 0; iy < L; ++iy) b[iy] = trans ? t[iy] * d[iy] : t[iy];
-            if (trans)
+            if constexpr (trans)
                 cb_apply_t<R, L>(b, geo, th);
             else
                 cb_apply<R, L>(b, geo, th);
@@ -1004,7 +1006,9 @@ __global__ void __launch_bounds__(KLane<L>::THREADS)
         }
 #pragma unroll
         for (int iy = 0; iy < L; ++iy) t[iy] = part == 0 ? A[iy] - sgn * Bo[iy] : A[iy] + sgn * Bo[iy];
-    }
+    };
+    if (mode & 1) series(std::true_type{});
+    if (mode & 2) series(std::false_type{});
     if (own) {
         R* vout_f = reinterpret_cast<R*>(vout);
 #pragma unroll
