@@ -1031,10 +1031,10 @@ template <int L>
 struct KBand {
     // bands per part: RB = L / NB even, 2 NB lane groups over as many warps
     // as that gives. Measured (P^{-1} P^{-T}, 2 rhs, against the
-    // shared-memory kernel): L = 8 82 / 215 us, 12 114 / 222, 16 173 / 309
-    // (Ltau = 160; 191 with NB = 4), 24 386 / 454, 28 454 / 544, 32 849 /
-    // 985 (Ltau = 200; 862 with NB = 8); L = 20 was slower (320 / 304) and
-    // keeps the shared-memory kernel, as do the sizes not listed
+    // shared-memory kernel): L = 8 82 / 215 us, 12 111 / 223, 16 176 / 308
+    // (Ltau = 160; 191 with NB = 4), 24 364 / 454, 28 432 / 544, 32 808 /
+    // 994 (Ltau = 200; 862 with NB = 8); L = 20 gained nothing (306 / 309)
+    // and keeps the shared-memory kernel, as do the sizes not listed
     static constexpr int NB = L == 4 ? 2 : L == 6 ? 3 : L == 8 ? 4 : L == 10 ? 5 : L == 12 ? 6
                             : L == 14 ? 7 : L == 16 ? 8 : L == 18 ? 3 : L == 24 ? 6 : L == 28 ? 7
                             : L == 32 ? 4 : 0;
@@ -1121,10 +1121,9 @@ __global__ void __launch_bounds__(KBand<L>::THREADS > 0 ? KBand<L>::THREADS : 32
 #pragma unroll
         for (int k = 0; k < RB; ++k) c[k] = fma(th, __shfl_sync(kFull, c[k], partner), c[k]);
     };
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool trans = (pass == 0);
-        if (trans && !(mode & 1)) continue;
-        if (!trans && !(mode & 2)) continue;
+    // one series; the direction is a compile-time constant
+    auto series = [&](auto trans_c) {
+        constexpr bool trans = decltype(trans_c)::value;
         const double sgn = trans ? -1.0 : 1.0;   // conj coefficients for the transpose
         double A[RB], B[RB], prev[RB];
         {
@@ -1140,7 +1139,7 @@ __global__ void __launch_bounds__(KBand<L>::THREADS > 0 ? KBand<L>::THREADS : 32
             double b[RB];
 #pragma unroll
             for (int k = 0; k < RB; ++k) b[k] = trans ? t[k] * d[k] : t[k];
-            if (trans) {   // C^T: colour 4 first
+            if constexpr (trans) {   // C^T: colour 4 first
                 colour4(b);
                 colour3(b);
                 xbond(b, geo.p2);
@@ -1175,7 +1174,9 @@ __global__ void __launch_bounds__(KBand<L>::THREADS > 0 ? KBand<L>::THREADS : 32
             t[k] = part == 0 ? A[k] - sgn * bo : A[k] + sgn * bo;
         }
         __syncthreads();   // xb is rewritten by the next series
-    }
+    };
+    if (mode & 1) series(std::true_type{});
+    if (mode & 2) series(std::false_type{});
     if (live) {
         double* vout_f = reinterpret_cast<double*>(vout);
 #pragma unroll
