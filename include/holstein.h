@@ -524,9 +524,11 @@ int hol_tune(hol_ctx* ctx, int n_rhs, int* best_k, int* best_warps, int* best_ve
  *                       layout (any L: one lane per column, the rows in
  *                       registers, the real and imaginary parts in two lane
  *                       groups). 1 and 2 fall back to the shared-memory
- *                       kernel for other L. Default 2 at L = 32, 1 at
- *                       L = 16, 3 otherwise. The FP64 KPM always uses the
- *                       shared-memory kernel
+ *                       kernel for other L. Default 2 at L = 32, 3
+ *                       otherwise. The FP64 KPM uses the banded lane layout
+ *                       (rows in bands over several warps) where it is
+ *                       built (L = 4-18 even, 24, 28, 32) unless this is 0,
+ *                       else the shared-memory kernel
  *   "persistent_cg"     plain mixed CG chunks in one cooperative launch (0/1)
  *   "pdl"               programmatic dependent launch of the CG iteration
  *                       kernels: each may be scheduled while its predecessor

@@ -286,11 +286,12 @@ extern "C" int hol_create(const hol_params* p, hol_ctx** out)
     c->mv_warps = 4;
     c->mv_vec = c->exact ? 0 : 1;
     // register KPM: two columns per lane at L = 32 (measured 0.126 against
-    // 0.149 ms for P^{-1} P^{-T} on 16 rhs), four at L = 16 (one warp per
-    // problem beats two warps and their barrier per Bbar apply), the lane
-    // layout (one lane per column, real and imaginary parts in two lane
-    // groups) for every other L
-    c->kpm_reg = c->exact ? 0 : (c->L == 32 ? 2 : c->L == 16 ? 1 : 3);
+    // 0.149 ms for P^{-1} P^{-T} on 16 rhs; 47 us against 58 us for the lane
+    // layout on 2 rhs at Ltau = 200), the lane layout (one lane per column,
+    // real and imaginary parts in two lane groups) for every other L (at
+    // L = 16, Ltau = 160, 2 rhs: 25.3 us against 29.0 us for four columns
+    // per lane)
+    c->kpm_reg = c->exact ? 0 : (c->L == 32 ? 2 : 3);
     c->persist = 0;
     c->merged = 0;
     c->fused = 0;
