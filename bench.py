@@ -571,19 +571,25 @@ def unit_rates_block(ctx, xd, vd, bd, Fd, nr, flush, cold, launches=10):
     o64 = torch.empty_like(v64)
     out = {"fp32_fused_mtm_matvecs_per_s": 2 * nr / (cold["median_us"] / 1e6),
            "fp32_fused_mtm_matvecs_per_s_streaming": 2 * nr / (cold["stream_us"] / 1e6)}
+    fp64_peak = hg.hol_fma_peak(hg.HOL_F64)   # GFLOP/s, the FP64 roofline of these kernels
     for name, op in (("fp64_M", hg.HOL_OP_M), ("fp64_MT", hg.HOL_OP_MT)):
         ctx.fermion_matvec(op, v64, o64)
         ms = statistics.median(event_times(lambda: ctx.fermion_matvec(op, v64, o64), flush,
                                            launches))
         out[name + "_us"] = ms * 1e3
         out[name + "_matvecs_per_s"] = nr / (ms / 1e3)
+        # 10 algorithmic flops per element (4 checkerboard colours, one FMA per
+        # site each; the D term's multiply and add)
+        out[name + "_frac_of_fp64_fma"] = 10.0 * nr * ctx.n / (ms / 1e3) / 1e9 / fp64_peak
     ctx.force(vd, bd, Fd, with_bosonic=True)
     ms = statistics.median(event_times(lambda: ctx.force(vd, bd, Fd, with_bosonic=True),
                                        flush, launches))
     out["force_us"] = ms * 1e3
     out["forces_per_s"] = nr / (ms / 1e3)
+    out["fp64_fma_gflops"] = fp64_peak
     out["note"] = ("cold single launches (L2 flushed before each); the FP32 figures are the "
-                   "cold operator block's, single and streaming")
+                   "cold operator block's, single and streaming; the FP64 fractions count 10 "
+                   "flops per element against the measured FP64 FMA rate")
     return out
 
 
