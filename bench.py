@@ -883,9 +883,9 @@ def chains_leg(dev, n_rv=128, precs=None, repeats=3):
     import paper_2203_01291_gb300 as hg
     precs = (hg.HOL_F32, hg.HOL_F64) if precs is None else precs
     ws = hi.chain_workloads(8, 120)
-    # probes solved in blocks of 64 (20.5 against 19.1 measurements/s in
-    # blocks of 16; the concurrent chains already fill the GPU)
-    ctxs = [hg.Context.from_workload(w, max_rhs=64) for w in ws]
+    # all 128 probes of a chain in one block solve (23.8 against 22.8
+    # measurements/s in blocks of 64, 19.1 in blocks of 16)
+    ctxs = [hg.Context.from_workload(w, max_rhs=n_rv) for w in ws]
     out = {"workload": "48 chains, L in {8..28} x 8, Ltau=120; one trajectory (N_t=20, n_t=4, "
                        "PCG, forces 1e-5, action 1e-10) per chain in each precision (graph "
                        "path; the host-thread path for comparison), and one 128-probe "
@@ -933,7 +933,7 @@ def chains_leg(dev, n_rv=128, precs=None, repeats=3):
                 out["fp64"]["trajectories_per_s"]
         for c, x in zip(ctxs, xs):
             c.set_field(x)
-            c.tune(64)                # shapes for the probe blocks (outside the timed region)
+            c.tune(n_rv)              # shapes for the probe block (outside the timed region)
         xis = [torch.tensor(hi.z2_vectors(w, n_rv, seed=w.seed + 3), device=dev) for w in ws]
         Gxis = [torch.empty_like(xi) for xi in xis]
         G2s = [torch.empty(2 * w.Ltau, w.L, w.L, dtype=torch.float64, device=dev) for w in ws]
