@@ -939,13 +939,15 @@ def chains_leg(dev, n_rv=128, precs=None, repeats=3):
         G2s = [torch.empty(2 * w.Ltau, w.L, w.L, dtype=torch.float64, device=dev) for w in ws]
         mo = hg.hol_cg_opts(1e-8, 100000, 0, hg.HOL_F32, 50, 10)
         meas = {}
-        for path in ("graph", "threads"):
+        for path in ("graph", "graph8", "threads"):
             times = []
             for rep in range(2):                    # the first pass warms up
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 if path == "graph":
                     hg.measure_batch_graph(ctxs, xis, Gxis, G2s, mo)
+                elif path == "graph8":   # at most 8 chains in flight
+                    hg.measure_batch_graph(ctxs, xis, Gxis, G2s, mo, concurrency=8)
                 else:
                     hg.measure_batch(ctxs, xis, Gxis, G2s, mo, n_threads=8)
                 torch.cuda.synchronize()
@@ -960,6 +962,7 @@ def chains_leg(dev, n_rv=128, precs=None, repeats=3):
                 "measurement_path": "all 48 chains' measurements (probe solves device-driven, "
                                     "FFT accumulation) in one captured graph "
                                     "(measure_batch_graph)",
+                "measurements_per_s_graph_8_in_flight": len(ws) / meas["graph8"],
                 "measurements_per_s_host_threads": len(ws) / meas["threads"]})
     return out
 

@@ -407,13 +407,15 @@ int cg_solve_graph(hol_ctx* ctx, const double* b, double* v, int n_rhs, const ho
  * solves graph-driven as in cg_solve_graph) and launched once. Arguments per
  * chain as stochastic_measure (xi[k], Gxi[k]: [n_rv][T_k][N_k]; G2[k]; G4[k]
  * when four_point != 0); no iteration counts. opts needs what cg_solve_graph
- * needs. Each chain's G2 / G4 / Gxi are bitwise those of stochastic_measure.
- * HOL_ENOTCONV or HOL_ENUMERIC names the first failing chain. Synchronises
- * `stream`.
+ * needs. concurrency: at most this many chains in flight (chain k follows
+ * chain k - concurrency; 0 = all chains at once). Each chain's G2 / G4 / Gxi
+ * are bitwise those of stochastic_measure, whatever the concurrency.
+ * HOL_ENOTCONV or HOL_ENUMERIC names the first failing chain; concurrency
+ * < 0 is HOL_EINVAL. Synchronises `stream`.
  */
 int measure_batch_graph(hol_ctx* const* ctxs, int n_chains, const double* const* xi, int n_rv,
                         const hol_cg_opts* opts, double* const* Gxi, double* const* G2,
-                        double* const* G4, int four_point, void* stream);
+                        double* const* G4, int four_point, int concurrency, void* stream);
 int hmc_batch_graph(hol_ctx* const* ctxs, int n_chains, double* const* x,
                     const double* const* R_pf, const double* const* R_p, int n_pf,
                     const hol_md_opts* opts, const double* u, int* accepted, double* dH,

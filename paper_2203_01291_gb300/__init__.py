@@ -285,15 +285,17 @@ def hmc_batch_graph(contexts, xs, R_pfs, R_ps, opts: hol_md_opts, us):
 
 
 def measure_batch_graph(contexts, xis, Gxis, G2s, opts: hol_cg_opts, G4s=None,
-                        four_point: int = 0) -> None:
+                        four_point: int = 0, concurrency: int = 0) -> None:
     """stochastic_measure for every chain, all chains in one captured CUDA
-    graph (include/holstein.h, measure_batch_graph)."""
+    graph, at most `concurrency` chains in flight (0: all; include/holstein.h,
+    measure_batch_graph)."""
     n = len(contexts)
     hs = (ctypes.c_void_p * n)(*[c.handle.value for c in contexts])
     n_rv = xis[0].numel() // contexts[0].n
     g4 = _ptrs(G4s) if G4s is not None else None
     _check(load().measure_batch_graph(hs, n, _ptrs(xis), n_rv, ctypes.byref(opts), _ptrs(Gxis),
-                                      _ptrs(G2s), g4, int(four_point), _stream()))
+                                      _ptrs(G2s), g4, int(four_point), int(concurrency),
+                                      _stream()))
 
 
 def measure_batch(contexts, xis, Gxis, G2s, opts: hol_cg_opts, G4s=None, four_point: int = 0,

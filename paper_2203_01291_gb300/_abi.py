@@ -89,7 +89,7 @@ SIGNATURES = {
                              ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D), _VP]),
     "measure_batch_graph": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), _I,
                                  ctypes.POINTER(hol_cg_opts), ctypes.POINTER(_VP),
-                                 ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _VP]),
+                                 ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I, _I, _VP]),
     "measure_batch": (_I, [ctypes.POINTER(_VP), _I, ctypes.POINTER(_VP), _I,
                            ctypes.POINTER(hol_cg_opts), ctypes.POINTER(_VP), ctypes.POINTER(_VP),
                            ctypes.POINTER(_VP), _I, _I]),

@@ -73,19 +73,23 @@ int capture(cudaStream_t s, Graph& g, F&& body)
 }
 
 // Capture per-chain work on forked streams: origin -> fork -> each chain on
-// its stream -> join back into origin. Every forked stream is joined, also
-// after a failure, so the capture can always be ended.
+// a stream -> join back into origin. With width w < n, chain k runs on
+// stream k % w after the chains before it on that stream (at most w chains
+// in flight; their working sets then share L2 with fewer others). Every
+// forked stream is joined, also after a failure, so the capture can always
+// be ended.
 template <class F>
-int fork_join(cudaStream_t origin, Streams& st, int n, F&& work)
+int fork_join(cudaStream_t origin, Streams& st, int n, F&& work, int width = 0)
 {
+    const int w = (width > 0 && width < n) ? width : n;
     HOL_CUDA(cudaEventRecord(st.e[0], origin));
+    for (int j = 0; j < w; ++j) HOL_CUDA(cudaStreamWaitEvent(st.s[j], st.e[0], 0));
     int first_rc = HOL_OK;
-    for (int k = 0; k < n; ++k) {
-        cudaStream_t sk = st.s[k];
-        HOL_CUDA(cudaStreamWaitEvent(sk, st.e[0], 0));
-        if (first_rc == HOL_OK) first_rc = work(k, sk);
-        HOL_CUDA(cudaEventRecord(st.e[1 + k], sk));
-        HOL_CUDA(cudaStreamWaitEvent(origin, st.e[1 + k], 0));
+    for (int k = 0; k < n; ++k)
+        if (first_rc == HOL_OK) first_rc = work(k, st.s[k % w]);
+    for (int j = 0; j < w; ++j) {
+        HOL_CUDA(cudaEventRecord(st.e[1 + j], st.s[j]));
+        HOL_CUDA(cudaStreamWaitEvent(origin, st.e[1 + j], 0));
     }
     return first_rc;
 }
@@ -271,13 +275,15 @@ extern "C" int hmc_batch_graph(hol_ctx* const* ctxs, int n_chains, double* const
 extern "C" int measure_batch_graph(hol_ctx* const* ctxs, int n_chains, const double* const* xi,
                                    int n_rv, const hol_cg_opts* opts, double* const* Gxi,
                                    double* const* G2, double* const* G4, int four_point,
-                                   void* stream)
+                                   int concurrency, void* stream)
 {
     HOL_TRACE("measure_batch_graph");
     if (!ctxs || !xi || !opts || !Gxi || !G2 || n_chains < 1)
         return set_error(HOL_EINVAL, "measure_batch_graph: null argument or no chains");
     if (four_point && !G4)
         return set_error(HOL_EINVAL, "measure_batch_graph: four-point products need G4");
+    if (concurrency < 0)
+        return set_error(HOL_EINVAL, "measure_batch_graph: concurrency must be >= 0");
     for (int k = 0; k < n_chains; ++k) {
         hol_ctx* c = ctxs[k];
         if (!c || !xi[k] || !Gxi[k] || !G2[k] || (four_point && !G4[k]))
@@ -303,10 +309,13 @@ extern "C" int measure_batch_graph(hol_ctx* const* ctxs, int n_chains, const dou
         std::vector<CaptureScope*> scopes;
         for (int k = 0; k < n_chains; ++k) scopes.push_back(new CaptureScope(ctxs[k]));
         rc = capture(os, g, [&]() {
-            return fork_join(os, st, n_chains, [&](int k, cudaStream_t sk) {
-                return measure_run(ctxs[k], xi[k], n_rv, opts, Gxi[k], G2[k],
-                                   four_point ? G4[k] : nullptr, four_point, nullptr, sk);
-            });
+            return fork_join(
+                os, st, n_chains,
+                [&](int k, cudaStream_t sk) {
+                    return measure_run(ctxs[k], xi[k], n_rv, opts, Gxi[k], G2[k],
+                                       four_point ? G4[k] : nullptr, four_point, nullptr, sk);
+                },
+                concurrency);
         });
         for (CaptureScope* p : scopes) delete p;
     }

@@ -124,10 +124,12 @@ def test_hmc_batch_graph_equals_sequential(prec, precond, n_steps):
             c.close()
 
 
-def test_measure_batch_graph_equals_stochastic_measure():
+@pytest.mark.parametrize("concurrency", [0, 3])
+def test_measure_batch_graph_equals_stochastic_measure(concurrency):
     """Every chain's 2-point function, Wick products and probe solutions from
     the one-graph batched measurement are bitwise those of stochastic_measure
-    run chain by chain (mixed precision, probes in blocks of max_rhs)."""
+    run chain by chain (mixed precision, probes in blocks of max_rhs), with
+    all chains in flight or at most three."""
     ws = _chains()[:4]
     opts = hg.hol_cg_opts(1e-10, 100000, 0, hg.HOL_F32, 50, 10)
     ctxs = [hg.Context.from_workload(w, max_rhs=4) for w in ws]
@@ -145,7 +147,8 @@ def test_measure_batch_graph_equals_stochastic_measure():
             Gxis.append(torch.full_like(xi, float("nan")))
             G2s.append(torch.full_like(G2, float("nan")))
             G4s.append(torch.full_like(G4, float("nan")))
-        hg.measure_batch_graph(ctxs, xis, Gxis, G2s, opts, G4s=G4s, four_point=7)
+        hg.measure_batch_graph(ctxs, xis, Gxis, G2s, opts, G4s=G4s, four_point=7,
+                               concurrency=concurrency)
         torch.cuda.synchronize()
         for k in range(len(ws)):
             assert np.array_equal(Gxis[k].cpu().numpy(), refs[k][0])
