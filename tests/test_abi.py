@@ -237,3 +237,21 @@ def test_static_operator_refuses_bad_arguments_on_the_host(case):
         assert "scratch" in msg
     if case.startswith("overlap"):
         assert "overlap" in msg
+
+
+def test_every_documented_launch_option_is_implemented_both_ways():
+    """The launch options listed in include/holstein.h (hol_set_option) are
+    exactly those hol_set_option and hol_get_option accept: a documented
+    option the library does not know, or an accepted one the header does not
+    describe, fails here."""
+    header = open(os.path.join(ROOT, "include", "holstein.h")).read()
+    a = header.index("Runtime launch options of a context")
+    b = header.index("*/", a)
+    documented = set(re.findall(r'^ \*   "([a-z0-9_]+)"', header[a:b], flags=re.M))
+    src = open(os.path.join(ROOT, "paper_2203_01291_gb300", "csrc", "context.cu")).read()
+    s0 = src.index("int hol_set_option(")
+    g0 = src.index("int hol_get_option(")
+    setter = set(re.findall(r'is\("([a-z0-9_]+)"\)', src[s0:g0]))
+    getter = set(re.findall(r'is\("([a-z0-9_]+)"\)', src[g0:]))
+    assert documented and documented == setter == getter, (documented ^ setter,
+                                                           documented ^ getter)
