@@ -255,3 +255,38 @@ def test_every_documented_launch_option_is_implemented_both_ways():
     getter = set(re.findall(r'is\("([a-z0-9_]+)"\)', src[g0:]))
     assert documented and documented == setter == getter, (documented ^ setter,
                                                            documented ^ getter)
+
+
+def _prototypes():
+    """name -> number of parameters of every function declared in include/."""
+    out = {}
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^(?!typedef|#)[\w \t*]+?\b(\w+)\s*\(([^;{]*?)\)\s*;", src,
+                             flags=re.M | re.S):
+            params = m.group(2).strip()
+            out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_and_definitions_match_the_header_prototypes():
+    """Every function the header declares has a definition in csrc/ with
+    extern "C" linkage and the ctypes prototype of the binding takes as many
+    arguments as the header's declaration (an argument added to one side
+    only fails here, without a GPU); no extern "C" definition is left out of
+    the header."""
+    from paper_2203_01291_gb300 import _abi
+    protos = _prototypes()
+    assert set(protos) == set(declared_functions())
+    for name, n in protos.items():
+        assert len(_abi.SIGNATURES[name][1]) == n, (name, n, len(_abi.SIGNATURES[name][1]))
+    defined = set()
+    csrc = os.path.join(ROOT, "paper_2203_01291_gb300", "csrc")
+    for f in os.listdir(csrc):
+        if f.endswith((".cu", ".cuh")):
+            defined |= set(re.findall(r'extern "C"[\w \t*]+?\b(\w+)\s*\(',
+                                      open(os.path.join(csrc, f)).read()))
+    assert defined == set(protos), (defined ^ set(protos))
