@@ -86,8 +86,8 @@ def test_precond_fp32_kpm_variants(kpm, queue, L, T):
 
 
 @pytest.mark.parametrize("L,T,nr", [(4, 12, 3), (6, 10, 3), (8, 12, 3), (10, 8, 2), (12, 12, 3),
-                                    (14, 6, 1), (16, 8, 3), (20, 8, 1), (24, 6, 2), (28, 6, 3),
-                                    (30, 4, 1), (32, 6, 2)])
+                                    (14, 6, 1), (16, 8, 3), (18, 6, 2), (20, 8, 1), (22, 4, 1),
+                                    (24, 6, 2), (26, 4, 3), (28, 6, 3), (30, 4, 1), (32, 6, 2)])
 def test_precond_fp32_lane_layout_vs_oracle(L, T, nr):
     """The lane-layout FP32 KPM (kpm_registers 3: lane = column, rows in
     registers, real and imaginary parts in two lane groups whose recurrences
