@@ -93,3 +93,19 @@ def test_bench_line_is_strict_json():
     out = b.strict_json(obj)
     assert out == {"a": None, "b": [1.5, None, {"c": None}], "d": 2, "e": "x"}
     json.loads(json.dumps(out, allow_nan=False))
+
+
+def test_profile_summaries_name_their_commands_and_committed_files_only():
+    """Every committed ncu summary gives the command that made it, clock
+    control off, and runs committed files only (no scratch scripts)."""
+    import glob
+    files = sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md")))
+    assert files
+    for path in files:
+        text = open(path).read()
+        assert "Command" in text, path
+        assert "_work" not in text, path
+        joined = text.replace("\\\n", " ")   # shell line continuations
+        for line in joined.splitlines():
+            if line.strip().startswith("ncu "):
+                assert "--clock-control none" in line, (path, line)
