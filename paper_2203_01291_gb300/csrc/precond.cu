@@ -16,13 +16,23 @@
 // inverse transform.
 //
 // Kernels:
-//   k_kpm_coeffs  N_P(omega) (Eq. (NP_heuristic), a1 = a2 = 1, floored at 1)
-//                 and c_m by Chebyshev-Gauss quadrature with N_Q = 2 N_P
-//                 points (Eq. (Cheby-Gauss)), one block per omega.
+//   k_kpm_coeffs  N_P(omega) (Eq. (NP_heuristic); a1 = a2 = 1 unless the
+//                 launch options say otherwise; floored at 1) and c_m by
+//                 Chebyshev-Gauss quadrature with N_Q = 2 N_P points
+//                 (Eq. (Cheby-Gauss)), one block per omega.
 //   k_tau_fwd     twisted DFT along tau, tiles of TS sites x T slices in
 //                 shared memory, Stockham mixed-radix passes (radix 4,2,3,5,7).
+//   k_tau_fwd_upd the same with the PCG vector update fused into its loads.
+//   k_kpm_reg     FP32, L = 16, 32: one (omega, rhs) problem per block, two
+//                 rows and two or four complex columns per lane.
+//   k_kpm_lane    FP32, any L: lane = column, rows in registers, the real and
+//                 imaginary parts in two lane groups (no barrier per step).
+//   k_kpm_band    FP64: the lane layout with the rows in bands over several
+//                 warps (one exchange per Bbar apply).
 //   k_kpm         one block per (omega, rhs); the N-vector lives in shared
-//                 memory, the checkerboard colours are applied pair-parallel.
+//                 memory, the checkerboard colours are applied pair-parallel
+//                 (the exact propagator, and FP64 where no band layout is
+//                 built).
 //   k_tau_inv     inverse twisted transform, real output, optional r.z sums.
 #include <math.h>
 #include <stdlib.h>
