@@ -8,10 +8,13 @@
 //   2. update: alpha = (r.z)/(p.q), x += alpha p, r -= alpha q and the partial
 //      sums of the new r.r;
 //   3. (preconditioned only) z = P^{-1} P^{-T} r with the partial sums of r.z
-//      (precond.cu); without a preconditioner z is r itself.
+//      (precond.cu); without a preconditioner z is r itself. By default the
+//      update of step 2 runs inside the forward transform of step 3
+//      (k_tau_fwd_upd, option fused_pc_update).
 // alpha and beta are recomputed by every consumer from the partial sums in a
 // fixed order, so no extra launch or grid barrier sits on the critical path.
-// All dot products accumulate in FP64.
+// Dot products are summed in FP64 across blocks; inside a block the mixed
+// path sums FP32 products as compensated float pairs (cb.cuh, F2).
 //
 // Mixed precision (opts->prec == HOL_F32): x is an FP32 increment e on top
 // of the FP64 solution v; every `reliable_every` iterations, and whenever the
